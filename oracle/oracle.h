@@ -1,0 +1,128 @@
+/*
+ * HARMRAD oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, FP64 CPU restatement of one GRRMHD+M1 time step of
+ * McKinney, Tchekhovskoy, Sadowski & Narayan (2014), "Three-dimensional
+ * GRRMHD simulation of super-Eddington accretion, using a new code HARMRAD
+ * with M1 closure".  It exists only so that tests, the smoke check and the
+ * benchmark's CPU-baseline leg can check and time the CUDA library against an
+ * independent implementation.  It shares no code, header or constant table
+ * with the CUDA path, and nothing in the product may call it.
+ *
+ * Conventions (paper Sec. 2-4): c = G = M = 1, Heaviside-Lorentz B.
+ * Primitive vector P (12 doubles per zone, index order fixed below):
+ *   rho0, u_g, u~^1..3 (ZAMO-relative gas 4-velocity), B^1..3 (lab field),
+ *   Ebar (radiation-frame energy density), u~^1..3_rad.
+ * Conserved vector U (densitised by sqrt(-g)):
+ *   rho0 u^t, T^t_t + rho0 u^t, T^t_i, B^i, R^t_t, R^t_i.
+ * Arrays passed through this API hold active zones only, layout
+ * [12][n3][n2][n1] (i fastest).
+ *
+ * Pinned by tests/test_oracle_pins.py (closed forms, textbook SR-MHD, M1
+ * closure identities, exact scalar roots, conservation).  Parity unpinned:
+ * the PPM shock flattener (its constants beyond SP0 = 0.75 are not in the
+ * paper), the polar-axis ghost rule and the floor procedure are readings of
+ * the paper that only oracle-versus-library agreement checks.
+ */
+#ifndef HARMRAD_ORACLE_H
+#define HARMRAD_ORACLE_H
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+  int n[3];               /* active zones per direction (1 = degenerate) */
+  double x0[3], dx[3];    /* uniform internal coordinates of the lower edge */
+  int metric;             /* 0 Minkowski Cartesian, 1 Kerr-Schild + MSP map */
+  double a_spin, R0, hslope;
+  int bc[6];              /* lower/upper per direction: 0 periodic, 1 outflow, 2 polar */
+  double gam, a_rad, courant;
+  int opacity;            /* 0 kappa = k0*rho (per length), 1 Kramers k0*rho^2*T^-3.5 */
+  double kappa_abs0, kappa_es0, kappa_scale, T_kappa_min;
+  int recon;              /* 0 PPM, 1 MC */
+  int flux;               /* 0 LAXF, 1 HLL */
+  double gamma_rad_max, gamma_gas_max;
+  double floor_rho0, floor_rho_pow, floor_u0, floor_u_pow;
+  double bsq_rho_max, bsq_u_max, u_rho_max;
+  int newton_max;
+  double newton_tol;
+} orc_params;
+
+/* Per-zone solver outcome codes (same meaning as the library's status byte). */
+enum { ORC_OK_PMHD = 0, ORC_OK_URAD = 1, ORC_BACKUP = 2 };
+
+typedef struct {
+  double e_T;      /* total normalised error of the accepted solution */
+  int iters_pmhd;  /* Newton iterations taken by the PMHD attempt */
+  int iters_urad;  /* Newton iterations taken by the URAD attempt (0 if none) */
+  int method;      /* ORC_OK_PMHD, ORC_OK_URAD or ORC_BACKUP */
+  int neg_erad;    /* 1 if the accepted solution hit the TYPE2 negative-energy branch */
+} orc_implicit_info;
+
+/* --- grid-level driver --------------------------------------------------- */
+void*  orc_create(const orc_params* p);
+void   orc_destroy(void* ctx);
+void   orc_set_prims(void* ctx, const double* P);
+void   orc_get_prims(void* ctx, double* P);
+double orc_cfl_dt(void* ctx);
+/* One full RK3 step; dt <= 0 means use the CFL time step. Returns the dt used. */
+double orc_step(void* ctx, double dt);
+/* Per-zone status bytes of the last step, worst over its three stages ([n3][n2][n1]). */
+void   orc_get_status(void* ctx, unsigned char* st);
+/* Per-zone Newton iteration totals summed over the three stages of the last step. */
+void   orc_get_iters(void* ctx, int* it);
+/* Counts over the last step: [0] PMHD-accepted, [1] URAD-accepted, [2] back-up,
+ * [3] total Newton iterations, [4] zone-stages solved. */
+void   orc_get_counts(void* ctx, long long* c);
+/* Face fluxes of one direction after the last call to orc_compute_fluxes
+ * (debug/test hook): computes ghost fill + fluxes (+flux-CT) for the current
+ * prims and copies F for faces [0..n_d] x active transverse range,
+ * layout [12][n3'][n2'][n1'] where n_d' = n_d + 1. */
+void   orc_compute_fluxes(void* ctx, int dir, double* F);
+/* Ghost-inclusive prim copy (layout [12][N3][N2][N1]); debug/test hook. */
+void   orc_get_prims_with_ghosts(void* ctx, double* P, int fill_ghosts);
+
+/* --- point-wise physics (for pins) --------------------------------------- */
+/* Metric at internal coordinates x[4] = (t, x1, x2, x3). */
+void   orc_metric(const orc_params* p, const double* x, double* gcov16,
+                  double* gcon16, double* gdet, double* alpha);
+/* Connection Gamma^l_{m k} at x, layout [l][m][k]. */
+void   orc_connection(const orc_params* p, const double* x, double* gam64);
+/* U(P) and geometric source SM(P) at x (12 each). */
+void   orc_prim_to_cons(const orc_params* p, const double* x, const double* P,
+                        double* U, double* SM);
+/* Flux along direction d (1..3) at x, plus gas and radiation wave speeds
+ * (vmin,vmax)[gas], (vmin,vmax)[rad]. */
+void   orc_flux(const orc_params* p, const double* x, int d, const double* P,
+                double* F, double* speeds4);
+/* Full mixed stress tensors T^mu_nu and R^mu_nu ([mu][nu], 16 each). */
+void   orc_stress(const orc_params* p, const double* x, const double* P,
+                  double* T16, double* R16);
+/* Covariant four-force G_nu (Eq. Gcov) for prims P at x. */
+void   orc_four_force(const orc_params* p, const double* x, const double* P,
+                      double* G4);
+/* M1 inversion from R^t_nu (4) to (Ebar, u~^i_rad) (4). limiter: 0 BASIC, 2 TYPE2.
+ * Returns 1 if the limiter saw E_rad <= 0. */
+int    orc_rad_invert(const orc_params* p, const double* x, const double* Rt,
+                      int limiter, double* Prad);
+/* Gas 1D_W inversion from U (12, densitised) using guess prims Pg (12);
+ * writes prims 0..4 of Pout and copies B. Returns 0 on success. */
+int    orc_gas_invert(const orc_params* p, const double* x, const double* U,
+                      const double* Pg, double tol, double* Pout);
+/* Implicit four-force solve of one zone: U* (12, densitised), guess P_s,
+ * h = b_s*dt.  Writes the new prims and info. */
+void   orc_implicit_zone(const orc_params* p, const double* x, const double* Ustar,
+                         const double* Ps, double h, double* Pout,
+                         orc_implicit_info* info);
+/* Residual of the PMHD system at gas unknowns xg = (u_g, u~^i):
+ * E[4] (gas rows), eT, eI.  Test hook. */
+void   orc_pmhd_residual(const orc_params* p, const double* x, const double* Ustar,
+                         double h, const double* xg, double* E4, double* eT,
+                         double* eI);
+/* Levermore Eddington factor xi(f) (Sec. 3.1). */
+double orc_levermore_xi(double f);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

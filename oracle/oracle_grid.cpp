@@ -1,0 +1,707 @@
+// HARMRAD oracle, grid driver and C API -- TEST INFRASTRUCTURE ONLY.
+//
+// One full time step as restated from Sec. 4 of McKinney et al. (2014):
+// the RK3 method with the same coefficients for the explicit and implicit
+// parts (Sec. 4.1), each sub-step running the algorithm of Sec. 4.2 --
+// ghost fill, U(P), geometric source, reconstruction (Sec. 4.3), face fluxes
+// and wave speeds (Sec. 4.4), HLL/LAXF (Eqs. hll, lax), flux-CT EMFs, the
+// update and the implicit solve with back-ups (Sec. 4.7-4.11).  Plain loops,
+// FP64, one thread.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "oracle_internal.h"
+
+namespace orc {
+
+namespace {
+
+const int NG = 4;  // ghost depth (PPM needs +-4 cells)
+
+struct Ctx {
+  orc_params p;
+  int n[3], ng[3], N[3];
+  long ntot;
+  std::vector<double> P;    // [NP][ntot], ghosts included
+  std::vector<double> Un;   // [NP][ntot]
+  std::vector<double> F[3]; // face fluxes [NP][ntot], face f of cell idx is its lower face
+  std::vector<double> spd[3];  // per-face max signal speed
+  std::vector<double> flat[3]; // [2][ntot] stored flattener (gas, rad), max over sub-steps
+  std::vector<Geom> geo;       // cell-centre geometry, ghosts included
+  std::vector<double> gam;     // cell-centre connection [ntot][64] (KS only)
+  std::vector<unsigned char> status;  // active zones
+  std::vector<int> iters;             // active zones
+  long long counts[5];
+};
+
+inline long idx(const Ctx& c, int i, int j, int k) {
+  return ((long)(k + c.ng[2]) * c.N[1] + (j + c.ng[1])) * c.N[0] + (i + c.ng[0]);
+}
+inline long aidx(const Ctx& c, int i, int j, int k) {
+  return ((long)k * c.n[1] + j) * c.n[0] + i;
+}
+inline double xc(const Ctx& c, int d, int i) { return c.p.x0[d] + (i + 0.5) * c.p.dx[d]; }
+inline double xf(const Ctx& c, int d, int i) { return c.p.x0[d] + i * c.p.dx[d]; }
+
+// ---------------------------------------------------------------- boundaries
+// Ghost fill in direction order 1, 2, 3 so that edges and corners are filled
+// from already-filled data.  Periodic: wrap.  Outflow: copy the last active
+// zone and clamp the normal velocities so nothing flows in from the ghost.
+// Polar (direction 2 only): mirror across the axis, taking the zone on the
+// opposite side in phi (shift n3/2) and negating the theta components.
+void fill_ghosts(Ctx& c, std::vector<double>& P) {
+  for (int d = 0; d < 3; ++d) {
+    if (c.n[d] == 1) continue;
+    int lo[3], hi[3];
+    for (int e = 0; e < 3; ++e) {
+      if (e < d) {
+        lo[e] = -c.ng[e];
+        hi[e] = c.n[e] + c.ng[e];
+      } else {
+        lo[e] = 0;
+        hi[e] = c.n[e];
+      }
+    }
+    for (int side = 0; side < 2; ++side) {
+      int bc = c.p.bc[2 * d + side];
+      for (int g = 0; g < c.ng[d]; ++g) {
+        int gi = side == 0 ? -1 - g : c.n[d] + g;
+        int a0 = d == 0 ? 0 : lo[0], a1 = d == 0 ? 1 : hi[0];
+        int b0 = d == 1 ? 0 : lo[1], b1 = d == 1 ? 1 : hi[1];
+        int e0 = d == 2 ? 0 : lo[2], e1 = d == 2 ? 1 : hi[2];
+        for (int k = e0; k < e1; ++k)
+          for (int j = b0; j < b1; ++j)
+            for (int i = a0; i < a1; ++i) {
+              int dst[3] = {i, j, k}, src[3] = {i, j, k};
+              dst[d] = gi;
+              double sign_d = 1.0;
+              int clamp = 0;
+              if (bc == 0) {
+                src[d] = side == 0 ? c.n[d] - 1 - g : g;
+              } else if (bc == 1) {
+                src[d] = side == 0 ? 0 : c.n[d] - 1;
+                clamp = side == 0 ? -1 : 1;
+              } else {
+                src[d] = side == 0 ? g : c.n[d] - 1 - g;
+                if (c.n[2] > 1) src[2] = (k + c.n[2] / 2) % c.n[2];
+                sign_d = -1.0;
+              }
+              long s = idx(c, src[0], src[1], src[2]);
+              long t = idx(c, dst[0], dst[1], dst[2]);
+              for (int q = 0; q < NP; ++q) P[(long)q * c.ntot + t] = P[(long)q * c.ntot + s];
+              if (sign_d < 0.0) {
+                P[(long)(U1 + d) * c.ntot + t] *= -1.0;
+                P[(long)(B1 + d) * c.ntot + t] *= -1.0;
+                P[(long)(UR1 + d) * c.ntot + t] *= -1.0;
+              }
+              if (clamp != 0) {
+                for (int q : {U1 + d, UR1 + d}) {
+                  double& v = P[(long)q * c.ntot + t];
+                  if (clamp < 0) v = std::min(v, 0.0);
+                  else v = std::max(v, 0.0);
+                }
+              }
+            }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------ reconstruction
+// Monotonised-central slope.
+double mc_slope(double qm, double q0, double qp) {
+  double dl = q0 - qm, dr = qp - q0, dc = 0.5 * (qp - qm);
+  if (dl * dr <= 0.0) return 0.0;
+  double m = std::min(std::fabs(dc), std::min(2.0 * std::fabs(dl), 2.0 * std::fabs(dr)));
+  return dc > 0.0 ? m : -m;
+}
+
+// PPM parabola of the centre cell of a 5-point stencil s[0..4] (Colella &
+// Woodward 1984 without contact steepening), flattened by chi, then made
+// monotone.  Returns the left and right edge values of the centre cell.
+void ppm_cell(const double s[5], double chi, double* aL, double* aR) {
+  double dm = mc_slope(s[0], s[1], s[2]);
+  double d0 = mc_slope(s[1], s[2], s[3]);
+  double dp = mc_slope(s[2], s[3], s[4]);
+  double l = 0.5 * (s[1] + s[2]) - (d0 - dm) / 6.0;
+  double r = 0.5 * (s[2] + s[3]) - (dp - d0) / 6.0;
+  double q = s[2];
+  l = (1.0 - chi) * l + chi * q;
+  r = (1.0 - chi) * r + chi * q;
+  if ((r - q) * (q - l) <= 0.0) {
+    l = q;
+    r = q;
+  } else {
+    double dd = r - l;
+    double m6 = 6.0 * (q - 0.5 * (l + r));
+    if (dd * m6 > dd * dd) l = 3.0 * q - 2.0 * r;
+    else if (-dd * dd > dd * m6) r = 3.0 * q - 2.0 * l;
+  }
+  *aL = l;
+  *aR = r;
+}
+
+// Shock flattener (Sec. 4.3): per cell, for GAS (gas pressure, sqrt(-g) u^d)
+// and RAD (radiation pressure, sqrt(-g) u^d_rad); each pressure is blended
+// toward the total with weight w = min(1, 2 tau) of the cell.
+struct FlatIn {
+  double pg, pr, vg, vr, w;
+};
+double ftilde(const FlatIn* c, int m, bool gas, double w) {
+  auto pe = [&](int o) { return gas ? c[m + o].pg + w * c[m + o].pr : c[m + o].pr + w * c[m + o].pg; };
+  auto ve = [&](int o) { return gas ? c[m + o].vg : c[m + o].vr; };
+  double dp1 = pe(1) - pe(-1), dp2 = pe(2) - pe(-2);
+  double dv = ve(1) - ve(-1);
+  if (std::fabs(dp1) > 0.33 * std::min(pe(1), pe(-1)) && dv < 0.0) {
+    double sp = dp2 != 0.0 ? dp1 / dp2 : 0.0;
+    return std::max(0.0, std::min(1.0, 10.0 * (sp - 0.75)));
+  }
+  return 0.0;
+}
+
+// Flattener of cell m of the stencil array (needs m-3..m+3).
+void flattener(const FlatIn* c, int m, double* fg, double* fr) {
+  double g0 = ftilde(c, m, true, c[m].w), r0 = ftilde(c, m, false, c[m].w);
+  double wg = c[m].w;
+  double pg1 = c[m + 1].pg + wg * c[m + 1].pr, pgm = c[m - 1].pg + wg * c[m - 1].pr;
+  double pr1 = c[m + 1].pr + wg * c[m + 1].pg, prm = c[m - 1].pr + wg * c[m - 1].pg;
+  int sg = (pg1 - pgm) < 0.0 ? 1 : -1;
+  int sr = (pr1 - prm) < 0.0 ? 1 : -1;
+  double g = std::max(g0, ftilde(c, m + sg, true, c[m + sg].w));
+  double r = std::max(r0, ftilde(c, m + sr, false, c[m + sr].w));
+  double mx = std::max(g, r);
+  *fg = (1.0 - wg) * g + wg * mx;
+  *fr = (1.0 - wg) * r + wg * mx;
+}
+
+bool weighted_var(const Ctx& c, int d, int q) {
+  if (c.p.metric != 1 || d == 1) return false;
+  return (q >= U1 && q <= B3) || (q >= UR1 && q <= UR3);
+}
+
+// Face fluxes along direction d (0-based) for every face that the update or
+// the flux-CT averaging needs; stores the per-face signal speed.  When
+// use_stored is true the flattener is max-ed with (and written back to) the
+// value stored from earlier sub-steps of this step.
+void compute_fluxes(Ctx& c, int d, bool use_stored) {
+  const orc_params& p = c.p;
+  int lo[3], hi[3];
+  for (int e = 0; e < 3; ++e) {
+    if (e == d) {
+      lo[e] = 0;
+      hi[e] = c.n[e] + 1;
+    } else if (c.n[e] > 1) {
+      lo[e] = -1;
+      hi[e] = c.n[e] + 1;
+    } else {
+      lo[e] = 0;
+      hi[e] = 1;
+    }
+  }
+  std::vector<double>& F = c.F[d];
+  std::fill(F.begin(), F.end(), 0.0);
+  std::fill(c.spd[d].begin(), c.spd[d].end(), 0.0);
+  long str = d == 0 ? 1 : (d == 1 ? c.N[0] : (long)c.N[0] * c.N[1]);
+  for (int k = lo[2]; k < hi[2]; ++k)
+    for (int j = lo[1]; j < hi[1]; ++j)
+      for (int i = lo[0]; i < hi[0]; ++i) {
+        int ii[3] = {i, j, k};
+        int f = ii[d];
+        long t = idx(c, i, j, k);  // cell just above the face
+        // polar faces: sqrt(-g) = 0 there, flux is zero
+        if (p.metric == 1 && d == 1 &&
+            ((f == 0 && p.bc[2] == 2) || (f == c.n[1] && p.bc[3] == 2)))
+          continue;
+        // stencil of 8 cells: f-4 .. f+3 along d
+        double s[8][NP];
+        FlatIn fin[8];
+        for (int m = 0; m < 8; ++m) {
+          long cm = t + (long)(m - 4) * str;
+          const Geom& G = c.geo[cm];
+          double Pm[NP];
+          for (int q = 0; q < NP; ++q) Pm[q] = c.P[(long)q * c.ntot + cm];
+          for (int q = 0; q < NP; ++q) s[m][q] = weighted_var(c, d, q) ? G.gdet * Pm[q] : Pm[q];
+          double ut[3] = {Pm[U1], Pm[U2], Pm[U3]}, ur[3] = {Pm[UR1], Pm[UR2], Pm[UR3]};
+          FourVel u, v;
+          fourvel(G, ut, u);
+          fourvel(G, ur, v);
+          fin[m].pg = (p.gam - 1.0) * Pm[UU];
+          fin[m].pr = Pm[ER] / 3.0;
+          fin[m].vg = G.gdet * u.ucon[d + 1];
+          fin[m].vr = G.gdet * v.ucon[d + 1];
+          double ka, ks;
+          opacity(p, Pm[RHO], Pm[UU], &ka, &ks);
+          double tau = (ka + ks) * std::sqrt(G.gcov[d + 1][d + 1]) * p.dx[d];
+          fin[m].w = std::min(1.0, 2.0 * tau);
+        }
+        double PL[NP], PR[NP];
+        for (int side = 0; side < 2; ++side) {
+          int m = side == 0 ? 3 : 4;  // cell f-1 (left state) or f (right state)
+          double fg = 0.0, fr = 0.0;
+          if (p.recon == 0) {
+            flattener(fin, m, &fg, &fr);
+            if (use_stored) {
+              long cm = t + (long)(m - 4) * str;
+              double& sg = c.flat[d][cm];
+              double& sr = c.flat[d][c.ntot + cm];
+              fg = std::max(fg, sg);
+              fr = std::max(fr, sr);
+              sg = fg;
+              sr = fr;
+            }
+          }
+          for (int q = 0; q < NP; ++q) {
+            double aL, aR;
+            if (p.recon == 0) {
+              double st[5] = {s[m - 2][q], s[m - 1][q], s[m][q], s[m + 1][q], s[m + 2][q]};
+              ppm_cell(st, q < ER ? fg : fr, &aL, &aR);
+            } else {
+              double dq = mc_slope(s[m - 1][q], s[m][q], s[m + 1][q]);
+              aL = s[m][q] - 0.5 * dq;
+              aR = s[m][q] + 0.5 * dq;
+            }
+            if (side == 0) PL[q] = aR;
+            else PR[q] = aL;
+          }
+        }
+        double x[3] = {xc(c, 0, i), xc(c, 1, j), xc(c, 2, k)};
+        x[d] = xf(c, d, f);
+        Geom G;
+        geom_at(p, x[0], x[1], x[2], G);
+        for (int q = 0; q < NP; ++q)
+          if (weighted_var(c, d, q)) {
+            PL[q] /= G.gdet;
+            PR[q] /= G.gdet;
+          }
+        double UL[NP], UR[NP], FL[NP], FR[NP], sL[4], sR[4];
+        face_state(p, G, d + 1, PL, UL, FL, sL);
+        face_state(p, G, d + 1, PR, UR, FR, sR);
+        double cmaxg = std::max(0.0, std::max(sL[1], sR[1]));
+        double cming = -std::min(0.0, std::min(sL[0], sR[0]));
+        double cmaxr = std::max(0.0, std::max(sL[3], sR[3]));
+        double cminr = -std::min(0.0, std::min(sL[2], sR[2]));
+        for (int q = 0; q < NP; ++q) {
+          double cmx = q < ER ? cmaxg : cmaxr, cmn = q < ER ? cming : cminr;
+          double fl;
+          if (p.flux == 0) {
+            double ctop = std::max(cmx, cmn);
+            fl = 0.5 * (FL[q] + FR[q] - ctop * (UR[q] - UL[q]));
+          } else {
+            if (cmx + cmn > 0.0)
+              fl = (cmn * FR[q] + cmx * FL[q] - cmn * cmx * (UR[q] - UL[q])) / (cmn + cmx);
+            else
+              fl = 0.5 * (FL[q] + FR[q]);
+          }
+          F[(long)q * c.ntot + t] = fl;
+        }
+        c.spd[d][t] = std::max(std::max(cmaxg, cming), std::max(cmaxr, cminr));
+      }
+}
+
+// Flux-CT (Toth 2000): for every pair (a,b) of active directions, the edge
+// EMF is the average of the four face fluxes that touch the edge, and the
+// induction fluxes are replaced by averages of the two adjacent edge EMFs.
+void flux_ct(Ctx& c) {
+  for (int a = 0; a < 3; ++a)
+    for (int b = a + 1; b < 3; ++b) {
+      if (c.n[a] == 1 || c.n[b] == 1) continue;
+      int e = 3 - a - b;
+      long sa = a == 0 ? 1 : (a == 1 ? c.N[0] : (long)c.N[0] * c.N[1]);
+      long sb = b == 0 ? 1 : (b == 1 ? c.N[0] : (long)c.N[0] * c.N[1]);
+      std::vector<double> emf(c.ntot, 0.0);
+      int lo[3] = {0, 0, 0}, hi[3];
+      for (int z = 0; z < 3; ++z) hi[z] = c.n[z];
+      hi[a] = c.n[a] + 1;
+      hi[b] = c.n[b] + 1;
+      const double* Fa = &c.F[a][(long)(B1 + b) * c.ntot];
+      const double* Fb = &c.F[b][(long)(B1 + a) * c.ntot];
+      for (int k = lo[2]; k < hi[2]; ++k)
+        for (int j = lo[1]; j < hi[1]; ++j)
+          for (int i = lo[0]; i < hi[0]; ++i) {
+            long t = idx(c, i, j, k);
+            int ii[3] = {i, j, k};
+            bool pole = false;
+            if (c.p.metric == 1 && (a == 1 || b == 1)) {
+              if ((ii[1] == 0 && c.p.bc[2] == 2) || (ii[1] == c.n[1] && c.p.bc[3] == 2)) pole = true;
+            }
+            (void)e;
+            emf[t] = pole ? 0.0 : 0.25 * (Fa[t] + Fa[t - sb] - Fb[t] - Fb[t - sa]);
+          }
+      double* Fa_w = &c.F[a][(long)(B1 + b) * c.ntot];
+      double* Fb_w = &c.F[b][(long)(B1 + a) * c.ntot];
+      // F_a[B_b] on a-faces: a in [0,n_a], b in [0,n_b)
+      for (int k = 0; k < (a == 2 ? c.n[2] + 1 : c.n[2]); ++k)
+        for (int j = 0; j < (a == 1 ? c.n[1] + 1 : c.n[1]); ++j)
+          for (int i = 0; i < (a == 0 ? c.n[0] + 1 : c.n[0]); ++i) {
+            long t = idx(c, i, j, k);
+            Fa_w[t] = 0.5 * (emf[t] + emf[t + sb]);
+          }
+      for (int k = 0; k < (b == 2 ? c.n[2] + 1 : c.n[2]); ++k)
+        for (int j = 0; j < (b == 1 ? c.n[1] + 1 : c.n[1]); ++j)
+          for (int i = 0; i < (b == 0 ? c.n[0] + 1 : c.n[0]); ++i) {
+            long t = idx(c, i, j, k);
+            Fb_w[t] = -0.5 * (emf[t] + emf[t + sa]);
+          }
+    }
+  for (int d = 0; d < 3; ++d) {
+    if (c.n[d] == 1) continue;
+    double* Fd = &c.F[d][(long)(B1 + d) * c.ntot];
+    for (long t = 0; t < c.ntot; ++t) Fd[t] = 0.0;
+  }
+}
+
+// Floors (Sec. 2 and Sec. 4.11; values from the configuration): Lorentz
+// factor caps, density and internal-energy floors, magnetisation caps and the
+// positivity of Ebar.
+void apply_floors(const orc_params& p, const Geom& G, double* P) {
+  double ut[3] = {P[U1], P[U2], P[U3]};
+  FourVel u;
+  fourvel(G, ut, u);
+  if (u.gamma > p.gamma_gas_max) {
+    double f = std::sqrt((p.gamma_gas_max * p.gamma_gas_max - 1.0) / (u.gamma * u.gamma - 1.0));
+    for (int i = 0; i < 3; ++i) P[U1 + i] *= f;
+  }
+  double ur[3] = {P[UR1], P[UR2], P[UR3]};
+  FourVel v;
+  fourvel(G, ur, v);
+  if (v.gamma > p.gamma_rad_max) {
+    double f = std::sqrt((p.gamma_rad_max * p.gamma_rad_max - 1.0) / (v.gamma * v.gamma - 1.0));
+    for (int i = 0; i < 3; ++i) P[UR1 + i] *= f;
+  }
+  double ut2[3] = {P[U1], P[U2], P[U3]};
+  fourvel(G, ut2, u);
+  double B[3] = {P[B1], P[B2], P[B3]}, bcon[4], bcov[4], bsq;
+  bfield(G, u, B, bcon, bcov, &bsq);
+  double rfl = std::max(p.floor_rho0 * std::pow(G.r, p.floor_rho_pow), bsq / p.bsq_rho_max);
+  double ufl = std::max(p.floor_u0 * std::pow(G.r, p.floor_u_pow), bsq / p.bsq_u_max);
+  P[RHO] = std::max(P[RHO], rfl);
+  P[UU] = std::max(P[UU], ufl);
+  P[RHO] = std::max(P[RHO], P[UU] / p.u_rho_max);
+  if (!(P[ER] > 0.0)) P[ER] = 1e-150;
+}
+
+double cfl_from_speeds(const Ctx& c) {
+  double best = HUGE_VAL;
+  for (int k = 0; k < c.n[2]; ++k)
+    for (int j = 0; j < c.n[1]; ++j)
+      for (int i = 0; i < c.n[0]; ++i) {
+        long t = idx(c, i, j, k);
+        double s = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          if (c.n[d] == 1) continue;
+          long st = d == 0 ? 1 : (d == 1 ? c.N[0] : (long)c.N[0] * c.N[1]);
+          double v = std::max(c.spd[d][t], c.spd[d][t + st]);
+          s += v / c.p.dx[d];
+        }
+        if (s > 0.0) best = std::min(best, 1.0 / s);
+      }
+  return c.p.courant * best;
+}
+
+double cfl_dt(Ctx& c) {
+  fill_ghosts(c, c.P);
+  for (int d = 0; d < 3; ++d)
+    if (c.n[d] > 1) compute_fluxes(c, d, false);
+  return cfl_from_speeds(c);
+}
+
+// One RK sub-step s (Sec. 4.1-4.2).
+void substep(Ctx& c, int s, double dt) {
+  static const double A[3] = {0.0, 0.75, 1.0 / 3.0};
+  static const double Bc[3] = {1.0, 0.25, 2.0 / 3.0};
+  fill_ghosts(c, c.P);
+  for (int d = 0; d < 3; ++d)
+    if (c.n[d] > 1) compute_fluxes(c, d, c.p.recon == 0);
+  flux_ct(c);
+  std::vector<double> Pnew((size_t)NP * c.ntot);
+  std::memcpy(Pnew.data(), c.P.data(), sizeof(double) * NP * c.ntot);
+  std::vector<unsigned char> failed((size_t)c.n[0] * c.n[1] * c.n[2], 0);
+  for (int k = 0; k < c.n[2]; ++k)
+    for (int j = 0; j < c.n[1]; ++j)
+      for (int i = 0; i < c.n[0]; ++i) {
+        long t = idx(c, i, j, k);
+        const Geom& G = c.geo[t];
+        double Ps[NP], Us[NP], SM[NP], X[NP], Ust[NP];
+        for (int q = 0; q < NP; ++q) Ps[q] = c.P[(long)q * c.ntot + t];
+        const double(*Gam)[4][4] = reinterpret_cast<const double(*)[4][4]>(&c.gam[(size_t)t * 64]);
+        prim_to_cons(c.p, G, Gam, Ps, Us, SM);
+        if (s == 0)
+          for (int q = 0; q < NP; ++q) c.Un[(long)q * c.ntot + t] = Us[q];
+        for (int q = 0; q < NP; ++q) {
+          double div = 0.0;
+          for (int d = 0; d < 3; ++d) {
+            if (c.n[d] == 1) continue;
+            long st = d == 0 ? 1 : (d == 1 ? c.N[0] : (long)c.N[0] * c.N[1]);
+            div += (c.F[d][(long)q * c.ntot + t + st] - c.F[d][(long)q * c.ntot + t]) / c.p.dx[d];
+          }
+          X[q] = -div + SM[q];
+          Ust[q] = A[s] * c.Un[(long)q * c.ntot + t] + Bc[s] * (Us[q] + dt * X[q]);
+        }
+        double Pn[NP];
+        orc_implicit_info info;
+        implicit_zone(c.p, G, Ust, Ps, Bc[s] * dt, Pn, &info);
+        long a = aidx(c, i, j, k);
+        c.status[a] = std::max(c.status[a], (unsigned char)info.method);
+        c.iters[a] += info.iters_pmhd + info.iters_urad;
+        c.counts[3] += info.iters_pmhd + info.iters_urad;
+        c.counts[4] += 1;
+        if (info.method == ORC_OK_PMHD) c.counts[0]++;
+        else if (info.method == ORC_OK_URAD) c.counts[1]++;
+        else c.counts[2]++;
+        failed[a] = info.method == ORC_BACKUP;
+        for (int q = 0; q < NP; ++q) Pnew[(long)q * c.ntot + t] = Pn[q];
+      }
+  // Back-up (Sec. 4.11): replace failed zones by the average of their good
+  // active face neighbours (all active neighbours if none is good); B keeps
+  // its constrained-transport value.
+  std::vector<double> Pavg = Pnew;
+  for (int k = 0; k < c.n[2]; ++k)
+    for (int j = 0; j < c.n[1]; ++j)
+      for (int i = 0; i < c.n[0]; ++i) {
+        if (!failed[aidx(c, i, j, k)]) continue;
+        long t = idx(c, i, j, k);
+        double sum_good[NP] = {0}, sum_all[NP] = {0};
+        int ngood = 0, nall = 0;
+        for (int d = 0; d < 3; ++d) {
+          if (c.n[d] == 1) continue;
+          for (int side = -1; side <= 1; side += 2) {
+            int nb[3] = {i, j, k};
+            nb[d] += side;
+            if (nb[d] < 0 || nb[d] >= c.n[d]) continue;
+            long tn = idx(c, nb[0], nb[1], nb[2]);
+            bool good = !failed[aidx(c, nb[0], nb[1], nb[2])];
+            for (int q = 0; q < NP; ++q) {
+              double v = Pnew[(long)q * c.ntot + tn];
+              sum_all[q] += v;
+              if (good) sum_good[q] += v;
+            }
+            nall++;
+            if (good) ngood++;
+          }
+        }
+        if (nall == 0) continue;
+        for (int q = 0; q < NP; ++q) {
+          if (q >= B1 && q <= B3) continue;
+          Pavg[(long)q * c.ntot + t] = ngood > 0 ? sum_good[q] / ngood : sum_all[q] / nall;
+        }
+      }
+  for (int k = 0; k < c.n[2]; ++k)
+    for (int j = 0; j < c.n[1]; ++j)
+      for (int i = 0; i < c.n[0]; ++i) {
+        long t = idx(c, i, j, k);
+        double Pz[NP];
+        for (int q = 0; q < NP; ++q) Pz[q] = Pavg[(long)q * c.ntot + t];
+        apply_floors(c.p, c.geo[t], Pz);
+        for (int q = 0; q < NP; ++q) c.P[(long)q * c.ntot + t] = Pz[q];
+      }
+}
+
+}  // namespace
+}  // namespace orc
+
+using namespace orc;
+
+extern "C" {
+
+void* orc_create(const orc_params* p) {
+  Ctx* c = new Ctx();
+  c->p = *p;
+  if (c->p.newton_max > 60) c->p.newton_max = 60;
+  c->ntot = 1;
+  for (int d = 0; d < 3; ++d) {
+    c->n[d] = p->n[d];
+    c->ng[d] = p->n[d] > 1 ? NG : 0;
+    c->N[d] = c->n[d] + 2 * c->ng[d];
+    c->ntot *= c->N[d];
+  }
+  c->P.assign((size_t)NP * c->ntot, 0.0);
+  c->Un.assign((size_t)NP * c->ntot, 0.0);
+  for (int d = 0; d < 3; ++d) {
+    c->F[d].assign((size_t)NP * c->ntot, 0.0);
+    c->spd[d].assign((size_t)c->ntot, 0.0);
+    c->flat[d].assign((size_t)2 * c->ntot, 0.0);
+  }
+  c->geo.resize(c->ntot);
+  c->gam.assign((size_t)c->ntot * 64, 0.0);
+  for (int k = -c->ng[2]; k < c->n[2] + c->ng[2]; ++k)
+    for (int j = -c->ng[1]; j < c->n[1] + c->ng[1]; ++j)
+      for (int i = -c->ng[0]; i < c->n[0] + c->ng[0]; ++i) {
+        long t = idx(*c, i, j, k);
+        double x1 = xc(*c, 0, i), x2 = xc(*c, 1, j), x3 = xc(*c, 2, k);
+        geom_at(c->p, x1, x2, x3, c->geo[t]);
+        double G4[4][4][4];
+        connection_at(c->p, x1, x2, x3, G4);
+        std::memcpy(&c->gam[(size_t)t * 64], G4, sizeof(G4));
+      }
+  long na = (long)c->n[0] * c->n[1] * c->n[2];
+  c->status.assign(na, 0);
+  c->iters.assign(na, 0);
+  for (int i = 0; i < 5; ++i) c->counts[i] = 0;
+  return c;
+}
+
+void orc_destroy(void* ctx) { delete static_cast<Ctx*>(ctx); }
+
+void orc_set_prims(void* ctx, const double* P) {
+  Ctx& c = *static_cast<Ctx*>(ctx);
+  long na = (long)c.n[0] * c.n[1] * c.n[2];
+  for (int q = 0; q < NP; ++q)
+    for (int k = 0; k < c.n[2]; ++k)
+      for (int j = 0; j < c.n[1]; ++j)
+        for (int i = 0; i < c.n[0]; ++i)
+          c.P[(long)q * c.ntot + idx(c, i, j, k)] = P[(long)q * na + aidx(c, i, j, k)];
+}
+
+void orc_get_prims(void* ctx, double* P) {
+  Ctx& c = *static_cast<Ctx*>(ctx);
+  long na = (long)c.n[0] * c.n[1] * c.n[2];
+  for (int q = 0; q < NP; ++q)
+    for (int k = 0; k < c.n[2]; ++k)
+      for (int j = 0; j < c.n[1]; ++j)
+        for (int i = 0; i < c.n[0]; ++i)
+          P[(long)q * na + aidx(c, i, j, k)] = c.P[(long)q * c.ntot + idx(c, i, j, k)];
+}
+
+void orc_get_prims_with_ghosts(void* ctx, double* P, int fill) {
+  Ctx& c = *static_cast<Ctx*>(ctx);
+  if (fill) fill_ghosts(c, c.P);
+  std::memcpy(P, c.P.data(), sizeof(double) * NP * c.ntot);
+}
+
+double orc_cfl_dt(void* ctx) { return cfl_dt(*static_cast<Ctx*>(ctx)); }
+
+double orc_step(void* ctx, double dt) {
+  Ctx& c = *static_cast<Ctx*>(ctx);
+  if (!(dt > 0.0)) dt = cfl_dt(c);
+  for (int d = 0; d < 3; ++d) std::fill(c.flat[d].begin(), c.flat[d].end(), 0.0);
+  std::fill(c.iters.begin(), c.iters.end(), 0);
+  std::fill(c.status.begin(), c.status.end(), 0);
+  for (int i = 0; i < 5; ++i) c.counts[i] = 0;
+  for (int s = 0; s < 3; ++s) substep(c, s, dt);
+  return dt;
+}
+
+void orc_get_status(void* ctx, unsigned char* st) {
+  Ctx& c = *static_cast<Ctx*>(ctx);
+  std::memcpy(st, c.status.data(), c.status.size());
+}
+
+void orc_get_iters(void* ctx, int* it) {
+  Ctx& c = *static_cast<Ctx*>(ctx);
+  std::memcpy(it, c.iters.data(), sizeof(int) * c.iters.size());
+}
+
+void orc_get_counts(void* ctx, long long* out) {
+  Ctx& c = *static_cast<Ctx*>(ctx);
+  for (int i = 0; i < 5; ++i) out[i] = c.counts[i];
+}
+
+void orc_compute_fluxes(void* ctx, int dir, double* Fout) {
+  Ctx& c = *static_cast<Ctx*>(ctx);
+  fill_ghosts(c, c.P);
+  for (int d = 0; d < 3; ++d) std::fill(c.flat[d].begin(), c.flat[d].end(), 0.0);
+  for (int d = 0; d < 3; ++d)
+    if (c.n[d] > 1) compute_fluxes(c, d, false);
+  flux_ct(c);
+  int d = dir - 1;
+  int m[3] = {c.n[0], c.n[1], c.n[2]};
+  m[d] += 1;
+  long nf = (long)m[0] * m[1] * m[2];
+  for (int q = 0; q < NP; ++q)
+    for (int k = 0; k < m[2]; ++k)
+      for (int j = 0; j < m[1]; ++j)
+        for (int i = 0; i < m[0]; ++i)
+          Fout[(long)q * nf + ((long)k * m[1] + j) * m[0] + i] = c.F[d][(long)q * c.ntot + idx(c, i, j, k)];
+}
+
+void orc_metric(const orc_params* p, const double* x, double* gcov, double* gcon, double* gdet,
+                double* alpha) {
+  Geom G;
+  geom_at(*p, x[1], x[2], x[3], G);
+  std::memcpy(gcov, G.gcov, sizeof(G.gcov));
+  std::memcpy(gcon, G.gcon, sizeof(G.gcon));
+  *gdet = G.gdet;
+  *alpha = G.alpha;
+}
+
+void orc_connection(const orc_params* p, const double* x, double* gam) {
+  double G4[4][4][4];
+  connection_at(*p, x[1], x[2], x[3], G4);
+  std::memcpy(gam, G4, sizeof(G4));
+}
+
+void orc_prim_to_cons(const orc_params* p, const double* x, const double* P, double* U,
+                      double* SM) {
+  Geom G;
+  geom_at(*p, x[1], x[2], x[3], G);
+  double G4[4][4][4];
+  connection_at(*p, x[1], x[2], x[3], G4);
+  prim_to_cons(*p, G, G4, P, U, SM);
+}
+
+void orc_flux(const orc_params* p, const double* x, int d, const double* P, double* F,
+              double* speeds4) {
+  Geom G;
+  geom_at(*p, x[1], x[2], x[3], G);
+  double U[NP];
+  face_state(*p, G, d, P, U, F, speeds4);
+}
+
+void orc_stress(const orc_params* p, const double* x, const double* P, double* T16, double* R16) {
+  Geom G;
+  geom_at(*p, x[1], x[2], x[3], G);
+  double T[4][4], R[4][4], bcon[4], bcov[4], bsq;
+  FourVel u, ur;
+  gas_stress(*p, G, P, T, u, bcon, bcov, &bsq);
+  rad_stress(G, P, R, ur);
+  std::memcpy(T16, T, sizeof(T));
+  std::memcpy(R16, R, sizeof(R));
+}
+
+void orc_four_force(const orc_params* p, const double* x, const double* P, double* G4) {
+  Geom G;
+  geom_at(*p, x[1], x[2], x[3], G);
+  double R[4][4];
+  FourVel ur, u;
+  rad_stress(G, P, R, ur);
+  double ut[3] = {P[U1], P[U2], P[U3]};
+  fourvel(G, ut, u);
+  four_force(*p, G, P[RHO], P[UU], u, R, G4);
+}
+
+int orc_rad_invert(const orc_params* p, const double* x, const double* Rt, int limiter,
+                   double* Prad) {
+  Geom G;
+  geom_at(*p, x[1], x[2], x[3], G);
+  return rad_invert(*p, G, Rt, limiter, Prad);
+}
+
+int orc_gas_invert(const orc_params* p, const double* x, const double* U, const double* Pg,
+                   double tol, double* Pout) {
+  Geom G;
+  geom_at(*p, x[1], x[2], x[3], G);
+  return gas_invert(*p, G, U, Pg, tol, Pout);
+}
+
+void orc_implicit_zone(const orc_params* p, const double* x, const double* Ustar, const double* Ps,
+                       double h, double* Pout, orc_implicit_info* info) {
+  Geom G;
+  geom_at(*p, x[1], x[2], x[3], G);
+  implicit_zone(*p, G, Ustar, Ps, h, Pout, info);
+}
+
+void orc_pmhd_residual(const orc_params* p, const double* x, const double* Ustar, double h,
+                       const double* xg, double* E4, double* eT, double* eI) {
+  Geom G;
+  geom_at(*p, x[1], x[2], x[3], G);
+  pmhd_residual_public(*p, G, Ustar, h, xg, E4, eT, eI);
+}
+
+double orc_levermore_xi(double f) {
+  double f2 = f * f;
+  return (3.0 + 4.0 * f2) / (5.0 + 2.0 * std::sqrt(4.0 - 3.0 * f2));
+}
+
+}  // extern "C"

@@ -1,0 +1,438 @@
+// HARMRAD oracle, implicit four-force solve -- TEST INFRASTRUCTURE ONLY.
+//
+// Restates Sec. 4.7-4.11 of McKinney et al. (2014): the energy-momentum
+// equations T^t_nu(i+1) - T^t_nu(i) = h G_nu(i+1) (Eq. source3) with
+// rho0 u^t and B fixed, solved by a 4D Newton-Raphson (Eq. newton) with a
+// finite-difference Jacobian, first iterating the gas primitives (PMHD), then,
+// if the error is not acceptable, the radiation conserved quantities (URAD).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "oracle_internal.h"
+
+namespace orc {
+
+namespace {
+
+struct Sys {
+  const orc_params* p;
+  const Geom* G;
+  double Dlab;      // rho0 u^t (fixed)
+  double Tstar[4];  // explicit T^t_nu with the rest-mass flux added to the t row
+  double Rstar[4];  // explicit R^t_nu
+  double B[3];      // lab field (fixed)
+  double h;         // b_s dt
+};
+
+struct Res {
+  double Eg[4], Er[4];  // gas and radiation error functions
+  double eg[4], er[4];  // normalised per row
+  double eT, eI;
+  int negE;
+  double Rt_pre[4];  // R^t_nu handed to the radiation inversion (pre-limiter)
+  double P[NP];      // consistent primitives of this iterate
+  bool ok;
+};
+
+// Normalised errors (Sec. 4.8): each row divided by the sum of the absolute
+// values of the terms that make it up; the three spatial rows share one norm
+// built in an orthonormal basis.  e_T takes, row by row, the larger of the gas
+// and radiation errors; e_I uses the iterated rows only.
+void normalise(const Sys& s, const double Tc[4], const double Rc[4], const double Gc[4],
+               bool iter_gas, Res& r) {
+  const Geom& G = *s.G;
+  double dg0 = std::fabs(Tc[0]) + std::fabs(s.Tstar[0]) + s.h * std::fabs(Gc[0]);
+  double dr0 = std::fabs(Rc[0]) + std::fabs(s.Rstar[0]) + s.h * std::fabs(Gc[0]);
+  double dgs = 0.0, drs = 0.0;
+  for (int k = 1; k < 4; ++k) {
+    double sk = std::sqrt(G.gcon[k][k]);
+    dgs += sk * (std::fabs(Tc[k]) + std::fabs(s.Tstar[k]) + s.h * std::fabs(Gc[k]));
+    drs += sk * (std::fabs(Rc[k]) + std::fabs(s.Rstar[k]) + s.h * std::fabs(Gc[k]));
+  }
+  r.eg[0] = dg0 > 0.0 ? std::fabs(r.Eg[0]) / dg0 : 0.0;
+  r.er[0] = dr0 > 0.0 ? std::fabs(r.Er[0]) / dr0 : 0.0;
+  for (int k = 1; k < 4; ++k) {
+    double sk = std::sqrt(G.gcon[k][k]);
+    r.eg[k] = dgs > 0.0 ? std::fabs(r.Eg[k]) * sk / dgs : 0.0;
+    r.er[k] = drs > 0.0 ? std::fabs(r.Er[k]) * sk / drs : 0.0;
+  }
+  if (r.negE) r.eg[0] = r.er[0] = 0.0;
+  double sT = 0.0, sI = 0.0;
+  for (int k = 0; k < 4; ++k) {
+    sT += std::max(r.eg[k], r.er[k]);
+    sI += iter_gas ? r.eg[k] : r.er[k];
+  }
+  r.eT = 0.25 * sT;
+  r.eI = 0.25 * sI;
+}
+
+// T^t_nu in conserved form (rest-mass flux added to the t row) and R^t_nu.
+void tt_row(const orc_params& p, const Geom& G, const double* P, double Tc[4], double Rc[4],
+            FourVel* ug, double rho_u_t_out[1]) {
+  double T[4][4], R[4][4], bcon[4], bcov[4], bsq;
+  FourVel u, ur;
+  gas_stress(p, G, P, T, u, bcon, bcov, &bsq);
+  rad_stress(G, P, R, ur);
+  double mt = P[RHO] * u.ucon[0];
+  Tc[0] = T[0][0] + mt;
+  for (int k = 1; k < 4; ++k) Tc[k] = T[0][k];
+  for (int k = 0; k < 4; ++k) Rc[k] = R[0][k];
+  if (ug) *ug = u;
+  if (rho_u_t_out) rho_u_t_out[0] = mt;
+}
+
+// PMHD error function: iterate (u_g, u~^i); rho0 = (rho0 u^t)/u^t; radiation
+// from total energy-momentum conservation; then G_nu and E_q (Sec. 4.8).
+void pmhd_res(const Sys& s, const double x[4], Res& r) {
+  const orc_params& p = *s.p;
+  const Geom& G = *s.G;
+  double ut[3] = {x[1], x[2], x[3]};
+  FourVel u;
+  fourvel(G, ut, u);
+  double P[NP];
+  P[RHO] = s.Dlab / u.ucon[0];
+  P[UU] = x[0];
+  P[U1] = x[1];
+  P[U2] = x[2];
+  P[U3] = x[3];
+  P[B1] = s.B[0];
+  P[B2] = s.B[1];
+  P[B3] = s.B[2];
+  double T[4][4], bcon[4], bcov[4], bsq;
+  gas_stress(p, G, P, T, u, bcon, bcov, &bsq);
+  double Tc[4];
+  Tc[0] = T[0][0] + P[RHO] * u.ucon[0];
+  for (int k = 1; k < 4; ++k) Tc[k] = T[0][k];
+  for (int k = 0; k < 4; ++k) r.Rt_pre[k] = s.Rstar[k] - (Tc[k] - s.Tstar[k]);
+  double Pr[4];
+  r.negE = rad_invert(p, G, r.Rt_pre, LIM_TYPE2, Pr);
+  P[ER] = Pr[0];
+  P[UR1] = Pr[1];
+  P[UR2] = Pr[2];
+  P[UR3] = Pr[3];
+  double R[4][4];
+  FourVel ur;
+  rad_stress(G, P, R, ur);
+  double Rc[4];
+  for (int k = 0; k < 4; ++k) Rc[k] = R[0][k];
+  double Gc[4];
+  four_force(p, G, P[RHO], P[UU], u, R, Gc);
+  for (int k = 0; k < 4; ++k) {
+    r.Eg[k] = Tc[k] - s.Tstar[k] - s.h * Gc[k];
+    r.Er[k] = Rc[k] - s.Rstar[k] + s.h * Gc[k];
+  }
+  normalise(s, Tc, Rc, Gc, true, r);
+  std::memcpy(r.P, P, sizeof(P));
+  r.ok = std::isfinite(r.eT);
+}
+
+// URAD error function: iterate R^t_nu; gas from conservation through the
+// 1D_W inversion; radiation from the M1 inversion; all conserved quantities
+// recomputed from the primitives before forming E_q (Sec. 4.8).
+bool urad_res(const Sys& s, const double x[4], const double* Pguess, double tol_inv, Res& r) {
+  const orc_params& p = *s.p;
+  const Geom& G = *s.G;
+  double U[NP];
+  double gd = G.gdet;
+  U[0] = gd * s.Dlab;
+  for (int k = 0; k < 4; ++k) U[1 + k] = gd * (s.Tstar[k] - (x[k] - s.Rstar[k]));
+  for (int i = 0; i < 3; ++i) U[5 + i] = gd * s.B[i];
+  for (int k = 0; k < 4; ++k) U[8 + k] = gd * x[k];
+  double P[NP];
+  if (gas_invert(p, G, U, Pguess, tol_inv, P) != 0) {
+    r.ok = false;
+    return false;
+  }
+  for (int k = 0; k < 4; ++k) r.Rt_pre[k] = x[k];
+  double Pr[4];
+  r.negE = rad_invert(p, G, x, LIM_TYPE2, Pr);
+  P[ER] = Pr[0];
+  P[UR1] = Pr[1];
+  P[UR2] = Pr[2];
+  P[UR3] = Pr[3];
+  double Tc[4], Rc[4];
+  FourVel u;
+  tt_row(p, G, P, Tc, Rc, &u, nullptr);
+  double T_[4][4], R[4][4];
+  FourVel ur;
+  (void)T_;
+  rad_stress(G, P, R, ur);
+  double Gc[4];
+  four_force(p, G, P[RHO], P[UU], u, R, Gc);
+  for (int k = 0; k < 4; ++k) {
+    r.Eg[k] = Tc[k] - s.Tstar[k] - s.h * Gc[k];
+    r.Er[k] = Rc[k] - s.Rstar[k] + s.h * Gc[k];
+  }
+  normalise(s, Tc, Rc, Gc, false, r);
+  std::memcpy(r.P, P, sizeof(P));
+  r.ok = std::isfinite(r.eT);
+  return r.ok;
+}
+
+// Solve A z = b (4x4) by Gaussian elimination with partial pivoting.
+bool solve4(double A[4][4], double b[4], double z[4]) {
+  double M[4][5];
+  for (int i = 0; i < 4; ++i) {
+    for (int j = 0; j < 4; ++j) M[i][j] = A[i][j];
+    M[i][4] = b[i];
+  }
+  for (int c = 0; c < 4; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < 4; ++r)
+      if (std::fabs(M[r][c]) > std::fabs(M[piv][c])) piv = r;
+    if (M[piv][c] == 0.0 || !std::isfinite(M[piv][c])) return false;
+    if (piv != c)
+      for (int j = 0; j < 5; ++j) std::swap(M[c][j], M[piv][j]);
+    for (int r = c + 1; r < 4; ++r) {
+      double f = M[r][c] / M[c][c];
+      for (int j = c; j < 5; ++j) M[r][j] -= f * M[c][j];
+    }
+  }
+  for (int i = 3; i >= 0; --i) {
+    double s = M[i][4];
+    for (int j = i + 1; j < 4; ++j) s -= M[i][j] * z[j];
+    z[i] = s / M[i][i];
+  }
+  for (int i = 0; i < 4; ++i)
+    if (!std::isfinite(z[i])) return false;
+  return true;
+}
+
+// Stopping checks shared by both methods (Sec. 4.10): after the 5th step the
+// error must have halved relative to the mean of the errors 4, 3 and 2 steps
+// earlier, and may not have risen 5 times.
+struct History {
+  double eT[64], eI[64];
+  int rises = 0;
+};
+bool stalled(History& hs, int k) {
+  if (k >= 1 && k > 5 && hs.eT[k] > hs.eT[k - 1]) {
+    hs.rises++;
+    if (hs.rises >= 5) return true;
+  }
+  if (k > 5) {
+    double mT = (hs.eT[k - 4] + hs.eT[k - 3] + hs.eT[k - 2]) / 3.0;
+    double mI = (hs.eI[k - 4] + hs.eI[k - 3] + hs.eI[k - 2]) / 3.0;
+    if (hs.eT[k] > 0.5 * mT || hs.eI[k] > 0.5 * mI) return true;
+  }
+  return false;
+}
+
+// PMHD Newton (Sec. 4.9-4.10): undamped, two-sided FD Jacobian with a
+// normalised offset of 1e-8 (1e-10 once e_I < 1e-9), u_g < 0 reset to |u_g|/2.
+int newton_pmhd(const Sys& s, const double x0[4], Res& best) {
+  const orc_params& p = *s.p;
+  const Geom& G = *s.G;
+  double x[4] = {x0[0], x0[1], x0[2], x0[3]};
+  History hs;
+  best.eT = HUGE_VAL;
+  best.ok = false;
+  int steps = 0;
+  double eps = 1e-8;
+  for (int k = 0;; ++k) {
+    Res r;
+    pmhd_res(s, x, r);
+    if (r.ok && r.eT < best.eT) best = r;
+    if (!r.ok) break;
+    hs.eT[k] = r.eT;
+    hs.eI[k] = r.eI;
+    if (r.eT < p.newton_tol) break;
+    if (stalled(hs, k)) break;
+    if (k >= p.newton_max) break;
+    if (r.eI < 1e-9) eps = 1e-10;
+    // Jacobian dE_gas/dx by centred differences
+    double usq = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) usq += G.gcov[i + 1][j + 1] * x[1 + i] * x[1 + j];
+    double umag = std::max(1.0, std::sqrt(usq));
+    double J[4][4];
+    for (int j = 0; j < 4; ++j) {
+      double dj = (j == 0) ? eps * std::fabs(x[0]) : eps * umag / std::sqrt(G.gcov[j][j]);
+      double xp[4], xm[4];
+      for (int i = 0; i < 4; ++i) xp[i] = xm[i] = x[i];
+      xp[j] += dj;
+      xm[j] -= dj;
+      Res rp, rm;
+      pmhd_res(s, xp, rp);
+      pmhd_res(s, xm, rm);
+      for (int i = 0; i < 4; ++i) J[i][j] = (rp.Eg[i] - rm.Eg[i]) / (2.0 * dj);
+    }
+    double dx[4], E[4] = {r.Eg[0], r.Eg[1], r.Eg[2], r.Eg[3]};
+    if (!solve4(J, E, dx)) break;
+    double xn[4];
+    for (int i = 0; i < 4; ++i) xn[i] = x[i] - dx[i];
+    if (xn[0] < 0.0) xn[0] = 0.5 * std::fabs(xn[0]);
+    bool tiny = true;
+    for (int i = 0; i < 4; ++i)
+      if (std::fabs(xn[i] - x[i]) > 10.0 * EPSM * std::fabs(x[i])) tiny = false;
+    for (int i = 0; i < 4; ++i) x[i] = xn[i];
+    ++steps;
+    if (tiny) {
+      Res rf;
+      pmhd_res(s, x, rf);
+      if (rf.ok && rf.eT < best.eT) best = rf;
+      break;
+    }
+  }
+  return steps;
+}
+
+// URAD Newton (Sec. 4.8-4.10): one-sided FD Jacobian, tolerance 1e-9, at most
+// 20 x 6 gas inversions, inversion failures inside the Jacobian retried with
+// larger offsets up to 0.3.
+int newton_urad(const Sys& s, const double x0[4], const double* Pg0, Res& best) {
+  const orc_params& p = *s.p;
+  const Geom& G = *s.G;
+  const double tol = 1e-9;
+  double x[4] = {x0[0], x0[1], x0[2], x0[3]};
+  double Pg[NP];
+  std::memcpy(Pg, Pg0, sizeof(Pg));
+  History hs;
+  best.eT = HUGE_VAL;
+  best.ok = false;
+  int steps = 0, ninv = 0;
+  const int inv_budget = 20 * 6;
+  double eps = 1e-8;
+  for (int k = 0;; ++k) {
+    Res r;
+    ++ninv;
+    if (!urad_res(s, x, Pg, 1e-13, r)) break;
+    std::memcpy(Pg, r.P, sizeof(Pg));
+    if (r.eT < best.eT) best = r;
+    hs.eT[k] = r.eT;
+    hs.eI[k] = r.eI;
+    if (r.eT < tol) break;
+    if (stalled(hs, k)) break;
+    if (k >= p.newton_max || ninv >= inv_budget) break;
+    if (r.eI < 1e-9) eps = 1e-10;
+    double J[4][4];
+    bool jok = true;
+    for (int j = 0; j < 4 && jok; ++j) {
+      double scale = std::fabs(x[0]) * (j == 0 ? 1.0 : std::sqrt(G.gcov[j][j]));
+      bool done = false;
+      for (double e = eps; e <= 0.3 && !done; e *= 10.0) {
+        double dj = e * scale;
+        if (dj == 0.0) break;
+        double xp[4] = {x[0], x[1], x[2], x[3]};
+        xp[j] += dj;
+        Res rp;
+        ++ninv;
+        if (urad_res(s, xp, Pg, 1e-2 * e, rp)) {
+          for (int i = 0; i < 4; ++i) J[i][j] = (rp.Er[i] - r.Er[i]) / dj;
+          done = true;
+        }
+      }
+      if (!done) jok = false;
+    }
+    if (!jok) break;
+    double dx[4], E[4] = {r.Er[0], r.Er[1], r.Er[2], r.Er[3]};
+    if (!solve4(J, E, dx)) break;
+    double xn[4];
+    for (int i = 0; i < 4; ++i) xn[i] = x[i] - dx[i];
+    // R^t_t must stay negative (positive lab energy): reflect to half its size.
+    if (xn[0] > 0.0) xn[0] = -0.5 * std::fabs(xn[0]);
+    bool tiny = true;
+    for (int i = 0; i < 4; ++i)
+      if (std::fabs(xn[i] - x[i]) > 10.0 * EPSM * std::fabs(x[i])) tiny = false;
+    for (int i = 0; i < 4; ++i) x[i] = xn[i];
+    ++steps;
+    if (tiny) {
+      Res rf;
+      ++ninv;
+      if (urad_res(s, x, Pg, 1e-13, rf) && rf.eT < best.eT) best = rf;
+      break;
+    }
+  }
+  return steps;
+}
+
+void build_sys(const orc_params& p, const Geom& G, const double* Ustar, double h, Sys& s) {
+  s.p = &p;
+  s.G = &G;
+  double gd = G.gdet;
+  s.Dlab = Ustar[0] / gd;
+  for (int k = 0; k < 4; ++k) s.Tstar[k] = Ustar[1 + k] / gd;
+  for (int k = 0; k < 4; ++k) s.Rstar[k] = Ustar[8 + k] / gd;
+  for (int i = 0; i < 3; ++i) s.B[i] = Ustar[5 + i] / gd;
+  s.h = h;
+}
+
+}  // namespace
+
+void pmhd_residual_public(const orc_params& p, const Geom& G, const double* Ustar, double h,
+                          const double* xg, double* E4, double* eT, double* eI) {
+  Sys s;
+  build_sys(p, G, Ustar, h, s);
+  Res r;
+  pmhd_res(s, xg, r);
+  for (int k = 0; k < 4; ++k) E4[k] = r.Eg[k];
+  *eT = r.eT;
+  *eI = r.eI;
+}
+
+// Method sequence (Sec. 4.10-4.11): PMHD first, guessed from P_s or, where the
+// cell is optically thin (tau < 2/3), from a gas inversion of U*; URAD if PMHD
+// leaves e_T > 1e-9; the lower-error solution is kept; e_T > 1e-7 marks the
+// zone for the neighbour-average back-up.  A solution that hit the TYPE2
+// negative-energy branch has its radiation re-inverted with the BASIC limiter.
+void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, const double* Ps,
+                   double h, double* Pout, orc_implicit_info* info) {
+  Sys s;
+  build_sys(p, G, Ustar, h, s);
+  double x0[4] = {Ps[UU], Ps[U1], Ps[U2], Ps[U3]};
+  double kabs, ksca;
+  opacity(p, Ps[RHO], Ps[UU], &kabs, &ksca);
+  double dl = 0.0;
+  for (int d = 1; d <= 3; ++d)
+    if (p.n[d - 1] > 1) dl = std::max(dl, std::sqrt(G.gcov[d][d]) * p.dx[d - 1]);
+  double tau = (kabs + ksca) * dl;
+  if (tau < 2.0 / 3.0) {
+    double Pt[NP];
+    if (gas_invert(p, G, Ustar, Ps, 1e-9, Pt) == 0) {
+      x0[0] = Pt[UU];
+      x0[1] = Pt[U1];
+      x0[2] = Pt[U2];
+      x0[3] = Pt[U3];
+    }
+  }
+  Res bp;
+  info->iters_pmhd = newton_pmhd(s, x0, bp);
+  info->iters_urad = 0;
+  Res best = bp;
+  int method = ORC_OK_PMHD;
+  if (!(bp.ok && bp.eT < 1e-9)) {
+    const double* Pg = (bp.ok && bp.eT < 1e-4) ? bp.P : Ps;
+    double Tc[4], Rc[4];
+    tt_row(p, G, Pg, Tc, Rc, nullptr, nullptr);
+    double xr[4] = {Rc[0], Rc[1], Rc[2], Rc[3]};
+    Res br;
+    info->iters_urad = newton_urad(s, xr, Pg, br);
+    if (br.ok && (!best.ok || br.eT < best.eT)) {
+      best = br;
+      method = ORC_OK_URAD;
+    }
+  }
+  if (!best.ok) {
+    for (int q = 0; q < NP; ++q) Pout[q] = Ps[q];
+    for (int i = 0; i < 3; ++i) Pout[B1 + i] = s.B[i];
+    info->e_T = HUGE_VAL;
+    info->method = ORC_BACKUP;
+    info->neg_erad = 0;
+    return;
+  }
+  for (int q = 0; q < NP; ++q) Pout[q] = best.P[q];
+  if (best.negE) {
+    double Pr[4];
+    rad_invert(p, G, best.Rt_pre, LIM_BASIC, Pr);
+    Pout[ER] = Pr[0];
+    Pout[UR1] = Pr[1];
+    Pout[UR2] = Pr[2];
+    Pout[UR3] = Pr[3];
+  }
+  info->e_T = best.eT;
+  info->neg_erad = best.negE;
+  info->method = (best.eT > 1e-7) ? ORC_BACKUP : method;
+}
+
+}  // namespace orc

@@ -1,0 +1,244 @@
+"""Seeded synthetic workloads for the HARMRAD step.
+
+Each generator returns ``(cfg, P)``: a plain dict of run parameters (the
+fields of ``harmrad_params``) and the initial primitives as a float64 array of
+shape ``[12, n3, n2, n1]``.  The same bytes feed the CUDA library and the CPU
+oracle.  Random draws use numpy's counter-based Philox generator with a fixed
+key, so every run reproduces bit for bit on any host.
+
+The workloads follow the shapes and value ranges the paper uses (McKinney et
+al. 2014): a stiff uniform radiating box (Sec. 5 style relaxation), a
+magnetised, radiation-supported torus on a Kerr-Schild grid with the paper's
+spin a = 0.9375 and fiducial 256x128x64 resolution (Sec. 6), and periodic
+Minkowski boxes with Gaussian radiation pulses (Sec. 5.3).  The torus builds
+its divergence-free initial field from a vector potential and normalises it to
+a plasma beta; those two set-up steps need sqrt(-g) and b^2 of a static
+observer, which are written out below as closed forms of the Kerr-Schild
+metric.  They are initial-condition formulas, not part of the time step.
+"""
+import math
+
+import numpy as np
+
+NP = 12
+RHO, UU, U1, U2, U3, B1, B2, B3, ER, UR1, UR2, UR3 = range(12)
+PERIODIC, OUTFLOW, POLAR = 0, 1, 2
+PPM, MC = 0, 1
+LAXF, HLL = 0, 1
+OPAC_CONST, OPAC_KRAMERS = 0, 1
+
+
+def rng(seed):
+    """Counter-based generator (Philox-4x64) keyed by ``seed``."""
+    return np.random.Generator(np.random.Philox(key=int(seed)))
+
+
+def base_params():
+    return dict(
+        n=[1, 1, 1], x0=[0.0, 0.0, 0.0], dx=[1.0, 1.0, 1.0],
+        metric=0, a_spin=0.0, R0=0.0, hslope=0.3,
+        bc=[PERIODIC] * 6,
+        gam=5.0 / 3.0, a_rad=1.0, courant=0.5,
+        opacity=OPAC_CONST, kappa_abs0=0.0, kappa_es0=0.0, kappa_scale=1.0, T_kappa_min=0.0,
+        recon=PPM, flux=LAXF,
+        gamma_rad_max=100.0, gamma_gas_max=50.0,
+        floor_rho0=1e-10, floor_rho_pow=0.0, floor_u0=1e-12, floor_u_pow=0.0,
+        bsq_rho_max=200.0, bsq_u_max=1e5, u_rho_max=1e10,
+        newton_max=20, newton_tol=1e-12,
+    )
+
+
+def relax_box(n1=256, perturb=1e-4):
+    """1D periodic Minkowski box, N=256: rho0=1, u_g=1e-2 (1 + A sin 2 pi x),
+    Ebar = 2 a_rad T0^4 with a_rad T0^4 = u_g0, tau_abs = 10 per zone,
+    kappa_es = 0.4.  Stiff relaxation toward radiative equilibrium."""
+    cfg = base_params()
+    dx = 1.0 / n1
+    T0 = (cfg["gam"] - 1.0) * 1e-2
+    a_rad = 1e-2 / T0 ** 4
+    cfg.update(n=[n1, 1, 1], dx=[dx, 1.0, 1.0], a_rad=a_rad,
+               opacity=OPAC_CONST, kappa_abs0=10.0 / dx, kappa_es0=0.4)
+    x = (np.arange(n1) + 0.5) * dx
+    P = np.zeros((NP, 1, 1, n1))
+    P[RHO] = 1.0
+    P[UU] = 1e-2 * (1.0 + perturb * np.sin(2 * np.pi * x))
+    P[ER] = 2.0 * a_rad * T0 ** 4
+    return cfg, P
+
+
+# --- Kerr-Schild torus ---------------------------------------------------------
+
+def _ks_setup(n, a=0.9375, hslope=0.3, rin=1.2, rout=50.0):
+    cfg = base_params()
+    x1a, x1b = math.log(rin), math.log(rout)
+    cfg.update(n=list(n), x0=[x1a, 0.0, 0.0],
+               dx=[(x1b - x1a) / n[0], 1.0 / n[1], 1.0 / n[2]],
+               metric=1, a_spin=a, R0=0.0, hslope=hslope,
+               bc=[OUTFLOW, OUTFLOW, POLAR, POLAR, PERIODIC, PERIODIC])
+    return cfg
+
+
+def _theta(x2, h):
+    return np.pi * x2 + 0.5 * (1.0 - h) * np.sin(2 * np.pi * x2)
+
+
+def _gaussian_torus(r, th):
+    return np.exp(-((r - 15.0) / 4.0) ** 2 - (np.cos(th) / 0.3) ** 2)
+
+
+def torus(n=(64, 32, 16), seed=12345):
+    """Seeded Kerr-Schild torus, a = 0.9375, r in [1.2, 50] log-spaced,
+    theta concentrated toward the equator (h = 0.3):
+    rho = max(G(r, theta) (1 + 0.02 sin phi_k), 1e-6 r^-1.5) with G a Gaussian
+    in (r - 15, cos theta) and phi_k a random phase per zone;
+    u_g = 0.01 rho^(4/3); gas and radiation at rest in the ZAMO frame;
+    radiation in LTE (Ebar = a_rad T^4) with p_rad = p_gas at the density
+    maximum; Kramers absorption (tau_abs = 10 per zone at the maximum) plus
+    electron scattering; B from A_phi ~ max(rho - 0.2, 0) scaled so that
+    max p_gas / max p_mag = 100."""
+    cfg = _ks_setup(n)
+    n1, n2, n3 = n
+    a, h = cfg["a_spin"], cfg["hslope"]
+    gam = cfg["gam"]
+    x1c = cfg["x0"][0] + (np.arange(n1) + 0.5) * cfg["dx"][0]
+    x2c = (np.arange(n2) + 0.5) * cfg["dx"][1]
+    x1f = cfg["x0"][0] + np.arange(n1 + 1) * cfg["dx"][0]
+    x2f = np.arange(n2 + 1) * cfg["dx"][1]
+    r = np.exp(x1c)[None, None, :]
+    th = _theta(x2c, h)[None, :, None]
+    phase = rng(seed).uniform(0.0, 2 * np.pi, size=(n3, n2, n1))
+    rho = np.maximum(_gaussian_torus(r, th) * (1.0 + 0.02 * np.sin(phase)), 1e-6 * r ** -1.5)
+    ug = 0.01 * rho ** (4.0 / 3.0)
+    T0 = (gam - 1.0) * 0.01
+    a_rad = 3.0 / T0 ** 3  # a T0^4 / 3 = p_gas at rho = 1
+    T = (gam - 1.0) * ug / rho
+    # vector potential at cell corners (axisymmetric, unperturbed density)
+    rf = np.exp(x1f)[None, :]
+    thf = _theta(x2f, h)[:, None]
+    A = np.maximum(_gaussian_torus(rf, thf) - 0.2, 0.0)  # [n2+1, n1+1]
+    # static-observer metric pieces at cell centres (closed forms of Kerr-Schild)
+    r2 = np.exp(x1c)[None, :]
+    th2 = _theta(x2c, h)[:, None]
+    Sig = r2 ** 2 + a * a * np.cos(th2) ** 2
+    drdx1 = r2
+    dthdx2 = np.pi * (1.0 + (1.0 - h) * np.cos(2 * np.pi * x2c))[:, None]
+    gdet = Sig * np.abs(np.sin(th2)) * drdx1 * dthdx2 * 2 * np.pi
+    B1c = (A[1:, :-1] + A[1:, 1:] - A[:-1, :-1] - A[:-1, 1:]) / (2 * cfg["dx"][1] * gdet)
+    B2c = -(A[:-1, 1:] + A[1:, 1:] - A[:-1, :-1] - A[1:, :-1]) / (2 * cfg["dx"][0] * gdet)
+    alpha2 = 1.0 / (1.0 + 2 * r2 / Sig)
+    g11 = (1.0 + 2 * r2 / Sig) * drdx1 ** 2
+    g22 = Sig * dthdx2 ** 2
+    bsq = alpha2 * (g11 * B1c ** 2 + g22 * B2c ** 2)
+    pg = (gam - 1.0) * ug
+    pb_max = 0.5 * bsq.max()
+    scale = math.sqrt(pg.max() / (100.0 * pb_max)) if pb_max > 0 else 0.0
+    P = np.zeros((NP, n3, n2, n1))
+    P[RHO] = rho
+    P[UU] = ug
+    P[B1] = (scale * B1c)[None, :, :]
+    P[B2] = (scale * B2c)[None, :, :]
+    P[ER] = a_rad * T ** 4
+    dx1 = cfg["dx"][0]
+    kK = 10.0 * T0 ** 3.5 / (15.0 * dx1)
+    cfg.update(a_rad=a_rad, opacity=OPAC_KRAMERS, kappa_abs0=kK, kappa_es0=0.4,
+               T_kappa_min=1e-3 * T0,
+               floor_rho0=1e-6, floor_rho_pow=-1.5, floor_u0=1e-8, floor_u_pow=-2.5)
+    return cfg, P
+
+
+# --- Minkowski boxes -------------------------------------------------------------
+
+def minkowski_box(n=(16, 16, 16), seed=7, B_amp=0.05, vmax=0.3, kappa=(1e-2, 1e2),
+                  recon=PPM, flux=LAXF):
+    """Periodic 3D Minkowski box with random smooth-ish gas, field and
+    radiation: rho log-normal (sigma 0.5), u_g = 0.01 rho (1 + noise),
+    random velocities up to vmax, a random field of amplitude B_amp, a
+    Gaussian radiation pulse, and a constant per-density absorption opacity
+    (kappa_abs per length = kappa_abs0 * rho)."""
+    cfg = base_params()
+    n1, n2, n3 = n
+    cfg.update(n=list(n), dx=[1.0 / n1, 1.0 / n2, 1.0 / n3], recon=recon, flux=flux)
+    g = rng(seed)
+    shape = (n3, n2, n1)
+    P = np.zeros((NP,) + shape)
+    P[RHO] = np.exp(0.5 * g.standard_normal(shape))
+    P[UU] = 0.01 * P[RHO] * (1.0 + 0.2 * g.uniform(-1, 1, shape))
+    v = g.standard_normal((3,) + shape)
+    v /= np.linalg.norm(v, axis=0, keepdims=True)
+    speed = g.uniform(0.0, vmax, shape)
+    gamma = 1.0 / np.sqrt(1.0 - speed ** 2)
+    P[U1:U3 + 1] = v * (gamma * speed)[None]
+    P[B1:B3 + 1] = B_amp * g.uniform(-1, 1, (3,) + shape)
+    T = (cfg["gam"] - 1.0) * P[UU] / P[RHO]
+    cfg["a_rad"] = 1e-2 / ((cfg["gam"] - 1.0) * 1e-2) ** 4
+    zc = [(np.arange(m) + 0.5) / m - 0.5 for m in n]
+    R2 = zc[2][:, None, None] ** 2 + zc[1][None, :, None] ** 2 + zc[0][None, None, :] ** 2
+    P[ER] = cfg["a_rad"] * T ** 4 * (1.0 + 10.0 * np.exp(-R2 / 0.1 ** 2))
+    ur = g.standard_normal((3,) + shape) * 0.05
+    P[UR1:UR3 + 1] = ur
+    kap = math.exp(g.uniform(math.log(kappa[0]), math.log(kappa[1])))
+    cfg.update(opacity=OPAC_CONST, kappa_abs0=kap, kappa_es0=0.4 * kap / 10.0)
+    return cfg, P
+
+
+def thin_pulse(n=(32, 32, 32), L=100.0, w=5.0, T_a=1e6):
+    """Optically thin 3D radiation pulse (Sec. 5.3): kappa = 0, rho0 = 1,
+    gas temperature T_a, Ebar = a_rad T_a^4 (1 + 100 exp(-r^2/w^2))^4 in
+    radiation temperature, centred in a periodic box of side L.
+    Temperatures are in code units of m_b c^2/k_b."""
+    cfg = base_params()
+    n1, n2, n3 = n
+    cfg.update(n=list(n), x0=[-L / 2] * 3, dx=[L / n1, L / n2, L / n3],
+               opacity=OPAC_CONST, kappa_abs0=0.0, kappa_es0=0.0)
+    Tg = T_a / 1.0888e13  # K -> m_b c^2 / k_b
+    cfg["a_rad"] = 1.0
+    zc = [cfg["x0"][i] + (np.arange(m) + 0.5) * cfg["dx"][i] for i, m in enumerate(n)]
+    R2 = zc[2][:, None, None] ** 2 + zc[1][None, :, None] ** 2 + zc[0][None, None, :] ** 2
+    P = np.zeros((NP, n3, n2, n1))
+    P[RHO] = 1.0
+    P[UU] = Tg / (cfg["gam"] - 1.0)
+    Trad = Tg * (1.0 + 100.0 * np.exp(-R2 / w ** 2))
+    P[ER] = cfg["a_rad"] * Trad ** 4
+    return cfg, P
+
+
+def random_states(n, seed=3, metric=0, gamma_max=50.0, magnetised=True):
+    """Random point states for per-zone tests: positions x[n,4] (internal
+    coordinates) and primitives P[n,12] spanning density, temperature,
+    Lorentz factor (up to gamma_max) and radiation ranges, plus a parameter
+    dict for the chosen metric (0 Minkowski, 1 Kerr-Schild a = 0.9375)."""
+    g = rng(seed)
+    cfg = base_params() if metric == 0 else _ks_setup((64, 32, 16))
+    cfg.update(a_rad=1.0, opacity=OPAC_CONST, kappa_abs0=1.0, kappa_es0=0.4)
+    x = np.zeros((n, 4))
+    if metric == 0:
+        x[:, 1:] = g.uniform(0, 1, (n, 3))
+    else:
+        x[:, 1] = np.log(g.uniform(1.2, 50.0, n))
+        x[:, 2] = g.uniform(0.03, 0.97, n)
+        x[:, 3] = g.uniform(0, 1, n)
+    P = np.zeros((n, NP))
+    P[:, RHO] = np.exp(g.uniform(np.log(1e-4), np.log(1e2), n))
+    P[:, UU] = P[:, RHO] * np.exp(g.uniform(np.log(1e-5), np.log(10.0), n))
+    lg = g.uniform(0.0, np.log(gamma_max), n)
+    gam = np.exp(lg)
+    d = g.standard_normal((n, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    P[:, U1:U3 + 1] = d * np.sqrt(gam ** 2 - 1.0)[:, None]
+    if magnetised:
+        P[:, B1:B3 + 1] = g.standard_normal((n, 3)) * np.sqrt(P[:, RHO])[:, None] * 0.3
+    P[:, ER] = P[:, UU] * np.exp(g.uniform(np.log(1e-3), np.log(1e3), n))
+    lgr = g.uniform(0.0, np.log(20.0), n)
+    gr = np.exp(lgr)
+    d2 = g.standard_normal((n, 3))
+    d2 /= np.linalg.norm(d2, axis=1, keepdims=True)
+    P[:, UR1:UR3 + 1] = d2 * np.sqrt(gr ** 2 - 1.0)[:, None]
+    if metric == 1:
+        # coordinate components: scale by the local radius so that the
+        # physical speeds stay in range (g_ii grows like r^2 in these charts)
+        r = np.exp(x[:, 1])
+        for c, s in ((U1, r), (U2, r * np.pi), (U3, r * 2 * np.pi)):
+            P[:, c] /= s
+            P[:, c + 7] /= s
+        P[:, B1:B3 + 1] /= r[:, None] ** 2
+    return cfg, x, P
