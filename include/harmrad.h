@@ -1,0 +1,214 @@
+/*
+ * harmrad.h -- C ABI of the GB300 GRRMHD + M1 time-step library.
+ *
+ * The library advances the equations of general-relativistic radiation
+ * magnetohydrodynamics with the M1 closure on a fixed Kerr-Schild or
+ * Minkowski metric by one full time step, following Sec. 4 of McKinney,
+ * Tchekhovskoy, Sadowski & Narayan (2014), "Three-dimensional GRRMHD
+ * simulation of super-Eddington accretion, using a new code HARMRAD with M1
+ * closure":
+ *   - the RK3 method, same coefficients for explicit and implicit parts
+ *     (Sec. 4.1, last paragraph);
+ *   - per sub-step the algorithm of Sec. 4.2: ghost fill, U(P), geometric
+ *     source, PPM/MC reconstruction (Sec. 4.3), face fluxes and wave speeds
+ *     (Sec. 4.4), HLL or LAXF (Eqs. hll, lax), flux-CT EMFs, the update, and
+ *     the implicit four-force solve (Sec. 4.7-4.11, Eq. source3) by a 4D
+ *     Newton-Raphson (Eq. newton) with gas 1D_W (Sec. 4.5) and M1 (Sec. 4.6)
+ *     inversions and back-ups.
+ *
+ * Units: c = G = M = 1, Heaviside-Lorentz magnetic field (Sec. 2).
+ *
+ * Primitive layout (12 FP64 values per zone, index order fixed):
+ *   0 rho0  1 u_g  2-4 u~^i (ZAMO-relative gas 4-velocity, Sec. 2)
+ *   5-7 B^i (lab-frame field)  8 Ebar (radiation-frame energy density)
+ *   9-11 u~^i_rad (ZAMO-relative radiation-frame 4-velocity).
+ * Conserved layout (densitised by sqrt(-g), Sec. 4 list of U_q):
+ *   0 rho0 u^t  1 T^t_t + rho0 u^t  2-4 T^t_i  5-7 B^i  8 R^t_t  9-11 R^t_i.
+ * Grid arrays exchanged through this API hold ACTIVE zones only, layout
+ * [12][n3][n2][n1] with i (x1) fastest, contiguous FP64.
+ *
+ * Ownership and streams: the library owns all device state of a context.
+ * Caller buffers are only read or written during the call, in order on the
+ * CUDA stream given to harmrad_init (host buffers: the call returns after the
+ * copy has completed).  Device pointers must be device memory of the current
+ * device.  No call throws; every int-returning call reports through its return
+ * code: 0 success, > 0 a warning, < 0 an error (see HARMRAD_E_*).
+ */
+#ifndef HARMRAD_H
+#define HARMRAD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HARMRAD_NPRIM 12
+
+/* return codes */
+#define HARMRAD_OK 0
+#define HARMRAD_W_BACKUP_USED 1   /* some zones took the neighbour-average back-up */
+#define HARMRAD_E_ARG (-1)        /* invalid argument or unsupported combination */
+#define HARMRAD_E_CUDA (-2)       /* a CUDA runtime call failed */
+#define HARMRAD_E_OOM (-3)        /* device allocation failed */
+#define HARMRAD_E_NAN_INPUT (-4)  /* primitives given to set_prims are not finite */
+#define HARMRAD_E_STATE (-5)      /* call out of order (e.g. step before set_prims) */
+
+/* boundary conditions (bc[2*d] lower, bc[2*d+1] upper face of direction d) */
+#define HARMRAD_BC_PERIODIC 0
+#define HARMRAD_BC_OUTFLOW 1
+#define HARMRAD_BC_POLAR 2     /* theta direction of the Kerr-Schild grid only */
+
+#define HARMRAD_METRIC_MINKOWSKI 0
+#define HARMRAD_METRIC_KS 1
+
+#define HARMRAD_OPAC_CONST 0    /* kappa_abs = kappa_abs0 * rho0 (per length) */
+#define HARMRAD_OPAC_KRAMERS 1  /* kappa_abs = kappa_abs0 * rho0^2 * max(T,T_min)^-3.5 */
+
+#define HARMRAD_RECON_PPM 0
+#define HARMRAD_RECON_MC 1
+#define HARMRAD_FLUX_LAXF 0
+#define HARMRAD_FLUX_HLL 1
+
+#define HARMRAD_PREC_FP64 0   /* every stage in FP64 */
+#define HARMRAD_PREC_SPLIT 1  /* reconstruction, Riemann fluxes, EMFs in FP32 */
+
+/*
+ * Run parameters.  Internal coordinates are uniform (Sec. 2): cell (i,j,k)
+ * has centre x0 + (i+1/2) dx.  For the Kerr-Schild metric
+ * r = R0 + exp(x1), theta = pi x2 + (1-hslope)/2 sin(2 pi x2), phi = 2 pi x3.
+ * A direction with n = 1 is degenerate (no fluxes, no ghosts).
+ */
+typedef struct harmrad_params {
+  int n[3];
+  double x0[3], dx[3];
+  int metric;
+  double a_spin, R0, hslope;
+  int bc[6];
+  double gam;       /* adiabatic index of the gas, p = (gam-1) u_g */
+  double a_rad;     /* radiation constant: Planck energy density a_rad T^4 */
+  double courant;   /* Courant factor of the CFL time step (Sec. 4.4) */
+  int opacity;
+  double kappa_abs0, kappa_es0, kappa_scale, T_kappa_min;
+  int recon, flux;
+  double gamma_rad_max, gamma_gas_max;   /* Lorentz-factor caps (Sec. 4.6, 5) */
+  double floor_rho0, floor_rho_pow, floor_u0, floor_u_pow;  /* floors f0 r^pow */
+  double bsq_rho_max, bsq_u_max, u_rho_max;                 /* magnetisation caps */
+  int newton_max;      /* Newton step limit per method (Sec. 4.10), <= 60 */
+  double newton_tol;   /* PMHD tolerance on e_T (Sec. 4.10) */
+  int precision;       /* HARMRAD_PREC_* */
+} harmrad_params;
+
+/* Per-zone outcome codes written by harmrad_get_status (worst over the three
+ * stages of the last step). */
+#define HARMRAD_ZONE_PMHD 0    /* PMHD Newton accepted */
+#define HARMRAD_ZONE_URAD 1    /* URAD Newton accepted after PMHD */
+#define HARMRAD_ZONE_BACKUP 2  /* neither reached e_T <= 1e-7: neighbour average */
+
+typedef struct harmrad_stats {
+  double dt;                   /* time step used by the last harmrad_step */
+  long long zone_stages;       /* implicit solves in the last step */
+  long long pmhd_ok, urad_ok, backup;
+  long long newton_iters;      /* Newton steps summed over all solves */
+  int kernel_launches;         /* kernels one harmrad_step launches */
+  int graph;                   /* 1 if the step is replayed as a CUDA graph */
+} harmrad_stats;
+
+typedef struct harmrad_ctx harmrad_ctx;
+
+/* Allocate a context for one grid on the current device.  stream: a
+ * cudaStream_t (NULL = legacy default stream).  Returns HARMRAD_E_ARG for
+ * invalid parameters (non-positive sizes, POLAR on a non-theta face or with
+ * an odd n3 > 1, newton_max outside [1,60], ...), HARMRAD_E_OOM when device
+ * memory is exhausted. */
+int harmrad_init(const harmrad_params* p, void* stream, harmrad_ctx** out);
+
+/* Release all device state of the context (NULL is ignored). */
+void harmrad_destroy(harmrad_ctx* ctx);
+
+/* Load the active-zone primitives ([12][n3][n2][n1] FP64).  on_device != 0:
+ * P is a device pointer, else host memory.  Returns HARMRAD_E_NAN_INPUT if any
+ * value is not finite, or if rho0, u_g or Ebar is not positive. */
+int harmrad_set_prims(harmrad_ctx* ctx, const double* P, int on_device);
+
+/* Copy the active-zone primitives out (same layout). */
+int harmrad_get_prims(harmrad_ctx* ctx, double* P, int on_device);
+
+/* CFL time step of the current state: Courant factor times the minimum over
+ * zones of 1 / sum_d (v_d / dx_d), v_d the largest gas or radiation signal
+ * speed on the two d-faces of the zone (Sec. 4.4, last paragraph). */
+int harmrad_cfl_dt(harmrad_ctx* ctx, double* dt);
+
+/* Advance one full RK3 step.  dt <= 0 selects the CFL step of the current
+ * state (computed on the device).  The call only enqueues work on the
+ * context's stream and does not wait for it; solver outcomes (back-up use,
+ * iteration counts) are read afterwards with harmrad_get_stats. */
+int harmrad_step(harmrad_ctx* ctx, double dt);
+
+/* Advance one full RK3 step with host input and output: copies P_in (host,
+ * active zones) to the device, steps with dt (<= 0: CFL), copies the result to
+ * P_out (host).  P_in and P_out may alias. */
+int harmrad_step_host(harmrad_ctx* ctx, const double* P_in, double* P_out, double dt);
+
+/* Solver statistics of the last step (synchronises the stream).  Returns
+ * HARMRAD_W_BACKUP_USED if any zone took the neighbour-average back-up. */
+int harmrad_get_stats(harmrad_ctx* ctx, harmrad_stats* st);
+
+/* Per-zone outcome bytes of the last step ([n3][n2][n1]). */
+int harmrad_get_status(harmrad_ctx* ctx, unsigned char* st, int on_device);
+
+/* Per-zone Newton iteration totals of the last step ([n3][n2][n1] int32). */
+int harmrad_get_iters(harmrad_ctx* ctx, int* it, int on_device);
+
+/* Face fluxes of direction dir (1..3) for the current primitives after ghost
+ * fill, reconstruction, Riemann solve and flux-CT, as the first sub-step of a
+ * step would compute them; layout [12][n3'][n2'][n1'] with n_dir' = n_dir + 1
+ * (faces 0..n_dir), FP64, host memory.  Diagnostic for tests. */
+int harmrad_compute_fluxes(harmrad_ctx* ctx, int dir, double* F_host);
+
+/* Point-wise physics at n independent points (device pointers, row-major):
+ * x[n][4] internal coordinates, P[n][12] primitives ->
+ * U[n][12] conserved, SM[n][12] geometric source, F[n][3][12] fluxes,
+ * speeds[n][3][4] (gas vmin, vmax, rad vmin, vmax per direction).  Any output
+ * pointer may be NULL. */
+int harmrad_zone_physics(const harmrad_params* p, int n, const double* x, const double* P,
+                         double* U, double* SM, double* F, double* speeds, void* stream);
+
+/* Implicit four-force solve of n independent zones (device pointers):
+ * x[n][4], Ustar[n][12] explicit conserved state, Ps[n][12] guess primitives,
+ * h[n] = b_s dt -> Pout[n][12], eT[n], iters[n], method[n] (HARMRAD_ZONE_*).
+ * Same solver as harmrad_step (Sec. 4.7-4.11). */
+int harmrad_zone_implicit(const harmrad_params* p, int n, const double* x, const double* Ustar,
+                          const double* Ps, const double* h, double* Pout, double* eT, int* iters,
+                          unsigned char* method, void* stream);
+
+/* Kernel classes timed by harmrad_profile_step. */
+#define HARMRAD_K_BC 0        /* ghost-zone fill */
+#define HARMRAD_K_PREP 1      /* per-cell metric factors and flattener inputs */
+#define HARMRAD_K_FLATTEN 2   /* PPM shock flattener */
+#define HARMRAD_K_FACE 3      /* reconstruction + face physics + Riemann flux */
+#define HARMRAD_K_CT 4        /* flux-CT EMFs */
+#define HARMRAD_K_UPDATE 5    /* update + geometric source + PMHD implicit solve */
+#define HARMRAD_K_RETRY 6     /* URAD retry queue */
+#define HARMRAD_K_BACKUP 7    /* neighbour-average back-up */
+#define HARMRAD_K_CFL 8       /* CFL reduction */
+#define HARMRAD_K_OTHER 9     /* memsets, time-step upload */
+#define HARMRAD_K_CLASSES 10
+
+typedef struct harmrad_kernel_times {
+  double ms[HARMRAD_K_CLASSES];  /* summed device time per class, milliseconds */
+  int launches[HARMRAD_K_CLASSES];
+  int total_launches;
+} harmrad_kernel_times;
+
+/* Advance one full step like harmrad_step, launched without the CUDA graph and
+ * with a CUDA event recorded after every kernel on the context's stream; the
+ * time between consecutive events is summed per kernel class.  Synchronises
+ * the stream.  For benchmarking and profiling. */
+int harmrad_profile_step(harmrad_ctx* ctx, double dt, harmrad_kernel_times* out);
+
+/* Human-readable text of a return code. */
+const char* harmrad_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HARMRAD_H */

@@ -451,11 +451,13 @@ void substep(Ctx& c, int s, double dt) {
         else if (info.method == ORC_OK_URAD) c.counts[1]++;
         else c.counts[2]++;
         failed[a] = info.method == ORC_BACKUP;
+        apply_floors(c.p, G, Pn);
         for (int q = 0; q < NP; ++q) Pnew[(long)q * c.ntot + t] = Pn[q];
       }
   // Back-up (Sec. 4.11): replace failed zones by the average of their good
   // active face neighbours (all active neighbours if none is good); B keeps
-  // its constrained-transport value.
+  // its constrained-transport value.  Every solution was floored above, and
+  // the floors are applied once more after averaging (they are idempotent).
   std::vector<double> Pavg = Pnew;
   for (int k = 0; k < c.n[2]; ++k)
     for (int j = 0; j < c.n[1]; ++j)

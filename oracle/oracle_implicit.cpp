@@ -38,7 +38,17 @@ struct Res {
 // Normalised errors (Sec. 4.8): each row divided by the sum of the absolute
 // values of the terms that make it up; the three spatial rows share one norm
 // built in an orthonormal basis.  e_T takes, row by row, the larger of the gas
-// and radiation errors; e_I uses the iterated rows only.
+// and radiation errors; e_I uses the iterated rows only.  The orthonormal
+// basis is the ZAMO frame: a covariant spatial component w_k has orthonormal
+// size |w_k| sqrt(gamma^{kk}), gamma^{ij} = g^{ij} - g^{ti} g^{tj} / g^{tt}, the
+// inverse metric of the t = const slice, positive also inside the horizon
+// (where g^{rr} < 0).  The spatial norm also carries the terms of the energy
+// row: momentum is bounded by energy, and a field at rest (all momentum terms
+// zero) must not have its round-off divided by round-off.
+double zamo_scale(const Geom& G, int k) {
+  return std::sqrt(G.gcon[k][k] - G.gcon[0][k] * G.gcon[0][k] / G.gcon[0][0]);
+}
+
 void normalise(const Sys& s, const double Tc[4], const double Rc[4], const double Gc[4],
                bool iter_gas, Res& r) {
   const Geom& G = *s.G;
@@ -46,14 +56,16 @@ void normalise(const Sys& s, const double Tc[4], const double Rc[4], const doubl
   double dr0 = std::fabs(Rc[0]) + std::fabs(s.Rstar[0]) + s.h * std::fabs(Gc[0]);
   double dgs = 0.0, drs = 0.0;
   for (int k = 1; k < 4; ++k) {
-    double sk = std::sqrt(G.gcon[k][k]);
+    double sk = zamo_scale(G, k);
     dgs += sk * (std::fabs(Tc[k]) + std::fabs(s.Tstar[k]) + s.h * std::fabs(Gc[k]));
     drs += sk * (std::fabs(Rc[k]) + std::fabs(s.Rstar[k]) + s.h * std::fabs(Gc[k]));
   }
+  dgs += dg0;
+  drs += dr0;
   r.eg[0] = dg0 > 0.0 ? std::fabs(r.Eg[0]) / dg0 : 0.0;
   r.er[0] = dr0 > 0.0 ? std::fabs(r.Er[0]) / dr0 : 0.0;
   for (int k = 1; k < 4; ++k) {
-    double sk = std::sqrt(G.gcon[k][k]);
+    double sk = zamo_scale(G, k);
     r.eg[k] = dgs > 0.0 ? std::fabs(r.Eg[k]) * sk / dgs : 0.0;
     r.er[k] = drs > 0.0 ? std::fabs(r.Er[k]) * sk / drs : 0.0;
   }

@@ -1,0 +1,82 @@
+// Host-side context of the harmrad library (internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "../../include/harmrad.h"
+#include "hr_common.cuh"
+
+namespace hr {
+struct Bufs;
+}
+
+struct harmrad_ctx {
+  harmrad_params prm;
+  hr::DevParams dp;
+  cudaStream_t stream;
+  bool own_stream;
+  int device;
+  int sms;
+  size_t real_size;  // 8 (FP64) or 4 (split)
+  // device memory
+  double* P;
+  double* Un;
+  void* F[3];
+  void* spd[3];
+  void* aux;
+  void* flat[3];
+  void* emf;
+  double* dt;
+  unsigned char* status;
+  int* iters;
+  unsigned char* failed;
+  int* qcount;
+  int* qzone;
+  double* qdata;
+  int* fzone;
+  double* ftmp;
+  unsigned long long* stats;
+  unsigned long long* dtmin;
+  double* stage_buf;      // [12][nact] active-layout staging for set/get
+  int* flag;              // validation flag
+  double* host_dt;        // pinned host scalar for dt uploads
+  bool has_prims;
+  // CUDA graphs of a full step: [0] dt given, [1] CFL dt
+  cudaGraphExec_t graph[2];
+  bool use_graph;
+  int launches_per_step;
+  double last_dt;
+  // per-kernel profiling (harmrad_profile_step): an event after every launch
+  bool profiling;
+  int nev;
+  cudaEvent_t ev[512];
+  int ev_tag[512];
+};
+
+namespace hr {
+// Record an event tagged with the kernel class after a launch (profiling only).
+inline void mark(harmrad_ctx* c, int tag) {
+  if (!c->profiling || c->nev >= 512) return;
+  if (!c->ev[c->nev]) cudaEventCreate(&c->ev[c->nev]);
+  c->ev_tag[c->nev] = tag;
+  cudaEventRecord(c->ev[c->nev], c->stream);
+  c->nev++;
+}
+}  // namespace hr
+
+namespace hr {
+
+// Launch sequences, instantiated per metric in hr_run_mink.cu / hr_run_ks.cu.
+// Each returns the number of kernels it enqueued, or a negative error code.
+template <int MET>
+struct Run {
+  static int faces(harmrad_ctx* c, bool fresh);     // ghosts, prep, flattener, fluxes, flux-CT
+  static int cfl(harmrad_ctx* c);                   // faces(fresh) + reduction into *dt
+  static int solve(harmrad_ctx* c, int stage);      // update + implicit, retry, back-up
+  static int zone_physics(const DevParams& dp, int n, const double* x, const double* P, double* U,
+                          double* SM, double* F, double* speeds, cudaStream_t st, int sms);
+  static int zone_implicit(const DevParams& dp, int n, const double* x, const double* Us,
+                           const double* Ps, const double* h, double* Pout, double* eT, int* iters,
+                           unsigned char* method, cudaStream_t st, int sms);
+};
+
+}  // namespace hr

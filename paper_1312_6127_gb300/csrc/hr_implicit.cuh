@@ -1,0 +1,452 @@
+// Implicit gas-radiation four-force solve of one zone (FP64), Sec. 4.7-4.10
+// of McKinney et al. (2014).
+//
+// Solves T^t_nu(x) - T*^t_nu = h G_nu(x) (Eq. source3) with rho0 u^t and B
+// fixed and the radiation taken from total energy-momentum conservation.
+// PMHD iterates the gas primitives x = (u_g, u~^i); URAD iterates x = R^t_nu
+// and recovers the gas from a 1D_W inversion inside every residual.  Newton
+// steps follow Eq. newton with D = 1 and a finite-difference Jacobian
+// (two-sided for PMHD, one-sided for URAD), normalised offset 1e-8, switching
+// to 1e-10 once e_I < 1e-9; the stopping rules of Sec. 4.10 (tolerance,
+// stalled error, repeated rises, tiny step, step limit) and the best-error
+// bookkeeping are applied.
+//
+// The four-force uses the rank-one-plus-isotropic form of the M1 tensor:
+// R^mu_a u^a = 4/3 Ebar (u_r.u) u_r^mu + 1/3 Ebar u^mu, so G_nu (Eq. Gcov) is a
+// combination of u_r_nu and u_nu and needs no 4x4 contraction.
+#pragma once
+#include "hr_phys.cuh"
+
+namespace hr {
+
+template <int MET>
+struct ImpSys {
+  Geo<MET, double> g;
+  double Dlab;   // rho0 u^t
+  double Ts[4];  // explicit T^t_nu, rest-mass flux added to the t row
+  double Rs[4];  // explicit R^t_nu
+  double B[3];
+  double h;      // b_s dt
+  double sgk[3]; // sqrt(gamma^{kk}) of the ZAMO slice
+};
+
+struct ImpRes {
+  double Eg[4], Er[4];
+  double eT, eI;
+  int negE;
+  bool ok;
+};
+
+// Gas and radiation state of an iterate: the pieces of the residual that the
+// final primitives need.
+struct ImpState {
+  double rho, ug, Pr[4];
+  double Rt_pre[4];
+};
+
+template <int MET>
+__device__ __forceinline__ void four_force_rad(const DevParams& p, double rho, double ug,
+                                               const double ucon[4], const double ucov[4],
+                                               const double urc[4], const double urv[4], double E,
+                                               double G[4]) {
+  double kabs, ksca;
+  opacity<double>(p, rho, ug, &kabs, &ksca);
+  double T = (p.gam - 1.0) * ug / rho;
+  double T2 = T * T;
+  double lam = kabs * p.a_rad * T2 * T2;
+  double uru = urv[0] * ucon[0] + urv[1] * ucon[1] + urv[2] * ucon[2] + urv[3] * ucon[3];
+  double c1 = (4.0 / 3.0) * E * uru, c2 = E * (1.0 / 3.0);
+  double uRu = c1 * uru - c2;
+  double kt = kabs + ksca;
+  double A = -kt * c1;
+  double C = -(kt * c2 + lam + ksca * uRu);
+  (void)urc;
+#pragma unroll
+  for (int n = 0; n < 4; ++n) G[n] = A * urv[n] + C * ucov[n];
+}
+
+template <int MET>
+__device__ __forceinline__ void normalise(const ImpSys<MET>& s, const double Tc[4],
+                                          const double Rc[4], const double G[4], bool iter_gas,
+                                          ImpRes& r) {
+  double dg0 = fabs(Tc[0]) + fabs(s.Ts[0]) + s.h * fabs(G[0]);
+  double dr0 = fabs(Rc[0]) + fabs(s.Rs[0]) + s.h * fabs(G[0]);
+  double dgs = 0.0, drs = 0.0;
+#pragma unroll
+  for (int k = 1; k < 4; ++k) {
+    dgs += s.sgk[k - 1] * (fabs(Tc[k]) + fabs(s.Ts[k]) + s.h * fabs(G[k]));
+    drs += s.sgk[k - 1] * (fabs(Rc[k]) + fabs(s.Rs[k]) + s.h * fabs(G[k]));
+  }
+  // the spatial norm also carries the energy-row terms (momentum is bounded
+  // by energy; a field at rest must not divide round-off by round-off)
+  dgs += dg0;
+  drs += dr0;
+  double eg[4], er[4];
+  eg[0] = dg0 > 0.0 ? fabs(r.Eg[0]) / dg0 : 0.0;
+  er[0] = dr0 > 0.0 ? fabs(r.Er[0]) / dr0 : 0.0;
+  double idgs = dgs > 0.0 ? 1.0 / dgs : 0.0, idrs = drs > 0.0 ? 1.0 / drs : 0.0;
+#pragma unroll
+  for (int k = 1; k < 4; ++k) {
+    eg[k] = fabs(r.Eg[k]) * s.sgk[k - 1] * idgs;
+    er[k] = fabs(r.Er[k]) * s.sgk[k - 1] * idrs;
+  }
+  if (r.negE) eg[0] = er[0] = 0.0;
+  double sT = 0.0, sI = 0.0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    sT += fmax(eg[k], er[k]);
+    sI += iter_gas ? eg[k] : er[k];
+  }
+  r.eT = 0.25 * sT;
+  r.eI = 0.25 * sI;
+}
+
+// PMHD error function.  With norm == false only Eg is formed (Jacobian columns).
+template <int MET>
+__device__ __forceinline__ void pmhd_res(const DevParams& p, const ImpSys<MET>& s, const double x[4],
+                                         ImpRes& r, ImpState* st, bool norm) {
+  const auto& g = s.g;
+  double ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq;
+  fourvel<MET, double>(g, x[1], x[2], x[3], ucon, ucov, &gm);
+  double rho = s.Dlab / ucon[0];
+  bvec<MET, double>(g, ucon, ucov, s.B[0], s.B[1], s.B[2], bcon, bcov, &bsq);
+  double pg = (p.gam - 1.0) * x[0];
+  double wb = rho + x[0] + pg + bsq, pt = pg + 0.5 * bsq;
+  double Tc[4];
+  Tc[0] = wb * ucon[0] * ucov[0] + pt - bcon[0] * bcov[0] + rho * ucon[0];
+#pragma unroll
+  for (int k = 1; k < 4; ++k) Tc[k] = wb * ucon[0] * ucov[k] - bcon[0] * bcov[k];
+  double Rt[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) Rt[k] = s.Rs[k] - (Tc[k] - s.Ts[k]);
+  double Pr[4];
+  r.negE = rad_invert<MET>(p, g, Rt, 2, Pr);
+  double urc[4], urv[4], gr;
+  fourvel<MET, double>(g, Pr[1], Pr[2], Pr[3], urc, urv, &gr);
+  double e43 = (4.0 / 3.0) * Pr[0];
+  double Rc[4];
+  Rc[0] = e43 * urc[0] * urv[0] + Pr[0] * (1.0 / 3.0);
+#pragma unroll
+  for (int k = 1; k < 4; ++k) Rc[k] = e43 * urc[0] * urv[k];
+  double G[4];
+  four_force_rad<MET>(p, rho, x[0], ucon, ucov, urc, urv, Pr[0], G);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    r.Eg[k] = Tc[k] - s.Ts[k] - s.h * G[k];
+    r.Er[k] = Rc[k] - s.Rs[k] + s.h * G[k];
+  }
+  if (norm) {
+    normalise<MET>(s, Tc, Rc, G, true, r);
+    r.ok = isfinite(r.eT);
+  } else {
+    r.ok = true;
+  }
+  if (st) {
+    st->rho = rho;
+    st->ug = x[0];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      st->Pr[k] = Pr[k];
+      st->Rt_pre[k] = Rt[k];
+    }
+  }
+}
+
+__device__ __forceinline__ bool solve4(double A[4][4], double b[4], double z[4]) {
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    int piv = c;
+    double best = fabs(A[c][c]);
+#pragma unroll
+    for (int r = c + 1; r < 4; ++r)
+      if (fabs(A[r][c]) > best) {
+        best = fabs(A[r][c]);
+        piv = r;
+      }
+    if (best == 0.0 || !isfinite(best)) return false;
+    if (piv != c) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        double t = A[c][j];
+        A[c][j] = A[piv][j];
+        A[piv][j] = t;
+      }
+      double t = b[c];
+      b[c] = b[piv];
+      b[piv] = t;
+    }
+    double ip = 1.0 / A[c][c];
+#pragma unroll
+    for (int r = c + 1; r < 4; ++r) {
+      double f = A[r][c] * ip;
+#pragma unroll
+      for (int j = c; j < 4; ++j) A[r][j] -= f * A[c][j];
+      b[r] -= f * b[c];
+    }
+  }
+#pragma unroll
+  for (int i = 3; i >= 0; --i) {
+    double sum = b[i];
+#pragma unroll
+    for (int j = i + 1; j < 4; ++j) sum -= A[i][j] * z[j];
+    z[i] = sum / A[i][i];
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (!isfinite(z[i])) return false;
+  return true;
+}
+
+// Error history for the stalled-error checks: errors at the last five iterates.
+struct Hist {
+  double eT[6], eI[6];
+  int rises;
+};
+
+__device__ __forceinline__ bool stalled(Hist& hs, int k, double eT, double eI) {
+  // ring buffer: slot k % 6 holds iterate k
+  hs.eT[k % 6] = eT;
+  hs.eI[k % 6] = eI;
+  bool stop = false;
+  if (k > 5) {
+    if (eT > hs.eT[(k - 1) % 6]) {
+      hs.rises++;
+      if (hs.rises >= 5) stop = true;
+    }
+    double mT = (hs.eT[(k - 4) % 6] + hs.eT[(k - 3) % 6] + hs.eT[(k - 2) % 6]) / 3.0;
+    double mI = (hs.eI[(k - 4) % 6] + hs.eI[(k - 3) % 6] + hs.eI[(k - 2) % 6]) / 3.0;
+    if (eT > 0.5 * mT || eI > 0.5 * mI) stop = true;
+  }
+  return stop;
+}
+
+// PMHD Newton.  Returns the number of Newton steps; best_x / best_eT hold the
+// lowest-error iterate (best_eT = inf if no residual was finite).
+template <int MET>
+__device__ int newton_pmhd(const DevParams& p, const ImpSys<MET>& s, const double x0[4],
+                           double best_x[4], double* best_eT) {
+  double x[4] = {x0[0], x0[1], x0[2], x0[3]};
+  Hist hs;
+  hs.rises = 0;
+  *best_eT = HUGE_VAL;
+  int steps = 0;
+  double eps = 1e-8;
+  for (int k = 0;; ++k) {
+    ImpRes r;
+    pmhd_res<MET>(p, s, x, r, nullptr, true);
+    if (!r.ok) break;
+    if (r.eT < *best_eT) {
+      *best_eT = r.eT;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) best_x[i] = x[i];
+    }
+    if (r.eT < p.newton_tol) break;
+    if (stalled(hs, k, r.eT, r.eI)) break;
+    if (k >= p.newton_max) break;
+    if (r.eI < 1e-9) eps = 1e-10;
+    double umag = fmax(1.0, sqrt(s.g.sq3(x[1], x[2], x[3])));
+    double J[4][4];
+#pragma unroll 1
+    for (int j = 0; j < 4; ++j) {
+      double dj = (j == 0) ? eps * fabs(x[0]) : eps * umag / sqrt(s.g.gdd(j));
+      double xp[4] = {x[0], x[1], x[2], x[3]}, xm[4] = {x[0], x[1], x[2], x[3]};
+      xp[j] += dj;
+      xm[j] -= dj;
+      ImpRes rp, rm;
+      pmhd_res<MET>(p, s, xp, rp, nullptr, false);
+      pmhd_res<MET>(p, s, xm, rm, nullptr, false);
+      double i2d = 1.0 / (2.0 * dj);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) J[i][j] = (rp.Eg[i] - rm.Eg[i]) * i2d;
+    }
+    double E[4] = {r.Eg[0], r.Eg[1], r.Eg[2], r.Eg[3]}, dx[4];
+    if (!solve4(J, E, dx)) break;
+    double xn[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) xn[i] = x[i] - dx[i];
+    if (xn[0] < 0.0) xn[0] = 0.5 * fabs(xn[0]);
+    bool tiny = true;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (fabs(xn[i] - x[i]) > 10.0 * 2.220446049250313e-16 * fabs(x[i])) tiny = false;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x[i] = xn[i];
+    ++steps;
+    if (tiny) {
+      ImpRes rf;
+      pmhd_res<MET>(p, s, x, rf, nullptr, true);
+      if (rf.ok && rf.eT < *best_eT) {
+        *best_eT = rf.eT;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) best_x[i] = x[i];
+      }
+      break;
+    }
+  }
+  return steps;
+}
+
+// URAD error function: iterate R^t_nu; gas from 1D_W inversion of
+// T^t_nu = T*^t_nu - (x - R*^t_nu); radiation from the M1 inversion of x.
+template <int MET>
+__device__ __forceinline__ bool urad_res(const DevParams& p, const ImpSys<MET>& s, const double x[4],
+                                         const double Pg[5], double tol_inv, ImpRes& r,
+                                         double gas_out[5], double Pr[4], bool norm) {
+  const auto& g = s.g;
+  double Tt[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) Tt[k] = s.Ts[k] - (x[k] - s.Rs[k]);
+  double Pg12[12];
+  Pg12[UU] = Pg[1];
+  Pg12[U1] = Pg[2];
+  Pg12[U2] = Pg[3];
+  Pg12[U3] = Pg[4];
+  double T3[3] = {Tt[1], Tt[2], Tt[3]};
+  if (gas_invert<MET>(p, g, s.Dlab, Tt[0], T3, s.B, Pg12, tol_inv, gas_out) != 0) {
+    r.ok = false;
+    return false;
+  }
+  r.negE = rad_invert<MET>(p, g, x, 2, Pr);
+  double ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq;
+  fourvel<MET, double>(g, gas_out[2], gas_out[3], gas_out[4], ucon, ucov, &gm);
+  bvec<MET, double>(g, ucon, ucov, s.B[0], s.B[1], s.B[2], bcon, bcov, &bsq);
+  double rho = gas_out[0], ug = gas_out[1];
+  double pg = (p.gam - 1.0) * ug;
+  double wb = rho + ug + pg + bsq, pt = pg + 0.5 * bsq;
+  double Tc[4];
+  Tc[0] = wb * ucon[0] * ucov[0] + pt - bcon[0] * bcov[0] + rho * ucon[0];
+#pragma unroll
+  for (int k = 1; k < 4; ++k) Tc[k] = wb * ucon[0] * ucov[k] - bcon[0] * bcov[k];
+  double urc[4], urv[4], gr;
+  fourvel<MET, double>(g, Pr[1], Pr[2], Pr[3], urc, urv, &gr);
+  double e43 = (4.0 / 3.0) * Pr[0];
+  double Rc[4];
+  Rc[0] = e43 * urc[0] * urv[0] + Pr[0] * (1.0 / 3.0);
+#pragma unroll
+  for (int k = 1; k < 4; ++k) Rc[k] = e43 * urc[0] * urv[k];
+  double G[4];
+  four_force_rad<MET>(p, rho, ug, ucon, ucov, urc, urv, Pr[0], G);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    r.Eg[k] = Tc[k] - s.Ts[k] - s.h * G[k];
+    r.Er[k] = Rc[k] - s.Rs[k] + s.h * G[k];
+  }
+  if (norm) {
+    normalise<MET>(s, Tc, Rc, G, false, r);
+    r.ok = isfinite(r.eT);
+  } else {
+    r.ok = true;
+  }
+  return r.ok;
+}
+
+// URAD Newton: one-sided Jacobian, tolerance 1e-9, at most 20 x 6 gas
+// inversions; inversion failures in a Jacobian column retried with offsets
+// x10 up to 0.3.  Pg (gas guess: rho, u_g, u~^i) is updated by every
+// successful residual.  best_x / best_Pg / best_eT hold the best iterate.
+template <int MET>
+__device__ int newton_urad(const DevParams& p, const ImpSys<MET>& s, const double x0[4], double Pg[5],
+                           double best_x[4], double best_Pg[5], double* best_eT) {
+  double x[4] = {x0[0], x0[1], x0[2], x0[3]};
+  Hist hs;
+  hs.rises = 0;
+  *best_eT = HUGE_VAL;
+  int steps = 0, ninv = 0;
+  const int budget = 20 * 6;
+  double eps = 1e-8;
+  for (int k = 0;; ++k) {
+    ImpRes r;
+    double go[5], Pr[4];
+    ++ninv;
+    if (!urad_res<MET>(p, s, x, Pg, 1e-13, r, go, Pr, true)) break;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) Pg[i] = go[i];
+    if (r.eT < *best_eT) {
+      *best_eT = r.eT;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) best_x[i] = x[i];
+#pragma unroll
+      for (int i = 0; i < 5; ++i) best_Pg[i] = go[i];
+    }
+    if (r.eT < 1e-9) break;
+    if (stalled(hs, k, r.eT, r.eI)) break;
+    if (k >= p.newton_max || ninv >= budget) break;
+    if (r.eI < 1e-9) eps = 1e-10;
+    double J[4][4];
+    bool jok = true;
+#pragma unroll 1
+    for (int j = 0; j < 4 && jok; ++j) {
+      double scale = fabs(x[0]) * (j == 0 ? 1.0 : sqrt(s.g.gdd(j)));
+      bool done = false;
+#pragma unroll 1
+      for (double e = eps; e <= 0.3 && !done; e *= 10.0) {
+        double dj = e * scale;
+        if (dj == 0.0) break;
+        double xp[4] = {x[0], x[1], x[2], x[3]};
+        xp[j] += dj;
+        ImpRes rp;
+        double go2[5], Pr2[4];
+        ++ninv;
+        if (urad_res<MET>(p, s, xp, Pg, 1e-2 * e, rp, go2, Pr2, false)) {
+          double id = 1.0 / dj;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) J[i][j] = (rp.Er[i] - r.Er[i]) * id;
+          done = true;
+        }
+      }
+      if (!done) jok = false;
+    }
+    if (!jok) break;
+    double E[4] = {r.Er[0], r.Er[1], r.Er[2], r.Er[3]}, dx[4];
+    if (!solve4(J, E, dx)) break;
+    double xn[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) xn[i] = x[i] - dx[i];
+    if (xn[0] > 0.0) xn[0] = -0.5 * fabs(xn[0]);
+    bool tiny = true;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (fabs(xn[i] - x[i]) > 10.0 * 2.220446049250313e-16 * fabs(x[i])) tiny = false;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x[i] = xn[i];
+    ++steps;
+    if (tiny) {
+      ImpRes rf;
+      double go3[5], Pr3[4];
+      ++ninv;
+      if (urad_res<MET>(p, s, x, Pg, 1e-13, rf, go3, Pr3, true) && rf.eT < *best_eT) {
+        *best_eT = rf.eT;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) best_x[i] = x[i];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) best_Pg[i] = go3[i];
+      }
+      break;
+    }
+  }
+  return steps;
+}
+
+template <int MET>
+__device__ __forceinline__ void build_sys(const DevParams& p, const Geo<MET, double>& g,
+                                          const double Us[12], double h, ImpSys<MET>& s) {
+  s.g = g;
+  double igd = 1.0 / g.gdet;
+  s.Dlab = Us[0] * igd;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    s.Ts[k] = Us[1 + k] * igd;
+    s.Rs[k] = Us[8 + k] * igd;
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) s.B[i] = Us[5 + i] * igd;
+  s.h = h;
+  // orthonormal (ZAMO) size of covariant spatial components:
+  // sqrt(gamma^{kk}), gamma^{kk} = g^{kk} - (g^{tk})^2 / g^{tt} > 0 everywhere
+  // on the slice, inside the horizon too
+#pragma unroll
+  for (int k = 1; k < 4; ++k) s.sgk[k - 1] = sqrt(g.Gdd(k) - g.Gt(k) * g.Gt(k) / g.Gtt());
+  (void)p;
+}
+
+}  // namespace hr

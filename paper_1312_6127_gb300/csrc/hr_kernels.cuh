@@ -1,0 +1,899 @@
+// Kernels of one RK3 sub-step (Sec. 4.2 of McKinney et al. 2014) for sm_103a.
+//
+// Data layout in HBM: structure of arrays, one FP64 plane per primitive,
+// [12][N3][N2][N1] with 4 ghost zones on each side of every active direction
+// (i fastest, so a warp reads 32 consecutive x1 zones of one variable).
+// Face fluxes of direction d share the cell indexing: the flux stored at cell
+// t is the flux through t's lower d-face.  Every kernel is launched with a
+// grid that covers its index space exactly once (grid-stride loops), sized in
+// multiples of the SM count by the host.
+#pragma once
+#include "hr_common.cuh"
+#include "hr_implicit.cuh"
+
+namespace hr {
+
+struct Bufs {
+  double* P;       // [12][ntot] primitives, ghosts included
+  double* Un;      // [12][nact] conserved state at the start of the step
+  void* F[3];      // [12][ntot] face fluxes (real type of the precision mode)
+  void* spd[3];    // [ntot] per-face max signal speed
+  void* aux;       // [10][ntot] per-cell gdet, sqrt(-g) u^d gas/rad, tau weights
+  void* flat[3];   // [2][ntot] flattener, max over the sub-steps of the step
+  void* emf;       // [ntot] edge EMF scratch
+  double* dt;      // device scalar: time step
+  unsigned char* status;  // [nact] worst outcome over the sub-steps
+  int* iters;             // [nact] Newton steps summed over the sub-steps
+  unsigned char* failed;  // [nact] back-up flag of the current sub-step
+  int* qcount;            // [2] retry-queue and back-up-list lengths
+  int* qzone;             // [nact] retry queue: active zone index
+  double* qdata;          // [nact][18] retry queue payload: U*, PMHD best x, e_T, h
+  int* fzone;             // [nact] back-up list
+  double* ftmp;           // [nact][12] averaged primitives of back-up zones
+  unsigned long long* stats;  // [8] counters
+  unsigned long long* dtmin;  // CFL minimum (ordered bits of a positive double)
+};
+
+// Counter update aggregated over the converged lanes of a warp.
+__device__ __forceinline__ void warp_add(unsigned long long* dst, unsigned v) {
+  unsigned mask = __activemask();
+  unsigned s = __reduce_add_sync(mask, v);
+  if ((int)(threadIdx.x & 31) == __ffs(mask) - 1 && s) atomicAdd(dst, (unsigned long long)s);
+}
+
+// ----------------------------------------------------------- ghost fill
+// One direction at a time, in the order 1, 2, 3, so that edges and corners
+// come from already-filled cells.  Periodic wraps; outflow copies the last
+// active zone and clamps the normal velocities (gas and radiation) so nothing
+// enters from the ghost; polar mirrors across the axis from the zone half a
+// turn away in phi, negating the theta components.
+static __global__ void k_bc_fill(DevParams p, double* __restrict__ P, int d) {
+  int lo[3], len[3];
+  for (int e = 0; e < 3; ++e) {
+    if (e == d) {
+      lo[e] = 0;
+      len[e] = p.ng[d];
+    } else if (e < d) {
+      lo[e] = -p.ng[e];
+      len[e] = p.n[e] + 2 * p.ng[e];
+    } else {
+      lo[e] = 0;
+      len[e] = p.n[e];
+    }
+  }
+  long long total = 2LL * len[0] * len[1] * len[2];
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    long long r = id;
+    int a0 = (int)(r % len[0]);
+    r /= len[0];
+    int a1 = (int)(r % len[1]);
+    r /= len[1];
+    int a2 = (int)(r % len[2]);
+    int side = (int)(r / len[2]);
+    int c[3] = {a0 + lo[0], a1 + lo[1], a2 + lo[2]};
+    int g = c[d];
+    int dst[3] = {c[0], c[1], c[2]}, src[3] = {c[0], c[1], c[2]};
+    int bc = p.bc[2 * d + side];
+    dst[d] = side == 0 ? -1 - g : p.n[d] + g;
+    double sgn = 1.0;
+    int clamp = 0;
+    if (bc == 0) {
+      src[d] = side == 0 ? p.n[d] - 1 - g : g;
+    } else if (bc == 1) {
+      src[d] = side == 0 ? 0 : p.n[d] - 1;
+      clamp = side == 0 ? -1 : 1;
+    } else {
+      src[d] = side == 0 ? g : p.n[d] - 1 - g;
+      if (p.n[2] > 1) src[2] = (c[2] + p.n[2] / 2) % p.n[2];
+      sgn = -1.0;
+    }
+    long long s = cell_index(p, src[0], src[1], src[2]);
+    long long t = cell_index(p, dst[0], dst[1], dst[2]);
+#pragma unroll
+    for (int q = 0; q < NPR; ++q) {
+      double v = P[q * p.ntot + s];
+      if (q == U1 + d || q == B1 + d || q == UR1 + d) v *= sgn;
+      if (clamp != 0 && (q == U1 + d || q == UR1 + d)) v = clamp < 0 ? fmin(v, 0.0) : fmax(v, 0.0);
+      P[q * p.ntot + t] = v;
+    }
+  }
+}
+
+// --------------------------------------------------------------- cell prep
+// Per cell: sqrt(-g), and for every active direction d the flattener inputs
+// sqrt(-g) u^d (gas, radiation) and the weight w_d = min(1, 2 tau_d) of the
+// optical depth of the cell along d (Sec. 4.3).
+template <int MET, typename R>
+__global__ void k_prep(DevParams p, const double* __restrict__ P, R* __restrict__ aux) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < p.ntot;
+       t += (long long)gridDim.x * blockDim.x) {
+    long long r = t;
+    int i = (int)(r % p.N[0]) - p.ng[0];
+    r /= p.N[0];
+    int j = (int)(r % p.N[1]) - p.ng[1];
+    int k = (int)(r / p.N[1]) - p.ng[2];
+    (void)k;
+    Geo<MET, R> g = make_geo<MET, R>(p, R(xcen(p, 0, i)), R(xcen(p, 1, j)));
+    R ucon[4], ucov[4], gm, urc[4], urv[4], gr;
+    fourvel<MET, R>(g, R(P[U1 * p.ntot + t]), R(P[U2 * p.ntot + t]), R(P[U3 * p.ntot + t]), ucon, ucov, &gm);
+    fourvel<MET, R>(g, R(P[UR1 * p.ntot + t]), R(P[UR2 * p.ntot + t]), R(P[UR3 * p.ntot + t]), urc, urv, &gr);
+    R kabs, ksca;
+    opacity<R>(p, R(P[RHO * p.ntot + t]), R(P[UU * p.ntot + t]), &kabs, &ksca);
+    aux[t] = g.gdet;
+#pragma unroll
+    for (int d = 1; d <= 3; ++d) {
+      aux[(1 + 3 * (d - 1)) * p.ntot + t] = g.gdet * ucon[d];
+      aux[(2 + 3 * (d - 1)) * p.ntot + t] = g.gdet * urc[d];
+      R tau = (kabs + ksca) * sqrt(g.gdd(d)) * R(p.dx[d - 1]);
+      R w = R(2) * tau;
+      aux[(3 + 3 * (d - 1)) * p.ntot + t] = w < R(1) ? w : R(1);
+    }
+  }
+}
+
+// ----------------------------------------------------------- flattener
+// Shock flattener of Sec. 4.3 (SP0 = 0.75): for GAS (gas pressure and
+// sqrt(-g) u^d) and RAD (radiation pressure and sqrt(-g) u^d_rad), each
+// pressure blended toward the total by the cell's w; flattening where
+// |dp| > 0.33 min p and the flow compresses, with the shock parameter
+// dp1/dp2 mapped by 10 (Sp - 0.75) to [0, 1]; the upstream neighbour's value
+// is max-ed in; GAS and RAD are blended to their maximum by w; and the result
+// is max-ed with the values of the earlier sub-steps of the step.
+template <typename R>
+struct FlatCell {
+  R pg, pr, vg, vr, w;
+};
+
+template <typename R>
+__device__ __forceinline__ R ftilde(const FlatCell<R>* c, int m, bool gas, R w) {
+  R pe1 = gas ? c[m + 1].pg + w * c[m + 1].pr : c[m + 1].pr + w * c[m + 1].pg;
+  R pem = gas ? c[m - 1].pg + w * c[m - 1].pr : c[m - 1].pr + w * c[m - 1].pg;
+  R pe2 = gas ? c[m + 2].pg + w * c[m + 2].pr : c[m + 2].pr + w * c[m + 2].pg;
+  R pe2m = gas ? c[m - 2].pg + w * c[m - 2].pr : c[m - 2].pr + w * c[m - 2].pg;
+  R dp1 = pe1 - pem, dp2 = pe2 - pe2m;
+  R dv = gas ? c[m + 1].vg - c[m - 1].vg : c[m + 1].vr - c[m - 1].vr;
+  R mn = pe1 < pem ? pe1 : pem;
+  if (fabs(dp1) > R(0.33) * mn && dv < R(0)) {
+    R sp = dp2 != R(0) ? dp1 / dp2 : R(0);
+    R f = R(10) * (sp - R(0.75));
+    return f < R(0) ? R(0) : (f > R(1) ? R(1) : f);
+  }
+  return R(0);
+}
+
+template <typename R>
+__global__ void k_flatten(DevParams p, const double* __restrict__ P, const R* __restrict__ aux,
+                          R* __restrict__ flat, int d) {
+  int len[3], off[3];
+  for (int e = 0; e < 3; ++e) {
+    if (p.n[e] > 1) {
+      len[e] = p.n[e] + 2;
+      off[e] = -1;
+    } else {
+      len[e] = 1;
+      off[e] = 0;
+    }
+  }
+  long long total = (long long)len[0] * len[1] * len[2];
+  const long long st = p.str[d];
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    long long r = id;
+    int i = (int)(r % len[0]) + off[0];
+    r /= len[0];
+    int j = (int)(r % len[1]) + off[1];
+    int k = (int)(r / len[1]) + off[2];
+    long long t = cell_index(p, i, j, k);
+    FlatCell<R> c[7];
+#pragma unroll
+    for (int m = 0; m < 7; ++m) {
+      long long cm = t + (m - 3) * st;
+      c[m].pg = R((p.gam - 1.0) * P[UU * p.ntot + cm]);
+      c[m].pr = R(P[ER * p.ntot + cm] * (1.0 / 3.0));
+      c[m].vg = aux[(1 + 3 * d) * p.ntot + cm];
+      c[m].vr = aux[(2 + 3 * d) * p.ntot + cm];
+      c[m].w = aux[(3 + 3 * d) * p.ntot + cm];
+    }
+    const R w = c[3].w;
+    R g0 = ftilde<R>(c, 3, true, w), r0 = ftilde<R>(c, 3, false, w);
+    R pg1 = c[4].pg + w * c[4].pr, pgm = c[2].pg + w * c[2].pr;
+    R pr1 = c[4].pr + w * c[4].pg, prm = c[2].pr + w * c[2].pg;
+    int sg = (pg1 - pgm) < R(0) ? 1 : -1;
+    int sr = (pr1 - prm) < R(0) ? 1 : -1;
+    R gn = ftilde<R>(c, 3 + sg, true, c[3 + sg].w);
+    R rn = ftilde<R>(c, 3 + sr, false, c[3 + sr].w);
+    R fg = g0 > gn ? g0 : gn;
+    R fr = r0 > rn ? r0 : rn;
+    R mx = fg > fr ? fg : fr;
+    R Fg = (R(1) - w) * fg + w * mx;
+    R Fr = (R(1) - w) * fr + w * mx;
+    R og = flat[t], orr = flat[p.ntot + t];
+    flat[t] = Fg > og ? Fg : og;
+    flat[p.ntot + t] = Fr > orr ? Fr : orr;
+  }
+}
+
+// ------------------------------------------------------------- reconstruction
+template <typename R>
+__device__ __forceinline__ R mc_slope(R qm, R q0, R qp) {
+  R dl = q0 - qm, dr = qp - q0, dc = R(0.5) * (qp - qm);
+  if (dl * dr <= R(0)) return R(0);
+  R m = fabs(dc);
+  R a = R(2) * fabs(dl), b = R(2) * fabs(dr);
+  m = m < a ? m : a;
+  m = m < b ? m : b;
+  return dc > R(0) ? m : -m;
+}
+
+// PPM edge values of the centre of s[0..4] (Colella & Woodward 1984, no
+// contact steepening), flattened toward the cell mean by chi, then limited.
+template <typename R>
+__device__ __forceinline__ void ppm_cell(const R s[5], R chi, R* aL, R* aR) {
+  R dm = mc_slope<R>(s[0], s[1], s[2]);
+  R d0 = mc_slope<R>(s[1], s[2], s[3]);
+  R dp = mc_slope<R>(s[2], s[3], s[4]);
+  R l = R(0.5) * (s[1] + s[2]) - (d0 - dm) / R(6);
+  R r = R(0.5) * (s[2] + s[3]) - (dp - d0) / R(6);
+  R q = s[2];
+  l = (R(1) - chi) * l + chi * q;
+  r = (R(1) - chi) * r + chi * q;
+  if ((r - q) * (q - l) <= R(0)) {
+    l = q;
+    r = q;
+  } else {
+    R dd = r - l;
+    R m6 = R(6) * (q - R(0.5) * (l + r));
+    if (dd * m6 > dd * dd) l = R(3) * q - R(2) * r;
+    else if (-dd * dd > dd * m6) r = R(3) * q - R(2) * l;
+  }
+  *aL = l;
+  *aR = r;
+}
+
+// ----------------------------------------------------------------- fluxes
+// One thread per face of direction d (faces 0..n_d, transverse range widened
+// by one layer for the EMF averages).  Loads the 6-cell stencil of each
+// primitive, reconstructs both states, evaluates the metric at the face in
+// registers, forms U, F and wave speeds of both states and the HLL or LAXF
+// flux (Eqs. hll, lax), gas and radiation groups with their own speeds.
+template <int MET, typename R>
+__global__ void __launch_bounds__(128) k_face(DevParams p, const double* __restrict__ P,
+                                              const R* __restrict__ aux, const R* __restrict__ flat,
+                                              R* __restrict__ F, R* __restrict__ spd, int d) {
+  int len[3], off[3];
+  for (int e = 0; e < 3; ++e) {
+    if (e == d) {
+      len[e] = p.n[e] + 1;
+      off[e] = 0;
+    } else if (p.n[e] > 1) {
+      len[e] = p.n[e] + 2;
+      off[e] = -1;
+    } else {
+      len[e] = 1;
+      off[e] = 0;
+    }
+  }
+  long long total = (long long)len[0] * len[1] * len[2];
+  const long long st = p.str[d];
+  const bool weighted = (MET == KS) && (d != 1);
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    long long r = id;
+    int ii[3];
+    ii[0] = (int)(r % len[0]) + off[0];
+    r /= len[0];
+    ii[1] = (int)(r % len[1]) + off[1];
+    ii[2] = (int)(r / len[1]) + off[2];
+    long long t = cell_index(p, ii[0], ii[1], ii[2]);
+    const int f = ii[d];
+    if (MET == KS && d == 1 && ((f == 0 && p.bc[2] == 2) || (f == p.n[1] && p.bc[3] == 2))) {
+#pragma unroll
+      for (int q = 0; q < NPR; ++q) F[q * p.ntot + t] = R(0);
+      spd[t] = R(0);
+      continue;
+    }
+    R xf[3];
+    for (int e = 0; e < 3; ++e) xf[e] = R(p.x0[e] + (ii[e] + (e == d ? 0.0 : 0.5)) * p.dx[e]);
+    Geo<MET, R> g = make_geo<MET, R>(p, xf[0], xf[1]);
+    R chiLg = R(0), chiLr = R(0), chiRg = R(0), chiRr = R(0);
+    if (p.recon == 0) {
+      chiLg = flat[t - st];
+      chiLr = flat[p.ntot + t - st];
+      chiRg = flat[t];
+      chiRr = flat[p.ntot + t];
+    }
+    R gw[6];
+    if (weighted) {
+#pragma unroll
+      for (int m = 0; m < 6; ++m) gw[m] = aux[t + (m - 3) * st];
+    }
+    const R igf = weighted ? R(1) / g.gdet : R(1);
+    R PL[NPR], PR[NPR];
+#pragma unroll
+    for (int q = 0; q < NPR; ++q) {
+      const bool wq = weighted && ((q >= U1 && q <= B3) || q >= UR1);
+      R s[6];
+#pragma unroll
+      for (int m = 0; m < 6; ++m) {
+        R v = R(P[q * p.ntot + t + (m - 3) * st]);
+        s[m] = wq ? gw[m] * v : v;
+      }
+      R aL, aR, bL, bR;
+      if (p.recon == 0) {
+        ppm_cell<R>(s, q < ER ? chiLg : chiLr, &aL, &aR);      // cell f-1: s[0..4]
+        ppm_cell<R>(s + 1, q < ER ? chiRg : chiRr, &bL, &bR);  // cell f:   s[1..5]
+      } else {
+        R dl = mc_slope<R>(s[1], s[2], s[3]);
+        R dr = mc_slope<R>(s[2], s[3], s[4]);
+        aR = s[2] + R(0.5) * dl;
+        bL = s[3] - R(0.5) * dr;
+        (void)aL;
+        (void)bR;
+      }
+      PL[q] = wq ? aR * igf : aR;
+      PR[q] = wq ? bL * igf : bL;
+    }
+    R UL[NPR], FL[NPR], sL[4], UR_[NPR], FR[NPR], sR[4];
+    face_state<MET, R>(p, g, d + 1, PL, UL, FL, sL);
+    face_state<MET, R>(p, g, d + 1, PR, UR_, FR, sR);
+    R cmaxg = fmax(R(0), fmax(sL[1], sR[1]));
+    R cming = -fmin(R(0), fmin(sL[0], sR[0]));
+    R cmaxr = fmax(R(0), fmax(sL[3], sR[3]));
+    R cminr = -fmin(R(0), fmin(sL[2], sR[2]));
+#pragma unroll
+    for (int q = 0; q < NPR; ++q) {
+      R cmx = q < ER ? cmaxg : cmaxr, cmn = q < ER ? cming : cminr;
+      R fl;
+      if (p.flux == 0) {
+        R ctop = cmx > cmn ? cmx : cmn;
+        fl = R(0.5) * (FL[q] + FR[q] - ctop * (UR_[q] - UL[q]));
+      } else if (cmx + cmn > R(0)) {
+        fl = (cmn * FR[q] + cmx * FL[q] - cmn * cmx * (UR_[q] - UL[q])) / (cmn + cmx);
+      } else {
+        fl = R(0.5) * (FL[q] + FR[q]);
+      }
+      if (q == B1 + d) fl = R(0);
+      F[q * p.ntot + t] = fl;
+    }
+    spd[t] = fmax(fmax(cmaxg, cming), fmax(cmaxr, cminr));
+  }
+}
+
+// ----------------------------------------------------------------- flux-CT
+// Toth (2000) constrained transport for the pair (a, b) of active directions:
+// edge EMF = 1/4 (F_a[B_b] + F_a[B_b](b-1) - F_b[B_a] - F_b[B_a](a-1)), zero on
+// the polar axis; then F_a[B_b] and F_b[B_a] become averages of the two
+// adjacent edge EMFs (with opposite signs).
+template <typename R>
+__global__ void k_emf(DevParams p, const R* __restrict__ Fa, const R* __restrict__ Fb,
+                      R* __restrict__ emf, int a, int b) {
+  int len[3];
+  for (int e = 0; e < 3; ++e) len[e] = p.n[e] + ((e == a || e == b) ? 1 : 0);
+  long long total = (long long)len[0] * len[1] * len[2];
+  const long long sa = p.str[a], sb = p.str[b];
+  const R* fab = Fa + (B1 + b) * p.ntot;
+  const R* fba = Fb + (B1 + a) * p.ntot;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    long long r = id;
+    int ii[3];
+    ii[0] = (int)(r % len[0]);
+    r /= len[0];
+    ii[1] = (int)(r % len[1]);
+    ii[2] = (int)(r / len[1]);
+    long long t = cell_index(p, ii[0], ii[1], ii[2]);
+    bool pole = p.metric == KS && (a == 1 || b == 1) &&
+                ((ii[1] == 0 && p.bc[2] == 2) || (ii[1] == p.n[1] && p.bc[3] == 2));
+    emf[t] = pole ? R(0) : R(0.25) * (fab[t] + fab[t - sb] - fba[t] - fba[t - sa]);
+  }
+}
+
+template <typename R>
+__global__ void k_ct(DevParams p, const R* __restrict__ emf, R* __restrict__ Fa, R* __restrict__ Fb,
+                     int a, int b) {
+  // two index spaces: a-faces (a in [0,n_a], b in [0,n_b)) then b-faces
+  int la[3], lb[3];
+  for (int e = 0; e < 3; ++e) {
+    la[e] = p.n[e] + (e == a ? 1 : 0);
+    lb[e] = p.n[e] + (e == b ? 1 : 0);
+  }
+  long long na = (long long)la[0] * la[1] * la[2];
+  long long nb = (long long)lb[0] * lb[1] * lb[2];
+  const long long sa = p.str[a], sb = p.str[b];
+  R* fab = Fa + (B1 + b) * p.ntot;
+  R* fba = Fb + (B1 + a) * p.ntot;
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < na + nb;
+       id += (long long)gridDim.x * blockDim.x) {
+    const int* L = id < na ? la : lb;
+    long long r = id < na ? id : id - na;
+    int i0 = (int)(r % L[0]);
+    r /= L[0];
+    int i1 = (int)(r % L[1]);
+    int i2 = (int)(r / L[1]);
+    long long t = cell_index(p, i0, i1, i2);
+    if (id < na) fab[t] = R(0.5) * (emf[t] + emf[t + sb]);
+    else fba[t] = R(-0.5) * (emf[t] + emf[t + sa]);
+  }
+}
+
+// ----------------------------------------------------------------- floors
+// Lorentz-factor caps, density and internal-energy floors f0 r^pow,
+// magnetisation caps b^2/rho, b^2/u_g, u_g/rho, and Ebar > 0.
+template <int MET>
+__device__ __forceinline__ void apply_floors(const DevParams& p, const Geo<MET, double>& g, double r,
+                                             double P[NPR]) {
+  double gm = sqrt(1.0 + g.sq3(P[U1], P[U2], P[U3]));
+  if (gm > p.ggas_max) {
+    double f = sqrt((p.ggas_max * p.ggas_max - 1.0) / (gm * gm - 1.0));
+    P[U1] *= f;
+    P[U2] *= f;
+    P[U3] *= f;
+  }
+  double gr = sqrt(1.0 + g.sq3(P[UR1], P[UR2], P[UR3]));
+  if (gr > p.grad_max) {
+    double f = sqrt((p.grad_max * p.grad_max - 1.0) / (gr * gr - 1.0));
+    P[UR1] *= f;
+    P[UR2] *= f;
+    P[UR3] *= f;
+  }
+  double ucon[4], ucov[4], bcon[4], bcov[4], bsq;
+  fourvel<MET, double>(g, P[U1], P[U2], P[U3], ucon, ucov, &gm);
+  bvec<MET, double>(g, ucon, ucov, P[B1], P[B2], P[B3], bcon, bcov, &bsq);
+  double rfl = p.rf0 * (p.rfp == 0.0 ? 1.0 : pow(r, p.rfp));
+  double ufl = p.uf0 * (p.ufp == 0.0 ? 1.0 : pow(r, p.ufp));
+  rfl = fmax(rfl, bsq / p.bsq_rho_max);
+  ufl = fmax(ufl, bsq / p.bsq_u_max);
+  P[RHO] = fmax(P[RHO], rfl);
+  P[UU] = fmax(P[UU], ufl);
+  P[RHO] = fmax(P[RHO], P[UU] / p.u_rho_max);
+  if (!(P[ER] > 0.0)) P[ER] = 1e-150;
+}
+
+// Final primitives of an accepted PMHD iterate: gas from x, B fixed, radiation
+// re-inverted with BASIC if the TYPE2 branch saw a negative energy (Sec. 4.10).
+template <int MET>
+__device__ __forceinline__ void pmhd_final(const DevParams& p, const ImpSys<MET>& s, const double x[4],
+                                           double P[NPR]) {
+  ImpRes r;
+  ImpState stt;
+  pmhd_res<MET>(p, s, x, r, &stt, false);
+  P[RHO] = stt.rho;
+  P[UU] = x[0];
+  P[U1] = x[1];
+  P[U2] = x[2];
+  P[U3] = x[3];
+  P[B1] = s.B[0];
+  P[B2] = s.B[1];
+  P[B3] = s.B[2];
+  double Pr[4] = {stt.Pr[0], stt.Pr[1], stt.Pr[2], stt.Pr[3]};
+  if (r.negE) rad_invert<MET>(p, s.g, stt.Rt_pre, 0, Pr);
+  P[ER] = Pr[0];
+  P[UR1] = Pr[1];
+  P[UR2] = Pr[2];
+  P[UR3] = Pr[3];
+}
+
+// Metric derivatives for the geometric source: forward-mode pair (d/dx1, d/dx2).
+struct D2 {
+  double v, a, b;
+};
+__device__ __forceinline__ D2 operator+(D2 x, D2 y) { return {x.v + y.v, x.a + y.a, x.b + y.b}; }
+__device__ __forceinline__ D2 operator-(D2 x, D2 y) { return {x.v - y.v, x.a - y.a, x.b - y.b}; }
+__device__ __forceinline__ D2 operator*(D2 x, D2 y) {
+  return {x.v * y.v, x.a * y.v + x.v * y.a, x.b * y.v + x.v * y.b};
+}
+__device__ __forceinline__ D2 operator*(double c, D2 y) { return {c * y.v, c * y.a, c * y.b}; }
+__device__ __forceinline__ D2 operator/(D2 x, D2 y) {
+  double iy = 1.0 / y.v;
+  double q = x.v * iy;
+  return {q, (x.a - q * y.a) * iy, (x.b - q * y.b) * iy};
+}
+
+// d_nu g_{mu kappa} (nu = x1, x2) of the covariant Kerr-Schild metric in the
+// internal chart and d_nu sqrt(-g).
+struct MetricDeriv {
+  double g00[2], g01[2], g03[2], g11[2], g13[2], g22[2], g33[2], sg[2];
+};
+__device__ __forceinline__ MetricDeriv ks_derivs(const DevParams& p, double x1, double x2) {
+  const double a = p.a, hh = p.h, pi = 3.14159265358979323846;
+  double ex = exp(x1);
+  D2 r = {p.R0 + ex, ex, 0.0};
+  double s2x, c2x;
+  sincospi(2.0 * x2, &s2x, &c2x);
+  D2 th = {pi * x2 + 0.5 * (1.0 - hh) * s2x, 0.0, pi + (1.0 - hh) * pi * c2x};
+  double st, ct;
+  sincos(th.v, &st, &ct);
+  D2 sth = {st, 0.0, ct * th.b}, cth = {ct, 0.0, -st * th.b};
+  D2 J1 = {ex, ex, 0.0};
+  D2 J2 = {pi * (1.0 + (1.0 - hh) * c2x), 0.0, -2.0 * pi * pi * (1.0 - hh) * s2x};
+  const double J3 = 2.0 * pi;
+  D2 s2 = sth * sth;
+  D2 S = r * r + (a * a) * (cth * cth);
+  D2 tr = (2.0 * r) / S;
+  D2 one = {1.0, 0.0, 0.0};
+  D2 m00 = tr - one;
+  D2 m01 = tr * J1;
+  D2 m03 = (-a * J3) * (tr * s2);
+  D2 m11 = (one + tr) * J1 * J1;
+  D2 m13 = (-a * J3) * (s2 * (one + tr) * J1);
+  D2 m22 = S * J2 * J2;
+  D2 m33 = (J3 * J3) * (s2 * (S + (a * a) * (s2 * (one + tr))));
+  D2 sg = J3 * (S * sth * J1 * J2);
+  MetricDeriv md;
+  md.g00[0] = m00.a; md.g00[1] = m00.b;
+  md.g01[0] = m01.a; md.g01[1] = m01.b;
+  md.g03[0] = m03.a; md.g03[1] = m03.b;
+  md.g11[0] = m11.a; md.g11[1] = m11.b;
+  md.g13[0] = m13.a; md.g13[1] = m13.b;
+  md.g22[0] = m22.a; md.g22[1] = m22.b;
+  md.g33[0] = m33.a; md.g33[1] = m33.b;
+  md.sg[0] = sg.a; md.sg[1] = sg.b;
+  return md;
+}
+
+// v^mu v^kappa d_nu g_{mu kappa}
+__device__ __forceinline__ double qform(const MetricDeriv& m, int n, const double v[4]) {
+  return m.g00[n] * v[0] * v[0] + 2.0 * m.g01[n] * v[0] * v[1] + 2.0 * m.g03[n] * v[0] * v[3] +
+         m.g11[n] * v[1] * v[1] + 2.0 * m.g13[n] * v[1] * v[3] + m.g22[n] * v[2] * v[2] +
+         m.g33[n] * v[3] * v[3];
+}
+
+// ------------------------------------------------------- update + implicit
+// One thread per active zone: U(P_s), the geometric source
+// SM_nu = 1/2 sqrt(-g) T^{mu kappa} d_nu g_{mu kappa}  (equal to
+// sqrt(-g) T^kappa_lambda Gamma^lambda_{nu kappa} for a symmetric T, nonzero
+// only for nu = x1, x2 on the stationary axisymmetric metric), the explicit
+// update X = -sum_d dF_d/dx_d + SM, the RK3 combination
+// U* = a_s U^n + b_s (U(P_s) + dt X) (Sec. 4.1), the PMHD Newton solve, floors.
+// Zones whose PMHD error exceeds 1e-9 go to the retry queue.
+template <int MET, typename R>
+__global__ void __launch_bounds__(128) k_update(DevParams p, Bufs b, int stage) {
+  const double A = stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0);
+  const double Bc = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
+  const double dt = *b.dt;
+  const R* F0 = (const R*)b.F[0];
+  const R* F1 = (const R*)b.F[1];
+  const R* F2 = (const R*)b.F[2];
+  for (long long z = blockIdx.x * (long long)blockDim.x + threadIdx.x; z < p.nact;
+       z += (long long)gridDim.x * blockDim.x) {
+    long long r = z;
+    int i = (int)(r % p.n[0]);
+    r /= p.n[0];
+    int j = (int)(r % p.n[1]);
+    int k = (int)(r / p.n[1]);
+    long long t = cell_index(p, i, j, k);
+    double x1 = xcen(p, 0, i), x2 = xcen(p, 1, j);
+    Geo<MET, double> g = make_geo<MET, double>(p, x1, x2);
+    double Ps[NPR];
+#pragma unroll
+    for (int q = 0; q < NPR; ++q) Ps[q] = b.P[q * p.ntot + t];
+    // U(P_s)
+    double ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq, urc[4], urv[4], gr;
+    fourvel<MET, double>(g, Ps[U1], Ps[U2], Ps[U3], ucon, ucov, &gm);
+    bvec<MET, double>(g, ucon, ucov, Ps[B1], Ps[B2], Ps[B3], bcon, bcov, &bsq);
+    fourvel<MET, double>(g, Ps[UR1], Ps[UR2], Ps[UR3], urc, urv, &gr);
+    const double pg = (p.gam - 1.0) * Ps[UU];
+    const double wb = Ps[RHO] + Ps[UU] + pg + bsq, pt = pg + 0.5 * bsq;
+    const double gd = g.gdet, mt = Ps[RHO] * ucon[0];
+    const double E = Ps[ER], e43 = (4.0 / 3.0) * E;
+    double Us[NPR];
+    Us[0] = gd * mt;
+    Us[1] = gd * (wb * ucon[0] * ucov[0] + pt - bcon[0] * bcov[0] + mt);
+#pragma unroll
+    for (int n = 1; n < 4; ++n) Us[1 + n] = gd * (wb * ucon[0] * ucov[n] - bcon[0] * bcov[n]);
+    Us[5] = gd * Ps[B1];
+    Us[6] = gd * Ps[B2];
+    Us[7] = gd * Ps[B3];
+    Us[8] = gd * (e43 * urc[0] * urv[0] + E * (1.0 / 3.0));
+#pragma unroll
+    for (int n = 1; n < 4; ++n) Us[8 + n] = gd * (e43 * urc[0] * urv[n]);
+    double X[NPR];
+#pragma unroll
+    for (int q = 0; q < NPR; ++q) X[q] = 0.0;
+    if constexpr (MET == KS) {
+      MetricDeriv md = ks_derivs(p, x1, x2);
+#pragma unroll
+      for (int n = 0; n < 2; ++n) {
+        double qu = qform(md, n, ucon), qb = qform(md, n, bcon), qr = qform(md, n, urc);
+        X[2 + n] = 0.5 * gd * (wb * qu - qb) + pt * md.sg[n];
+        X[9 + n] = 0.5 * gd * e43 * qr + E * (1.0 / 3.0) * md.sg[n];
+      }
+    }
+    // flux divergence
+    const R* Fd[3] = {F0, F1, F2};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      if (p.n[d] == 1) continue;
+      const long long s = p.str[d];
+      const double idx_ = 1.0 / p.dx[d];
+#pragma unroll
+      for (int q = 0; q < NPR; ++q) {
+        R df = Fd[d][q * p.ntot + t + s] - Fd[d][q * p.ntot + t];
+        X[q] -= double(df) * idx_;
+      }
+    }
+    double Ust[NPR];
+#pragma unroll
+    for (int q = 0; q < NPR; ++q) {
+      double un;
+      if (stage == 0) {
+        b.Un[q * p.nact + z] = Us[q];
+        un = Us[q];
+      } else {
+        un = b.Un[q * p.nact + z];
+      }
+      Ust[q] = A * un + Bc * (Us[q] + dt * X[q]);
+    }
+    // implicit solve
+    const double h = Bc * dt;
+    ImpSys<MET> s;
+    build_sys<MET>(p, g, Ust, h, s);
+    double x0[4] = {Ps[UU], Ps[U1], Ps[U2], Ps[U3]};
+    {
+      double kabs, ksca;
+      opacity<double>(p, Ps[RHO], Ps[UU], &kabs, &ksca);
+      double dl = 0.0;
+#pragma unroll
+      for (int d = 1; d <= 3; ++d)
+        if (p.n[d - 1] > 1) dl = fmax(dl, sqrt(g.gdd(d)) * p.dx[d - 1]);
+      if ((kabs + ksca) * dl < 2.0 / 3.0) {
+        double go[5];
+        double T3[3] = {s.Ts[1], s.Ts[2], s.Ts[3]};
+        if (gas_invert<MET>(p, g, s.Dlab, s.Ts[0], T3, s.B, Ps, 1e-9, go) == 0) {
+          x0[0] = go[1];
+          x0[1] = go[2];
+          x0[2] = go[3];
+          x0[3] = go[4];
+        }
+      }
+    }
+    double bx[4], beT;
+    int steps = newton_pmhd<MET>(p, s, x0, bx, &beT);
+    b.iters[z] += steps;
+    bool accept = beT < 1e-9;
+    if (accept) {
+      double Pn[NPR];
+      pmhd_final<MET>(p, s, bx, Pn);
+      apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn);
+#pragma unroll
+      for (int q = 0; q < NPR; ++q) b.P[q * p.ntot + t] = Pn[q];
+    } else {
+      int slot = atomicAdd(&b.qcount[0], 1);
+      b.qzone[slot] = (int)z;
+      double* qd = b.qdata + (long long)slot * QSTRIDE;
+#pragma unroll
+      for (int q = 0; q < NPR; ++q) qd[q] = Ust[q];
+      for (int q = 0; q < 4; ++q) qd[12 + q] = isfinite(beT) ? bx[q] : 0.0;
+      qd[16] = beT;
+      qd[17] = h;
+    }
+    warp_add(&b.stats[ST_PMHD], accept ? 1u : 0u);
+    warp_add(&b.stats[ST_ITERS], (unsigned)steps);
+    warp_add(&b.stats[ST_SOLVES], 1u);
+  }
+}
+
+// ----------------------------------------------------------- retry (URAD)
+// Persistent grid over the retry queue (its length is read on the device, so
+// the launch needs no host round trip and can live in a CUDA graph).  URAD is
+// guessed from the PMHD solution when that reached e_T < 1e-4, else from P_s;
+// the lower-error of the two solutions is kept; e_T > 1e-7 sends the zone to
+// the neighbour-average back-up.
+template <int MET>
+__global__ void __launch_bounds__(128) k_retry(DevParams p, Bufs b) {
+  const int nq = b.qcount[0];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nq; e += gridDim.x * blockDim.x) {
+    const long long z = b.qzone[e];
+    const double* qd = b.qdata + (long long)e * QSTRIDE;
+    long long r = z;
+    int i = (int)(r % p.n[0]);
+    r /= p.n[0];
+    int j = (int)(r % p.n[1]);
+    int k = (int)(r / p.n[1]);
+    long long t = cell_index(p, i, j, k);
+    double x1 = xcen(p, 0, i), x2 = xcen(p, 1, j);
+    Geo<MET, double> g = make_geo<MET, double>(p, x1, x2);
+    double Ust[NPR], Ps[NPR], px[4];
+    for (int q = 0; q < NPR; ++q) {
+      Ust[q] = qd[q];
+      Ps[q] = b.P[q * p.ntot + t];
+    }
+    for (int q = 0; q < 4; ++q) px[q] = qd[12 + q];
+    const double peT = qd[16], h = qd[17];
+    ImpSys<MET> s;
+    build_sys<MET>(p, g, Ust, h, s);
+    // PMHD iterate as the error function left it (TYPE2 radiation)
+    double Pb[NPR];
+    if (isfinite(peT)) {
+      ImpRes rr;
+      ImpState stt;
+      pmhd_res<MET>(p, s, px, rr, &stt, false);
+      Pb[RHO] = stt.rho;
+      Pb[UU] = px[0];
+      Pb[U1] = px[1];
+      Pb[U2] = px[2];
+      Pb[U3] = px[3];
+      Pb[B1] = s.B[0];
+      Pb[B2] = s.B[1];
+      Pb[B3] = s.B[2];
+      for (int q = 0; q < 4; ++q) Pb[ER + q] = stt.Pr[q];
+    }
+    const double* Pg = (isfinite(peT) && peT < 1e-4) ? Pb : Ps;
+    // R^t_nu of the guess radiation state
+    double urc[4], urv[4], gr;
+    fourvel<MET, double>(g, Pg[UR1], Pg[UR2], Pg[UR3], urc, urv, &gr);
+    double e43 = (4.0 / 3.0) * Pg[ER];
+    double xr[4];
+    xr[0] = e43 * urc[0] * urv[0] + Pg[ER] * (1.0 / 3.0);
+    for (int n = 1; n < 4; ++n) xr[n] = e43 * urc[0] * urv[n];
+    double gas[5] = {Pg[RHO], Pg[UU], Pg[U1], Pg[U2], Pg[U3]};
+    double bx[4], bgas[5], beT;
+    int steps = newton_urad<MET>(p, s, xr, gas, bx, bgas, &beT);
+    b.iters[z] += steps;
+    double Pn[NPR];
+    int method;
+    double eT;
+    if (isfinite(beT) && (!isfinite(peT) || beT < peT)) {
+      Pn[RHO] = bgas[0];
+      Pn[UU] = bgas[1];
+      Pn[U1] = bgas[2];
+      Pn[U2] = bgas[3];
+      Pn[U3] = bgas[4];
+      Pn[B1] = s.B[0];
+      Pn[B2] = s.B[1];
+      Pn[B3] = s.B[2];
+      double Pr[4];
+      int neg = rad_invert<MET>(p, g, bx, 2, Pr);
+      if (neg) rad_invert<MET>(p, g, bx, 0, Pr);
+      Pn[ER] = Pr[0];
+      Pn[UR1] = Pr[1];
+      Pn[UR2] = Pr[2];
+      Pn[UR3] = Pr[3];
+      method = ST_URAD;
+      eT = beT;
+    } else if (isfinite(peT)) {
+      pmhd_final<MET>(p, s, px, Pn);
+      method = ST_PMHD;
+      eT = peT;
+    } else {
+      for (int q = 0; q < NPR; ++q) Pn[q] = Ps[q];
+      Pn[B1] = s.B[0];
+      Pn[B2] = s.B[1];
+      Pn[B3] = s.B[2];
+      method = ST_BACKUP;
+      eT = HUGE_VAL;
+    }
+    if (eT > 1e-7) method = ST_BACKUP;
+    apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn);
+    for (int q = 0; q < NPR; ++q) b.P[q * p.ntot + t] = Pn[q];
+    unsigned char m = (unsigned char)method;
+    if (m > b.status[z]) b.status[z] = m;
+    if (method == ST_BACKUP) {
+      b.failed[z] = 1;
+      int slot = atomicAdd(&b.qcount[1], 1);
+      b.fzone[slot] = (int)z;
+      atomicAdd(&b.stats[ST_BACKUP], 1ULL);
+    } else if (method == ST_URAD) {
+      atomicAdd(&b.stats[ST_URAD], 1ULL);
+    } else {
+      atomicAdd(&b.stats[ST_PMHD], 1ULL);
+    }
+    atomicAdd(&b.stats[ST_ITERS], (unsigned long long)steps);
+  }
+}
+
+// ------------------------------------------------------------- back-up
+// Average of the good active face neighbours (all active neighbours if none
+// is good); B keeps its constrained-transport value (Sec. 4.11).
+static __global__ void k_backup_avg(DevParams p, Bufs b) {
+  const int nf = b.qcount[1];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nf; e += gridDim.x * blockDim.x) {
+    long long z = b.fzone[e];
+    long long r = z;
+    int ii[3];
+    ii[0] = (int)(r % p.n[0]);
+    r /= p.n[0];
+    ii[1] = (int)(r % p.n[1]);
+    ii[2] = (int)(r / p.n[1]);
+    double sg[NPR], sa[NPR];
+    for (int q = 0; q < NPR; ++q) sg[q] = sa[q] = 0.0;
+    int ng = 0, na = 0;
+    for (int d = 0; d < 3; ++d) {
+      if (p.n[d] == 1) continue;
+      for (int side = -1; side <= 1; side += 2) {
+        int nb[3] = {ii[0], ii[1], ii[2]};
+        nb[d] += side;
+        if (nb[d] < 0 || nb[d] >= p.n[d]) continue;
+        long long zn = ((long long)nb[2] * p.n[1] + nb[1]) * p.n[0] + nb[0];
+        long long tn = cell_index(p, nb[0], nb[1], nb[2]);
+        bool good = !b.failed[zn];
+        for (int q = 0; q < NPR; ++q) {
+          double v = b.P[q * p.ntot + tn];
+          sa[q] += v;
+          if (good) sg[q] += v;
+        }
+        ++na;
+        if (good) ++ng;
+      }
+    }
+    long long t = cell_index(p, ii[0], ii[1], ii[2]);
+    for (int q = 0; q < NPR; ++q) {
+      double v = b.P[q * p.ntot + t];
+      if (na > 0 && !(q >= B1 && q <= B3)) v = ng > 0 ? sg[q] / ng : sa[q] / na;
+      b.ftmp[(long long)e * NPR + q] = v;
+    }
+  }
+}
+
+template <int MET>
+__global__ void k_backup_apply(DevParams p, Bufs b) {
+  const int nf = b.qcount[1];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nf; e += gridDim.x * blockDim.x) {
+    long long z = b.fzone[e];
+    long long r = z;
+    int i = (int)(r % p.n[0]);
+    r /= p.n[0];
+    int j = (int)(r % p.n[1]);
+    int k = (int)(r / p.n[1]);
+    long long t = cell_index(p, i, j, k);
+    double x1 = xcen(p, 0, i), x2 = xcen(p, 1, j);
+    Geo<MET, double> g = make_geo<MET, double>(p, x1, x2);
+    double Pn[NPR];
+    for (int q = 0; q < NPR; ++q) Pn[q] = b.ftmp[(long long)e * NPR + q];
+    apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn);
+    for (int q = 0; q < NPR; ++q) b.P[q * p.ntot + t] = Pn[q];
+  }
+}
+
+// --------------------------------------------------------------- CFL dt
+// dt = C min_zones 1 / sum_d (v_d/dx_d), v_d = larger face speed of the zone
+// along d.  Block minimum by warp shuffles, then one atomicMin on the bit
+// pattern (positive doubles order like unsigned integers).
+template <typename R>
+__global__ void k_cfl(DevParams p, Bufs b) {
+  double best = HUGE_VAL;
+  for (long long z = blockIdx.x * (long long)blockDim.x + threadIdx.x; z < p.nact;
+       z += (long long)gridDim.x * blockDim.x) {
+    long long r = z;
+    int i = (int)(r % p.n[0]);
+    r /= p.n[0];
+    int j = (int)(r % p.n[1]);
+    int k = (int)(r / p.n[1]);
+    long long t = cell_index(p, i, j, k);
+    double sum = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      if (p.n[d] == 1) continue;
+      const R* sp = (const R*)b.spd[d];
+      double v = fmax((double)sp[t], (double)sp[t + p.str[d]]);
+      sum += v / p.dx[d];
+    }
+    if (sum > 0.0) best = fmin(best, 1.0 / sum);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_down_sync(0xffffffffu, best, o));
+  __shared__ double sm[32];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sm[w] = best;
+  __syncthreads();
+  if (w == 0) {
+    best = lane < (int)(blockDim.x >> 5) ? sm[lane] : HUGE_VAL;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_down_sync(0xffffffffu, best, o));
+    if (lane == 0 && best < HUGE_VAL) atomicMin(b.dtmin, (unsigned long long)__double_as_longlong(best));
+  }
+}
+
+static __global__ void k_cfl_init(Bufs b) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *b.dtmin = 0x7FF0000000000000ULL;  // +inf
+}
+
+static __global__ void k_cfl_finish(DevParams p, Bufs b) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    unsigned long long bits = *b.dtmin;
+    double m = __longlong_as_double((long long)bits);
+    *b.dt = p.courant * m;
+  }
+}
+
+}  // namespace hr

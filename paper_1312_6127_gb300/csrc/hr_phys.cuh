@@ -1,0 +1,438 @@
+// Per-zone GRRMHD + M1 physics for sm_103a, evaluated in registers.
+//
+// Conventions follow Sec. 2-4 of McKinney et al. (2014): c = G = M = 1,
+// Heaviside-Lorentz field, ZAMO-relative 4-velocities u~^i as primitives.
+// Every function is templated on the metric (0 Minkowski Cartesian,
+// 1 Kerr-Schild with the modified spherical-polar map) and, where the split
+// precision path uses it, on the real type.  The metric is never streamed:
+// each zone or face evaluates it from its internal coordinates.  Contractions
+// are written for the sparsity of the Kerr-Schild metric in (t, r, theta, phi)
+// charts: g_{t theta} = g_{r theta} = g_{theta phi} = 0 and g^{t phi} = 0.
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace hr {
+
+enum { RHO = 0, UU, U1, U2, U3, B1, B2, B3, ER, UR1, UR2, UR3, NPR = 12 };
+enum { MINK = 0, KS = 1 };
+
+struct DevParams {
+  int n[3], ng[3], N[3];
+  long long ntot, nact;
+  long long str[3];  // strides of the ghost-inclusive array per direction
+  double x0[3], dx[3];
+  int metric;
+  double a, R0, h;
+  int bc[6];
+  double gam, a_rad, courant;
+  int opacity;
+  double kabs0, kes0, kscale, Tmin;
+  int recon, flux;
+  double grad_max, ggas_max, ymax_rad;
+  double rf0, rfp, uf0, ufp, bsq_rho_max, bsq_u_max, u_rho_max;
+  int newton_max;
+  double newton_tol;
+  int precision;
+};
+
+// ----------------------------------------------------------------- geometry
+template <int MET, typename R>
+struct Geo {
+  R g00, g01, g03, g11, g13, g22, g33;  // covariant, nonzero pattern of KS
+  R G00, G01, G11, G13, G22, G33;       // contravariant
+  R gdet, alpha;
+
+  __device__ __forceinline__ void lower(const R v[4], R w[4]) const {
+    if constexpr (MET == MINK) {
+      w[0] = -v[0];
+      w[1] = v[1];
+      w[2] = v[2];
+      w[3] = v[3];
+    } else {
+      w[0] = g00 * v[0] + g01 * v[1] + g03 * v[3];
+      w[1] = g01 * v[0] + g11 * v[1] + g13 * v[3];
+      w[2] = g22 * v[2];
+      w[3] = g03 * v[0] + g13 * v[1] + g33 * v[3];
+    }
+  }
+  // g_ij v^i v^j over the spatial block
+  __device__ __forceinline__ R sq3(R v1, R v2, R v3) const {
+    if constexpr (MET == MINK) return v1 * v1 + v2 * v2 + v3 * v3;
+    else return g11 * v1 * v1 + g22 * v2 * v2 + g33 * v3 * v3 + R(2) * g13 * v1 * v3;
+  }
+  // g^{t d}, g^{d d}, g_{d d} for d = 1..3
+  __device__ __forceinline__ R Gt(int d) const {
+    if constexpr (MET == MINK) return R(0);
+    else return d == 1 ? G01 : R(0);
+  }
+  __device__ __forceinline__ R Gdd(int d) const {
+    if constexpr (MET == MINK) return R(1);
+    else return d == 1 ? G11 : (d == 2 ? G22 : G33);
+  }
+  __device__ __forceinline__ R gdd(int d) const {
+    if constexpr (MET == MINK) return R(1);
+    else return d == 1 ? g11 : (d == 2 ? g22 : g33);
+  }
+  __device__ __forceinline__ R Gtt() const {
+    if constexpr (MET == MINK) return R(-1);
+    else return G00;
+  }
+  // contravariant spatial components of a covariant 4-vector: g^{i mu} w_mu
+  __device__ __forceinline__ void raise3(const R w[4], R v[3]) const {
+    if constexpr (MET == MINK) {
+      v[0] = w[1];
+      v[1] = w[2];
+      v[2] = w[3];
+    } else {
+      v[0] = G01 * w[0] + G11 * w[1] + G13 * w[3];
+      v[1] = G22 * w[2];
+      v[2] = G13 * w[1] + G33 * w[3];
+    }
+  }
+  // g^{t mu} w_mu
+  __device__ __forceinline__ R raise_t(const R w[4]) const {
+    if constexpr (MET == MINK) return -w[0];
+    else return G00 * w[0] + G01 * w[1];
+  }
+};
+
+template <typename R> __device__ __forceinline__ R rsqrt_(R x);
+template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return 1.0 / sqrt(x); }
+template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
+
+// Kerr-Schild metric in the internal chart at (x1, x2): covariant components
+// scaled by the diagonal map Jacobian, the closed-form inverse of the
+// Kerr-Schild metric (g^{tt} = -(1+2r/S), g^{tr} = 2r/S, g^{rr} = D/S,
+// g^{r phi} = a/S, g^{theta theta} = 1/S, g^{phi phi} = 1/(S sin^2)),
+// sqrt(-g) = S |sin theta| J1 J2 J3 and the lapse 1/sqrt(1 + 2r/S).
+template <int MET, typename R>
+__device__ __forceinline__ Geo<MET, R> make_geo(const DevParams& p, R x1, R x2) {
+  Geo<MET, R> g;
+  if constexpr (MET == MINK) {
+    g.g00 = R(-1); g.g01 = R(0); g.g03 = R(0); g.g11 = R(1); g.g13 = R(0); g.g22 = R(1); g.g33 = R(1);
+    g.G00 = R(-1); g.G01 = R(0); g.G11 = R(1); g.G13 = R(0); g.G22 = R(1); g.G33 = R(1);
+    g.gdet = R(1);
+    g.alpha = R(1);
+    (void)x1; (void)x2; (void)p;
+  } else {
+    const R a = R(p.a), hh = R(p.h);
+    const R pi = R(3.14159265358979323846);
+    R ex = exp(x1);
+    R r = R(p.R0) + ex;
+    R s2x, c2x;
+    if constexpr (sizeof(R) == 8) sincospi(R(2) * x2, &s2x, &c2x);
+    else sincospif(R(2) * x2, &s2x, &c2x);
+    R th = pi * x2 + R(0.5) * (R(1) - hh) * s2x;
+    R sth, cth;
+    sincos(th, &sth, &cth);
+    R J1 = ex, J2 = pi * (R(1) + (R(1) - hh) * c2x), J3 = R(2) * pi;
+    R s2 = sth * sth;
+    R S = r * r + a * a * cth * cth;
+    R iS = R(1) / S;
+    R tr = R(2) * r * iS;
+    g.g00 = -(R(1) - tr);
+    g.g01 = tr * J1;
+    g.g03 = -a * tr * s2 * J3;
+    g.g11 = (R(1) + tr) * J1 * J1;
+    g.g13 = -a * s2 * (R(1) + tr) * J1 * J3;
+    g.g22 = S * J2 * J2;
+    g.g33 = s2 * (S + a * a * s2 * (R(1) + tr)) * J3 * J3;
+    R D = r * r - R(2) * r + a * a;
+    g.G00 = -(R(1) + tr);
+    g.G01 = tr / J1;
+    g.G11 = D * iS / (J1 * J1);
+    g.G13 = a * iS / (J1 * J3);
+    g.G22 = iS / (J2 * J2);
+    g.G33 = iS / (s2 * J3 * J3);
+    g.gdet = S * fabs(sth) * J1 * J2 * J3;
+    g.alpha = rsqrt_<R>(R(1) + tr);
+  }
+  return g;
+}
+
+// ------------------------------------------------------------- 4-vectors
+// u^t = gamma/alpha, u^i = u~^i - gamma alpha g^{ti}, gamma^2 = 1 + g_ij u~^i u~^j.
+template <int MET, typename R>
+__device__ __forceinline__ void fourvel(const Geo<MET, R>& g, R q1, R q2, R q3, R ucon[4],
+                                        R ucov[4], R* gamma) {
+  R gm = sqrt(R(1) + g.sq3(q1, q2, q3));
+  *gamma = gm;
+  if constexpr (MET == MINK) {
+    ucon[0] = gm;
+    ucon[1] = q1;
+    ucon[2] = q2;
+    ucon[3] = q3;
+  } else {
+    ucon[0] = gm / g.alpha;
+    ucon[1] = q1 - gm * g.alpha * g.G01;
+    ucon[2] = q2;
+    ucon[3] = q3;
+  }
+  g.lower(ucon, ucov);
+}
+
+// b^t = B^i u_i, b^i = (B^i + b^t u^i)/u^t, b^2 = b^mu b_mu.
+template <int MET, typename R>
+__device__ __forceinline__ void bvec(const Geo<MET, R>& g, const R ucon[4], const R ucov[4], R Bx,
+                                     R By, R Bz, R bcon[4], R bcov[4], R* bsq) {
+  R bt = Bx * ucov[1] + By * ucov[2] + Bz * ucov[3];
+  R iut = R(1) / ucon[0];
+  bcon[0] = bt;
+  bcon[1] = (Bx + bt * ucon[1]) * iut;
+  bcon[2] = (By + bt * ucon[2]) * iut;
+  bcon[3] = (Bz + bt * ucon[3]) * iut;
+  g.lower(bcon, bcov);
+  *bsq = bcon[0] * bcov[0] + bcon[1] * bcov[1] + bcon[2] * bcov[2] + bcon[3] * bcov[3];
+}
+
+template <typename R>
+__device__ __forceinline__ void opacity(const DevParams& p, R rho, R ug, R* kabs, R* ksca) {
+  R T = R(p.gam - 1.0) * ug / rho;
+  if (p.opacity == 1) {
+    R Tc = T > R(p.Tmin) ? T : R(p.Tmin);
+    // T^-3.5 = 1 / (T^3 sqrt(T))
+    R t35 = R(1) / (Tc * Tc * Tc * sqrt(Tc));
+    *kabs = R(p.kscale * p.kabs0) * rho * rho * t35;
+  } else {
+    *kabs = R(p.kscale * p.kabs0) * rho;
+  }
+  *ksca = R(p.kscale * p.kes0) * rho;
+}
+
+// ------------------------------------------------------- face state physics
+// U, F^d (12 each) and the gas/radiation signal speeds for one reconstructed
+// state at a face: T^d_nu = (w+b^2) u^d u_nu + (p+b^2/2) delta - b^d b_nu,
+// R^d_nu = 4/3 Ebar u_r^d u_r_nu + 1/3 Ebar delta; speeds from the fluid-frame
+// dispersion (k.u)^2 = c^2 (k.k + (k.u)^2) with k = delta^d - v delta^t
+// (Sec. 4.4), gas c^2 = c_s^2 + v_A^2 - c_s^2 v_A^2, radiation
+// c^2 = min(1/3, (4/(3 tau))^2) with tau the optical depth of the cell along d.
+template <int MET, typename R>
+__device__ __forceinline__ void char_speeds(const Geo<MET, R>& g, const R ucon[4], R c2, int d,
+                                            R* vmin, R* vmax) {
+  R Au = ucon[d], Bu = ucon[0];
+  R AA = g.Gdd(d), BB = g.Gtt(), AB = g.Gt(d);
+  R qa = Bu * Bu - c2 * (BB + Bu * Bu);
+  R qb = R(-2) * (Au * Bu - c2 * (AB + Au * Bu));
+  R qc = Au * Au - c2 * (AA + Au * Au);
+  R disc = qb * qb - R(4) * qa * qc;
+  disc = disc > R(0) ? disc : R(0);
+  R sd = sqrt(disc);
+  R i2a = R(0.5) / qa;
+  R v1 = (-qb + sd) * i2a, v2 = (-qb - sd) * i2a;
+  *vmax = v1 > v2 ? v1 : v2;
+  *vmin = v1 > v2 ? v2 : v1;
+}
+
+template <int MET, typename R>
+__device__ __forceinline__ void face_state(const DevParams& p, const Geo<MET, R>& g, int d,
+                                           const R P[NPR], R U[NPR], R F[NPR], R sp[4]) {
+  R ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq;
+  fourvel<MET, R>(g, P[U1], P[U2], P[U3], ucon, ucov, &gm);
+  bvec<MET, R>(g, ucon, ucov, P[B1], P[B2], P[B3], bcon, bcov, &bsq);
+  const R rho = P[RHO], ug = P[UU];
+  const R pg = R(p.gam - 1.0) * ug;
+  const R w = rho + ug + pg;
+  const R wb = w + bsq, pt = pg + R(0.5) * bsq;
+  const R gd = g.gdet;
+  const R mt = rho * ucon[0], md = rho * ucon[d];
+  U[0] = gd * mt;
+  U[1] = gd * (wb * ucon[0] * ucov[0] + pt - bcon[0] * bcov[0] + mt);
+  U[2] = gd * (wb * ucon[0] * ucov[1] - bcon[0] * bcov[1]);
+  U[3] = gd * (wb * ucon[0] * ucov[2] - bcon[0] * bcov[2]);
+  U[4] = gd * (wb * ucon[0] * ucov[3] - bcon[0] * bcov[3]);
+  U[5] = gd * P[B1];
+  U[6] = gd * P[B2];
+  U[7] = gd * P[B3];
+  F[0] = gd * md;
+  F[1] = gd * (wb * ucon[d] * ucov[0] - bcon[d] * bcov[0] + md);
+#pragma unroll
+  for (int i = 1; i <= 3; ++i)
+    F[1 + i] = gd * (wb * ucon[d] * ucov[i] + (i == d ? pt : R(0)) - bcon[d] * bcov[i]);
+  const R iut = R(1) / ucon[0];
+  const R vd = ucon[d] * iut;
+  const R Bd = P[B1 + d - 1];
+#pragma unroll
+  for (int i = 1; i <= 3; ++i) F[4 + i] = (i == d) ? R(0) : gd * (P[B1 + i - 1] * vd - Bd * ucon[i] * iut);
+  // radiation
+  R urc[4], urv[4], gr;
+  fourvel<MET, R>(g, P[UR1], P[UR2], P[UR3], urc, urv, &gr);
+  const R E = P[ER];
+  const R e43 = R(4.0 / 3.0) * E, e13 = E * R(1.0 / 3.0);
+  U[8] = gd * (e43 * urc[0] * urv[0] + e13);
+  U[9] = gd * (e43 * urc[0] * urv[1]);
+  U[10] = gd * (e43 * urc[0] * urv[2]);
+  U[11] = gd * (e43 * urc[0] * urv[3]);
+#pragma unroll
+  for (int n = 0; n < 4; ++n) F[8 + n] = gd * (e43 * urc[d] * urv[n] + (n == d ? e13 : R(0)));
+  // gas fast magnetosonic speed
+  R cs2 = R(p.gam) * pg / w;
+  R va2 = bsq / (w + bsq);
+  R cms2 = cs2 + va2 - cs2 * va2;
+  cms2 = cms2 > R(1) ? R(1) : (cms2 < R(0) ? R(0) : cms2);
+  char_speeds<MET, R>(g, ucon, cms2, d, &sp[0], &sp[1]);
+  R kabs, ksca;
+  opacity<R>(p, rho, ug, &kabs, &ksca);
+  R tau = (kabs + ksca) * sqrt(g.gdd(d)) * R(p.dx[d - 1]);
+  R cr2 = R(1.0 / 3.0);
+  if (tau > R(0)) {
+    R lim = R(4.0 / 3.0) / tau;
+    lim = lim * lim;
+    cr2 = lim < cr2 ? lim : cr2;
+  }
+  char_speeds<MET, R>(g, urc, cr2, d, &sp[2], &sp[3]);
+}
+
+// ------------------------------------------------------ M1 inversion (FP64)
+// Closed form in the ZAMO frame (Sec. 4.6): E_rad = alpha^2 R^{tt},
+// U~^i = alpha g^{i mu} R^t_mu + E_rad alpha g^{ti}, y = U~^2/E_rad^2,
+// gamma^2 = (2 - y + sqrt(4-3y)) / (4(1-y)), p_rad = E_rad/(4 gamma^2 - 1),
+// u~^i = gamma U~^i / (4 p_rad gamma^2).  Limiters: BASIC (lim 0) and TYPE2
+// (lim 2).  Returns 1 if E_rad <= 0 on entry.
+template <int MET>
+__device__ __forceinline__ int rad_invert(const DevParams& p, const Geo<MET, double>& g,
+                                          const double Rt[4], int lim, double out[4]) {
+  const double a = g.alpha;
+  double Erad = a * a * g.raise_t(Rt);
+  double Ut[3];
+  g.raise3(Rt, Ut);
+  const double et = Erad * g.Gt(1);
+  Ut[0] = a * (Ut[0] + et);
+  Ut[1] = a * Ut[1];
+  Ut[2] = a * Ut[2];
+  double Utsq = g.sq3(Ut[0], Ut[1], Ut[2]);
+  const double ymax = p.ymax_rad;
+  int negE = Erad <= 0.0;
+  double y;
+  if (lim == 0) {
+    if (Erad <= 0.0) {
+      out[0] = 1e-300;
+      out[1] = out[2] = out[3] = 0.0;
+      return negE;
+    }
+    y = Utsq / (Erad * Erad);
+    if (y < 0.0) {
+      y = 0.0;
+      Ut[0] = Ut[1] = Ut[2] = 0.0;
+    }
+    if (y > ymax) {
+      double f = sqrt(ymax / y);
+      Ut[0] *= f;
+      Ut[1] *= f;
+      Ut[2] *= f;
+      y = ymax;
+    }
+  } else {
+    y = Erad > 0.0 ? Utsq / (Erad * Erad) : HUGE_VAL;
+    if (Erad <= 0.0 || y > ymax) {
+      Erad = 1e-150 + sqrt(Utsq / ymax);
+      y = Utsq / (Erad * Erad);
+    }
+    if (y < 0.0) y = 0.0;
+  }
+  double gam2 = (2.0 - y + sqrt(4.0 - 3.0 * y)) / (4.0 * (1.0 - y));
+  double prad = Erad / (4.0 * gam2 - 1.0);
+  out[0] = 3.0 * prad;
+  double f = sqrt(gam2) / (4.0 * prad * gam2);
+  out[1] = f * Ut[0];
+  out[2] = f * Ut[1];
+  out[3] = f * Ut[2];
+  return negE;
+}
+
+// ---------------------------------------------------- gas 1D_W inversion (FP64)
+// Sec. 4.5: Newton on f(W') = W' - E' - p + B^2 (1+v~^2)/2 - S^2/(2W^2) with
+// W = W' + D, v~^2 from Eq. vsqeq, then v~^i from Eq. tveq.  Input in
+// conserved form: Dlab = rho0 u^t, taue = T^t_t + rho0 u^t, Tt[3] = T^t_i,
+// B[3] lab field; guess primitives give the starting W'.  Writes rho0, u_g,
+// u~^i into out[0..4].  Returns 0 on success.
+template <int MET>
+__device__ __forceinline__ int gas_invert(const DevParams& p, const Geo<MET, double>& g, double Dlab,
+                                          double taue, const double Tt[3], const double B[3],
+                                          const double* Pg, double tol, double out[5]) {
+  const double a = g.alpha, gam = p.gam;
+  const double D = a * Dlab;
+  const double Ttt = taue - Dlab;
+  double Ep = -taue + (1.0 - a) * Dlab + a * a * g.Gt(1) * Tt[0];
+  const double E = Ep + D;
+  double Q[4] = {a * Ttt, a * Tt[0], a * Tt[1], a * Tt[2]};
+  double Qt[3];
+  g.raise3(Q, Qt);
+  Qt[0] += E * a * g.Gt(1);
+  const double Bz0 = a * B[0], Bz1 = a * B[1], Bz2 = a * B[2];
+  const double QdB = Q[1] * Bz0 + Q[2] * Bz1 + Q[3] * Bz2;
+  const double Bsq = g.sq3(Bz0, Bz1, Bz2);
+  const double Qtsq = g.sq3(Qt[0], Qt[1], Qt[2]);
+  const double S2 = QdB * QdB;
+  if (!(D > 0.0) || !isfinite(E)) return 1;
+  double q0 = g.sq3(Pg[U1], Pg[U2], Pg[U3]);
+  double gm0 = sqrt(1.0 + q0);
+  double ugg = Pg[UU] > 0.0 ? Pg[UU] : 0.0;
+  double Wp = D * q0 / (1.0 + gm0) + gam * ugg * gm0 * gm0;
+  if (!(Wp > 0.0)) Wp = fmax(fabs(Ep), 1e-300);
+  const double gfac = (gam - 1.0) / gam;
+  double f = 0.0, df = 0.0;
+  auto resid = [&](double Wpv, double* fo, double* dfo) -> bool {
+    double W = Wpv + D;
+    double WB = Bsq + W;
+    double iW = 1.0 / W, iWB = 1.0 / WB;
+    double vsq = (Qtsq * W * W + S2 * (Bsq + 2.0 * W)) * (iWB * iWB) * (iW * iW);
+    if (!(vsq < 1.0) || !(W > 0.0)) return false;
+    double g2 = 1.0 / (1.0 - vsq);
+    double gg = sqrt(g2);
+    double usq = g2 * vsq;
+    double chi = (Wpv - D * usq / (gg + 1.0)) * (1.0 - vsq);
+    double pg = gfac * chi;
+    *fo = Wpv - Ep - pg + 0.5 * Bsq * (1.0 + vsq) - 0.5 * S2 * iW * iW;
+    double iW3 = iW * iW * iW, iWB3 = iWB * iWB * iWB;
+    double dvsq = -2.0 * iW3 * iWB3 * (S2 * (3.0 * W * WB + Bsq * Bsq) + Qtsq * W * W * W);
+    double dchi = (1.0 - vsq) - W * dvsq + 0.5 * D * gg * dvsq;
+    *dfo = 1.0 - gfac * dchi + 0.5 * Bsq * dvsq + S2 * iW3;
+    return true;
+  };
+  int guard = 0;
+  while (!resid(Wp, &f, &df) && guard < 200) {
+    Wp = 2.0 * Wp + 1e-300;
+    ++guard;
+  }
+  if (guard >= 200) return 2;
+  bool conv = false;
+  for (int it = 0; it < 50; ++it) {
+    if (!(df != 0.0) || !isfinite(f) || !isfinite(df)) return 3;
+    double dW = -f / df;
+    double Wn = Wp + dW, fn = 0.0, dfn = 0.0;
+    int back = 0;
+    while ((!(Wn > 0.0) || !resid(Wn, &fn, &dfn)) && back < 60) {
+      dW *= 0.5;
+      Wn = Wp + dW;
+      ++back;
+    }
+    if (back >= 60) return 4;
+    Wp = Wn;
+    f = fn;
+    df = dfn;
+    if (fabs(dW) <= tol * fabs(Wp)) {
+      conv = true;
+      break;
+    }
+  }
+  if (!conv) return 5;
+  double W = Wp + D;
+  double vsq = (Qtsq * W * W + S2 * (Bsq + 2.0 * W)) / ((Bsq + W) * (Bsq + W) * W * W);
+  double g2 = 1.0 / (1.0 - vsq);
+  double gg = sqrt(g2);
+  double usq = g2 * vsq;
+  double chi = (Wp - D * usq / (gg + 1.0)) / g2;
+  double rho = D / gg, ug = chi / gam;
+  if (!(rho > 0.0) || !(ug > 0.0) || !isfinite(ug)) return 6;
+  out[0] = rho;
+  out[1] = ug;
+  double iv = gg / (W + Bsq), sb = QdB / W;
+  out[2] = iv * (Qt[0] + sb * Bz0);
+  out[3] = iv * (Qt[1] + sb * Bz1);
+  out[4] = iv * (Qt[2] + sb * Bz2);
+  return 0;
+}
+
+}  // namespace hr

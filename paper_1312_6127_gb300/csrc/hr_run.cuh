@@ -1,0 +1,291 @@
+// Launch sequences of one sub-step for a given metric (internal).
+#pragma once
+#include "hr_ctx.h"
+#include "hr_kernels.cuh"
+
+namespace hr {
+
+inline Bufs make_bufs(harmrad_ctx* c) {
+  Bufs b;
+  b.P = c->P;
+  b.Un = c->Un;
+  for (int d = 0; d < 3; ++d) {
+    b.F[d] = c->F[d];
+    b.spd[d] = c->spd[d];
+    b.flat[d] = c->flat[d];
+  }
+  b.aux = c->aux;
+  b.emf = c->emf;
+  b.dt = c->dt;
+  b.status = c->status;
+  b.iters = c->iters;
+  b.failed = c->failed;
+  b.qcount = c->qcount;
+  b.qzone = c->qzone;
+  b.qdata = c->qdata;
+  b.fzone = c->fzone;
+  b.ftmp = c->ftmp;
+  b.stats = c->stats;
+  b.dtmin = c->dtmin;
+  return b;
+}
+
+template <int MET, typename R>
+int faces_impl(harmrad_ctx* c, bool fresh) {
+  const DevParams& p = c->dp;
+  cudaStream_t st = c->stream;
+  int nk = 0;
+  for (int d = 0; d < 3; ++d) {
+    if (p.n[d] == 1) continue;
+    long long work = 2LL * p.ng[d];
+    for (int e = 0; e < 3; ++e)
+      if (e != d) work *= (e < d) ? p.N[e] : p.n[e];
+    k_bc_fill<<<grid_for(work, c->sms, 256), 256, 0, st>>>(p, c->P, d);
+    mark(c, HARMRAD_K_BC);
+    ++nk;
+  }
+  k_prep<MET, R><<<grid_for(p.ntot, c->sms, 256), 256, 0, st>>>(p, c->P, (R*)c->aux);
+  mark(c, HARMRAD_K_PREP);
+  ++nk;
+  if (p.recon == 0) {
+    for (int d = 0; d < 3; ++d) {
+      if (p.n[d] == 1) continue;
+      if (fresh) {
+        if (cudaMemsetAsync(c->flat[d], 0, 2 * p.ntot * sizeof(R), st) != cudaSuccess) return HARMRAD_E_CUDA;
+        mark(c, HARMRAD_K_OTHER);
+      }
+      long long work = 1;
+      for (int e = 0; e < 3; ++e) work *= p.n[e] > 1 ? p.n[e] + 2 : 1;
+      k_flatten<R><<<grid_for(work, c->sms, 256), 256, 0, st>>>(p, c->P, (const R*)c->aux, (R*)c->flat[d], d);
+      mark(c, HARMRAD_K_FLATTEN);
+      ++nk;
+    }
+  }
+  for (int d = 0; d < 3; ++d) {
+    if (p.n[d] == 1) continue;
+    long long work = 1;
+    for (int e = 0; e < 3; ++e) work *= (e == d) ? p.n[e] + 1 : (p.n[e] > 1 ? p.n[e] + 2 : 1);
+    k_face<MET, R><<<grid_for(work, c->sms, 128), 128, 0, st>>>(p, c->P, (const R*)c->aux, (const R*)c->flat[d],
+                                                               (R*)c->F[d], (R*)c->spd[d], d);
+    mark(c, HARMRAD_K_FACE);
+    ++nk;
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int b = a + 1; b < 3; ++b) {
+      if (p.n[a] == 1 || p.n[b] == 1) continue;
+      long long we = 1, wc = 0;
+      for (int e = 0; e < 3; ++e) we *= p.n[e] + ((e == a || e == b) ? 1 : 0);
+      long long la = 1, lb = 1;
+      for (int e = 0; e < 3; ++e) {
+        la *= p.n[e] + (e == a ? 1 : 0);
+        lb *= p.n[e] + (e == b ? 1 : 0);
+      }
+      wc = la + lb;
+      k_emf<R><<<grid_for(we, c->sms, 256), 256, 0, st>>>(p, (const R*)c->F[a], (const R*)c->F[b], (R*)c->emf, a, b);
+      mark(c, HARMRAD_K_CT);
+      k_ct<R><<<grid_for(wc, c->sms, 256), 256, 0, st>>>(p, (const R*)c->emf, (R*)c->F[a], (R*)c->F[b], a, b);
+      mark(c, HARMRAD_K_CT);
+      nk += 2;
+    }
+  if (cudaGetLastError() != cudaSuccess) return HARMRAD_E_CUDA;
+  return nk;
+}
+
+template <int MET, typename R>
+int cfl_impl(harmrad_ctx* c) {
+  int nk = faces_impl<MET, R>(c, true);
+  if (nk < 0) return nk;
+  Bufs b = make_bufs(c);
+  k_cfl_init<<<1, 32, 0, c->stream>>>(b);
+  mark(c, HARMRAD_K_CFL);
+  k_cfl<R><<<grid_for(c->dp.nact, c->sms, 256), 256, 0, c->stream>>>(c->dp, b);
+  mark(c, HARMRAD_K_CFL);
+  k_cfl_finish<<<1, 32, 0, c->stream>>>(c->dp, b);
+  mark(c, HARMRAD_K_CFL);
+  if (cudaGetLastError() != cudaSuccess) return HARMRAD_E_CUDA;
+  return nk + 3;
+}
+
+template <int MET, typename R>
+int solve_impl(harmrad_ctx* c, int stage) {
+  const DevParams& p = c->dp;
+  cudaStream_t st = c->stream;
+  if (cudaMemsetAsync(c->qcount, 0, 2 * sizeof(int), st) != cudaSuccess) return HARMRAD_E_CUDA;
+  if (cudaMemsetAsync(c->failed, 0, p.nact, st) != cudaSuccess) return HARMRAD_E_CUDA;
+  mark(c, HARMRAD_K_OTHER);
+  Bufs b = make_bufs(c);
+  k_update<MET, R><<<grid_for(p.nact, c->sms, 128), 128, 0, st>>>(p, b, stage);
+  mark(c, HARMRAD_K_UPDATE);
+  // the retry queue and back-up list are short: one persistent wave of blocks
+  k_retry<MET><<<c->sms * 2, 128, 0, st>>>(p, b);
+  mark(c, HARMRAD_K_RETRY);
+  k_backup_avg<<<c->sms, 128, 0, st>>>(p, b);
+  mark(c, HARMRAD_K_BACKUP);
+  k_backup_apply<MET><<<c->sms, 128, 0, st>>>(p, b);
+  mark(c, HARMRAD_K_BACKUP);
+  if (cudaGetLastError() != cudaSuccess) return HARMRAD_E_CUDA;
+  return 4;
+}
+
+// --------------------------------------------------- point-wise entry kernels
+template <int MET>
+__global__ void k_zone_physics(DevParams p, int n, const double* __restrict__ x,
+                               const double* __restrict__ P, double* U, double* SM, double* F,
+                               double* speeds) {
+  for (int z = blockIdx.x * blockDim.x + threadIdx.x; z < n; z += gridDim.x * blockDim.x) {
+    double x1 = x[4 * z + 1], x2 = x[4 * z + 2];
+    Geo<MET, double> g = make_geo<MET, double>(p, x1, x2);
+    double Pz[NPR];
+    for (int q = 0; q < NPR; ++q) Pz[q] = P[NPR * z + q];
+    for (int d = 1; d <= 3; ++d) {
+      double Uq[NPR], Fq[NPR], sp[4];
+      face_state<MET, double>(p, g, d, Pz, Uq, Fq, sp);
+      if (F)
+        for (int q = 0; q < NPR; ++q) F[(3 * z + d - 1) * NPR + q] = Fq[q];
+      if (speeds)
+        for (int q = 0; q < 4; ++q) speeds[(3 * z + d - 1) * 4 + q] = sp[q];
+      if (d == 1 && U)
+        for (int q = 0; q < NPR; ++q) U[NPR * z + q] = Uq[q];
+    }
+    if (SM) {
+      double S[NPR];
+      for (int q = 0; q < NPR; ++q) S[q] = 0.0;
+      if constexpr (MET == KS) {
+        double ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq, urc[4], urv[4], gr;
+        fourvel<MET, double>(g, Pz[U1], Pz[U2], Pz[U3], ucon, ucov, &gm);
+        bvec<MET, double>(g, ucon, ucov, Pz[B1], Pz[B2], Pz[B3], bcon, bcov, &bsq);
+        fourvel<MET, double>(g, Pz[UR1], Pz[UR2], Pz[UR3], urc, urv, &gr);
+        double pg = (p.gam - 1.0) * Pz[UU];
+        double wb = Pz[RHO] + Pz[UU] + pg + bsq, pt = pg + 0.5 * bsq;
+        double e43 = (4.0 / 3.0) * Pz[ER];
+        MetricDeriv md = ks_derivs(p, x1, x2);
+        for (int m = 0; m < 2; ++m) {
+          S[2 + m] = 0.5 * g.gdet * (wb * qform(md, m, ucon) - qform(md, m, bcon)) + pt * md.sg[m];
+          S[9 + m] = 0.5 * g.gdet * e43 * qform(md, m, urc) + Pz[ER] * (1.0 / 3.0) * md.sg[m];
+        }
+      }
+      for (int q = 0; q < NPR; ++q) SM[NPR * z + q] = S[q];
+    }
+  }
+}
+
+template <int MET>
+__global__ void k_zone_implicit(DevParams p, int n, const double* __restrict__ x,
+                                const double* __restrict__ Us, const double* __restrict__ Ps,
+                                const double* __restrict__ hh, double* Pout, double* eTo, int* itso,
+                                unsigned char* meth) {
+  for (int z = blockIdx.x * blockDim.x + threadIdx.x; z < n; z += gridDim.x * blockDim.x) {
+    double x1 = x[4 * z + 1], x2 = x[4 * z + 2];
+    Geo<MET, double> g = make_geo<MET, double>(p, x1, x2);
+    double Ust[NPR], P0[NPR];
+    for (int q = 0; q < NPR; ++q) {
+      Ust[q] = Us[NPR * z + q];
+      P0[q] = Ps[NPR * z + q];
+    }
+    ImpSys<MET> s;
+    build_sys<MET>(p, g, Ust, hh[z], s);
+    double x0[4] = {P0[UU], P0[U1], P0[U2], P0[U3]};
+    double kabs, ksca;
+    opacity<double>(p, P0[RHO], P0[UU], &kabs, &ksca);
+    double dl = 0.0;
+    for (int d = 1; d <= 3; ++d)
+      if (p.n[d - 1] > 1) dl = fmax(dl, sqrt(g.gdd(d)) * p.dx[d - 1]);
+    if ((kabs + ksca) * dl < 2.0 / 3.0) {
+      double go[5], T3[3] = {s.Ts[1], s.Ts[2], s.Ts[3]};
+      if (gas_invert<MET>(p, g, s.Dlab, s.Ts[0], T3, s.B, P0, 1e-9, go) == 0) {
+        x0[0] = go[1];
+        x0[1] = go[2];
+        x0[2] = go[3];
+        x0[3] = go[4];
+      }
+    }
+    double bx[4], beT;
+    int steps = newton_pmhd<MET>(p, s, x0, bx, &beT);
+    double Pn[NPR];
+    int method = 0;
+    double eT = beT;
+    if (beT < 1e-9) {
+      pmhd_final<MET>(p, s, bx, Pn);
+    } else {
+      double Pb[NPR];
+      if (isfinite(beT)) {
+        ImpRes rr;
+        ImpState stt;
+        pmhd_res<MET>(p, s, bx, rr, &stt, false);
+        Pb[RHO] = stt.rho;
+        Pb[UU] = bx[0];
+        Pb[U1] = bx[1];
+        Pb[U2] = bx[2];
+        Pb[U3] = bx[3];
+        for (int q = 0; q < 4; ++q) Pb[ER + q] = stt.Pr[q];
+      }
+      const double* Pg = (isfinite(beT) && beT < 1e-4) ? Pb : P0;
+      double urc[4], urv[4], gr;
+      fourvel<MET, double>(g, Pg[UR1], Pg[UR2], Pg[UR3], urc, urv, &gr);
+      double e43 = (4.0 / 3.0) * Pg[ER];
+      double xr[4];
+      xr[0] = e43 * urc[0] * urv[0] + Pg[ER] * (1.0 / 3.0);
+      for (int m = 1; m < 4; ++m) xr[m] = e43 * urc[0] * urv[m];
+      double gas[5] = {Pg[RHO], Pg[UU], Pg[U1], Pg[U2], Pg[U3]};
+      double ux[4], ugas[5], ueT;
+      steps += newton_urad<MET>(p, s, xr, gas, ux, ugas, &ueT);
+      if (isfinite(ueT) && (!isfinite(beT) || ueT < beT)) {
+        Pn[RHO] = ugas[0];
+        Pn[UU] = ugas[1];
+        Pn[U1] = ugas[2];
+        Pn[U2] = ugas[3];
+        Pn[U3] = ugas[4];
+        Pn[B1] = s.B[0];
+        Pn[B2] = s.B[1];
+        Pn[B3] = s.B[2];
+        double Pr[4];
+        int neg = rad_invert<MET>(p, g, ux, 2, Pr);
+        if (neg) rad_invert<MET>(p, g, ux, 0, Pr);
+        for (int q = 0; q < 4; ++q) Pn[ER + q] = Pr[q];
+        method = 1;
+        eT = ueT;
+      } else if (isfinite(beT)) {
+        pmhd_final<MET>(p, s, bx, Pn);
+      } else {
+        for (int q = 0; q < NPR; ++q) Pn[q] = P0[q];
+        Pn[B1] = s.B[0];
+        Pn[B2] = s.B[1];
+        Pn[B3] = s.B[2];
+        method = 2;
+      }
+      if (eT > 1e-7) method = 2;
+    }
+    for (int q = 0; q < NPR; ++q) Pout[NPR * z + q] = Pn[q];
+    if (eTo) eTo[z] = eT;
+    if (itso) itso[z] = steps;
+    if (meth) meth[z] = (unsigned char)method;
+  }
+}
+
+template <int MET>
+int Run<MET>::faces(harmrad_ctx* c, bool fresh) {
+  return c->real_size == 8 ? faces_impl<MET, double>(c, fresh) : faces_impl<MET, float>(c, fresh);
+}
+template <int MET>
+int Run<MET>::cfl(harmrad_ctx* c) {
+  return c->real_size == 8 ? cfl_impl<MET, double>(c) : cfl_impl<MET, float>(c);
+}
+template <int MET>
+int Run<MET>::solve(harmrad_ctx* c, int stage) {
+  return c->real_size == 8 ? solve_impl<MET, double>(c, stage) : solve_impl<MET, float>(c, stage);
+}
+template <int MET>
+int Run<MET>::zone_physics(const DevParams& dp, int n, const double* x, const double* P, double* U,
+                           double* SM, double* F, double* speeds, cudaStream_t st, int sms) {
+  k_zone_physics<MET><<<grid_for(n, sms, 128), 128, 0, st>>>(dp, n, x, P, U, SM, F, speeds);
+  return cudaGetLastError() == cudaSuccess ? 1 : HARMRAD_E_CUDA;
+}
+template <int MET>
+int Run<MET>::zone_implicit(const DevParams& dp, int n, const double* x, const double* Us,
+                            const double* Ps, const double* h, double* Pout, double* eT, int* iters,
+                            unsigned char* method, cudaStream_t st, int sms) {
+  k_zone_implicit<MET><<<grid_for(n, sms, 128), 128, 0, st>>>(dp, n, x, Us, Ps, h, Pout, eT, iters, method);
+  return cudaGetLastError() == cudaSuccess ? 1 : HARMRAD_E_CUDA;
+}
+
+}  // namespace hr

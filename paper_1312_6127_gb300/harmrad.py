@@ -1,0 +1,279 @@
+"""Python binding of the harmrad C ABI (include/harmrad.h).
+
+Argument marshalling only: every step of the time step runs in the CUDA
+kernels of ``libharmrad.so``.  PyTorch provides device memory and the CUDA
+stream.  Importing works without a GPU; creating a grid or calling a kernel
+requires the built library and a CUDA device, and raises otherwise.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libharmrad.so")
+NPRIM = 12
+
+OK, W_BACKUP_USED = 0, 1
+ZONE_PMHD, ZONE_URAD, ZONE_BACKUP = 0, 1, 2
+PREC_FP64, PREC_SPLIT = 0, 1
+
+EXPORTS = [
+    "harmrad_init", "harmrad_destroy", "harmrad_set_prims", "harmrad_get_prims",
+    "harmrad_cfl_dt", "harmrad_step", "harmrad_step_host", "harmrad_get_stats",
+    "harmrad_get_status", "harmrad_get_iters", "harmrad_compute_fluxes",
+    "harmrad_zone_physics", "harmrad_zone_implicit", "harmrad_profile_step", "harmrad_strerror",
+]
+KERNEL_CLASSES = ["bc", "prep", "flatten", "face", "ct", "update", "retry", "backup", "cfl", "other"]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("n", ctypes.c_int * 3),
+        ("x0", ctypes.c_double * 3),
+        ("dx", ctypes.c_double * 3),
+        ("metric", ctypes.c_int),
+        ("a_spin", ctypes.c_double),
+        ("R0", ctypes.c_double),
+        ("hslope", ctypes.c_double),
+        ("bc", ctypes.c_int * 6),
+        ("gam", ctypes.c_double),
+        ("a_rad", ctypes.c_double),
+        ("courant", ctypes.c_double),
+        ("opacity", ctypes.c_int),
+        ("kappa_abs0", ctypes.c_double),
+        ("kappa_es0", ctypes.c_double),
+        ("kappa_scale", ctypes.c_double),
+        ("T_kappa_min", ctypes.c_double),
+        ("recon", ctypes.c_int),
+        ("flux", ctypes.c_int),
+        ("gamma_rad_max", ctypes.c_double),
+        ("gamma_gas_max", ctypes.c_double),
+        ("floor_rho0", ctypes.c_double),
+        ("floor_rho_pow", ctypes.c_double),
+        ("floor_u0", ctypes.c_double),
+        ("floor_u_pow", ctypes.c_double),
+        ("bsq_rho_max", ctypes.c_double),
+        ("bsq_u_max", ctypes.c_double),
+        ("u_rho_max", ctypes.c_double),
+        ("newton_max", ctypes.c_int),
+        ("newton_tol", ctypes.c_double),
+        ("precision", ctypes.c_int),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("dt", ctypes.c_double),
+        ("zone_stages", ctypes.c_longlong),
+        ("pmhd_ok", ctypes.c_longlong),
+        ("urad_ok", ctypes.c_longlong),
+        ("backup", ctypes.c_longlong),
+        ("newton_iters", ctypes.c_longlong),
+        ("kernel_launches", ctypes.c_int),
+        ("graph", ctypes.c_int),
+    ]
+
+
+class KernelTimes(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 10), ("launches", ctypes.c_int * 10),
+                ("total_launches", ctypes.c_int)]
+
+
+class HarmradError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libharmrad.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise HarmradError("libharmrad.so not found at %s: build it first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')" % path)
+    L = ctypes.CDLL(path)
+    vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
+    pp = ctypes.POINTER(Params)
+    L.harmrad_init.argtypes = [pp, vp, ctypes.POINTER(vp)]
+    L.harmrad_destroy.argtypes = [vp]
+    L.harmrad_destroy.restype = None
+    L.harmrad_set_prims.argtypes = [vp, vp, ip]
+    L.harmrad_get_prims.argtypes = [vp, vp, ip]
+    L.harmrad_cfl_dt.argtypes = [vp, dp]
+    L.harmrad_step.argtypes = [vp, ctypes.c_double]
+    L.harmrad_step_host.argtypes = [vp, vp, vp, ctypes.c_double]
+    L.harmrad_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    L.harmrad_get_status.argtypes = [vp, vp, ip]
+    L.harmrad_get_iters.argtypes = [vp, vp, ip]
+    L.harmrad_compute_fluxes.argtypes = [vp, ip, vp]
+    L.harmrad_zone_physics.argtypes = [pp, ip, vp, vp, vp, vp, vp, vp, vp]
+    L.harmrad_zone_implicit.argtypes = [pp, ip, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.harmrad_profile_step.argtypes = [vp, ctypes.c_double, ctypes.POINTER(KernelTimes)]
+    L.harmrad_strerror.restype = ctypes.c_char_p
+    L.harmrad_strerror.argtypes = [ip]
+    _lib = L
+    return L
+
+
+def _check(rc, what):
+    if rc < 0:
+        raise HarmradError("%s failed: %s (%d)" % (what, load().harmrad_strerror(rc).decode(), rc))
+    return rc
+
+
+def make_params(cfg, precision=None):
+    p = Params()
+    for name, ctype in Params._fields_:
+        if name == "precision":
+            v = cfg.get("precision", PREC_FP64) if precision is None else precision
+        else:
+            if name not in cfg:
+                raise KeyError("missing parameter %s" % name)
+            v = cfg[name]
+        if hasattr(ctype, "_length_"):
+            arr = getattr(p, name)
+            for i, x in enumerate(v):
+                arr[i] = x
+        else:
+            setattr(p, name, v)
+    return p
+
+
+def _stream_ptr(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Grid:
+    """One grid on the current CUDA device, stepped by the library."""
+
+    def __init__(self, cfg, precision=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise HarmradError("a CUDA device is required")
+        L = load()
+        self.cfg = dict(cfg)
+        self.params = make_params(cfg, precision)
+        self.n = tuple(cfg["n"])
+        self.shape = (NPRIM, self.n[2], self.n[1], self.n[0])
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check(L.harmrad_init(ctypes.byref(self.params), _stream_ptr(self.stream), ctypes.byref(h)),
+               "harmrad_init")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().harmrad_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_prims(self, P):
+        """P: numpy float64 array (host) or torch CUDA float64 tensor, [12,n3,n2,n1]."""
+        import torch
+        if isinstance(P, torch.Tensor):
+            assert P.is_cuda and P.dtype == torch.float64 and tuple(P.shape) == self.shape
+            P = P.contiguous()
+            _check(load().harmrad_set_prims(self._h, ctypes.c_void_p(P.data_ptr()), 1), "set_prims")
+        else:
+            P = np.ascontiguousarray(P, dtype=np.float64).reshape(self.shape)
+            _check(load().harmrad_set_prims(self._h, P.ctypes.data_as(ctypes.c_void_p), 0), "set_prims")
+
+    def get_prims(self, device=False):
+        import torch
+        if device:
+            out = torch.empty(self.shape, dtype=torch.float64, device="cuda")
+            _check(load().harmrad_get_prims(self._h, ctypes.c_void_p(out.data_ptr()), 1), "get_prims")
+            return out
+        out = np.empty(self.shape)
+        _check(load().harmrad_get_prims(self._h, out.ctypes.data_as(ctypes.c_void_p), 0), "get_prims")
+        return out
+
+    def cfl_dt(self):
+        dt = ctypes.c_double()
+        _check(load().harmrad_cfl_dt(self._h, ctypes.byref(dt)), "cfl_dt")
+        return dt.value
+
+    def step(self, dt=0.0):
+        _check(load().harmrad_step(self._h, float(dt)), "step")
+
+    def step_host(self, P_in, P_out, dt=0.0):
+        """Host-in, host-out step through the C ABI (both numpy float64)."""
+        _check(load().harmrad_step_host(self._h, P_in.ctypes.data_as(ctypes.c_void_p),
+                                        P_out.ctypes.data_as(ctypes.c_void_p), float(dt)), "step_host")
+
+    def profile_step(self, dt=0.0):
+        """One eager step with an event after every kernel: per-class device ms."""
+        kt = KernelTimes()
+        _check(load().harmrad_profile_step(self._h, float(dt), ctypes.byref(kt)), "profile_step")
+        return {name: (kt.ms[i], kt.launches[i]) for i, name in enumerate(KERNEL_CLASSES)}
+
+    def stats(self):
+        s = Stats()
+        _check(load().harmrad_get_stats(self._h, ctypes.byref(s)), "get_stats")
+        return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+    def status(self):
+        st = np.empty(self.shape[1:], dtype=np.uint8)
+        _check(load().harmrad_get_status(self._h, st.ctypes.data_as(ctypes.c_void_p), 0), "get_status")
+        return st
+
+    def iters(self):
+        it = np.empty(self.shape[1:], dtype=np.int32)
+        _check(load().harmrad_get_iters(self._h, it.ctypes.data_as(ctypes.c_void_p), 0), "get_iters")
+        return it
+
+    def fluxes(self, d):
+        m = list(self.n)
+        m[d - 1] += 1
+        F = np.empty((NPRIM, m[2], m[1], m[0]))
+        _check(load().harmrad_compute_fluxes(self._h, int(d), F.ctypes.data_as(ctypes.c_void_p)),
+               "compute_fluxes")
+        return F
+
+
+def _dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def zone_physics(cfg, x, P):
+    """Point-wise U, SM, F[3], speeds[3][4] at n points (numpy in, numpy out)."""
+    import torch
+    n = len(x)
+    xd, Pd = _dev(x), _dev(P)
+    U = torch.empty((n, 12), dtype=torch.float64, device="cuda")
+    SM = torch.empty((n, 12), dtype=torch.float64, device="cuda")
+    F = torch.empty((n, 3, 12), dtype=torch.float64, device="cuda")
+    S = torch.empty((n, 3, 4), dtype=torch.float64, device="cuda")
+    p = make_params(cfg)
+    vp = lambda t: ctypes.c_void_p(t.data_ptr())
+    _check(load().harmrad_zone_physics(ctypes.byref(p), n, vp(xd), vp(Pd), vp(U), vp(SM), vp(F), vp(S),
+                                       _stream_ptr(None)), "zone_physics")
+    return U.cpu().numpy(), SM.cpu().numpy(), F.cpu().numpy(), S.cpu().numpy()
+
+
+def zone_implicit(cfg, x, Ustar, Ps, h):
+    """Implicit four-force solve of n independent zones (numpy in, numpy out)."""
+    import torch
+    n = len(x)
+    xd, Ud, Pd, hd = _dev(x), _dev(Ustar), _dev(Ps), _dev(np.broadcast_to(h, (n,)))
+    Pout = torch.empty((n, 12), dtype=torch.float64, device="cuda")
+    eT = torch.empty(n, dtype=torch.float64, device="cuda")
+    it = torch.empty(n, dtype=torch.int32, device="cuda")
+    meth = torch.empty(n, dtype=torch.uint8, device="cuda")
+    p = make_params(cfg)
+    vp = lambda t: ctypes.c_void_p(t.data_ptr())
+    _check(load().harmrad_zone_implicit(ctypes.byref(p), n, vp(xd), vp(Ud), vp(Pd), vp(hd), vp(Pout),
+                                        vp(eT), vp(it), vp(meth), _stream_ptr(None)), "zone_implicit")
+    return Pout.cpu().numpy(), eT.cpu().numpy(), it.cpu().numpy(), meth.cpu().numpy()

@@ -539,3 +539,26 @@ def test_contact_advection_converges():
         errs.append(np.abs(Q[RHO, 0, 0] - exact).mean())
     assert errs[0] < 2e-3
     assert errs[0] / errs[1] > 3.0
+
+
+def test_error_norm_sees_momentum_inside_horizon():
+    """Inside the horizon g^{rr} < 0; the merged spatial error norm (Sec. 4.8)
+    must still weigh the momentum rows, so a pure theta-momentum perturbation
+    of size delta raises e_T at first order in delta."""
+    cfg = ks_params()
+    cfg.update(kappa_abs0=1.0, kappa_es0=0.4, a_rad=1.0)
+    p = O.make_params(cfg)
+    x = [0.0, math.log(1.25), 0.43, 0.1]
+    P = np.zeros(12)
+    P[RHO], P[UU], P[ER] = 1.0, 0.05, 0.02
+    P[U1], P[U2], P[U3] = -0.3, 0.01, 0.02
+    P[B1], P[B2] = 0.01, 0.002
+    U, _ = O.prim_to_cons(p, x, P)
+    base = [P[UU], P[U1], P[U2], P[U3]]
+    _, e0, _ = O.pmhd_residual(p, x, U, 0.0, base)
+    assert e0 < 1e-13
+    for delta in (1e-4, 1e-6):
+        xg = list(base)
+        xg[2] += delta * 0.01
+        _, e1, _ = O.pmhd_residual(p, x, U, 0.0, xg)
+        assert math.isfinite(e1) and e1 > 1e-3 * delta
