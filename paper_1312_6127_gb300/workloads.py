@@ -202,10 +202,11 @@ def thin_pulse(n=(32, 32, 32), L=100.0, w=5.0, T_a=1e6):
     return cfg, P
 
 
-def random_states(n, seed=3, metric=0, gamma_max=50.0, magnetised=True):
+def random_states(n, seed=3, metric=0, gamma_max=50.0, magnetised=True, gamma_rad_max=20.0):
     """Random point states for per-zone tests: positions x[n,4] (internal
     coordinates) and primitives P[n,12] spanning density, temperature,
-    Lorentz factor (up to gamma_max) and radiation ranges, plus a parameter
+    Lorentz factor (gas up to gamma_max, radiation frame up to gamma_rad_max)
+    and radiation ranges, plus a parameter
     dict for the chosen metric (0 Minkowski, 1 Kerr-Schild a = 0.9375)."""
     g = rng(seed)
     cfg = base_params() if metric == 0 else _ks_setup((64, 32, 16))
@@ -228,7 +229,7 @@ def random_states(n, seed=3, metric=0, gamma_max=50.0, magnetised=True):
     if magnetised:
         P[:, B1:B3 + 1] = g.standard_normal((n, 3)) * np.sqrt(P[:, RHO])[:, None] * 0.3
     P[:, ER] = P[:, UU] * np.exp(g.uniform(np.log(1e-3), np.log(1e3), n))
-    lgr = g.uniform(0.0, np.log(20.0), n)
+    lgr = g.uniform(0.0, np.log(gamma_rad_max), n)
     gr = np.exp(lgr)
     d2 = g.standard_normal((n, 3))
     d2 /= np.linalg.norm(d2, axis=1, keepdims=True)

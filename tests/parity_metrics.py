@@ -107,8 +107,15 @@ def flux_errors(Fg, Fo, scales=None):
     return E
 
 
-def point_errors(metric_cfg, x, A, R, gam):
-    """Errors of point states A vs R ([12] each) at internal position x."""
+def point_errors(metric_cfg, x, A, R, gam, rad_conserved=False):
+    """Errors of point states A vs R ([12] each) at internal position x.
+
+    rad_conserved: measure the radiation (entries 8..11) in conserved form,
+    |dR^t_nu| (orthonormal ZAMO size for the spatial components) against
+    |R^t_t| + |T^t_t + rho0 u^t|.  The PMHD solve recovers the radiation from
+    total energy-momentum conservation, so its absolute precision is set by the
+    total energy scale, and a sub-dominant radiation field carries that error
+    relative to its own, smaller, primitives."""
     p = O.make_params(metric_cfg)
     gcov = O.metric(p, x)[0]
     sg = np.sqrt(np.diag(gcov)[1:])
@@ -130,4 +137,12 @@ def point_errors(metric_cfg, x, A, R, gam):
         e[2 + i] = abs(A[2 + i] - R[2 + i]) * sg[i] / ug
         e[5 + i] = abs(A[5 + i] - R[5 + i]) * sg[i] / bs
         e[9 + i] = abs(A[9 + i] - R[9 + i]) * sg[i] / ur
+    if rad_conserved:
+        gcon = O.metric(p, x)[1]
+        UA, _ = O.prim_to_cons(p, x, A)
+        scale = abs(U[8]) + abs(U[1])
+        e[8] = abs(UA[8] - U[8]) / scale
+        for i in range(3):
+            zi = np.sqrt(gcon[i + 1, i + 1] - gcon[0, i + 1] ** 2 / gcon[0, 0])
+            e[9 + i] = abs(UA[9 + i] - U[9 + i]) * zi / scale
     return e

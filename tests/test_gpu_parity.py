@@ -40,7 +40,17 @@ def test_zone_physics_matches_oracle(metric):
 
 @pytest.mark.parametrize("metric", [0, 1])
 def test_zone_implicit_matches_oracle(metric):
-    cfg, x, P = W.random_states(300, seed=201 + metric, metric=metric, gamma_max=5.0)
+    """Per-zone implicit solve (Sec. 4.7-4.10) on random states with gas Lorentz
+    factors up to 5 and radiation-frame Lorentz factors up to 3.  Zones that
+    both sides solve with PMHD agree to 1e-10 in the gas primitives; where they
+    stop at different iterates inside the Newton tolerance the GPU root must
+    satisfy the oracle's equations (Eq. source3) to the accepted error (its own
+    e_T, at least 1e-9, up to a factor 2 of evaluation round-off).  The
+    radiation, recovered from total energy-momentum conservation, agrees to
+    1e-10 in conserved form against the total energy scale (see
+    parity_metrics.point_errors)."""
+    cfg, x, P = W.random_states(300, seed=201 + metric, metric=metric, gamma_max=5.0,
+                                gamma_rad_max=3.0)
     cfg.update(kappa_abs0=3.0, kappa_es0=1.0)
     p = O.make_params(cfg)
     g = W.rng(5)
@@ -58,15 +68,12 @@ def test_zone_implicit_matches_oracle(metric):
         if info.method != 0 or meth[n] != 0:
             continue
         nsame += 1
-        e = point_errors(cfg, x[n], Pout[n], Po, cfg["gam"])
-        if e.max() >= 1e-10:
-            # two accepted Newton roots (Sec. 4.10 accepts e_T < 1e-9): the GPU
-            # root must satisfy the oracle's equations (Eq. source3) to the
-            # acceptance tolerance, up to the round-off of evaluating e_T there
-            # (a factor 2), and agree to 1e-7
+        e = point_errors(cfg, x[n], Pout[n], Po, cfg["gam"], rad_conserved=True)
+        assert e[8:].max() < 1e-10, (n, e)
+        if e[:8].max() >= 1e-10:
             xg = [Pout[n][1], Pout[n][2], Pout[n][3], Pout[n][4]]
             _, eT_o, _ = O.pmhd_residual(p, x[n], Ust[n], h[n], xg)
-            assert eT_o < 2e-9 and e.max() < 1e-7, (n, e, eT_o)
+            assert eT_o < 2.0 * max(eT[n], 1e-9) and e.max() < 1e-7, (n, e, eT_o, eT[n])
     assert nsame > 250
 
 
