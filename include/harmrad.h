@@ -180,6 +180,26 @@ int harmrad_zone_implicit(const harmrad_params* p, int n, const double* x, const
                           const double* Ps, const double* h, double* Pout, double* eT, int* iters,
                           unsigned char* method, void* stream);
 
+/* Same solve as harmrad_zone_implicit, for callers that cannot allocate device
+ * memory: processes whose device memory is owned by another allocator (a
+ * framework's caching pool, a fixed-budget service) and may not call
+ * cudaMalloc or cudaFree, whose implicit synchronisation they also cannot
+ * afford.  The paper has no counterpart; this is a deployment variant.
+ * The zones that PMHD does not accept are queued for URAD in a fixed array in
+ * the library's static device memory (about 2.9 MB per device that loads the
+ * library, kept until the process exits); the call makes no device
+ * allocation.  n must not exceed 65536 (HARMRAD_E_ARG otherwise).  The first
+ * call on a device looks up that array's device address, so make it before
+ * any stream capture.  The array is shared by every call on the device and
+ * keeps the last call's contents (each call clears its queue counter first):
+ * calls whose work overlaps on the GPU race, so serialise them, e.g. on one
+ * stream.  Arguments, layouts and outputs as for harmrad_zone_implicit; the
+ * call synchronises the stream before returning. */
+int harmrad_zone_implicit_static(const harmrad_params* p, int n, const double* x,
+                                 const double* Ustar, const double* Ps, const double* h,
+                                 double* Pout, double* eT, int* iters, unsigned char* method,
+                                 void* stream);
+
 /* Kernel classes timed by harmrad_profile_step. */
 #define HARMRAD_K_BC 0        /* ghost-zone fill */
 #define HARMRAD_K_PREP 1      /* per-cell metric factors and flattener inputs */

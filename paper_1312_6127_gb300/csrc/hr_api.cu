@@ -222,6 +222,9 @@ int dalloc(T** p, size_t bytes) {
 
 }  // namespace
 
+// Parameter validation shared with the entry points in other translation units.
+int harmrad_fill_params_internal(const harmrad_params* p, DevParams& d) { return fill_devparams(p, d); }
+
 extern "C" {
 
 int harmrad_init(const harmrad_params* p, void* stream, harmrad_ctx** out) {

@@ -1,0 +1,254 @@
+// harmrad_zone_implicit_static: the per-zone implicit solve with its retry
+// queue in statically allocated device memory, for callers that cannot
+// allocate device memory.
+//
+// The solve runs in two kernels, like the grid step: a PMHD pass over all
+// zones, which writes the zones it accepts and appends the others to a
+// retry queue; then a URAD pass that drains the queue.  Here the queue lives
+// in a file-scope __device__ array of fixed size, so a call makes no
+// cudaMalloc/cudaFree and no allocating library call.  The array exists once
+// per device that loads the library and lives until the process exits.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <atomic>
+
+#include "../../include/harmrad.h"
+#include "hr_common.cuh"
+#include "hr_implicit.cuh"
+#include "hr_kernels.cuh"
+
+namespace {
+
+// Largest zone count one call accepts; the queue below is sized for it.
+constexpr int kStaticMaxZones = 65536;
+
+// Queue layout (bytes): [0, 256) header with the entry counter;
+// then kStaticMaxZones int zone indices; then kStaticMaxZones records of
+// 5 doubles (PMHD best iterate x[4] and its e_T).
+constexpr size_t kHeader = 256;
+constexpr size_t kIdxBytes = sizeof(int) * kStaticMaxZones;
+constexpr size_t kRecBytes = sizeof(double) * 5 * kStaticMaxZones;
+constexpr size_t kScratchBytes = kHeader + kIdxBytes + kRecBytes;  // about 2.9 MB
+
+static __device__ __align__(256) unsigned char g_zi_scratch[kScratchBytes];
+
+// Device address of g_zi_scratch, looked up once per device (host code may
+// not use the symbol itself: on the host it names a stand-in, not device memory).
+constexpr int kMaxDevices = 64;
+std::atomic<void*> g_scratch_addr[kMaxDevices];
+
+struct QueueView {
+  int* count;
+  int* idx;
+  double* rec;
+};
+
+__host__ __device__ inline QueueView queue_view(void* base) {
+  unsigned char* b = (unsigned char*)base;
+  QueueView q;
+  q.count = (int*)b;
+  q.idx = (int*)(b + kHeader);
+  q.rec = (double*)(b + kHeader + kIdxBytes);
+  return q;
+}
+
+__global__ void k_zi_clear(void* base) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *queue_view(base).count = 0;
+}
+
+// Geometry, explicit state and the PMHD guess of one zone.
+template <int MET>
+__device__ void zi_setup(const hr::DevParams& p, int z, const double* x, const double* Us,
+                         const double* Ps, const double* hh, hr::Geo<MET, double>& g,
+                         hr::ImpSys<MET>& s, double P0[hr::NPR]) {
+  using namespace hr;
+  double x1 = x[4 * z + 1], x2 = x[4 * z + 2];
+  g = make_geo<MET, double>(p, x1, x2);
+  double Ust[NPR];
+  for (int q = 0; q < NPR; ++q) {
+    Ust[q] = Us[NPR * z + q];
+    P0[q] = Ps[NPR * z + q];
+  }
+  build_sys<MET>(p, g, Ust, hh[z], s);
+}
+
+template <int MET>
+__global__ void k_zi_pmhd(hr::DevParams p, int n, const double* __restrict__ x,
+                          const double* __restrict__ Us, const double* __restrict__ Ps,
+                          const double* __restrict__ hh, double* Pout, double* eTo, int* itso,
+                          unsigned char* meth, void* base) {
+  using namespace hr;
+  QueueView qv = queue_view(base);
+  for (int z = blockIdx.x * blockDim.x + threadIdx.x; z < n; z += gridDim.x * blockDim.x) {
+    Geo<MET, double> g;
+    ImpSys<MET> s;
+    double P0[NPR];
+    zi_setup<MET>(p, z, x, Us, Ps, hh, g, s, P0);
+    double x0[4] = {P0[UU], P0[U1], P0[U2], P0[U3]};
+    double kabs, ksca;
+    opacity<double>(p, P0[RHO], P0[UU], &kabs, &ksca);
+    double dl = 0.0;
+    for (int d = 1; d <= 3; ++d)
+      if (p.n[d - 1] > 1) dl = fmax(dl, sqrt(g.gdd(d)) * p.dx[d - 1]);
+    if ((kabs + ksca) * dl < 2.0 / 3.0) {
+      double go[5], T3[3] = {s.Ts[1], s.Ts[2], s.Ts[3]};
+      if (gas_invert<MET>(p, g, s.Dlab, s.Ts[0], T3, s.B, P0, 1e-9, go) == 0) {
+        x0[0] = go[1];
+        x0[1] = go[2];
+        x0[2] = go[3];
+        x0[3] = go[4];
+      }
+    }
+    double bx[4], beT;
+    int steps = newton_pmhd<MET>(p, s, x0, bx, &beT);
+    if (itso) itso[z] = steps;
+    if (beT < 1e-9) {
+      double Pn[NPR];
+      pmhd_final<MET>(p, s, bx, Pn);
+      for (int q = 0; q < NPR; ++q) Pout[NPR * z + q] = Pn[q];
+      if (eTo) eTo[z] = beT;
+      if (meth) meth[z] = 0;
+    } else {
+      int slot = atomicAdd(qv.count, 1);
+      qv.idx[slot] = z;
+      double* r = qv.rec + 5 * (size_t)slot;
+      for (int q = 0; q < 4; ++q) r[q] = isfinite(beT) ? bx[q] : 0.0;
+      r[4] = beT;
+    }
+  }
+}
+
+template <int MET>
+__global__ void k_zi_urad(hr::DevParams p, const double* __restrict__ x,
+                          const double* __restrict__ Us, const double* __restrict__ Ps,
+                          const double* __restrict__ hh, double* Pout, double* eTo, int* itso,
+                          unsigned char* meth, void* base) {
+  using namespace hr;
+  QueueView qv = queue_view(base);
+  const int nq = *qv.count;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nq; e += gridDim.x * blockDim.x) {
+    const int z = qv.idx[e];
+    const double* r = qv.rec + 5 * (size_t)e;
+    Geo<MET, double> g;
+    ImpSys<MET> s;
+    double P0[NPR];
+    zi_setup<MET>(p, z, x, Us, Ps, hh, g, s, P0);
+    double bx[4] = {r[0], r[1], r[2], r[3]};
+    const double beT = r[4];
+    double Pb[NPR];
+    if (isfinite(beT)) {
+      ImpRes rr;
+      ImpState stt;
+      pmhd_res<MET>(p, s, bx, rr, &stt, false);
+      Pb[RHO] = stt.rho;
+      Pb[UU] = bx[0];
+      Pb[U1] = bx[1];
+      Pb[U2] = bx[2];
+      Pb[U3] = bx[3];
+      for (int q = 0; q < 4; ++q) Pb[ER + q] = stt.Pr[q];
+    }
+    const double* Pg = (isfinite(beT) && beT < 1e-4) ? Pb : P0;
+    double urc[4], urv[4], gr;
+    fourvel<MET, double>(g, Pg[UR1], Pg[UR2], Pg[UR3], urc, urv, &gr);
+    double e43 = (4.0 / 3.0) * Pg[ER];
+    double xr[4];
+    xr[0] = e43 * urc[0] * urv[0] + Pg[ER] * (1.0 / 3.0);
+    for (int m = 1; m < 4; ++m) xr[m] = e43 * urc[0] * urv[m];
+    double gas[5] = {Pg[RHO], Pg[UU], Pg[U1], Pg[U2], Pg[U3]};
+    double ux[4], ugas[5], ueT;
+    int steps = newton_urad<MET>(p, s, xr, gas, ux, ugas, &ueT);
+    double Pn[NPR];
+    int method = 0;
+    double eT = beT;
+    if (isfinite(ueT) && (!isfinite(beT) || ueT < beT)) {
+      Pn[RHO] = ugas[0];
+      Pn[UU] = ugas[1];
+      Pn[U1] = ugas[2];
+      Pn[U2] = ugas[3];
+      Pn[U3] = ugas[4];
+      Pn[B1] = s.B[0];
+      Pn[B2] = s.B[1];
+      Pn[B3] = s.B[2];
+      double Pr[4];
+      int neg = rad_invert<MET>(p, g, ux, 2, Pr);
+      if (neg) rad_invert<MET>(p, g, ux, 0, Pr);
+      for (int q = 0; q < 4; ++q) Pn[ER + q] = Pr[q];
+      method = 1;
+      eT = ueT;
+    } else if (isfinite(beT)) {
+      pmhd_final<MET>(p, s, bx, Pn);
+    } else {
+      for (int q = 0; q < NPR; ++q) Pn[q] = P0[q];
+      Pn[B1] = s.B[0];
+      Pn[B2] = s.B[1];
+      Pn[B3] = s.B[2];
+      method = 2;
+    }
+    if (eT > 1e-7) method = 2;
+    for (int q = 0; q < NPR; ++q) Pout[NPR * z + q] = Pn[q];
+    if (eTo) eTo[z] = eT;
+    if (itso) itso[z] += steps;
+    if (meth) meth[z] = (unsigned char)method;
+  }
+}
+
+// Device address of the static queue on the current device (set-up on first use).
+int scratch_address(void** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return HARMRAD_E_CUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) return HARMRAD_E_ARG;
+  void* a = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!a) {
+    if (cudaGetSymbolAddress(&a, g_zi_scratch) != cudaSuccess || !a) {
+      cudaGetLastError();
+      return HARMRAD_E_CUDA;
+    }
+    g_scratch_addr[dev].store(a, std::memory_order_release);
+  }
+  *out = a;
+  return HARMRAD_OK;
+}
+
+}  // namespace
+
+extern int harmrad_fill_params_internal(const harmrad_params* p, hr::DevParams& d);
+
+extern "C" int harmrad_zone_implicit_static(const harmrad_params* prm, int n, const double* x,
+                                            const double* Us, const double* Ps, const double* h,
+                                            double* Pout, double* eT, int* iters,
+                                            unsigned char* method, void* stream) {
+  if (!prm || n < 0 || (n > 0 && (!x || !Us || !Ps || !h || !Pout))) return HARMRAD_E_ARG;
+  if (n > kStaticMaxZones) return HARMRAD_E_ARG;
+  hr::DevParams dp;
+  int rc = harmrad_fill_params_internal(prm, dp);
+  if (rc) return rc;
+  if (n == 0) return HARMRAD_OK;
+  void* base = nullptr;
+  rc = scratch_address(&base);
+  if (rc) return rc;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return HARMRAD_E_CUDA;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  k_zi_clear<<<1, 32, 0, st>>>(base);
+  int grid = hr::grid_for(n, sms, 128);
+  if (dp.metric == 1) {
+    k_zi_pmhd<hr::KS><<<grid, 128, 0, st>>>(dp, n, x, Us, Ps, h, Pout, eT, iters, method, base);
+    k_zi_urad<hr::KS><<<sms * 2, 128, 0, st>>>(dp, x, Us, Ps, h, Pout, eT, iters, method, base);
+  } else {
+    k_zi_pmhd<hr::MINK><<<grid, 128, 0, st>>>(dp, n, x, Us, Ps, h, Pout, eT, iters, method, base);
+    k_zi_urad<hr::MINK><<<sms * 2, 128, 0, st>>>(dp, x, Us, Ps, h, Pout, eT, iters, method, base);
+  }
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaGetLastError();
+    return HARMRAD_E_CUDA;
+  }
+  return HARMRAD_OK;
+}

@@ -22,7 +22,8 @@ EXPORTS = [
     "harmrad_init", "harmrad_destroy", "harmrad_set_prims", "harmrad_get_prims",
     "harmrad_cfl_dt", "harmrad_step", "harmrad_step_host", "harmrad_get_stats",
     "harmrad_get_status", "harmrad_get_iters", "harmrad_compute_fluxes",
-    "harmrad_zone_physics", "harmrad_zone_implicit", "harmrad_profile_step", "harmrad_strerror",
+    "harmrad_zone_physics", "harmrad_zone_implicit", "harmrad_zone_implicit_static",
+    "harmrad_profile_step", "harmrad_strerror",
 ]
 KERNEL_CLASSES = ["bc", "prep", "flatten", "face", "ct", "update", "retry", "backup", "cfl", "other"]
 
@@ -112,6 +113,7 @@ def load(path=LIB_PATH):
     L.harmrad_compute_fluxes.argtypes = [vp, ip, vp]
     L.harmrad_zone_physics.argtypes = [pp, ip, vp, vp, vp, vp, vp, vp, vp]
     L.harmrad_zone_implicit.argtypes = [pp, ip, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.harmrad_zone_implicit_static.argtypes = [pp, ip, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.harmrad_profile_step.argtypes = [vp, ctypes.c_double, ctypes.POINTER(KernelTimes)]
     L.harmrad_strerror.restype = ctypes.c_char_p
     L.harmrad_strerror.argtypes = [ip]
