@@ -237,7 +237,7 @@ def main():
         fresh = entry.get("kernel_hash") == kernel_hash() and entry.get("size") == list(n)
         flops_per_zone = entry.get("fp64_flops_per_zone_stage")
         traffic = entry.get("dram_bytes_per_launch") if fresh else None
-        if flops_per_zone:
+        if flops_per_zone and fresh:
             achieved = flops_per_zone * nact / (avg_ms / 1e3) / 1e12
             roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3,
                         "unit": "TFLOP/s", "frac": achieved / (FP64_PEAK_GFLOPS / 1e3),
@@ -248,7 +248,8 @@ def main():
             roofline = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS / 1e3,
                         "unit": "TFLOP/s", "frac": None, "traffic": traffic,
                         "kernel": "k_update", "kernel_ms": avg_ms,
-                        "note": "FP64 op count per zone not yet captured"}
+                        "note": "FP64 op count per zone not captured for this kernel build "
+                                "(profiles/k_update_counters.json kernel_hash differs)"}
         # HBM view of the whole step: algorithmic bytes per zone-cycle
         hbm = measured_peaks().get("hbm_gbs")
         step_ms = ms / args.steps

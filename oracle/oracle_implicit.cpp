@@ -231,8 +231,10 @@ bool stalled(History& hs, int k) {
   return false;
 }
 
-// PMHD Newton (Sec. 4.9-4.10): undamped, two-sided FD Jacobian with a
-// normalised offset of 1e-8 (1e-10 once e_I < 1e-9), u_g < 0 reset to |u_g|/2.
+// PMHD Newton (Sec. 4.9-4.10): undamped, one-sided FD Jacobian (the paper
+// takes two-sided differences for PMHD only in its staged scheme, which is not
+// used here) with a normalised offset of 1e-8 (1e-10 once e_I < 1e-9),
+// u_g < 0 reset to |u_g|/2.
 int newton_pmhd(const Sys& s, const double x0[4], Res& best) {
   const orc_params& p = *s.p;
   const Geom& G = *s.G;
@@ -253,7 +255,7 @@ int newton_pmhd(const Sys& s, const double x0[4], Res& best) {
     if (stalled(hs, k)) break;
     if (k >= p.newton_max) break;
     if (r.eI < 1e-9) eps = 1e-10;
-    // Jacobian dE_gas/dx by centred differences
+    // Jacobian dE_gas/dx by forward differences
     double usq = 0.0;
     for (int i = 0; i < 3; ++i)
       for (int j = 0; j < 3; ++j) usq += G.gcov[i + 1][j + 1] * x[1 + i] * x[1 + j];
@@ -261,14 +263,12 @@ int newton_pmhd(const Sys& s, const double x0[4], Res& best) {
     double J[4][4];
     for (int j = 0; j < 4; ++j) {
       double dj = (j == 0) ? eps * std::fabs(x[0]) : eps * umag / std::sqrt(G.gcov[j][j]);
-      double xp[4], xm[4];
-      for (int i = 0; i < 4; ++i) xp[i] = xm[i] = x[i];
+      double xp[4];
+      for (int i = 0; i < 4; ++i) xp[i] = x[i];
       xp[j] += dj;
-      xm[j] -= dj;
-      Res rp, rm;
+      Res rp;
       pmhd_res(s, xp, rp);
-      pmhd_res(s, xm, rm);
-      for (int i = 0; i < 4; ++i) J[i][j] = (rp.Eg[i] - rm.Eg[i]) / (2.0 * dj);
+      for (int i = 0; i < 4; ++i) J[i][j] = (rp.Eg[i] - r.Eg[i]) / dj;
     }
     double dx[4], E[4] = {r.Eg[0], r.Eg[1], r.Eg[2], r.Eg[3]};
     if (!solve4(J, E, dx)) break;

@@ -197,7 +197,7 @@ int launch_step(harmrad_ctx* c, bool with_cfl) {
 
 void free_all(harmrad_ctx* c) {
   void* ptrs[] = {c->P, c->Un, c->F[0], c->F[1], c->F[2], c->spd[0], c->spd[1], c->spd[2],
-                  c->aux, c->flat[0], c->flat[1], c->flat[2], c->emf, c->dt, c->status, c->iters,
+                  c->aux, c->flat[0], c->flat[1], c->flat[2], c->emf, c->edges, c->dt, c->status, c->iters,
                   c->failed, c->qcount, c->qzone, c->qdata, c->fzone, c->ftmp, c->stats, c->dtmin,
                   c->stage_buf, c->flag};
   for (void* q : ptrs)
@@ -267,6 +267,7 @@ int harmrad_init(const harmrad_params* p, void* stream, harmrad_ctx** out) {
   }
   rc = rc ? rc : dalloc(&c->aux, 10 * nt * rs);
   rc = rc ? rc : dalloc(&c->emf, nt * rs);
+  rc = rc ? rc : dalloc(&c->edges, 24 * nt * rs);
   rc = rc ? rc : dalloc(&c->dt, sizeof(double));
   rc = rc ? rc : dalloc(&c->status, na);
   rc = rc ? rc : dalloc(&c->iters, na * sizeof(int));

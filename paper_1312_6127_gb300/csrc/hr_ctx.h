@@ -25,6 +25,7 @@ struct harmrad_ctx {
   void* aux;
   void* flat[3];
   void* emf;
+  void* edges;  // [2][12][ntot] reconstructed edge values of one direction
   double* dt;
   unsigned char* status;
   int* iters;

@@ -6,7 +6,8 @@
 // PMHD iterates the gas primitives x = (u_g, u~^i); URAD iterates x = R^t_nu
 // and recovers the gas from a 1D_W inversion inside every residual.  Newton
 // steps follow Eq. newton with D = 1 and a finite-difference Jacobian
-// (two-sided for PMHD, one-sided for URAD), normalised offset 1e-8, switching
+// (one-sided; the paper's two-sided PMHD differences belong to its staged
+// scheme, which is not used), normalised offset 1e-8, switching
 // to 1e-10 once e_I < 1e-9; the stopping rules of Sec. 4.10 (tolerance,
 // stalled error, repeated rises, tiny step, step limit) and the best-error
 // bookkeeping are applied.
@@ -23,6 +24,7 @@ template <int MET>
 struct ImpSys {
   Geo<MET, double> g;
   double Dlab;   // rho0 u^t
+  double iDlab;  // 1 / (rho0 u^t)
   double Ts[4];  // explicit T^t_nu, rest-mass flux added to the t row
   double Rs[4];  // explicit R^t_nu
   double B[3];
@@ -44,14 +46,15 @@ struct ImpState {
   double Rt_pre[4];
 };
 
+// G_nu for gas temperature T (given, so the caller can form it without a
+// division).
 template <int MET>
-__device__ __forceinline__ void four_force_rad(const DevParams& p, double rho, double ug,
+__device__ __forceinline__ void four_force_rad(const DevParams& p, double rho, double T,
                                                const double ucon[4], const double ucov[4],
                                                const double urc[4], const double urv[4], double E,
                                                double G[4]) {
   double kabs, ksca;
-  opacity<double>(p, rho, ug, &kabs, &ksca);
-  double T = (p.gam - 1.0) * ug / rho;
+  opacity_T<double>(p, rho, T, &kabs, &ksca);
   double T2 = T * T;
   double lam = kabs * p.a_rad * T2 * T2;
   double uru = urv[0] * ucon[0] + urv[1] * ucon[1] + urv[2] * ucon[2] + urv[3] * ucon[3];
@@ -108,8 +111,9 @@ __device__ __forceinline__ void pmhd_res(const DevParams& p, const ImpSys<MET>& 
   const auto& g = s.g;
   double ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq;
   fourvel<MET, double>(g, x[1], x[2], x[3], ucon, ucov, &gm);
-  double rho = s.Dlab / ucon[0];
-  bvec<MET, double>(g, ucon, ucov, s.B[0], s.B[1], s.B[2], bcon, bcov, &bsq);
+  const double iut = g.alpha / gm;  // 1/u^t
+  double rho = s.Dlab * iut;
+  bvec_iut<MET, double>(g, ucon, ucov, iut, s.B[0], s.B[1], s.B[2], bcon, bcov, &bsq);
   double pg = (p.gam - 1.0) * x[0];
   double wb = rho + x[0] + pg + bsq, pt = pg + 0.5 * bsq;
   double Tc[4];
@@ -123,19 +127,20 @@ __device__ __forceinline__ void pmhd_res(const DevParams& p, const ImpSys<MET>& 
   r.negE = rad_invert<MET>(p, g, Rt, 2, Pr);
   double urc[4], urv[4], gr;
   fourvel<MET, double>(g, Pr[1], Pr[2], Pr[3], urc, urv, &gr);
-  double e43 = (4.0 / 3.0) * Pr[0];
-  double Rc[4];
-  Rc[0] = e43 * urc[0] * urv[0] + Pr[0] * (1.0 / 3.0);
-#pragma unroll
-  for (int k = 1; k < 4; ++k) Rc[k] = e43 * urc[0] * urv[k];
   double G[4];
-  four_force_rad<MET>(p, rho, x[0], ucon, ucov, urc, urv, Pr[0], G);
+  // T = p_g / rho0 = (gamma-1) u_g u^t / (rho0 u^t)
+  four_force_rad<MET>(p, rho, (p.gam - 1.0) * x[0] * ucon[0] * s.iDlab, ucon, ucov, urc, urv, Pr[0],
+                      G);
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    r.Eg[k] = Tc[k] - s.Ts[k] - s.h * G[k];
-    r.Er[k] = Rc[k] - s.Rs[k] + s.h * G[k];
-  }
+  for (int k = 0; k < 4; ++k) r.Eg[k] = Tc[k] - s.Ts[k] - s.h * G[k];
   if (norm) {
+    double e43 = (4.0 / 3.0) * Pr[0];
+    double Rc[4];
+    Rc[0] = e43 * urc[0] * urv[0] + Pr[0] * (1.0 / 3.0);
+#pragma unroll
+    for (int k = 1; k < 4; ++k) Rc[k] = e43 * urc[0] * urv[k];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) r.Er[k] = Rc[k] - s.Rs[k] + s.h * G[k];
     normalise<MET>(s, Tc, Rc, G, true, r);
     r.ok = isfinite(r.eT);
   } else {
@@ -197,26 +202,33 @@ __device__ __forceinline__ bool solve4(double A[4][4], double b[4], double z[4])
   return true;
 }
 
-// Error history for the stalled-error checks: errors at the last five iterates.
+// Error history for the stalled-error checks: the errors of the four previous
+// iterates, shifted every iteration (register-resident: no indexed array).
 struct Hist {
-  double eT[6], eI[6];
+  double t1, t2, t3, t4;  // e_T of iterates k-1 .. k-4
+  double i2, i3, i4, i1;  // e_I of iterates k-2 .. k-4, k-1
   int rises;
 };
 
 __device__ __forceinline__ bool stalled(Hist& hs, int k, double eT, double eI) {
-  // ring buffer: slot k % 6 holds iterate k
-  hs.eT[k % 6] = eT;
-  hs.eI[k % 6] = eI;
   bool stop = false;
   if (k > 5) {
-    if (eT > hs.eT[(k - 1) % 6]) {
+    if (eT > hs.t1) {
       hs.rises++;
       if (hs.rises >= 5) stop = true;
     }
-    double mT = (hs.eT[(k - 4) % 6] + hs.eT[(k - 3) % 6] + hs.eT[(k - 2) % 6]) / 3.0;
-    double mI = (hs.eI[(k - 4) % 6] + hs.eI[(k - 3) % 6] + hs.eI[(k - 2) % 6]) / 3.0;
+    double mT = (hs.t4 + hs.t3 + hs.t2) / 3.0;
+    double mI = (hs.i4 + hs.i3 + hs.i2) / 3.0;
     if (eT > 0.5 * mT || eI > 0.5 * mI) stop = true;
   }
+  hs.t4 = hs.t3;
+  hs.t3 = hs.t2;
+  hs.t2 = hs.t1;
+  hs.t1 = eT;
+  hs.i4 = hs.i3;
+  hs.i3 = hs.i2;
+  hs.i2 = hs.i1;
+  hs.i1 = eI;
   return stop;
 }
 
@@ -226,8 +238,7 @@ template <int MET>
 __device__ int newton_pmhd(const DevParams& p, const ImpSys<MET>& s, const double x0[4],
                            double best_x[4], double* best_eT) {
   double x[4] = {x0[0], x0[1], x0[2], x0[3]};
-  Hist hs;
-  hs.rises = 0;
+  Hist hs = {HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, 0};
   *best_eT = HUGE_VAL;
   int steps = 0;
   double eps = 1e-8;
@@ -249,15 +260,18 @@ __device__ int newton_pmhd(const DevParams& p, const ImpSys<MET>& s, const doubl
 #pragma unroll 1
     for (int j = 0; j < 4; ++j) {
       double dj = (j == 0) ? eps * fabs(x[0]) : eps * umag / sqrt(s.g.gdd(j));
-      double xp[4] = {x[0], x[1], x[2], x[3]}, xm[4] = {x[0], x[1], x[2], x[3]};
-      xp[j] += dj;
-      xm[j] -= dj;
-      ImpRes rp, rm;
-      pmhd_res<MET>(p, s, xp, rp, nullptr, false);
-      pmhd_res<MET>(p, s, xm, rm, nullptr, false);
-      double i2d = 1.0 / (2.0 * dj);
+      double xp[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) J[i][j] = (rp.Eg[i] - rm.Eg[i]) * i2d;
+      for (int i = 0; i < 4; ++i) xp[i] = x[i] + (i == j ? dj : 0.0);
+      ImpRes rp;
+      pmhd_res<MET>(p, s, xp, rp, nullptr, false);
+      double id = 1.0 / dj;
+      // column j of J, written through compile-time indices
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (c == j) J[i][c] = (rp.Eg[i] - r.Eg[i]) * id;
     }
     double E[4] = {r.Eg[0], r.Eg[1], r.Eg[2], r.Eg[3]}, dx[4];
     if (!solve4(J, E, dx)) break;
@@ -325,7 +339,7 @@ __device__ __forceinline__ bool urad_res(const DevParams& p, const ImpSys<MET>& 
 #pragma unroll
   for (int k = 1; k < 4; ++k) Rc[k] = e43 * urc[0] * urv[k];
   double G[4];
-  four_force_rad<MET>(p, rho, ug, ucon, ucov, urc, urv, Pr[0], G);
+  four_force_rad<MET>(p, rho, (p.gam - 1.0) * ug / rho, ucon, ucov, urc, urv, Pr[0], G);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     r.Eg[k] = Tc[k] - s.Ts[k] - s.h * G[k];
@@ -348,8 +362,7 @@ template <int MET>
 __device__ int newton_urad(const DevParams& p, const ImpSys<MET>& s, const double x0[4], double Pg[5],
                            double best_x[4], double best_Pg[5], double* best_eT) {
   double x[4] = {x0[0], x0[1], x0[2], x0[3]};
-  Hist hs;
-  hs.rises = 0;
+  Hist hs = {HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, 0};
   *best_eT = HUGE_VAL;
   int steps = 0, ninv = 0;
   const int budget = 20 * 6;
@@ -433,6 +446,7 @@ __device__ __forceinline__ void build_sys(const DevParams& p, const Geo<MET, dou
   s.g = g;
   double igd = 1.0 / g.gdet;
   s.Dlab = Us[0] * igd;
+  s.iDlab = 1.0 / s.Dlab;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     s.Ts[k] = Us[1 + k] * igd;

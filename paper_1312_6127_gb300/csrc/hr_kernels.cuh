@@ -233,8 +233,9 @@ __device__ __forceinline__ void ppm_cell(const R s[5], R chi, R* aL, R* aR) {
   R dm = mc_slope<R>(s[0], s[1], s[2]);
   R d0 = mc_slope<R>(s[1], s[2], s[3]);
   R dp = mc_slope<R>(s[2], s[3], s[4]);
-  R l = R(0.5) * (s[1] + s[2]) - (d0 - dm) / R(6);
-  R r = R(0.5) * (s[2] + s[3]) - (dp - d0) / R(6);
+  const R sixth = R(1.0 / 6.0);
+  R l = R(0.5) * (s[1] + s[2]) - (d0 - dm) * sixth;
+  R r = R(0.5) * (s[2] + s[3]) - (dp - d0) * sixth;
   R q = s[2];
   l = (R(1) - chi) * l + chi * q;
   r = (R(1) - chi) * r + chi * q;
@@ -251,16 +252,84 @@ __device__ __forceinline__ void ppm_cell(const R s[5], R chi, R* aL, R* aR) {
   *aR = r;
 }
 
+// ------------------------------------------------------- edge reconstruction
+// One thread per cell of the face range of direction d (cells -1..n_d along d,
+// transverse range widened by one layer): the cell's PPM parabola (or MC
+// slope) for all 12 primitives, flattened by the cell's GAS or RAD
+// flattener, stored as the two edge values E[0][q] (lower) and E[1][q]
+// (upper).  Every parabola is built once per direction; the face kernel reads
+// the upper edge of cell f-1 and the lower edge of cell f.  In r and phi on
+// the Kerr-Schild grid the velocity and field components are reconstructed
+// as sqrt(-g) times the primitive (Sec. 4.3).
+template <int MET, typename R, int d>
+__global__ void __launch_bounds__(256) k_edges(DevParams p, const double* __restrict__ P,
+                                               const R* __restrict__ aux, const R* __restrict__ flat,
+                                               R* __restrict__ E) {
+  int len[3], off[3];
+  for (int e = 0; e < 3; ++e) {
+    if (p.n[e] > 1) {
+      len[e] = p.n[e] + 2;
+      off[e] = -1;
+    } else {
+      len[e] = 1;
+      off[e] = 0;
+    }
+  }
+  long long total = (long long)len[0] * len[1] * len[2];
+  const long long st = p.str[d];
+  const bool weighted = (MET == KS) && (d != 1);
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+       id += (long long)gridDim.x * blockDim.x) {
+    long long r = id;
+    int i = (int)(r % len[0]) + off[0];
+    r /= len[0];
+    int j = (int)(r % len[1]) + off[1];
+    int k = (int)(r / len[1]) + off[2];
+    long long t = cell_index(p, i, j, k);
+    R chg = R(0), chr = R(0);
+    if (p.recon == 0) {
+      chg = flat[t];
+      chr = flat[p.ntot + t];
+    }
+    R gw[5];
+    if (weighted) {
+#pragma unroll
+      for (int m = 0; m < 5; ++m) gw[m] = aux[t + (m - 2) * st];
+    }
+#pragma unroll
+    for (int q = 0; q < NPR; ++q) {
+      const bool wq = weighted && ((q >= U1 && q <= B3) || q >= UR1);
+      R s[5];
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        R v = R(P[q * p.ntot + t + (m - 2) * st]);
+        s[m] = wq ? gw[m] * v : v;
+      }
+      R aL, aR;
+      if (p.recon == 0) {
+        ppm_cell<R>(s, q < ER ? chg : chr, &aL, &aR);
+      } else {
+        R dq = mc_slope<R>(s[1], s[2], s[3]);
+        aL = s[2] - R(0.5) * dq;
+        aR = s[2] + R(0.5) * dq;
+      }
+      E[q * p.ntot + t] = aL;
+      E[(NPR + q) * p.ntot + t] = aR;
+    }
+  }
+}
+
 // ----------------------------------------------------------------- fluxes
 // One thread per face of direction d (faces 0..n_d, transverse range widened
-// by one layer for the EMF averages).  Loads the 6-cell stencil of each
-// primitive, reconstructs both states, evaluates the metric at the face in
-// registers, forms U, F and wave speeds of both states and the HLL or LAXF
-// flux (Eqs. hll, lax), gas and radiation groups with their own speeds.
-template <int MET, typename R>
-__global__ void __launch_bounds__(128) k_face(DevParams p, const double* __restrict__ P,
-                                              const R* __restrict__ aux, const R* __restrict__ flat,
-                                              R* __restrict__ F, R* __restrict__ spd, int d) {
+// by one layer for the EMF averages).  Reads the two reconstructed states
+// (upper edge of cell f-1, lower edge of cell f), evaluates the metric at the
+// face in registers, the gas and radiation signal speeds of both states and
+// the HLL or LAXF flux (Eqs. hll, lax), gas and radiation groups with their own
+// speeds.  The direction is a template parameter so that every index into a
+// 4-vector or the primitive array is resolved at compile time.
+template <int MET, typename R, int d>
+__global__ void __launch_bounds__(128) k_face(DevParams p, const R* __restrict__ E,
+                                              R* __restrict__ F, R* __restrict__ spd) {
   int len[3], off[3];
   for (int e = 0; e < 3; ++e) {
     if (e == d) {
@@ -296,66 +365,62 @@ __global__ void __launch_bounds__(128) k_face(DevParams p, const double* __restr
     R xf[3];
     for (int e = 0; e < 3; ++e) xf[e] = R(p.x0[e] + (ii[e] + (e == d ? 0.0 : 0.5)) * p.dx[e]);
     Geo<MET, R> g = make_geo<MET, R>(p, xf[0], xf[1]);
-    R chiLg = R(0), chiLr = R(0), chiRg = R(0), chiRr = R(0);
-    if (p.recon == 0) {
-      chiLg = flat[t - st];
-      chiLr = flat[p.ntot + t - st];
-      chiRg = flat[t];
-      chiRr = flat[p.ntot + t];
-    }
-    R gw[6];
-    if (weighted) {
-#pragma unroll
-      for (int m = 0; m < 6; ++m) gw[m] = aux[t + (m - 3) * st];
-    }
     const R igf = weighted ? R(1) / g.gdet : R(1);
     R PL[NPR], PR[NPR];
 #pragma unroll
     for (int q = 0; q < NPR; ++q) {
       const bool wq = weighted && ((q >= U1 && q <= B3) || q >= UR1);
-      R s[6];
-#pragma unroll
-      for (int m = 0; m < 6; ++m) {
-        R v = R(P[q * p.ntot + t + (m - 3) * st]);
-        s[m] = wq ? gw[m] * v : v;
-      }
-      R aL, aR, bL, bR;
-      if (p.recon == 0) {
-        ppm_cell<R>(s, q < ER ? chiLg : chiLr, &aL, &aR);      // cell f-1: s[0..4]
-        ppm_cell<R>(s + 1, q < ER ? chiRg : chiRr, &bL, &bR);  // cell f:   s[1..5]
-      } else {
-        R dl = mc_slope<R>(s[1], s[2], s[3]);
-        R dr = mc_slope<R>(s[2], s[3], s[4]);
-        aR = s[2] + R(0.5) * dl;
-        bL = s[3] - R(0.5) * dr;
-        (void)aL;
-        (void)bR;
-      }
+      R aR = E[(NPR + q) * p.ntot + t - st];  // upper edge of cell f-1
+      R bL = E[q * p.ntot + t];               // lower edge of cell f
       PL[q] = wq ? aR * igf : aR;
       PR[q] = wq ? bL * igf : bL;
     }
-    R UL[NPR], FL[NPR], sL[4], UR_[NPR], FR[NPR], sR[4];
-    face_state<MET, R>(p, g, d + 1, PL, UL, FL, sL);
-    face_state<MET, R>(p, g, d + 1, PR, UR_, FR, sR);
+    R sL[4], sR[4];
+    face_speeds<MET, R>(p, g, d + 1, PL, sL);
+    face_speeds<MET, R>(p, g, d + 1, PR, sR);
     R cmaxg = fmax(R(0), fmax(sL[1], sR[1]));
     R cming = -fmin(R(0), fmin(sL[0], sR[0]));
     R cmaxr = fmax(R(0), fmax(sL[3], sR[3]));
     R cminr = -fmin(R(0), fmin(sL[2], sR[2]));
-#pragma unroll
-    for (int q = 0; q < NPR; ++q) {
-      R cmx = q < ER ? cmaxg : cmaxr, cmn = q < ER ? cming : cminr;
-      R fl;
-      if (p.flux == 0) {
-        R ctop = cmx > cmn ? cmx : cmn;
-        fl = R(0.5) * (FL[q] + FR[q] - ctop * (UR_[q] - UL[q]));
-      } else if (cmx + cmn > R(0)) {
-        fl = (cmn * FR[q] + cmx * FL[q] - cmn * cmx * (UR_[q] - UL[q])) / (cmn + cmx);
+    // weights of (F_L, U_L) and (F_R, U_R) in the flux, gas and radiation groups
+    R fLg, uLg, fRg, uRg, fLr, uLr, fRr, uRr;
+    if (p.flux == 0) {  // LAXF: 1/2 (F_L + F_R - c (U_R - U_L))
+      R cg = cmaxg > cming ? cmaxg : cming, cr = cmaxr > cminr ? cmaxr : cminr;
+      fLg = fRg = fLr = fRr = R(0.5);
+      uLg = R(0.5) * cg;
+      uRg = -uLg;
+      uLr = R(0.5) * cr;
+      uRr = -uLr;
+    } else {  // HLL: (c- F_R + c+ F_L - c- c+ (U_R - U_L)) / (c- + c+)
+      R sg = cmaxg + cming, sr = cmaxr + cminr;
+      if (sg > R(0)) {
+        R isg = R(1) / sg;
+        fLg = cmaxg * isg;
+        fRg = cming * isg;
+        uLg = cming * cmaxg * isg;
+        uRg = -uLg;
       } else {
-        fl = R(0.5) * (FL[q] + FR[q]);
+        fLg = fRg = R(0.5);
+        uLg = uRg = R(0);
       }
-      if (q == B1 + d) fl = R(0);
-      F[q * p.ntot + t] = fl;
+      if (sr > R(0)) {
+        R isr = R(1) / sr;
+        fLr = cmaxr * isr;
+        fRr = cminr * isr;
+        uLr = cminr * cmaxr * isr;
+        uRr = -uLr;
+      } else {
+        fLr = fRr = R(0.5);
+        uLr = uRr = R(0);
+      }
     }
+    R out[NPR];
+#pragma unroll
+    for (int q = 0; q < NPR; ++q) out[q] = R(0);
+    face_accum<MET, R>(p, g, d + 1, PL, fLg, uLg, fLr, uLr, out);
+    face_accum<MET, R>(p, g, d + 1, PR, fRg, uRg, fRr, uRr, out);
+#pragma unroll
+    for (int q = 0; q < NPR; ++q) F[q * p.ntot + t] = (q == B1 + d) ? R(0) : out[q];
     spd[t] = fmax(fmax(cmaxg, cming), fmax(cmaxr, cminr));
   }
 }

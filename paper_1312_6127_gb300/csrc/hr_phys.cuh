@@ -42,7 +42,7 @@ template <int MET, typename R>
 struct Geo {
   R g00, g01, g03, g11, g13, g22, g33;  // covariant, nonzero pattern of KS
   R G00, G01, G11, G13, G22, G33;       // contravariant
-  R gdet, alpha;
+  R gdet, alpha, ialpha;
 
   __device__ __forceinline__ void lower(const R v[4], R w[4]) const {
     if constexpr (MET == MINK) {
@@ -99,7 +99,7 @@ struct Geo {
 };
 
 template <typename R> __device__ __forceinline__ R rsqrt_(R x);
-template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return 1.0 / sqrt(x); }
+template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return rsqrt(x); }
 template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
 
 // Kerr-Schild metric in the internal chart at (x1, x2): covariant components
@@ -115,6 +115,7 @@ __device__ __forceinline__ Geo<MET, R> make_geo(const DevParams& p, R x1, R x2) 
     g.G00 = R(-1); g.G01 = R(0); g.G11 = R(1); g.G13 = R(0); g.G22 = R(1); g.G33 = R(1);
     g.gdet = R(1);
     g.alpha = R(1);
+    g.ialpha = R(1);
     (void)x1; (void)x2; (void)p;
   } else {
     const R a = R(p.a), hh = R(p.h);
@@ -140,14 +141,16 @@ __device__ __forceinline__ Geo<MET, R> make_geo(const DevParams& p, R x1, R x2) 
     g.g22 = S * J2 * J2;
     g.g33 = s2 * (S + a * a * s2 * (R(1) + tr)) * J3 * J3;
     R D = r * r - R(2) * r + a * a;
+    const R iJ1 = R(1) / J1, iJ2 = R(1) / J2, iJ3 = R(1.0 / (2.0 * 3.14159265358979323846));
     g.G00 = -(R(1) + tr);
-    g.G01 = tr / J1;
-    g.G11 = D * iS / (J1 * J1);
-    g.G13 = a * iS / (J1 * J3);
-    g.G22 = iS / (J2 * J2);
-    g.G33 = iS / (s2 * J3 * J3);
+    g.G01 = tr * iJ1;
+    g.G11 = D * iS * iJ1 * iJ1;
+    g.G13 = a * iS * iJ1 * iJ3;
+    g.G22 = iS * iJ2 * iJ2;
+    g.G33 = iS * iJ3 * iJ3 / s2;
     g.gdet = S * fabs(sth) * J1 * J2 * J3;
     g.alpha = rsqrt_<R>(R(1) + tr);
+    g.ialpha = (R(1) + tr) * g.alpha;
   }
   return g;
 }
@@ -165,7 +168,7 @@ __device__ __forceinline__ void fourvel(const Geo<MET, R>& g, R q1, R q2, R q3, 
     ucon[2] = q2;
     ucon[3] = q3;
   } else {
-    ucon[0] = gm / g.alpha;
+    ucon[0] = gm * g.ialpha;
     ucon[1] = q1 - gm * g.alpha * g.G01;
     ucon[2] = q2;
     ucon[3] = q3;
@@ -175,10 +178,9 @@ __device__ __forceinline__ void fourvel(const Geo<MET, R>& g, R q1, R q2, R q3, 
 
 // b^t = B^i u_i, b^i = (B^i + b^t u^i)/u^t, b^2 = b^mu b_mu.
 template <int MET, typename R>
-__device__ __forceinline__ void bvec(const Geo<MET, R>& g, const R ucon[4], const R ucov[4], R Bx,
-                                     R By, R Bz, R bcon[4], R bcov[4], R* bsq) {
+__device__ __forceinline__ void bvec_iut(const Geo<MET, R>& g, const R ucon[4], const R ucov[4],
+                                         R iut, R Bx, R By, R Bz, R bcon[4], R bcov[4], R* bsq) {
   R bt = Bx * ucov[1] + By * ucov[2] + Bz * ucov[3];
-  R iut = R(1) / ucon[0];
   bcon[0] = bt;
   bcon[1] = (Bx + bt * ucon[1]) * iut;
   bcon[2] = (By + bt * ucon[2]) * iut;
@@ -187,18 +189,34 @@ __device__ __forceinline__ void bvec(const Geo<MET, R>& g, const R ucon[4], cons
   *bsq = bcon[0] * bcov[0] + bcon[1] * bcov[1] + bcon[2] * bcov[2] + bcon[3] * bcov[3];
 }
 
+template <int MET, typename R>
+__device__ __forceinline__ void bvec(const Geo<MET, R>& g, const R ucon[4], const R ucov[4], R Bx,
+                                     R By, R Bz, R bcon[4], R bcov[4], R* bsq) {
+  bvec_iut<MET, R>(g, ucon, ucov, R(1) / ucon[0], Bx, By, Bz, bcon, bcov, bsq);
+}
+
+// Opacities per length at density rho and gas temperature T.
 template <typename R>
-__device__ __forceinline__ void opacity(const DevParams& p, R rho, R ug, R* kabs, R* ksca) {
-  R T = R(p.gam - 1.0) * ug / rho;
+__device__ __forceinline__ void opacity_T(const DevParams& p, R rho, R T, R* kabs, R* ksca) {
   if (p.opacity == 1) {
     R Tc = T > R(p.Tmin) ? T : R(p.Tmin);
-    // T^-3.5 = 1 / (T^3 sqrt(T))
-    R t35 = R(1) / (Tc * Tc * Tc * sqrt(Tc));
+    R T2 = Tc * Tc;
+    R t35;
+    if constexpr (sizeof(R) == 8) {
+      t35 = rsqrt_<R>(T2 * T2 * T2 * Tc);  // T^-3.5 = 1/sqrt(T^7): one reciprocal square root
+    } else {
+      t35 = rsqrt_<R>(Tc) / (T2 * Tc);  // T^7 would underflow in FP32
+    }
     *kabs = R(p.kscale * p.kabs0) * rho * rho * t35;
   } else {
     *kabs = R(p.kscale * p.kabs0) * rho;
   }
   *ksca = R(p.kscale * p.kes0) * rho;
+}
+
+template <typename R>
+__device__ __forceinline__ void opacity(const DevParams& p, R rho, R ug, R* kabs, R* ksca) {
+  opacity_T<R>(p, rho, R(p.gam - 1.0) * ug / rho, kabs, ksca);
 }
 
 // ------------------------------------------------------- face state physics
@@ -284,6 +302,75 @@ __device__ __forceinline__ void face_state(const DevParams& p, const Geo<MET, R>
   char_speeds<MET, R>(g, urc, cr2, d, &sp[2], &sp[3]);
 }
 
+// Gas and radiation signal speeds (vmin, vmax) of one reconstructed state.
+template <int MET, typename R>
+__device__ __forceinline__ void face_speeds(const DevParams& p, const Geo<MET, R>& g, int d,
+                                            const R P[NPR], R sp[4]) {
+  R ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq;
+  fourvel<MET, R>(g, P[U1], P[U2], P[U3], ucon, ucov, &gm);
+  bvec<MET, R>(g, ucon, ucov, P[B1], P[B2], P[B3], bcon, bcov, &bsq);
+  const R rho = P[RHO], ug = P[UU];
+  const R pg = R(p.gam - 1.0) * ug;
+  const R w = rho + ug + pg;
+  R cs2 = R(p.gam) * pg / w;
+  R va2 = bsq / (w + bsq);
+  R cms2 = cs2 + va2 - cs2 * va2;
+  cms2 = cms2 > R(1) ? R(1) : (cms2 < R(0) ? R(0) : cms2);
+  char_speeds<MET, R>(g, ucon, cms2, d, &sp[0], &sp[1]);
+  R urc[4], urv[4], gr;
+  fourvel<MET, R>(g, P[UR1], P[UR2], P[UR3], urc, urv, &gr);
+  R kabs, ksca;
+  opacity<R>(p, rho, ug, &kabs, &ksca);
+  R tau = (kabs + ksca) * sqrt(g.gdd(d)) * R(p.dx[d - 1]);
+  R cr2 = R(1.0 / 3.0);
+  if (tau > R(0)) {
+    R lim = R(4.0 / 3.0) / tau;
+    lim = lim * lim;
+    cr2 = lim < cr2 ? lim : cr2;
+  }
+  char_speeds<MET, R>(g, urc, cr2, d, &sp[2], &sp[3]);
+}
+
+// out[q] += aF_q F_q + aU_q U_q for one reconstructed state, with (aF, aU)
+// taking the gas values for q < 8 and the radiation values for q >= 8.  HLL
+// and LAXF are linear in (F_L, U_L, F_R, U_R), so each state adds its own
+// share and the two states' U and F never need to be held together.
+template <int MET, typename R>
+__device__ __forceinline__ void face_accum(const DevParams& p, const Geo<MET, R>& g, int d,
+                                           const R P[NPR], R aFg, R aUg, R aFr, R aUr, R out[NPR]) {
+  R ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq;
+  fourvel<MET, R>(g, P[U1], P[U2], P[U3], ucon, ucov, &gm);
+  const R iut = g.alpha / gm;
+  bvec_iut<MET, R>(g, ucon, ucov, iut, P[B1], P[B2], P[B3], bcon, bcov, &bsq);
+  const R rho = P[RHO], ug = P[UU];
+  const R pg = R(p.gam - 1.0) * ug;
+  const R wb = rho + ug + pg + bsq, pt = pg + R(0.5) * bsq;
+  const R gd = g.gdet;
+  const R mt = rho * ucon[0], md = rho * ucon[d];
+  out[0] += gd * (aFg * md + aUg * mt);
+  out[1] += gd * (aFg * (wb * ucon[d] * ucov[0] - bcon[d] * bcov[0] + md) +
+                  aUg * (wb * ucon[0] * ucov[0] + pt - bcon[0] * bcov[0] + mt));
+#pragma unroll
+  for (int i = 1; i <= 3; ++i)
+    out[1 + i] += gd * (aFg * (wb * ucon[d] * ucov[i] + (i == d ? pt : R(0)) - bcon[d] * bcov[i]) +
+                        aUg * (wb * ucon[0] * ucov[i] - bcon[0] * bcov[i]));
+  const R vd = ucon[d] * iut;
+  const R Bd = P[B1 + d - 1];
+#pragma unroll
+  for (int i = 1; i <= 3; ++i) {
+    R f = (i == d) ? R(0) : (P[B1 + i - 1] * vd - Bd * ucon[i] * iut);
+    out[4 + i] += gd * (aFg * f + aUg * P[B1 + i - 1]);
+  }
+  R urc[4], urv[4], gr;
+  fourvel<MET, R>(g, P[UR1], P[UR2], P[UR3], urc, urv, &gr);
+  const R E = P[ER];
+  const R e43 = R(4.0 / 3.0) * E, e13 = E * R(1.0 / 3.0);
+#pragma unroll
+  for (int n = 0; n < 4; ++n)
+    out[8 + n] += gd * (aFr * (e43 * urc[d] * urv[n] + (n == d ? e13 : R(0))) +
+                        aUr * (e43 * urc[0] * urv[n] + (n == 0 ? e13 : R(0))));
+}
+
 // ------------------------------------------------------ M1 inversion (FP64)
 // Closed form in the ZAMO frame (Sec. 4.6): E_rad = alpha^2 R^{tt},
 // U~^i = alpha g^{i mu} R^t_mu + E_rad alpha g^{ti}, y = U~^2/E_rad^2,
@@ -331,10 +418,13 @@ __device__ __forceinline__ int rad_invert(const DevParams& p, const Geo<MET, dou
     }
     if (y < 0.0) y = 0.0;
   }
-  double gam2 = (2.0 - y + sqrt(4.0 - 3.0 * y)) / (4.0 * (1.0 - y));
-  double prad = Erad / (4.0 * gam2 - 1.0);
-  out[0] = 3.0 * prad;
-  double f = sqrt(gam2) / (4.0 * prad * gam2);
+  // With s = sqrt(4 - 3y), Eq. gammarvsy gives gamma^2 = (s+2)/(4(s-1)) and
+  // 4 gamma^2 - 1 = 3/(s-1), so Ebar = 3 p_rad = E_rad (s-1) and
+  // u~^i = gamma U~^i/(4 p_rad gamma^2) = 3 U~^i / (2 E_rad sqrt((s+2)(s-1))).
+  const double sq = sqrt(4.0 - 3.0 * y);
+  const double sm1 = sq - 1.0;
+  out[0] = Erad * sm1;
+  double f = 1.5 / Erad * rsqrt((sq + 2.0) * sm1);
   out[1] = f * Ut[0];
   out[2] = f * Ut[1];
   out[3] = f * Ut[2];

@@ -63,12 +63,33 @@ int faces_impl(harmrad_ctx* c, bool fresh) {
   }
   for (int d = 0; d < 3; ++d) {
     if (p.n[d] == 1) continue;
-    long long work = 1;
-    for (int e = 0; e < 3; ++e) work *= (e == d) ? p.n[e] + 1 : (p.n[e] > 1 ? p.n[e] + 2 : 1);
-    k_face<MET, R><<<grid_for(work, c->sms, 128), 128, 0, st>>>(p, c->P, (const R*)c->aux, (const R*)c->flat[d],
-                                                               (R*)c->F[d], (R*)c->spd[d], d);
+    long long wc = 1, work = 1;
+    for (int e = 0; e < 3; ++e) {
+      wc *= p.n[e] > 1 ? p.n[e] + 2 : 1;
+      work *= (e == d) ? p.n[e] + 1 : (p.n[e] > 1 ? p.n[e] + 2 : 1);
+    }
+    const int ge = grid_for(wc, c->sms, 256);
+    const int g = grid_for(work, c->sms, 128);
+    const R* aux = (const R*)c->aux;
+    const R* fl = (const R*)c->flat[d];
+    R* Ed = (R*)c->edges;
+    R* Fd = (R*)c->F[d];
+    R* sd = (R*)c->spd[d];
+    if (d == 0) {
+      k_edges<MET, R, 0><<<ge, 256, 0, st>>>(p, c->P, aux, fl, Ed);
+      mark(c, HARMRAD_K_FACE);
+      k_face<MET, R, 0><<<g, 128, 0, st>>>(p, Ed, Fd, sd);
+    } else if (d == 1) {
+      k_edges<MET, R, 1><<<ge, 256, 0, st>>>(p, c->P, aux, fl, Ed);
+      mark(c, HARMRAD_K_FACE);
+      k_face<MET, R, 1><<<g, 128, 0, st>>>(p, Ed, Fd, sd);
+    } else {
+      k_edges<MET, R, 2><<<ge, 256, 0, st>>>(p, c->P, aux, fl, Ed);
+      mark(c, HARMRAD_K_FACE);
+      k_face<MET, R, 2><<<g, 128, 0, st>>>(p, Ed, Fd, sd);
+    }
     mark(c, HARMRAD_K_FACE);
-    ++nk;
+    nk += 2;
   }
   for (int a = 0; a < 3; ++a)
     for (int b = a + 1; b < 3; ++b) {
