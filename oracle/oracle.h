@@ -119,6 +119,13 @@ void   orc_implicit_zone(const orc_params* p, const double* x, const double* Ust
 void   orc_pmhd_residual(const orc_params* p, const double* x, const double* Ustar,
                          double h, const double* xg, double* E4, double* eT,
                          double* eI);
+/* Face flux of direction d (1..3) from an 8-cell stencil S[8][12] of active or
+ * ghost primitives along d (cells f-4 .. f+3 around the face f), with the
+ * stencil cells' internal coordinates xc[8][3] and the face centre xf[3];
+ * fresh flattener (first sub-step), no flux-CT.  Writes F[12] and the face's
+ * max signal speed.  Test hook for sampled faces of large grids. */
+void   orc_face_flux_stencil(const orc_params* p, int d, const double* S, const double* xc,
+                             const double* xf, double* F, double* speed);
 /* Levermore Eddington factor xi(f) (Sec. 3.1). */
 double orc_levermore_xi(double f);
 

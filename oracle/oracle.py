@@ -116,6 +116,7 @@ def lib():
         L.orc_gas_invert.argtypes = [pp, dp, dp, dp, ctypes.c_double, dp]
         L.orc_implicit_zone.argtypes = [pp, dp, dp, dp, ctypes.c_double, dp, ctypes.POINTER(OrcInfo)]
         L.orc_pmhd_residual.argtypes = [pp, dp, dp, ctypes.c_double, dp, dp, dp, dp]
+        L.orc_face_flux_stencil.argtypes = [pp, ctypes.c_int, dp, dp, dp, dp, dp]
         L.orc_levermore_xi.restype = ctypes.c_double
         L.orc_levermore_xi.argtypes = [ctypes.c_double]
     return _lib
@@ -292,6 +293,15 @@ def pmhd_residual(p, x, Ustar, h, xg):
     lib().orc_pmhd_residual(ctypes.byref(p), _dp(x), _dp(Ustar), float(h), _dp(xg), _dp(E),
                             ctypes.byref(eT), ctypes.byref(eI))
     return E, eT.value, eI.value
+
+
+def face_flux_stencil(p, d, S, xc, xf):
+    """Flux of one face of direction d from its 8-cell stencil S[8][12]."""
+    S, xc, xf = _vec(S), _vec(xc), _vec(xf)
+    F = np.empty(NP)
+    sp = ctypes.c_double()
+    lib().orc_face_flux_stencil(ctypes.byref(p), int(d), _dp(S), _dp(xc), _dp(xf), _dp(F), ctypes.byref(sp))
+    return F, sp.value
 
 
 def levermore_xi(f):

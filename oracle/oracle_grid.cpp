@@ -176,9 +176,91 @@ void flattener(const FlatIn* c, int m, double* fg, double* fr) {
   *fr = (1.0 - wg) * r + wg * mx;
 }
 
-bool weighted_var(const Ctx& c, int d, int q) {
-  if (c.p.metric != 1 || d == 1) return false;
-  return (q >= U1 && q <= B3) || (q >= UR1 && q <= UR3);
+
+// Flux through one face of direction d (0-based) from its 8-cell stencil
+// s[m] (cells f-4 .. f+3) with the stencil cells' geometry geo[m]; fg/fr
+// return the flattener of the left (m = 3) and right (m = 4) cells.  When
+// stored != nullptr the flattener is max-ed with (and written back to) the
+// values of earlier sub-steps: stored[side][gas/rad].
+void face_flux(const orc_params& p, int d, const double P8[8][NP], const Geom* geo[8], const Geom& Gf,
+               double* stored[2][2], double F[NP], double* speed) {
+  const bool wvar = p.metric == 1 && d != 1;
+  auto weighted = [&](int q) { return wvar && ((q >= U1 && q <= B3) || (q >= UR1 && q <= UR3)); };
+  double s[8][NP];
+  FlatIn fin[8];
+  for (int m = 0; m < 8; ++m) {
+    const Geom& G = *geo[m];
+    const double* Pm = P8[m];
+    for (int q = 0; q < NP; ++q) s[m][q] = weighted(q) ? G.gdet * Pm[q] : Pm[q];
+    double ut[3] = {Pm[U1], Pm[U2], Pm[U3]}, ur[3] = {Pm[UR1], Pm[UR2], Pm[UR3]};
+    FourVel u, v;
+    fourvel(G, ut, u);
+    fourvel(G, ur, v);
+    fin[m].pg = (p.gam - 1.0) * Pm[UU];
+    fin[m].pr = Pm[ER] / 3.0;
+    fin[m].vg = G.gdet * u.ucon[d + 1];
+    fin[m].vr = G.gdet * v.ucon[d + 1];
+    double ka, ks;
+    opacity(p, Pm[RHO], Pm[UU], &ka, &ks);
+    double tau = (ka + ks) * std::sqrt(G.gcov[d + 1][d + 1]) * p.dx[d];
+    fin[m].w = std::min(1.0, 2.0 * tau);
+  }
+  double PL[NP], PR[NP];
+  for (int side = 0; side < 2; ++side) {
+    int m = side == 0 ? 3 : 4;  // cell f-1 (left state) or f (right state)
+    double fg = 0.0, fr = 0.0;
+    if (p.recon == 0) {
+      flattener(fin, m, &fg, &fr);
+      if (stored) {
+        double& sg = *stored[side][0];
+        double& sr = *stored[side][1];
+        fg = std::max(fg, sg);
+        fr = std::max(fr, sr);
+        sg = fg;
+        sr = fr;
+      }
+    }
+    for (int q = 0; q < NP; ++q) {
+      double aL, aR;
+      if (p.recon == 0) {
+        double st[5] = {s[m - 2][q], s[m - 1][q], s[m][q], s[m + 1][q], s[m + 2][q]};
+        ppm_cell(st, q < ER ? fg : fr, &aL, &aR);
+      } else {
+        double dq = mc_slope(s[m - 1][q], s[m][q], s[m + 1][q]);
+        aL = s[m][q] - 0.5 * dq;
+        aR = s[m][q] + 0.5 * dq;
+      }
+      if (side == 0) PL[q] = aR;
+      else PR[q] = aL;
+    }
+  }
+  for (int q = 0; q < NP; ++q)
+    if (weighted(q)) {
+      PL[q] /= Gf.gdet;
+      PR[q] /= Gf.gdet;
+    }
+  double UL[NP], UR[NP], FL[NP], FR[NP], sL[4], sR[4];
+  face_state(p, Gf, d + 1, PL, UL, FL, sL);
+  face_state(p, Gf, d + 1, PR, UR, FR, sR);
+  double cmaxg = std::max(0.0, std::max(sL[1], sR[1]));
+  double cming = -std::min(0.0, std::min(sL[0], sR[0]));
+  double cmaxr = std::max(0.0, std::max(sL[3], sR[3]));
+  double cminr = -std::min(0.0, std::min(sL[2], sR[2]));
+  for (int q = 0; q < NP; ++q) {
+    double cmx = q < ER ? cmaxg : cmaxr, cmn = q < ER ? cming : cminr;
+    double fl;
+    if (p.flux == 0) {
+      double ctop = std::max(cmx, cmn);
+      fl = 0.5 * (FL[q] + FR[q] - ctop * (UR[q] - UL[q]));
+    } else {
+      if (cmx + cmn > 0.0)
+        fl = (cmn * FR[q] + cmx * FL[q] - cmn * cmx * (UR[q] - UL[q])) / (cmn + cmx);
+      else
+        fl = 0.5 * (FL[q] + FR[q]);
+    }
+    F[q] = fl;
+  }
+  *speed = std::max(std::max(cmaxg, cming), std::max(cmaxr, cminr));
 }
 
 // Face fluxes along direction d (0-based) for every face that the update or
@@ -214,89 +296,23 @@ void compute_fluxes(Ctx& c, int d, bool use_stored) {
         if (p.metric == 1 && d == 1 &&
             ((f == 0 && p.bc[2] == 2) || (f == c.n[1] && p.bc[3] == 2)))
           continue;
-        // stencil of 8 cells: f-4 .. f+3 along d
-        double s[8][NP];
-        FlatIn fin[8];
+        double P8[8][NP];
+        const Geom* geo[8];
         for (int m = 0; m < 8; ++m) {
           long cm = t + (long)(m - 4) * str;
-          const Geom& G = c.geo[cm];
-          double Pm[NP];
-          for (int q = 0; q < NP; ++q) Pm[q] = c.P[(long)q * c.ntot + cm];
-          for (int q = 0; q < NP; ++q) s[m][q] = weighted_var(c, d, q) ? G.gdet * Pm[q] : Pm[q];
-          double ut[3] = {Pm[U1], Pm[U2], Pm[U3]}, ur[3] = {Pm[UR1], Pm[UR2], Pm[UR3]};
-          FourVel u, v;
-          fourvel(G, ut, u);
-          fourvel(G, ur, v);
-          fin[m].pg = (p.gam - 1.0) * Pm[UU];
-          fin[m].pr = Pm[ER] / 3.0;
-          fin[m].vg = G.gdet * u.ucon[d + 1];
-          fin[m].vr = G.gdet * v.ucon[d + 1];
-          double ka, ks;
-          opacity(p, Pm[RHO], Pm[UU], &ka, &ks);
-          double tau = (ka + ks) * std::sqrt(G.gcov[d + 1][d + 1]) * p.dx[d];
-          fin[m].w = std::min(1.0, 2.0 * tau);
-        }
-        double PL[NP], PR[NP];
-        for (int side = 0; side < 2; ++side) {
-          int m = side == 0 ? 3 : 4;  // cell f-1 (left state) or f (right state)
-          double fg = 0.0, fr = 0.0;
-          if (p.recon == 0) {
-            flattener(fin, m, &fg, &fr);
-            if (use_stored) {
-              long cm = t + (long)(m - 4) * str;
-              double& sg = c.flat[d][cm];
-              double& sr = c.flat[d][c.ntot + cm];
-              fg = std::max(fg, sg);
-              fr = std::max(fr, sr);
-              sg = fg;
-              sr = fr;
-            }
-          }
-          for (int q = 0; q < NP; ++q) {
-            double aL, aR;
-            if (p.recon == 0) {
-              double st[5] = {s[m - 2][q], s[m - 1][q], s[m][q], s[m + 1][q], s[m + 2][q]};
-              ppm_cell(st, q < ER ? fg : fr, &aL, &aR);
-            } else {
-              double dq = mc_slope(s[m - 1][q], s[m][q], s[m + 1][q]);
-              aL = s[m][q] - 0.5 * dq;
-              aR = s[m][q] + 0.5 * dq;
-            }
-            if (side == 0) PL[q] = aR;
-            else PR[q] = aL;
-          }
+          geo[m] = &c.geo[cm];
+          for (int q = 0; q < NP; ++q) P8[m][q] = c.P[(long)q * c.ntot + cm];
         }
         double x[3] = {xc(c, 0, i), xc(c, 1, j), xc(c, 2, k)};
         x[d] = xf(c, d, f);
         Geom G;
         geom_at(p, x[0], x[1], x[2], G);
-        for (int q = 0; q < NP; ++q)
-          if (weighted_var(c, d, q)) {
-            PL[q] /= G.gdet;
-            PR[q] /= G.gdet;
-          }
-        double UL[NP], UR[NP], FL[NP], FR[NP], sL[4], sR[4];
-        face_state(p, G, d + 1, PL, UL, FL, sL);
-        face_state(p, G, d + 1, PR, UR, FR, sR);
-        double cmaxg = std::max(0.0, std::max(sL[1], sR[1]));
-        double cming = -std::min(0.0, std::min(sL[0], sR[0]));
-        double cmaxr = std::max(0.0, std::max(sL[3], sR[3]));
-        double cminr = -std::min(0.0, std::min(sL[2], sR[2]));
-        for (int q = 0; q < NP; ++q) {
-          double cmx = q < ER ? cmaxg : cmaxr, cmn = q < ER ? cming : cminr;
-          double fl;
-          if (p.flux == 0) {
-            double ctop = std::max(cmx, cmn);
-            fl = 0.5 * (FL[q] + FR[q] - ctop * (UR[q] - UL[q]));
-          } else {
-            if (cmx + cmn > 0.0)
-              fl = (cmn * FR[q] + cmx * FL[q] - cmn * cmx * (UR[q] - UL[q])) / (cmn + cmx);
-            else
-              fl = 0.5 * (FL[q] + FR[q]);
-          }
-          F[(long)q * c.ntot + t] = fl;
-        }
-        c.spd[d][t] = std::max(std::max(cmaxg, cming), std::max(cmaxr, cminr));
+        double* st[2][2] = {{&c.flat[d][t - str], &c.flat[d][c.ntot + t - str]},
+                            {&c.flat[d][t], &c.flat[d][c.ntot + t]}};
+        double Fq[NP], sp;
+        face_flux(p, d, P8, geo, G, use_stored ? st : nullptr, Fq, &sp);
+        for (int q = 0; q < NP; ++q) F[(long)q * c.ntot + t] = Fq[q];
+        c.spd[d][t] = sp;
       }
 }
 
@@ -699,6 +715,21 @@ void orc_pmhd_residual(const orc_params* p, const double* x, const double* Ustar
   Geom G;
   geom_at(*p, x[1], x[2], x[3], G);
   pmhd_residual_public(*p, G, Ustar, h, xg, E4, eT, eI);
+}
+
+void orc_face_flux_stencil(const orc_params* p, int d, const double* S, const double* xc8,
+                           const double* xfc, double* F, double* speed) {
+  Geom G8[8];
+  const Geom* geo[8];
+  double P8[8][NP];
+  for (int m = 0; m < 8; ++m) {
+    geom_at(*p, xc8[3 * m], xc8[3 * m + 1], xc8[3 * m + 2], G8[m]);
+    geo[m] = &G8[m];
+    for (int q = 0; q < NP; ++q) P8[m][q] = S[NP * m + q];
+  }
+  Geom Gf;
+  geom_at(*p, xfc[0], xfc[1], xfc[2], Gf);
+  face_flux(*p, d - 1, P8, geo, Gf, nullptr, F, speed);
 }
 
 double orc_levermore_xi(double f) {

@@ -1,0 +1,179 @@
+"""The 256x128x64 Kerr-Schild torus (the benchmark's workload, same launch
+configuration): sampled face fluxes against the oracle one face at a time,
+and properties that hold at any size (constrained transport keeps the corner
+divergence of sqrt(-g) B, the CUDA-graph step equals the eagerly launched
+step bit for bit, split precision keeps the conserved totals of FP64).
+Also the split-precision error against the oracle on the 64x32x16 torus."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_1312_6127_gb300 import harmrad as H
+from paper_1312_6127_gb300 import workloads as W
+from tests.parity_metrics import GROUPS, zone_errors
+
+pytestmark = pytest.mark.gpu
+
+FULL = (256, 128, 64)
+
+
+@pytest.fixture(scope="module")
+def torus_full():
+    return W.torus(FULL, seed=12345)
+
+
+def test_sampled_face_fluxes_full_size(torus_full):
+    cfg, P = torus_full
+    g = H.Grid(cfg)
+    g.set_prims(P)
+    p = O.make_params(cfg)
+    rng = W.rng(77)
+    n = cfg["n"]
+    for d in (1, 2, 3):
+        Fg = g.fluxes(d)
+        # interior faces: the 8-cell stencil f-4..f+3 lies in the active grid
+        lo = [0, 0, 0]
+        hi = list(n)
+        lo[d - 1], hi[d - 1] = 4, n[d - 1] - 3
+        Fo, Fs = [], []
+        for _ in range(120):
+            ijk = [int(rng.integers(lo[e], hi[e])) for e in range(3)]
+            S = np.zeros((8, 12))
+            xc = np.zeros((8, 3))
+            for m in range(8):
+                c = list(ijk)
+                c[d - 1] += m - 4
+                S[m] = P[:, c[2], c[1], c[0]]
+                xc[m] = [cfg["x0"][e] + (c[e] + 0.5) * cfg["dx"][e] for e in range(3)]
+            xf = [cfg["x0"][e] + (ijk[e] + 0.5) * cfg["dx"][e] for e in range(3)]
+            xf[d - 1] = cfg["x0"][d - 1] + ijk[d - 1] * cfg["dx"][d - 1]
+            F, _ = O.face_flux_stencil(p, d, S, xc, xf)
+            Fo.append(F)
+            Fs.append(Fg[:, ijk[2], ijk[1], ijk[0]])
+        Fo, Fs = np.array(Fo).T, np.array(Fs).T
+        # induction fluxes are replaced by flux-CT in the library's output
+        for grp in (GROUPS[0], GROUPS[1], GROUPS[3]):
+            sc = max(np.abs(Fo[list(grp)]).max(), 1e-300)
+            for q in grp:
+                err = np.abs(Fs[q] - Fo[q]) / (np.abs(Fo[q]) + 1e-3 * sc)
+                assert err.max() < 1e-10, (d, q, err.max())
+
+
+def corner_div(cfg, Pd):
+    """Corner-centred divergence of sqrt(-g) B at interior corners (torch, GPU)."""
+    n1, n2, n3 = cfg["n"]
+    x = np.zeros((n2 * n1, 4))
+    jj, ii = np.meshgrid(np.arange(n2), np.arange(n1), indexing="ij")
+    x[:, 1] = cfg["x0"][0] + (ii.ravel() + 0.5) * cfg["dx"][0]
+    x[:, 2] = cfg["x0"][1] + (jj.ravel() + 0.5) * cfg["dx"][1]
+    Pz = np.zeros((n2 * n1, 12))
+    Pz[:, 0], Pz[:, 1], Pz[:, 8] = 1.0, 1.0, 1.0
+    Pz[:, 5] = 1.0  # B^1 = 1: U_5 = sqrt(-g)
+    U, _, _, _ = H.zone_physics(cfg, x, Pz)
+    gd = torch.as_tensor(U[:, 5].reshape(1, n2, n1), device="cuda")
+    dx = cfg["dx"]
+    div = 0.0
+    for c in range(3):
+        b = Pd[5 + c] * gd  # [k, j, i]
+        ax = 2 - c
+        t = b - torch.roll(b, 1, dims=ax)
+        for o in range(3):
+            if o != c:
+                t = t + torch.roll(t, 1, dims=2 - o)
+        div = div + t / (4.0 * dx[c])
+    scale = sum((Pd[5 + c] * gd).abs().max() / dx[c] for c in range(3))
+    return div[2:-2, 2:-2, 2:-2], float(scale)  # away from the grid edges
+
+
+def test_corner_divergence_preserved_full_size(torus_full):
+    cfg, P = torus_full
+    g = H.Grid(cfg)
+    g.set_prims(P)
+    d0, sc = corner_div(cfg, g.get_prims(device=True))
+    g.step(0.0)
+    g.step(0.0)
+    d1, _ = corner_div(cfg, g.get_prims(device=True))
+    assert float((d1 - d0).abs().max()) < 1e-12 * sc
+
+
+def test_graph_replay_equals_eager_full_size(torus_full):
+    cfg, P = torus_full
+    g1 = H.Grid(cfg)
+    g1.set_prims(P)
+    g1.step(0.0)
+    g1.step(0.0)
+    A = g1.get_prims(device=True)
+    del g1
+    os.environ["HARMRAD_NO_GRAPH"] = "1"
+    try:
+        g2 = H.Grid(cfg)
+    finally:
+        del os.environ["HARMRAD_NO_GRAPH"]
+    g2.set_prims(P)
+    g2.step(0.0)
+    g2.step(0.0)
+    assert g2.stats()["graph"] == 0
+    B = g2.get_prims(device=True)
+    assert torch.equal(A, B)
+
+
+def conserved_totals(cfg, Pd):
+    n1, n2, n3 = cfg["n"]
+    x = np.zeros((n3 * n2 * n1, 4))
+    kk, jj, ii = np.meshgrid(np.arange(n3), np.arange(n2), np.arange(n1), indexing="ij")
+    x[:, 1] = cfg["x0"][0] + (ii.ravel() + 0.5) * cfg["dx"][0]
+    x[:, 2] = cfg["x0"][1] + (jj.ravel() + 0.5) * cfg["dx"][1]
+    x[:, 3] = cfg["x0"][2] + (kk.ravel() + 0.5) * cfg["dx"][2]
+    Pz = Pd.reshape(12, -1).T.cpu().numpy()
+    U, _, _, _ = H.zone_physics(cfg, x, Pz)
+    tot = U.sum(axis=0)
+    absum = np.abs(U).sum(axis=0)
+    # mass, total energy (gas + radiation), total momentum (gas + radiation)
+    return np.array([tot[0], tot[1] + tot[8], tot[2] + tot[9], tot[3] + tot[10], tot[4] + tot[11]]), \
+        np.array([absum[0], absum[1] + absum[8], absum[2] + absum[9], absum[3] + absum[10],
+                  absum[4] + absum[11]])
+
+
+def test_split_precision_conserved_totals_full_size(torus_full):
+    """20 steps at 256x128x64: each conserved total of the split-precision
+    run (FP32 reconstruction, fluxes and EMFs) within 1e-5 of the FP64 run,
+    relative to the total's absolute sum."""
+    cfg, P = torus_full
+    out = {}
+    for prec in (H.PREC_FP64, H.PREC_SPLIT):
+        g = H.Grid(cfg, precision=prec)
+        g.set_prims(P)
+        for _ in range(20):
+            g.step(0.0)
+        out[prec] = g.get_prims(device=True)
+        del g
+    t64, s64 = conserved_totals(cfg, out[H.PREC_FP64])
+    t32, _ = conserved_totals(cfg, out[H.PREC_SPLIT])
+    rel = np.abs(t32 - t64) / s64
+    print("split vs FP64 conserved totals (mass, energy, momenta):", rel)
+    assert rel.max() < 1e-5
+
+
+def test_split_precision_against_oracle():
+    """64x32x16 torus, 10 steps: split precision against the FP64 oracle,
+    conserved totals within 1e-5; per-zone errors reported."""
+    cfg, P = W.torus((64, 32, 16), seed=12345)
+    g = H.Grid(cfg, precision=H.PREC_SPLIT)
+    g.set_prims(P)
+    o = O.Oracle(cfg)
+    o.set_prims(P)
+    for _ in range(10):
+        dt = o.cfl_dt()
+        o.step(dt)
+        g.step(dt)
+    A, R = g.get_prims(), o.get_prims()
+    tA, sA = conserved_totals(cfg, torch.as_tensor(A, device="cuda"))
+    tR, _ = conserved_totals(cfg, torch.as_tensor(R, device="cuda"))
+    rel = np.abs(tA - tR) / sA
+    e = zone_errors(cfg, A, R)
+    print("split vs oracle: conserved totals", rel, "per-zone error median %.2e p99 %.2e max %.2e" %
+          (np.median(e.max(0)), np.quantile(e.max(0), 0.99), e.max()))
+    assert rel.max() < 1e-5
