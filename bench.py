@@ -167,6 +167,9 @@ def main():
     ap.add_argument("--impl", default="harmrad", choices=["harmrad", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "split"])
     ap.add_argument("--size", default="256,128,64")
+    ap.add_argument("--workload", default="torus", choices=["torus", "batch48"],
+                    help="torus: the Kerr-Schild torus (default); batch48: 48 uneven Minkowski "
+                         "boxes with a per-zone absorption field in one batched context")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
@@ -188,11 +191,25 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     n = tuple(int(x) for x in args.size.split(","))
     prec = H.PREC_SPLIT if args.precision == "split" else H.PREC_FP64
-    cfg, P = W.torus(n, seed=12345 + rank)
-    nact = n[0] * n[1] * n[2]
     stream = torch.cuda.current_stream()
-    g = H.Grid(cfg, precision=prec, stream=stream)
-    g.set_prims(P)
+    if args.workload == "torus":
+        cfg, P = W.torus(n, seed=12345 + rank)
+        nact = n[0] * n[1] * n[2]
+        g = H.Grid(cfg, precision=prec, stream=stream)
+        g.set_prims(P)
+        wl = "KS torus a=0.9375 %dx%dx%d (PPM, LAXF, flux-CT, PMHD/URAD)" % n
+        size_key, prof_key = list(n), args.precision
+    else:
+        cfgs, Ps, Ks = W.box_batch(seed=4242 + rank)
+        g = H.Batch(cfgs, precision=prec, stream=stream)
+        g.set_prims(Ps)
+        g.set_opacity_field(Ks)
+        nact = g.nact
+        del Ps, Ks
+        wl = ("48 periodic Minkowski boxes, edges log-uniform 32..128 (%d zones), per-zone "
+              "absorption with optical depth per cell log-uniform 1e-4..1e6, one batched context"
+              % nact)
+        size_key, prof_key = "batch48", "batch48_" + args.precision
     for _ in range(args.warmup):
         g.step(0.0)
     torch.cuda.synchronize()
@@ -233,8 +250,8 @@ def main():
                 prof = json.load(fh)
         except (OSError, ValueError):
             prof = {}
-        entry = prof.get(args.precision, {})
-        fresh = entry.get("kernel_hash") == kernel_hash() and entry.get("size") == list(n)
+        entry = prof.get(prof_key, {})
+        fresh = entry.get("kernel_hash") == kernel_hash() and entry.get("size") == size_key
         flops_per_zone = entry.get("fp64_flops_per_zone_stage")
         traffic = entry.get("dram_bytes_per_launch") if fresh else None
         if flops_per_zone and fresh:
@@ -261,9 +278,10 @@ def main():
     # end to end through the C ABI with host buffers: H2D + step + D2H per step
     e2e = None
     if not args.no_e2e:
-        pin_in = torch.empty(P.size, dtype=torch.float64, pin_memory=True).numpy()
-        pin_out = torch.empty(P.size, dtype=torch.float64, pin_memory=True).numpy()
-        pin_in[:] = g.get_prims().ravel()
+        size = 12 * nact
+        pin_in = torch.empty(size, dtype=torch.float64, pin_memory=True).numpy()
+        pin_out = torch.empty(size, dtype=torch.float64, pin_memory=True).numpy()
+        pin_in[:] = g.get_prims(device=True).reshape(-1).cpu().numpy()
         g.step_host(pin_in, pin_out, 0.0)  # warm
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -272,7 +290,7 @@ def main():
             g.step_host(src, dst, 0.0)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        nbytes = P.size * 8
+        nbytes = size * 8
         e2e = {"value": nact * args.steps * ws / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes}
 
@@ -290,7 +308,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == H.PREC_FP64 else "f64+f32",
             "data": "synthetic",
-            "config": {"workload": "KS torus a=0.9375 %dx%dx%d (PPM, LAXF, flux-CT, PMHD/URAD)" % n,
+            "config": {"workload": wl,
                        "precision": args.precision, "zones": nact,
                        "l2": "working set > L2 (129 MB); no flush needed",
                        "parallelism": "replicas" if ws > 1 else "single GPU"},

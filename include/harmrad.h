@@ -62,6 +62,11 @@ extern "C" {
 
 #define HARMRAD_OPAC_CONST 0    /* kappa_abs = kappa_abs0 * rho0 (per length) */
 #define HARMRAD_OPAC_KRAMERS 1  /* kappa_abs = kappa_abs0 * rho0^2 * max(T,T_min)^-3.5 */
+#define HARMRAD_OPAC_FIELD 2    /* kappa_abs = kappa_scale * K, K a per-zone field
+                                   (harmrad_set_opacity_field); ghosts follow the bc */
+/* In every mode kappa_abs is multiplied by kappa_scale (also in FIELD mode,
+ * above) and the scattering coefficient is kappa_scale * kappa_es0 * rho0;
+ * both are per unit proper length. */
 
 #define HARMRAD_RECON_PPM 0
 #define HARMRAD_RECON_MC 1
@@ -121,6 +126,19 @@ typedef struct harmrad_ctx harmrad_ctx;
  * memory is exhausted. */
 int harmrad_init(const harmrad_params* p, void* stream, harmrad_ctx** out);
 
+/* Allocate one context for a batch of count independent grids ("boxes"),
+ * advanced together: every kernel of a step covers all boxes, so a batch of
+ * small boxes runs in the launches one grid takes.  p[0..count-1] may differ
+ * only in n, x0, dx and bc; the active directions (n > 1) and every physics
+ * parameter must agree (HARMRAD_E_ARG otherwise).  Arrays exchanged with the
+ * context (primitives, status, iterations, opacity field) hold the boxes'
+ * active-zone blocks one after another, box 0 first, each in the single-grid
+ * layout.  Each box takes its own CFL time step when harmrad_step gets dt <= 0
+ * (the boxes are independent problems); harmrad_cfl_dt and harmrad_stats.dt
+ * report the smallest.  harmrad_init(p, s, out) is harmrad_init_batch(p, 1, s,
+ * out).  harmrad_compute_fluxes accepts single-grid contexts only. */
+int harmrad_init_batch(const harmrad_params* p, int count, void* stream, harmrad_ctx** out);
+
 /* Release all device state of the context (NULL is ignored). */
 void harmrad_destroy(harmrad_ctx* ctx);
 
@@ -128,6 +146,14 @@ void harmrad_destroy(harmrad_ctx* ctx);
  * P is a device pointer, else host memory.  Returns HARMRAD_E_NAN_INPUT if any
  * value is not finite, or if rho0, u_g or Ebar is not positive. */
 int harmrad_set_prims(harmrad_ctx* ctx, const double* P, int on_device);
+
+/* Load the per-zone absorption field K (active zones, [n3][n2][n1] FP64 per
+ * box, boxes concatenated) of a context created with opacity =
+ * HARMRAD_OPAC_FIELD (HARMRAD_E_ARG otherwise); kappa_abs = kappa_scale * K per
+ * unit length.  Ghost values follow the boundary conditions like the
+ * primitives.  Returns HARMRAD_E_NAN_INPUT for a negative or non-finite value.
+ * The field starts at zero; it is kept until the next call. */
+int harmrad_set_opacity_field(harmrad_ctx* ctx, const double* K, int on_device);
 
 /* Copy the active-zone primitives out (same layout). */
 int harmrad_get_prims(harmrad_ctx* ctx, double* P, int on_device);
@@ -164,7 +190,8 @@ int harmrad_get_iters(harmrad_ctx* ctx, int* it, int on_device);
  * (faces 0..n_dir), FP64, host memory.  Diagnostic for tests. */
 int harmrad_compute_fluxes(harmrad_ctx* ctx, int dir, double* F_host);
 
-/* Point-wise physics at n independent points (device pointers, row-major):
+/* Point-wise physics at n independent points (device pointers, row-major;
+ * opacity mode HARMRAD_OPAC_FIELD is rejected with HARMRAD_E_ARG):
  * x[n][4] internal coordinates, P[n][12] primitives ->
  * U[n][12] conserved, SM[n][12] geometric source, F[n][3][12] fluxes,
  * speeds[n][3][4] (gas vmin, vmax, rad vmin, vmax per direction).  Any output

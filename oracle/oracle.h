@@ -37,7 +37,8 @@ typedef struct {
   double a_spin, R0, hslope;
   int bc[6];              /* lower/upper per direction: 0 periodic, 1 outflow, 2 polar */
   double gam, a_rad, courant;
-  int opacity;            /* 0 kappa = k0*rho (per length), 1 Kramers k0*rho^2*T^-3.5 */
+  int opacity;            /* 0 kappa = k0*rho (per length), 1 Kramers k0*rho^2*T^-3.5,
+                             2 per-zone field K (orc_set_opacity_field), kappa = K */
   double kappa_abs0, kappa_es0, kappa_scale, T_kappa_min;
   int recon;              /* 0 PPM, 1 MC */
   int flux;               /* 0 LAXF, 1 HLL */
@@ -64,6 +65,9 @@ void*  orc_create(const orc_params* p);
 void   orc_destroy(void* ctx);
 void   orc_set_prims(void* ctx, const double* P);
 void   orc_get_prims(void* ctx, double* P);
+/* Absorption field K of opacity mode 2, active zones [n3][n2][n1]; absorption
+ * per unit length kappa_scale * K; ghosts follow the boundary conditions. */
+void   orc_set_opacity_field(void* ctx, const double* K);
 double orc_cfl_dt(void* ctx);
 /* One full RK3 step; dt <= 0 means use the CFL time step. Returns the dt used. */
 double orc_step(void* ctx, double dt);

@@ -95,6 +95,7 @@ def lib():
         L.orc_destroy.argtypes = [ctypes.c_void_p]
         L.orc_set_prims.argtypes = [ctypes.c_void_p, dp]
         L.orc_get_prims.argtypes = [ctypes.c_void_p, dp]
+        L.orc_set_opacity_field.argtypes = [ctypes.c_void_p, dp]
         L.orc_get_prims_with_ghosts.argtypes = [ctypes.c_void_p, dp, ctypes.c_int]
         L.orc_cfl_dt.restype = ctypes.c_double
         L.orc_cfl_dt.argtypes = [ctypes.c_void_p]
@@ -168,6 +169,11 @@ class Oracle:
     def set_prims(self, P):
         P = _vec(P).reshape(self.shape)
         lib().orc_set_prims(self._h, _dp(P))
+
+    def set_opacity_field(self, K):
+        """Absorption field of opacity mode 2 ([n3,n2,n1]; per length kappa_scale K)."""
+        K = _vec(K).reshape(self.shape[1:])
+        lib().orc_set_opacity_field(self._h, _dp(K))
 
     def get_prims(self):
         P = np.empty(self.shape)

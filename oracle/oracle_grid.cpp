@@ -25,6 +25,7 @@ struct Ctx {
   int n[3], ng[3], N[3];
   long ntot;
   std::vector<double> P;    // [NP][ntot], ghosts included
+  std::vector<double> K;    // [ntot] absorption field (opacity mode 2 only), ghosts included
   std::vector<double> Un;   // [NP][ntot]
   std::vector<double> F[3]; // face fluxes [NP][ntot], face f of cell idx is its lower face
   std::vector<double> spd[3];  // per-face max signal speed
@@ -42,6 +43,13 @@ inline long idx(const Ctx& c, int i, int j, int k) {
 inline long aidx(const Ctx& c, int i, int j, int k) {
   return ((long)k * c.n[1] + j) * c.n[0] + i;
 }
+// Parameters for the physics of cell t: in opacity mode 2 the cell's field
+// value stands in for kappa_abs0.
+inline orc_params cell_params(const Ctx& c, long t) {
+  orc_params q = c.p;
+  if (c.p.opacity == 2) q.kappa_abs0 = c.K[t];
+  return q;
+}
 inline double xc(const Ctx& c, int d, int i) { return c.p.x0[d] + (i + 0.5) * c.p.dx[d]; }
 inline double xf(const Ctx& c, int d, int i) { return c.p.x0[d] + i * c.p.dx[d]; }
 
@@ -50,7 +58,8 @@ inline double xf(const Ctx& c, int d, int i) { return c.p.x0[d] + i * c.p.dx[d];
 // from already-filled data.  Periodic: wrap.  Outflow: copy the last active
 // zone and clamp the normal velocities so nothing flows in from the ghost.
 // Polar (direction 2 only): mirror across the axis, taking the zone on the
-// opposite side in phi (shift n3/2) and negating the theta components.
+// opposite side in phi (shift n3/2) and negating the theta components.  The
+// absorption field (opacity mode 2) is copied from the same source zone.
 void fill_ghosts(Ctx& c, std::vector<double>& P) {
   for (int d = 0; d < 3; ++d) {
     if (c.n[d] == 1) continue;
@@ -91,6 +100,7 @@ void fill_ghosts(Ctx& c, std::vector<double>& P) {
               long s = idx(c, src[0], src[1], src[2]);
               long t = idx(c, dst[0], dst[1], dst[2]);
               for (int q = 0; q < NP; ++q) P[(long)q * c.ntot + t] = P[(long)q * c.ntot + s];
+              if (!c.K.empty()) c.K[t] = c.K[s];
               if (sign_d < 0.0) {
                 P[(long)(U1 + d) * c.ntot + t] *= -1.0;
                 P[(long)(B1 + d) * c.ntot + t] *= -1.0;
@@ -181,9 +191,16 @@ void flattener(const FlatIn* c, int m, double* fg, double* fr) {
 // s[m] (cells f-4 .. f+3) with the stencil cells' geometry geo[m]; fg/fr
 // return the flattener of the left (m = 3) and right (m = 4) cells.  When
 // stored != nullptr the flattener is max-ed with (and written back to) the
-// values of earlier sub-steps: stored[side][gas/rad].
+// values of earlier sub-steps: stored[side][gas/rad].  K8 (opacity mode 2,
+// else nullptr): the stencil cells' absorption field; a reconstructed face
+// state takes the value of the cell it was reconstructed from.
 void face_flux(const orc_params& p, int d, const double P8[8][NP], const Geom* geo[8], const Geom& Gf,
-               double* stored[2][2], double F[NP], double* speed) {
+               const double* K8, double* stored[2][2], double F[NP], double* speed) {
+  auto at = [&](int m) {
+    orc_params q = p;
+    if (K8) q.kappa_abs0 = K8[m];
+    return q;
+  };
   const bool wvar = p.metric == 1 && d != 1;
   auto weighted = [&](int q) { return wvar && ((q >= U1 && q <= B3) || (q >= UR1 && q <= UR3)); };
   double s[8][NP];
@@ -201,7 +218,7 @@ void face_flux(const orc_params& p, int d, const double P8[8][NP], const Geom* g
     fin[m].vg = G.gdet * u.ucon[d + 1];
     fin[m].vr = G.gdet * v.ucon[d + 1];
     double ka, ks;
-    opacity(p, Pm[RHO], Pm[UU], &ka, &ks);
+    opacity(at(m), Pm[RHO], Pm[UU], &ka, &ks);
     double tau = (ka + ks) * std::sqrt(G.gcov[d + 1][d + 1]) * p.dx[d];
     fin[m].w = std::min(1.0, 2.0 * tau);
   }
@@ -240,8 +257,8 @@ void face_flux(const orc_params& p, int d, const double P8[8][NP], const Geom* g
       PR[q] /= Gf.gdet;
     }
   double UL[NP], UR[NP], FL[NP], FR[NP], sL[4], sR[4];
-  face_state(p, Gf, d + 1, PL, UL, FL, sL);
-  face_state(p, Gf, d + 1, PR, UR, FR, sR);
+  face_state(at(3), Gf, d + 1, PL, UL, FL, sL);
+  face_state(at(4), Gf, d + 1, PR, UR, FR, sR);
   double cmaxg = std::max(0.0, std::max(sL[1], sR[1]));
   double cming = -std::min(0.0, std::min(sL[0], sR[0]));
   double cmaxr = std::max(0.0, std::max(sL[3], sR[3]));
@@ -296,12 +313,13 @@ void compute_fluxes(Ctx& c, int d, bool use_stored) {
         if (p.metric == 1 && d == 1 &&
             ((f == 0 && p.bc[2] == 2) || (f == c.n[1] && p.bc[3] == 2)))
           continue;
-        double P8[8][NP];
+        double P8[8][NP], K8[8];
         const Geom* geo[8];
         for (int m = 0; m < 8; ++m) {
           long cm = t + (long)(m - 4) * str;
           geo[m] = &c.geo[cm];
           for (int q = 0; q < NP; ++q) P8[m][q] = c.P[(long)q * c.ntot + cm];
+          K8[m] = c.K.empty() ? 0.0 : c.K[cm];
         }
         double x[3] = {xc(c, 0, i), xc(c, 1, j), xc(c, 2, k)};
         x[d] = xf(c, d, f);
@@ -310,7 +328,7 @@ void compute_fluxes(Ctx& c, int d, bool use_stored) {
         double* st[2][2] = {{&c.flat[d][t - str], &c.flat[d][c.ntot + t - str]},
                             {&c.flat[d][t], &c.flat[d][c.ntot + t]}};
         double Fq[NP], sp;
-        face_flux(p, d, P8, geo, G, use_stored ? st : nullptr, Fq, &sp);
+        face_flux(p, d, P8, geo, G, c.K.empty() ? nullptr : K8, use_stored ? st : nullptr, Fq, &sp);
         for (int q = 0; q < NP; ++q) F[(long)q * c.ntot + t] = Fq[q];
         c.spd[d][t] = sp;
       }
@@ -457,7 +475,7 @@ void substep(Ctx& c, int s, double dt) {
         }
         double Pn[NP];
         orc_implicit_info info;
-        implicit_zone(c.p, G, Ust, Ps, Bc[s] * dt, Pn, &info);
+        implicit_zone(cell_params(c, t), G, Ust, Ps, Bc[s] * dt, Pn, &info);
         long a = aidx(c, i, j, k);
         c.status[a] = std::max(c.status[a], (unsigned char)info.method);
         c.iters[a] += info.iters_pmhd + info.iters_urad;
@@ -535,6 +553,7 @@ void* orc_create(const orc_params* p) {
     c->ntot *= c->N[d];
   }
   c->P.assign((size_t)NP * c->ntot, 0.0);
+  if (p->opacity == 2) c->K.assign((size_t)c->ntot, 0.0);
   c->Un.assign((size_t)NP * c->ntot, 0.0);
   for (int d = 0; d < 3; ++d) {
     c->F[d].assign((size_t)NP * c->ntot, 0.0);
@@ -570,6 +589,14 @@ void orc_set_prims(void* ctx, const double* P) {
       for (int j = 0; j < c.n[1]; ++j)
         for (int i = 0; i < c.n[0]; ++i)
           c.P[(long)q * c.ntot + idx(c, i, j, k)] = P[(long)q * na + aidx(c, i, j, k)];
+}
+
+void orc_set_opacity_field(void* ctx, const double* K) {
+  Ctx& c = *static_cast<Ctx*>(ctx);
+  if (c.K.empty()) return;
+  for (int k = 0; k < c.n[2]; ++k)
+    for (int j = 0; j < c.n[1]; ++j)
+      for (int i = 0; i < c.n[0]; ++i) c.K[idx(c, i, j, k)] = K[aidx(c, i, j, k)];
 }
 
 void orc_get_prims(void* ctx, double* P) {
@@ -729,7 +756,7 @@ void orc_face_flux_stencil(const orc_params* p, int d, const double* S, const do
   }
   Geom Gf;
   geom_at(*p, xfc[0], xfc[1], xfc[2], Gf);
-  face_flux(*p, d - 1, P8, geo, Gf, nullptr, F, speed);
+  face_flux(*p, d - 1, P8, geo, Gf, nullptr, nullptr, F, speed);
 }
 
 double orc_levermore_xi(double f) {

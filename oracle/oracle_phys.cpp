@@ -253,9 +253,14 @@ void rad_stress(const Geom& G, const double* P, double R[4][4], FourVel& ur) {
       R[m][n] = (4.0 / 3.0) * E * ur.ucon[m] * ur.ucov[n] + (m == n ? E / 3.0 : 0.0);
 }
 
+// Absorption and scattering coefficients per unit proper length.  Mode 2 is a
+// per-zone absorption field: the grid driver puts the zone's field value into
+// kappa_abs0 of the parameters it passes down for that zone.
 void opacity(const orc_params& p, double rho, double ug, double* kabs, double* ksca) {
   double T = (p.gam - 1.0) * ug / rho;
-  if (p.opacity == 1) {
+  if (p.opacity == 2) {
+    *kabs = p.kappa_scale * p.kappa_abs0;
+  } else if (p.opacity == 1) {
     double Tc = std::max(T, p.T_kappa_min);
     *kabs = p.kappa_scale * p.kappa_abs0 * rho * rho * std::pow(Tc, -3.5);
   } else {

@@ -1,13 +1,17 @@
 // C ABI of the harmrad library: context management, data movement and the
 // sequence of one full RK3 step (Sec. 4.1-4.2 of McKinney et al. 2014),
-// replayed as a CUDA graph.
+// replayed as a CUDA graph.  A context holds one grid, or the boxes of a
+// batch, all advanced by the same kernel launches.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
+#include <vector>
+
 #include "hr_ctx.h"
 
+using hr::BoxGeo;
 using hr::DevParams;
 
 namespace {
@@ -20,87 +24,89 @@ namespace {
     }                                        \
   } while (0)
 
-// active layout [12][n3][n2][n1] <-> ghost-inclusive layout
-__global__ void k_unpack(DevParams p, const double* __restrict__ src, double* __restrict__ P) {
-  long long total = (long long)hr::NPR * p.nact;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
-    long long q = id / p.nact, z = id % p.nact, r = z;
-    int i = (int)(r % p.n[0]);
-    r /= p.n[0];
-    int j = (int)(r % p.n[1]);
-    int k = (int)(r / p.n[1]);
-    P[q * p.ntot + hr::cell_index(p, i, j, k)] = src[id];
+// Active layout of a context: the grids' [nv][n3][n2][n1] blocks one after the
+// other.  These kernels move nv planes between it and the ghost-inclusive
+// cell layout (nv = 12 for the primitives, 1 for the opacity field).
+__global__ void k_unpack(const BoxGeo* __restrict__ boxes, int nbox, int nv,
+                         const double* __restrict__ src, double* __restrict__ dst0) {
+  for (int b = 0; b < nbox; ++b) {
+    const BoxGeo bx = boxes[b];
+    const double* s = src + nv * bx.aoff;
+    double* dst = dst0 + nv * bx.coff;
+    long long total = (long long)nv * bx.nact;
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+         id += (long long)gridDim.x * blockDim.x) {
+      long long q = id / bx.nact, z = id % bx.nact, r = z;
+      int i = (int)(r % bx.n[0]);
+      r /= bx.n[0];
+      int j = (int)(r % bx.n[1]);
+      int k = (int)(r / bx.n[1]);
+      dst[q * bx.ntot + hr::cell_index(bx, i, j, k)] = s[id];
+    }
   }
 }
 
-__global__ void k_pack(DevParams p, const double* __restrict__ P, double* __restrict__ dst) {
-  long long total = (long long)hr::NPR * p.nact;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
-    long long q = id / p.nact, z = id % p.nact, r = z;
-    int i = (int)(r % p.n[0]);
-    r /= p.n[0];
-    int j = (int)(r % p.n[1]);
-    int k = (int)(r / p.n[1]);
-    dst[id] = P[q * p.ntot + hr::cell_index(p, i, j, k)];
+__global__ void k_pack(const BoxGeo* __restrict__ boxes, int nbox, const double* __restrict__ P0,
+                       double* __restrict__ dst0) {
+  for (int b = 0; b < nbox; ++b) {
+    const BoxGeo bx = boxes[b];
+    const double* P = P0 + 12 * bx.coff;
+    double* d = dst0 + 12 * bx.aoff;
+    long long total = (long long)hr::NPR * bx.nact;
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+         id += (long long)gridDim.x * blockDim.x) {
+      long long q = id / bx.nact, z = id % bx.nact, r = z;
+      int i = (int)(r % bx.n[0]);
+      r /= bx.n[0];
+      int j = (int)(r % bx.n[1]);
+      int k = (int)(r / bx.n[1]);
+      d[id] = P[q * bx.ntot + hr::cell_index(bx, i, j, k)];
+    }
   }
 }
 
 // flag = 1 if any value is not finite or rho0, u_g, Ebar is not positive
-__global__ void k_validate(DevParams p, const double* __restrict__ src, int* flag) {
-  long long total = (long long)hr::NPR * p.nact;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
-    double v = src[id];
-    long long q = id / p.nact;
-    bool bad = !isfinite(v) || ((q == hr::RHO || q == hr::UU || q == hr::ER) && !(v > 0.0));
-    if (bad) atomicOr(flag, 1);
+// (nv = 12), or if any opacity-field value is negative or not finite (nv = 1)
+__global__ void k_validate(const BoxGeo* __restrict__ boxes, int nbox, int nv,
+                           const double* __restrict__ src, int* flag) {
+  for (int b = 0; b < nbox; ++b) {
+    const BoxGeo bx = boxes[b];
+    const double* s = src + nv * bx.aoff;
+    long long total = (long long)nv * bx.nact;
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
+         id += (long long)gridDim.x * blockDim.x) {
+      double v = s[id];
+      long long q = id / bx.nact;
+      bool bad = !isfinite(v);
+      if (nv == 12) bad = bad || ((q == hr::RHO || q == hr::UU || q == hr::ER) && !(v > 0.0));
+      else bad = bad || v < 0.0;
+      if (bad) atomicOr(flag, 1);
+    }
   }
 }
 
-__global__ void k_set_dt(double* dt, double v) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *dt = v;
+__global__ void k_set_dt(double* dt, int nbox, double v) {
+  for (int i = threadIdx.x; i < nbox; i += blockDim.x) dt[i] = v;
 }
 
-int fill_devparams(const harmrad_params* p, DevParams& d) {
+// Physics parameters shared by the grids of a context.
+int fill_physics(const harmrad_params* p, DevParams& d) {
   memset(&d, 0, sizeof(d));
-  long long ntot = 1, nact = 1;
   for (int e = 0; e < 3; ++e) {
     if (p->n[e] < 1) return HARMRAD_E_ARG;
-    if (!(p->dx[e] > 0.0)) return HARMRAD_E_ARG;
-    d.n[e] = p->n[e];
-    d.ng[e] = p->n[e] > 1 ? 4 : 0;
-    if (p->n[e] > 1 && p->n[e] < 4) return HARMRAD_E_ARG;  // ghosts need 4 active zones
-    d.N[e] = d.n[e] + 2 * d.ng[e];
-    ntot *= d.N[e];
-    nact *= d.n[e];
-    d.x0[e] = p->x0[e];
-    d.dx[e] = p->dx[e];
+    d.act[e] = p->n[e] > 1 ? 1 : 0;
   }
-  d.ntot = ntot;
-  d.nact = nact;
-  d.str[0] = 1;
-  d.str[1] = d.N[0];
-  d.str[2] = (long long)d.N[0] * d.N[1];
   if (p->metric != 0 && p->metric != 1) return HARMRAD_E_ARG;
   d.metric = p->metric;
   d.a = p->a_spin;
   d.R0 = p->R0;
   d.h = p->hslope;
   if (p->metric == 1 && (fabs(p->a_spin) >= 1.0 || p->hslope <= 0.0 || p->hslope > 1.0)) return HARMRAD_E_ARG;
-  for (int s = 0; s < 6; ++s) {
-    int bc = p->bc[s];
-    if (bc < 0 || bc > 2) return HARMRAD_E_ARG;
-    if (bc == 2 && (s / 2 != 1 || p->metric != 1)) return HARMRAD_E_ARG;
-    d.bc[s] = bc;
-  }
-  if ((p->bc[2] == 2 || p->bc[3] == 2) && p->n[2] > 1 && (p->n[2] % 2)) return HARMRAD_E_ARG;
   if (!(p->gam > 1.0) || !(p->a_rad >= 0.0) || !(p->courant > 0.0)) return HARMRAD_E_ARG;
   d.gam = p->gam;
   d.a_rad = p->a_rad;
   d.courant = p->courant;
-  if (p->opacity != 0 && p->opacity != 1) return HARMRAD_E_ARG;
+  if (p->opacity < 0 || p->opacity > 2) return HARMRAD_E_ARG;
   d.opacity = p->opacity;
   d.kabs0 = p->kappa_abs0;
   d.kes0 = p->kappa_es0;
@@ -133,6 +139,53 @@ int fill_devparams(const harmrad_params* p, DevParams& d) {
   return HARMRAD_OK;
 }
 
+// Geometry of one grid (offsets left at zero).
+int fill_geometry(const harmrad_params* p, BoxGeo& b) {
+  memset(&b, 0, sizeof(b));
+  long long ntot = 1, nact = 1;
+  for (int e = 0; e < 3; ++e) {
+    if (p->n[e] < 1) return HARMRAD_E_ARG;
+    if (!(p->dx[e] > 0.0)) return HARMRAD_E_ARG;
+    b.n[e] = p->n[e];
+    b.ng[e] = p->n[e] > 1 ? 4 : 0;
+    if (p->n[e] > 1 && p->n[e] < 4) return HARMRAD_E_ARG;  // ghosts need 4 active zones
+    b.N[e] = b.n[e] + 2 * b.ng[e];
+    ntot *= b.N[e];
+    nact *= b.n[e];
+    b.x0[e] = p->x0[e];
+    b.dx[e] = p->dx[e];
+  }
+  b.ntot = ntot;
+  b.nact = nact;
+  b.str[0] = 1;
+  b.str[1] = b.N[0];
+  b.str[2] = (long long)b.N[0] * b.N[1];
+  for (int s = 0; s < 6; ++s) {
+    int bc = p->bc[s];
+    if (bc < 0 || bc > 2) return HARMRAD_E_ARG;
+    if (bc == 2 && (s / 2 != 1 || p->metric != 1)) return HARMRAD_E_ARG;
+    b.bc[s] = bc;
+  }
+  if ((p->bc[2] == 2 || p->bc[3] == 2) && p->n[2] > 1 && (p->n[2] % 2)) return HARMRAD_E_ARG;
+  return HARMRAD_OK;
+}
+
+// The grids of a batch share every parameter except sizes, coordinates and
+// boundary conditions, and have the same active directions.
+bool same_physics(const harmrad_params& a, const harmrad_params& b) {
+  for (int e = 0; e < 3; ++e)
+    if ((a.n[e] > 1) != (b.n[e] > 1)) return false;
+  return a.metric == b.metric && a.a_spin == b.a_spin && a.R0 == b.R0 && a.hslope == b.hslope &&
+         a.gam == b.gam && a.a_rad == b.a_rad && a.courant == b.courant && a.opacity == b.opacity &&
+         a.kappa_abs0 == b.kappa_abs0 && a.kappa_es0 == b.kappa_es0 && a.kappa_scale == b.kappa_scale &&
+         a.T_kappa_min == b.T_kappa_min && a.recon == b.recon && a.flux == b.flux &&
+         a.gamma_rad_max == b.gamma_rad_max && a.gamma_gas_max == b.gamma_gas_max &&
+         a.floor_rho0 == b.floor_rho0 && a.floor_rho_pow == b.floor_rho_pow && a.floor_u0 == b.floor_u0 &&
+         a.floor_u_pow == b.floor_u_pow && a.bsq_rho_max == b.bsq_rho_max && a.bsq_u_max == b.bsq_u_max &&
+         a.u_rho_max == b.u_rho_max && a.newton_max == b.newton_max && a.newton_tol == b.newton_tol &&
+         a.precision == b.precision;
+}
+
 int run_faces(harmrad_ctx* c, bool fresh) {
   return c->dp.metric == 1 ? hr::Run<hr::KS>::faces(c, fresh) : hr::Run<hr::MINK>::faces(c, fresh);
 }
@@ -146,11 +199,10 @@ int run_solve(harmrad_ctx* c, int s) {
 // Enqueue one full step.  with_cfl: the time step comes from the CFL pass of
 // the current state, whose fluxes are then those of the first sub-step.
 int enqueue_step(harmrad_ctx* c, bool with_cfl) {
-  const DevParams& p = c->dp;
   cudaStream_t st = c->stream;
   int nk = 0, r;
-  HR_CHECK(cudaMemsetAsync(c->status, 0, p.nact, st));
-  HR_CHECK(cudaMemsetAsync(c->iters, 0, p.nact * sizeof(int), st));
+  HR_CHECK(cudaMemsetAsync(c->status, 0, c->nact, st));
+  HR_CHECK(cudaMemsetAsync(c->iters, 0, c->nact * sizeof(int), st));
   HR_CHECK(cudaMemsetAsync(c->stats, 0, 8 * sizeof(unsigned long long), st));
   hr::mark(c, HARMRAD_K_OTHER);
   if (with_cfl) {
@@ -196,10 +248,10 @@ int launch_step(harmrad_ctx* c, bool with_cfl) {
 }
 
 void free_all(harmrad_ctx* c) {
-  void* ptrs[] = {c->P, c->Un, c->F[0], c->F[1], c->F[2], c->spd[0], c->spd[1], c->spd[2],
-                  c->aux, c->flat[0], c->flat[1], c->flat[2], c->emf, c->edges, c->dt, c->status, c->iters,
-                  c->failed, c->qcount, c->qzone, c->qdata, c->fzone, c->ftmp, c->stats, c->dtmin,
-                  c->stage_buf, c->flag};
+  void* ptrs[] = {c->P, c->K, c->Un, c->F[0], c->F[1], c->F[2], c->spd[0], c->spd[1], c->spd[2],
+                  c->aux, c->flat[0], c->flat[1], c->flat[2], c->emf, c->edges, c->dt, c->status,
+                  c->iters, c->failed, c->qcount, c->qzone, c->qbox, c->qdata, c->fzone, c->fbox,
+                  c->ftmp, c->stats, c->dtmin, c->stage_buf, c->flag, c->dboxes};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (c->host_dt) cudaFreeHost(c->host_dt);
@@ -208,6 +260,7 @@ void free_all(harmrad_ctx* c) {
   for (int e = 0; e < 512; ++e)
     if (c->ev[e]) cudaEventDestroy(c->ev[e]);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  free(c->boxes);
 }
 
 template <typename T>
@@ -220,28 +273,46 @@ int dalloc(T** p, size_t bytes) {
   return HARMRAD_OK;
 }
 
-}  // namespace
-
-// Parameter validation shared with the entry points in other translation units.
-int harmrad_fill_params_internal(const harmrad_params* p, DevParams& d) { return fill_devparams(p, d); }
-
-extern "C" {
-
-int harmrad_init(const harmrad_params* p, void* stream, harmrad_ctx** out) {
-  if (!p || !out) return HARMRAD_E_ARG;
+int create(const harmrad_params* p, int count, void* stream, harmrad_ctx** out) {
+  if (!p || !out || count < 1) return HARMRAD_E_ARG;
   *out = nullptr;
   DevParams dp;
-  int rc = fill_devparams(p, dp);
+  int rc = fill_physics(&p[0], dp);
   if (rc) return rc;
+  std::vector<BoxGeo> boxes(count);
+  long long coff = 0, aoff = 0, maxc = 0, maxa = 0;
+  for (int b = 0; b < count; ++b) {
+    if (b > 0 && !same_physics(p[0], p[b])) return HARMRAD_E_ARG;
+    rc = fill_geometry(&p[b], boxes[b]);
+    if (rc) return rc;
+    boxes[b].coff = coff;
+    boxes[b].aoff = aoff;
+    coff += boxes[b].ntot;
+    aoff += boxes[b].nact;
+    maxc = boxes[b].ntot > maxc ? boxes[b].ntot : maxc;
+    maxa = boxes[b].nact > maxa ? boxes[b].nact : maxa;
+  }
   harmrad_ctx* c = (harmrad_ctx*)calloc(1, sizeof(harmrad_ctx));
   if (!c) return HARMRAD_E_OOM;
-  c->prm = *p;
+  c->prm = p[0];
   c->dp = dp;
-  c->real_size = p->precision == HARMRAD_PREC_SPLIT ? 4 : 8;
+  c->nbox = count;
+  c->boxes = (BoxGeo*)malloc(sizeof(BoxGeo) * count);
+  if (!c->boxes) {
+    free(c);
+    return HARMRAD_E_OOM;
+  }
+  memcpy(c->boxes, boxes.data(), sizeof(BoxGeo) * count);
+  c->ncell = coff;
+  c->nact = aoff;
+  c->maxcell = maxc;
+  c->maxact = maxa;
+  c->real_size = p[0].precision == HARMRAD_PREC_SPLIT ? 4 : 8;
   c->use_graph = getenv("HARMRAD_NO_GRAPH") == nullptr;
   if (cudaGetDevice(&c->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
     cudaGetLastError();
+    free(c->boxes);
     free(c);
     return HARMRAD_E_CUDA;
   }
@@ -250,17 +321,21 @@ int harmrad_init(const harmrad_params* p, void* stream, harmrad_ctx** out) {
   } else {
     if (cudaStreamCreate(&c->stream) != cudaSuccess) {
       cudaGetLastError();
+      free(c->boxes);
       free(c);
       return HARMRAD_E_CUDA;
     }
     c->own_stream = true;
   }
-  const size_t nt = dp.ntot, na = dp.nact, rs = c->real_size;
+  const size_t nt = c->ncell, na = c->nact, rs = c->real_size;
+  const size_t nk = dp.opacity == 2 ? nt : 1;
   rc = HARMRAD_OK;
+  rc = rc ? rc : dalloc(&c->dboxes, sizeof(BoxGeo) * count);
   rc = rc ? rc : dalloc(&c->P, 12 * nt * sizeof(double));
+  rc = rc ? rc : dalloc(&c->K, nk * sizeof(double));
   rc = rc ? rc : dalloc(&c->Un, 12 * na * sizeof(double));
   for (int d = 0; d < 3; ++d) {
-    size_t fn = dp.n[d] > 1 ? nt : 0;
+    size_t fn = dp.act[d] ? nt : 0;
     rc = rc ? rc : dalloc(&c->F[d], 12 * fn * rs);
     rc = rc ? rc : dalloc(&c->spd[d], fn * rs);
     rc = rc ? rc : dalloc(&c->flat[d], 2 * fn * rs);
@@ -268,32 +343,37 @@ int harmrad_init(const harmrad_params* p, void* stream, harmrad_ctx** out) {
   rc = rc ? rc : dalloc(&c->aux, 10 * nt * rs);
   rc = rc ? rc : dalloc(&c->emf, nt * rs);
   rc = rc ? rc : dalloc(&c->edges, 24 * nt * rs);
-  rc = rc ? rc : dalloc(&c->dt, sizeof(double));
+  rc = rc ? rc : dalloc(&c->dt, count * sizeof(double));
   rc = rc ? rc : dalloc(&c->status, na);
   rc = rc ? rc : dalloc(&c->iters, na * sizeof(int));
   rc = rc ? rc : dalloc(&c->failed, na);
   rc = rc ? rc : dalloc(&c->qcount, 2 * sizeof(int));
   rc = rc ? rc : dalloc(&c->qzone, na * sizeof(int));
+  rc = rc ? rc : dalloc(&c->qbox, na * sizeof(int));
   rc = rc ? rc : dalloc(&c->qdata, na * hr::QSTRIDE * sizeof(double));
   rc = rc ? rc : dalloc(&c->fzone, na * sizeof(int));
+  rc = rc ? rc : dalloc(&c->fbox, na * sizeof(int));
   rc = rc ? rc : dalloc(&c->ftmp, na * 12 * sizeof(double));
   rc = rc ? rc : dalloc(&c->stats, 8 * sizeof(unsigned long long));
-  rc = rc ? rc : dalloc(&c->dtmin, sizeof(unsigned long long));
+  rc = rc ? rc : dalloc(&c->dtmin, count * sizeof(unsigned long long));
   rc = rc ? rc : dalloc(&c->stage_buf, 12 * na * sizeof(double));
   rc = rc ? rc : dalloc(&c->flag, sizeof(int));
-  if (!rc && cudaMallocHost((void**)&c->host_dt, sizeof(double)) != cudaSuccess) {
+  if (!rc && cudaMallocHost((void**)&c->host_dt, count * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     rc = HARMRAD_E_OOM;
   }
   if (!rc) {
-    // zero everything that a kernel may read before writing
-    if (cudaMemsetAsync(c->P, 0, 12 * nt * sizeof(double), c->stream) != cudaSuccess ||
+    // the grid table, and zeros in everything a kernel may read before writing
+    if (cudaMemcpyAsync(c->dboxes, c->boxes, sizeof(BoxGeo) * count, cudaMemcpyHostToDevice,
+                        c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->P, 0, 12 * nt * sizeof(double), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->K, 0, nk * sizeof(double), c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->stats, 0, 8 * sizeof(unsigned long long), c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->status, 0, na, c->stream) != cudaSuccess ||
         cudaMemsetAsync(c->iters, 0, na * sizeof(int), c->stream) != cudaSuccess)
       rc = HARMRAD_E_CUDA;
     for (int d = 0; d < 3 && !rc; ++d) {
-      size_t fn = dp.n[d] > 1 ? nt : 0;
+      size_t fn = dp.act[d] ? nt : 0;
       if (fn && (cudaMemsetAsync(c->F[d], 0, 12 * fn * rs, c->stream) != cudaSuccess ||
                  cudaMemsetAsync(c->spd[d], 0, fn * rs, c->stream) != cudaSuccess ||
                  cudaMemsetAsync(c->flat[d], 0, 2 * fn * rs, c->stream) != cudaSuccess))
@@ -310,6 +390,40 @@ int harmrad_init(const harmrad_params* p, void* stream, harmrad_ctx** out) {
   return HARMRAD_OK;
 }
 
+int upload_planes(harmrad_ctx* c, int nv, const double* src_in, int on_device, double* dst) {
+  size_t bytes = nv * (size_t)c->nact * sizeof(double);
+  const double* src = src_in;
+  if (!on_device) {
+    HR_CHECK(cudaMemcpyAsync(c->stage_buf, src_in, bytes, cudaMemcpyHostToDevice, c->stream));
+    src = c->stage_buf;
+  }
+  HR_CHECK(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+  int g = hr::grid_for(nv * c->maxact, c->sms, 256);
+  k_validate<<<g, 256, 0, c->stream>>>(c->dboxes, c->nbox, nv, src, c->flag);
+  k_unpack<<<g, 256, 0, c->stream>>>(c->dboxes, c->nbox, nv, src, dst);
+  HR_CHECK(cudaGetLastError());
+  int flag = 0;
+  HR_CHECK(cudaMemcpyAsync(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  HR_CHECK(cudaStreamSynchronize(c->stream));
+  return flag ? HARMRAD_E_NAN_INPUT : HARMRAD_OK;
+}
+
+}  // namespace
+
+// Parameter validation shared with the entry points in other translation units.
+int harmrad_fill_params_internal(const harmrad_params* p, DevParams& d) { return fill_physics(p, d); }
+int harmrad_fill_geometry_internal(const harmrad_params* p, BoxGeo& b) { return fill_geometry(p, b); }
+
+extern "C" {
+
+int harmrad_init(const harmrad_params* p, void* stream, harmrad_ctx** out) {
+  return create(p, 1, stream, out);
+}
+
+int harmrad_init_batch(const harmrad_params* p, int count, void* stream, harmrad_ctx** out) {
+  return create(p, count, stream, out);
+}
+
 void harmrad_destroy(harmrad_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
@@ -319,33 +433,24 @@ void harmrad_destroy(harmrad_ctx* c) {
 
 int harmrad_set_prims(harmrad_ctx* c, const double* P, int on_device) {
   if (!c || !P) return HARMRAD_E_ARG;
-  const DevParams& p = c->dp;
-  size_t bytes = 12 * (size_t)p.nact * sizeof(double);
-  const double* src = P;
-  if (!on_device) {
-    HR_CHECK(cudaMemcpyAsync(c->stage_buf, P, bytes, cudaMemcpyHostToDevice, c->stream));
-    src = c->stage_buf;
-  }
-  HR_CHECK(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
-  int g = hr::grid_for(12 * p.nact, c->sms, 256);
-  k_validate<<<g, 256, 0, c->stream>>>(p, src, c->flag);
-  k_unpack<<<g, 256, 0, c->stream>>>(p, src, c->P);
-  HR_CHECK(cudaGetLastError());
-  int flag = 0;
-  HR_CHECK(cudaMemcpyAsync(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-  HR_CHECK(cudaStreamSynchronize(c->stream));
-  if (flag) return HARMRAD_E_NAN_INPUT;
+  int rc = upload_planes(c, 12, P, on_device, c->P);
+  if (rc) return rc;
   c->has_prims = true;
   return HARMRAD_OK;
 }
 
+int harmrad_set_opacity_field(harmrad_ctx* c, const double* kabs, int on_device) {
+  if (!c || !kabs) return HARMRAD_E_ARG;
+  if (c->dp.opacity != HARMRAD_OPAC_FIELD) return HARMRAD_E_ARG;
+  return upload_planes(c, 1, kabs, on_device, c->K);
+}
+
 int harmrad_get_prims(harmrad_ctx* c, double* P, int on_device) {
   if (!c || !P) return HARMRAD_E_ARG;
-  const DevParams& p = c->dp;
-  size_t bytes = 12 * (size_t)p.nact * sizeof(double);
-  int g = hr::grid_for(12 * p.nact, c->sms, 256);
+  size_t bytes = 12 * (size_t)c->nact * sizeof(double);
+  int g = hr::grid_for(12 * c->maxact, c->sms, 256);
   double* dst = on_device ? P : c->stage_buf;
-  k_pack<<<g, 256, 0, c->stream>>>(p, c->P, dst);
+  k_pack<<<g, 256, 0, c->stream>>>(c->dboxes, c->nbox, c->P, dst);
   HR_CHECK(cudaGetLastError());
   if (!on_device) {
     HR_CHECK(cudaMemcpyAsync(P, c->stage_buf, bytes, cudaMemcpyDeviceToHost, c->stream));
@@ -359,9 +464,11 @@ int harmrad_cfl_dt(harmrad_ctx* c, double* dt) {
   if (!c->has_prims) return HARMRAD_E_STATE;
   int r = run_cfl(c);
   if (r < 0) return r;
-  HR_CHECK(cudaMemcpyAsync(c->host_dt, c->dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  HR_CHECK(cudaMemcpyAsync(c->host_dt, c->dt, c->nbox * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   HR_CHECK(cudaStreamSynchronize(c->stream));
-  *dt = *c->host_dt;
+  double m = c->host_dt[0];
+  for (int b = 1; b < c->nbox; ++b) m = c->host_dt[b] < m ? c->host_dt[b] : m;
+  *dt = m;
   return HARMRAD_OK;
 }
 
@@ -371,7 +478,7 @@ int harmrad_step(harmrad_ctx* c, double dt) {
   bool with_cfl = !(dt > 0.0);
   if (!with_cfl) {
     // the value travels as a kernel argument: no host synchronisation
-    k_set_dt<<<1, 32, 0, c->stream>>>(c->dt, dt);
+    k_set_dt<<<1, 128, 0, c->stream>>>(c->dt, c->nbox, dt);
     HR_CHECK(cudaGetLastError());
   }
   c->last_dt = dt;
@@ -389,7 +496,7 @@ int harmrad_profile_step(harmrad_ctx* c, double dt, harmrad_kernel_times* out) {
   hr::mark(c, HARMRAD_K_OTHER);  // start marker
   int r = 0;
   if (!with_cfl) {
-    k_set_dt<<<1, 32, 0, c->stream>>>(c->dt, dt);
+    k_set_dt<<<1, 128, 0, c->stream>>>(c->dt, c->nbox, dt);
     hr::mark(c, HARMRAD_K_OTHER);
   }
   r = enqueue_step(c, with_cfl);
@@ -419,11 +526,12 @@ int harmrad_step_host(harmrad_ctx* c, const double* P_in, double* P_out, double 
 int harmrad_get_stats(harmrad_ctx* c, harmrad_stats* s) {
   if (!c || !s) return HARMRAD_E_ARG;
   unsigned long long h[8];
-  double dt = 0.0;
   HR_CHECK(cudaMemcpyAsync(h, c->stats, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
-  HR_CHECK(cudaMemcpyAsync(&dt, c->dt, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  HR_CHECK(cudaMemcpyAsync(c->host_dt, c->dt, c->nbox * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   HR_CHECK(cudaStreamSynchronize(c->stream));
-  s->dt = dt;
+  double m = c->host_dt[0];
+  for (int b = 1; b < c->nbox; ++b) m = c->host_dt[b] < m ? c->host_dt[b] : m;
+  s->dt = m;
   s->pmhd_ok = (long long)h[hr::ST_PMHD];
   s->urad_ok = (long long)h[hr::ST_URAD];
   s->backup = (long long)h[hr::ST_BACKUP];
@@ -436,7 +544,7 @@ int harmrad_get_stats(harmrad_ctx* c, harmrad_stats* s) {
 
 int harmrad_get_status(harmrad_ctx* c, unsigned char* st, int on_device) {
   if (!c || !st) return HARMRAD_E_ARG;
-  HR_CHECK(cudaMemcpyAsync(st, c->status, c->dp.nact,
+  HR_CHECK(cudaMemcpyAsync(st, c->status, c->nact,
                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
   HR_CHECK(cudaStreamSynchronize(c->stream));
   return HARMRAD_OK;
@@ -444,7 +552,7 @@ int harmrad_get_status(harmrad_ctx* c, unsigned char* st, int on_device) {
 
 int harmrad_get_iters(harmrad_ctx* c, int* it, int on_device) {
   if (!c || !it) return HARMRAD_E_ARG;
-  HR_CHECK(cudaMemcpyAsync(it, c->iters, c->dp.nact * sizeof(int),
+  HR_CHECK(cudaMemcpyAsync(it, c->iters, c->nact * sizeof(int),
                            on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
   HR_CHECK(cudaStreamSynchronize(c->stream));
   return HARMRAD_OK;
@@ -453,13 +561,14 @@ int harmrad_get_iters(harmrad_ctx* c, int* it, int on_device) {
 int harmrad_compute_fluxes(harmrad_ctx* c, int dir, double* F_host) {
   if (!c || !F_host || dir < 1 || dir > 3) return HARMRAD_E_ARG;
   if (!c->has_prims) return HARMRAD_E_STATE;
-  const DevParams& p = c->dp;
+  if (c->nbox != 1) return HARMRAD_E_ARG;
+  const BoxGeo& b = c->boxes[0];
   int d = dir - 1;
-  if (p.n[d] == 1) return HARMRAD_E_ARG;
+  if (b.n[d] == 1) return HARMRAD_E_ARG;
   int r = run_faces(c, true);
   if (r < 0) return r;
   size_t rs = c->real_size;
-  size_t bytes = 12 * (size_t)p.ntot * rs;
+  size_t bytes = 12 * (size_t)b.ntot * rs;
   char* hbuf = (char*)malloc(bytes);
   if (!hbuf) return HARMRAD_E_OOM;
   if (cudaMemcpyAsync(hbuf, c->F[d], bytes, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
@@ -468,16 +577,16 @@ int harmrad_compute_fluxes(harmrad_ctx* c, int dir, double* F_host) {
     cudaGetLastError();
     return HARMRAD_E_CUDA;
   }
-  int m[3] = {p.n[0], p.n[1], p.n[2]};
+  int m[3] = {b.n[0], b.n[1], b.n[2]};
   m[d] += 1;
   long long nf = (long long)m[0] * m[1] * m[2];
   for (int q = 0; q < 12; ++q)
     for (int k = 0; k < m[2]; ++k)
       for (int j = 0; j < m[1]; ++j)
         for (int i = 0; i < m[0]; ++i) {
-          long long t = ((long long)(k + p.ng[2]) * p.N[1] + (j + p.ng[1])) * p.N[0] + (i + p.ng[0]);
+          long long t = hr::cell_index(b, i, j, k);
           long long o = (long long)q * nf + ((long long)k * m[1] + j) * m[0] + i;
-          F_host[o] = rs == 8 ? ((double*)hbuf)[q * p.ntot + t] : (double)((float*)hbuf)[q * p.ntot + t];
+          F_host[o] = rs == 8 ? ((double*)hbuf)[q * b.ntot + t] : (double)((float*)hbuf)[q * b.ntot + t];
         }
   free(hbuf);
   return HARMRAD_OK;
@@ -487,15 +596,18 @@ int harmrad_zone_physics(const harmrad_params* prm, int n, const double* x, cons
                          double* SM, double* F, double* speeds, void* stream) {
   if (!prm || n < 0 || (n > 0 && (!x || !P))) return HARMRAD_E_ARG;
   DevParams dp;
-  int rc = fill_devparams(prm, dp);
+  BoxGeo bg;
+  int rc = fill_physics(prm, dp);
+  if (!rc) rc = fill_geometry(prm, bg);
   if (rc) return rc;
+  if (dp.opacity == HARMRAD_OPAC_FIELD) return HARMRAD_E_ARG;
   if (n == 0) return HARMRAD_OK;
   int dev, sms;
   HR_CHECK(cudaGetDevice(&dev));
   HR_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   cudaStream_t st = (cudaStream_t)stream;
-  int r = dp.metric == 1 ? hr::Run<hr::KS>::zone_physics(dp, n, x, P, U, SM, F, speeds, st, sms)
-                         : hr::Run<hr::MINK>::zone_physics(dp, n, x, P, U, SM, F, speeds, st, sms);
+  int r = dp.metric == 1 ? hr::Run<hr::KS>::zone_physics(dp, bg, n, x, P, U, SM, F, speeds, st, sms)
+                         : hr::Run<hr::MINK>::zone_physics(dp, bg, n, x, P, U, SM, F, speeds, st, sms);
   if (r < 0) return r;
   HR_CHECK(cudaStreamSynchronize(st));
   return HARMRAD_OK;
@@ -506,16 +618,19 @@ int harmrad_zone_implicit(const harmrad_params* prm, int n, const double* x, con
                           unsigned char* method, void* stream) {
   if (!prm || n < 0 || (n > 0 && (!x || !Us || !Ps || !h || !Pout))) return HARMRAD_E_ARG;
   DevParams dp;
-  int rc = fill_devparams(prm, dp);
+  BoxGeo bg;
+  int rc = fill_physics(prm, dp);
+  if (!rc) rc = fill_geometry(prm, bg);
   if (rc) return rc;
+  if (dp.opacity == HARMRAD_OPAC_FIELD) return HARMRAD_E_ARG;
   if (n == 0) return HARMRAD_OK;
   int dev, sms;
   HR_CHECK(cudaGetDevice(&dev));
   HR_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   cudaStream_t st = (cudaStream_t)stream;
   int r = dp.metric == 1
-              ? hr::Run<hr::KS>::zone_implicit(dp, n, x, Us, Ps, h, Pout, eT, iters, method, st, sms)
-              : hr::Run<hr::MINK>::zone_implicit(dp, n, x, Us, Ps, h, Pout, eT, iters, method, st, sms);
+              ? hr::Run<hr::KS>::zone_implicit(dp, bg, n, x, Us, Ps, h, Pout, eT, iters, method, st, sms)
+              : hr::Run<hr::MINK>::zone_implicit(dp, bg, n, x, Us, Ps, h, Pout, eT, iters, method, st, sms);
   if (r < 0) return r;
   HR_CHECK(cudaStreamSynchronize(st));
   return HARMRAD_OK;
@@ -528,7 +643,7 @@ const char* harmrad_strerror(int code) {
     case HARMRAD_E_ARG: return "invalid argument";
     case HARMRAD_E_CUDA: return "CUDA runtime error";
     case HARMRAD_E_OOM: return "out of device memory";
-    case HARMRAD_E_NAN_INPUT: return "primitives not finite or not positive";
+    case HARMRAD_E_NAN_INPUT: return "input not finite or out of range";
     case HARMRAD_E_STATE: return "call out of order (no primitives loaded)";
     default: return "unknown harmrad return code";
   }

@@ -7,11 +7,13 @@ namespace hr {
 enum { ST_PMHD = 0, ST_URAD = 1, ST_BACKUP = 2, ST_SOLVES = 3, ST_ITERS = 4 };
 constexpr int QSTRIDE = 18;
 
-__device__ __forceinline__ long long cell_index(const DevParams& p, int i, int j, int k) {
-  return ((long long)(k + p.ng[2]) * p.N[1] + (j + p.ng[1])) * p.N[0] + (i + p.ng[0]);
+// Index of cell (i, j, k) (active indices, ghosts negative or >= n) within
+// its grid's block of a cell-indexed array.
+__host__ __device__ __forceinline__ long long cell_index(const BoxGeo& b, int i, int j, int k) {
+  return ((long long)(k + b.ng[2]) * b.N[1] + (j + b.ng[1])) * b.N[0] + (i + b.ng[0]);
 }
-__device__ __forceinline__ double xcen(const DevParams& p, int d, int i) {
-  return p.x0[d] + (i + 0.5) * p.dx[d];
+__host__ __device__ __forceinline__ double xcen(const BoxGeo& b, int d, int i) {
+  return b.x0[d] + (i + 0.5) * b.dx[d];
 }
 
 inline int grid_for(long long work, int sms, int block) {

@@ -10,8 +10,13 @@ struct Bufs;
 }
 
 struct harmrad_ctx {
-  harmrad_params prm;
-  hr::DevParams dp;
+  harmrad_params prm;        // parameters of the first grid
+  hr::DevParams dp;          // physics shared by every grid
+  int nbox;                  // grids in this context (1, or the boxes of a batch)
+  hr::BoxGeo* boxes;         // host copy of the grid table
+  hr::BoxGeo* dboxes;        // device copy
+  long long ncell, nact;     // totals over the grids
+  long long maxcell, maxact; // largest grid
   cudaStream_t stream;
   bool own_stream;
   int device;
@@ -19,6 +24,7 @@ struct harmrad_ctx {
   size_t real_size;  // 8 (FP64) or 4 (split)
   // device memory
   double* P;
+  double* K;
   double* Un;
   void* F[3];
   void* spd[3];
@@ -32,14 +38,16 @@ struct harmrad_ctx {
   unsigned char* failed;
   int* qcount;
   int* qzone;
+  int* qbox;
   double* qdata;
   int* fzone;
+  int* fbox;
   double* ftmp;
   unsigned long long* stats;
   unsigned long long* dtmin;
   double* stage_buf;      // [12][nact] active-layout staging for set/get
   int* flag;              // validation flag
-  double* host_dt;        // pinned host scalar for dt uploads
+  double* host_dt;        // pinned host scalar for dt read-back
   bool has_prims;
   // CUDA graphs of a full step: [0] dt given, [1] CFL dt
   cudaGraphExec_t graph[2];
@@ -73,11 +81,12 @@ struct Run {
   static int faces(harmrad_ctx* c, bool fresh);     // ghosts, prep, flattener, fluxes, flux-CT
   static int cfl(harmrad_ctx* c);                   // faces(fresh) + reduction into *dt
   static int solve(harmrad_ctx* c, int stage);      // update + implicit, retry, back-up
-  static int zone_physics(const DevParams& dp, int n, const double* x, const double* P, double* U,
-                          double* SM, double* F, double* speeds, cudaStream_t st, int sms);
-  static int zone_implicit(const DevParams& dp, int n, const double* x, const double* Us,
-                           const double* Ps, const double* h, double* Pout, double* eT, int* iters,
-                           unsigned char* method, cudaStream_t st, int sms);
+  static int zone_physics(const DevParams& dp, const BoxGeo& bg, int n, const double* x,
+                          const double* P, double* U, double* SM, double* F, double* speeds,
+                          cudaStream_t st, int sms);
+  static int zone_implicit(const DevParams& dp, const BoxGeo& bg, int n, const double* x,
+                           const double* Us, const double* Ps, const double* h, double* Pout,
+                           double* eT, int* iters, unsigned char* method, cudaStream_t st, int sms);
 };
 
 }  // namespace hr

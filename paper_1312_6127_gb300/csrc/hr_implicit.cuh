@@ -29,6 +29,7 @@ struct ImpSys {
   double Rs[4];  // explicit R^t_nu
   double B[3];
   double h;      // b_s dt
+  double kf;     // the zone's absorption opacity when it is a per-zone field
   double sgk[3]; // sqrt(gamma^{kk}) of the ZAMO slice
 };
 
@@ -49,12 +50,12 @@ struct ImpState {
 // G_nu for gas temperature T (given, so the caller can form it without a
 // division).
 template <int MET>
-__device__ __forceinline__ void four_force_rad(const DevParams& p, double rho, double T,
+__device__ __forceinline__ void four_force_rad(const DevParams& p, double rho, double T, double kf,
                                                const double ucon[4], const double ucov[4],
                                                const double urc[4], const double urv[4], double E,
                                                double G[4]) {
   double kabs, ksca;
-  opacity_T<double>(p, rho, T, &kabs, &ksca);
+  opacity_T<double>(p, rho, T, kf, &kabs, &ksca);
   double T2 = T * T;
   double lam = kabs * p.a_rad * T2 * T2;
   double uru = urv[0] * ucon[0] + urv[1] * ucon[1] + urv[2] * ucon[2] + urv[3] * ucon[3];
@@ -129,8 +130,8 @@ __device__ __forceinline__ void pmhd_res(const DevParams& p, const ImpSys<MET>& 
   fourvel<MET, double>(g, Pr[1], Pr[2], Pr[3], urc, urv, &gr);
   double G[4];
   // T = p_g / rho0 = (gamma-1) u_g u^t / (rho0 u^t)
-  four_force_rad<MET>(p, rho, (p.gam - 1.0) * x[0] * ucon[0] * s.iDlab, ucon, ucov, urc, urv, Pr[0],
-                      G);
+  four_force_rad<MET>(p, rho, (p.gam - 1.0) * x[0] * ucon[0] * s.iDlab, s.kf, ucon, ucov, urc, urv,
+                      Pr[0], G);
 #pragma unroll
   for (int k = 0; k < 4; ++k) r.Eg[k] = Tc[k] - s.Ts[k] - s.h * G[k];
   if (norm) {
@@ -339,7 +340,7 @@ __device__ __forceinline__ bool urad_res(const DevParams& p, const ImpSys<MET>& 
 #pragma unroll
   for (int k = 1; k < 4; ++k) Rc[k] = e43 * urc[0] * urv[k];
   double G[4];
-  four_force_rad<MET>(p, rho, (p.gam - 1.0) * ug / rho, ucon, ucov, urc, urv, Pr[0], G);
+  four_force_rad<MET>(p, rho, (p.gam - 1.0) * ug / rho, s.kf, ucon, ucov, urc, urv, Pr[0], G);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     r.Eg[k] = Tc[k] - s.Ts[k] - s.h * G[k];
@@ -442,8 +443,9 @@ __device__ int newton_urad(const DevParams& p, const ImpSys<MET>& s, const doubl
 
 template <int MET>
 __device__ __forceinline__ void build_sys(const DevParams& p, const Geo<MET, double>& g,
-                                          const double Us[12], double h, ImpSys<MET>& s) {
+                                          const double Us[12], double h, double kf, ImpSys<MET>& s) {
   s.g = g;
+  s.kf = kf;
   double igd = 1.0 / g.gdet;
   s.Dlab = Us[0] * igd;
   s.iDlab = 1.0 / s.Dlab;

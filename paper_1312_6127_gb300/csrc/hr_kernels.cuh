@@ -4,9 +4,14 @@
 // [12][N3][N2][N1] with 4 ghost zones on each side of every active direction
 // (i fastest, so a warp reads 32 consecutive x1 zones of one variable).
 // Face fluxes of direction d share the cell indexing: the flux stored at cell
-// t is the flux through t's lower d-face.  Every kernel is launched with a
-// grid that covers its index space exactly once (grid-stride loops), sized in
-// multiples of the SM count by the host.
+// t is the flux through t's lower d-face.
+//
+// A context holds one or more grids (the boxes of a batch).  Every array is
+// the concatenation of per-grid blocks, each laid out as above; BoxGeo gives a
+// grid's sizes and its offsets.  Every kernel loops over the grids and, inside
+// a grid, over its index space with a grid-stride loop, so one launch advances
+// all grids of a batch.  Grids are sized by the host in multiples of the SM
+// count.
 #pragma once
 #include "hr_common.cuh"
 #include "hr_implicit.cuh"
@@ -14,24 +19,28 @@
 namespace hr {
 
 struct Bufs {
-  double* P;       // [12][ntot] primitives, ghosts included
+  double* P;       // [12][ntot] primitives, ghosts included (per grid)
+  double* K;       // [ntot] per-zone absorption opacity (opacity field mode), ghosts included
   double* Un;      // [12][nact] conserved state at the start of the step
   void* F[3];      // [12][ntot] face fluxes (real type of the precision mode)
   void* spd[3];    // [ntot] per-face max signal speed
   void* aux;       // [10][ntot] per-cell gdet, sqrt(-g) u^d gas/rad, tau weights
   void* flat[3];   // [2][ntot] flattener, max over the sub-steps of the step
   void* emf;       // [ntot] edge EMF scratch
-  double* dt;      // device scalar: time step
+  void* edges;     // [24][ntot] reconstructed edges of one direction
+  double* dt;      // [nbox] time step of each grid
   unsigned char* status;  // [nact] worst outcome over the sub-steps
   int* iters;             // [nact] Newton steps summed over the sub-steps
   unsigned char* failed;  // [nact] back-up flag of the current sub-step
   int* qcount;            // [2] retry-queue and back-up-list lengths
-  int* qzone;             // [nact] retry queue: active zone index
+  int* qzone;             // [nact] retry queue: zone index within its grid
+  int* qbox;              // [nact] retry queue: grid of the entry
   double* qdata;          // [nact][18] retry queue payload: U*, PMHD best x, e_T, h
-  int* fzone;             // [nact] back-up list
+  int* fzone;             // [nact] back-up list: zone index within its grid
+  int* fbox;              // [nact] back-up list: grid of the entry
   double* ftmp;           // [nact][12] averaged primitives of back-up zones
   unsigned long long* stats;  // [8] counters
-  unsigned long long* dtmin;  // CFL minimum (ordered bits of a positive double)
+  unsigned long long* dtmin;  // [nbox] CFL minimum (ordered bits of a positive double)
 };
 
 // Counter update aggregated over the converged lanes of a warp.
@@ -41,61 +50,76 @@ __device__ __forceinline__ void warp_add(unsigned long long* dst, unsigned v) {
   if ((int)(threadIdx.x & 31) == __ffs(mask) - 1 && s) atomicAdd(dst, (unsigned long long)s);
 }
 
+#define HR_TID (blockIdx.x * (long long)blockDim.x + threadIdx.x)
+#define HR_STRIDE ((long long)gridDim.x * blockDim.x)
+
+// Opacity-field value of a cell (1 when the opacity is not a field).
+__device__ __forceinline__ double kfield(const DevParams& p, const double* K, long long t) {
+  return p.opacity == 2 ? K[t] : 1.0;
+}
+
 // ----------------------------------------------------------- ghost fill
 // One direction at a time, in the order 1, 2, 3, so that edges and corners
 // come from already-filled cells.  Periodic wraps; outflow copies the last
 // active zone and clamps the normal velocities (gas and radiation) so nothing
 // enters from the ghost; polar mirrors across the axis from the zone half a
-// turn away in phi, negating the theta components.
-static __global__ void k_bc_fill(DevParams p, double* __restrict__ P, int d) {
-  int lo[3], len[3];
-  for (int e = 0; e < 3; ++e) {
-    if (e == d) {
-      lo[e] = 0;
-      len[e] = p.ng[d];
-    } else if (e < d) {
-      lo[e] = -p.ng[e];
-      len[e] = p.n[e] + 2 * p.ng[e];
-    } else {
-      lo[e] = 0;
-      len[e] = p.n[e];
+// turn away in phi, negating the theta components.  The opacity field, when
+// present, is copied like a scalar primitive.
+static __global__ void k_bc_fill(DevParams p, const BoxGeo* __restrict__ boxes, int nbox,
+                                 double* __restrict__ P0, double* __restrict__ K0, int d) {
+  for (int bi = 0; bi < nbox; ++bi) {
+    const BoxGeo& bx = boxes[bi];
+    double* P = P0 + 12 * bx.coff;
+    double* K = K0 ? K0 + bx.coff : nullptr;
+    int lo[3], len[3];
+    for (int e = 0; e < 3; ++e) {
+      if (e == d) {
+        lo[e] = 0;
+        len[e] = bx.ng[d];
+      } else if (e < d) {
+        lo[e] = -bx.ng[e];
+        len[e] = bx.n[e] + 2 * bx.ng[e];
+      } else {
+        lo[e] = 0;
+        len[e] = bx.n[e];
+      }
     }
-  }
-  long long total = 2LL * len[0] * len[1] * len[2];
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
-    long long r = id;
-    int a0 = (int)(r % len[0]);
-    r /= len[0];
-    int a1 = (int)(r % len[1]);
-    r /= len[1];
-    int a2 = (int)(r % len[2]);
-    int side = (int)(r / len[2]);
-    int c[3] = {a0 + lo[0], a1 + lo[1], a2 + lo[2]};
-    int g = c[d];
-    int dst[3] = {c[0], c[1], c[2]}, src[3] = {c[0], c[1], c[2]};
-    int bc = p.bc[2 * d + side];
-    dst[d] = side == 0 ? -1 - g : p.n[d] + g;
-    double sgn = 1.0;
-    int clamp = 0;
-    if (bc == 0) {
-      src[d] = side == 0 ? p.n[d] - 1 - g : g;
-    } else if (bc == 1) {
-      src[d] = side == 0 ? 0 : p.n[d] - 1;
-      clamp = side == 0 ? -1 : 1;
-    } else {
-      src[d] = side == 0 ? g : p.n[d] - 1 - g;
-      if (p.n[2] > 1) src[2] = (c[2] + p.n[2] / 2) % p.n[2];
-      sgn = -1.0;
-    }
-    long long s = cell_index(p, src[0], src[1], src[2]);
-    long long t = cell_index(p, dst[0], dst[1], dst[2]);
+    long long total = 2LL * len[0] * len[1] * len[2];
+    for (long long id = HR_TID; id < total; id += HR_STRIDE) {
+      long long r = id;
+      int a0 = (int)(r % len[0]);
+      r /= len[0];
+      int a1 = (int)(r % len[1]);
+      r /= len[1];
+      int a2 = (int)(r % len[2]);
+      int side = (int)(r / len[2]);
+      int c[3] = {a0 + lo[0], a1 + lo[1], a2 + lo[2]};
+      int g = c[d];
+      int dst[3] = {c[0], c[1], c[2]}, src[3] = {c[0], c[1], c[2]};
+      int bc = bx.bc[2 * d + side];
+      dst[d] = side == 0 ? -1 - g : bx.n[d] + g;
+      double sgn = 1.0;
+      int clamp = 0;
+      if (bc == 0) {
+        src[d] = side == 0 ? bx.n[d] - 1 - g : g;
+      } else if (bc == 1) {
+        src[d] = side == 0 ? 0 : bx.n[d] - 1;
+        clamp = side == 0 ? -1 : 1;
+      } else {
+        src[d] = side == 0 ? g : bx.n[d] - 1 - g;
+        if (bx.n[2] > 1) src[2] = (c[2] + bx.n[2] / 2) % bx.n[2];
+        sgn = -1.0;
+      }
+      long long s = cell_index(bx, src[0], src[1], src[2]);
+      long long t = cell_index(bx, dst[0], dst[1], dst[2]);
 #pragma unroll
-    for (int q = 0; q < NPR; ++q) {
-      double v = P[q * p.ntot + s];
-      if (q == U1 + d || q == B1 + d || q == UR1 + d) v *= sgn;
-      if (clamp != 0 && (q == U1 + d || q == UR1 + d)) v = clamp < 0 ? fmin(v, 0.0) : fmax(v, 0.0);
-      P[q * p.ntot + t] = v;
+      for (int q = 0; q < NPR; ++q) {
+        double v = P[q * bx.ntot + s];
+        if (q == U1 + d || q == B1 + d || q == UR1 + d) v *= sgn;
+        if (clamp != 0 && (q == U1 + d || q == UR1 + d)) v = clamp < 0 ? fmin(v, 0.0) : fmax(v, 0.0);
+        P[q * bx.ntot + t] = v;
+      }
+      if (K) K[t] = K[s];
     }
   }
 }
@@ -105,29 +129,34 @@ static __global__ void k_bc_fill(DevParams p, double* __restrict__ P, int d) {
 // sqrt(-g) u^d (gas, radiation) and the weight w_d = min(1, 2 tau_d) of the
 // optical depth of the cell along d (Sec. 4.3).
 template <int MET, typename R>
-__global__ void k_prep(DevParams p, const double* __restrict__ P, R* __restrict__ aux) {
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < p.ntot;
-       t += (long long)gridDim.x * blockDim.x) {
-    long long r = t;
-    int i = (int)(r % p.N[0]) - p.ng[0];
-    r /= p.N[0];
-    int j = (int)(r % p.N[1]) - p.ng[1];
-    int k = (int)(r / p.N[1]) - p.ng[2];
-    (void)k;
-    Geo<MET, R> g = make_geo<MET, R>(p, R(xcen(p, 0, i)), R(xcen(p, 1, j)));
-    R ucon[4], ucov[4], gm, urc[4], urv[4], gr;
-    fourvel<MET, R>(g, R(P[U1 * p.ntot + t]), R(P[U2 * p.ntot + t]), R(P[U3 * p.ntot + t]), ucon, ucov, &gm);
-    fourvel<MET, R>(g, R(P[UR1 * p.ntot + t]), R(P[UR2 * p.ntot + t]), R(P[UR3 * p.ntot + t]), urc, urv, &gr);
-    R kabs, ksca;
-    opacity<R>(p, R(P[RHO * p.ntot + t]), R(P[UU * p.ntot + t]), &kabs, &ksca);
-    aux[t] = g.gdet;
+__global__ void k_prep(DevParams p, const BoxGeo* __restrict__ boxes, int nbox,
+                       const double* __restrict__ P0, const double* __restrict__ K0,
+                       R* __restrict__ aux0) {
+  for (int bi = 0; bi < nbox; ++bi) {
+    const BoxGeo& bx = boxes[bi];
+    const double* P = P0 + 12 * bx.coff;
+    const double* K = K0 + bx.coff;
+    R* aux = aux0 + 10 * bx.coff;
+    for (long long t = HR_TID; t < bx.ntot; t += HR_STRIDE) {
+      long long r = t;
+      int i = (int)(r % bx.N[0]) - bx.ng[0];
+      r /= bx.N[0];
+      int j = (int)(r % bx.N[1]) - bx.ng[1];
+      Geo<MET, R> g = make_geo<MET, R>(p, R(xcen(bx, 0, i)), R(xcen(bx, 1, j)));
+      R ucon[4], ucov[4], gm, urc[4], urv[4], gr;
+      fourvel<MET, R>(g, R(P[U1 * bx.ntot + t]), R(P[U2 * bx.ntot + t]), R(P[U3 * bx.ntot + t]), ucon, ucov, &gm);
+      fourvel<MET, R>(g, R(P[UR1 * bx.ntot + t]), R(P[UR2 * bx.ntot + t]), R(P[UR3 * bx.ntot + t]), urc, urv, &gr);
+      R kabs, ksca;
+      opacity<R>(p, R(P[RHO * bx.ntot + t]), R(P[UU * bx.ntot + t]), R(kfield(p, K, t)), &kabs, &ksca);
+      aux[t] = g.gdet;
 #pragma unroll
-    for (int d = 1; d <= 3; ++d) {
-      aux[(1 + 3 * (d - 1)) * p.ntot + t] = g.gdet * ucon[d];
-      aux[(2 + 3 * (d - 1)) * p.ntot + t] = g.gdet * urc[d];
-      R tau = (kabs + ksca) * sqrt(g.gdd(d)) * R(p.dx[d - 1]);
-      R w = R(2) * tau;
-      aux[(3 + 3 * (d - 1)) * p.ntot + t] = w < R(1) ? w : R(1);
+      for (int d = 1; d <= 3; ++d) {
+        aux[(1 + 3 * (d - 1)) * bx.ntot + t] = g.gdet * ucon[d];
+        aux[(2 + 3 * (d - 1)) * bx.ntot + t] = g.gdet * urc[d];
+        R tau = (kabs + ksca) * sqrt(g.gdd(d)) * R(bx.dx[d - 1]);
+        R w = R(2) * tau;
+        aux[(3 + 3 * (d - 1)) * bx.ntot + t] = w < R(1) ? w : R(1);
+      }
     }
   }
 }
@@ -163,54 +192,60 @@ __device__ __forceinline__ R ftilde(const FlatCell<R>* c, int m, bool gas, R w) 
 }
 
 template <typename R>
-__global__ void k_flatten(DevParams p, const double* __restrict__ P, const R* __restrict__ aux,
-                          R* __restrict__ flat, int d) {
-  int len[3], off[3];
-  for (int e = 0; e < 3; ++e) {
-    if (p.n[e] > 1) {
-      len[e] = p.n[e] + 2;
-      off[e] = -1;
-    } else {
-      len[e] = 1;
-      off[e] = 0;
+__global__ void k_flatten(DevParams p, const BoxGeo* __restrict__ boxes, int nbox,
+                          const double* __restrict__ P0, const R* __restrict__ aux0,
+                          R* __restrict__ flat0, int d) {
+  for (int bi = 0; bi < nbox; ++bi) {
+    const BoxGeo& bx = boxes[bi];
+    const double* P = P0 + 12 * bx.coff;
+    const R* aux = aux0 + 10 * bx.coff;
+    R* flat = flat0 + 2 * bx.coff;
+    int len[3], off[3];
+    for (int e = 0; e < 3; ++e) {
+      if (bx.n[e] > 1) {
+        len[e] = bx.n[e] + 2;
+        off[e] = -1;
+      } else {
+        len[e] = 1;
+        off[e] = 0;
+      }
     }
-  }
-  long long total = (long long)len[0] * len[1] * len[2];
-  const long long st = p.str[d];
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
-    long long r = id;
-    int i = (int)(r % len[0]) + off[0];
-    r /= len[0];
-    int j = (int)(r % len[1]) + off[1];
-    int k = (int)(r / len[1]) + off[2];
-    long long t = cell_index(p, i, j, k);
-    FlatCell<R> c[7];
+    long long total = (long long)len[0] * len[1] * len[2];
+    const long long st = bx.str[d];
+    for (long long id = HR_TID; id < total; id += HR_STRIDE) {
+      long long r = id;
+      int i = (int)(r % len[0]) + off[0];
+      r /= len[0];
+      int j = (int)(r % len[1]) + off[1];
+      int k = (int)(r / len[1]) + off[2];
+      long long t = cell_index(bx, i, j, k);
+      FlatCell<R> c[7];
 #pragma unroll
-    for (int m = 0; m < 7; ++m) {
-      long long cm = t + (m - 3) * st;
-      c[m].pg = R((p.gam - 1.0) * P[UU * p.ntot + cm]);
-      c[m].pr = R(P[ER * p.ntot + cm] * (1.0 / 3.0));
-      c[m].vg = aux[(1 + 3 * d) * p.ntot + cm];
-      c[m].vr = aux[(2 + 3 * d) * p.ntot + cm];
-      c[m].w = aux[(3 + 3 * d) * p.ntot + cm];
+      for (int m = 0; m < 7; ++m) {
+        long long cm = t + (m - 3) * st;
+        c[m].pg = R((p.gam - 1.0) * P[UU * bx.ntot + cm]);
+        c[m].pr = R(P[ER * bx.ntot + cm] * (1.0 / 3.0));
+        c[m].vg = aux[(1 + 3 * d) * bx.ntot + cm];
+        c[m].vr = aux[(2 + 3 * d) * bx.ntot + cm];
+        c[m].w = aux[(3 + 3 * d) * bx.ntot + cm];
+      }
+      const R w = c[3].w;
+      R g0 = ftilde<R>(c, 3, true, w), r0 = ftilde<R>(c, 3, false, w);
+      R pg1 = c[4].pg + w * c[4].pr, pgm = c[2].pg + w * c[2].pr;
+      R pr1 = c[4].pr + w * c[4].pg, prm = c[2].pr + w * c[2].pg;
+      int sg = (pg1 - pgm) < R(0) ? 1 : -1;
+      int sr = (pr1 - prm) < R(0) ? 1 : -1;
+      R gn = ftilde<R>(c, 3 + sg, true, c[3 + sg].w);
+      R rn = ftilde<R>(c, 3 + sr, false, c[3 + sr].w);
+      R fg = g0 > gn ? g0 : gn;
+      R fr = r0 > rn ? r0 : rn;
+      R mx = fg > fr ? fg : fr;
+      R Fg = (R(1) - w) * fg + w * mx;
+      R Fr = (R(1) - w) * fr + w * mx;
+      R og = flat[t], orr = flat[bx.ntot + t];
+      flat[t] = Fg > og ? Fg : og;
+      flat[bx.ntot + t] = Fr > orr ? Fr : orr;
     }
-    const R w = c[3].w;
-    R g0 = ftilde<R>(c, 3, true, w), r0 = ftilde<R>(c, 3, false, w);
-    R pg1 = c[4].pg + w * c[4].pr, pgm = c[2].pg + w * c[2].pr;
-    R pr1 = c[4].pr + w * c[4].pg, prm = c[2].pr + w * c[2].pg;
-    int sg = (pg1 - pgm) < R(0) ? 1 : -1;
-    int sr = (pr1 - prm) < R(0) ? 1 : -1;
-    R gn = ftilde<R>(c, 3 + sg, true, c[3 + sg].w);
-    R rn = ftilde<R>(c, 3 + sr, false, c[3 + sr].w);
-    R fg = g0 > gn ? g0 : gn;
-    R fr = r0 > rn ? r0 : rn;
-    R mx = fg > fr ? fg : fr;
-    R Fg = (R(1) - w) * fg + w * mx;
-    R Fr = (R(1) - w) * fr + w * mx;
-    R og = flat[t], orr = flat[p.ntot + t];
-    flat[t] = Fg > og ? Fg : og;
-    flat[p.ntot + t] = Fr > orr ? Fr : orr;
   }
 }
 
@@ -262,59 +297,65 @@ __device__ __forceinline__ void ppm_cell(const R s[5], R chi, R* aL, R* aR) {
 // the Kerr-Schild grid the velocity and field components are reconstructed
 // as sqrt(-g) times the primitive (Sec. 4.3).
 template <int MET, typename R, int d>
-__global__ void __launch_bounds__(256) k_edges(DevParams p, const double* __restrict__ P,
-                                               const R* __restrict__ aux, const R* __restrict__ flat,
-                                               R* __restrict__ E) {
-  int len[3], off[3];
-  for (int e = 0; e < 3; ++e) {
-    if (p.n[e] > 1) {
-      len[e] = p.n[e] + 2;
-      off[e] = -1;
-    } else {
-      len[e] = 1;
-      off[e] = 0;
-    }
-  }
-  long long total = (long long)len[0] * len[1] * len[2];
-  const long long st = p.str[d];
+__global__ void __launch_bounds__(256) k_edges(DevParams p, const BoxGeo* __restrict__ boxes, int nbox,
+                                               const double* __restrict__ P0, const R* __restrict__ aux0,
+                                               const R* __restrict__ flat0, R* __restrict__ E0) {
   const bool weighted = (MET == KS) && (d != 1);
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
-    long long r = id;
-    int i = (int)(r % len[0]) + off[0];
-    r /= len[0];
-    int j = (int)(r % len[1]) + off[1];
-    int k = (int)(r / len[1]) + off[2];
-    long long t = cell_index(p, i, j, k);
-    R chg = R(0), chr = R(0);
-    if (p.recon == 0) {
-      chg = flat[t];
-      chr = flat[p.ntot + t];
-    }
-    R gw[5];
-    if (weighted) {
-#pragma unroll
-      for (int m = 0; m < 5; ++m) gw[m] = aux[t + (m - 2) * st];
-    }
-#pragma unroll
-    for (int q = 0; q < NPR; ++q) {
-      const bool wq = weighted && ((q >= U1 && q <= B3) || q >= UR1);
-      R s[5];
-#pragma unroll
-      for (int m = 0; m < 5; ++m) {
-        R v = R(P[q * p.ntot + t + (m - 2) * st]);
-        s[m] = wq ? gw[m] * v : v;
-      }
-      R aL, aR;
-      if (p.recon == 0) {
-        ppm_cell<R>(s, q < ER ? chg : chr, &aL, &aR);
+  for (int bi = 0; bi < nbox; ++bi) {
+    const BoxGeo& bx = boxes[bi];
+    const double* P = P0 + 12 * bx.coff;
+    const R* aux = aux0 + 10 * bx.coff;
+    const R* flat = flat0 + 2 * bx.coff;
+    R* E = E0 + 24 * bx.coff;
+    int len[3], off[3];
+    for (int e = 0; e < 3; ++e) {
+      if (bx.n[e] > 1) {
+        len[e] = bx.n[e] + 2;
+        off[e] = -1;
       } else {
-        R dq = mc_slope<R>(s[1], s[2], s[3]);
-        aL = s[2] - R(0.5) * dq;
-        aR = s[2] + R(0.5) * dq;
+        len[e] = 1;
+        off[e] = 0;
       }
-      E[q * p.ntot + t] = aL;
-      E[(NPR + q) * p.ntot + t] = aR;
+    }
+    long long total = (long long)len[0] * len[1] * len[2];
+    const long long st = bx.str[d];
+    for (long long id = HR_TID; id < total; id += HR_STRIDE) {
+      long long r = id;
+      int i = (int)(r % len[0]) + off[0];
+      r /= len[0];
+      int j = (int)(r % len[1]) + off[1];
+      int k = (int)(r / len[1]) + off[2];
+      long long t = cell_index(bx, i, j, k);
+      R chg = R(0), chr = R(0);
+      if (p.recon == 0) {
+        chg = flat[t];
+        chr = flat[bx.ntot + t];
+      }
+      R gw[5];
+      if (weighted) {
+#pragma unroll
+        for (int m = 0; m < 5; ++m) gw[m] = aux[t + (m - 2) * st];
+      }
+#pragma unroll
+      for (int q = 0; q < NPR; ++q) {
+        const bool wq = weighted && ((q >= U1 && q <= B3) || q >= UR1);
+        R s[5];
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+          R v = R(P[q * bx.ntot + t + (m - 2) * st]);
+          s[m] = wq ? gw[m] * v : v;
+        }
+        R aL, aR;
+        if (p.recon == 0) {
+          ppm_cell<R>(s, q < ER ? chg : chr, &aL, &aR);
+        } else {
+          R dq = mc_slope<R>(s[1], s[2], s[3]);
+          aL = s[2] - R(0.5) * dq;
+          aR = s[2] + R(0.5) * dq;
+        }
+        E[q * bx.ntot + t] = aL;
+        E[(NPR + q) * bx.ntot + t] = aR;
+      }
     }
   }
 }
@@ -328,100 +369,109 @@ __global__ void __launch_bounds__(256) k_edges(DevParams p, const double* __rest
 // speeds.  The direction is a template parameter so that every index into a
 // 4-vector or the primitive array is resolved at compile time.
 template <int MET, typename R, int d>
-__global__ void __launch_bounds__(128) k_face(DevParams p, const R* __restrict__ E,
-                                              R* __restrict__ F, R* __restrict__ spd) {
-  int len[3], off[3];
-  for (int e = 0; e < 3; ++e) {
-    if (e == d) {
-      len[e] = p.n[e] + 1;
-      off[e] = 0;
-    } else if (p.n[e] > 1) {
-      len[e] = p.n[e] + 2;
-      off[e] = -1;
-    } else {
-      len[e] = 1;
-      off[e] = 0;
-    }
-  }
-  long long total = (long long)len[0] * len[1] * len[2];
-  const long long st = p.str[d];
+__global__ void __launch_bounds__(128) k_face(DevParams p, const BoxGeo* __restrict__ boxes, int nbox,
+                                              const R* __restrict__ E0, const double* __restrict__ K0,
+                                              R* __restrict__ F0, R* __restrict__ spd0) {
   const bool weighted = (MET == KS) && (d != 1);
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
-    long long r = id;
-    int ii[3];
-    ii[0] = (int)(r % len[0]) + off[0];
-    r /= len[0];
-    ii[1] = (int)(r % len[1]) + off[1];
-    ii[2] = (int)(r / len[1]) + off[2];
-    long long t = cell_index(p, ii[0], ii[1], ii[2]);
-    const int f = ii[d];
-    if (MET == KS && d == 1 && ((f == 0 && p.bc[2] == 2) || (f == p.n[1] && p.bc[3] == 2))) {
-#pragma unroll
-      for (int q = 0; q < NPR; ++q) F[q * p.ntot + t] = R(0);
-      spd[t] = R(0);
-      continue;
+  for (int bi = 0; bi < nbox; ++bi) {
+    const BoxGeo& bx = boxes[bi];
+    const R* E = E0 + 24 * bx.coff;
+    const double* K = K0 + bx.coff;
+    R* F = F0 + 12 * bx.coff;
+    R* spd = spd0 + bx.coff;
+    int len[3], off[3];
+    for (int e = 0; e < 3; ++e) {
+      if (e == d) {
+        len[e] = bx.n[e] + 1;
+        off[e] = 0;
+      } else if (bx.n[e] > 1) {
+        len[e] = bx.n[e] + 2;
+        off[e] = -1;
+      } else {
+        len[e] = 1;
+        off[e] = 0;
+      }
     }
-    R xf[3];
-    for (int e = 0; e < 3; ++e) xf[e] = R(p.x0[e] + (ii[e] + (e == d ? 0.0 : 0.5)) * p.dx[e]);
-    Geo<MET, R> g = make_geo<MET, R>(p, xf[0], xf[1]);
-    const R igf = weighted ? R(1) / g.gdet : R(1);
-    R PL[NPR], PR[NPR];
+    long long total = (long long)len[0] * len[1] * len[2];
+    const long long st = bx.str[d];
+    const R dxd = R(bx.dx[d]);
+    for (long long id = HR_TID; id < total; id += HR_STRIDE) {
+      long long r = id;
+      int ii[3];
+      ii[0] = (int)(r % len[0]) + off[0];
+      r /= len[0];
+      ii[1] = (int)(r % len[1]) + off[1];
+      ii[2] = (int)(r / len[1]) + off[2];
+      long long t = cell_index(bx, ii[0], ii[1], ii[2]);
+      const int f = ii[d];
+      if (MET == KS && d == 1 && ((f == 0 && bx.bc[2] == 2) || (f == bx.n[1] && bx.bc[3] == 2))) {
 #pragma unroll
-    for (int q = 0; q < NPR; ++q) {
-      const bool wq = weighted && ((q >= U1 && q <= B3) || q >= UR1);
-      R aR = E[(NPR + q) * p.ntot + t - st];  // upper edge of cell f-1
-      R bL = E[q * p.ntot + t];               // lower edge of cell f
-      PL[q] = wq ? aR * igf : aR;
-      PR[q] = wq ? bL * igf : bL;
-    }
-    R sL[4], sR[4];
-    face_speeds<MET, R>(p, g, d + 1, PL, sL);
-    face_speeds<MET, R>(p, g, d + 1, PR, sR);
-    R cmaxg = fmax(R(0), fmax(sL[1], sR[1]));
-    R cming = -fmin(R(0), fmin(sL[0], sR[0]));
-    R cmaxr = fmax(R(0), fmax(sL[3], sR[3]));
-    R cminr = -fmin(R(0), fmin(sL[2], sR[2]));
-    // weights of (F_L, U_L) and (F_R, U_R) in the flux, gas and radiation groups
-    R fLg, uLg, fRg, uRg, fLr, uLr, fRr, uRr;
-    if (p.flux == 0) {  // LAXF: 1/2 (F_L + F_R - c (U_R - U_L))
-      R cg = cmaxg > cming ? cmaxg : cming, cr = cmaxr > cminr ? cmaxr : cminr;
-      fLg = fRg = fLr = fRr = R(0.5);
-      uLg = R(0.5) * cg;
-      uRg = -uLg;
-      uLr = R(0.5) * cr;
-      uRr = -uLr;
-    } else {  // HLL: (c- F_R + c+ F_L - c- c+ (U_R - U_L)) / (c- + c+)
-      R sg = cmaxg + cming, sr = cmaxr + cminr;
-      if (sg > R(0)) {
-        R isg = R(1) / sg;
-        fLg = cmaxg * isg;
-        fRg = cming * isg;
-        uLg = cming * cmaxg * isg;
+        for (int q = 0; q < NPR; ++q) F[q * bx.ntot + t] = R(0);
+        spd[t] = R(0);
+        continue;
+      }
+      R xf[3];
+      for (int e = 0; e < 3; ++e) xf[e] = R(bx.x0[e] + (ii[e] + (e == d ? 0.0 : 0.5)) * bx.dx[e]);
+      Geo<MET, R> g = make_geo<MET, R>(p, xf[0], xf[1]);
+      const R igf = weighted ? R(1) / g.gdet : R(1);
+      R PL[NPR], PR[NPR];
+#pragma unroll
+      for (int q = 0; q < NPR; ++q) {
+        const bool wq = weighted && ((q >= U1 && q <= B3) || q >= UR1);
+        R aR = E[(NPR + q) * bx.ntot + t - st];  // upper edge of cell f-1
+        R bL = E[q * bx.ntot + t];               // lower edge of cell f
+        PL[q] = wq ? aR * igf : aR;
+        PR[q] = wq ? bL * igf : bL;
+      }
+      const R kL = R(kfield(p, K, t - st)), kR = R(kfield(p, K, t));
+      R sL[4], sR[4];
+      face_speeds<MET, R>(p, g, d + 1, dxd, kL, PL, sL);
+      face_speeds<MET, R>(p, g, d + 1, dxd, kR, PR, sR);
+      R cmaxg = fmax(R(0), fmax(sL[1], sR[1]));
+      R cming = -fmin(R(0), fmin(sL[0], sR[0]));
+      R cmaxr = fmax(R(0), fmax(sL[3], sR[3]));
+      R cminr = -fmin(R(0), fmin(sL[2], sR[2]));
+      // weights of (F_L, U_L) and (F_R, U_R) in the flux, gas and radiation groups
+      R fLg, uLg, fRg, uRg, fLr, uLr, fRr, uRr;
+      if (p.flux == 0) {  // LAXF: 1/2 (F_L + F_R - c (U_R - U_L))
+        R cg = cmaxg > cming ? cmaxg : cming, cr = cmaxr > cminr ? cmaxr : cminr;
+        fLg = fRg = fLr = fRr = R(0.5);
+        uLg = R(0.5) * cg;
         uRg = -uLg;
-      } else {
-        fLg = fRg = R(0.5);
-        uLg = uRg = R(0);
-      }
-      if (sr > R(0)) {
-        R isr = R(1) / sr;
-        fLr = cmaxr * isr;
-        fRr = cminr * isr;
-        uLr = cminr * cmaxr * isr;
+        uLr = R(0.5) * cr;
         uRr = -uLr;
-      } else {
-        fLr = fRr = R(0.5);
-        uLr = uRr = R(0);
+      } else {  // HLL: (c- F_R + c+ F_L - c- c+ (U_R - U_L)) / (c- + c+)
+        R sg = cmaxg + cming, sr = cmaxr + cminr;
+        if (sg > R(0)) {
+          R isg = R(1) / sg;
+          fLg = cmaxg * isg;
+          fRg = cming * isg;
+          uLg = cming * cmaxg * isg;
+          uRg = -uLg;
+        } else {
+          fLg = fRg = R(0.5);
+          uLg = uRg = R(0);
+        }
+        if (sr > R(0)) {
+          R isr = R(1) / sr;
+          fLr = cmaxr * isr;
+          fRr = cminr * isr;
+          uLr = cminr * cmaxr * isr;
+          uRr = -uLr;
+        } else {
+          fLr = fRr = R(0.5);
+          uLr = uRr = R(0);
+        }
       }
+      R out[NPR];
+#pragma unroll
+      for (int q = 0; q < NPR; ++q) out[q] = R(0);
+      face_accum<MET, R>(p, g, d + 1, PL, fLg, uLg, fLr, uLr, out);
+      face_accum<MET, R>(p, g, d + 1, PR, fRg, uRg, fRr, uRr, out);
+#pragma unroll
+      for (int q = 0; q < NPR; ++q) F[q * bx.ntot + t] = (q == B1 + d) ? R(0) : out[q];
+      spd[t] = fmax(fmax(cmaxg, cming), fmax(cmaxr, cminr));
     }
-    R out[NPR];
-#pragma unroll
-    for (int q = 0; q < NPR; ++q) out[q] = R(0);
-    face_accum<MET, R>(p, g, d + 1, PL, fLg, uLg, fLr, uLr, out);
-    face_accum<MET, R>(p, g, d + 1, PR, fRg, uRg, fRr, uRr, out);
-#pragma unroll
-    for (int q = 0; q < NPR; ++q) F[q * p.ntot + t] = (q == B1 + d) ? R(0) : out[q];
-    spd[t] = fmax(fmax(cmaxg, cming), fmax(cmaxr, cminr));
   }
 }
 
@@ -431,54 +481,60 @@ __global__ void __launch_bounds__(128) k_face(DevParams p, const R* __restrict__
 // the polar axis; then F_a[B_b] and F_b[B_a] become averages of the two
 // adjacent edge EMFs (with opposite signs).
 template <typename R>
-__global__ void k_emf(DevParams p, const R* __restrict__ Fa, const R* __restrict__ Fb,
-                      R* __restrict__ emf, int a, int b) {
-  int len[3];
-  for (int e = 0; e < 3; ++e) len[e] = p.n[e] + ((e == a || e == b) ? 1 : 0);
-  long long total = (long long)len[0] * len[1] * len[2];
-  const long long sa = p.str[a], sb = p.str[b];
-  const R* fab = Fa + (B1 + b) * p.ntot;
-  const R* fba = Fb + (B1 + a) * p.ntot;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < total;
-       id += (long long)gridDim.x * blockDim.x) {
-    long long r = id;
-    int ii[3];
-    ii[0] = (int)(r % len[0]);
-    r /= len[0];
-    ii[1] = (int)(r % len[1]);
-    ii[2] = (int)(r / len[1]);
-    long long t = cell_index(p, ii[0], ii[1], ii[2]);
-    bool pole = p.metric == KS && (a == 1 || b == 1) &&
-                ((ii[1] == 0 && p.bc[2] == 2) || (ii[1] == p.n[1] && p.bc[3] == 2));
-    emf[t] = pole ? R(0) : R(0.25) * (fab[t] + fab[t - sb] - fba[t] - fba[t - sa]);
+__global__ void k_emf(DevParams p, const BoxGeo* __restrict__ boxes, int nbox, const R* __restrict__ Fa0,
+                      const R* __restrict__ Fb0, R* __restrict__ emf0, int a, int b) {
+  for (int bi = 0; bi < nbox; ++bi) {
+    const BoxGeo& bx = boxes[bi];
+    const R* fab = Fa0 + 12 * bx.coff + (B1 + b) * bx.ntot;
+    const R* fba = Fb0 + 12 * bx.coff + (B1 + a) * bx.ntot;
+    R* emf = emf0 + bx.coff;
+    int len[3];
+    for (int e = 0; e < 3; ++e) len[e] = bx.n[e] + ((e == a || e == b) ? 1 : 0);
+    long long total = (long long)len[0] * len[1] * len[2];
+    const long long sa = bx.str[a], sb = bx.str[b];
+    for (long long id = HR_TID; id < total; id += HR_STRIDE) {
+      long long r = id;
+      int ii[3];
+      ii[0] = (int)(r % len[0]);
+      r /= len[0];
+      ii[1] = (int)(r % len[1]);
+      ii[2] = (int)(r / len[1]);
+      long long t = cell_index(bx, ii[0], ii[1], ii[2]);
+      bool pole = p.metric == KS && (a == 1 || b == 1) &&
+                  ((ii[1] == 0 && bx.bc[2] == 2) || (ii[1] == bx.n[1] && bx.bc[3] == 2));
+      emf[t] = pole ? R(0) : R(0.25) * (fab[t] + fab[t - sb] - fba[t] - fba[t - sa]);
+    }
   }
 }
 
 template <typename R>
-__global__ void k_ct(DevParams p, const R* __restrict__ emf, R* __restrict__ Fa, R* __restrict__ Fb,
-                     int a, int b) {
-  // two index spaces: a-faces (a in [0,n_a], b in [0,n_b)) then b-faces
-  int la[3], lb[3];
-  for (int e = 0; e < 3; ++e) {
-    la[e] = p.n[e] + (e == a ? 1 : 0);
-    lb[e] = p.n[e] + (e == b ? 1 : 0);
-  }
-  long long na = (long long)la[0] * la[1] * la[2];
-  long long nb = (long long)lb[0] * lb[1] * lb[2];
-  const long long sa = p.str[a], sb = p.str[b];
-  R* fab = Fa + (B1 + b) * p.ntot;
-  R* fba = Fb + (B1 + a) * p.ntot;
-  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < na + nb;
-       id += (long long)gridDim.x * blockDim.x) {
-    const int* L = id < na ? la : lb;
-    long long r = id < na ? id : id - na;
-    int i0 = (int)(r % L[0]);
-    r /= L[0];
-    int i1 = (int)(r % L[1]);
-    int i2 = (int)(r / L[1]);
-    long long t = cell_index(p, i0, i1, i2);
-    if (id < na) fab[t] = R(0.5) * (emf[t] + emf[t + sb]);
-    else fba[t] = R(-0.5) * (emf[t] + emf[t + sa]);
+__global__ void k_ct(DevParams p, const BoxGeo* __restrict__ boxes, int nbox, const R* __restrict__ emf0,
+                     R* __restrict__ Fa0, R* __restrict__ Fb0, int a, int b) {
+  for (int bi = 0; bi < nbox; ++bi) {
+    const BoxGeo& bx = boxes[bi];
+    R* fab = Fa0 + 12 * bx.coff + (B1 + b) * bx.ntot;
+    R* fba = Fb0 + 12 * bx.coff + (B1 + a) * bx.ntot;
+    const R* emf = emf0 + bx.coff;
+    // two index spaces: a-faces (a in [0,n_a], b in [0,n_b)) then b-faces
+    int la[3], lb[3];
+    for (int e = 0; e < 3; ++e) {
+      la[e] = bx.n[e] + (e == a ? 1 : 0);
+      lb[e] = bx.n[e] + (e == b ? 1 : 0);
+    }
+    long long na = (long long)la[0] * la[1] * la[2];
+    long long nb = (long long)lb[0] * lb[1] * lb[2];
+    const long long sa = bx.str[a], sb = bx.str[b];
+    for (long long id = HR_TID; id < na + nb; id += HR_STRIDE) {
+      const int* L = id < na ? la : lb;
+      long long r = id < na ? id : id - na;
+      int i0 = (int)(r % L[0]);
+      r /= L[0];
+      int i1 = (int)(r % L[1]);
+      int i2 = (int)(r / L[1]);
+      long long t = cell_index(bx, i0, i1, i2);
+      if (id < na) fab[t] = R(0.5) * (emf[t] + emf[t + sb]);
+      else fba[t] = R(-0.5) * (emf[t] + emf[t + sa]);
+    }
   }
 }
 
@@ -613,129 +669,148 @@ __device__ __forceinline__ double qform(const MetricDeriv& m, int n, const doubl
 // U* = a_s U^n + b_s (U(P_s) + dt X) (Sec. 4.1), the PMHD Newton solve, floors.
 // Zones whose PMHD error exceeds 1e-9 go to the retry queue.
 template <int MET, typename R>
-__global__ void __launch_bounds__(128) k_update(DevParams p, Bufs b, int stage) {
+__device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx, int bi, const Bufs& b,
+                                           int stage) {
   const double A = stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0);
   const double Bc = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
-  const double dt = *b.dt;
-  const R* F0 = (const R*)b.F[0];
-  const R* F1 = (const R*)b.F[1];
-  const R* F2 = (const R*)b.F[2];
-  for (long long z = blockIdx.x * (long long)blockDim.x + threadIdx.x; z < p.nact;
-       z += (long long)gridDim.x * blockDim.x) {
-    long long r = z;
-    int i = (int)(r % p.n[0]);
-    r /= p.n[0];
-    int j = (int)(r % p.n[1]);
-    int k = (int)(r / p.n[1]);
-    long long t = cell_index(p, i, j, k);
-    double x1 = xcen(p, 0, i), x2 = xcen(p, 1, j);
-    Geo<MET, double> g = make_geo<MET, double>(p, x1, x2);
-    double Ps[NPR];
+  {
+    const double dt = b.dt[bi];
+    double* P = b.P + 12 * bx.coff;
+    const double* K = b.K + bx.coff;
+    double* Un = b.Un + 12 * bx.aoff;
+    const R* Fd[3] = {(const R*)b.F[0] + 12 * bx.coff, (const R*)b.F[1] + 12 * bx.coff,
+                      (const R*)b.F[2] + 12 * bx.coff};
+    for (long long z = HR_TID; z < bx.nact; z += HR_STRIDE) {
+      long long r = z;
+      int i = (int)(r % bx.n[0]);
+      r /= bx.n[0];
+      int j = (int)(r % bx.n[1]);
+      int k = (int)(r / bx.n[1]);
+      long long t = cell_index(bx, i, j, k);
+      double x1 = xcen(bx, 0, i), x2 = xcen(bx, 1, j);
+      Geo<MET, double> g = make_geo<MET, double>(p, x1, x2);
+      double Ps[NPR];
 #pragma unroll
-    for (int q = 0; q < NPR; ++q) Ps[q] = b.P[q * p.ntot + t];
-    // U(P_s)
-    double ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq, urc[4], urv[4], gr;
-    fourvel<MET, double>(g, Ps[U1], Ps[U2], Ps[U3], ucon, ucov, &gm);
-    bvec<MET, double>(g, ucon, ucov, Ps[B1], Ps[B2], Ps[B3], bcon, bcov, &bsq);
-    fourvel<MET, double>(g, Ps[UR1], Ps[UR2], Ps[UR3], urc, urv, &gr);
-    const double pg = (p.gam - 1.0) * Ps[UU];
-    const double wb = Ps[RHO] + Ps[UU] + pg + bsq, pt = pg + 0.5 * bsq;
-    const double gd = g.gdet, mt = Ps[RHO] * ucon[0];
-    const double E = Ps[ER], e43 = (4.0 / 3.0) * E;
-    double Us[NPR];
-    Us[0] = gd * mt;
-    Us[1] = gd * (wb * ucon[0] * ucov[0] + pt - bcon[0] * bcov[0] + mt);
+      for (int q = 0; q < NPR; ++q) Ps[q] = P[q * bx.ntot + t];
+      const double kz = kfield(p, K, t);
+      // U(P_s)
+      double ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq, urc[4], urv[4], gr;
+      fourvel<MET, double>(g, Ps[U1], Ps[U2], Ps[U3], ucon, ucov, &gm);
+      bvec<MET, double>(g, ucon, ucov, Ps[B1], Ps[B2], Ps[B3], bcon, bcov, &bsq);
+      fourvel<MET, double>(g, Ps[UR1], Ps[UR2], Ps[UR3], urc, urv, &gr);
+      const double pg = (p.gam - 1.0) * Ps[UU];
+      const double wb = Ps[RHO] + Ps[UU] + pg + bsq, pt = pg + 0.5 * bsq;
+      const double gd = g.gdet, mt = Ps[RHO] * ucon[0];
+      const double E = Ps[ER], e43 = (4.0 / 3.0) * E;
+      double Us[NPR];
+      Us[0] = gd * mt;
+      Us[1] = gd * (wb * ucon[0] * ucov[0] + pt - bcon[0] * bcov[0] + mt);
 #pragma unroll
-    for (int n = 1; n < 4; ++n) Us[1 + n] = gd * (wb * ucon[0] * ucov[n] - bcon[0] * bcov[n]);
-    Us[5] = gd * Ps[B1];
-    Us[6] = gd * Ps[B2];
-    Us[7] = gd * Ps[B3];
-    Us[8] = gd * (e43 * urc[0] * urv[0] + E * (1.0 / 3.0));
+      for (int n = 1; n < 4; ++n) Us[1 + n] = gd * (wb * ucon[0] * ucov[n] - bcon[0] * bcov[n]);
+      Us[5] = gd * Ps[B1];
+      Us[6] = gd * Ps[B2];
+      Us[7] = gd * Ps[B3];
+      Us[8] = gd * (e43 * urc[0] * urv[0] + E * (1.0 / 3.0));
 #pragma unroll
-    for (int n = 1; n < 4; ++n) Us[8 + n] = gd * (e43 * urc[0] * urv[n]);
-    double X[NPR];
+      for (int n = 1; n < 4; ++n) Us[8 + n] = gd * (e43 * urc[0] * urv[n]);
+      double X[NPR];
 #pragma unroll
-    for (int q = 0; q < NPR; ++q) X[q] = 0.0;
-    if constexpr (MET == KS) {
-      MetricDeriv md = ks_derivs(p, x1, x2);
+      for (int q = 0; q < NPR; ++q) X[q] = 0.0;
+      if constexpr (MET == KS) {
+        MetricDeriv md = ks_derivs(p, x1, x2);
 #pragma unroll
-      for (int n = 0; n < 2; ++n) {
-        double qu = qform(md, n, ucon), qb = qform(md, n, bcon), qr = qform(md, n, urc);
-        X[2 + n] = 0.5 * gd * (wb * qu - qb) + pt * md.sg[n];
-        X[9 + n] = 0.5 * gd * e43 * qr + E * (1.0 / 3.0) * md.sg[n];
-      }
-    }
-    // flux divergence
-    const R* Fd[3] = {F0, F1, F2};
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      if (p.n[d] == 1) continue;
-      const long long s = p.str[d];
-      const double idx_ = 1.0 / p.dx[d];
-#pragma unroll
-      for (int q = 0; q < NPR; ++q) {
-        R df = Fd[d][q * p.ntot + t + s] - Fd[d][q * p.ntot + t];
-        X[q] -= double(df) * idx_;
-      }
-    }
-    double Ust[NPR];
-#pragma unroll
-    for (int q = 0; q < NPR; ++q) {
-      double un;
-      if (stage == 0) {
-        b.Un[q * p.nact + z] = Us[q];
-        un = Us[q];
-      } else {
-        un = b.Un[q * p.nact + z];
-      }
-      Ust[q] = A * un + Bc * (Us[q] + dt * X[q]);
-    }
-    // implicit solve
-    const double h = Bc * dt;
-    ImpSys<MET> s;
-    build_sys<MET>(p, g, Ust, h, s);
-    double x0[4] = {Ps[UU], Ps[U1], Ps[U2], Ps[U3]};
-    {
-      double kabs, ksca;
-      opacity<double>(p, Ps[RHO], Ps[UU], &kabs, &ksca);
-      double dl = 0.0;
-#pragma unroll
-      for (int d = 1; d <= 3; ++d)
-        if (p.n[d - 1] > 1) dl = fmax(dl, sqrt(g.gdd(d)) * p.dx[d - 1]);
-      if ((kabs + ksca) * dl < 2.0 / 3.0) {
-        double go[5];
-        double T3[3] = {s.Ts[1], s.Ts[2], s.Ts[3]};
-        if (gas_invert<MET>(p, g, s.Dlab, s.Ts[0], T3, s.B, Ps, 1e-9, go) == 0) {
-          x0[0] = go[1];
-          x0[1] = go[2];
-          x0[2] = go[3];
-          x0[3] = go[4];
+        for (int n = 0; n < 2; ++n) {
+          double qu = qform(md, n, ucon), qb = qform(md, n, bcon), qr = qform(md, n, urc);
+          X[2 + n] = 0.5 * gd * (wb * qu - qb) + pt * md.sg[n];
+          X[9 + n] = 0.5 * gd * e43 * qr + E * (1.0 / 3.0) * md.sg[n];
         }
       }
-    }
-    double bx[4], beT;
-    int steps = newton_pmhd<MET>(p, s, x0, bx, &beT);
-    b.iters[z] += steps;
-    bool accept = beT < 1e-9;
-    if (accept) {
-      double Pn[NPR];
-      pmhd_final<MET>(p, s, bx, Pn);
-      apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn);
+      // flux divergence
 #pragma unroll
-      for (int q = 0; q < NPR; ++q) b.P[q * p.ntot + t] = Pn[q];
-    } else {
-      int slot = atomicAdd(&b.qcount[0], 1);
-      b.qzone[slot] = (int)z;
-      double* qd = b.qdata + (long long)slot * QSTRIDE;
+      for (int d = 0; d < 3; ++d) {
+        if (!p.act[d]) continue;
+        const long long s = bx.str[d];
+        const double idx_ = 1.0 / bx.dx[d];
 #pragma unroll
-      for (int q = 0; q < NPR; ++q) qd[q] = Ust[q];
-      for (int q = 0; q < 4; ++q) qd[12 + q] = isfinite(beT) ? bx[q] : 0.0;
-      qd[16] = beT;
-      qd[17] = h;
+        for (int q = 0; q < NPR; ++q) {
+          R df = Fd[d][q * bx.ntot + t + s] - Fd[d][q * bx.ntot + t];
+          X[q] -= double(df) * idx_;
+        }
+      }
+      double Ust[NPR];
+#pragma unroll
+      for (int q = 0; q < NPR; ++q) {
+        double un;
+        if (stage == 0) {
+          Un[q * bx.nact + z] = Us[q];
+          un = Us[q];
+        } else {
+          un = Un[q * bx.nact + z];
+        }
+        Ust[q] = A * un + Bc * (Us[q] + dt * X[q]);
+      }
+      // implicit solve
+      const double h = Bc * dt;
+      ImpSys<MET> s;
+      build_sys<MET>(p, g, Ust, h, kz, s);
+      double x0[4] = {Ps[UU], Ps[U1], Ps[U2], Ps[U3]};
+      {
+        double kabs, ksca;
+        opacity<double>(p, Ps[RHO], Ps[UU], kz, &kabs, &ksca);
+        double dl = 0.0;
+#pragma unroll
+        for (int d = 1; d <= 3; ++d)
+          if (p.act[d - 1]) dl = fmax(dl, sqrt(g.gdd(d)) * bx.dx[d - 1]);
+        if ((kabs + ksca) * dl < 2.0 / 3.0) {
+          double go[5];
+          double T3[3] = {s.Ts[1], s.Ts[2], s.Ts[3]};
+          if (gas_invert<MET>(p, g, s.Dlab, s.Ts[0], T3, s.B, Ps, 1e-9, go) == 0) {
+            x0[0] = go[1];
+            x0[1] = go[2];
+            x0[2] = go[3];
+            x0[3] = go[4];
+          }
+        }
+      }
+      double bxn[4], beT;
+      int steps = newton_pmhd<MET>(p, s, x0, bxn, &beT);
+      const long long zg = bx.aoff + z;
+      b.iters[zg] += steps;
+      bool accept = beT < 1e-9;
+      if (accept) {
+        double Pn[NPR];
+        pmhd_final<MET>(p, s, bxn, Pn);
+        apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn);
+#pragma unroll
+        for (int q = 0; q < NPR; ++q) P[q * bx.ntot + t] = Pn[q];
+      } else {
+        int slot = atomicAdd(&b.qcount[0], 1);
+        b.qzone[slot] = (int)z;
+        b.qbox[slot] = bi;
+        double* qd = b.qdata + (long long)slot * QSTRIDE;
+#pragma unroll
+        for (int q = 0; q < NPR; ++q) qd[q] = Ust[q];
+        for (int q = 0; q < 4; ++q) qd[12 + q] = isfinite(beT) ? bxn[q] : 0.0;
+        qd[16] = beT;
+        qd[17] = h;
+      }
+      warp_add(&b.stats[ST_PMHD], accept ? 1u : 0u);
+      warp_add(&b.stats[ST_ITERS], (unsigned)steps);
+      warp_add(&b.stats[ST_SOLVES], 1u);
     }
-    warp_add(&b.stats[ST_PMHD], accept ? 1u : 0u);
-    warp_add(&b.stats[ST_ITERS], (unsigned)steps);
-    warp_add(&b.stats[ST_SOLVES], 1u);
+  }
+}
+
+// ONE: a single grid whose geometry travels in the kernel's parameter space
+// (no registers held for it across the Newton solve); otherwise the boxes of
+// a batch, read from the device table.
+template <int MET, typename R, bool ONE>
+__global__ void __launch_bounds__(128) k_update(DevParams p, BoxGeo one, const BoxGeo* __restrict__ boxes,
+                                                int nbox, Bufs b, int stage) {
+  if constexpr (ONE) {
+    update_box<MET, R>(p, one, 0, b, stage);
+  } else {
+    for (int bi = 0; bi < nbox; ++bi) update_box<MET, R>(p, boxes[bi], bi, b, stage);
   }
 }
 
@@ -746,28 +821,32 @@ __global__ void __launch_bounds__(128) k_update(DevParams p, Bufs b, int stage) 
 // the lower-error of the two solutions is kept; e_T > 1e-7 sends the zone to
 // the neighbour-average back-up.
 template <int MET>
-__global__ void __launch_bounds__(128) k_retry(DevParams p, Bufs b) {
+__global__ void __launch_bounds__(128) k_retry(DevParams p, const BoxGeo* __restrict__ boxes, Bufs b) {
   const int nq = b.qcount[0];
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nq; e += gridDim.x * blockDim.x) {
     const long long z = b.qzone[e];
+    const int bi = b.qbox[e];
+    const BoxGeo& bx = boxes[bi];
+    double* P = b.P + 12 * bx.coff;
+    const double* K = b.K + bx.coff;
     const double* qd = b.qdata + (long long)e * QSTRIDE;
     long long r = z;
-    int i = (int)(r % p.n[0]);
-    r /= p.n[0];
-    int j = (int)(r % p.n[1]);
-    int k = (int)(r / p.n[1]);
-    long long t = cell_index(p, i, j, k);
-    double x1 = xcen(p, 0, i), x2 = xcen(p, 1, j);
+    int i = (int)(r % bx.n[0]);
+    r /= bx.n[0];
+    int j = (int)(r % bx.n[1]);
+    int k = (int)(r / bx.n[1]);
+    long long t = cell_index(bx, i, j, k);
+    double x1 = xcen(bx, 0, i), x2 = xcen(bx, 1, j);
     Geo<MET, double> g = make_geo<MET, double>(p, x1, x2);
     double Ust[NPR], Ps[NPR], px[4];
     for (int q = 0; q < NPR; ++q) {
       Ust[q] = qd[q];
-      Ps[q] = b.P[q * p.ntot + t];
+      Ps[q] = P[q * bx.ntot + t];
     }
     for (int q = 0; q < 4; ++q) px[q] = qd[12 + q];
     const double peT = qd[16], h = qd[17];
     ImpSys<MET> s;
-    build_sys<MET>(p, g, Ust, h, s);
+    build_sys<MET>(p, g, Ust, h, kfield(p, K, t), s);
     // PMHD iterate as the error function left it (TYPE2 radiation)
     double Pb[NPR];
     if (isfinite(peT)) {
@@ -793,9 +872,10 @@ __global__ void __launch_bounds__(128) k_retry(DevParams p, Bufs b) {
     xr[0] = e43 * urc[0] * urv[0] + Pg[ER] * (1.0 / 3.0);
     for (int n = 1; n < 4; ++n) xr[n] = e43 * urc[0] * urv[n];
     double gas[5] = {Pg[RHO], Pg[UU], Pg[U1], Pg[U2], Pg[U3]};
-    double bx[4], bgas[5], beT;
-    int steps = newton_urad<MET>(p, s, xr, gas, bx, bgas, &beT);
-    b.iters[z] += steps;
+    double bxn[4], bgas[5], beT;
+    int steps = newton_urad<MET>(p, s, xr, gas, bxn, bgas, &beT);
+    const long long zg = bx.aoff + z;
+    b.iters[zg] += steps;
     double Pn[NPR];
     int method;
     double eT;
@@ -809,8 +889,8 @@ __global__ void __launch_bounds__(128) k_retry(DevParams p, Bufs b) {
       Pn[B2] = s.B[1];
       Pn[B3] = s.B[2];
       double Pr[4];
-      int neg = rad_invert<MET>(p, g, bx, 2, Pr);
-      if (neg) rad_invert<MET>(p, g, bx, 0, Pr);
+      int neg = rad_invert<MET>(p, g, bxn, 2, Pr);
+      if (neg) rad_invert<MET>(p, g, bxn, 0, Pr);
       Pn[ER] = Pr[0];
       Pn[UR1] = Pr[1];
       Pn[UR2] = Pr[2];
@@ -831,13 +911,14 @@ __global__ void __launch_bounds__(128) k_retry(DevParams p, Bufs b) {
     }
     if (eT > 1e-7) method = ST_BACKUP;
     apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn);
-    for (int q = 0; q < NPR; ++q) b.P[q * p.ntot + t] = Pn[q];
+    for (int q = 0; q < NPR; ++q) P[q * bx.ntot + t] = Pn[q];
     unsigned char m = (unsigned char)method;
-    if (m > b.status[z]) b.status[z] = m;
+    if (m > b.status[zg]) b.status[zg] = m;
     if (method == ST_BACKUP) {
-      b.failed[z] = 1;
+      b.failed[zg] = 1;
       int slot = atomicAdd(&b.qcount[1], 1);
       b.fzone[slot] = (int)z;
+      b.fbox[slot] = bi;
       atomicAdd(&b.stats[ST_BACKUP], 1ULL);
     } else if (method == ST_URAD) {
       atomicAdd(&b.stats[ST_URAD], 1ULL);
@@ -851,30 +932,32 @@ __global__ void __launch_bounds__(128) k_retry(DevParams p, Bufs b) {
 // ------------------------------------------------------------- back-up
 // Average of the good active face neighbours (all active neighbours if none
 // is good); B keeps its constrained-transport value (Sec. 4.11).
-static __global__ void k_backup_avg(DevParams p, Bufs b) {
+static __global__ void k_backup_avg(DevParams p, const BoxGeo* __restrict__ boxes, Bufs b) {
   const int nf = b.qcount[1];
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nf; e += gridDim.x * blockDim.x) {
+    const BoxGeo& bx = boxes[b.fbox[e]];
+    const double* P = b.P + 12 * bx.coff;
     long long z = b.fzone[e];
     long long r = z;
     int ii[3];
-    ii[0] = (int)(r % p.n[0]);
-    r /= p.n[0];
-    ii[1] = (int)(r % p.n[1]);
-    ii[2] = (int)(r / p.n[1]);
+    ii[0] = (int)(r % bx.n[0]);
+    r /= bx.n[0];
+    ii[1] = (int)(r % bx.n[1]);
+    ii[2] = (int)(r / bx.n[1]);
     double sg[NPR], sa[NPR];
     for (int q = 0; q < NPR; ++q) sg[q] = sa[q] = 0.0;
     int ng = 0, na = 0;
     for (int d = 0; d < 3; ++d) {
-      if (p.n[d] == 1) continue;
+      if (bx.n[d] == 1) continue;
       for (int side = -1; side <= 1; side += 2) {
         int nb[3] = {ii[0], ii[1], ii[2]};
         nb[d] += side;
-        if (nb[d] < 0 || nb[d] >= p.n[d]) continue;
-        long long zn = ((long long)nb[2] * p.n[1] + nb[1]) * p.n[0] + nb[0];
-        long long tn = cell_index(p, nb[0], nb[1], nb[2]);
-        bool good = !b.failed[zn];
+        if (nb[d] < 0 || nb[d] >= bx.n[d]) continue;
+        long long zn = ((long long)nb[2] * bx.n[1] + nb[1]) * bx.n[0] + nb[0];
+        long long tn = cell_index(bx, nb[0], nb[1], nb[2]);
+        bool good = !b.failed[bx.aoff + zn];
         for (int q = 0; q < NPR; ++q) {
-          double v = b.P[q * p.ntot + tn];
+          double v = P[q * bx.ntot + tn];
           sa[q] += v;
           if (good) sg[q] += v;
         }
@@ -882,9 +965,9 @@ static __global__ void k_backup_avg(DevParams p, Bufs b) {
         if (good) ++ng;
       }
     }
-    long long t = cell_index(p, ii[0], ii[1], ii[2]);
+    long long t = cell_index(bx, ii[0], ii[1], ii[2]);
     for (int q = 0; q < NPR; ++q) {
-      double v = b.P[q * p.ntot + t];
+      double v = P[q * bx.ntot + t];
       if (na > 0 && !(q >= B1 && q <= B3)) v = ng > 0 ? sg[q] / ng : sa[q] / na;
       b.ftmp[(long long)e * NPR + q] = v;
     }
@@ -892,73 +975,76 @@ static __global__ void k_backup_avg(DevParams p, Bufs b) {
 }
 
 template <int MET>
-__global__ void k_backup_apply(DevParams p, Bufs b) {
+__global__ void k_backup_apply(DevParams p, const BoxGeo* __restrict__ boxes, Bufs b) {
   const int nf = b.qcount[1];
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nf; e += gridDim.x * blockDim.x) {
+    const BoxGeo& bx = boxes[b.fbox[e]];
+    double* P = b.P + 12 * bx.coff;
     long long z = b.fzone[e];
     long long r = z;
-    int i = (int)(r % p.n[0]);
-    r /= p.n[0];
-    int j = (int)(r % p.n[1]);
-    int k = (int)(r / p.n[1]);
-    long long t = cell_index(p, i, j, k);
-    double x1 = xcen(p, 0, i), x2 = xcen(p, 1, j);
+    int i = (int)(r % bx.n[0]);
+    r /= bx.n[0];
+    int j = (int)(r % bx.n[1]);
+    int k = (int)(r / bx.n[1]);
+    long long t = cell_index(bx, i, j, k);
+    double x1 = xcen(bx, 0, i), x2 = xcen(bx, 1, j);
     Geo<MET, double> g = make_geo<MET, double>(p, x1, x2);
     double Pn[NPR];
     for (int q = 0; q < NPR; ++q) Pn[q] = b.ftmp[(long long)e * NPR + q];
     apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn);
-    for (int q = 0; q < NPR; ++q) b.P[q * p.ntot + t] = Pn[q];
+    for (int q = 0; q < NPR; ++q) P[q * bx.ntot + t] = Pn[q];
   }
 }
 
 // --------------------------------------------------------------- CFL dt
 // dt = C min_zones 1 / sum_d (v_d/dx_d), v_d = larger face speed of the zone
-// along d.  Block minimum by warp shuffles, then one atomicMin on the bit
-// pattern (positive doubles order like unsigned integers).
+// along d, per grid.  Block minimum by warp shuffles, then one atomicMin on
+// the bit pattern (positive doubles order like unsigned integers).
 template <typename R>
-__global__ void k_cfl(DevParams p, Bufs b) {
-  double best = HUGE_VAL;
-  for (long long z = blockIdx.x * (long long)blockDim.x + threadIdx.x; z < p.nact;
-       z += (long long)gridDim.x * blockDim.x) {
-    long long r = z;
-    int i = (int)(r % p.n[0]);
-    r /= p.n[0];
-    int j = (int)(r % p.n[1]);
-    int k = (int)(r / p.n[1]);
-    long long t = cell_index(p, i, j, k);
-    double sum = 0.0;
-    for (int d = 0; d < 3; ++d) {
-      if (p.n[d] == 1) continue;
-      const R* sp = (const R*)b.spd[d];
-      double v = fmax((double)sp[t], (double)sp[t + p.str[d]]);
-      sum += v / p.dx[d];
-    }
-    if (sum > 0.0) best = fmin(best, 1.0 / sum);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_down_sync(0xffffffffu, best, o));
+__global__ void k_cfl(DevParams p, const BoxGeo* __restrict__ boxes, int nbox, Bufs b) {
   __shared__ double sm[32];
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) sm[w] = best;
-  __syncthreads();
-  if (w == 0) {
-    best = lane < (int)(blockDim.x >> 5) ? sm[lane] : HUGE_VAL;
+  for (int bi = 0; bi < nbox; ++bi) {
+    const BoxGeo& bx = boxes[bi];
+    double best = HUGE_VAL;
+    for (long long z = HR_TID; z < bx.nact; z += HR_STRIDE) {
+      long long r = z;
+      int i = (int)(r % bx.n[0]);
+      r /= bx.n[0];
+      int j = (int)(r % bx.n[1]);
+      int k = (int)(r / bx.n[1]);
+      long long t = cell_index(bx, i, j, k);
+      double sum = 0.0;
+      for (int d = 0; d < 3; ++d) {
+        if (bx.n[d] == 1) continue;
+        const R* sp = (const R*)b.spd[d] + bx.coff;
+        double v = fmax((double)sp[t], (double)sp[t + bx.str[d]]);
+        sum += v / bx.dx[d];
+      }
+      if (sum > 0.0) best = fmin(best, 1.0 / sum);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_down_sync(0xffffffffu, best, o));
-    if (lane == 0 && best < HUGE_VAL) atomicMin(b.dtmin, (unsigned long long)__double_as_longlong(best));
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sm[w] = best;
+    __syncthreads();
+    if (w == 0) {
+      best = lane < (int)(blockDim.x >> 5) ? sm[lane] : HUGE_VAL;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) best = fmin(best, __shfl_down_sync(0xffffffffu, best, o));
+      if (lane == 0 && best < HUGE_VAL)
+        atomicMin(&b.dtmin[bi], (unsigned long long)__double_as_longlong(best));
+    }
   }
 }
 
-static __global__ void k_cfl_init(Bufs b) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *b.dtmin = 0x7FF0000000000000ULL;  // +inf
+static __global__ void k_cfl_init(Bufs b, int nbox) {
+  for (int i = threadIdx.x; i < nbox; i += blockDim.x) b.dtmin[i] = 0x7FF0000000000000ULL;  // +inf
 }
 
-static __global__ void k_cfl_finish(DevParams p, Bufs b) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    unsigned long long bits = *b.dtmin;
-    double m = __longlong_as_double((long long)bits);
-    *b.dt = p.courant * m;
-  }
+static __global__ void k_cfl_finish(DevParams p, Bufs b, int nbox) {
+  for (int i = threadIdx.x; i < nbox; i += blockDim.x)
+    b.dt[i] = p.courant * __longlong_as_double((long long)b.dtmin[i]);
 }
 
 }  // namespace hr

@@ -18,11 +18,10 @@ namespace hr {
 enum { RHO = 0, UU, U1, U2, U3, B1, B2, B3, ER, UR1, UR2, UR3, NPR = 12 };
 enum { MINK = 0, KS = 1 };
 
+// Physics and solver parameters shared by every grid of a context (kernel
+// argument, read from the constant bank).
 struct DevParams {
-  int n[3], ng[3], N[3];
-  long long ntot, nact;
-  long long str[3];  // strides of the ghost-inclusive array per direction
-  double x0[3], dx[3];
+  int act[3];        // 1 if the direction is active (n > 1) in every grid
   int metric;
   double a, R0, h;
   int bc[6];
@@ -35,6 +34,19 @@ struct DevParams {
   int newton_max;
   double newton_tol;
   int precision;
+};
+
+// Geometry of one grid of a context: sizes, ghost depth, strides, internal
+// coordinates, boundary conditions and the grid's offsets in the context's
+// cell-indexed and active-zone-indexed arrays (one grid per box of a batch).
+struct BoxGeo {
+  int n[3], ng[3], N[3];
+  long long ntot, nact;
+  long long str[3];  // strides of the ghost-inclusive array per direction
+  double x0[3], dx[3];
+  int bc[6];
+  long long coff;    // first cell of this grid in cell-indexed arrays
+  long long aoff;    // first active zone of this grid in active-zone arrays
 };
 
 // ----------------------------------------------------------------- geometry
@@ -195,10 +207,13 @@ __device__ __forceinline__ void bvec(const Geo<MET, R>& g, const R ucon[4], cons
   bvec_iut<MET, R>(g, ucon, ucov, R(1) / ucon[0], Bx, By, Bz, bcon, bcov, bsq);
 }
 
-// Opacities per length at density rho and gas temperature T.
+// Opacities per length at density rho and gas temperature T; kf is the
+// zone's absorption opacity when the opacity is a per-zone field.
 template <typename R>
-__device__ __forceinline__ void opacity_T(const DevParams& p, R rho, R T, R* kabs, R* ksca) {
-  if (p.opacity == 1) {
+__device__ __forceinline__ void opacity_T(const DevParams& p, R rho, R T, R kf, R* kabs, R* ksca) {
+  if (p.opacity == 2) {
+    *kabs = R(p.kscale) * kf;
+  } else if (p.opacity == 1) {
     R Tc = T > R(p.Tmin) ? T : R(p.Tmin);
     R T2 = Tc * Tc;
     R t35;
@@ -215,8 +230,8 @@ __device__ __forceinline__ void opacity_T(const DevParams& p, R rho, R T, R* kab
 }
 
 template <typename R>
-__device__ __forceinline__ void opacity(const DevParams& p, R rho, R ug, R* kabs, R* ksca) {
-  opacity_T<R>(p, rho, R(p.gam - 1.0) * ug / rho, kabs, ksca);
+__device__ __forceinline__ void opacity(const DevParams& p, R rho, R ug, R kf, R* kabs, R* ksca) {
+  opacity_T<R>(p, rho, R(p.gam - 1.0) * ug / rho, kf, kabs, ksca);
 }
 
 // ------------------------------------------------------- face state physics
@@ -244,8 +259,8 @@ __device__ __forceinline__ void char_speeds(const Geo<MET, R>& g, const R ucon[4
 }
 
 template <int MET, typename R>
-__device__ __forceinline__ void face_state(const DevParams& p, const Geo<MET, R>& g, int d,
-                                           const R P[NPR], R U[NPR], R F[NPR], R sp[4]) {
+__device__ __forceinline__ void face_state(const DevParams& p, const Geo<MET, R>& g, int d, R dxd,
+                                           R kf, const R P[NPR], R U[NPR], R F[NPR], R sp[4]) {
   R ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq;
   fourvel<MET, R>(g, P[U1], P[U2], P[U3], ucon, ucov, &gm);
   bvec<MET, R>(g, ucon, ucov, P[B1], P[B2], P[B3], bcon, bcov, &bsq);
@@ -291,8 +306,8 @@ __device__ __forceinline__ void face_state(const DevParams& p, const Geo<MET, R>
   cms2 = cms2 > R(1) ? R(1) : (cms2 < R(0) ? R(0) : cms2);
   char_speeds<MET, R>(g, ucon, cms2, d, &sp[0], &sp[1]);
   R kabs, ksca;
-  opacity<R>(p, rho, ug, &kabs, &ksca);
-  R tau = (kabs + ksca) * sqrt(g.gdd(d)) * R(p.dx[d - 1]);
+  opacity<R>(p, rho, ug, kf, &kabs, &ksca);
+  R tau = (kabs + ksca) * sqrt(g.gdd(d)) * dxd;
   R cr2 = R(1.0 / 3.0);
   if (tau > R(0)) {
     R lim = R(4.0 / 3.0) / tau;
@@ -302,10 +317,11 @@ __device__ __forceinline__ void face_state(const DevParams& p, const Geo<MET, R>
   char_speeds<MET, R>(g, urc, cr2, d, &sp[2], &sp[3]);
 }
 
-// Gas and radiation signal speeds (vmin, vmax) of one reconstructed state.
+// Gas and radiation signal speeds (vmin, vmax) of one reconstructed state;
+// dxd is the cell size along d and kf the per-zone opacity of the state's cell.
 template <int MET, typename R>
-__device__ __forceinline__ void face_speeds(const DevParams& p, const Geo<MET, R>& g, int d,
-                                            const R P[NPR], R sp[4]) {
+__device__ __forceinline__ void face_speeds(const DevParams& p, const Geo<MET, R>& g, int d, R dxd,
+                                            R kf, const R P[NPR], R sp[4]) {
   R ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq;
   fourvel<MET, R>(g, P[U1], P[U2], P[U3], ucon, ucov, &gm);
   bvec<MET, R>(g, ucon, ucov, P[B1], P[B2], P[B3], bcon, bcov, &bsq);
@@ -320,8 +336,8 @@ __device__ __forceinline__ void face_speeds(const DevParams& p, const Geo<MET, R
   R urc[4], urv[4], gr;
   fourvel<MET, R>(g, P[UR1], P[UR2], P[UR3], urc, urv, &gr);
   R kabs, ksca;
-  opacity<R>(p, rho, ug, &kabs, &ksca);
-  R tau = (kabs + ksca) * sqrt(g.gdd(d)) * R(p.dx[d - 1]);
+  opacity<R>(p, rho, ug, kf, &kabs, &ksca);
+  R tau = (kabs + ksca) * sqrt(g.gdd(d)) * dxd;
   R cr2 = R(1.0 / 3.0);
   if (tau > R(0)) {
     R lim = R(4.0 / 3.0) / tau;

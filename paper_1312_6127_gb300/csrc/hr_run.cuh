@@ -8,6 +8,7 @@ namespace hr {
 inline Bufs make_bufs(harmrad_ctx* c) {
   Bufs b;
   b.P = c->P;
+  b.K = c->K;
   b.Un = c->Un;
   for (int d = 0; d < 3; ++d) {
     b.F[d] = c->F[d];
@@ -16,95 +17,126 @@ inline Bufs make_bufs(harmrad_ctx* c) {
   }
   b.aux = c->aux;
   b.emf = c->emf;
+  b.edges = c->edges;
   b.dt = c->dt;
   b.status = c->status;
   b.iters = c->iters;
   b.failed = c->failed;
   b.qcount = c->qcount;
   b.qzone = c->qzone;
+  b.qbox = c->qbox;
   b.qdata = c->qdata;
   b.fzone = c->fzone;
+  b.fbox = c->fbox;
   b.ftmp = c->ftmp;
   b.stats = c->stats;
   b.dtmin = c->dtmin;
   return b;
 }
 
+// Largest per-grid work count of a kernel class, for sizing its launch.
+template <typename Fn>
+inline long long max_work(const harmrad_ctx* c, Fn work) {
+  long long m = 1;
+  for (int i = 0; i < c->nbox; ++i) {
+    long long w = work(c->boxes[i]);
+    if (w > m) m = w;
+  }
+  return m;
+}
+
 template <int MET, typename R>
 int faces_impl(harmrad_ctx* c, bool fresh) {
   const DevParams& p = c->dp;
   cudaStream_t st = c->stream;
+  const BoxGeo* bt = c->dboxes;
+  const int nb = c->nbox;
+  double* K = p.opacity == 2 ? c->K : nullptr;
   int nk = 0;
   for (int d = 0; d < 3; ++d) {
-    if (p.n[d] == 1) continue;
-    long long work = 2LL * p.ng[d];
-    for (int e = 0; e < 3; ++e)
-      if (e != d) work *= (e < d) ? p.N[e] : p.n[e];
-    k_bc_fill<<<grid_for(work, c->sms, 256), 256, 0, st>>>(p, c->P, d);
+    if (!p.act[d]) continue;
+    long long work = max_work(c, [d](const BoxGeo& b) {
+      long long w = 2LL * b.ng[d];
+      for (int e = 0; e < 3; ++e)
+        if (e != d) w *= (e < d) ? b.N[e] : b.n[e];
+      return w;
+    });
+    k_bc_fill<<<grid_for(work, c->sms, 256), 256, 0, st>>>(p, bt, nb, c->P, K, d);
     mark(c, HARMRAD_K_BC);
     ++nk;
   }
-  k_prep<MET, R><<<grid_for(p.ntot, c->sms, 256), 256, 0, st>>>(p, c->P, (R*)c->aux);
+  k_prep<MET, R><<<grid_for(c->maxcell, c->sms, 256), 256, 0, st>>>(p, bt, nb, c->P, c->K, (R*)c->aux);
   mark(c, HARMRAD_K_PREP);
   ++nk;
+  auto range_cells = [](const BoxGeo& b) {
+    long long w = 1;
+    for (int e = 0; e < 3; ++e) w *= b.n[e] > 1 ? b.n[e] + 2 : 1;
+    return w;
+  };
   if (p.recon == 0) {
     for (int d = 0; d < 3; ++d) {
-      if (p.n[d] == 1) continue;
+      if (!p.act[d]) continue;
       if (fresh) {
-        if (cudaMemsetAsync(c->flat[d], 0, 2 * p.ntot * sizeof(R), st) != cudaSuccess) return HARMRAD_E_CUDA;
+        if (cudaMemsetAsync(c->flat[d], 0, 2 * c->ncell * sizeof(R), st) != cudaSuccess) return HARMRAD_E_CUDA;
         mark(c, HARMRAD_K_OTHER);
       }
-      long long work = 1;
-      for (int e = 0; e < 3; ++e) work *= p.n[e] > 1 ? p.n[e] + 2 : 1;
-      k_flatten<R><<<grid_for(work, c->sms, 256), 256, 0, st>>>(p, c->P, (const R*)c->aux, (R*)c->flat[d], d);
+      k_flatten<R><<<grid_for(max_work(c, range_cells), c->sms, 256), 256, 0, st>>>(
+          p, bt, nb, c->P, (const R*)c->aux, (R*)c->flat[d], d);
       mark(c, HARMRAD_K_FLATTEN);
       ++nk;
     }
   }
   for (int d = 0; d < 3; ++d) {
-    if (p.n[d] == 1) continue;
-    long long wc = 1, work = 1;
-    for (int e = 0; e < 3; ++e) {
-      wc *= p.n[e] > 1 ? p.n[e] + 2 : 1;
-      work *= (e == d) ? p.n[e] + 1 : (p.n[e] > 1 ? p.n[e] + 2 : 1);
-    }
-    const int ge = grid_for(wc, c->sms, 256);
-    const int g = grid_for(work, c->sms, 128);
+    if (!p.act[d]) continue;
+    long long wf = max_work(c, [d](const BoxGeo& b) {
+      long long w = 1;
+      for (int e = 0; e < 3; ++e) w *= (e == d) ? b.n[e] + 1 : (b.n[e] > 1 ? b.n[e] + 2 : 1);
+      return w;
+    });
+    const int ge = grid_for(max_work(c, range_cells), c->sms, 256);
+    const int g = grid_for(wf, c->sms, 128);
     const R* aux = (const R*)c->aux;
     const R* fl = (const R*)c->flat[d];
     R* Ed = (R*)c->edges;
     R* Fd = (R*)c->F[d];
     R* sd = (R*)c->spd[d];
     if (d == 0) {
-      k_edges<MET, R, 0><<<ge, 256, 0, st>>>(p, c->P, aux, fl, Ed);
+      k_edges<MET, R, 0><<<ge, 256, 0, st>>>(p, bt, nb, c->P, aux, fl, Ed);
       mark(c, HARMRAD_K_FACE);
-      k_face<MET, R, 0><<<g, 128, 0, st>>>(p, Ed, Fd, sd);
+      k_face<MET, R, 0><<<g, 128, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd);
     } else if (d == 1) {
-      k_edges<MET, R, 1><<<ge, 256, 0, st>>>(p, c->P, aux, fl, Ed);
+      k_edges<MET, R, 1><<<ge, 256, 0, st>>>(p, bt, nb, c->P, aux, fl, Ed);
       mark(c, HARMRAD_K_FACE);
-      k_face<MET, R, 1><<<g, 128, 0, st>>>(p, Ed, Fd, sd);
+      k_face<MET, R, 1><<<g, 128, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd);
     } else {
-      k_edges<MET, R, 2><<<ge, 256, 0, st>>>(p, c->P, aux, fl, Ed);
+      k_edges<MET, R, 2><<<ge, 256, 0, st>>>(p, bt, nb, c->P, aux, fl, Ed);
       mark(c, HARMRAD_K_FACE);
-      k_face<MET, R, 2><<<g, 128, 0, st>>>(p, Ed, Fd, sd);
+      k_face<MET, R, 2><<<g, 128, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd);
     }
     mark(c, HARMRAD_K_FACE);
     nk += 2;
   }
   for (int a = 0; a < 3; ++a)
     for (int b = a + 1; b < 3; ++b) {
-      if (p.n[a] == 1 || p.n[b] == 1) continue;
-      long long we = 1, wc = 0;
-      for (int e = 0; e < 3; ++e) we *= p.n[e] + ((e == a || e == b) ? 1 : 0);
-      long long la = 1, lb = 1;
-      for (int e = 0; e < 3; ++e) {
-        la *= p.n[e] + (e == a ? 1 : 0);
-        lb *= p.n[e] + (e == b ? 1 : 0);
-      }
-      wc = la + lb;
-      k_emf<R><<<grid_for(we, c->sms, 256), 256, 0, st>>>(p, (const R*)c->F[a], (const R*)c->F[b], (R*)c->emf, a, b);
+      if (!p.act[a] || !p.act[b]) continue;
+      long long we = max_work(c, [a, b](const BoxGeo& x) {
+        long long w = 1;
+        for (int e = 0; e < 3; ++e) w *= x.n[e] + ((e == a || e == b) ? 1 : 0);
+        return w;
+      });
+      long long wc = max_work(c, [a, b](const BoxGeo& x) {
+        long long la = 1, lb = 1;
+        for (int e = 0; e < 3; ++e) {
+          la *= x.n[e] + (e == a ? 1 : 0);
+          lb *= x.n[e] + (e == b ? 1 : 0);
+        }
+        return la + lb;
+      });
+      k_emf<R><<<grid_for(we, c->sms, 256), 256, 0, st>>>(p, bt, nb, (const R*)c->F[a], (const R*)c->F[b],
+                                                            (R*)c->emf, a, b);
       mark(c, HARMRAD_K_CT);
-      k_ct<R><<<grid_for(wc, c->sms, 256), 256, 0, st>>>(p, (const R*)c->emf, (R*)c->F[a], (R*)c->F[b], a, b);
+      k_ct<R><<<grid_for(wc, c->sms, 256), 256, 0, st>>>(p, bt, nb, (const R*)c->emf, (R*)c->F[a],
+                                                           (R*)c->F[b], a, b);
       mark(c, HARMRAD_K_CT);
       nk += 2;
     }
@@ -117,11 +149,11 @@ int cfl_impl(harmrad_ctx* c) {
   int nk = faces_impl<MET, R>(c, true);
   if (nk < 0) return nk;
   Bufs b = make_bufs(c);
-  k_cfl_init<<<1, 32, 0, c->stream>>>(b);
+  k_cfl_init<<<1, 128, 0, c->stream>>>(b, c->nbox);
   mark(c, HARMRAD_K_CFL);
-  k_cfl<R><<<grid_for(c->dp.nact, c->sms, 256), 256, 0, c->stream>>>(c->dp, b);
+  k_cfl<R><<<grid_for(c->maxact, c->sms, 256), 256, 0, c->stream>>>(c->dp, c->dboxes, c->nbox, b);
   mark(c, HARMRAD_K_CFL);
-  k_cfl_finish<<<1, 32, 0, c->stream>>>(c->dp, b);
+  k_cfl_finish<<<1, 128, 0, c->stream>>>(c->dp, b, c->nbox);
   mark(c, HARMRAD_K_CFL);
   if (cudaGetLastError() != cudaSuccess) return HARMRAD_E_CUDA;
   return nk + 3;
@@ -132,17 +164,21 @@ int solve_impl(harmrad_ctx* c, int stage) {
   const DevParams& p = c->dp;
   cudaStream_t st = c->stream;
   if (cudaMemsetAsync(c->qcount, 0, 2 * sizeof(int), st) != cudaSuccess) return HARMRAD_E_CUDA;
-  if (cudaMemsetAsync(c->failed, 0, p.nact, st) != cudaSuccess) return HARMRAD_E_CUDA;
+  if (cudaMemsetAsync(c->failed, 0, c->nact, st) != cudaSuccess) return HARMRAD_E_CUDA;
   mark(c, HARMRAD_K_OTHER);
   Bufs b = make_bufs(c);
-  k_update<MET, R><<<grid_for(p.nact, c->sms, 128), 128, 0, st>>>(p, b, stage);
+  const int gu = grid_for(c->maxact, c->sms, 128);
+  if (c->nbox == 1)
+    k_update<MET, R, true><<<gu, 128, 0, st>>>(p, c->boxes[0], c->dboxes, 1, b, stage);
+  else
+    k_update<MET, R, false><<<gu, 128, 0, st>>>(p, c->boxes[0], c->dboxes, c->nbox, b, stage);
   mark(c, HARMRAD_K_UPDATE);
   // the retry queue and back-up list are short: one persistent wave of blocks
-  k_retry<MET><<<c->sms * 2, 128, 0, st>>>(p, b);
+  k_retry<MET><<<c->sms * 2, 128, 0, st>>>(p, c->dboxes, b);
   mark(c, HARMRAD_K_RETRY);
-  k_backup_avg<<<c->sms, 128, 0, st>>>(p, b);
+  k_backup_avg<<<c->sms, 128, 0, st>>>(p, c->dboxes, b);
   mark(c, HARMRAD_K_BACKUP);
-  k_backup_apply<MET><<<c->sms, 128, 0, st>>>(p, b);
+  k_backup_apply<MET><<<c->sms, 128, 0, st>>>(p, c->dboxes, b);
   mark(c, HARMRAD_K_BACKUP);
   if (cudaGetLastError() != cudaSuccess) return HARMRAD_E_CUDA;
   return 4;
@@ -150,7 +186,7 @@ int solve_impl(harmrad_ctx* c, int stage) {
 
 // --------------------------------------------------- point-wise entry kernels
 template <int MET>
-__global__ void k_zone_physics(DevParams p, int n, const double* __restrict__ x,
+__global__ void k_zone_physics(DevParams p, BoxGeo bg, int n, const double* __restrict__ x,
                                const double* __restrict__ P, double* U, double* SM, double* F,
                                double* speeds) {
   for (int z = blockIdx.x * blockDim.x + threadIdx.x; z < n; z += gridDim.x * blockDim.x) {
@@ -160,7 +196,7 @@ __global__ void k_zone_physics(DevParams p, int n, const double* __restrict__ x,
     for (int q = 0; q < NPR; ++q) Pz[q] = P[NPR * z + q];
     for (int d = 1; d <= 3; ++d) {
       double Uq[NPR], Fq[NPR], sp[4];
-      face_state<MET, double>(p, g, d, Pz, Uq, Fq, sp);
+      face_state<MET, double>(p, g, d, bg.dx[d - 1], 1.0, Pz, Uq, Fq, sp);
       if (F)
         for (int q = 0; q < NPR; ++q) F[(3 * z + d - 1) * NPR + q] = Fq[q];
       if (speeds)
@@ -191,7 +227,7 @@ __global__ void k_zone_physics(DevParams p, int n, const double* __restrict__ x,
 }
 
 template <int MET>
-__global__ void k_zone_implicit(DevParams p, int n, const double* __restrict__ x,
+__global__ void k_zone_implicit(DevParams p, BoxGeo bg, int n, const double* __restrict__ x,
                                 const double* __restrict__ Us, const double* __restrict__ Ps,
                                 const double* __restrict__ hh, double* Pout, double* eTo, int* itso,
                                 unsigned char* meth) {
@@ -204,13 +240,13 @@ __global__ void k_zone_implicit(DevParams p, int n, const double* __restrict__ x
       P0[q] = Ps[NPR * z + q];
     }
     ImpSys<MET> s;
-    build_sys<MET>(p, g, Ust, hh[z], s);
+    build_sys<MET>(p, g, Ust, hh[z], 1.0, s);
     double x0[4] = {P0[UU], P0[U1], P0[U2], P0[U3]};
     double kabs, ksca;
-    opacity<double>(p, P0[RHO], P0[UU], &kabs, &ksca);
+    opacity<double>(p, P0[RHO], P0[UU], 1.0, &kabs, &ksca);
     double dl = 0.0;
     for (int d = 1; d <= 3; ++d)
-      if (p.n[d - 1] > 1) dl = fmax(dl, sqrt(g.gdd(d)) * p.dx[d - 1]);
+      if (p.act[d - 1]) dl = fmax(dl, sqrt(g.gdd(d)) * bg.dx[d - 1]);
     if ((kabs + ksca) * dl < 2.0 / 3.0) {
       double go[5], T3[3] = {s.Ts[1], s.Ts[2], s.Ts[3]};
       if (gas_invert<MET>(p, g, s.Dlab, s.Ts[0], T3, s.B, P0, 1e-9, go) == 0) {
@@ -296,16 +332,18 @@ int Run<MET>::solve(harmrad_ctx* c, int stage) {
   return c->real_size == 8 ? solve_impl<MET, double>(c, stage) : solve_impl<MET, float>(c, stage);
 }
 template <int MET>
-int Run<MET>::zone_physics(const DevParams& dp, int n, const double* x, const double* P, double* U,
-                           double* SM, double* F, double* speeds, cudaStream_t st, int sms) {
-  k_zone_physics<MET><<<grid_for(n, sms, 128), 128, 0, st>>>(dp, n, x, P, U, SM, F, speeds);
+int Run<MET>::zone_physics(const DevParams& dp, const BoxGeo& bg, int n, const double* x,
+                           const double* P, double* U, double* SM, double* F, double* speeds,
+                           cudaStream_t st, int sms) {
+  k_zone_physics<MET><<<grid_for(n, sms, 128), 128, 0, st>>>(dp, bg, n, x, P, U, SM, F, speeds);
   return cudaGetLastError() == cudaSuccess ? 1 : HARMRAD_E_CUDA;
 }
 template <int MET>
-int Run<MET>::zone_implicit(const DevParams& dp, int n, const double* x, const double* Us,
-                            const double* Ps, const double* h, double* Pout, double* eT, int* iters,
-                            unsigned char* method, cudaStream_t st, int sms) {
-  k_zone_implicit<MET><<<grid_for(n, sms, 128), 128, 0, st>>>(dp, n, x, Us, Ps, h, Pout, eT, iters, method);
+int Run<MET>::zone_implicit(const DevParams& dp, const BoxGeo& bg, int n, const double* x,
+                            const double* Us, const double* Ps, const double* h, double* Pout,
+                            double* eT, int* iters, unsigned char* method, cudaStream_t st, int sms) {
+  k_zone_implicit<MET><<<grid_for(n, sms, 128), 128, 0, st>>>(dp, bg, n, x, Us, Ps, h, Pout, eT, iters,
+                                                              method);
   return cudaGetLastError() == cudaSuccess ? 1 : HARMRAD_E_CUDA;
 }
 

@@ -70,11 +70,11 @@ __device__ void zi_setup(const hr::DevParams& p, int z, const double* x, const d
     Ust[q] = Us[NPR * z + q];
     P0[q] = Ps[NPR * z + q];
   }
-  build_sys<MET>(p, g, Ust, hh[z], s);
+  build_sys<MET>(p, g, Ust, hh[z], 1.0, s);
 }
 
 template <int MET>
-__global__ void k_zi_pmhd(hr::DevParams p, int n, const double* __restrict__ x,
+__global__ void k_zi_pmhd(hr::DevParams p, hr::BoxGeo bg, int n, const double* __restrict__ x,
                           const double* __restrict__ Us, const double* __restrict__ Ps,
                           const double* __restrict__ hh, double* Pout, double* eTo, int* itso,
                           unsigned char* meth, void* base) {
@@ -87,10 +87,10 @@ __global__ void k_zi_pmhd(hr::DevParams p, int n, const double* __restrict__ x,
     zi_setup<MET>(p, z, x, Us, Ps, hh, g, s, P0);
     double x0[4] = {P0[UU], P0[U1], P0[U2], P0[U3]};
     double kabs, ksca;
-    opacity<double>(p, P0[RHO], P0[UU], &kabs, &ksca);
+    opacity<double>(p, P0[RHO], P0[UU], 1.0, &kabs, &ksca);
     double dl = 0.0;
     for (int d = 1; d <= 3; ++d)
-      if (p.n[d - 1] > 1) dl = fmax(dl, sqrt(g.gdd(d)) * p.dx[d - 1]);
+      if (p.act[d - 1]) dl = fmax(dl, sqrt(g.gdd(d)) * bg.dx[d - 1]);
     if ((kabs + ksca) * dl < 2.0 / 3.0) {
       double go[5], T3[3] = {s.Ts[1], s.Ts[2], s.Ts[3]};
       if (gas_invert<MET>(p, g, s.Dlab, s.Ts[0], T3, s.B, P0, 1e-9, go) == 0) {
@@ -216,6 +216,7 @@ int scratch_address(void** out) {
 }  // namespace
 
 extern int harmrad_fill_params_internal(const harmrad_params* p, hr::DevParams& d);
+extern int harmrad_fill_geometry_internal(const harmrad_params* p, hr::BoxGeo& b);
 
 extern "C" int harmrad_zone_implicit_static(const harmrad_params* prm, int n, const double* x,
                                             const double* Us, const double* Ps, const double* h,
@@ -224,8 +225,11 @@ extern "C" int harmrad_zone_implicit_static(const harmrad_params* prm, int n, co
   if (!prm || n < 0 || (n > 0 && (!x || !Us || !Ps || !h || !Pout))) return HARMRAD_E_ARG;
   if (n > kStaticMaxZones) return HARMRAD_E_ARG;
   hr::DevParams dp;
+  hr::BoxGeo bg;
   int rc = harmrad_fill_params_internal(prm, dp);
+  if (!rc) rc = harmrad_fill_geometry_internal(prm, bg);
   if (rc) return rc;
+  if (dp.opacity == HARMRAD_OPAC_FIELD) return HARMRAD_E_ARG;
   if (n == 0) return HARMRAD_OK;
   void* base = nullptr;
   rc = scratch_address(&base);
@@ -240,10 +244,10 @@ extern "C" int harmrad_zone_implicit_static(const harmrad_params* prm, int n, co
   k_zi_clear<<<1, 32, 0, st>>>(base);
   int grid = hr::grid_for(n, sms, 128);
   if (dp.metric == 1) {
-    k_zi_pmhd<hr::KS><<<grid, 128, 0, st>>>(dp, n, x, Us, Ps, h, Pout, eT, iters, method, base);
+    k_zi_pmhd<hr::KS><<<grid, 128, 0, st>>>(dp, bg, n, x, Us, Ps, h, Pout, eT, iters, method, base);
     k_zi_urad<hr::KS><<<sms * 2, 128, 0, st>>>(dp, x, Us, Ps, h, Pout, eT, iters, method, base);
   } else {
-    k_zi_pmhd<hr::MINK><<<grid, 128, 0, st>>>(dp, n, x, Us, Ps, h, Pout, eT, iters, method, base);
+    k_zi_pmhd<hr::MINK><<<grid, 128, 0, st>>>(dp, bg, n, x, Us, Ps, h, Pout, eT, iters, method, base);
     k_zi_urad<hr::MINK><<<sms * 2, 128, 0, st>>>(dp, x, Us, Ps, h, Pout, eT, iters, method, base);
   }
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {

@@ -17,9 +17,10 @@ NPRIM = 12
 OK, W_BACKUP_USED = 0, 1
 ZONE_PMHD, ZONE_URAD, ZONE_BACKUP = 0, 1, 2
 PREC_FP64, PREC_SPLIT = 0, 1
+OPAC_CONST, OPAC_KRAMERS, OPAC_FIELD = 0, 1, 2
 
 EXPORTS = [
-    "harmrad_init", "harmrad_destroy", "harmrad_set_prims", "harmrad_get_prims",
+    "harmrad_init", "harmrad_init_batch", "harmrad_destroy", "harmrad_set_opacity_field", "harmrad_set_prims", "harmrad_get_prims",
     "harmrad_cfl_dt", "harmrad_step", "harmrad_step_host", "harmrad_get_stats",
     "harmrad_get_status", "harmrad_get_iters", "harmrad_compute_fluxes",
     "harmrad_zone_physics", "harmrad_zone_implicit", "harmrad_zone_implicit_static",
@@ -100,6 +101,8 @@ def load(path=LIB_PATH):
     vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int
     pp = ctypes.POINTER(Params)
     L.harmrad_init.argtypes = [pp, vp, ctypes.POINTER(vp)]
+    L.harmrad_init_batch.argtypes = [pp, ip, vp, ctypes.POINTER(vp)]
+    L.harmrad_set_opacity_field.argtypes = [vp, vp, ip]
     L.harmrad_destroy.argtypes = [vp]
     L.harmrad_destroy.restype = None
     L.harmrad_set_prims.argtypes = [vp, vp, ip]
@@ -191,6 +194,12 @@ class Grid:
             P = np.ascontiguousarray(P, dtype=np.float64).reshape(self.shape)
             _check(load().harmrad_set_prims(self._h, P.ctypes.data_as(ctypes.c_void_p), 0), "set_prims")
 
+    def set_opacity_field(self, K):
+        """Per-zone absorption field K ([n3,n2,n1]; kappa_abs = kappa_scale K)."""
+        K = np.ascontiguousarray(K, dtype=np.float64).reshape(self.shape[1:])
+        _check(load().harmrad_set_opacity_field(self._h, K.ctypes.data_as(ctypes.c_void_p), 0),
+               "set_opacity_field")
+
     def get_prims(self, device=False):
         import torch
         if device:
@@ -242,6 +251,83 @@ class Grid:
         _check(load().harmrad_compute_fluxes(self._h, int(d), F.ctypes.data_as(ctypes.c_void_p)),
                "compute_fluxes")
         return F
+
+
+class Batch(Grid):
+    """A batch of independent grids ("boxes") in one context: every kernel of
+    a step covers all boxes.  Per-box arrays are passed and returned as lists
+    in box order; the context holds them concatenated."""
+
+    def __init__(self, cfgs, precision=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise HarmradError("a CUDA device is required")
+        L = load()
+        self.cfgs = [dict(c) for c in cfgs]
+        self.cfg = self.cfgs[0]
+        arr = (Params * len(cfgs))(*[make_params(c, precision) for c in cfgs])
+        self.params = arr
+        self.shapes = [(NPRIM, c["n"][2], c["n"][1], c["n"][0]) for c in cfgs]
+        self.sizes = [int(np.prod(s[1:])) for s in self.shapes]
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        self.nact = int(self.offsets[-1])
+        self.shape = (NPRIM * self.nact,)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        h = ctypes.c_void_p()
+        _check(L.harmrad_init_batch(arr, len(cfgs), _stream_ptr(self.stream), ctypes.byref(h)),
+               "harmrad_init_batch")
+        self._h = h
+
+    def pack(self, Ps):
+        """List of [12,n3,n2,n1] arrays -> the context's flat layout (numpy)."""
+        return np.concatenate([np.ascontiguousarray(P, dtype=np.float64).reshape(-1) for P in Ps])
+
+    def unpack(self, flat, nv=NPRIM):
+        out = []
+        for b, s in enumerate(self.shapes):
+            o, m = self.offsets[b], self.sizes[b]
+            out.append(flat[nv * o:nv * (o + m)].reshape((nv,) + s[1:]) if nv > 1 else
+                       flat[o:o + m].reshape(s[1:]))
+        return out
+
+    def set_prims(self, Ps):
+        import torch
+        if isinstance(Ps, torch.Tensor):
+            assert Ps.is_cuda and Ps.dtype == torch.float64 and Ps.numel() == NPRIM * self.nact
+            Ps = Ps.contiguous()
+            _check(load().harmrad_set_prims(self._h, ctypes.c_void_p(Ps.data_ptr()), 1), "set_prims")
+            return
+        flat = self.pack(Ps)
+        _check(load().harmrad_set_prims(self._h, flat.ctypes.data_as(ctypes.c_void_p), 0), "set_prims")
+
+    def set_opacity_field(self, Ks):
+        flat = np.concatenate([np.ascontiguousarray(K, dtype=np.float64).reshape(-1) for K in Ks])
+        assert flat.size == self.nact
+        _check(load().harmrad_set_opacity_field(self._h, flat.ctypes.data_as(ctypes.c_void_p), 0),
+               "set_opacity_field")
+
+    def get_prims(self, device=False):
+        import torch
+        if device:
+            out = torch.empty(NPRIM * self.nact, dtype=torch.float64, device="cuda")
+            _check(load().harmrad_get_prims(self._h, ctypes.c_void_p(out.data_ptr()), 1), "get_prims")
+            return out
+        out = np.empty(NPRIM * self.nact)
+        _check(load().harmrad_get_prims(self._h, out.ctypes.data_as(ctypes.c_void_p), 0), "get_prims")
+        return self.unpack(out)
+
+    def status(self):
+        st = np.empty(self.nact, dtype=np.uint8)
+        _check(load().harmrad_get_status(self._h, st.ctypes.data_as(ctypes.c_void_p), 0), "get_status")
+        return self.unpack(st, 1)
+
+    def iters(self):
+        it = np.empty(self.nact, dtype=np.int32)
+        _check(load().harmrad_get_iters(self._h, it.ctypes.data_as(ctypes.c_void_p), 0), "get_iters")
+        return self.unpack(it, 1)
+
+    def fluxes(self, d):
+        raise HarmradError("face fluxes are available for single-grid contexts only")
 
 
 def _dev(a):

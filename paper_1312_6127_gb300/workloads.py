@@ -25,7 +25,7 @@ RHO, UU, U1, U2, U3, B1, B2, B3, ER, UR1, UR2, UR3 = range(12)
 PERIODIC, OUTFLOW, POLAR = 0, 1, 2
 PPM, MC = 0, 1
 LAXF, HLL = 0, 1
-OPAC_CONST, OPAC_KRAMERS = 0, 1
+OPAC_CONST, OPAC_KRAMERS, OPAC_FIELD = 0, 1, 2
 
 
 def rng(seed):
@@ -179,6 +179,48 @@ def minkowski_box(n=(16, 16, 16), seed=7, B_amp=0.05, vmax=0.3, kappa=(1e-2, 1e2
     kap = math.exp(g.uniform(math.log(kappa[0]), math.log(kappa[1])))
     cfg.update(opacity=OPAC_CONST, kappa_abs0=kap, kappa_es0=0.4 * kap / 10.0)
     return cfg, P
+
+
+def box_batch(count=48, seed=4242, edge=(32, 128), tau=(1e-4, 1e6), vmax=0.3):
+    """``count`` independent periodic 3D Minkowski unit boxes of uneven size,
+    for one batched context.  Each edge is round(lo * (hi/lo)^U), U uniform,
+    so sizes are log-uniform between edge[0] and edge[1] per direction.  Per
+    box: rho log-normal (sigma 1), u_g = 0.01 rho, velocities of random
+    direction and speed uniform up to vmax, B = 0, a Gaussian radiation pulse
+    a T0^4 (1 + 100 exp(-r^2/w^2)), w = 0.1 of the box, T0 the mean gas temperature,
+    radiation frame at rest in the ZAMO frame, and a per-zone absorption
+    field whose optical depth per cell is log-uniform over ``tau`` (so Newton
+    iteration counts are heavy-tailed), electron scattering kappa_es = 0.4.
+    Returns (cfgs, Ps, Ks): per-box parameter dicts, primitives [12,n3,n2,n1]
+    and absorption fields K [n3,n2,n1] (kappa_abs per length = K)."""
+    g = rng(seed)
+    lo, hi = edge
+    cfgs, Ps, Ks = [], [], []
+    gam = 5.0 / 3.0
+    T0 = (gam - 1.0) * 1e-2
+    for b in range(count):
+        n = [int(round(lo * (hi / lo) ** g.uniform())) for _ in range(3)]
+        n1, n2, n3 = n
+        cfg = base_params()
+        cfg.update(n=n, dx=[1.0 / n1, 1.0 / n2, 1.0 / n3], gam=gam, a_rad=1e-2 / T0 ** 4,
+                   opacity=OPAC_FIELD, kappa_abs0=0.0, kappa_es0=0.4, kappa_scale=1.0)
+        shape = (n3, n2, n1)
+        P = np.zeros((NP,) + shape)
+        P[RHO] = np.exp(g.standard_normal(shape))
+        P[UU] = 0.01 * P[RHO]
+        v = g.standard_normal((3,) + shape)
+        v /= np.linalg.norm(v, axis=0, keepdims=True)
+        speed = g.uniform(0.0, vmax, shape)
+        P[U1:U3 + 1] = v * (speed / np.sqrt(1.0 - speed ** 2))[None]
+        zc = [(np.arange(m) + 0.5) / m - 0.5 for m in n]
+        R2 = zc[2][:, None, None] ** 2 + zc[1][None, :, None] ** 2 + zc[0][None, None, :] ** 2
+        P[ER] = cfg["a_rad"] * T0 ** 4 * (1.0 + 100.0 * np.exp(-R2 / 0.1 ** 2))
+        dxm = min(cfg["dx"])
+        K = np.exp(g.uniform(math.log(tau[0]), math.log(tau[1]), shape)) / dxm
+        cfgs.append(cfg)
+        Ps.append(P)
+        Ks.append(K)
+    return cfgs, Ps, Ks
 
 
 def thin_pulse(n=(32, 32, 32), L=100.0, w=5.0, T_a=1e6):
