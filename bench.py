@@ -30,9 +30,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "GRRMHD+M1 zone-cycles/s at 256x128x64 (FP64 vs split); frac of HBM roofline"
 UNIT = "zone-cycles/s"
-# FP64 peak of a GB300 from its unit counts and clock: 152 SMs x 2 DFMA per
-# clock x 2 flops x 2.07 GHz (the FMA probe in profiles/ measured 1201 GFLOP/s
-# at 2.01 GHz).
+# FP64 peak of a GB300 from its unit counts and clock: 152 SMs x 2 FP64 FMA per
+# clock x 2 flops x 2.07 GHz = 1.26 TFLOP/s (the nominal 1.25 TFLOP/s).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 PROFILE_JSON = os.path.join(ROOT, "profiles", "k_update_counters.json")
 KERNEL_SOURCES = ["hr_phys.cuh", "hr_implicit.cuh", "hr_kernels.cuh"]
@@ -173,6 +172,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -210,6 +210,7 @@ def main():
               "absorption with optical depth per cell log-uniform 1e-4..1e6, one batched context"
               % nact)
         size_key, prof_key = "batch48", "batch48_" + args.precision
+    tuning = g.tuning() if args.no_autotune else g.autotune(reps=1)
     for _ in range(args.warmup):
         g.step(0.0)
     torch.cuda.synchronize()
@@ -260,7 +261,9 @@ def main():
                         "unit": "TFLOP/s", "frac": achieved / (FP64_PEAK_GFLOPS / 1e3),
                         "traffic": traffic, "kernel": "k_update (update + PMHD Newton)",
                         "kernel_ms": avg_ms, "counters_fresh": fresh,
-                        "peak_note": "FP64 from unit counts: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz"}
+                        "fp64_pipe_active_pct": entry.get("fp64_pipe_active_pct"),
+                        "peak_note": "FP64 from unit counts: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz; "
+                                     "achieved counts DFMA/DMUL/DADD only"}
         else:
             roofline = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS / 1e3,
                         "unit": "TFLOP/s", "frac": None, "traffic": traffic,
@@ -311,7 +314,9 @@ def main():
             "config": {"workload": wl,
                        "precision": args.precision, "zones": nact,
                        "l2": "working set > L2 (129 MB); no flush needed",
-                       "parallelism": "replicas" if ws > 1 else "single GPU"},
+                       "parallelism": "replicas" if ws > 1 else "single GPU",
+                       "launch_shapes": {k: v for k, v in tuning.items() if not k.endswith("_ms")},
+                       "autotuned": not args.no_autotune},
             "gpu_launches": st["kernel_launches"] * args.steps,
             "clocks": clk,
             "solver": {"newton_iters_per_solve": st["newton_iters"] / max(st["zone_stages"], 1),

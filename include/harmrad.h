@@ -231,14 +231,15 @@ int harmrad_zone_implicit_static(const harmrad_params* p, int n, const double* x
 #define HARMRAD_K_BC 0        /* ghost-zone fill */
 #define HARMRAD_K_PREP 1      /* per-cell metric factors and flattener inputs */
 #define HARMRAD_K_FLATTEN 2   /* PPM shock flattener */
-#define HARMRAD_K_FACE 3      /* reconstruction + face physics + Riemann flux */
+#define HARMRAD_K_FACE 3      /* face physics + Riemann flux */
 #define HARMRAD_K_CT 4        /* flux-CT EMFs */
 #define HARMRAD_K_UPDATE 5    /* update + geometric source + PMHD implicit solve */
 #define HARMRAD_K_RETRY 6     /* URAD retry queue */
 #define HARMRAD_K_BACKUP 7    /* neighbour-average back-up */
 #define HARMRAD_K_CFL 8       /* CFL reduction */
 #define HARMRAD_K_OTHER 9     /* memsets, time-step upload */
-#define HARMRAD_K_CLASSES 10
+#define HARMRAD_K_EDGE 10     /* PPM / MC reconstruction of the face values */
+#define HARMRAD_K_CLASSES 11
 
 typedef struct harmrad_kernel_times {
   double ms[HARMRAD_K_CLASSES];  /* summed device time per class, milliseconds */
@@ -251,6 +252,31 @@ typedef struct harmrad_kernel_times {
  * time between consecutive events is summed per kernel class.  Synchronises
  * the stream.  For benchmarking and profiling. */
 int harmrad_profile_step(harmrad_ctx* ctx, double dt, harmrad_kernel_times* out);
+
+/* Launch shapes of the three heaviest kernels: threads per block and the cap
+ * on blocks per SM of their grid-stride grids (the grid is the smaller of the
+ * work and sms x cap blocks).  Shapes change no result: every zone and face
+ * runs the same arithmetic under any shape. */
+typedef struct harmrad_tuning {
+  int face_block, face_blocks_per_sm;      /* face physics + Riemann; block 32..128 */
+  int update_block, update_blocks_per_sm;  /* update + implicit solve; block 32..128 */
+  int edge_block, edge_blocks_per_sm;      /* reconstruction; block 32..256 */
+  double face_ms, update_ms, edge_ms;      /* autotune: best device ms per step */
+} harmrad_tuning;
+
+/* Autotune the launch shapes on the context's current state: time `reps`
+ * eager steps (dt <= 0: CFL) for each candidate shape, with CUDA events on the
+ * context's stream, keep the fastest per kernel class, restore the primitives
+ * and drop the captured graphs (the next step re-captures).  Candidates:
+ * blocks of 64 or 128 threads (edges 128 or 256) with caps of 4..64 blocks per
+ * SM.  Writes the chosen shapes to *out (may be NULL).  Synchronises; allocates
+ * a scratch copy of the primitives for the duration of the call. */
+int harmrad_autotune(harmrad_ctx* ctx, int reps, harmrad_tuning* out);
+
+/* Read or set the launch shapes (set: values outside the ranges above give
+ * HARMRAD_E_ARG; the captured graphs are dropped). */
+int harmrad_get_tuning(harmrad_ctx* ctx, harmrad_tuning* out);
+int harmrad_set_tuning(harmrad_ctx* ctx, const harmrad_tuning* t);
 
 /* Human-readable text of a return code. */
 const char* harmrad_strerror(int code);

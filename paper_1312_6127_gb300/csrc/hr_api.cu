@@ -247,6 +247,32 @@ int launch_step(harmrad_ctx* c, bool with_cfl) {
   return HARMRAD_OK;
 }
 
+harmrad_tuning default_tuning() {
+  harmrad_tuning t;
+  memset(&t, 0, sizeof(t));
+  t.face_block = 128;
+  t.face_blocks_per_sm = 16;
+  t.update_block = 128;
+  t.update_blocks_per_sm = 16;
+  t.edge_block = 256;
+  t.edge_blocks_per_sm = 16;
+  return t;
+}
+
+bool tuning_ok(const harmrad_tuning& t) {
+  auto ok = [](int b, int cap, int bmax) { return b >= 32 && b <= bmax && b % 32 == 0 && cap >= 1 && cap <= 64; };
+  return ok(t.face_block, t.face_blocks_per_sm, 128) && ok(t.update_block, t.update_blocks_per_sm, 128) &&
+         ok(t.edge_block, t.edge_blocks_per_sm, 256);
+}
+
+void drop_graphs(harmrad_ctx* c) {
+  for (int g = 0; g < 2; ++g)
+    if (c->graph[g]) {
+      cudaGraphExecDestroy(c->graph[g]);
+      c->graph[g] = nullptr;
+    }
+}
+
 void free_all(harmrad_ctx* c) {
   void* ptrs[] = {c->P, c->K, c->Un, c->F[0], c->F[1], c->F[2], c->spd[0], c->spd[1], c->spd[2],
                   c->aux, c->flat[0], c->flat[1], c->flat[2], c->emf, c->edges, c->dt, c->status,
@@ -309,6 +335,7 @@ int create(const harmrad_params* p, int count, void* stream, harmrad_ctx** out) 
   c->maxact = maxa;
   c->real_size = p[0].precision == HARMRAD_PREC_SPLIT ? 4 : 8;
   c->use_graph = getenv("HARMRAD_NO_GRAPH") == nullptr;
+  c->tune = default_tuning();
   if (cudaGetDevice(&c->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
     cudaGetLastError();
@@ -633,6 +660,92 @@ int harmrad_zone_implicit(const harmrad_params* prm, int n, const double* x, con
               : hr::Run<hr::MINK>::zone_implicit(dp, bg, n, x, Us, Ps, h, Pout, eT, iters, method, st, sms);
   if (r < 0) return r;
   HR_CHECK(cudaStreamSynchronize(st));
+  return HARMRAD_OK;
+}
+
+int harmrad_get_tuning(harmrad_ctx* c, harmrad_tuning* out) {
+  if (!c || !out) return HARMRAD_E_ARG;
+  *out = c->tune;
+  return HARMRAD_OK;
+}
+
+int harmrad_set_tuning(harmrad_ctx* c, const harmrad_tuning* t) {
+  if (!c || !t || !tuning_ok(*t)) return HARMRAD_E_ARG;
+  HR_CHECK(cudaStreamSynchronize(c->stream));
+  c->tune = *t;
+  drop_graphs(c);
+  return HARMRAD_OK;
+}
+
+int harmrad_autotune(harmrad_ctx* c, int reps, harmrad_tuning* out) {
+  if (!c) return HARMRAD_E_ARG;
+  if (!c->has_prims) return HARMRAD_E_STATE;
+  if (reps < 1) reps = 1;
+  struct Shape {
+    int block, cap;
+  };
+  // candidate i pairs the i-th shape of each class; the classes are timed
+  // separately within the same step
+  const Shape fc[] = {{128, 16}, {64, 16}, {128, 8}, {128, 32}, {64, 32}, {128, 64}, {128, 4}};
+  const Shape uc[] = {{128, 16}, {64, 16}, {128, 8}, {128, 32}, {64, 32}, {128, 64}, {64, 64}};
+  const Shape ec[] = {{256, 16}, {128, 16}, {256, 8}, {256, 32}, {128, 32}, {256, 64}, {128, 64}};
+  const int ncand = 7;
+  const size_t bytes = 12 * (size_t)c->ncell * sizeof(double);
+  double* save = nullptr;
+  if (cudaMalloc((void**)&save, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return HARMRAD_E_OOM;
+  }
+  const harmrad_tuning orig = c->tune;
+  harmrad_tuning best = orig;
+  best.face_ms = best.update_ms = best.edge_ms = HUGE_VAL;
+  int rc = HARMRAD_OK;
+  if (cudaMemcpyAsync(save, c->P, bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) rc = HARMRAD_E_CUDA;
+  for (int it = -1; it < reps * ncand && rc >= 0; ++it) {
+    harmrad_tuning t = orig;
+    if (it >= 0) {  // it = -1: one untimed step loads every kernel
+      int i = it % ncand;
+      t.face_block = fc[i].block;
+      t.face_blocks_per_sm = fc[i].cap;
+      t.update_block = uc[i].block;
+      t.update_blocks_per_sm = uc[i].cap;
+      t.edge_block = ec[i].block;
+      t.edge_blocks_per_sm = ec[i].cap;
+    }
+    c->tune = t;
+    harmrad_kernel_times kt;
+    rc = harmrad_profile_step(c, 0.0, &kt);
+    if (rc < 0) break;
+    if (cudaMemcpyAsync(c->P, save, bytes, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess) {
+      rc = HARMRAD_E_CUDA;
+      break;
+    }
+    if (it < 0) continue;
+    if (kt.ms[HARMRAD_K_FACE] < best.face_ms) {
+      best.face_ms = kt.ms[HARMRAD_K_FACE];
+      best.face_block = t.face_block;
+      best.face_blocks_per_sm = t.face_blocks_per_sm;
+    }
+    if (kt.ms[HARMRAD_K_UPDATE] < best.update_ms) {
+      best.update_ms = kt.ms[HARMRAD_K_UPDATE];
+      best.update_block = t.update_block;
+      best.update_blocks_per_sm = t.update_blocks_per_sm;
+    }
+    if (kt.ms[HARMRAD_K_EDGE] < best.edge_ms) {
+      best.edge_ms = kt.ms[HARMRAD_K_EDGE];
+      best.edge_block = t.edge_block;
+      best.edge_blocks_per_sm = t.edge_blocks_per_sm;
+    }
+  }
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess && rc >= 0) rc = HARMRAD_E_CUDA;
+  cudaFree(save);
+  if (rc < 0) {
+    c->tune = orig;
+    return rc;
+  }
+  c->tune = best;
+  drop_graphs(c);
+  if (out) *out = best;
   return HARMRAD_OK;
 }
 

@@ -16,9 +16,9 @@ __host__ __device__ __forceinline__ double xcen(const BoxGeo& b, int d, int i) {
   return b.x0[d] + (i + 0.5) * b.dx[d];
 }
 
-inline int grid_for(long long work, int sms, int block) {
+inline int grid_for(long long work, int sms, int block, int per_sm = 16) {
   long long g = (work + block - 1) / block;
-  long long cap = (long long)sms * 16;
+  long long cap = (long long)sms * per_sm;
   if (g > cap) g = cap;
   if (g < 1) g = 1;
   return (int)g;

@@ -49,6 +49,9 @@ struct harmrad_ctx {
   int* flag;              // validation flag
   double* host_dt;        // pinned host scalar for dt read-back
   bool has_prims;
+  // launch shapes of the heavy kernels (threads per block, resident-block cap
+  // per SM of the grid-stride grid); chosen by harmrad_autotune
+  harmrad_tuning tune;
   // CUDA graphs of a full step: [0] dt given, [1] CFL dt
   cudaGraphExec_t graph[2];
   bool use_graph;

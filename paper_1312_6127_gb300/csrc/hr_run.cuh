@@ -93,25 +93,27 @@ int faces_impl(harmrad_ctx* c, bool fresh) {
       for (int e = 0; e < 3; ++e) w *= (e == d) ? b.n[e] + 1 : (b.n[e] > 1 ? b.n[e] + 2 : 1);
       return w;
     });
-    const int ge = grid_for(max_work(c, range_cells), c->sms, 256);
-    const int g = grid_for(wf, c->sms, 128);
+    const harmrad_tuning& tu = c->tune;
+    const int be = tu.edge_block, bf = tu.face_block;
+    const int ge = grid_for(max_work(c, range_cells), c->sms, be, tu.edge_blocks_per_sm);
+    const int g = grid_for(wf, c->sms, bf, tu.face_blocks_per_sm);
     const R* aux = (const R*)c->aux;
     const R* fl = (const R*)c->flat[d];
     R* Ed = (R*)c->edges;
     R* Fd = (R*)c->F[d];
     R* sd = (R*)c->spd[d];
     if (d == 0) {
-      k_edges<MET, R, 0><<<ge, 256, 0, st>>>(p, bt, nb, c->P, aux, fl, Ed);
-      mark(c, HARMRAD_K_FACE);
-      k_face<MET, R, 0><<<g, 128, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd);
+      k_edges<MET, R, 0><<<ge, be, 0, st>>>(p, bt, nb, c->P, aux, fl, Ed);
+      mark(c, HARMRAD_K_EDGE);
+      k_face<MET, R, 0><<<g, bf, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd);
     } else if (d == 1) {
-      k_edges<MET, R, 1><<<ge, 256, 0, st>>>(p, bt, nb, c->P, aux, fl, Ed);
-      mark(c, HARMRAD_K_FACE);
-      k_face<MET, R, 1><<<g, 128, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd);
+      k_edges<MET, R, 1><<<ge, be, 0, st>>>(p, bt, nb, c->P, aux, fl, Ed);
+      mark(c, HARMRAD_K_EDGE);
+      k_face<MET, R, 1><<<g, bf, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd);
     } else {
-      k_edges<MET, R, 2><<<ge, 256, 0, st>>>(p, bt, nb, c->P, aux, fl, Ed);
-      mark(c, HARMRAD_K_FACE);
-      k_face<MET, R, 2><<<g, 128, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd);
+      k_edges<MET, R, 2><<<ge, be, 0, st>>>(p, bt, nb, c->P, aux, fl, Ed);
+      mark(c, HARMRAD_K_EDGE);
+      k_face<MET, R, 2><<<g, bf, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd);
     }
     mark(c, HARMRAD_K_FACE);
     nk += 2;
@@ -167,11 +169,12 @@ int solve_impl(harmrad_ctx* c, int stage) {
   if (cudaMemsetAsync(c->failed, 0, c->nact, st) != cudaSuccess) return HARMRAD_E_CUDA;
   mark(c, HARMRAD_K_OTHER);
   Bufs b = make_bufs(c);
-  const int gu = grid_for(c->maxact, c->sms, 128);
+  const int bu = c->tune.update_block;
+  const int gu = grid_for(c->maxact, c->sms, bu, c->tune.update_blocks_per_sm);
   if (c->nbox == 1)
-    k_update<MET, R, true><<<gu, 128, 0, st>>>(p, c->boxes[0], c->dboxes, 1, b, stage);
+    k_update<MET, R, true><<<gu, bu, 0, st>>>(p, c->boxes[0], c->dboxes, 1, b, stage);
   else
-    k_update<MET, R, false><<<gu, 128, 0, st>>>(p, c->boxes[0], c->dboxes, c->nbox, b, stage);
+    k_update<MET, R, false><<<gu, bu, 0, st>>>(p, c->boxes[0], c->dboxes, c->nbox, b, stage);
   mark(c, HARMRAD_K_UPDATE);
   // the retry queue and back-up list are short: one persistent wave of blocks
   k_retry<MET><<<c->sms * 2, 128, 0, st>>>(p, c->dboxes, b);

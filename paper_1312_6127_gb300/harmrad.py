@@ -24,9 +24,11 @@ EXPORTS = [
     "harmrad_cfl_dt", "harmrad_step", "harmrad_step_host", "harmrad_get_stats",
     "harmrad_get_status", "harmrad_get_iters", "harmrad_compute_fluxes",
     "harmrad_zone_physics", "harmrad_zone_implicit", "harmrad_zone_implicit_static",
-    "harmrad_profile_step", "harmrad_strerror",
+    "harmrad_profile_step", "harmrad_autotune", "harmrad_get_tuning", "harmrad_set_tuning",
+    "harmrad_strerror",
 ]
-KERNEL_CLASSES = ["bc", "prep", "flatten", "face", "ct", "update", "retry", "backup", "cfl", "other"]
+KERNEL_CLASSES = ["bc", "prep", "flatten", "face", "ct", "update", "retry", "backup", "cfl", "other",
+                  "edge"]
 
 
 class Params(ctypes.Structure):
@@ -78,8 +80,17 @@ class Stats(ctypes.Structure):
 
 
 class KernelTimes(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 10), ("launches", ctypes.c_int * 10),
+    _fields_ = [("ms", ctypes.c_double * 11), ("launches", ctypes.c_int * 11),
                 ("total_launches", ctypes.c_int)]
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [
+        ("face_block", ctypes.c_int), ("face_blocks_per_sm", ctypes.c_int),
+        ("update_block", ctypes.c_int), ("update_blocks_per_sm", ctypes.c_int),
+        ("edge_block", ctypes.c_int), ("edge_blocks_per_sm", ctypes.c_int),
+        ("face_ms", ctypes.c_double), ("update_ms", ctypes.c_double), ("edge_ms", ctypes.c_double),
+    ]
 
 
 class HarmradError(RuntimeError):
@@ -118,6 +129,9 @@ def load(path=LIB_PATH):
     L.harmrad_zone_implicit.argtypes = [pp, ip, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.harmrad_zone_implicit_static.argtypes = [pp, ip, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.harmrad_profile_step.argtypes = [vp, ctypes.c_double, ctypes.POINTER(KernelTimes)]
+    L.harmrad_autotune.argtypes = [vp, ip, ctypes.POINTER(Tuning)]
+    L.harmrad_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+    L.harmrad_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
     L.harmrad_strerror.restype = ctypes.c_char_p
     L.harmrad_strerror.argtypes = [ip]
     _lib = L
@@ -228,6 +242,24 @@ class Grid:
         kt = KernelTimes()
         _check(load().harmrad_profile_step(self._h, float(dt), ctypes.byref(kt)), "profile_step")
         return {name: (kt.ms[i], kt.launches[i]) for i, name in enumerate(KERNEL_CLASSES)}
+
+    def autotune(self, reps=2):
+        """Pick the fastest launch shapes on the current state (state kept)."""
+        t = Tuning()
+        _check(load().harmrad_autotune(self._h, int(reps), ctypes.byref(t)), "autotune")
+        return {k: getattr(t, k) for k, _ in Tuning._fields_}
+
+    def tuning(self):
+        t = Tuning()
+        _check(load().harmrad_get_tuning(self._h, ctypes.byref(t)), "get_tuning")
+        return {k: getattr(t, k) for k, _ in Tuning._fields_}
+
+    def set_tuning(self, **kw):
+        t = Tuning()
+        _check(load().harmrad_get_tuning(self._h, ctypes.byref(t)), "get_tuning")
+        for k, v in kw.items():
+            setattr(t, k, v)
+        _check(load().harmrad_set_tuning(self._h, ctypes.byref(t)), "set_tuning")
 
     def stats(self):
         s = Stats()

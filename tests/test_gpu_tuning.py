@@ -1,0 +1,45 @@
+"""Launch-shape autotuner: the chosen shapes come from the candidate set, the
+call leaves the state unchanged, and steps under any shape give the same
+bytes as the default shapes (every zone runs the same arithmetic)."""
+import numpy as np
+import pytest
+
+from paper_1312_6127_gb300 import harmrad as H
+from paper_1312_6127_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def test_autotune_keeps_state_and_results():
+    cfg, P = W.torus((64, 32, 16), seed=12345)
+    a = H.Grid(cfg)
+    a.set_prims(P)
+    t = a.autotune(reps=1)
+    assert t["face_block"] in (64, 128) and t["update_block"] in (64, 128)
+    assert t["edge_block"] in (128, 256)
+    assert t["face_ms"] > 0 and t["update_ms"] > 0 and t["edge_ms"] > 0
+    assert np.array_equal(a.get_prims(), P)
+    b = H.Grid(cfg)
+    b.set_prims(P)
+    b.set_tuning(face_block=64, face_blocks_per_sm=3, update_block=32, update_blocks_per_sm=5,
+                 edge_block=96, edge_blocks_per_sm=7)
+    c = H.Grid(cfg)
+    c.set_prims(P)
+    for _ in range(2):
+        a.step(0.0)
+        b.step(0.0)
+        c.step(0.0)
+    A, B, C = a.get_prims(), b.get_prims(), c.get_prims()
+    assert np.array_equal(A, C)
+    assert np.array_equal(B, C)
+
+
+def test_set_tuning_rejects_bad_shapes():
+    cfg, P = W.torus((64, 32, 16), seed=12345)
+    g = H.Grid(cfg)
+    with pytest.raises(H.HarmradError):
+        g.set_tuning(face_block=256)
+    with pytest.raises(H.HarmradError):
+        g.set_tuning(update_block=48)
+    with pytest.raises(H.HarmradError):
+        g.set_tuning(edge_blocks_per_sm=0)
