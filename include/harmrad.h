@@ -253,6 +253,31 @@ typedef struct harmrad_kernel_times {
  * the stream.  For benchmarking and profiling. */
 int harmrad_profile_step(harmrad_ctx* ctx, double dt, harmrad_kernel_times* out);
 
+/* Adjoint of the step (reverse-mode derivative), FP64 single-grid contexts.
+ *
+ * harmrad_adjoint_enable(ctx, 1) allocates the adjoint's workspace (about 40
+ * doubles per cell) and makes every later harmrad_step keep a copy of its
+ * input; 0 releases it.  HARMRAD_E_ARG for a batch or split precision.
+ *
+ * harmrad_step_adjoint(ctx, gP_out, gP_in, g_kappa, on_device) differentiates
+ * the last harmrad_step of the context: given gP_out = dL/dP^{n+1} (active
+ * layout [12][n3][n2][n1]) it writes gP_in = dL/dP^n (same layout; may alias
+ * gP_out) and *g_kappa = dL/d kappa_scale (g_kappa may be NULL), with the time
+ * step of that step held fixed.  It recomputes the step from the saved input
+ * (the context's primitives end as that step's result again) and sweeps the
+ * three sub-steps in reverse: implicit solve by the implicit-function theorem
+ * at the converged solution (one transposed 4x4 solve per zone, no unrolled
+ * Newton iterations), explicit update, flux-CT, Riemann fluxes,
+ * reconstruction, flattener, ghost fill, each as the transpose of its local
+ * Jacobian.  Branches (limiters, wave-speed maxima, flattener clamps, outflow
+ * clamps) take the derivative of the branch the step took.  Zones whose
+ * solution a floor changed are constant except for B; back-up zones pass
+ * their cotangent to the neighbours they averaged.  The paper has no adjoint;
+ * this is an extension.  HARMRAD_E_STATE if no step ran since enabling. */
+int harmrad_adjoint_enable(harmrad_ctx* ctx, int on);
+int harmrad_step_adjoint(harmrad_ctx* ctx, const double* gP_out, double* gP_in, double* g_kappa,
+                         int on_device);
+
 /* Launch shapes of the three heaviest kernels: threads per block and the cap
  * on blocks per SM of their grid-stride grids (the grid is the smaller of the
  * work and sms x cap blocks).  Shapes change no result: every zone and face

@@ -9,6 +9,7 @@
 
 #include <vector>
 
+#include "hr_adjoint.cuh"
 #include "hr_ctx.h"
 
 using hr::BoxGeo;
@@ -201,6 +202,9 @@ int run_solve(harmrad_ctx* c, int s) {
 int enqueue_step(harmrad_ctx* c, bool with_cfl) {
   cudaStream_t st = c->stream;
   int nk = 0, r;
+  if (c->adj)  // the adjoint recomputes the step from its input
+    HR_CHECK(cudaMemcpyAsync(c->adj_Pn, c->P, 12 * (size_t)c->ncell * sizeof(double), cudaMemcpyDeviceToDevice,
+                             st));
   HR_CHECK(cudaMemsetAsync(c->status, 0, c->nact, st));
   HR_CHECK(cudaMemsetAsync(c->iters, 0, c->nact * sizeof(int), st));
   HR_CHECK(cudaMemsetAsync(c->stats, 0, 8 * sizeof(unsigned long long), st));
@@ -273,7 +277,22 @@ void drop_graphs(harmrad_ctx* c) {
     }
 }
 
+void free_adjoint(harmrad_ctx* c) {
+  if (c->adj) {
+    hr::AdjBufs& a = *c->adj;
+    void* ptrs[] = {a.Pst, a.chi, a.Ust, a.meth, a.Psol, a.gP, a.gN, a.gUn, a.gU, a.gX, a.gF[0], a.gF[1], a.gF[2],
+                    a.gE, a.gchi, a.carry, a.gaux, a.gemf, a.gk};
+    for (void* q : ptrs)
+      if (q) cudaFree(q);
+    delete c->adj;
+    c->adj = nullptr;
+  }
+  if (c->adj_Pn) cudaFree(c->adj_Pn);
+  c->adj_Pn = nullptr;
+}
+
 void free_all(harmrad_ctx* c) {
+  free_adjoint(c);
   void* ptrs[] = {c->P, c->K, c->Un, c->F[0], c->F[1], c->F[2], c->spd[0], c->spd[1], c->spd[2],
                   c->aux, c->flat[0], c->flat[1], c->flat[2], c->emf, c->edges, c->dt, c->status,
                   c->iters, c->failed, c->qcount, c->qzone, c->qbox, c->qdata, c->fzone, c->fbox,
@@ -509,7 +528,9 @@ int harmrad_step(harmrad_ctx* c, double dt) {
     HR_CHECK(cudaGetLastError());
   }
   c->last_dt = dt;
-  return launch_step(c, with_cfl);
+  int r = launch_step(c, with_cfl);
+  c->adj_ready = c->adj != nullptr && r == HARMRAD_OK;
+  return r;
 }
 
 int harmrad_profile_step(harmrad_ctx* c, double dt, harmrad_kernel_times* out) {
@@ -660,6 +681,71 @@ int harmrad_zone_implicit(const harmrad_params* prm, int n, const double* x, con
               : hr::Run<hr::MINK>::zone_implicit(dp, bg, n, x, Us, Ps, h, Pout, eT, iters, method, st, sms);
   if (r < 0) return r;
   HR_CHECK(cudaStreamSynchronize(st));
+  return HARMRAD_OK;
+}
+
+int harmrad_adjoint_enable(harmrad_ctx* c, int on) {
+  if (!c) return HARMRAD_E_ARG;
+  HR_CHECK(cudaStreamSynchronize(c->stream));
+  drop_graphs(c);
+  c->adj_ready = false;
+  if (!on) {
+    free_adjoint(c);
+    return HARMRAD_OK;
+  }
+  if (c->nbox != 1 || c->real_size != 8) return HARMRAD_E_ARG;
+  if (c->adj) return HARMRAD_OK;
+  c->adj = new hr::AdjBufs();
+  memset(c->adj, 0, sizeof(hr::AdjBufs));
+  hr::AdjBufs& a = *c->adj;
+  const size_t nt = c->ncell, na = c->nact, D = sizeof(double);
+  int rc = HARMRAD_OK;
+  rc = rc ? rc : dalloc(&c->adj_Pn, 12 * nt * D);
+  rc = rc ? rc : dalloc(&a.Pst, 4 * 12 * nt * D);
+  rc = rc ? rc : dalloc(&a.chi, 3 * 3 * 2 * nt * D);
+  rc = rc ? rc : dalloc(&a.Ust, 3 * 12 * na * D);
+  rc = rc ? rc : dalloc(&a.meth, 3 * na);
+  rc = rc ? rc : dalloc(&a.Psol, 3 * 12 * na * D);
+  rc = rc ? rc : dalloc(&a.gP, 12 * nt * D);
+  rc = rc ? rc : dalloc(&a.gN, 12 * na * D);
+  rc = rc ? rc : dalloc(&a.gUn, 12 * na * D);
+  rc = rc ? rc : dalloc(&a.gU, 12 * na * D);
+  rc = rc ? rc : dalloc(&a.gX, 12 * na * D);
+  for (int d = 0; d < 3; ++d) rc = rc ? rc : dalloc(&a.gF[d], 12 * nt * D);
+  rc = rc ? rc : dalloc(&a.gE, 24 * nt * D);
+  rc = rc ? rc : dalloc(&a.gchi, 2 * nt * D);
+  rc = rc ? rc : dalloc(&a.carry, 6 * nt * D);
+  rc = rc ? rc : dalloc(&a.gaux, 3 * nt * D);
+  rc = rc ? rc : dalloc(&a.gemf, nt * D);
+  rc = rc ? rc : dalloc(&a.gk, D);
+  if (!rc && cudaMemsetAsync(a.chi, 0, 3 * 3 * 2 * nt * D, c->stream) != cudaSuccess) rc = HARMRAD_E_CUDA;
+  if (!rc && cudaMemsetAsync(a.gF[0], 0, 12 * nt * D, c->stream) != cudaSuccess) rc = HARMRAD_E_CUDA;
+  if (!rc && cudaMemsetAsync(a.gF[1], 0, 12 * nt * D, c->stream) != cudaSuccess) rc = HARMRAD_E_CUDA;
+  if (!rc && cudaMemsetAsync(a.gF[2], 0, 12 * nt * D, c->stream) != cudaSuccess) rc = HARMRAD_E_CUDA;
+  if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = HARMRAD_E_CUDA;
+  if (rc) free_adjoint(c);
+  return rc;
+}
+
+int harmrad_step_adjoint(harmrad_ctx* c, const double* gP_out, double* gP_in, double* g_kappa, int on_device) {
+  if (!c || !gP_out || !gP_in) return HARMRAD_E_ARG;
+  if (!c->adj || !c->adj_ready) return HARMRAD_E_STATE;
+  const size_t bytes = 12 * (size_t)c->nact * sizeof(double);
+  const double* gin = gP_out;
+  double* gout = gP_in;
+  if (!on_device) {  // stage through the cotangent buffers of the workspace
+    HR_CHECK(cudaMemcpyAsync(c->stage_buf, gP_out, bytes, cudaMemcpyHostToDevice, c->stream));
+    gin = c->stage_buf;
+    gout = c->stage_buf;
+  }
+  int r = c->dp.metric == 1 ? hr::Run<hr::KS>::adjoint(c, gin, gout, nullptr)
+                            : hr::Run<hr::MINK>::adjoint(c, gin, gout, nullptr);
+  if (r < 0) return r;
+  double gk = 0.0;
+  HR_CHECK(cudaMemcpyAsync(&gk, c->adj->gk, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  if (!on_device) HR_CHECK(cudaMemcpyAsync(gP_in, c->stage_buf, bytes, cudaMemcpyDeviceToHost, c->stream));
+  HR_CHECK(cudaStreamSynchronize(c->stream));
+  if (g_kappa) *g_kappa = gk;
   return HARMRAD_OK;
 }
 

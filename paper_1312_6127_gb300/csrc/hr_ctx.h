@@ -7,6 +7,7 @@
 
 namespace hr {
 struct Bufs;
+struct AdjBufs;
 }
 
 struct harmrad_ctx {
@@ -49,6 +50,15 @@ struct harmrad_ctx {
   int* flag;              // validation flag
   double* host_dt;        // pinned host scalar for dt read-back
   bool has_prims;
+  // adjoint (harmrad_adjoint_enable): workspace, the saved input of the last
+  // step, and the record pointers the forward kernels fill while the adjoint
+  // recomputes that step
+  hr::AdjBufs* adj;
+  double* adj_Pn;
+  bool adj_ready;  // a step has run since the adjoint was enabled
+  double* rec_ust;
+  unsigned char* rec_meth;
+  double* rec_psol;
   // launch shapes of the heavy kernels (threads per block, resident-block cap
   // per SM of the grid-stride grid); chosen by harmrad_autotune
   harmrad_tuning tune;
@@ -84,6 +94,8 @@ struct Run {
   static int faces(harmrad_ctx* c, bool fresh);     // ghosts, prep, flattener, fluxes, flux-CT
   static int cfl(harmrad_ctx* c);                   // faces(fresh) + reduction into *dt
   static int solve(harmrad_ctx* c, int stage);      // update + implicit, retry, back-up
+  // reverse sweep of the last step: gPout (device, active layout) -> gPin, gk
+  static int adjoint(harmrad_ctx* c, const double* gPout, double* gPin, double* gk);
   static int zone_physics(const DevParams& dp, const BoxGeo& bg, int n, const double* x,
                           const double* P, double* U, double* SM, double* F, double* speeds,
                           cudaStream_t st, int sms);

@@ -20,62 +20,69 @@
 
 namespace hr {
 
-template <int MET>
-struct ImpSys {
-  Geo<MET, double> g;
-  double Dlab;   // rho0 u^t
-  double iDlab;  // 1 / (rho0 u^t)
-  double Ts[4];  // explicit T^t_nu, rest-mass flux added to the t row
-  double Rs[4];  // explicit R^t_nu
-  double B[3];
-  double h;      // b_s dt
-  double kf;     // the zone's absorption opacity when it is a per-zone field
-  double sgk[3]; // sqrt(gamma^{kk}) of the ZAMO slice
+// The implicit system of one zone.  T is double in the step; the adjoint
+// evaluates the same functions on dual numbers.
+template <int MET, typename T = double>
+struct ImpSysT {
+  Geo<MET, T> g;
+  T Dlab;   // rho0 u^t
+  T iDlab;  // 1 / (rho0 u^t)
+  T Ts[4];  // explicit T^t_nu, rest-mass flux added to the t row
+  T Rs[4];  // explicit R^t_nu
+  T B[3];
+  T h;      // b_s dt
+  T kf;     // the zone's absorption opacity when it is a per-zone field
+  T ks;     // global opacity scale kappa_scale
+  T sgk[3]; // sqrt(gamma^{kk}) of the ZAMO slice
 };
+template <int MET>
+using ImpSys = ImpSysT<MET, double>;
 
-struct ImpRes {
-  double Eg[4], Er[4];
-  double eT, eI;
+template <typename T = double>
+struct ImpResT {
+  T Eg[4], Er[4];
+  T eT, eI;
   int negE;
   bool ok;
 };
+using ImpRes = ImpResT<double>;
 
 // Gas and radiation state of an iterate: the pieces of the residual that the
 // final primitives need.
-struct ImpState {
-  double rho, ug, Pr[4];
-  double Rt_pre[4];
+template <typename T = double>
+struct ImpStateT {
+  T rho, ug, Pr[4];
+  T Rt_pre[4];
 };
+using ImpState = ImpStateT<double>;
 
 // G_nu for gas temperature T (given, so the caller can form it without a
 // division).
-template <int MET>
-__device__ __forceinline__ void four_force_rad(const DevParams& p, double rho, double T, double kf,
-                                               const double ucon[4], const double ucov[4],
-                                               const double urc[4], const double urv[4], double E,
-                                               double G[4]) {
-  double kabs, ksca;
-  opacity_T<double>(p, rho, T, kf, &kabs, &ksca);
-  double T2 = T * T;
-  double lam = kabs * p.a_rad * T2 * T2;
-  double uru = urv[0] * ucon[0] + urv[1] * ucon[1] + urv[2] * ucon[2] + urv[3] * ucon[3];
-  double c1 = (4.0 / 3.0) * E * uru, c2 = E * (1.0 / 3.0);
-  double uRu = c1 * uru - c2;
-  double kt = kabs + ksca;
-  double A = -kt * c1;
-  double C = -(kt * c2 + lam + ksca * uRu);
+template <int MET, typename T = double>
+__device__ __forceinline__ void four_force_rad(const DevParams& p, T rho, T Tg, T kf, T ks, const T ucon[4],
+                                               const T ucov[4], const T urc[4], const T urv[4], T E,
+                                               T G[4]) {
+  T kabs, ksca;
+  opacity_ks<T>(p, rho, Tg, kf, ks, &kabs, &ksca);
+  T T2 = Tg * Tg;
+  T lam = kabs * p.a_rad * T2 * T2;
+  T uru = urv[0] * ucon[0] + urv[1] * ucon[1] + urv[2] * ucon[2] + urv[3] * ucon[3];
+  T c1 = (4.0 / 3.0) * E * uru, c2 = E * (1.0 / 3.0);
+  T uRu = c1 * uru - c2;
+  T kt = kabs + ksca;
+  T A = -kt * c1;
+  T C = -(kt * c2 + lam + ksca * uRu);
   (void)urc;
 #pragma unroll
   for (int n = 0; n < 4; ++n) G[n] = A * urv[n] + C * ucov[n];
 }
 
-template <int MET>
-__device__ __forceinline__ void normalise(const ImpSys<MET>& s, const double Tc[4],
-                                          const double Rc[4], const double G[4], bool iter_gas,
-                                          ImpRes& r) {
-  double dg0 = fabs(Tc[0]) + fabs(s.Ts[0]) + s.h * fabs(G[0]);
-  double dr0 = fabs(Rc[0]) + fabs(s.Rs[0]) + s.h * fabs(G[0]);
-  double dgs = 0.0, drs = 0.0;
+template <int MET, typename T = double>
+__device__ __forceinline__ void normalise(const ImpSysT<MET, T>& s, const T Tc[4], const T Rc[4],
+                                          const T G[4], bool iter_gas, ImpResT<T>& r) {
+  T dg0 = fabs(Tc[0]) + fabs(s.Ts[0]) + s.h * fabs(G[0]);
+  T dr0 = fabs(Rc[0]) + fabs(s.Rs[0]) + s.h * fabs(G[0]);
+  T dgs = T(0.0), drs = T(0.0);
 #pragma unroll
   for (int k = 1; k < 4; ++k) {
     dgs += s.sgk[k - 1] * (fabs(Tc[k]) + fabs(s.Ts[k]) + s.h * fabs(G[k]));
@@ -85,17 +92,17 @@ __device__ __forceinline__ void normalise(const ImpSys<MET>& s, const double Tc[
   // by energy; a field at rest must not divide round-off by round-off)
   dgs += dg0;
   drs += dr0;
-  double eg[4], er[4];
-  eg[0] = dg0 > 0.0 ? fabs(r.Eg[0]) / dg0 : 0.0;
-  er[0] = dr0 > 0.0 ? fabs(r.Er[0]) / dr0 : 0.0;
-  double idgs = dgs > 0.0 ? 1.0 / dgs : 0.0, idrs = drs > 0.0 ? 1.0 / drs : 0.0;
+  T eg[4], er[4];
+  eg[0] = dg0 > 0.0 ? fabs(r.Eg[0]) / dg0 : T(0.0);
+  er[0] = dr0 > 0.0 ? fabs(r.Er[0]) / dr0 : T(0.0);
+  T idgs = dgs > 0.0 ? 1.0 / dgs : T(0.0), idrs = drs > 0.0 ? 1.0 / drs : T(0.0);
 #pragma unroll
   for (int k = 1; k < 4; ++k) {
     eg[k] = fabs(r.Eg[k]) * s.sgk[k - 1] * idgs;
     er[k] = fabs(r.Er[k]) * s.sgk[k - 1] * idrs;
   }
-  if (r.negE) eg[0] = er[0] = 0.0;
-  double sT = 0.0, sI = 0.0;
+  if (r.negE) eg[0] = er[0] = T(0.0);
+  T sT = T(0.0), sI = T(0.0);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     sT += fmax(eg[k], er[k]);
@@ -106,43 +113,49 @@ __device__ __forceinline__ void normalise(const ImpSys<MET>& s, const double Tc[
 }
 
 // PMHD error function.  With norm == false only Eg is formed (Jacobian columns).
-template <int MET>
-__device__ __forceinline__ void pmhd_res(const DevParams& p, const ImpSys<MET>& s, const double x[4],
-                                         ImpRes& r, ImpState* st, bool norm) {
+template <class X>
+struct nondeduced {
+  using type = X;
+};
+
+template <int MET, typename T = double>
+__device__ __forceinline__ void pmhd_res(const DevParams& p, const ImpSysT<MET, T>& s, const T x[4],
+                                         ImpResT<T>& r, typename nondeduced<ImpStateT<T>>::type* st,
+                                         bool norm) {
   const auto& g = s.g;
-  double ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq;
-  fourvel<MET, double>(g, x[1], x[2], x[3], ucon, ucov, &gm);
-  const double iut = g.alpha / gm;  // 1/u^t
-  double rho = s.Dlab * iut;
-  bvec_iut<MET, double>(g, ucon, ucov, iut, s.B[0], s.B[1], s.B[2], bcon, bcov, &bsq);
-  double pg = (p.gam - 1.0) * x[0];
-  double wb = rho + x[0] + pg + bsq, pt = pg + 0.5 * bsq;
-  double Tc[4];
+  T ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq;
+  fourvel<MET, T>(g, x[1], x[2], x[3], ucon, ucov, &gm);
+  const T iut = g.alpha / gm;  // 1/u^t
+  T rho = s.Dlab * iut;
+  bvec_iut<MET, T>(g, ucon, ucov, iut, s.B[0], s.B[1], s.B[2], bcon, bcov, &bsq);
+  T pg = (p.gam - 1.0) * x[0];
+  T wb = rho + x[0] + pg + bsq, pt = pg + 0.5 * bsq;
+  T Tc[4];
   Tc[0] = wb * ucon[0] * ucov[0] + pt - bcon[0] * bcov[0] + rho * ucon[0];
 #pragma unroll
   for (int k = 1; k < 4; ++k) Tc[k] = wb * ucon[0] * ucov[k] - bcon[0] * bcov[k];
-  double Rt[4];
+  T Rt[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) Rt[k] = s.Rs[k] - (Tc[k] - s.Ts[k]);
-  double Pr[4];
-  r.negE = rad_invert<MET>(p, g, Rt, 2, Pr);
-  double urc[4], urv[4], gr;
-  fourvel<MET, double>(g, Pr[1], Pr[2], Pr[3], urc, urv, &gr);
-  double G[4];
+  T Pr[4];
+  r.negE = rad_invert<MET, T>(p, g, Rt, 2, Pr);
+  T urc[4], urv[4], gr;
+  fourvel<MET, T>(g, Pr[1], Pr[2], Pr[3], urc, urv, &gr);
+  T G[4];
   // T = p_g / rho0 = (gamma-1) u_g u^t / (rho0 u^t)
-  four_force_rad<MET>(p, rho, (p.gam - 1.0) * x[0] * ucon[0] * s.iDlab, s.kf, ucon, ucov, urc, urv,
-                      Pr[0], G);
+  four_force_rad<MET, T>(p, rho, (p.gam - 1.0) * x[0] * ucon[0] * s.iDlab, s.kf, s.ks, ucon, ucov, urc,
+                         urv, Pr[0], G);
 #pragma unroll
   for (int k = 0; k < 4; ++k) r.Eg[k] = Tc[k] - s.Ts[k] - s.h * G[k];
   if (norm) {
-    double e43 = (4.0 / 3.0) * Pr[0];
-    double Rc[4];
+    T e43 = (4.0 / 3.0) * Pr[0];
+    T Rc[4];
     Rc[0] = e43 * urc[0] * urv[0] + Pr[0] * (1.0 / 3.0);
 #pragma unroll
     for (int k = 1; k < 4; ++k) Rc[k] = e43 * urc[0] * urv[k];
 #pragma unroll
     for (int k = 0; k < 4; ++k) r.Er[k] = Rc[k] - s.Rs[k] + s.h * G[k];
-    normalise<MET>(s, Tc, Rc, G, true, r);
+    normalise<MET, T>(s, Tc, Rc, G, true, r);
     r.ok = isfinite(r.eT);
   } else {
     r.ok = true;
@@ -340,7 +353,7 @@ __device__ __forceinline__ bool urad_res(const DevParams& p, const ImpSys<MET>& 
 #pragma unroll
   for (int k = 1; k < 4; ++k) Rc[k] = e43 * urc[0] * urv[k];
   double G[4];
-  four_force_rad<MET>(p, rho, (p.gam - 1.0) * ug / rho, s.kf, ucon, ucov, urc, urv, Pr[0], G);
+  four_force_rad<MET>(p, rho, (p.gam - 1.0) * ug / rho, s.kf, s.ks, ucon, ucov, urc, urv, Pr[0], G);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     r.Eg[k] = Tc[k] - s.Ts[k] - s.h * G[k];
@@ -441,12 +454,13 @@ __device__ int newton_urad(const DevParams& p, const ImpSys<MET>& s, const doubl
   return steps;
 }
 
-template <int MET>
-__device__ __forceinline__ void build_sys(const DevParams& p, const Geo<MET, double>& g,
-                                          const double Us[12], double h, double kf, ImpSys<MET>& s) {
+template <int MET, typename T = double>
+__device__ __forceinline__ void build_sys(const DevParams& p, const Geo<MET, T>& g, const T Us[12], double h,
+                                          T kf, ImpSysT<MET, T>& s) {
   s.g = g;
   s.kf = kf;
-  double igd = 1.0 / g.gdet;
+  s.ks = T(p.kscale);
+  T igd = 1.0 / g.gdet;
   s.Dlab = Us[0] * igd;
   s.iDlab = 1.0 / s.Dlab;
 #pragma unroll
@@ -456,7 +470,7 @@ __device__ __forceinline__ void build_sys(const DevParams& p, const Geo<MET, dou
   }
 #pragma unroll
   for (int i = 0; i < 3; ++i) s.B[i] = Us[5 + i] * igd;
-  s.h = h;
+  s.h = T(h);
   // orthonormal (ZAMO) size of covariant spatial components:
   // sqrt(gamma^{kk}), gamma^{kk} = g^{kk} - (g^{tk})^2 / g^{tt} > 0 everywhere
   // on the slice, inside the horizon too

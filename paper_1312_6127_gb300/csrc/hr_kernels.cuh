@@ -41,6 +41,10 @@ struct Bufs {
   double* ftmp;           // [nact][12] averaged primitives of back-up zones
   unsigned long long* stats;  // [8] counters
   unsigned long long* dtmin;  // [nbox] CFL minimum (ordered bits of a positive double)
+  // records for the adjoint's recomputation of a step (null otherwise):
+  double* ust_rec;            // [12][nact] U* of every zone of the sub-step
+  unsigned char* meth_rec;    // [nact] outcome of every zone of the sub-step
+  double* psol_rec;           // [12][nact] solution of every zone before the floors
 };
 
 // Counter update aggregated over the converged lanes of a warp.
@@ -191,6 +195,24 @@ __device__ __forceinline__ R ftilde(const FlatCell<R>* c, int m, bool gas, R w) 
   return R(0);
 }
 
+// Flattener of the centre cell c[3] of a 7-cell stencil (GAS, RAD).
+template <typename R>
+__device__ __forceinline__ void flatten_cell(const FlatCell<R>* c, R* Fg, R* Fr) {
+  const R w = c[3].w;
+  R g0 = ftilde<R>(c, 3, true, w), r0 = ftilde<R>(c, 3, false, w);
+  R pg1 = c[4].pg + w * c[4].pr, pgm = c[2].pg + w * c[2].pr;
+  R pr1 = c[4].pr + w * c[4].pg, prm = c[2].pr + w * c[2].pg;
+  int sg = (pg1 - pgm) < R(0) ? 1 : -1;
+  int sr = (pr1 - prm) < R(0) ? 1 : -1;
+  R gn = ftilde<R>(c, 3 + sg, true, c[3 + sg].w);
+  R rn = ftilde<R>(c, 3 + sr, false, c[3 + sr].w);
+  R fg = g0 > gn ? g0 : gn;
+  R fr = r0 > rn ? r0 : rn;
+  R mx = fg > fr ? fg : fr;
+  *Fg = (R(1) - w) * fg + w * mx;
+  *Fr = (R(1) - w) * fr + w * mx;
+}
+
 template <typename R>
 __global__ void k_flatten(DevParams p, const BoxGeo* __restrict__ boxes, int nbox,
                           const double* __restrict__ P0, const R* __restrict__ aux0,
@@ -229,19 +251,8 @@ __global__ void k_flatten(DevParams p, const BoxGeo* __restrict__ boxes, int nbo
         c[m].vr = aux[(2 + 3 * d) * bx.ntot + cm];
         c[m].w = aux[(3 + 3 * d) * bx.ntot + cm];
       }
-      const R w = c[3].w;
-      R g0 = ftilde<R>(c, 3, true, w), r0 = ftilde<R>(c, 3, false, w);
-      R pg1 = c[4].pg + w * c[4].pr, pgm = c[2].pg + w * c[2].pr;
-      R pr1 = c[4].pr + w * c[4].pg, prm = c[2].pr + w * c[2].pg;
-      int sg = (pg1 - pgm) < R(0) ? 1 : -1;
-      int sr = (pr1 - prm) < R(0) ? 1 : -1;
-      R gn = ftilde<R>(c, 3 + sg, true, c[3 + sg].w);
-      R rn = ftilde<R>(c, 3 + sr, false, c[3 + sr].w);
-      R fg = g0 > gn ? g0 : gn;
-      R fr = r0 > rn ? r0 : rn;
-      R mx = fg > fr ? fg : fr;
-      R Fg = (R(1) - w) * fg + w * mx;
-      R Fr = (R(1) - w) * fr + w * mx;
+      R Fg, Fr;
+      flatten_cell<R>(c, &Fg, &Fr);
       R og = flat[t], orr = flat[bx.ntot + t];
       flat[t] = Fg > og ? Fg : og;
       flat[bx.ntot + t] = Fr > orr ? Fr : orr;
@@ -360,6 +371,61 @@ __global__ void __launch_bounds__(256) k_edges(DevParams p, const BoxGeo* __rest
   }
 }
 
+// Riemann flux through one face of direction d (0-based) from the two
+// reconstructed states: both states' gas and radiation signal speeds, then
+// HLL or LAXF (Eqs. hll, lax), the gas and radiation groups with their own
+// speeds; F[B_d] = 0.  smax: the largest signal speed (for the CFL step).
+// Used by the face kernel and, on dual numbers, by the adjoint.
+template <int MET, typename R, int d>
+__device__ __forceinline__ void face_flux(const DevParams& p, const Geo<MET, R>& g, R dxd, R kL, R kR, R ks,
+                                          const R PL[NPR], const R PR[NPR], R out[NPR], R* smax) {
+  R sL[4], sR[4];
+  face_speeds<MET, R>(p, g, d + 1, dxd, kL, ks, PL, sL);
+  face_speeds<MET, R>(p, g, d + 1, dxd, kR, ks, PR, sR);
+  R cmaxg = fmax(R(0), fmax(sL[1], sR[1]));
+  R cming = -fmin(R(0), fmin(sL[0], sR[0]));
+  R cmaxr = fmax(R(0), fmax(sL[3], sR[3]));
+  R cminr = -fmin(R(0), fmin(sL[2], sR[2]));
+  // weights of (F_L, U_L) and (F_R, U_R) in the flux, gas and radiation groups
+  R fLg, uLg, fRg, uRg, fLr, uLr, fRr, uRr;
+  if (p.flux == 0) {  // LAXF: 1/2 (F_L + F_R - c (U_R - U_L))
+    R cg = cmaxg > cming ? cmaxg : cming, cr = cmaxr > cminr ? cmaxr : cminr;
+    fLg = fRg = fLr = fRr = R(0.5);
+    uLg = R(0.5) * cg;
+    uRg = -uLg;
+    uLr = R(0.5) * cr;
+    uRr = -uLr;
+  } else {  // HLL: (c- F_R + c+ F_L - c- c+ (U_R - U_L)) / (c- + c+)
+    R sg = cmaxg + cming, sr = cmaxr + cminr;
+    if (sg > R(0)) {
+      R isg = R(1) / sg;
+      fLg = cmaxg * isg;
+      fRg = cming * isg;
+      uLg = cming * cmaxg * isg;
+      uRg = -uLg;
+    } else {
+      fLg = fRg = R(0.5);
+      uLg = uRg = R(0);
+    }
+    if (sr > R(0)) {
+      R isr = R(1) / sr;
+      fLr = cmaxr * isr;
+      fRr = cminr * isr;
+      uLr = cminr * cmaxr * isr;
+      uRr = -uLr;
+    } else {
+      fLr = fRr = R(0.5);
+      uLr = uRr = R(0);
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NPR; ++q) out[q] = R(0);
+  face_accum<MET, R>(p, g, d + 1, PL, fLg, uLg, fLr, uLr, out);
+  face_accum<MET, R>(p, g, d + 1, PR, fRg, uRg, fRr, uRr, out);
+  out[B1 + d] = R(0);
+  *smax = fmax(fmax(cmaxg, cming), fmax(cmaxr, cminr));
+}
+
 // ----------------------------------------------------------------- fluxes
 // One thread per face of direction d (faces 0..n_d, transverse range widened
 // by one layer for the EMF averages).  Reads the two reconstructed states
@@ -424,53 +490,11 @@ __global__ void __launch_bounds__(128) k_face(DevParams p, const BoxGeo* __restr
         PR[q] = wq ? bL * igf : bL;
       }
       const R kL = R(kfield(p, K, t - st)), kR = R(kfield(p, K, t));
-      R sL[4], sR[4];
-      face_speeds<MET, R>(p, g, d + 1, dxd, kL, PL, sL);
-      face_speeds<MET, R>(p, g, d + 1, dxd, kR, PR, sR);
-      R cmaxg = fmax(R(0), fmax(sL[1], sR[1]));
-      R cming = -fmin(R(0), fmin(sL[0], sR[0]));
-      R cmaxr = fmax(R(0), fmax(sL[3], sR[3]));
-      R cminr = -fmin(R(0), fmin(sL[2], sR[2]));
-      // weights of (F_L, U_L) and (F_R, U_R) in the flux, gas and radiation groups
-      R fLg, uLg, fRg, uRg, fLr, uLr, fRr, uRr;
-      if (p.flux == 0) {  // LAXF: 1/2 (F_L + F_R - c (U_R - U_L))
-        R cg = cmaxg > cming ? cmaxg : cming, cr = cmaxr > cminr ? cmaxr : cminr;
-        fLg = fRg = fLr = fRr = R(0.5);
-        uLg = R(0.5) * cg;
-        uRg = -uLg;
-        uLr = R(0.5) * cr;
-        uRr = -uLr;
-      } else {  // HLL: (c- F_R + c+ F_L - c- c+ (U_R - U_L)) / (c- + c+)
-        R sg = cmaxg + cming, sr = cmaxr + cminr;
-        if (sg > R(0)) {
-          R isg = R(1) / sg;
-          fLg = cmaxg * isg;
-          fRg = cming * isg;
-          uLg = cming * cmaxg * isg;
-          uRg = -uLg;
-        } else {
-          fLg = fRg = R(0.5);
-          uLg = uRg = R(0);
-        }
-        if (sr > R(0)) {
-          R isr = R(1) / sr;
-          fLr = cmaxr * isr;
-          fRr = cminr * isr;
-          uLr = cminr * cmaxr * isr;
-          uRr = -uLr;
-        } else {
-          fLr = fRr = R(0.5);
-          uLr = uRr = R(0);
-        }
-      }
-      R out[NPR];
+      R out[NPR], smax;
+      face_flux<MET, R, d>(p, g, dxd, kL, kR, R(p.kscale), PL, PR, out, &smax);
 #pragma unroll
-      for (int q = 0; q < NPR; ++q) out[q] = R(0);
-      face_accum<MET, R>(p, g, d + 1, PL, fLg, uLg, fLr, uLr, out);
-      face_accum<MET, R>(p, g, d + 1, PR, fRg, uRg, fRr, uRr, out);
-#pragma unroll
-      for (int q = 0; q < NPR; ++q) F[q * bx.ntot + t] = (q == B1 + d) ? R(0) : out[q];
-      spd[t] = fmax(fmax(cmaxg, cming), fmax(cmaxr, cminr));
+      for (int q = 0; q < NPR; ++q) F[q * bx.ntot + t] = out[q];
+      spd[t] = smax;
     }
   }
 }
@@ -541,44 +565,45 @@ __global__ void k_ct(DevParams p, const BoxGeo* __restrict__ boxes, int nbox, co
 // ----------------------------------------------------------------- floors
 // Lorentz-factor caps, density and internal-energy floors f0 r^pow,
 // magnetisation caps b^2/rho, b^2/u_g, u_g/rho, and Ebar > 0.
-template <int MET>
-__device__ __forceinline__ void apply_floors(const DevParams& p, const Geo<MET, double>& g, double r,
-                                             double P[NPR]) {
-  double gm = sqrt(1.0 + g.sq3(P[U1], P[U2], P[U3]));
+template <int MET, typename T = double>
+__device__ __forceinline__ void apply_floors(const DevParams& p, const Geo<MET, T>& g, double r, T P[NPR]) {
+  T gm = sqrt(1.0 + g.sq3(P[U1], P[U2], P[U3]));
   if (gm > p.ggas_max) {
-    double f = sqrt((p.ggas_max * p.ggas_max - 1.0) / (gm * gm - 1.0));
+    T f = sqrt((p.ggas_max * p.ggas_max - 1.0) / (gm * gm - 1.0));
     P[U1] *= f;
     P[U2] *= f;
     P[U3] *= f;
   }
-  double gr = sqrt(1.0 + g.sq3(P[UR1], P[UR2], P[UR3]));
+  T gr = sqrt(1.0 + g.sq3(P[UR1], P[UR2], P[UR3]));
   if (gr > p.grad_max) {
-    double f = sqrt((p.grad_max * p.grad_max - 1.0) / (gr * gr - 1.0));
+    T f = sqrt((p.grad_max * p.grad_max - 1.0) / (gr * gr - 1.0));
     P[UR1] *= f;
     P[UR2] *= f;
     P[UR3] *= f;
   }
-  double ucon[4], ucov[4], bcon[4], bcov[4], bsq;
-  fourvel<MET, double>(g, P[U1], P[U2], P[U3], ucon, ucov, &gm);
-  bvec<MET, double>(g, ucon, ucov, P[B1], P[B2], P[B3], bcon, bcov, &bsq);
-  double rfl = p.rf0 * (p.rfp == 0.0 ? 1.0 : pow(r, p.rfp));
-  double ufl = p.uf0 * (p.ufp == 0.0 ? 1.0 : pow(r, p.ufp));
+  T ucon[4], ucov[4], bcon[4], bcov[4], bsq;
+  fourvel<MET, T>(g, P[U1], P[U2], P[U3], ucon, ucov, &gm);
+  bvec<MET, T>(g, ucon, ucov, P[B1], P[B2], P[B3], bcon, bcov, &bsq);
+  T rfl = T(p.rf0 * (p.rfp == 0.0 ? 1.0 : pow(r, p.rfp)));
+  T ufl = T(p.uf0 * (p.ufp == 0.0 ? 1.0 : pow(r, p.ufp)));
   rfl = fmax(rfl, bsq / p.bsq_rho_max);
   ufl = fmax(ufl, bsq / p.bsq_u_max);
   P[RHO] = fmax(P[RHO], rfl);
   P[UU] = fmax(P[UU], ufl);
   P[RHO] = fmax(P[RHO], P[UU] / p.u_rho_max);
-  if (!(P[ER] > 0.0)) P[ER] = 1e-150;
+  if (!(P[ER] > 0.0)) P[ER] = T(1e-150);
 }
 
 // Final primitives of an accepted PMHD iterate: gas from x, B fixed, radiation
 // re-inverted with BASIC if the TYPE2 branch saw a negative energy (Sec. 4.10).
-template <int MET>
-__device__ __forceinline__ void pmhd_final(const DevParams& p, const ImpSys<MET>& s, const double x[4],
-                                           double P[NPR]) {
-  ImpRes r;
-  ImpState stt;
-  pmhd_res<MET>(p, s, x, r, &stt, false);
+template <int MET, typename T = double>
+__device__ __forceinline__ void pmhd_final(const DevParams& p, const ImpSysT<MET, T>& s, const T x[4], T P[NPR],
+                                           T* Eg = nullptr) {
+  ImpResT<T> r;
+  ImpStateT<T> stt;
+  pmhd_res<MET, T>(p, s, x, r, &stt, false);
+  if (Eg)
+    for (int k = 0; k < 4; ++k) Eg[k] = r.Eg[k];
   P[RHO] = stt.rho;
   P[UU] = x[0];
   P[U1] = x[1];
@@ -587,8 +612,8 @@ __device__ __forceinline__ void pmhd_final(const DevParams& p, const ImpSys<MET>
   P[B1] = s.B[0];
   P[B2] = s.B[1];
   P[B3] = s.B[2];
-  double Pr[4] = {stt.Pr[0], stt.Pr[1], stt.Pr[2], stt.Pr[3]};
-  if (r.negE) rad_invert<MET>(p, s.g, stt.Rt_pre, 0, Pr);
+  T Pr[4] = {stt.Pr[0], stt.Pr[1], stt.Pr[2], stt.Pr[3]};
+  if (r.negE) rad_invert<MET, T>(p, s.g, stt.Rt_pre, 0, Pr);
   P[ER] = Pr[0];
   P[UR1] = Pr[1];
   P[UR2] = Pr[2];
@@ -654,10 +679,51 @@ __device__ __forceinline__ MetricDeriv ks_derivs(const DevParams& p, double x1, 
 }
 
 // v^mu v^kappa d_nu g_{mu kappa}
-__device__ __forceinline__ double qform(const MetricDeriv& m, int n, const double v[4]) {
+template <typename T>
+__device__ __forceinline__ T qform(const MetricDeriv& m, int n, const T v[4]) {
   return m.g00[n] * v[0] * v[0] + 2.0 * m.g01[n] * v[0] * v[1] + 2.0 * m.g03[n] * v[0] * v[3] +
          m.g11[n] * v[1] * v[1] + 2.0 * m.g13[n] * v[1] * v[3] + m.g22[n] * v[2] * v[2] +
          m.g33[n] * v[3] * v[3];
+}
+
+// U(P) and the geometric source SM(P) of one zone (X = SM on return):
+// SM_nu = 1/2 sqrt(-g) T^{mu kappa} d_nu g_{mu kappa}, equal to
+// sqrt(-g) T^kappa_lambda Gamma^lambda_{nu kappa} for a symmetric T and nonzero
+// only for nu = x1, x2 on the stationary axisymmetric metric.
+template <int MET, typename T>
+__device__ __forceinline__ void cons_source(const DevParams& p, const Geo<MET, T>& g, double x1, double x2,
+                                            const T Ps[NPR], T Us[NPR], T X[NPR]) {
+  T ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq, urc[4], urv[4], gr;
+  fourvel<MET, T>(g, Ps[U1], Ps[U2], Ps[U3], ucon, ucov, &gm);
+  bvec<MET, T>(g, ucon, ucov, Ps[B1], Ps[B2], Ps[B3], bcon, bcov, &bsq);
+  fourvel<MET, T>(g, Ps[UR1], Ps[UR2], Ps[UR3], urc, urv, &gr);
+  const T pg = (p.gam - 1.0) * Ps[UU];
+  const T wb = Ps[RHO] + Ps[UU] + pg + bsq, pt = pg + 0.5 * bsq;
+  const T gd = g.gdet, mt = Ps[RHO] * ucon[0];
+  const T E = Ps[ER], e43 = (4.0 / 3.0) * E;
+  Us[0] = gd * mt;
+  Us[1] = gd * (wb * ucon[0] * ucov[0] + pt - bcon[0] * bcov[0] + mt);
+#pragma unroll
+  for (int n = 1; n < 4; ++n) Us[1 + n] = gd * (wb * ucon[0] * ucov[n] - bcon[0] * bcov[n]);
+  Us[5] = gd * Ps[B1];
+  Us[6] = gd * Ps[B2];
+  Us[7] = gd * Ps[B3];
+  Us[8] = gd * (e43 * urc[0] * urv[0] + E * (1.0 / 3.0));
+#pragma unroll
+  for (int n = 1; n < 4; ++n) Us[8 + n] = gd * (e43 * urc[0] * urv[n]);
+#pragma unroll
+  for (int q = 0; q < NPR; ++q) X[q] = T(0.0);
+  if constexpr (MET == KS) {
+    MetricDeriv md = ks_derivs(p, x1, x2);
+#pragma unroll
+    for (int n = 0; n < 2; ++n) {
+      T qu = qform(md, n, ucon), qb = qform(md, n, bcon), qr = qform(md, n, urc);
+      X[2 + n] = 0.5 * gd * (wb * qu - qb) + pt * md.sg[n];
+      X[9 + n] = 0.5 * gd * e43 * qr + E * (1.0 / 3.0) * md.sg[n];
+    }
+  }
+  (void)x1;
+  (void)x2;
 }
 
 // ------------------------------------------------------- update + implicit
@@ -693,38 +759,8 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
 #pragma unroll
       for (int q = 0; q < NPR; ++q) Ps[q] = P[q * bx.ntot + t];
       const double kz = kfield(p, K, t);
-      // U(P_s)
-      double ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq, urc[4], urv[4], gr;
-      fourvel<MET, double>(g, Ps[U1], Ps[U2], Ps[U3], ucon, ucov, &gm);
-      bvec<MET, double>(g, ucon, ucov, Ps[B1], Ps[B2], Ps[B3], bcon, bcov, &bsq);
-      fourvel<MET, double>(g, Ps[UR1], Ps[UR2], Ps[UR3], urc, urv, &gr);
-      const double pg = (p.gam - 1.0) * Ps[UU];
-      const double wb = Ps[RHO] + Ps[UU] + pg + bsq, pt = pg + 0.5 * bsq;
-      const double gd = g.gdet, mt = Ps[RHO] * ucon[0];
-      const double E = Ps[ER], e43 = (4.0 / 3.0) * E;
-      double Us[NPR];
-      Us[0] = gd * mt;
-      Us[1] = gd * (wb * ucon[0] * ucov[0] + pt - bcon[0] * bcov[0] + mt);
-#pragma unroll
-      for (int n = 1; n < 4; ++n) Us[1 + n] = gd * (wb * ucon[0] * ucov[n] - bcon[0] * bcov[n]);
-      Us[5] = gd * Ps[B1];
-      Us[6] = gd * Ps[B2];
-      Us[7] = gd * Ps[B3];
-      Us[8] = gd * (e43 * urc[0] * urv[0] + E * (1.0 / 3.0));
-#pragma unroll
-      for (int n = 1; n < 4; ++n) Us[8 + n] = gd * (e43 * urc[0] * urv[n]);
-      double X[NPR];
-#pragma unroll
-      for (int q = 0; q < NPR; ++q) X[q] = 0.0;
-      if constexpr (MET == KS) {
-        MetricDeriv md = ks_derivs(p, x1, x2);
-#pragma unroll
-        for (int n = 0; n < 2; ++n) {
-          double qu = qform(md, n, ucon), qb = qform(md, n, bcon), qr = qform(md, n, urc);
-          X[2 + n] = 0.5 * gd * (wb * qu - qb) + pt * md.sg[n];
-          X[9 + n] = 0.5 * gd * e43 * qr + E * (1.0 / 3.0) * md.sg[n];
-        }
-      }
+      double Us[NPR], X[NPR];
+      cons_source<MET, double>(p, g, x1, x2, Ps, Us, X);
       // flux divergence
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
@@ -748,6 +784,10 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
           un = Un[q * bx.nact + z];
         }
         Ust[q] = A * un + Bc * (Us[q] + dt * X[q]);
+      }
+      if (b.ust_rec) {
+#pragma unroll
+        for (int q = 0; q < NPR; ++q) b.ust_rec[q * bx.nact + z] = Ust[q];
       }
       // implicit solve
       const double h = Bc * dt;
@@ -780,9 +820,12 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
       if (accept) {
         double Pn[NPR];
         pmhd_final<MET>(p, s, bxn, Pn);
+        if (b.psol_rec)
+          for (int q = 0; q < NPR; ++q) b.psol_rec[q * bx.nact + z] = Pn[q];
         apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn);
 #pragma unroll
         for (int q = 0; q < NPR; ++q) P[q * bx.ntot + t] = Pn[q];
+        if (b.meth_rec) b.meth_rec[zg] = ST_PMHD;
       } else {
         int slot = atomicAdd(&b.qcount[0], 1);
         b.qzone[slot] = (int)z;
@@ -910,10 +953,13 @@ __global__ void __launch_bounds__(128) k_retry(DevParams p, const BoxGeo* __rest
       eT = HUGE_VAL;
     }
     if (eT > 1e-7) method = ST_BACKUP;
+    if (b.psol_rec)
+      for (int q = 0; q < NPR; ++q) b.psol_rec[q * bx.nact + z] = Pn[q];
     apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn);
     for (int q = 0; q < NPR; ++q) P[q * bx.ntot + t] = Pn[q];
     unsigned char m = (unsigned char)method;
     if (m > b.status[zg]) b.status[zg] = m;
+    if (b.meth_rec) b.meth_rec[zg] = m;
     if (method == ST_BACKUP) {
       b.failed[zg] = 1;
       int slot = atomicAdd(&b.qcount[1], 1);

@@ -9,6 +9,9 @@
 // are written for the sparsity of the Kerr-Schild metric in (t, r, theta, phi)
 // charts: g_{t theta} = g_{r theta} = g_{theta phi} = 0 and g^{t phi} = 0.
 #pragma once
+#include <type_traits>
+
+#include "hr_dual.cuh"
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -110,9 +113,21 @@ struct Geo {
   }
 };
 
-template <typename R> __device__ __forceinline__ R rsqrt_(R x);
-template <> __device__ __forceinline__ double rsqrt_<double>(double x) { return rsqrt(x); }
+template <typename R> __device__ __forceinline__ R rsqrt_(R x) { return rsqrt(x); }
 template <> __device__ __forceinline__ float rsqrt_<float>(float x) { return rsqrtf(x); }
+
+// Geometry of another scalar type (the adjoint evaluates the physics on dual
+// numbers at the same, constant, metric).
+template <typename T, int MET, typename R>
+__device__ __forceinline__ Geo<MET, T> geo_cast(const Geo<MET, R>& a) {
+  Geo<MET, T> g;
+  g.g00 = T(a.g00); g.g01 = T(a.g01); g.g03 = T(a.g03); g.g11 = T(a.g11); g.g13 = T(a.g13);
+  g.g22 = T(a.g22); g.g33 = T(a.g33);
+  g.G00 = T(a.G00); g.G01 = T(a.G01); g.G11 = T(a.G11); g.G13 = T(a.G13); g.G22 = T(a.G22);
+  g.G33 = T(a.G33);
+  g.gdet = T(a.gdet); g.alpha = T(a.alpha); g.ialpha = T(a.ialpha);
+  return g;
+}
 
 // Kerr-Schild metric in the internal chart at (x1, x2): covariant components
 // scaled by the diagonal map Jacobian, the closed-form inverse of the
@@ -208,30 +223,41 @@ __device__ __forceinline__ void bvec(const Geo<MET, R>& g, const R ucon[4], cons
 }
 
 // Opacities per length at density rho and gas temperature T; kf is the
-// zone's absorption opacity when the opacity is a per-zone field.
+// zone's absorption opacity when the opacity is a per-zone field; ks the
+// global opacity scale (kappa_scale; a separate argument so that the adjoint
+// can differentiate with respect to it).
 template <typename R>
-__device__ __forceinline__ void opacity_T(const DevParams& p, R rho, R T, R kf, R* kabs, R* ksca) {
+__device__ __forceinline__ void opacity_ks(const DevParams& p, R rho, R T, R kf, R ks, R* kabs, R* ksca) {
   if (p.opacity == 2) {
-    *kabs = R(p.kscale) * kf;
+    *kabs = ks * kf;
   } else if (p.opacity == 1) {
     R Tc = T > R(p.Tmin) ? T : R(p.Tmin);
     R T2 = Tc * Tc;
     R t35;
-    if constexpr (sizeof(R) == 8) {
+    if constexpr (!std::is_same<R, float>::value) {
       t35 = rsqrt_<R>(T2 * T2 * T2 * Tc);  // T^-3.5 = 1/sqrt(T^7): one reciprocal square root
     } else {
       t35 = rsqrt_<R>(Tc) / (T2 * Tc);  // T^7 would underflow in FP32
     }
-    *kabs = R(p.kscale * p.kabs0) * rho * rho * t35;
+    *kabs = ks * R(p.kabs0) * rho * rho * t35;
   } else {
-    *kabs = R(p.kscale * p.kabs0) * rho;
+    *kabs = ks * R(p.kabs0) * rho;
   }
-  *ksca = R(p.kscale * p.kes0) * rho;
+  *ksca = ks * R(p.kes0) * rho;
 }
 
 template <typename R>
+__device__ __forceinline__ void opacity_T(const DevParams& p, R rho, R T, R kf, R* kabs, R* ksca) {
+  opacity_ks<R>(p, rho, T, kf, R(p.kscale), kabs, ksca);
+}
+
+template <typename R>
+__device__ __forceinline__ void opacity(const DevParams& p, R rho, R ug, R kf, R* kabs, R* ksca, R ks) {
+  opacity_ks<R>(p, rho, R(p.gam - 1.0) * ug / rho, kf, ks, kabs, ksca);
+}
+template <typename R>
 __device__ __forceinline__ void opacity(const DevParams& p, R rho, R ug, R kf, R* kabs, R* ksca) {
-  opacity_T<R>(p, rho, R(p.gam - 1.0) * ug / rho, kf, kabs, ksca);
+  opacity<R>(p, rho, ug, kf, kabs, ksca, R(p.kscale));
 }
 
 // ------------------------------------------------------- face state physics
@@ -261,6 +287,7 @@ __device__ __forceinline__ void char_speeds(const Geo<MET, R>& g, const R ucon[4
 template <int MET, typename R>
 __device__ __forceinline__ void face_state(const DevParams& p, const Geo<MET, R>& g, int d, R dxd,
                                            R kf, const R P[NPR], R U[NPR], R F[NPR], R sp[4]) {
+  const R ks = R(p.kscale);
   R ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq;
   fourvel<MET, R>(g, P[U1], P[U2], P[U3], ucon, ucov, &gm);
   bvec<MET, R>(g, ucon, ucov, P[B1], P[B2], P[B3], bcon, bcov, &bsq);
@@ -306,7 +333,7 @@ __device__ __forceinline__ void face_state(const DevParams& p, const Geo<MET, R>
   cms2 = cms2 > R(1) ? R(1) : (cms2 < R(0) ? R(0) : cms2);
   char_speeds<MET, R>(g, ucon, cms2, d, &sp[0], &sp[1]);
   R kabs, ksca;
-  opacity<R>(p, rho, ug, kf, &kabs, &ksca);
+  opacity<R>(p, rho, ug, kf, &kabs, &ksca, ks);
   R tau = (kabs + ksca) * sqrt(g.gdd(d)) * dxd;
   R cr2 = R(1.0 / 3.0);
   if (tau > R(0)) {
@@ -321,7 +348,7 @@ __device__ __forceinline__ void face_state(const DevParams& p, const Geo<MET, R>
 // dxd is the cell size along d and kf the per-zone opacity of the state's cell.
 template <int MET, typename R>
 __device__ __forceinline__ void face_speeds(const DevParams& p, const Geo<MET, R>& g, int d, R dxd,
-                                            R kf, const R P[NPR], R sp[4]) {
+                                            R kf, R ks, const R P[NPR], R sp[4]) {
   R ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq;
   fourvel<MET, R>(g, P[U1], P[U2], P[U3], ucon, ucov, &gm);
   bvec<MET, R>(g, ucon, ucov, P[B1], P[B2], P[B3], bcon, bcov, &bsq);
@@ -336,7 +363,7 @@ __device__ __forceinline__ void face_speeds(const DevParams& p, const Geo<MET, R
   R urc[4], urv[4], gr;
   fourvel<MET, R>(g, P[UR1], P[UR2], P[UR3], urc, urv, &gr);
   R kabs, ksca;
-  opacity<R>(p, rho, ug, kf, &kabs, &ksca);
+  opacity<R>(p, rho, ug, kf, &kabs, &ksca, ks);
   R tau = (kabs + ksca) * sqrt(g.gdd(d)) * dxd;
   R cr2 = R(1.0 / 3.0);
   if (tau > R(0)) {
@@ -393,54 +420,54 @@ __device__ __forceinline__ void face_accum(const DevParams& p, const Geo<MET, R>
 // gamma^2 = (2 - y + sqrt(4-3y)) / (4(1-y)), p_rad = E_rad/(4 gamma^2 - 1),
 // u~^i = gamma U~^i / (4 p_rad gamma^2).  Limiters: BASIC (lim 0) and TYPE2
 // (lim 2).  Returns 1 if E_rad <= 0 on entry.
-template <int MET>
-__device__ __forceinline__ int rad_invert(const DevParams& p, const Geo<MET, double>& g,
-                                          const double Rt[4], int lim, double out[4]) {
-  const double a = g.alpha;
-  double Erad = a * a * g.raise_t(Rt);
-  double Ut[3];
+template <int MET, typename T = double>
+__device__ __forceinline__ int rad_invert(const DevParams& p, const Geo<MET, T>& g, const T Rt[4], int lim,
+                                          T out[4]) {
+  const T a = g.alpha;
+  T Erad = a * a * g.raise_t(Rt);
+  T Ut[3];
   g.raise3(Rt, Ut);
-  const double et = Erad * g.Gt(1);
+  const T et = Erad * g.Gt(1);
   Ut[0] = a * (Ut[0] + et);
   Ut[1] = a * Ut[1];
   Ut[2] = a * Ut[2];
-  double Utsq = g.sq3(Ut[0], Ut[1], Ut[2]);
+  T Utsq = g.sq3(Ut[0], Ut[1], Ut[2]);
   const double ymax = p.ymax_rad;
   int negE = Erad <= 0.0;
-  double y;
+  T y;
   if (lim == 0) {
     if (Erad <= 0.0) {
-      out[0] = 1e-300;
-      out[1] = out[2] = out[3] = 0.0;
+      out[0] = T(1e-300);
+      out[1] = out[2] = out[3] = T(0.0);
       return negE;
     }
     y = Utsq / (Erad * Erad);
     if (y < 0.0) {
-      y = 0.0;
-      Ut[0] = Ut[1] = Ut[2] = 0.0;
+      y = T(0.0);
+      Ut[0] = Ut[1] = Ut[2] = T(0.0);
     }
     if (y > ymax) {
-      double f = sqrt(ymax / y);
+      T f = sqrt(T(ymax) / y);
       Ut[0] *= f;
       Ut[1] *= f;
       Ut[2] *= f;
-      y = ymax;
+      y = T(ymax);
     }
   } else {
-    y = Erad > 0.0 ? Utsq / (Erad * Erad) : HUGE_VAL;
+    y = Erad > 0.0 ? Utsq / (Erad * Erad) : T(HUGE_VAL);
     if (Erad <= 0.0 || y > ymax) {
-      Erad = 1e-150 + sqrt(Utsq / ymax);
+      Erad = T(1e-150) + sqrt(Utsq / T(ymax));
       y = Utsq / (Erad * Erad);
     }
-    if (y < 0.0) y = 0.0;
+    if (y < 0.0) y = T(0.0);
   }
   // With s = sqrt(4 - 3y), Eq. gammarvsy gives gamma^2 = (s+2)/(4(s-1)) and
   // 4 gamma^2 - 1 = 3/(s-1), so Ebar = 3 p_rad = E_rad (s-1) and
   // u~^i = gamma U~^i/(4 p_rad gamma^2) = 3 U~^i / (2 E_rad sqrt((s+2)(s-1))).
-  const double sq = sqrt(4.0 - 3.0 * y);
-  const double sm1 = sq - 1.0;
+  const T sq = sqrt(T(4.0) - T(3.0) * y);
+  const T sm1 = sq - T(1.0);
   out[0] = Erad * sm1;
-  double f = 1.5 / Erad * rsqrt((sq + 2.0) * sm1);
+  T f = T(1.5) / Erad * rsqrt_<T>((sq + T(2.0)) * sm1);
   out[1] = f * Ut[0];
   out[2] = f * Ut[1];
   out[3] = f * Ut[2];

@@ -31,6 +31,9 @@ inline Bufs make_bufs(harmrad_ctx* c) {
   b.ftmp = c->ftmp;
   b.stats = c->stats;
   b.dtmin = c->dtmin;
+  b.ust_rec = c->rec_ust;
+  b.meth_rec = c->rec_meth;
+  b.psol_rec = c->rec_psol;
   return b;
 }
 

@@ -25,6 +25,7 @@ EXPORTS = [
     "harmrad_get_status", "harmrad_get_iters", "harmrad_compute_fluxes",
     "harmrad_zone_physics", "harmrad_zone_implicit", "harmrad_zone_implicit_static",
     "harmrad_profile_step", "harmrad_autotune", "harmrad_get_tuning", "harmrad_set_tuning",
+    "harmrad_adjoint_enable", "harmrad_step_adjoint",
     "harmrad_strerror",
 ]
 KERNEL_CLASSES = ["bc", "prep", "flatten", "face", "ct", "update", "retry", "backup", "cfl", "other",
@@ -129,6 +130,8 @@ def load(path=LIB_PATH):
     L.harmrad_zone_implicit.argtypes = [pp, ip, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.harmrad_zone_implicit_static.argtypes = [pp, ip, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.harmrad_profile_step.argtypes = [vp, ctypes.c_double, ctypes.POINTER(KernelTimes)]
+    L.harmrad_adjoint_enable.argtypes = [vp, ip]
+    L.harmrad_step_adjoint.argtypes = [vp, vp, vp, ctypes.POINTER(ctypes.c_double), ip]
     L.harmrad_autotune.argtypes = [vp, ip, ctypes.POINTER(Tuning)]
     L.harmrad_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
     L.harmrad_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
@@ -242,6 +245,31 @@ class Grid:
         kt = KernelTimes()
         _check(load().harmrad_profile_step(self._h, float(dt), ctypes.byref(kt)), "profile_step")
         return {name: (kt.ms[i], kt.launches[i]) for i, name in enumerate(KERNEL_CLASSES)}
+
+    def adjoint_enable(self, on=True):
+        """Keep each step's input so that step_adjoint can differentiate it."""
+        _check(load().harmrad_adjoint_enable(self._h, 1 if on else 0), "adjoint_enable")
+
+    def step_adjoint(self, gP_out):
+        """Reverse-mode derivative of the last step: dL/dP^{n+1} -> (dL/dP^n,
+        dL/dkappa_scale), time step fixed.  Torch CUDA tensors stay on the
+        device; numpy arrays are copied through the host."""
+        import torch
+        gk = ctypes.c_double()
+        if isinstance(gP_out, torch.Tensor):
+            assert gP_out.is_cuda and gP_out.dtype == torch.float64
+            gin = gP_out.contiguous()
+            out = torch.empty_like(gin)
+            _check(load().harmrad_step_adjoint(self._h, ctypes.c_void_p(gin.data_ptr()),
+                                               ctypes.c_void_p(out.data_ptr()), ctypes.byref(gk), 1),
+                   "step_adjoint")
+            return out, gk.value
+        gin = np.ascontiguousarray(gP_out, dtype=np.float64)
+        out = np.empty_like(gin)
+        _check(load().harmrad_step_adjoint(self._h, gin.ctypes.data_as(ctypes.c_void_p),
+                                           out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(gk), 0),
+               "step_adjoint")
+        return out, gk.value
 
     def autotune(self, reps=2):
         """Pick the fastest launch shapes on the current state (state kept)."""

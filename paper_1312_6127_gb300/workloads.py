@@ -86,7 +86,7 @@ def _gaussian_torus(r, th):
     return np.exp(-((r - 15.0) / 4.0) ** 2 - (np.cos(th) / 0.3) ** 2)
 
 
-def torus(n=(64, 32, 16), seed=12345):
+def torus(n=(64, 32, 16), seed=12345, b_background=0.0):
     """Seeded Kerr-Schild torus, a = 0.9375, r in [1.2, 50] log-spaced,
     theta concentrated toward the equator (h = 0.3):
     rho = max(G(r, theta) (1 + 0.02 sin phi_k), 1e-6 r^-1.5) with G a Gaussian
@@ -95,7 +95,9 @@ def torus(n=(64, 32, 16), seed=12345):
     radiation in LTE (Ebar = a_rad T^4) with p_rad = p_gas at the density
     maximum; Kramers absorption (tau_abs = 10 per zone at the maximum) plus
     electron scattering; B from A_phi ~ max(rho - 0.2, 0) scaled so that
-    max p_gas / max p_mag = 100."""
+    max p_gas / max p_mag = 100.  b_background > 0 adds the field of
+    A_phi = b_background (r sin theta)^2 (a weak vertical field threading the
+    whole grid)."""
     cfg = _ks_setup(n)
     n1, n2, n3 = n
     a, h = cfg["a_spin"], cfg["hslope"]
@@ -135,6 +137,11 @@ def torus(n=(64, 32, 16), seed=12345):
     P = np.zeros((NP, n3, n2, n1))
     P[RHO] = rho
     P[UU] = ug
+    if b_background > 0.0:
+        Ab = b_background * (rf * np.sin(thf)) ** 2
+        B1c = scale * B1c + (Ab[1:, :-1] + Ab[1:, 1:] - Ab[:-1, :-1] - Ab[:-1, 1:]) / (2 * cfg["dx"][1] * gdet)
+        B2c = scale * B2c - (Ab[:-1, 1:] + Ab[1:, 1:] - Ab[:-1, :-1] - Ab[1:, :-1]) / (2 * cfg["dx"][0] * gdet)
+        scale = 1.0
     P[B1] = (scale * B1c)[None, :, :]
     P[B2] = (scale * B2c)[None, :, :]
     P[ER] = a_rad * T ** 4
@@ -143,6 +150,64 @@ def torus(n=(64, 32, 16), seed=12345):
     cfg.update(a_rad=a_rad, opacity=OPAC_KRAMERS, kappa_abs0=kK, kappa_es0=0.4,
                T_kappa_min=1e-3 * T0,
                floor_rho0=1e-6, floor_rho_pow=-1.5, floor_u0=1e-8, floor_u_pow=-2.5)
+    return cfg, P
+
+
+def generic_torus(n=(32, 16, 8), seed=12345):
+    """The torus made differentiable in every zone, for derivative checks:
+    a weak vertical background field (no zone with B = 0), velocity noise of
+    amplitude 1e-4 in every gas and radiation component (no zone at rest, so
+    no limiter sits on its kink at zero slope), field noise of relative size
+    1e-3 in every component (no direction along which the field is constant;
+    this noise is not divergence-free, which the step, constrained transport
+    included, does not need), and an atmosphere three times above the floors
+    (no floor acts on the initial state)."""
+    cfg, P = torus(n, seed, b_background=1e-5)
+    g = rng(seed + 1)
+    P[U1:U3 + 1] += 1e-4 * g.standard_normal(P[U1:U3 + 1].shape)
+    P[UR1:UR3 + 1] += 1e-4 * g.standard_normal(P[UR1:UR3 + 1].shape)
+    bmag = np.sqrt(P[B1] ** 2 + P[B2] ** 2)
+    P[B1] *= 1.0 + 1e-3 * g.standard_normal(bmag.shape)
+    P[B2] *= 1.0 + 1e-3 * g.standard_normal(bmag.shape)
+    P[B3] = 1e-3 * bmag * g.standard_normal(bmag.shape)
+    r = np.exp(cfg["x0"][0] + (np.arange(n[0]) + 0.5) * cfg["dx"][0])[None, None, :]
+    P[RHO] = np.maximum(P[RHO], 3.0 * cfg["floor_rho0"] * r ** cfg["floor_rho_pow"])
+    P[UU] = np.maximum(P[UU], 3.0 * cfg["floor_u0"] * r ** cfg["floor_u_pow"])
+    return cfg, P
+
+
+def ks_random_state(n=(32, 16, 8), seed=9, recon=PPM, tau=10.0):
+    """A random state on the Kerr-Schild grid of the torus (r in [1.2, 50],
+    polar and outflow boundaries), for derivative checks: rho log-normal
+    (sigma 0.5), u_g = 0.01 rho (1 +- 0.2), random velocities of ~0.1, field
+    of ~0.02 and radiation-frame velocities of ~0.05 (orthonormal sizes),
+    Ebar between 1 and 2 times a_rad T^4, Kramers absorption with optical
+    depth ~tau per zone.  Zone-to-zone variations of order one keep every
+    slope limiter away from its switching points for small perturbations."""
+    cfg = _ks_setup(n)
+    n1, n2, n3 = n
+    gam = cfg["gam"]
+    T0 = (gam - 1.0) * 0.01
+    cfg.update(recon=recon, a_rad=1e-2 / T0 ** 4, opacity=OPAC_KRAMERS,
+               kappa_abs0=tau * T0 ** 3.5 / cfg["dx"][0], kappa_es0=0.4, T_kappa_min=1e-3 * T0,
+               floor_rho0=1e-12, floor_u0=1e-14, floor_rho_pow=0.0, floor_u_pow=0.0)
+    g = rng(seed)
+    shape = (n3, n2, n1)
+    x1 = cfg["x0"][0] + (np.arange(n1) + 0.5) * cfg["dx"][0]
+    x2 = (np.arange(n2) + 0.5) * cfg["dx"][1]
+    r = np.exp(x1)[None, None, :]
+    th = _theta(x2, cfg["hslope"])[None, :, None]
+    P = np.zeros((NP,) + shape)
+    P[RHO] = np.exp(0.5 * g.standard_normal(shape))
+    P[UU] = 0.01 * P[RHO] * (1.0 + 0.2 * g.uniform(-1, 1, shape))
+    # coordinate components of orthonormal sizes (dr/dx1 = r, r dtheta ~ pi r, r sin dphi = 2 pi r sin)
+    sc = [1.0 / r, 1.0 / (np.pi * r) + 0.0 * th, 1.0 / (2 * np.pi * r * np.sin(th))]
+    for c in range(3):
+        P[U1 + c] = 0.1 * g.standard_normal(shape) * sc[c]
+        P[B1 + c] = 0.02 * g.standard_normal(shape) * sc[c]
+        P[UR1 + c] = 0.05 * g.standard_normal(shape) * sc[c]
+    T = (gam - 1.0) * P[UU] / P[RHO]
+    P[ER] = cfg["a_rad"] * T ** 4 * (1.0 + g.uniform(0, 1, shape))
     return cfg, P
 
 
