@@ -19,7 +19,10 @@
  * [12][n3][n2][n1] (i fastest).
  *
  * Pinned by tests/test_oracle_pins.py (closed forms, textbook SR-MHD, M1
- * closure identities, exact scalar roots, conservation).  Parity unpinned:
+ * closure identities, exact scalar roots, conservation) and by
+ * tests/test_oracle_waves.py (the linear-wave eigenvalues the paper prints in
+ * its Table t.waves: wave speed and radiative damping of sound, fast and slow
+ * modes, optically thin and thick, gas- and radiation-dominated).  Parity unpinned:
  * the PPM shock flattener (its constants beyond SP0 = 0.75 are not in the
  * paper), the polar-axis ghost rule and the floor procedure are readings of
  * the paper that only oracle-versus-library agreement checks.

@@ -288,6 +288,55 @@ def box_batch(count=48, seed=4242, edge=(32, 128), tau=(1e-4, 1e6), vmax=0.3):
     return cfgs, Ps, Ks
 
 
+def linear_wave(N, bg, mode):
+    """1D periodic Minkowski box [0, 1) of N zones carrying one linear
+    eigenmode q = Re[q_a + dq exp(-i k x)] at t = 0 (Sec. 5 linear waves): bg
+    holds rho, e_gas, gam, k; mode holds tau (kappa_es), P (p_rad/p_gas), B0
+    and the complex amplitudes [re, im] drho, dug, dux, duy, dBy, dE, dFx,
+    dFy (fluid-frame radiation energy and flux).  To first order the
+    radiation-frame energy density equals the fluid-frame one and the
+    radiation frame moves relative to the fluid with v = 3 F / (4 E), so
+    u~_rad = u~ + 3 dF / (4 E_a).  The opacity tau is absorption, with the
+    background radiation in equilibrium with the gas (a_rad T^4 = E_a,
+    T = p/rho) and no scattering: the printed eigenvalues are those of the
+    linearised equations with absorption (the accompanying text names the
+    opacity scattering; with scattering alone no mode has these
+    eigenvalues)."""
+    cfg = base_params()
+    gam = bg["gam"]
+    pg = (gam - 1.0) * bg["e_gas"]
+    Ea = 3.0 * mode["P"] * pg
+    T0 = pg / bg["rho"]
+    cfg.update(n=[N, 1, 1], dx=[1.0 / N, 1.0, 1.0], gam=gam, a_rad=Ea / T0 ** 4, opacity=OPAC_CONST,
+               kappa_abs0=mode["tau"], kappa_es0=0.0, recon=PPM, flux=LAXF,
+               floor_rho0=1e-12, floor_u0=1e-14)
+    x = (np.arange(N) + 0.5) / N
+    ph = np.exp(-1j * bg["k"] * x)
+
+    def pert(key):
+        re, im = mode[key]
+        return np.real((re + 1j * im) * ph)
+
+    P = np.zeros((NP, 1, 1, N))
+    P[RHO] = bg["rho"] + pert("drho")
+    P[UU] = bg["e_gas"] + pert("dug")
+    P[U1] = pert("dux")
+    P[U2] = pert("duy")
+    P[B1] = mode["B0"]
+    P[B2] = mode["B0"] + pert("dBy")
+    P[ER] = Ea + pert("dE")
+    P[UR1] = P[U1] + 0.75 * pert("dFx") / Ea
+    P[UR2] = P[U2] + 0.75 * pert("dFy") / Ea
+    return cfg, P
+
+
+def wave_amplitude(rho, k):
+    """Complex amplitude of the exp(-i k x) mode of rho on [0, 1)."""
+    N = rho.size
+    x = (np.arange(N) + 0.5) / N
+    return 2.0 / N * np.sum((rho.ravel() - rho.mean()) * np.exp(1j * k * x))
+
+
 def thin_pulse(n=(32, 32, 32), L=100.0, w=5.0, T_a=1e6):
     """Optically thin 3D radiation pulse (Sec. 5.3): kappa = 0, rho0 = 1,
     gas temperature T_a, Ebar = a_rad T_a^4 (1 + 100 exp(-r^2/w^2))^4 in
