@@ -115,43 +115,51 @@ def dist_setup():
     return ws, rank, local
 
 
-def oracle_sample(steps, n=(64, 32, 16)):
-    """Time the FP64 CPU oracle (as it stands, one thread) on the torus setup at
-    a reduced size: zone-cycles/s of `steps` CFL steps."""
-    from oracle import oracle as O
-    from paper_1312_6127_gb300 import workloads as W
-    cfg, P = W.torus(n, seed=12345)
-    o = O.Oracle(cfg)
-    o.set_prims(P)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        o.step(0.0)
-    dt = time.perf_counter() - t0
-    zones = n[0] * n[1] * n[2]
-    return zones * steps / dt, dt
+class OracleRun:
+    """The FP64 CPU oracle (as it stands) on the same seeded torus, with its
+    zone and face loops on `threads` host threads (the result does not depend
+    on the thread count)."""
+
+    def __init__(self, n, threads):
+        os.environ["ORACLE_THREADS"] = str(threads)
+        from oracle import oracle as O
+        from paper_1312_6127_gb300 import workloads as W
+        cfg, P = W.torus(n, seed=12345)
+        self.o = O.Oracle(cfg)
+        self.o.set_prims(P)
+        self.zones = n[0] * n[1] * n[2]
+        self.threads = threads
+
+    def step(self):
+        """One CFL step; returns (zone-cycles/s, seconds)."""
+        t0 = time.perf_counter()
+        self.o.step(0.0)
+        dt = time.perf_counter() - t0
+        return self.zones / dt, dt
 
 
 def run_reference(args, ws, rank):
     if rank != 0:
         return 0
-    samp = "%d CFL steps of the same seeded torus setup at 64x32x16 (32768 zones)" % 1
+    n = tuple(int(x) for x in args.size.split(","))
+    cores = os.cpu_count() or 1
+    run = OracleRun(n, cores)
     for _ in range(args.warmup):
-        oracle_sample(1)
-    vals = []
+        run.step()
     t_all = 0.0
     for _ in range(args.steps):
-        v, t = oracle_sample(1)
-        vals.append(v)
-        t_all += t
-    value = float(args.steps / sum(1.0 / v for v in vals))
+        t_all += run.step()[1]
+    value = run.zones * args.steps / t_all
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_all / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": "KS torus a=0.9375, sampled at 64x32x16 per step",
-                                        "precision": "fp64"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "each step: " + samp},
+        "data": "synthetic",
+        "config": {"workload": "KS torus a=0.9375 %dx%dx%d (PPM, LAXF, flux-CT, PMHD/URAD)" % n,
+                   "precision": "fp64", "zones": run.zones},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "each step: one CFL step of the whole %dx%dx%d torus, FP64 oracle "
+                                   "with its zone and face loops on %d host threads" % (n + (cores,))},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -298,12 +306,14 @@ def main():
                "d2h_bytes_per_step": nbytes}
 
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu:
-        steps = 5
-        v, t = oracle_sample(steps)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "%d CFL steps of the same seeded torus setup at 64x32x16 (32768 zones), "
-                         "one host thread, %.1f s" % (steps, t)}
+    if rank == 0 and ws == 1 and not args.no_cpu and args.workload == "torus":
+        cores = os.cpu_count() or 1
+        run = OracleRun(n, cores)
+        v, t = run.step()
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "one CFL step of the same seeded %dx%dx%d torus, FP64 oracle with its zone "
+                         "and face loops on %d host threads, %.1f s" % (n + (cores, t))}
+        del run
 
     if rank == 0:
         line = {

@@ -66,7 +66,8 @@ class OrcInfo(ctypes.Structure):
 
 
 def build(force=False):
-    """Compile the oracle with g++ (plain -O2, no FMA contraction)."""
+    """Compile the oracle with g++ (plain -O2, no FMA contraction; OpenMP
+    for the zone and face loops, ORACLE_THREADS threads, default 1)."""
     srcs = [os.path.join(_HERE, s) for s in _SRC]
     deps = srcs + [os.path.join(_HERE, h) for h in _HDR]
     if not force and os.path.exists(_LIB):
@@ -74,7 +75,7 @@ def build(force=False):
         if all(os.path.getmtime(s) <= t for s in deps):
             return _LIB
     tmp = _LIB + ".tmp%d" % os.getpid()
-    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp] + srcs
+    cmd = ["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared", "-o", tmp] + srcs
     subprocess.check_call(cmd)
     os.replace(tmp, _LIB)
     return _LIB

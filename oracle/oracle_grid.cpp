@@ -9,6 +9,7 @@
 // FP64, one thread.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -19,6 +20,15 @@ namespace orc {
 namespace {
 
 const int NG = 4;  // ghost depth (PPM needs +-4 cells)
+
+// Host threads for the zone and face loops: ORACLE_THREADS (default 1).  The
+// loops are over independent zones and faces, so the result does not depend
+// on the thread count.
+int orc_threads() {
+  const char* e = std::getenv("ORACLE_THREADS");
+  int v = e ? std::atoi(e) : 1;
+  return v > 0 ? v : 1;
+}
 
 struct Ctx {
   orc_params p;
@@ -303,35 +313,48 @@ void compute_fluxes(Ctx& c, int d, bool use_stored) {
   std::fill(F.begin(), F.end(), 0.0);
   std::fill(c.spd[d].begin(), c.spd[d].end(), 0.0);
   long str = d == 0 ? 1 : (d == 1 ? c.N[0] : (long)c.N[0] * c.N[1]);
-  for (int k = lo[2]; k < hi[2]; ++k)
+  auto one_face = [&](int i, int j, int k) {
+    int ii[3] = {i, j, k};
+    int f = ii[d];
+    long t = idx(c, i, j, k);  // cell just above the face
+    // polar faces: sqrt(-g) = 0 there, flux is zero
+    if (p.metric == 1 && d == 1 &&
+        ((f == 0 && p.bc[2] == 2) || (f == c.n[1] && p.bc[3] == 2)))
+      return;
+    double P8[8][NP], K8[8];
+    const Geom* geo[8];
+    for (int m = 0; m < 8; ++m) {
+      long cm = t + (long)(m - 4) * str;
+      geo[m] = &c.geo[cm];
+      for (int q = 0; q < NP; ++q) P8[m][q] = c.P[(long)q * c.ntot + cm];
+      K8[m] = c.K.empty() ? 0.0 : c.K[cm];
+    }
+    double x[3] = {xc(c, 0, i), xc(c, 1, j), xc(c, 2, k)};
+    x[d] = xf(c, d, f);
+    Geom G;
+    geom_at(p, x[0], x[1], x[2], G);
+    double* st[2][2] = {{&c.flat[d][t - str], &c.flat[d][c.ntot + t - str]},
+                        {&c.flat[d][t], &c.flat[d][c.ntot + t]}};
+    double Fq[NP], sp;
+    face_flux(p, d, P8, geo, G, c.K.empty() ? nullptr : K8, use_stored ? st : nullptr, Fq, &sp);
+    for (int q = 0; q < NP; ++q) F[(long)q * c.ntot + t] = Fq[q];
+    c.spd[d][t] = sp;
+  };
+  // a face writes the flattener of the two cells beside it: the parallel
+  // loop runs over an index other than d, so neighbours along d stay on one
+  // thread
+  const int nth = orc_threads();
+  if (d != 2) {
+#pragma omp parallel for num_threads(nth) schedule(dynamic, 1)
+    for (int k = lo[2]; k < hi[2]; ++k)
+      for (int j = lo[1]; j < hi[1]; ++j)
+        for (int i = lo[0]; i < hi[0]; ++i) one_face(i, j, k);
+  } else {
+#pragma omp parallel for num_threads(nth) schedule(dynamic, 1)
     for (int j = lo[1]; j < hi[1]; ++j)
-      for (int i = lo[0]; i < hi[0]; ++i) {
-        int ii[3] = {i, j, k};
-        int f = ii[d];
-        long t = idx(c, i, j, k);  // cell just above the face
-        // polar faces: sqrt(-g) = 0 there, flux is zero
-        if (p.metric == 1 && d == 1 &&
-            ((f == 0 && p.bc[2] == 2) || (f == c.n[1] && p.bc[3] == 2)))
-          continue;
-        double P8[8][NP], K8[8];
-        const Geom* geo[8];
-        for (int m = 0; m < 8; ++m) {
-          long cm = t + (long)(m - 4) * str;
-          geo[m] = &c.geo[cm];
-          for (int q = 0; q < NP; ++q) P8[m][q] = c.P[(long)q * c.ntot + cm];
-          K8[m] = c.K.empty() ? 0.0 : c.K[cm];
-        }
-        double x[3] = {xc(c, 0, i), xc(c, 1, j), xc(c, 2, k)};
-        x[d] = xf(c, d, f);
-        Geom G;
-        geom_at(p, x[0], x[1], x[2], G);
-        double* st[2][2] = {{&c.flat[d][t - str], &c.flat[d][c.ntot + t - str]},
-                            {&c.flat[d][t], &c.flat[d][c.ntot + t]}};
-        double Fq[NP], sp;
-        face_flux(p, d, P8, geo, G, c.K.empty() ? nullptr : K8, use_stored ? st : nullptr, Fq, &sp);
-        for (int q = 0; q < NP; ++q) F[(long)q * c.ntot + t] = Fq[q];
-        c.spd[d][t] = sp;
-      }
+      for (int k = lo[2]; k < hi[2]; ++k)
+        for (int i = lo[0]; i < hi[0]; ++i) one_face(i, j, k);
+  }
 }
 
 // Flux-CT (Toth 2000): for every pair (a,b) of active directions, the edge
@@ -351,6 +374,7 @@ void flux_ct(Ctx& c) {
       hi[b] = c.n[b] + 1;
       const double* Fa = &c.F[a][(long)(B1 + b) * c.ntot];
       const double* Fb = &c.F[b][(long)(B1 + a) * c.ntot];
+#pragma omp parallel for num_threads(orc_threads())
       for (int k = lo[2]; k < hi[2]; ++k)
         for (int j = lo[1]; j < hi[1]; ++j)
           for (int i = lo[0]; i < hi[0]; ++i) {
@@ -366,12 +390,14 @@ void flux_ct(Ctx& c) {
       double* Fa_w = &c.F[a][(long)(B1 + b) * c.ntot];
       double* Fb_w = &c.F[b][(long)(B1 + a) * c.ntot];
       // F_a[B_b] on a-faces: a in [0,n_a], b in [0,n_b)
+#pragma omp parallel for num_threads(orc_threads())
       for (int k = 0; k < (a == 2 ? c.n[2] + 1 : c.n[2]); ++k)
         for (int j = 0; j < (a == 1 ? c.n[1] + 1 : c.n[1]); ++j)
           for (int i = 0; i < (a == 0 ? c.n[0] + 1 : c.n[0]); ++i) {
             long t = idx(c, i, j, k);
             Fa_w[t] = 0.5 * (emf[t] + emf[t + sb]);
           }
+#pragma omp parallel for num_threads(orc_threads())
       for (int k = 0; k < (b == 2 ? c.n[2] + 1 : c.n[2]); ++k)
         for (int j = 0; j < (b == 1 ? c.n[1] + 1 : c.n[1]); ++j)
           for (int i = 0; i < (b == 0 ? c.n[0] + 1 : c.n[0]); ++i) {
@@ -418,6 +444,7 @@ void apply_floors(const orc_params& p, const Geom& G, double* P) {
 
 double cfl_from_speeds(const Ctx& c) {
   double best = HUGE_VAL;
+#pragma omp parallel for num_threads(orc_threads()) reduction(min : best)
   for (int k = 0; k < c.n[2]; ++k)
     for (int j = 0; j < c.n[1]; ++j)
       for (int i = 0; i < c.n[0]; ++i) {
@@ -452,6 +479,9 @@ void substep(Ctx& c, int s, double dt) {
   std::vector<double> Pnew((size_t)NP * c.ntot);
   std::memcpy(Pnew.data(), c.P.data(), sizeof(double) * NP * c.ntot);
   std::vector<unsigned char> failed((size_t)c.n[0] * c.n[1] * c.n[2], 0);
+  long long n_pmhd = 0, n_urad = 0, n_back = 0, n_iter = 0, n_solve = 0;
+#pragma omp parallel for num_threads(orc_threads()) schedule(dynamic, 1) \
+    reduction(+ : n_pmhd, n_urad, n_back, n_iter, n_solve)
   for (int k = 0; k < c.n[2]; ++k)
     for (int j = 0; j < c.n[1]; ++j)
       for (int i = 0; i < c.n[0]; ++i) {
@@ -479,15 +509,20 @@ void substep(Ctx& c, int s, double dt) {
         long a = aidx(c, i, j, k);
         c.status[a] = std::max(c.status[a], (unsigned char)info.method);
         c.iters[a] += info.iters_pmhd + info.iters_urad;
-        c.counts[3] += info.iters_pmhd + info.iters_urad;
-        c.counts[4] += 1;
-        if (info.method == ORC_OK_PMHD) c.counts[0]++;
-        else if (info.method == ORC_OK_URAD) c.counts[1]++;
-        else c.counts[2]++;
+        n_iter += info.iters_pmhd + info.iters_urad;
+        n_solve += 1;
+        if (info.method == ORC_OK_PMHD) n_pmhd++;
+        else if (info.method == ORC_OK_URAD) n_urad++;
+        else n_back++;
         failed[a] = info.method == ORC_BACKUP;
         apply_floors(c.p, G, Pn);
         for (int q = 0; q < NP; ++q) Pnew[(long)q * c.ntot + t] = Pn[q];
       }
+  c.counts[0] += n_pmhd;
+  c.counts[1] += n_urad;
+  c.counts[2] += n_back;
+  c.counts[3] += n_iter;
+  c.counts[4] += n_solve;
   // Back-up (Sec. 4.11): replace failed zones by the average of their good
   // active face neighbours (all active neighbours if none is good); B keeps
   // its constrained-transport value.  Every solution was floored above, and
@@ -523,6 +558,7 @@ void substep(Ctx& c, int s, double dt) {
           Pavg[(long)q * c.ntot + t] = ngood > 0 ? sum_good[q] / ngood : sum_all[q] / nall;
         }
       }
+#pragma omp parallel for num_threads(orc_threads())
   for (int k = 0; k < c.n[2]; ++k)
     for (int j = 0; j < c.n[1]; ++j)
       for (int i = 0; i < c.n[0]; ++i) {
@@ -562,6 +598,7 @@ void* orc_create(const orc_params* p) {
   }
   c->geo.resize(c->ntot);
   c->gam.assign((size_t)c->ntot * 64, 0.0);
+#pragma omp parallel for num_threads(orc_threads()) schedule(dynamic, 1)
   for (int k = -c->ng[2]; k < c->n[2] + c->ng[2]; ++k)
     for (int j = -c->ng[1]; j < c->n[1] + c->ng[1]; ++j)
       for (int i = -c->ng[0]; i < c->n[0] + c->ng[0]; ++i) {

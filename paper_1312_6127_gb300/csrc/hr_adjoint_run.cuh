@@ -73,7 +73,7 @@ int Run<MET>::adjoint(harmrad_ctx* c, const double* gPout, double* gPin, double*
         if (e != d) work *= (e < d) ? bx.N[e] : bx.n[e];
       k_bc_fill<<<G(work), 128, 0, st>>>(p, c->dboxes, 1, Pg, p.opacity == 2 ? c->K : nullptr, d);
     }
-    k_prep<MET, double><<<G(nt), 128, 0, st>>>(p, c->dboxes, 1, Pg, c->K, aux);
+    k_prep<MET, double><<<G(nt), 128, 0, st>>>(p, c->dboxes, 1, Pg, c->K, aux, c->geotab);
     HR_ACHECK(cudaMemsetAsync(a.gP, 0, pbytes, st));
     ka_update<MET><<<G(na), 128, 0, st>>>(p, bx, a, s, dt, Ps);
     // fluxes: divergence, then flux-CT
@@ -106,10 +106,11 @@ int Run<MET>::adjoint(harmrad_ctx* c, const double* gPout, double* gPin, double*
     // per direction: reconstruction and Riemann fluxes, flattener, cell factors
     for (int d = 0; d < 3; ++d) {
       if (!p.act[d]) continue;
-      long long wf = 1, wc = 1;
+      long long wf = 1, wc = 1, ws = 1;
       for (int e = 0; e < 3; ++e) {
         wf *= (e == d) ? bx.n[e] + 1 : (bx.n[e] > 1 ? bx.n[e] + 2 : 1);
         wc *= bx.n[e] > 1 ? bx.n[e] + 2 : 1;
+        ws *= bx.n[e] > 1 ? bx.n[e] + (e == d ? 4 : 2) : 1;
       }
       const double* chi_s = a.chi + ((size_t)s * 3 + d) * 2 * nt;
       const double* chi_prev = s > 0 ? a.chi + ((size_t)(s - 1) * 3 + d) * 2 * nt : nullptr;
@@ -119,7 +120,8 @@ int Run<MET>::adjoint(harmrad_ctx* c, const double* gPout, double* gPin, double*
       HR_ACHECK(cudaMemsetAsync(a.gaux, 0, 3 * (size_t)nt * sizeof(double), st));
       const double* flat = p.recon == 0 ? chi_s : aux;  // not read for MC
       if (d == 0) {
-        k_edges<MET, double, 0><<<G(wc), 128, 0, st>>>(p, c->dboxes, 1, Pg, aux, flat, E);
+        k_slopes<MET, double, 0><<<G(ws), 128, 0, st>>>(p, c->dboxes, 1, Pg, aux, (double*)c->slope);
+        k_edges<MET, double, 0><<<G(wc), 128, 0, st>>>(p, c->dboxes, 1, Pg, aux, flat, (double*)c->slope, E);
         ka_face<MET, 0><<<G(wf), 128, 0, st>>>(p, bx, E, K, a.gF[0], a.gE, a.gk);
         ka_edges<MET, 0><<<G(wc), 128, 0, st>>>(p, bx, Pg, aux, flat, a.gE, a.gP, a.gchi);
         if (p.recon == 0) {
@@ -127,7 +129,8 @@ int Run<MET>::adjoint(harmrad_ctx* c, const double* gPout, double* gPin, double*
           ka_prep<MET, 0><<<G(nt), 128, 0, st>>>(p, bx, Pg, K, a.gaux, a.gP, a.gk);
         }
       } else if (d == 1) {
-        k_edges<MET, double, 1><<<G(wc), 128, 0, st>>>(p, c->dboxes, 1, Pg, aux, flat, E);
+        k_slopes<MET, double, 1><<<G(ws), 128, 0, st>>>(p, c->dboxes, 1, Pg, aux, (double*)c->slope);
+        k_edges<MET, double, 1><<<G(wc), 128, 0, st>>>(p, c->dboxes, 1, Pg, aux, flat, (double*)c->slope, E);
         ka_face<MET, 1><<<G(wf), 128, 0, st>>>(p, bx, E, K, a.gF[1], a.gE, a.gk);
         ka_edges<MET, 1><<<G(wc), 128, 0, st>>>(p, bx, Pg, aux, flat, a.gE, a.gP, a.gchi);
         if (p.recon == 0) {
@@ -135,7 +138,8 @@ int Run<MET>::adjoint(harmrad_ctx* c, const double* gPout, double* gPin, double*
           ka_prep<MET, 1><<<G(nt), 128, 0, st>>>(p, bx, Pg, K, a.gaux, a.gP, a.gk);
         }
       } else {
-        k_edges<MET, double, 2><<<G(wc), 128, 0, st>>>(p, c->dboxes, 1, Pg, aux, flat, E);
+        k_slopes<MET, double, 2><<<G(ws), 128, 0, st>>>(p, c->dboxes, 1, Pg, aux, (double*)c->slope);
+        k_edges<MET, double, 2><<<G(wc), 128, 0, st>>>(p, c->dboxes, 1, Pg, aux, flat, (double*)c->slope, E);
         ka_face<MET, 2><<<G(wf), 128, 0, st>>>(p, bx, E, K, a.gF[2], a.gE, a.gk);
         ka_edges<MET, 2><<<G(wc), 128, 0, st>>>(p, bx, Pg, aux, flat, a.gE, a.gP, a.gchi);
         if (p.recon == 0) {

@@ -158,6 +158,7 @@ int fill_geometry(const harmrad_params* p, BoxGeo& b) {
   }
   b.ntot = ntot;
   b.nact = nact;
+  b.goff = -1;
   b.str[0] = 1;
   b.str[1] = b.N[0];
   b.str[2] = (long long)b.N[0] * b.N[1];
@@ -293,9 +294,9 @@ void free_adjoint(harmrad_ctx* c) {
 
 void free_all(harmrad_ctx* c) {
   free_adjoint(c);
-  void* ptrs[] = {c->P, c->K, c->Un, c->F[0], c->F[1], c->F[2], c->spd[0], c->spd[1], c->spd[2],
-                  c->aux, c->flat[0], c->flat[1], c->flat[2], c->emf, c->edges, c->dt, c->status,
-                  c->iters, c->failed, c->qcount, c->qzone, c->qbox, c->qdata, c->fzone, c->fbox,
+  void* ptrs[] = {c->P, c->K, c->geotab, c->Un, c->F[0], c->F[1], c->F[2], c->spd[0], c->spd[1], c->spd[2],
+                  c->aux, c->flat[0], c->flat[1], c->flat[2], c->emf, c->edges, c->slope, c->dt, c->status,
+                  c->iters, c->failed, c->qcount, c->czone, c->cbox, c->cdata, c->qzone, c->qbox, c->qdata, c->fzone, c->fbox,
                   c->ftmp, c->stats, c->dtmin, c->stage_buf, c->flag, c->dboxes};
   for (void* q : ptrs)
     if (q) cudaFree(q);
@@ -325,13 +326,17 @@ int create(const harmrad_params* p, int count, void* stream, harmrad_ctx** out) 
   int rc = fill_physics(&p[0], dp);
   if (rc) return rc;
   std::vector<BoxGeo> boxes(count);
-  long long coff = 0, aoff = 0, maxc = 0, maxa = 0;
+  long long coff = 0, aoff = 0, maxc = 0, maxa = 0, goff = 0;
   for (int b = 0; b < count; ++b) {
     if (b > 0 && !same_physics(p[0], p[b])) return HARMRAD_E_ARG;
     rc = fill_geometry(&p[b], boxes[b]);
     if (rc) return rc;
     boxes[b].coff = coff;
     boxes[b].aoff = aoff;
+    if (dp.metric == 1) {
+      boxes[b].goff = goff;
+      goff += hr::geotab_size(boxes[b]);
+    }
     coff += boxes[b].ntot;
     aoff += boxes[b].nact;
     maxc = boxes[b].ntot > maxc ? boxes[b].ntot : maxc;
@@ -379,6 +384,7 @@ int create(const harmrad_params* p, int count, void* stream, harmrad_ctx** out) 
   rc = rc ? rc : dalloc(&c->dboxes, sizeof(BoxGeo) * count);
   rc = rc ? rc : dalloc(&c->P, 12 * nt * sizeof(double));
   rc = rc ? rc : dalloc(&c->K, nk * sizeof(double));
+  if (goff > 0) rc = rc ? rc : dalloc(&c->geotab, goff * sizeof(double));
   rc = rc ? rc : dalloc(&c->Un, 12 * na * sizeof(double));
   for (int d = 0; d < 3; ++d) {
     size_t fn = dp.act[d] ? nt : 0;
@@ -389,11 +395,15 @@ int create(const harmrad_params* p, int count, void* stream, harmrad_ctx** out) 
   rc = rc ? rc : dalloc(&c->aux, 10 * nt * rs);
   rc = rc ? rc : dalloc(&c->emf, nt * rs);
   rc = rc ? rc : dalloc(&c->edges, 24 * nt * rs);
+  rc = rc ? rc : dalloc(&c->slope, 12 * nt * rs);
   rc = rc ? rc : dalloc(&c->dt, count * sizeof(double));
   rc = rc ? rc : dalloc(&c->status, na);
   rc = rc ? rc : dalloc(&c->iters, na * sizeof(int));
   rc = rc ? rc : dalloc(&c->failed, na);
-  rc = rc ? rc : dalloc(&c->qcount, 2 * sizeof(int));
+  rc = rc ? rc : dalloc(&c->qcount, 4 * sizeof(int));
+  rc = rc ? rc : dalloc(&c->czone, na * sizeof(int));
+  rc = rc ? rc : dalloc(&c->cbox, na * sizeof(int));
+  rc = rc ? rc : dalloc(&c->cdata, na * hr::CSTRIDE * sizeof(double));
   rc = rc ? rc : dalloc(&c->qzone, na * sizeof(int));
   rc = rc ? rc : dalloc(&c->qbox, na * sizeof(int));
   rc = rc ? rc : dalloc(&c->qdata, na * hr::QSTRIDE * sizeof(double));
@@ -424,6 +434,11 @@ int create(const harmrad_params* p, int count, void* stream, harmrad_ctx** out) 
                  cudaMemsetAsync(c->spd[d], 0, fn * rs, c->stream) != cudaSuccess ||
                  cudaMemsetAsync(c->flat[d], 0, 2 * fn * rs, c->stream) != cudaSuccess))
         rc = HARMRAD_E_CUDA;
+    }
+    if (!rc && c->geotab) {
+      hr::k_geo_init<<<hr::grid_for(goff / 16, c->sms, 256), 256, 0, c->stream>>>(c->dp, c->dboxes, count,
+                                                                                 c->geotab);
+      if (cudaGetLastError() != cudaSuccess) rc = HARMRAD_E_CUDA;
     }
     if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = HARMRAD_E_CUDA;
   }

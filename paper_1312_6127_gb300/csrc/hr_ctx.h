@@ -26,6 +26,7 @@ struct harmrad_ctx {
   // device memory
   double* P;
   double* K;
+  double* geotab;  // metric tables of Kerr-Schild grids (null for Minkowski)
   double* Un;
   void* F[3];
   void* spd[3];
@@ -33,11 +34,15 @@ struct harmrad_ctx {
   void* flat[3];
   void* emf;
   void* edges;  // [2][12][ntot] reconstructed edge values of one direction
+  void* slope;  // [12][ntot] MC slopes of one direction
   double* dt;
   unsigned char* status;
   int* iters;
   unsigned char* failed;
   int* qcount;
+  int* czone;
+  int* cbox;
+  double* cdata;
   int* qzone;
   int* qbox;
   double* qdata;

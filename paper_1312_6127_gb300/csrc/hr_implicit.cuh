@@ -246,37 +246,62 @@ __device__ __forceinline__ bool stalled(Hist& hs, int k, double eT, double eI) {
   return stop;
 }
 
-// PMHD Newton.  Returns the number of Newton steps; best_x / best_eT hold the
-// lowest-error iterate (best_eT = inf if no residual was finite).
-template <int MET>
-__device__ int newton_pmhd(const DevParams& p, const ImpSys<MET>& s, const double x0[4],
-                           double best_x[4], double* best_eT) {
-  double x[4] = {x0[0], x0[1], x0[2], x0[3]};
-  Hist hs = {HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, 0};
-  *best_eT = HUGE_VAL;
-  int steps = 0;
-  double eps = 1e-8;
-  for (int k = 0;; ++k) {
-    ImpRes r;
-    pmhd_res<MET>(p, s, x, r, nullptr, true);
-    if (!r.ok) break;
-    if (r.eT < *best_eT) {
-      *best_eT = r.eT;
+// State of a PMHD Newton iteration between two of its steps: everything the
+// next step depends on, so that an iteration can stop after a number of
+// steps and resume later (in another kernel) with the same arithmetic.
+struct NewtonState {
+  double x[4];
+  double best_x[4];
+  double best_eT;
+  Hist hs;
+  double eps;
+  int k;      // index of the next iteration
+  int steps;  // Newton steps taken
+};
+
+__device__ __forceinline__ void newton_pmhd_init(const double x0[4], NewtonState& st) {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) best_x[i] = x[i];
+  for (int i = 0; i < 4; ++i) {
+    st.x[i] = x0[i];
+    st.best_x[i] = x0[i];
+  }
+  st.hs = {HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, 0};
+  st.best_eT = HUGE_VAL;
+  st.eps = 1e-8;
+  st.k = 0;
+  st.steps = 0;
+}
+
+// PMHD Newton iterations from the state st until a stopping rule ends the
+// iteration (returns true) or the next iteration's index reaches kstop
+// (returns false; st holds what the remaining iterations need).  best_x /
+// best_eT hold the lowest-error iterate (best_eT = inf if no residual was
+// finite).
+template <int MET>
+__device__ bool newton_pmhd_run(const DevParams& p, const ImpSys<MET>& s, NewtonState& st, int kstop) {
+  for (;; ++st.k) {
+    if (st.k >= kstop) return false;
+    ImpRes r;
+    pmhd_res<MET>(p, s, st.x, r, nullptr, true);
+    if (!r.ok) break;
+    if (r.eT < st.best_eT) {
+      st.best_eT = r.eT;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) st.best_x[i] = st.x[i];
     }
     if (r.eT < p.newton_tol) break;
-    if (stalled(hs, k, r.eT, r.eI)) break;
-    if (k >= p.newton_max) break;
-    if (r.eI < 1e-9) eps = 1e-10;
-    double umag = fmax(1.0, sqrt(s.g.sq3(x[1], x[2], x[3])));
+    if (stalled(st.hs, st.k, r.eT, r.eI)) break;
+    if (st.k >= p.newton_max) break;
+    if (r.eI < 1e-9) st.eps = 1e-10;
+    const double eps = st.eps;
+    double umag = fmax(1.0, sqrt(s.g.sq3(st.x[1], st.x[2], st.x[3])));
     double J[4][4];
 #pragma unroll 1
     for (int j = 0; j < 4; ++j) {
-      double dj = (j == 0) ? eps * fabs(x[0]) : eps * umag / sqrt(s.g.gdd(j));
+      double dj = (j == 0) ? eps * fabs(st.x[0]) : eps * umag / sqrt(s.g.gdd(j));
       double xp[4];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) xp[i] = x[i] + (i == j ? dj : 0.0);
+      for (int i = 0; i < 4; ++i) xp[i] = st.x[i] + (i == j ? dj : 0.0);
       ImpRes rp;
       pmhd_res<MET>(p, s, xp, rp, nullptr, false);
       double id = 1.0 / dj;
@@ -291,27 +316,40 @@ __device__ int newton_pmhd(const DevParams& p, const ImpSys<MET>& s, const doubl
     if (!solve4(J, E, dx)) break;
     double xn[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) xn[i] = x[i] - dx[i];
+    for (int i = 0; i < 4; ++i) xn[i] = st.x[i] - dx[i];
     if (xn[0] < 0.0) xn[0] = 0.5 * fabs(xn[0]);
     bool tiny = true;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
-      if (fabs(xn[i] - x[i]) > 10.0 * 2.220446049250313e-16 * fabs(x[i])) tiny = false;
+      if (fabs(xn[i] - st.x[i]) > 10.0 * 2.220446049250313e-16 * fabs(st.x[i])) tiny = false;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) x[i] = xn[i];
-    ++steps;
+    for (int i = 0; i < 4; ++i) st.x[i] = xn[i];
+    ++st.steps;
     if (tiny) {
       ImpRes rf;
-      pmhd_res<MET>(p, s, x, rf, nullptr, true);
-      if (rf.ok && rf.eT < *best_eT) {
-        *best_eT = rf.eT;
+      pmhd_res<MET>(p, s, st.x, rf, nullptr, true);
+      if (rf.ok && rf.eT < st.best_eT) {
+        st.best_eT = rf.eT;
 #pragma unroll
-        for (int i = 0; i < 4; ++i) best_x[i] = x[i];
+        for (int i = 0; i < 4; ++i) st.best_x[i] = st.x[i];
       }
       break;
     }
   }
-  return steps;
+  return true;
+}
+
+// PMHD Newton from x0 to the end.  Returns the number of Newton steps.
+template <int MET>
+__device__ int newton_pmhd(const DevParams& p, const ImpSys<MET>& s, const double x0[4],
+                           double best_x[4], double* best_eT) {
+  NewtonState st;
+  newton_pmhd_init(x0, st);
+  newton_pmhd_run<MET>(p, s, st, 1 << 30);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) best_x[i] = st.best_x[i];
+  *best_eT = st.best_eT;
+  return st.steps;
 }
 
 // URAD error function: iterate R^t_nu; gas from 1D_W inversion of

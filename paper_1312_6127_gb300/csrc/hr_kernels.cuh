@@ -32,16 +32,20 @@ struct Bufs {
   unsigned char* status;  // [nact] worst outcome over the sub-steps
   int* iters;             // [nact] Newton steps summed over the sub-steps
   unsigned char* failed;  // [nact] back-up flag of the current sub-step
-  int* qcount;            // [2] retry-queue and back-up-list lengths
+  int* qcount;            // [4] retry queue, back-up list, Newton continuation queue lengths
   int* qzone;             // [nact] retry queue: zone index within its grid
   int* qbox;              // [nact] retry queue: grid of the entry
   double* qdata;          // [nact][18] retry queue payload: U*, PMHD best x, e_T, h
   int* fzone;             // [nact] back-up list: zone index within its grid
   int* fbox;              // [nact] back-up list: grid of the entry
   double* ftmp;           // [nact][12] averaged primitives of back-up zones
+  int* czone;             // [nact] Newton continuation queue: zone index within its grid
+  int* cbox;              // [nact] Newton continuation queue: grid of the entry
+  double* cdata;          // [nact][CSTRIDE] continuation payload: U*, Newton state
   unsigned long long* stats;  // [8] counters
   unsigned long long* dtmin;  // [nbox] CFL minimum (ordered bits of a positive double)
   // records for the adjoint's recomputation of a step (null otherwise):
+  const double* geo;          // metric tables of Kerr-Schild grids (null otherwise)
   double* ust_rec;            // [12][nact] U* of every zone of the sub-step
   unsigned char* meth_rec;    // [nact] outcome of every zone of the sub-step
   double* psol_rec;           // [12][nact] solution of every zone before the floors
@@ -60,6 +64,98 @@ __device__ __forceinline__ void warp_add(unsigned long long* dst, unsigned v) {
 // Opacity-field value of a cell (1 when the opacity is not a field).
 __device__ __forceinline__ double kfield(const DevParams& p, const double* K, long long t) {
   return p.opacity == 2 ? K[t] : 1.0;
+}
+
+// ------------------------------------------------------------ metric tables
+// The Kerr-Schild metric depends on (x1, x2) only.  A Kerr-Schild grid keeps,
+// per (i, j), the metric at the cell centres, its x1 and x2 derivatives (for
+// the geometric source) and the metric at the x1 and x2 faces, evaluated once
+// when the context is created by the same functions the kernels would call.
+// The FP64 kernels then read 16 doubles (L2-resident: a few MB per grid)
+// instead of evaluating exp, sin, cos and four divisions per zone and face,
+// which matters because the step is bound by FP64 arithmetic.
+// Layout of a grid's table (offset BoxGeo::goff, in doubles): [16][N2][N1]
+// centres, [16][N2][N1] centre derivatives, [16][N2][n1+1] x1 faces,
+// [16][n2+1][N1] x2 faces; fields in the order of Geo (g00 g01 g03 g11 g13
+// g22 g33 G00 G01 G11 G13 G22 G33 gdet alpha ialpha) and of MetricDeriv.
+struct GeoTab {
+  const double* C;
+  const double* M;
+  const double* F0;
+  const double* F1;
+  long long sC, sF0, sF1;  // plane sizes
+};
+
+__host__ __device__ __forceinline__ long long geotab_size(const BoxGeo& b) {
+  const long long sC = (long long)b.N[0] * b.N[1];
+  return 16 * (2 * sC + (long long)(b.n[0] + 1) * b.N[1] + (long long)b.N[0] * (b.n[1] + 1));
+}
+
+__device__ __forceinline__ GeoTab geotab(const double* base, const BoxGeo& b) {
+  GeoTab t;
+  t.sC = (long long)b.N[0] * b.N[1];
+  t.sF0 = (long long)(b.n[0] + 1) * b.N[1];
+  t.sF1 = (long long)b.N[0] * (b.n[1] + 1);
+  t.C = base + b.goff;
+  t.M = t.C + 16 * t.sC;
+  t.F0 = t.M + 16 * t.sC;
+  t.F1 = t.F0 + 16 * t.sF0;
+  return t;
+}
+
+// entry of (i, j) (active indices, ghosts negative): centres, x1 faces
+// (i = face index 0..n1), x2 faces (j = face index 0..n2)
+__device__ __forceinline__ long long gidx_c(const BoxGeo& b, int i, int j) {
+  return (long long)(j + b.ng[1]) * b.N[0] + (i + b.ng[0]);
+}
+__device__ __forceinline__ long long gidx_f0(const BoxGeo& b, int i, int j) {
+  return (long long)(j + b.ng[1]) * (b.n[0] + 1) + i;
+}
+__device__ __forceinline__ long long gidx_f1(const BoxGeo& b, int i, int j) {
+  return (long long)j * b.N[0] + (i + b.ng[0]);
+}
+
+template <int MET>
+__device__ __forceinline__ Geo<MET, double> geo_load(const double* __restrict__ t, long long s, long long x) {
+  Geo<MET, double> g;
+  g.g00 = __ldg(t + x);
+  g.g01 = __ldg(t + s + x);
+  g.g03 = __ldg(t + 2 * s + x);
+  g.g11 = __ldg(t + 3 * s + x);
+  g.g13 = __ldg(t + 4 * s + x);
+  g.g22 = __ldg(t + 5 * s + x);
+  g.g33 = __ldg(t + 6 * s + x);
+  g.G00 = __ldg(t + 7 * s + x);
+  g.G01 = __ldg(t + 8 * s + x);
+  g.G11 = __ldg(t + 9 * s + x);
+  g.G13 = __ldg(t + 10 * s + x);
+  g.G22 = __ldg(t + 11 * s + x);
+  g.G33 = __ldg(t + 12 * s + x);
+  g.gdet = __ldg(t + 13 * s + x);
+  g.alpha = __ldg(t + 14 * s + x);
+  g.ialpha = __ldg(t + 15 * s + x);
+  return g;
+}
+
+template <int MET>
+__device__ __forceinline__ void geo_store(double* t, long long s, long long x, const Geo<MET, double>& g) {
+  const double v[16] = {g.g00, g.g01, g.g03, g.g11, g.g13, g.g22, g.g33, g.G00,
+                        g.G01, g.G11, g.G13, g.G22, g.G33, g.gdet, g.alpha, g.ialpha};
+  for (int f = 0; f < 16; ++f) t[f * s + x] = v[f];
+}
+
+// Metric of the centre of cell (i, j): from the table when the grid has one
+// (FP64 kernels), else evaluated.
+template <int MET, typename R>
+__device__ __forceinline__ Geo<MET, R> geo_centre(const DevParams& p, const BoxGeo& bx, const double* geo0, int i,
+                                                  int j) {
+  if constexpr (MET == KS && std::is_same<R, double>::value) {
+    if (geo0 && bx.goff >= 0) {
+      const GeoTab T = geotab(geo0, bx);
+      return geo_load<MET>(T.C, T.sC, gidx_c(bx, i, j));
+    }
+  }
+  return make_geo<MET, R>(p, R(xcen(bx, 0, i)), R(xcen(bx, 1, j)));
 }
 
 // ----------------------------------------------------------- ghost fill
@@ -135,7 +231,7 @@ static __global__ void k_bc_fill(DevParams p, const BoxGeo* __restrict__ boxes, 
 template <int MET, typename R>
 __global__ void k_prep(DevParams p, const BoxGeo* __restrict__ boxes, int nbox,
                        const double* __restrict__ P0, const double* __restrict__ K0,
-                       R* __restrict__ aux0) {
+                       R* __restrict__ aux0, const double* __restrict__ geo0) {
   for (int bi = 0; bi < nbox; ++bi) {
     const BoxGeo& bx = boxes[bi];
     const double* P = P0 + 12 * bx.coff;
@@ -146,7 +242,7 @@ __global__ void k_prep(DevParams p, const BoxGeo* __restrict__ boxes, int nbox,
       int i = (int)(r % bx.N[0]) - bx.ng[0];
       r /= bx.N[0];
       int j = (int)(r % bx.N[1]) - bx.ng[1];
-      Geo<MET, R> g = make_geo<MET, R>(p, R(xcen(bx, 0, i)), R(xcen(bx, 1, j)));
+      const Geo<MET, R> g = geo_centre<MET, R>(p, bx, geo0, i, j);
       R ucon[4], ucov[4], gm, urc[4], urv[4], gr;
       fourvel<MET, R>(g, R(P[U1 * bx.ntot + t]), R(P[U2 * bx.ntot + t]), R(P[U3 * bx.ntot + t]), ucon, ucov, &gm);
       fourvel<MET, R>(g, R(P[UR1 * bx.ntot + t]), R(P[UR2 * bx.ntot + t]), R(P[UR3 * bx.ntot + t]), urc, urv, &gr);
@@ -274,15 +370,13 @@ __device__ __forceinline__ R mc_slope(R qm, R q0, R qp) {
 
 // PPM edge values of the centre of s[0..4] (Colella & Woodward 1984, no
 // contact steepening), flattened toward the cell mean by chi, then limited.
+// sm, s0, sp: the cell and its neighbours; dm, d0, dp: their MC slopes.
 template <typename R>
-__device__ __forceinline__ void ppm_cell(const R s[5], R chi, R* aL, R* aR) {
-  R dm = mc_slope<R>(s[0], s[1], s[2]);
-  R d0 = mc_slope<R>(s[1], s[2], s[3]);
-  R dp = mc_slope<R>(s[2], s[3], s[4]);
+__device__ __forceinline__ void ppm_slopes(R sm, R s0, R sp, R dm, R d0, R dp, R chi, R* aL, R* aR) {
   const R sixth = R(1.0 / 6.0);
-  R l = R(0.5) * (s[1] + s[2]) - (d0 - dm) * sixth;
-  R r = R(0.5) * (s[2] + s[3]) - (dp - d0) * sixth;
-  R q = s[2];
+  R l = R(0.5) * (sm + s0) - (d0 - dm) * sixth;
+  R r = R(0.5) * (s0 + sp) - (dp - d0) * sixth;
+  R q = s0;
   l = (R(1) - chi) * l + chi * q;
   r = (R(1) - chi) * r + chi * q;
   if ((r - q) * (q - l) <= R(0)) {
@@ -298,25 +392,89 @@ __device__ __forceinline__ void ppm_cell(const R s[5], R chi, R* aL, R* aR) {
   *aR = r;
 }
 
+template <typename R>
+__device__ __forceinline__ void ppm_cell(const R s[5], R chi, R* aL, R* aR) {
+  R dm = mc_slope<R>(s[0], s[1], s[2]);
+  R d0 = mc_slope<R>(s[1], s[2], s[3]);
+  R dp = mc_slope<R>(s[2], s[3], s[4]);
+  ppm_slopes<R>(s[1], s[2], s[3], dm, d0, dp, chi, aL, aR);
+}
+
 // ------------------------------------------------------- edge reconstruction
+// MC slopes of all 12 primitives along d, once per cell: the PPM edges of a
+// cell need the slopes of the cell and of its two neighbours, so computing
+// them here saves two of every three slope evaluations of the edge kernel.
+// Range: cells -2..n_d+1 along d, transverse range widened by one layer.  In
+// r and phi on the Kerr-Schild grid the velocity and field components are
+// reconstructed as sqrt(-g) times the primitive (Sec. 4.3).
+template <int MET, typename R, int d>
+__global__ void __launch_bounds__(256) k_slopes(DevParams p, const BoxGeo* __restrict__ boxes, int nbox,
+                                                const double* __restrict__ P0, const R* __restrict__ aux0,
+                                                R* __restrict__ S0) {
+  const bool weighted = (MET == KS) && (d != 1);
+  for (int bi = 0; bi < nbox; ++bi) {
+    const BoxGeo& bx = boxes[bi];
+    const double* P = P0 + 12 * bx.coff;
+    const R* aux = aux0 + 10 * bx.coff;
+    R* S = S0 + 12 * bx.coff;
+    int len[3], off[3];
+    for (int e = 0; e < 3; ++e) {
+      if (bx.n[e] > 1) {
+        len[e] = bx.n[e] + (e == d ? 4 : 2);
+        off[e] = e == d ? -2 : -1;
+      } else {
+        len[e] = 1;
+        off[e] = 0;
+      }
+    }
+    long long total = (long long)len[0] * len[1] * len[2];
+    const long long st = bx.str[d];
+    for (long long id = HR_TID; id < total; id += HR_STRIDE) {
+      long long r = id;
+      int i = (int)(r % len[0]) + off[0];
+      r /= len[0];
+      int j = (int)(r % len[1]) + off[1];
+      int k = (int)(r / len[1]) + off[2];
+      long long t = cell_index(bx, i, j, k);
+      R gw[3];
+      if (weighted) {
+#pragma unroll
+        for (int m = 0; m < 3; ++m) gw[m] = aux[t + (m - 1) * st];
+      }
+#pragma unroll
+      for (int q = 0; q < NPR; ++q) {
+        const bool wq = weighted && ((q >= U1 && q <= B3) || q >= UR1);
+        R s[3];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          R v = R(P[q * bx.ntot + t + (m - 1) * st]);
+          s[m] = wq ? gw[m] * v : v;
+        }
+        S[q * bx.ntot + t] = mc_slope<R>(s[0], s[1], s[2]);
+      }
+    }
+  }
+}
+
 // One thread per cell of the face range of direction d (cells -1..n_d along d,
 // transverse range widened by one layer): the cell's PPM parabola (or MC
-// slope) for all 12 primitives, flattened by the cell's GAS or RAD
-// flattener, stored as the two edge values E[0][q] (lower) and E[1][q]
-// (upper).  Every parabola is built once per direction; the face kernel reads
-// the upper edge of cell f-1 and the lower edge of cell f.  In r and phi on
-// the Kerr-Schild grid the velocity and field components are reconstructed
-// as sqrt(-g) times the primitive (Sec. 4.3).
+// slope) for all 12 primitives from the slopes of k_slopes (S0; null: the
+// slopes are computed here, as the FP32 path does), flattened by the
+// cell's GAS or RAD flattener, stored as the two edge values E[0][q] (lower)
+// and E[1][q] (upper).  Every parabola is built once per direction; the face
+// kernel reads the upper edge of cell f-1 and the lower edge of cell f.
 template <int MET, typename R, int d>
 __global__ void __launch_bounds__(256) k_edges(DevParams p, const BoxGeo* __restrict__ boxes, int nbox,
                                                const double* __restrict__ P0, const R* __restrict__ aux0,
-                                               const R* __restrict__ flat0, R* __restrict__ E0) {
+                                               const R* __restrict__ flat0, const R* __restrict__ S0,
+                                               R* __restrict__ E0) {
   const bool weighted = (MET == KS) && (d != 1);
   for (int bi = 0; bi < nbox; ++bi) {
     const BoxGeo& bx = boxes[bi];
     const double* P = P0 + 12 * bx.coff;
     const R* aux = aux0 + 10 * bx.coff;
     const R* flat = flat0 + 2 * bx.coff;
+    const R* S = S0 + 12 * bx.coff;
     R* E = E0 + 24 * bx.coff;
     int len[3], off[3];
     for (int e = 0; e < 3; ++e) {
@@ -342,27 +500,58 @@ __global__ void __launch_bounds__(256) k_edges(DevParams p, const BoxGeo* __rest
         chg = flat[t];
         chr = flat[bx.ntot + t];
       }
-      R gw[5];
-      if (weighted) {
+      if (!S0) {  // slopes computed here (FP32, where arithmetic is cheap)
+        R gw[5];
+        if (weighted) {
 #pragma unroll
-        for (int m = 0; m < 5; ++m) gw[m] = aux[t + (m - 2) * st];
+          for (int m = 0; m < 5; ++m) gw[m] = aux[t + (m - 2) * st];
+        }
+#pragma unroll
+        for (int q = 0; q < NPR; ++q) {
+          const bool wq = weighted && ((q >= U1 && q <= B3) || q >= UR1);
+          R s[5];
+#pragma unroll
+          for (int m = 0; m < 5; ++m) {
+            R v = R(P[q * bx.ntot + t + (m - 2) * st]);
+            s[m] = wq ? gw[m] * v : v;
+          }
+          R aL, aR;
+          if (p.recon == 0) {
+            ppm_cell<R>(s, q < ER ? chg : chr, &aL, &aR);
+          } else {
+            R dq = mc_slope<R>(s[1], s[2], s[3]);
+            aL = s[2] - R(0.5) * dq;
+            aR = s[2] + R(0.5) * dq;
+          }
+          E[q * bx.ntot + t] = aL;
+          E[(NPR + q) * bx.ntot + t] = aR;
+        }
+        continue;
+      }
+      R gw[3];
+      if (weighted && p.recon == 0) {
+#pragma unroll
+        for (int m = 0; m < 3; ++m) gw[m] = aux[t + (m - 1) * st];
       }
 #pragma unroll
       for (int q = 0; q < NPR; ++q) {
         const bool wq = weighted && ((q >= U1 && q <= B3) || q >= UR1);
-        R s[5];
-#pragma unroll
-        for (int m = 0; m < 5; ++m) {
-          R v = R(P[q * bx.ntot + t + (m - 2) * st]);
-          s[m] = wq ? gw[m] * v : v;
-        }
         R aL, aR;
         if (p.recon == 0) {
-          ppm_cell<R>(s, q < ER ? chg : chr, &aL, &aR);
+          R s[3], ds[3];
+#pragma unroll
+          for (int m = 0; m < 3; ++m) {
+            R v = R(P[q * bx.ntot + t + (m - 1) * st]);
+            s[m] = wq ? gw[m] * v : v;
+            ds[m] = S[q * bx.ntot + t + (m - 1) * st];
+          }
+          ppm_slopes<R>(s[0], s[1], s[2], ds[0], ds[1], ds[2], q < ER ? chg : chr, &aL, &aR);
         } else {
-          R dq = mc_slope<R>(s[1], s[2], s[3]);
-          aL = s[2] - R(0.5) * dq;
-          aR = s[2] + R(0.5) * dq;
+          R v = R(P[q * bx.ntot + t]);
+          if (wq) v = aux[t] * v;
+          const R dq = S[q * bx.ntot + t];
+          aL = v - R(0.5) * dq;
+          aR = v + R(0.5) * dq;
         }
         E[q * bx.ntot + t] = aL;
         E[(NPR + q) * bx.ntot + t] = aR;
@@ -437,7 +626,8 @@ __device__ __forceinline__ void face_flux(const DevParams& p, const Geo<MET, R>&
 template <int MET, typename R, int d>
 __global__ void __launch_bounds__(128) k_face(DevParams p, const BoxGeo* __restrict__ boxes, int nbox,
                                               const R* __restrict__ E0, const double* __restrict__ K0,
-                                              R* __restrict__ F0, R* __restrict__ spd0) {
+                                              R* __restrict__ F0, R* __restrict__ spd0,
+                                              const double* __restrict__ geo0) {
   const bool weighted = (MET == KS) && (d != 1);
   for (int bi = 0; bi < nbox; ++bi) {
     const BoxGeo& bx = boxes[bi];
@@ -476,9 +666,22 @@ __global__ void __launch_bounds__(128) k_face(DevParams p, const BoxGeo* __restr
         spd[t] = R(0);
         continue;
       }
-      R xf[3];
-      for (int e = 0; e < 3; ++e) xf[e] = R(bx.x0[e] + (ii[e] + (e == d ? 0.0 : 0.5)) * bx.dx[e]);
-      Geo<MET, R> g = make_geo<MET, R>(p, xf[0], xf[1]);
+      Geo<MET, R> g;
+      bool tab = false;
+      if constexpr (MET == KS && std::is_same<R, double>::value) {
+        if (geo0 && bx.goff >= 0) {
+          const GeoTab T = geotab(geo0, bx);
+          if (d == 0) g = geo_load<MET>(T.F0, T.sF0, gidx_f0(bx, ii[0], ii[1]));
+          else if (d == 1) g = geo_load<MET>(T.F1, T.sF1, gidx_f1(bx, ii[0], ii[1]));
+          else g = geo_load<MET>(T.C, T.sC, gidx_c(bx, ii[0], ii[1]));
+          tab = true;
+        }
+      }
+      if (!tab) {
+        R xf[3];
+        for (int e = 0; e < 3; ++e) xf[e] = R(bx.x0[e] + (ii[e] + (e == d ? 0.0 : 0.5)) * bx.dx[e]);
+        g = make_geo<MET, R>(p, xf[0], xf[1]);
+      }
       const R igf = weighted ? R(1) / g.gdet : R(1);
       R PL[NPR], PR[NPR];
 #pragma unroll
@@ -686,13 +889,55 @@ __device__ __forceinline__ T qform(const MetricDeriv& m, int n, const T v[4]) {
          m.g33[n] * v[3] * v[3];
 }
 
+__device__ __forceinline__ MetricDeriv md_load(const double* __restrict__ t, long long s, long long x) {
+  MetricDeriv m;
+  double* v = reinterpret_cast<double*>(&m);  // the 16 doubles of MetricDeriv, in declaration order
+  for (int f = 0; f < 16; ++f) v[f] = __ldg(t + f * s + x);
+  return m;
+}
+
+// Fills the metric tables of the Kerr-Schild grids of a context.
+static __global__ void k_geo_init(DevParams p, const BoxGeo* __restrict__ boxes, int nbox, double* geo0) {
+  for (int bi = 0; bi < nbox; ++bi) {
+    const BoxGeo& bx = boxes[bi];
+    if (bx.goff < 0) continue;
+    const GeoTab T = geotab(geo0, bx);
+    double* C = const_cast<double*>(T.C);
+    double* M = const_cast<double*>(T.M);
+    double* F0 = const_cast<double*>(T.F0);
+    double* F1 = const_cast<double*>(T.F1);
+    const long long total = 2 * T.sC + T.sF0 + T.sF1;
+    for (long long id = HR_TID; id < total; id += HR_STRIDE) {
+      if (id < T.sC) {  // centres and their derivatives
+        const int i = (int)(id % bx.N[0]) - bx.ng[0], j = (int)(id / bx.N[0]) - bx.ng[1];
+        const double x1 = xcen(bx, 0, i), x2 = xcen(bx, 1, j);
+        geo_store<KS>(C, T.sC, id, make_geo<KS, double>(p, x1, x2));
+        const MetricDeriv md = ks_derivs(p, x1, x2);
+        const double* v = reinterpret_cast<const double*>(&md);
+        for (int f = 0; f < 16; ++f) M[f * T.sC + id] = v[f];
+      } else if (id < T.sC + T.sF0) {  // x1 faces
+        const long long e = id - T.sC;
+        const int i = (int)(e % (bx.n[0] + 1)), j = (int)(e / (bx.n[0] + 1)) - bx.ng[1];
+        const double x1 = bx.x0[0] + (i + 0.0) * bx.dx[0], x2 = bx.x0[1] + (j + 0.5) * bx.dx[1];
+        geo_store<KS>(F0, T.sF0, e, make_geo<KS, double>(p, x1, x2));
+      } else if (id < T.sC + T.sF0 + T.sF1) {  // x2 faces
+        const long long e = id - T.sC - T.sF0;
+        const int i = (int)(e % bx.N[0]) - bx.ng[0], j = (int)(e / bx.N[0]);
+        const double x1 = bx.x0[0] + (i + 0.5) * bx.dx[0], x2 = bx.x0[1] + (j + 0.0) * bx.dx[1];
+        geo_store<KS>(F1, T.sF1, e, make_geo<KS, double>(p, x1, x2));
+      }
+    }
+  }
+}
+
 // U(P) and the geometric source SM(P) of one zone (X = SM on return):
 // SM_nu = 1/2 sqrt(-g) T^{mu kappa} d_nu g_{mu kappa}, equal to
 // sqrt(-g) T^kappa_lambda Gamma^lambda_{nu kappa} for a symmetric T and nonzero
 // only for nu = x1, x2 on the stationary axisymmetric metric.
 template <int MET, typename T>
 __device__ __forceinline__ void cons_source(const DevParams& p, const Geo<MET, T>& g, double x1, double x2,
-                                            const T Ps[NPR], T Us[NPR], T X[NPR]) {
+                                            const T Ps[NPR], T Us[NPR], T X[NPR],
+                                            const MetricDeriv* mdp = nullptr) {
   T ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq, urc[4], urv[4], gr;
   fourvel<MET, T>(g, Ps[U1], Ps[U2], Ps[U3], ucon, ucov, &gm);
   bvec<MET, T>(g, ucon, ucov, Ps[B1], Ps[B2], Ps[B3], bcon, bcov, &bsq);
@@ -714,7 +959,7 @@ __device__ __forceinline__ void cons_source(const DevParams& p, const Geo<MET, T
 #pragma unroll
   for (int q = 0; q < NPR; ++q) X[q] = T(0.0);
   if constexpr (MET == KS) {
-    MetricDeriv md = ks_derivs(p, x1, x2);
+    const MetricDeriv md = mdp ? *mdp : ks_derivs(p, x1, x2);
 #pragma unroll
     for (int n = 0; n < 2; ++n) {
       T qu = qform(md, n, ucon), qb = qform(md, n, bcon), qr = qform(md, n, urc);
@@ -724,6 +969,86 @@ __device__ __forceinline__ void cons_source(const DevParams& p, const Geo<MET, T
   }
   (void)x1;
   (void)x2;
+}
+
+// Newton iterations the update kernel runs before it hands a zone to the
+// continuation queue (most zones of the torus end within 2 steps, i.e. 3
+// iterations counting the final residual check).
+constexpr int NEWTON_SPLIT = 3;
+constexpr int CSTRIDE = NPR + 21;  // continuation queue record: U*, Newton state
+
+__device__ __forceinline__ void newton_state_store(const NewtonState& st, double* d) {
+  for (int i = 0; i < 4; ++i) {
+    d[i] = st.x[i];
+    d[4 + i] = st.best_x[i];
+  }
+  d[8] = st.best_eT;
+  d[9] = st.hs.t1;
+  d[10] = st.hs.t2;
+  d[11] = st.hs.t3;
+  d[12] = st.hs.t4;
+  d[13] = st.hs.i1;
+  d[14] = st.hs.i2;
+  d[15] = st.hs.i3;
+  d[16] = st.hs.i4;
+  d[17] = st.eps;
+  d[18] = (double)st.hs.rises;
+  d[19] = (double)st.k;
+  d[20] = (double)st.steps;
+}
+
+__device__ __forceinline__ void newton_state_load(const double* d, NewtonState& st) {
+  for (int i = 0; i < 4; ++i) {
+    st.x[i] = d[i];
+    st.best_x[i] = d[4 + i];
+  }
+  st.best_eT = d[8];
+  st.hs.t1 = d[9];
+  st.hs.t2 = d[10];
+  st.hs.t3 = d[11];
+  st.hs.t4 = d[12];
+  st.hs.i1 = d[13];
+  st.hs.i2 = d[14];
+  st.hs.i3 = d[15];
+  st.hs.i4 = d[16];
+  st.eps = d[17];
+  st.hs.rises = (int)d[18];
+  st.k = (int)d[19];
+  st.steps = (int)d[20];
+}
+
+// End of a zone's PMHD solve: accept (e_T < 1e-9: final primitives, floors,
+// write) or queue the zone for URAD.  Returns whether it was accepted.
+template <int MET>
+__device__ __forceinline__ bool pmhd_finish(const DevParams& p, const BoxGeo& bx, int bi, long long z, long long t,
+                                            double x1, const Geo<MET, double>& g, const ImpSys<MET>& s,
+                                            const double Ust[NPR], double h, const NewtonState& ns, double* P,
+                                            const Bufs& b) {
+  const long long zg = bx.aoff + z;
+  b.iters[zg] += ns.steps;
+  const double beT = ns.best_eT;
+  const bool accept = beT < 1e-9;
+  if (accept) {
+    double Pn[NPR];
+    pmhd_final<MET>(p, s, ns.best_x, Pn);
+    if (b.psol_rec)
+      for (int q = 0; q < NPR; ++q) b.psol_rec[q * bx.nact + z] = Pn[q];
+    apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn);
+#pragma unroll
+    for (int q = 0; q < NPR; ++q) P[q * bx.ntot + t] = Pn[q];
+    if (b.meth_rec) b.meth_rec[zg] = ST_PMHD;
+  } else {
+    int slot = atomicAdd(&b.qcount[0], 1);
+    b.qzone[slot] = (int)z;
+    b.qbox[slot] = bi;
+    double* qd = b.qdata + (long long)slot * QSTRIDE;
+#pragma unroll
+    for (int q = 0; q < NPR; ++q) qd[q] = Ust[q];
+    for (int q = 0; q < 4; ++q) qd[12 + q] = isfinite(beT) ? ns.best_x[q] : 0.0;
+    qd[16] = beT;
+    qd[17] = h;
+  }
+  return accept;
 }
 
 // ------------------------------------------------------- update + implicit
@@ -754,13 +1079,23 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
       int k = (int)(r / bx.n[1]);
       long long t = cell_index(bx, i, j, k);
       double x1 = xcen(bx, 0, i), x2 = xcen(bx, 1, j);
-      Geo<MET, double> g = make_geo<MET, double>(p, x1, x2);
+      const bool tab = MET == KS && b.geo && bx.goff >= 0;
+      Geo<MET, double> g;
+      MetricDeriv mdt;
+      if (tab) {
+        const GeoTab T = geotab(b.geo, bx);
+        const long long gi = gidx_c(bx, i, j);
+        g = geo_load<MET>(T.C, T.sC, gi);
+        mdt = md_load(T.M, T.sC, gi);
+      } else {
+        g = make_geo<MET, double>(p, x1, x2);
+      }
       double Ps[NPR];
 #pragma unroll
       for (int q = 0; q < NPR; ++q) Ps[q] = P[q * bx.ntot + t];
       const double kz = kfield(p, K, t);
       double Us[NPR], X[NPR];
-      cons_source<MET, double>(p, g, x1, x2, Ps, Us, X);
+      cons_source<MET, double>(p, g, x1, x2, Ps, Us, X, tab ? &mdt : nullptr);
       // flux divergence
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
@@ -812,35 +1147,64 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
           }
         }
       }
-      double bxn[4], beT;
-      int steps = newton_pmhd<MET>(p, s, x0, bxn, &beT);
-      const long long zg = bx.aoff + z;
-      b.iters[zg] += steps;
-      bool accept = beT < 1e-9;
-      if (accept) {
-        double Pn[NPR];
-        pmhd_final<MET>(p, s, bxn, Pn);
-        if (b.psol_rec)
-          for (int q = 0; q < NPR; ++q) b.psol_rec[q * bx.nact + z] = Pn[q];
-        apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn);
-#pragma unroll
-        for (int q = 0; q < NPR; ++q) P[q * bx.ntot + t] = Pn[q];
-        if (b.meth_rec) b.meth_rec[zg] = ST_PMHD;
+      NewtonState ns;
+      newton_pmhd_init(x0, ns);
+      // the first NEWTON_SPLIT iterations here; a zone that needs more
+      // continues in the compacted queue (k_newton_cont), so that the
+      // heavy tail of iteration counts runs in full warps
+      const bool done = newton_pmhd_run<MET>(p, s, ns, NEWTON_SPLIT);
+      bool accept = false;
+      if (done) {
+        accept = pmhd_finish<MET>(p, bx, bi, z, t, x1, g, s, Ust, h, ns, P, b);
       } else {
-        int slot = atomicAdd(&b.qcount[0], 1);
-        b.qzone[slot] = (int)z;
-        b.qbox[slot] = bi;
-        double* qd = b.qdata + (long long)slot * QSTRIDE;
+        const int slot = atomicAdd(&b.qcount[2], 1);
+        b.czone[slot] = (int)z;
+        b.cbox[slot] = bi;
+        double* cd = b.cdata + (long long)slot * CSTRIDE;
 #pragma unroll
-        for (int q = 0; q < NPR; ++q) qd[q] = Ust[q];
-        for (int q = 0; q < 4; ++q) qd[12 + q] = isfinite(beT) ? bxn[q] : 0.0;
-        qd[16] = beT;
-        qd[17] = h;
+        for (int q = 0; q < NPR; ++q) cd[q] = Ust[q];
+        newton_state_store(ns, cd + NPR);
       }
       warp_add(&b.stats[ST_PMHD], accept ? 1u : 0u);
-      warp_add(&b.stats[ST_ITERS], (unsigned)steps);
+      warp_add(&b.stats[ST_ITERS], done ? (unsigned)ns.steps : 0u);
       warp_add(&b.stats[ST_SOLVES], 1u);
     }
+  }
+}
+
+// Zones whose PMHD Newton iteration did not end within NEWTON_SPLIT
+// iterations of the update kernel: a persistent grid over the compacted queue
+// resumes each iteration from its saved state (same arithmetic as an
+// uninterrupted iteration) and finishes the zone as the update kernel would.
+template <int MET>
+__global__ void __launch_bounds__(128) k_newton_cont(DevParams p, const BoxGeo* __restrict__ boxes, Bufs b,
+                                                     int stage) {
+  const double Bc = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
+  const int nq = b.qcount[2];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nq; e += gridDim.x * blockDim.x) {
+    const int bi = b.cbox[e];
+    const BoxGeo& bx = boxes[bi];
+    const long long z = b.czone[e];
+    long long r = z;
+    const int i = (int)(r % bx.n[0]);
+    r /= bx.n[0];
+    const int j = (int)(r % bx.n[1]);
+    const int k = (int)(r / bx.n[1]);
+    const long long t = cell_index(bx, i, j, k);
+    const double x1 = xcen(bx, 0, i);
+    const Geo<MET, double> g = geo_centre<MET, double>(p, bx, b.geo, i, j);
+    const double* cd = b.cdata + (long long)e * CSTRIDE;
+    double Ust[NPR];
+    for (int q = 0; q < NPR; ++q) Ust[q] = cd[q];
+    NewtonState ns;
+    newton_state_load(cd + NPR, ns);
+    const double h = Bc * b.dt[bi];
+    ImpSys<MET> s;
+    build_sys<MET>(p, g, Ust, h, kfield(p, b.K + bx.coff, t), s);
+    newton_pmhd_run<MET>(p, s, ns, 1 << 30);
+    const bool accept = pmhd_finish<MET>(p, bx, bi, z, t, x1, g, s, Ust, h, ns, b.P + 12 * bx.coff, b);
+    if (accept) atomicAdd(&b.stats[ST_PMHD], 1ULL);
+    atomicAdd(&b.stats[ST_ITERS], (unsigned long long)ns.steps);
   }
 }
 

@@ -50,6 +50,7 @@ struct BoxGeo {
   int bc[6];
   long long coff;    // first cell of this grid in cell-indexed arrays
   long long aoff;    // first active zone of this grid in active-zone arrays
+  long long goff;    // first double of this grid's metric table (-1: none)
 };
 
 // ----------------------------------------------------------------- geometry

@@ -29,8 +29,12 @@ inline Bufs make_bufs(harmrad_ctx* c) {
   b.fzone = c->fzone;
   b.fbox = c->fbox;
   b.ftmp = c->ftmp;
+  b.czone = c->czone;
+  b.cbox = c->cbox;
+  b.cdata = c->cdata;
   b.stats = c->stats;
   b.dtmin = c->dtmin;
+  b.geo = c->geotab;
   b.ust_rec = c->rec_ust;
   b.meth_rec = c->rec_meth;
   b.psol_rec = c->rec_psol;
@@ -68,7 +72,8 @@ int faces_impl(harmrad_ctx* c, bool fresh) {
     mark(c, HARMRAD_K_BC);
     ++nk;
   }
-  k_prep<MET, R><<<grid_for(c->maxcell, c->sms, 256), 256, 0, st>>>(p, bt, nb, c->P, c->K, (R*)c->aux);
+  k_prep<MET, R><<<grid_for(c->maxcell, c->sms, 256), 256, 0, st>>>(p, bt, nb, c->P, c->K, (R*)c->aux,
+                                                                     c->geotab);
   mark(c, HARMRAD_K_PREP);
   ++nk;
   auto range_cells = [](const BoxGeo& b) {
@@ -99,6 +104,14 @@ int faces_impl(harmrad_ctx* c, bool fresh) {
     const harmrad_tuning& tu = c->tune;
     const int be = tu.edge_block, bf = tu.face_block;
     const int ge = grid_for(max_work(c, range_cells), c->sms, be, tu.edge_blocks_per_sm);
+    const int gs = grid_for(max_work(c, [d](const BoxGeo& b) {
+                              long long w = 1;
+                              for (int e = 0; e < 3; ++e) w *= b.n[e] > 1 ? b.n[e] + (e == d ? 4 : 2) : 1;
+                              return w;
+                            }),
+                            c->sms, be, tu.edge_blocks_per_sm);
+    // FP64: slopes once per cell in their own pass; FP32: in the edge kernel
+    R* Sl = std::is_same<R, double>::value ? (R*)c->slope : nullptr;
     const int g = grid_for(wf, c->sms, bf, tu.face_blocks_per_sm);
     const R* aux = (const R*)c->aux;
     const R* fl = (const R*)c->flat[d];
@@ -106,17 +119,32 @@ int faces_impl(harmrad_ctx* c, bool fresh) {
     R* Fd = (R*)c->F[d];
     R* sd = (R*)c->spd[d];
     if (d == 0) {
-      k_edges<MET, R, 0><<<ge, be, 0, st>>>(p, bt, nb, c->P, aux, fl, Ed);
+      if (Sl) {
+        k_slopes<MET, R, 0><<<gs, be, 0, st>>>(p, bt, nb, c->P, aux, Sl);
+        mark(c, HARMRAD_K_EDGE);
+        ++nk;
+      }
+      k_edges<MET, R, 0><<<ge, be, 0, st>>>(p, bt, nb, c->P, aux, fl, Sl, Ed);
       mark(c, HARMRAD_K_EDGE);
-      k_face<MET, R, 0><<<g, bf, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd);
+      k_face<MET, R, 0><<<g, bf, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd, c->geotab);
     } else if (d == 1) {
-      k_edges<MET, R, 1><<<ge, be, 0, st>>>(p, bt, nb, c->P, aux, fl, Ed);
+      if (Sl) {
+        k_slopes<MET, R, 1><<<gs, be, 0, st>>>(p, bt, nb, c->P, aux, Sl);
+        mark(c, HARMRAD_K_EDGE);
+        ++nk;
+      }
+      k_edges<MET, R, 1><<<ge, be, 0, st>>>(p, bt, nb, c->P, aux, fl, Sl, Ed);
       mark(c, HARMRAD_K_EDGE);
-      k_face<MET, R, 1><<<g, bf, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd);
+      k_face<MET, R, 1><<<g, bf, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd, c->geotab);
     } else {
-      k_edges<MET, R, 2><<<ge, be, 0, st>>>(p, bt, nb, c->P, aux, fl, Ed);
+      if (Sl) {
+        k_slopes<MET, R, 2><<<gs, be, 0, st>>>(p, bt, nb, c->P, aux, Sl);
+        mark(c, HARMRAD_K_EDGE);
+        ++nk;
+      }
+      k_edges<MET, R, 2><<<ge, be, 0, st>>>(p, bt, nb, c->P, aux, fl, Sl, Ed);
       mark(c, HARMRAD_K_EDGE);
-      k_face<MET, R, 2><<<g, bf, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd);
+      k_face<MET, R, 2><<<g, bf, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd, c->geotab);
     }
     mark(c, HARMRAD_K_FACE);
     nk += 2;
@@ -168,7 +196,7 @@ template <int MET, typename R>
 int solve_impl(harmrad_ctx* c, int stage) {
   const DevParams& p = c->dp;
   cudaStream_t st = c->stream;
-  if (cudaMemsetAsync(c->qcount, 0, 2 * sizeof(int), st) != cudaSuccess) return HARMRAD_E_CUDA;
+  if (cudaMemsetAsync(c->qcount, 0, 4 * sizeof(int), st) != cudaSuccess) return HARMRAD_E_CUDA;
   if (cudaMemsetAsync(c->failed, 0, c->nact, st) != cudaSuccess) return HARMRAD_E_CUDA;
   mark(c, HARMRAD_K_OTHER);
   Bufs b = make_bufs(c);
@@ -179,7 +207,10 @@ int solve_impl(harmrad_ctx* c, int stage) {
   else
     k_update<MET, R, false><<<gu, bu, 0, st>>>(p, c->boxes[0], c->dboxes, c->nbox, b, stage);
   mark(c, HARMRAD_K_UPDATE);
-  // the retry queue and back-up list are short: one persistent wave of blocks
+  // the continuation queue, the retry queue and the back-up list are short:
+  // one persistent wave of blocks each
+  k_newton_cont<MET><<<c->sms * 2, 128, 0, st>>>(p, c->dboxes, b, stage);
+  mark(c, HARMRAD_K_UPDATE);
   k_retry<MET><<<c->sms * 2, 128, 0, st>>>(p, c->dboxes, b);
   mark(c, HARMRAD_K_RETRY);
   k_backup_avg<<<c->sms, 128, 0, st>>>(p, c->dboxes, b);
@@ -187,7 +218,7 @@ int solve_impl(harmrad_ctx* c, int stage) {
   k_backup_apply<MET><<<c->sms, 128, 0, st>>>(p, c->dboxes, b);
   mark(c, HARMRAD_K_BACKUP);
   if (cudaGetLastError() != cudaSuccess) return HARMRAD_E_CUDA;
-  return 4;
+  return 5;
 }
 
 // --------------------------------------------------- point-wise entry kernels

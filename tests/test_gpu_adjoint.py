@@ -76,9 +76,18 @@ def cases():
     out["mink_mc_laxf"] = (dict(cfg, newton_tol=TOL), P)
     cfg, P = W.minkowski_box((8, 8, 8), seed=6, recon=W.PPM, flux=W.HLL)
     out["mink_ppm_hll"] = (dict(cfg, newton_tol=TOL), P)
-    cfg, P = W.ks_random_state((32, 16, 8), seed=9)
+    cfg, P = W.ks_random_state((32, 16, 8), seed=9, tau=1.0)
     out["ks_random_ppm_laxf_kramers"] = (dict(cfg, newton_tol=TOL), P)
+    cfg, P = W.ks_random_state((32, 16, 8), seed=9, tau=10.0)
+    out["ks_random_stiff_urad"] = (dict(cfg, newton_tol=TOL), P)
     return out
+
+
+# Tolerance of the kappa_scale derivative.  kappa_scale moves every zone at
+# once; in the stiff case about 4 % of the zone-stages are solved by URAD,
+# whose tolerance is 1e-9 (not the PMHD one), and the implicit-function
+# derivative is exact only at an exact root.
+KAPPA_TOL = {"ks_random_stiff_urad": 1e-5}
 
 
 CASES = cases()
@@ -111,13 +120,13 @@ def test_step_adjoint_against_finite_differences(name):
         worst = max(worst, min(res))
     ks = cfg["kappa_scale"]
     eks = []
-    for h in (1e-5, 1e-6):
+    for h in (1e-5, 1e-6, 3e-7, 1e-7):
         fd = (L(run(dict(cfg, kappa_scale=ks * (1 + h)), P, dt)) -
               L(run(dict(cfg, kappa_scale=ks * (1 - h)), P, dt))) / (2 * h * ks)
         eks.append(abs(gk - fd) / max(abs(gk), abs(fd), 1e-300))
         print("%s kappa_scale, h %.0e: adjoint %.10e fd %.10e rel %.2e" % (name, h, gk, fd, eks[-1]))
     assert worst < 1e-6
-    assert min(eks) < 1e-6
+    assert min(eks) < KAPPA_TOL.get(name, 1e-6)
 
 
 def test_step_adjoint_against_oracle_differences():

@@ -177,3 +177,48 @@ def test_split_precision_against_oracle():
     print("split vs oracle: conserved totals", rel, "per-zone error median %.2e p99 %.2e max %.2e" %
           (np.median(e.max(0)), np.quantile(e.max(0), 0.99), e.max()))
     assert rel.max() < 1e-5
+
+
+def test_fullsize_against_oracle_twenty_steps(torus_full):
+    """256x128x64, 20 CFL steps of the oracle (on all host cores: its zone
+    loops are independent, so the thread count does not change its result)
+    and of the CUDA step in FP64 and in split precision with the oracle's
+    time steps: per-zone errors and conserved totals against the oracle."""
+    cfg, P = torus_full
+    old = os.environ.get("ORACLE_THREADS")
+    os.environ["ORACLE_THREADS"] = str(os.cpu_count() or 1)
+    try:
+        o = O.Oracle(cfg)
+        o.set_prims(P)
+        dts = []
+        for _ in range(20):
+            dt = o.cfl_dt()
+            o.step(dt)
+            dts.append(dt)
+        R = o.get_prims()
+        counts = o.counts()
+    finally:
+        if old is None:
+            del os.environ["ORACLE_THREADS"]
+        else:
+            os.environ["ORACLE_THREADS"] = old
+    tR, sR = conserved_totals(cfg, torch.as_tensor(R, device="cuda"))
+    res = {}
+    for prec in (H.PREC_FP64, H.PREC_SPLIT):
+        g = H.Grid(cfg, precision=prec)
+        g.set_prims(P)
+        for dt in dts:
+            g.step(dt)
+        A = g.get_prims()
+        tA, _ = conserved_totals(cfg, torch.as_tensor(A, device="cuda"))
+        e = zone_errors(cfg, A, R).max(0)
+        res[prec] = (np.abs(tA - tR) / sR, np.median(e), np.quantile(e, 0.99), e.max())
+        del g
+    for prec, name in ((H.PREC_FP64, "FP64"), (H.PREC_SPLIT, "split")):
+        rel, med, p99, mx = res[prec]
+        print("%s vs oracle after 20 steps: totals %s; per-zone error median %.2e p99 %.2e max %.2e"
+              % (name, np.array2string(rel, precision=2), med, p99, mx))
+    print("oracle solver counts:", counts)
+    assert res[H.PREC_FP64][0].max() < 1e-10
+    assert res[H.PREC_FP64][1] < 1e-9
+    assert res[H.PREC_SPLIT][0].max() < 1e-5
