@@ -54,8 +54,9 @@ extern "C" {
 
 /* boundary conditions (bc[2*d] lower, bc[2*d+1] upper face of direction d) */
 #define HARMRAD_BC_PERIODIC 0
-#define HARMRAD_BC_OUTFLOW 1
+#define HARMRAD_BC_OUTFLOW 1   /* copy the edge zone; the normal velocities may not point inward */
 #define HARMRAD_BC_POLAR 2     /* theta direction of the Kerr-Schild grid only */
+#define HARMRAD_BC_COPY 3      /* copy the edge zone (zero gradient), inflow allowed (shock tubes) */
 
 #define HARMRAD_METRIC_MINKOWSKI 0
 #define HARMRAD_METRIC_KS 1
@@ -286,6 +287,9 @@ typedef struct harmrad_tuning {
   int face_block, face_blocks_per_sm;      /* face physics + Riemann; block 32..128 */
   int update_block, update_blocks_per_sm;  /* update + implicit solve; block 32..128 */
   int edge_block, edge_blocks_per_sm;      /* reconstruction; block 32..256 */
+  int newton_split;  /* PMHD iterations the update kernel runs before a zone moves to the
+                        compacted continuation queue (0: none, the zone finishes in place);
+                        1..60.  The resumed iteration is the same arithmetic. */
   double face_ms, update_ms, edge_ms;      /* autotune: best device ms per step */
 } harmrad_tuning;
 
@@ -294,7 +298,7 @@ typedef struct harmrad_tuning {
  * context's stream, keep the fastest per kernel class, restore the primitives
  * and drop the captured graphs (the next step re-captures).  Candidates:
  * blocks of 64 or 128 threads (edges 128 or 256) with caps of 4..64 blocks per
- * SM.  Writes the chosen shapes to *out (may be NULL).  Synchronises; allocates
+ * SM, and Newton splits of 0 (no continuation queue), 3 and 5.  Writes the chosen shapes to *out (may be NULL).  Synchronises; allocates
  * a scratch copy of the primitives for the duration of the call. */
 int harmrad_autotune(harmrad_ctx* ctx, int reps, harmrad_tuning* out);
 

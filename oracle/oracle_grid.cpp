@@ -99,9 +99,9 @@ void fill_ghosts(Ctx& c, std::vector<double>& P) {
               int clamp = 0;
               if (bc == 0) {
                 src[d] = side == 0 ? c.n[d] - 1 - g : g;
-              } else if (bc == 1) {
+              } else if (bc == 1 || bc == 3) {
                 src[d] = side == 0 ? 0 : c.n[d] - 1;
-                clamp = side == 0 ? -1 : 1;
+                clamp = bc == 3 ? 0 : (side == 0 ? -1 : 1);
               } else {
                 src[d] = side == 0 ? g : c.n[d] - 1 - g;
                 if (c.n[2] > 1) src[2] = (k + c.n[2] / 2) % c.n[2];

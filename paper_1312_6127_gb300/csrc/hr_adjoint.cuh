@@ -698,9 +698,9 @@ static __global__ void ka_bc_T(BoxGeo bx, const double* __restrict__ P, double* 
     int clamp = 0;
     if (bc == 0) {
       src[d] = side == 0 ? bx.n[d] - 1 - g : g;
-    } else if (bc == 1) {
+    } else if (bc == 1 || bc == 3) {
       src[d] = side == 0 ? 0 : bx.n[d] - 1;
-      clamp = side == 0 ? -1 : 1;
+      clamp = bc == 3 ? 0 : (side == 0 ? -1 : 1);
     } else {
       src[d] = side == 0 ? g : bx.n[d] - 1 - g;
       if (bx.n[2] > 1) src[2] = (c[2] + bx.n[2] / 2) % bx.n[2];

@@ -164,7 +164,7 @@ int fill_geometry(const harmrad_params* p, BoxGeo& b) {
   b.str[2] = (long long)b.N[0] * b.N[1];
   for (int s = 0; s < 6; ++s) {
     int bc = p->bc[s];
-    if (bc < 0 || bc > 2) return HARMRAD_E_ARG;
+    if (bc < 0 || bc > 3) return HARMRAD_E_ARG;
     if (bc == 2 && (s / 2 != 1 || p->metric != 1)) return HARMRAD_E_ARG;
     b.bc[s] = bc;
   }
@@ -261,13 +261,14 @@ harmrad_tuning default_tuning() {
   t.update_blocks_per_sm = 16;
   t.edge_block = 256;
   t.edge_blocks_per_sm = 16;
+  t.newton_split = 0;
   return t;
 }
 
 bool tuning_ok(const harmrad_tuning& t) {
   auto ok = [](int b, int cap, int bmax) { return b >= 32 && b <= bmax && b % 32 == 0 && cap >= 1 && cap <= 64; };
   return ok(t.face_block, t.face_blocks_per_sm, 128) && ok(t.update_block, t.update_blocks_per_sm, 128) &&
-         ok(t.edge_block, t.edge_blocks_per_sm, 256);
+         ok(t.edge_block, t.edge_blocks_per_sm, 256) && t.newton_split >= 0 && t.newton_split <= 60;
 }
 
 void drop_graphs(harmrad_ctx* c) {
@@ -360,6 +361,7 @@ int create(const harmrad_params* p, int count, void* stream, harmrad_ctx** out) 
   c->real_size = p[0].precision == HARMRAD_PREC_SPLIT ? 4 : 8;
   c->use_graph = getenv("HARMRAD_NO_GRAPH") == nullptr;
   c->tune = default_tuning();
+  if (count > 1) c->tune.newton_split = 3;  // batches: heavy-tailed Newton counts expected
   if (cudaGetDevice(&c->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
     cudaGetLastError();
@@ -783,14 +785,17 @@ int harmrad_autotune(harmrad_ctx* c, int reps, harmrad_tuning* out) {
   if (!c->has_prims) return HARMRAD_E_STATE;
   if (reps < 1) reps = 1;
   struct Shape {
-    int block, cap;
+    int block, cap, split;
   };
   // candidate i pairs the i-th shape of each class; the classes are timed
   // separately within the same step
-  const Shape fc[] = {{128, 16}, {64, 16}, {128, 8}, {128, 32}, {64, 32}, {128, 64}, {128, 4}};
-  const Shape uc[] = {{128, 16}, {64, 16}, {128, 8}, {128, 32}, {64, 32}, {128, 64}, {64, 64}};
-  const Shape ec[] = {{256, 16}, {128, 16}, {256, 8}, {256, 32}, {128, 32}, {256, 64}, {128, 64}};
-  const int ncand = 7;
+  const Shape fc[] = {{128, 16, 0}, {64, 16, 0}, {128, 8, 0}, {128, 32, 0}, {64, 32, 0},
+                      {128, 64, 0}, {128, 4, 0}, {128, 32, 0}, {64, 64, 0}};
+  const Shape uc[] = {{128, 16, 0}, {64, 16, 3}, {128, 8, 5}, {128, 32, 0}, {64, 32, 3},
+                      {128, 64, 3}, {64, 64, 0}, {128, 32, 3}, {128, 32, 5}};
+  const Shape ec[] = {{256, 16, 0}, {128, 16, 0}, {256, 8, 0}, {256, 32, 0}, {128, 32, 0},
+                      {256, 64, 0}, {128, 64, 0}, {256, 32, 0}, {128, 8, 0}};
+  const int ncand = 9;
   const size_t bytes = 12 * (size_t)c->ncell * sizeof(double);
   double* save = nullptr;
   if (cudaMalloc((void**)&save, bytes) != cudaSuccess) {
@@ -810,6 +815,7 @@ int harmrad_autotune(harmrad_ctx* c, int reps, harmrad_tuning* out) {
       t.face_blocks_per_sm = fc[i].cap;
       t.update_block = uc[i].block;
       t.update_blocks_per_sm = uc[i].cap;
+      t.newton_split = uc[i].split;
       t.edge_block = ec[i].block;
       t.edge_blocks_per_sm = ec[i].cap;
     }
@@ -831,6 +837,7 @@ int harmrad_autotune(harmrad_ctx* c, int reps, harmrad_tuning* out) {
       best.update_ms = kt.ms[HARMRAD_K_UPDATE];
       best.update_block = t.update_block;
       best.update_blocks_per_sm = t.update_blocks_per_sm;
+      best.newton_split = t.newton_split;
     }
     if (kt.ms[HARMRAD_K_EDGE] < best.edge_ms) {
       best.edge_ms = kt.ms[HARMRAD_K_EDGE];

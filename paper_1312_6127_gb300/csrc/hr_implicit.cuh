@@ -278,7 +278,7 @@ __device__ __forceinline__ void newton_pmhd_init(const double x0[4], NewtonState
 // best_eT hold the lowest-error iterate (best_eT = inf if no residual was
 // finite).
 template <int MET>
-__device__ bool newton_pmhd_run(const DevParams& p, const ImpSys<MET>& s, NewtonState& st, int kstop) {
+__device__ __forceinline__ bool newton_pmhd_run(const DevParams& p, const ImpSys<MET>& s, NewtonState& st, int kstop) {
   for (;; ++st.k) {
     if (st.k >= kstop) return false;
     ImpRes r;
@@ -339,17 +339,74 @@ __device__ bool newton_pmhd_run(const DevParams& p, const ImpSys<MET>& s, Newton
   return true;
 }
 
-// PMHD Newton from x0 to the end.  Returns the number of Newton steps.
+// PMHD Newton from x0 to the end (the same iterations as newton_pmhd_run
+// without a pause, in local variables).  Returns the number of Newton steps;
+// best_x / best_eT hold the lowest-error iterate (best_eT = inf if no
+// residual was finite).
 template <int MET>
 __device__ int newton_pmhd(const DevParams& p, const ImpSys<MET>& s, const double x0[4],
                            double best_x[4], double* best_eT) {
-  NewtonState st;
-  newton_pmhd_init(x0, st);
-  newton_pmhd_run<MET>(p, s, st, 1 << 30);
+  double x[4] = {x0[0], x0[1], x0[2], x0[3]};
+  Hist hs = {HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, 0};
+  *best_eT = HUGE_VAL;
+  int steps = 0;
+  double eps = 1e-8;
+  for (int k = 0;; ++k) {
+    ImpRes r;
+    pmhd_res<MET>(p, s, x, r, nullptr, true);
+    if (!r.ok) break;
+    if (r.eT < *best_eT) {
+      *best_eT = r.eT;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) best_x[i] = st.best_x[i];
-  *best_eT = st.best_eT;
-  return st.steps;
+      for (int i = 0; i < 4; ++i) best_x[i] = x[i];
+    }
+    if (r.eT < p.newton_tol) break;
+    if (stalled(hs, k, r.eT, r.eI)) break;
+    if (k >= p.newton_max) break;
+    if (r.eI < 1e-9) eps = 1e-10;
+    double umag = fmax(1.0, sqrt(s.g.sq3(x[1], x[2], x[3])));
+    double J[4][4];
+#pragma unroll 1
+    for (int j = 0; j < 4; ++j) {
+      double dj = (j == 0) ? eps * fabs(x[0]) : eps * umag / sqrt(s.g.gdd(j));
+      double xp[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) xp[i] = x[i] + (i == j ? dj : 0.0);
+      ImpRes rp;
+      pmhd_res<MET>(p, s, xp, rp, nullptr, false);
+      double id = 1.0 / dj;
+      // column j of J, written through compile-time indices
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          if (c == j) J[i][c] = (rp.Eg[i] - r.Eg[i]) * id;
+    }
+    double E[4] = {r.Eg[0], r.Eg[1], r.Eg[2], r.Eg[3]}, dx[4];
+    if (!solve4(J, E, dx)) break;
+    double xn[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) xn[i] = x[i] - dx[i];
+    if (xn[0] < 0.0) xn[0] = 0.5 * fabs(xn[0]);
+    bool tiny = true;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (fabs(xn[i] - x[i]) > 10.0 * 2.220446049250313e-16 * fabs(x[i])) tiny = false;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x[i] = xn[i];
+    ++steps;
+    if (tiny) {
+      ImpRes rf;
+      pmhd_res<MET>(p, s, x, rf, nullptr, true);
+      if (rf.ok && rf.eT < *best_eT) {
+        *best_eT = rf.eT;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) best_x[i] = x[i];
+      }
+      break;
+    }
+  }
+  return steps;
 }
 
 // URAD error function: iterate R^t_nu; gas from 1D_W inversion of

@@ -202,9 +202,9 @@ static __global__ void k_bc_fill(DevParams p, const BoxGeo* __restrict__ boxes, 
       int clamp = 0;
       if (bc == 0) {
         src[d] = side == 0 ? bx.n[d] - 1 - g : g;
-      } else if (bc == 1) {
+      } else if (bc == 1 || bc == 3) {
         src[d] = side == 0 ? 0 : bx.n[d] - 1;
-        clamp = side == 0 ? -1 : 1;
+        clamp = bc == 3 ? 0 : (side == 0 ? -1 : 1);
       } else {
         src[d] = side == 0 ? g : bx.n[d] - 1 - g;
         if (bx.n[2] > 1) src[2] = (c[2] + bx.n[2] / 2) % bx.n[2];
@@ -971,10 +971,6 @@ __device__ __forceinline__ void cons_source(const DevParams& p, const Geo<MET, T
   (void)x2;
 }
 
-// Newton iterations the update kernel runs before it hands a zone to the
-// continuation queue (most zones of the torus end within 2 steps, i.e. 3
-// iterations counting the final residual check).
-constexpr int NEWTON_SPLIT = 3;
 constexpr int CSTRIDE = NPR + 21;  // continuation queue record: U*, Newton state
 
 __device__ __forceinline__ void newton_state_store(const NewtonState& st, double* d) {
@@ -1022,15 +1018,14 @@ __device__ __forceinline__ void newton_state_load(const double* d, NewtonState& 
 template <int MET>
 __device__ __forceinline__ bool pmhd_finish(const DevParams& p, const BoxGeo& bx, int bi, long long z, long long t,
                                             double x1, const Geo<MET, double>& g, const ImpSys<MET>& s,
-                                            const double Ust[NPR], double h, const NewtonState& ns, double* P,
-                                            const Bufs& b) {
+                                            const double Ust[NPR], double h, const double best_x[4],
+                                            double beT, int steps, double* P, const Bufs& b) {
   const long long zg = bx.aoff + z;
-  b.iters[zg] += ns.steps;
-  const double beT = ns.best_eT;
+  b.iters[zg] += steps;
   const bool accept = beT < 1e-9;
   if (accept) {
     double Pn[NPR];
-    pmhd_final<MET>(p, s, ns.best_x, Pn);
+    pmhd_final<MET>(p, s, best_x, Pn);
     if (b.psol_rec)
       for (int q = 0; q < NPR; ++q) b.psol_rec[q * bx.nact + z] = Pn[q];
     apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn);
@@ -1044,7 +1039,7 @@ __device__ __forceinline__ bool pmhd_finish(const DevParams& p, const BoxGeo& bx
     double* qd = b.qdata + (long long)slot * QSTRIDE;
 #pragma unroll
     for (int q = 0; q < NPR; ++q) qd[q] = Ust[q];
-    for (int q = 0; q < 4; ++q) qd[12 + q] = isfinite(beT) ? ns.best_x[q] : 0.0;
+    for (int q = 0; q < 4; ++q) qd[12 + q] = isfinite(beT) ? best_x[q] : 0.0;
     qd[16] = beT;
     qd[17] = h;
   }
@@ -1059,9 +1054,9 @@ __device__ __forceinline__ bool pmhd_finish(const DevParams& p, const BoxGeo& bx
 // update X = -sum_d dF_d/dx_d + SM, the RK3 combination
 // U* = a_s U^n + b_s (U(P_s) + dt X) (Sec. 4.1), the PMHD Newton solve, floors.
 // Zones whose PMHD error exceeds 1e-9 go to the retry queue.
-template <int MET, typename R>
+template <int MET, typename R, bool CONT>
 __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx, int bi, const Bufs& b,
-                                           int stage) {
+                                           int stage, int split) {
   const double A = stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0);
   const double Bc = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
   {
@@ -1147,33 +1142,41 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
           }
         }
       }
-      NewtonState ns;
-      newton_pmhd_init(x0, ns);
-      // the first NEWTON_SPLIT iterations here; a zone that needs more
-      // continues in the compacted queue (k_newton_cont), so that the
-      // heavy tail of iteration counts runs in full warps
-      const bool done = newton_pmhd_run<MET>(p, s, ns, NEWTON_SPLIT);
       bool accept = false;
-      if (done) {
-        accept = pmhd_finish<MET>(p, bx, bi, z, t, x1, g, s, Ust, h, ns, P, b);
+      unsigned done_steps = 0;
+      if constexpr (!CONT) {
+        double bxn[4], beT;
+        const int steps = newton_pmhd<MET>(p, s, x0, bxn, &beT);
+        accept = pmhd_finish<MET>(p, bx, bi, z, t, x1, g, s, Ust, h, bxn, beT, steps, P, b);
+        done_steps = (unsigned)steps;
       } else {
-        const int slot = atomicAdd(&b.qcount[2], 1);
-        b.czone[slot] = (int)z;
-        b.cbox[slot] = bi;
-        double* cd = b.cdata + (long long)slot * CSTRIDE;
+        // the first `split` iterations here; a zone that needs more
+        // continues in the compacted queue (k_newton_cont), so that the
+        // heavy tail of iteration counts runs in full warps
+        NewtonState ns;
+        newton_pmhd_init(x0, ns);
+        if (newton_pmhd_run<MET>(p, s, ns, split)) {
+          accept = pmhd_finish<MET>(p, bx, bi, z, t, x1, g, s, Ust, h, ns.best_x, ns.best_eT, ns.steps, P, b);
+          done_steps = (unsigned)ns.steps;
+        } else {
+          const int slot = atomicAdd(&b.qcount[2], 1);
+          b.czone[slot] = (int)z;
+          b.cbox[slot] = bi;
+          double* cd = b.cdata + (long long)slot * CSTRIDE;
 #pragma unroll
-        for (int q = 0; q < NPR; ++q) cd[q] = Ust[q];
-        newton_state_store(ns, cd + NPR);
+          for (int q = 0; q < NPR; ++q) cd[q] = Ust[q];
+          newton_state_store(ns, cd + NPR);
+        }
       }
       warp_add(&b.stats[ST_PMHD], accept ? 1u : 0u);
-      warp_add(&b.stats[ST_ITERS], done ? (unsigned)ns.steps : 0u);
+      warp_add(&b.stats[ST_ITERS], done_steps);
       warp_add(&b.stats[ST_SOLVES], 1u);
     }
   }
 }
 
-// Zones whose PMHD Newton iteration did not end within NEWTON_SPLIT
-// iterations of the update kernel: a persistent grid over the compacted queue
+// Zones whose PMHD Newton iteration did not end within the update kernel's
+// `split` iterations: a persistent grid over the compacted queue
 // resumes each iteration from its saved state (same arithmetic as an
 // uninterrupted iteration) and finishes the zone as the update kernel would.
 template <int MET>
@@ -1202,7 +1205,8 @@ __global__ void __launch_bounds__(128) k_newton_cont(DevParams p, const BoxGeo* 
     ImpSys<MET> s;
     build_sys<MET>(p, g, Ust, h, kfield(p, b.K + bx.coff, t), s);
     newton_pmhd_run<MET>(p, s, ns, 1 << 30);
-    const bool accept = pmhd_finish<MET>(p, bx, bi, z, t, x1, g, s, Ust, h, ns, b.P + 12 * bx.coff, b);
+    const bool accept =
+        pmhd_finish<MET>(p, bx, bi, z, t, x1, g, s, Ust, h, ns.best_x, ns.best_eT, ns.steps, b.P + 12 * bx.coff, b);
     if (accept) atomicAdd(&b.stats[ST_PMHD], 1ULL);
     atomicAdd(&b.stats[ST_ITERS], (unsigned long long)ns.steps);
   }
@@ -1210,14 +1214,16 @@ __global__ void __launch_bounds__(128) k_newton_cont(DevParams p, const BoxGeo* 
 
 // ONE: a single grid whose geometry travels in the kernel's parameter space
 // (no registers held for it across the Newton solve); otherwise the boxes of
-// a batch, read from the device table.
-template <int MET, typename R, bool ONE>
+// a batch, read from the device table.  CONT: PMHD iterations beyond `split`
+// continue in k_newton_cont (the queue costs registers; it pays where the
+// iteration counts are heavy-tailed, which the autotuner measures).
+template <int MET, typename R, bool ONE, bool CONT>
 __global__ void __launch_bounds__(128) k_update(DevParams p, BoxGeo one, const BoxGeo* __restrict__ boxes,
-                                                int nbox, Bufs b, int stage) {
+                                                int nbox, Bufs b, int stage, int split) {
   if constexpr (ONE) {
-    update_box<MET, R>(p, one, 0, b, stage);
+    update_box<MET, R, CONT>(p, one, 0, b, stage, split);
   } else {
-    for (int bi = 0; bi < nbox; ++bi) update_box<MET, R>(p, boxes[bi], bi, b, stage);
+    for (int bi = 0; bi < nbox; ++bi) update_box<MET, R, CONT>(p, boxes[bi], bi, b, stage, split);
   }
 }
 

@@ -202,15 +202,25 @@ int solve_impl(harmrad_ctx* c, int stage) {
   Bufs b = make_bufs(c);
   const int bu = c->tune.update_block;
   const int gu = grid_for(c->maxact, c->sms, bu, c->tune.update_blocks_per_sm);
-  if (c->nbox == 1)
-    k_update<MET, R, true><<<gu, bu, 0, st>>>(p, c->boxes[0], c->dboxes, 1, b, stage);
+  const int split = c->tune.newton_split;
+  const bool one = c->nbox == 1;
+  if (one && split == 0)
+    k_update<MET, R, true, false><<<gu, bu, 0, st>>>(p, c->boxes[0], c->dboxes, 1, b, stage, 0);
+  else if (one)
+    k_update<MET, R, true, true><<<gu, bu, 0, st>>>(p, c->boxes[0], c->dboxes, 1, b, stage, split);
+  else if (split == 0)
+    k_update<MET, R, false, false><<<gu, bu, 0, st>>>(p, c->boxes[0], c->dboxes, c->nbox, b, stage, 0);
   else
-    k_update<MET, R, false><<<gu, bu, 0, st>>>(p, c->boxes[0], c->dboxes, c->nbox, b, stage);
+    k_update<MET, R, false, true><<<gu, bu, 0, st>>>(p, c->boxes[0], c->dboxes, c->nbox, b, stage, split);
   mark(c, HARMRAD_K_UPDATE);
-  // the continuation queue, the retry queue and the back-up list are short:
-  // one persistent wave of blocks each
-  k_newton_cont<MET><<<c->sms * 2, 128, 0, st>>>(p, c->dboxes, b, stage);
-  mark(c, HARMRAD_K_UPDATE);
+  int nk = 4;
+  if (split > 0) {
+    // the continuation queue, the retry queue and the back-up list are
+    // short: one persistent wave of blocks each
+    k_newton_cont<MET><<<c->sms * 2, 128, 0, st>>>(p, c->dboxes, b, stage);
+    mark(c, HARMRAD_K_UPDATE);
+    ++nk;
+  }
   k_retry<MET><<<c->sms * 2, 128, 0, st>>>(p, c->dboxes, b);
   mark(c, HARMRAD_K_RETRY);
   k_backup_avg<<<c->sms, 128, 0, st>>>(p, c->dboxes, b);
@@ -218,7 +228,7 @@ int solve_impl(harmrad_ctx* c, int stage) {
   k_backup_apply<MET><<<c->sms, 128, 0, st>>>(p, c->dboxes, b);
   mark(c, HARMRAD_K_BACKUP);
   if (cudaGetLastError() != cudaSuccess) return HARMRAD_E_CUDA;
-  return 5;
+  return nk;
 }
 
 // --------------------------------------------------- point-wise entry kernels

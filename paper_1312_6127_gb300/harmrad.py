@@ -90,6 +90,7 @@ class Tuning(ctypes.Structure):
         ("face_block", ctypes.c_int), ("face_blocks_per_sm", ctypes.c_int),
         ("update_block", ctypes.c_int), ("update_blocks_per_sm", ctypes.c_int),
         ("edge_block", ctypes.c_int), ("edge_blocks_per_sm", ctypes.c_int),
+        ("newton_split", ctypes.c_int),
         ("face_ms", ctypes.c_double), ("update_ms", ctypes.c_double), ("edge_ms", ctypes.c_double),
     ]
 

@@ -22,7 +22,7 @@ import numpy as np
 
 NP = 12
 RHO, UU, U1, U2, U3, B1, B2, B3, ER, UR1, UR2, UR3 = range(12)
-PERIODIC, OUTFLOW, POLAR = 0, 1, 2
+PERIODIC, OUTFLOW, POLAR, COPY = 0, 1, 2, 3
 PPM, MC = 0, 1
 LAXF, HLL = 0, 1
 OPAC_CONST, OPAC_KRAMERS, OPAC_FIELD = 0, 1, 2
@@ -355,6 +355,32 @@ def thin_pulse(n=(32, 32, 32), L=100.0, w=5.0, T_a=1e6):
     P[UU] = Tg / (cfg["gam"] - 1.0)
     Trad = Tg * (1.0 + 100.0 * np.exp(-R2 / w ** 2))
     P[ER] = cfg["a_rad"] * Trad ** 4
+    return cfg, P
+
+
+def shock_tube(state, n1=800, xlim=(-20.0, 20.0), recon=PPM, flux=LAXF):
+    """1D radiative shock tube (Sec. 5, HD radiative shocks): the left and
+    right states (rho0, p_g, u^x, Ehat) of ``state`` (keys L, R, gam, sigma,
+    kappa) on either side of x = 0, LTE radiation moving with the gas (u~_rad
+    = u~, Ebar = Ehat), a_rad = 4 sigma, absorption opacity kappa rho0, no
+    scattering, zero-gradient ends with inflow allowed."""
+    cfg = base_params()
+    gam = float(state["gam"])
+    x0, x1 = xlim
+    dx = (x1 - x0) / n1
+    cfg.update(n=[n1, 1, 1], x0=[x0, 0.0, 0.0], dx=[dx, 1.0, 1.0], gam=gam,
+               a_rad=4.0 * float(state["sigma"]), opacity=OPAC_CONST, kappa_abs0=float(state["kappa"]),
+               kappa_es0=0.0, recon=recon, flux=flux, bc=[COPY, COPY] + [PERIODIC] * 4,
+               floor_rho0=1e-12, floor_u0=1e-14)
+    x = x0 + (np.arange(n1) + 0.5) * dx
+    P = np.zeros((NP, 1, 1, n1))
+    for side, sel in (("L", x < 0.0), ("R", x >= 0.0)):
+        rho, pg, ux, E = (float(v) for v in state[side])
+        P[RHO][..., sel] = rho
+        P[UU][..., sel] = pg / (gam - 1.0)
+        P[U1][..., sel] = ux
+        P[ER][..., sel] = E
+        P[UR1][..., sel] = ux
     return cfg, P
 
 

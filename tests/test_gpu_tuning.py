@@ -1,11 +1,17 @@
 """Launch-shape autotuner: the chosen shapes come from the candidate set, the
 call leaves the state unchanged, and steps under any shape give the same
-bytes as the default shapes (every zone runs the same arithmetic)."""
+bytes as the default shapes (every zone runs the same arithmetic); a Newton
+split that moves most zones' iterations to the continuation queue gives the
+same result within the Newton tolerance (the resumed iteration repeats the
+same operations, compiled in another kernel, so round-off can end an
+iteration one step earlier or later: both iterates solve the implicit
+equations to e_T < 1e-12)."""
 import numpy as np
 import pytest
 
 from paper_1312_6127_gb300 import harmrad as H
 from paper_1312_6127_gb300 import workloads as W
+from tests.parity_metrics import zone_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -17,12 +23,13 @@ def test_autotune_keeps_state_and_results():
     t = a.autotune(reps=1)
     assert t["face_block"] in (64, 128) and t["update_block"] in (64, 128)
     assert t["edge_block"] in (128, 256)
+    assert t["newton_split"] in (0, 3, 5)
     assert t["face_ms"] > 0 and t["update_ms"] > 0 and t["edge_ms"] > 0
     assert np.array_equal(a.get_prims(), P)
     b = H.Grid(cfg)
     b.set_prims(P)
     b.set_tuning(face_block=64, face_blocks_per_sm=3, update_block=32, update_blocks_per_sm=5,
-                 edge_block=96, edge_blocks_per_sm=7)
+                 edge_block=96, edge_blocks_per_sm=7, newton_split=1)
     c = H.Grid(cfg)
     c.set_prims(P)
     for _ in range(2):
@@ -30,8 +37,17 @@ def test_autotune_keeps_state_and_results():
         b.step(0.0)
         c.step(0.0)
     A, B, C = a.get_prims(), b.get_prims(), c.get_prims()
-    assert np.array_equal(A, C)
-    assert np.array_equal(B, C)
+    # launch shapes alone change no byte; with a Newton split the iterations
+    # past the split run in another kernel, whose multiply-add fusion the
+    # compiler may choose differently: agreement within the Newton tolerance,
+    # in the per-zone parity measure
+    if t["newton_split"] == 0:
+        assert np.array_equal(A, C)
+    else:
+        assert zone_errors(cfg, A, C).max() < 1e-10
+    e = zone_errors(cfg, B, C)
+    print("newton_split 1 against none: max zone error %.2e" % e.max())
+    assert e.max() < 1e-10
 
 
 def test_set_tuning_rejects_bad_shapes():
@@ -43,3 +59,5 @@ def test_set_tuning_rejects_bad_shapes():
         g.set_tuning(update_block=48)
     with pytest.raises(H.HarmradError):
         g.set_tuning(edge_blocks_per_sm=0)
+    with pytest.raises(H.HarmradError):
+        g.set_tuning(newton_split=-1)
