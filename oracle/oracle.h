@@ -22,7 +22,10 @@
  * closure identities, exact scalar roots, conservation) and by
  * tests/test_oracle_waves.py (the linear-wave eigenvalues the paper prints in
  * its Table t.waves: wave speed and radiative damping of sound, fast and slow
- * modes, optically thin and thick, gas- and radiation-dominated).  Parity unpinned:
+ * modes, optically thin and thick, gas- and radiation-dominated), by
+ * tests/test_oracle_shocks.py (the jump conditions of the radiative shock-tube
+ * states of Table t.radtube) and by tests/test_oracle_imex.py (the orders of
+ * accuracy of the IMEX integrators on stiff relaxation).  Parity unpinned:
  * the PPM shock flattener (its constants beyond SP0 = 0.75 are not in the
  * paper), the polar-axis ghost rule and the floor procedure are readings of
  * the paper that only oracle-versus-library agreement checks.
@@ -38,7 +41,8 @@ typedef struct {
   double x0[3], dx[3];    /* uniform internal coordinates of the lower edge */
   int metric;             /* 0 Minkowski Cartesian, 1 Kerr-Schild + MSP map */
   double a_spin, R0, hslope;
-  int bc[6];              /* lower/upper per direction: 0 periodic, 1 outflow, 2 polar */
+  int bc[6];              /* lower/upper per direction: 0 periodic, 1 outflow, 2 polar,
+                             3 zero gradient with inflow allowed */
   double gam, a_rad, courant;
   int opacity;            /* 0 kappa = k0*rho (per length), 1 Kramers k0*rho^2*T^-3.5,
                              2 per-zone field K (orc_set_opacity_field), kappa = K */
@@ -50,6 +54,9 @@ typedef struct {
   double bsq_rho_max, bsq_u_max, u_rho_max;
   int newton_max;
   double newton_tol;
+  int integrator;         /* 0 RK3 with the same coefficients for the explicit and
+                             implicit parts (the paper's runs), 1 IMEX2, 2 IMEX2B,
+                             3 IMEX3 (Sec. 4.1, Eqs. IMEX2, IMEX2B, IMEX3) */
 } orc_params;
 
 /* Per-zone solver outcome codes (same meaning as the library's status byte). */

@@ -52,6 +52,7 @@ class OrcParams(ctypes.Structure):
         ("u_rho_max", ctypes.c_double),
         ("newton_max", ctypes.c_int),
         ("newton_tol", ctypes.c_double),
+        ("integrator", ctypes.c_int),
     ]
 
 

@@ -2,7 +2,9 @@
 //
 // One full time step as restated from Sec. 4 of McKinney et al. (2014):
 // the RK3 method with the same coefficients for the explicit and implicit
-// parts (Sec. 4.1), each sub-step running the algorithm of Sec. 4.2 --
+// parts (Sec. 4.1; the paper's runs), or one of the IMEX schemes IMEX2,
+// IMEX2B, IMEX3 it prints in the same section; each sub-step runs the
+// algorithm of Sec. 4.2 --
 // ghost fill, U(P), geometric source, reconstruction (Sec. 4.3), face fluxes
 // and wave speeds (Sec. 4.4), HLL/LAXF (Eqs. hll, lax), flux-CT EMFs, the
 // update and the implicit solve with back-ups (Sec. 4.7-4.11).  Plain loops,
@@ -45,6 +47,7 @@ struct Ctx {
   std::vector<unsigned char> status;  // active zones
   std::vector<int> iters;             // active zones
   long long counts[5];
+  std::vector<double> M[4];  // IMEX: implicit source of stage j, gas rows [4][ntot]
 };
 
 inline long idx(const Ctx& c, int i, int j, int k) {
@@ -468,14 +471,115 @@ double cfl_dt(Ctx& c) {
   return cfl_from_speeds(c);
 }
 
-// One RK sub-step s (Sec. 4.1-4.2).
+// Stage k of an IMEX scheme of Sec. 4.1 in the paper's bracket form: the
+// explicit part U* = an U^n + ap U(P) + d dt F(P) + dt sum_j c_j M^j, with P
+// the primitives the previous stage left and F the explicit right-hand side
+// (flux divergence and geometric source) at P, then the implicit stage
+// U = U* + g dt M(U); the final combination has g = 0 (the conserved state is
+// only inverted).  M^j is the implicit source of stage j: +G on the gas
+// energy-momentum rows, -G on the radiation rows.
+struct Pass {
+  double an, ap, d, c[4], g;
+};
+
+int n_passes(int integrator) {
+  static const int n[4] = {3, 3, 4, 5};
+  return n[integrator];
+}
+
+Pass imex_pass(int integrator, int k) {
+  Pass s = {0.0, 0.0, 0.0, {0.0, 0.0, 0.0, 0.0}, 0.0};
+  if (integrator == 1) {
+    // IMEX2, gamma = 1 - 1/sqrt(2)
+    const double ga = 1.0 - 1.0 / std::sqrt(2.0);
+    if (k == 0) {  // U^0 = [U^n] + gamma dt M^0
+      s.an = 1.0;
+      s.g = ga;
+    } else if (k == 1) {  // U^1 = [(3gamma-1)/gamma U^n + (1-2gamma)/gamma U^0 + dt F^0] + gamma dt M^1
+      s.an = (3.0 * ga - 1.0) / ga;
+      s.ap = (1.0 - 2.0 * ga) / ga;
+      s.d = 1.0;
+      s.g = ga;
+    } else {  // U^{n+1} = [U^n/2 + U^1/2 + dt/2 F^1 + gamma dt M^0 + (1-gamma)/2 dt M^1]
+      s.an = 0.5;
+      s.ap = 0.5;
+      s.d = 0.5;
+      s.c[0] = ga;
+      s.c[1] = 0.5 * (1.0 - ga);
+    }
+  } else if (integrator == 2) {
+    // IMEX2B
+    if (k == 0) {  // U^0 = [U^n] + dt/4 M^0
+      s.an = 1.0;
+      s.g = 0.25;
+    } else if (k == 1) {  // U^1 = [U^n + dt/2 F^0] + dt/4 M^1
+      s.an = 1.0;
+      s.d = 0.5;
+      s.g = 0.25;
+    } else if (k == 2) {  // U^2 = [U^1 + dt/2 F^1 + dt/3 M^0 + dt/12 M^1] + dt/3 M^2
+      s.ap = 1.0;
+      s.d = 0.5;
+      s.c[0] = 1.0 / 3.0;
+      s.c[1] = 1.0 / 12.0;
+      s.g = 1.0 / 3.0;
+    } else {  // U^{n+1} = [U^n/3 + 2U^2/3 + dt/3 F^2 + dt/9 (M^0 + M^1 + M^2)]
+      s.an = 1.0 / 3.0;
+      s.ap = 2.0 / 3.0;
+      s.d = 1.0 / 3.0;
+      s.c[0] = s.c[1] = s.c[2] = 1.0 / 9.0;
+    }
+  } else if (integrator == 3) {
+    // IMEX3 with the printed alpha, beta, eta
+    const double al = 0.24169426078821, be = 0.06042356519705, et = 0.12915286960590;
+    if (k == 0) {  // U^0 = [U^n] + alpha dt M^0
+      s.an = 1.0;
+      s.g = al;
+    } else if (k == 1) {  // U^1 = [2U^n - U^0] + alpha dt M^1
+      s.an = 2.0;
+      s.ap = -1.0;
+      s.g = al;
+    } else if (k == 2) {  // U^2 = [U^n + dt F^1 + (1-alpha) dt M^1] + alpha dt M^2
+      s.an = 1.0;
+      s.d = 1.0;
+      s.c[1] = 1.0 - al;
+      s.g = al;
+    } else if (k == 3) {  // U^3 = [3U^n/4 + U^2/4 + dt/4 F^2 + beta dt M^0
+                          //        + (-1+alpha+4eta)/4 dt M^1 + (2-5alpha-4(beta+eta))/4 dt M^2] + alpha dt M^3
+      s.an = 0.75;
+      s.ap = 0.25;
+      s.d = 0.25;
+      s.c[0] = be;
+      s.c[1] = (-1.0 + al + 4.0 * et) / 4.0;
+      s.c[2] = (2.0 - 5.0 * al - 4.0 * (be + et)) / 4.0;
+      s.g = al;
+    } else {  // U^{n+1} = [U^n/3 + 2U^3/3 + 2dt/3 F^3 - 2beta/3 dt M^0 + (1-4eta)/6 dt M^1
+              //            + (-1+4alpha+4(beta+eta))/6 dt M^2 + 4(1-alpha)/6 dt M^3]
+      s.an = 1.0 / 3.0;
+      s.ap = 2.0 / 3.0;
+      s.d = 2.0 / 3.0;
+      s.c[0] = -2.0 * be / 3.0;
+      s.c[1] = (1.0 - 4.0 * et) / 6.0;
+      s.c[2] = (-1.0 + 4.0 * al + 4.0 * (be + et)) / 6.0;
+      s.c[3] = 4.0 * (1.0 - al) / 6.0;
+    }
+  }
+  return s;
+}
+
+// One sub-step s (Sec. 4.1-4.2): an RK3 stage, or stage s of an IMEX scheme.
 void substep(Ctx& c, int s, double dt) {
   static const double A[3] = {0.0, 0.75, 1.0 / 3.0};
   static const double Bc[3] = {1.0, 0.25, 2.0 / 3.0};
-  fill_ghosts(c, c.P);
-  for (int d = 0; d < 3; ++d)
-    if (c.n[d] > 1) compute_fluxes(c, d, c.p.recon == 0);
-  flux_ct(c);
+  const bool imex = c.p.integrator != 0;
+  const Pass ps = imex_pass(c.p.integrator, s);
+  // an IMEX stage without an explicit right-hand side needs no fluxes
+  const bool rhs = !imex || ps.d != 0.0;
+  if (rhs) {
+    fill_ghosts(c, c.P);
+    for (int d = 0; d < 3; ++d)
+      if (c.n[d] > 1) compute_fluxes(c, d, c.p.recon == 0);
+    flux_ct(c);
+  }
   std::vector<double> Pnew((size_t)NP * c.ntot);
   std::memcpy(Pnew.data(), c.P.data(), sizeof(double) * NP * c.ntot);
   std::vector<unsigned char> failed((size_t)c.n[0] * c.n[1] * c.n[2], 0);
@@ -494,18 +598,46 @@ void substep(Ctx& c, int s, double dt) {
         if (s == 0)
           for (int q = 0; q < NP; ++q) c.Un[(long)q * c.ntot + t] = Us[q];
         for (int q = 0; q < NP; ++q) {
-          double div = 0.0;
-          for (int d = 0; d < 3; ++d) {
-            if (c.n[d] == 1) continue;
-            long st = d == 0 ? 1 : (d == 1 ? c.N[0] : (long)c.N[0] * c.N[1]);
-            div += (c.F[d][(long)q * c.ntot + t + st] - c.F[d][(long)q * c.ntot + t]) / c.p.dx[d];
+          X[q] = 0.0;
+          if (rhs) {
+            double div = 0.0;
+            for (int d = 0; d < 3; ++d) {
+              if (c.n[d] == 1) continue;
+              long st = d == 0 ? 1 : (d == 1 ? c.N[0] : (long)c.N[0] * c.N[1]);
+              div += (c.F[d][(long)q * c.ntot + t + st] - c.F[d][(long)q * c.ntot + t]) / c.p.dx[d];
+            }
+            X[q] = -div + SM[q];
           }
-          X[q] = -div + SM[q];
-          Ust[q] = A[s] * c.Un[(long)q * c.ntot + t] + Bc[s] * (Us[q] + dt * X[q]);
+          if (!imex) {
+            Ust[q] = A[s] * c.Un[(long)q * c.ntot + t] + Bc[s] * (Us[q] + dt * X[q]);
+          } else {
+            double v = ps.an * c.Un[(long)q * c.ntot + t] + ps.ap * Us[q] + ps.d * dt * X[q];
+            // earlier stages' implicit sources: +M on the gas rows, -M on the radiation rows
+            int row = -1;
+            double sg = 0.0;
+            if (q >= UU && q <= U3) {
+              row = q - UU;
+              sg = 1.0;
+            } else if (q >= ER && q <= UR3) {
+              row = q - ER;
+              sg = -1.0;
+            }
+            if (row >= 0)
+              for (int j = 0; j < s; ++j) v += dt * ps.c[j] * sg * c.M[j][(long)row * c.ntot + t];
+            Ust[q] = v;
+          }
         }
         double Pn[NP];
         orc_implicit_info info;
-        implicit_zone(cell_params(c, t), G, Ust, Ps, Bc[s] * dt, Pn, &info);
+        const double h = imex ? ps.g * dt : Bc[s] * dt;
+        implicit_zone(cell_params(c, t), G, Ust, Ps, h, Pn, &info);
+        if (imex && ps.g > 0.0) {
+          // M^s = (U(P) - U*) / (g dt) on the gas rows, P the implicit stage's
+          // solution (the source as the change the implicit stage made)
+          double Uz[NP], SMz[NP];
+          prim_to_cons(c.p, G, Gam, Pn, Uz, SMz);
+          for (int r = 0; r < 4; ++r) c.M[s][(long)r * c.ntot + t] = (Uz[UU + r] - Ust[UU + r]) / h;
+        }
         long a = aidx(c, i, j, k);
         c.status[a] = std::max(c.status[a], (unsigned char)info.method);
         c.iters[a] += info.iters_pmhd + info.iters_urad;
@@ -596,6 +728,9 @@ void* orc_create(const orc_params* p) {
     c->spd[d].assign((size_t)c->ntot, 0.0);
     c->flat[d].assign((size_t)2 * c->ntot, 0.0);
   }
+  if (c->p.integrator < 0 || c->p.integrator > 3) c->p.integrator = 0;
+  if (c->p.integrator != 0)
+    for (int j = 0; j < 4; ++j) c->M[j].assign((size_t)4 * c->ntot, 0.0);
   c->geo.resize(c->ntot);
   c->gam.assign((size_t)c->ntot * 64, 0.0);
 #pragma omp parallel for num_threads(orc_threads()) schedule(dynamic, 1)
@@ -661,7 +796,7 @@ double orc_step(void* ctx, double dt) {
   std::fill(c.iters.begin(), c.iters.end(), 0);
   std::fill(c.status.begin(), c.status.end(), 0);
   for (int i = 0; i < 5; ++i) c.counts[i] = 0;
-  for (int s = 0; s < 3; ++s) substep(c, s, dt);
+  for (int s = 0; s < n_passes(c.p.integrator); ++s) substep(c, s, dt);
   return dt;
 }
 

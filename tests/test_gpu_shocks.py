@@ -32,6 +32,13 @@ pytestmark = pytest.mark.gpu
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "radiative_shocks.json")))
 
 
+def zone_total_flux(cfg, P12):
+    """Total x-fluxes (rest mass, energy incl. rest mass, x-momentum) of the
+    primitives of one zone, from the oracle's flux function."""
+    F, _ = O.flux(O.make_params(cfg), [0.5, 0.5, 0.5], 1, P12)
+    return np.array([F[0], F[1] + F[8], F[2] + F[9]])
+
+
 def state(name):
     st = dict(GOLD["tests"][name])
     st["gam"] = float(Fraction(st["gam"]))
@@ -47,8 +54,9 @@ def test_shock_tube_matches_oracle(name):
     o.set_prims(P)
     urad = np.zeros(P.shape[1:], dtype=bool)
     for _ in range(20):
+        # the CFL dt follows the states, which agree to the Newton tolerance
         d = o.cfl_dt()
-        assert g.cfl_dt() == pytest.approx(d, rel=1e-12)
+        assert g.cfl_dt() == pytest.approx(d, rel=1e-8)
         o.step(d)
         g.step(d)
         urad |= (o.status() != 0) | (g.status() != 0)
@@ -75,7 +83,7 @@ def test_shock_stands_still(name):
     Q = g.get_prims()
     assert np.isfinite(Q).all()
     sig = float(st["sigma"])
-    F = np.array([total_flux(st["gam"], sig, Q[:, 0, 0, i]) for i in range(Q.shape[-1])])
+    F = np.array([zone_total_flux(cfg, Q[:, 0, 0, i]) for i in range(Q.shape[-1])])
     FL = total_flux(st["gam"], sig, [float(v) for v in st["L"]])
     dev = np.abs(F - FL).max(axis=0) / np.abs(FL)
     far = np.abs(Q[:, 0, 0, :40] - P[:, 0, 0, :40]).max(axis=1)
