@@ -77,6 +77,18 @@ extern "C" {
 #define HARMRAD_PREC_FP64 0   /* every stage in FP64 */
 #define HARMRAD_PREC_SPLIT 1  /* reconstruction, Riemann fluxes, EMFs in FP32 */
 
+/* Time integrators (Sec. 4.1).  RK3 uses the same stages and coefficients for
+ * the explicit and the implicit terms (the paper's runs: 3 sub-steps).  The
+ * IMEX schemes are the paper's Eqs. IMEX2 (2 implicit stages and a final
+ * combination: 3 sub-steps), IMEX2B (4 sub-steps) and IMEX3 (5 sub-steps);
+ * their final combination has no implicit term, and its conserved state is
+ * inverted by the same Newton solve with a zero source step.  A stage whose
+ * explicit bracket holds no flux term runs no reconstruction or flux kernel. */
+#define HARMRAD_INT_RK3 0
+#define HARMRAD_INT_IMEX2 1
+#define HARMRAD_INT_IMEX2B 2
+#define HARMRAD_INT_IMEX3 3
+
 /*
  * Run parameters.  Internal coordinates are uniform (Sec. 2): cell (i,j,k)
  * has centre x0 + (i+1/2) dx.  For the Kerr-Schild metric
@@ -101,6 +113,7 @@ typedef struct harmrad_params {
   int newton_max;      /* Newton step limit per method (Sec. 4.10), <= 60 */
   double newton_tol;   /* PMHD tolerance on e_T (Sec. 4.10) */
   int precision;       /* HARMRAD_PREC_* */
+  int integrator;      /* HARMRAD_INT_* */
 } harmrad_params;
 
 /* Per-zone outcome codes written by harmrad_get_status (worst over the three
@@ -258,7 +271,8 @@ int harmrad_profile_step(harmrad_ctx* ctx, double dt, harmrad_kernel_times* out)
  *
  * harmrad_adjoint_enable(ctx, 1) allocates the adjoint's workspace (about 40
  * doubles per cell) and makes every later harmrad_step keep a copy of its
- * input; 0 releases it.  HARMRAD_E_ARG for a batch or split precision.
+ * input; 0 releases it.  HARMRAD_E_ARG for a batch, split precision or an
+ * IMEX integrator.
  *
  * harmrad_step_adjoint(ctx, gP_out, gP_in, g_kappa, on_device) differentiates
  * the last harmrad_step of the context: given gP_out = dL/dP^{n+1} (active

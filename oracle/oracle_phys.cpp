@@ -414,7 +414,8 @@ int rad_invert(const orc_params& p, const Geom& G, const double Rt[4], int limit
       out[1] = out[2] = out[3] = 0.0;
       return negE;
     }
-    y = Utsq / (Erad * Erad);
+    // y = 0 without momentum (Erad^2 may underflow for Erad near 1e-300)
+    y = Utsq > 0.0 ? Utsq / (Erad * Erad) : 0.0;
     if (y < 0.0) {
       y = 0.0;
       Ut[0] = Ut[1] = Ut[2] = 0.0;
@@ -425,7 +426,7 @@ int rad_invert(const orc_params& p, const Geom& G, const double Rt[4], int limit
       y = ymax;
     }
   } else {  // TYPE2: keep the momentum, raise the energy to reach y = ymax
-    y = (Erad > 0.0) ? Utsq / (Erad * Erad) : HUGE_VAL;
+    y = (Erad > 0.0) ? (Utsq > 0.0 ? Utsq / (Erad * Erad) : 0.0) : HUGE_VAL;
     if (Erad <= 0.0 || y > ymax) {
       Erad = 1e-150 + std::sqrt(Utsq / ymax);
       y = Utsq / (Erad * Erad);

@@ -40,7 +40,7 @@ int Run<MET>::adjoint(harmrad_ctx* c, const double* gPout, double* gPin, double*
     c->rec_ust = a.Ust + (size_t)s * 12 * na;
     c->rec_meth = a.meth + (size_t)s * na;
     c->rec_psol = a.Psol + (size_t)s * 12 * na;
-    r = solve_impl<MET, double>(c, s);
+    r = solve_impl<MET, double>(c, s, ImexStage{});
     c->rec_ust = nullptr;
     c->rec_meth = nullptr;
     c->rec_psol = nullptr;

@@ -137,6 +137,8 @@ int fill_physics(const harmrad_params* p, DevParams& d) {
   d.newton_tol = p->newton_tol;
   if (p->precision != 0 && p->precision != 1) return HARMRAD_E_ARG;
   d.precision = p->precision;
+  if (p->integrator < 0 || p->integrator > 3) return HARMRAD_E_ARG;
+  d.integrator = p->integrator;
   return HARMRAD_OK;
 }
 
@@ -185,7 +187,7 @@ bool same_physics(const harmrad_params& a, const harmrad_params& b) {
          a.floor_rho0 == b.floor_rho0 && a.floor_rho_pow == b.floor_rho_pow && a.floor_u0 == b.floor_u0 &&
          a.floor_u_pow == b.floor_u_pow && a.bsq_rho_max == b.bsq_rho_max && a.bsq_u_max == b.bsq_u_max &&
          a.u_rho_max == b.u_rho_max && a.newton_max == b.newton_max && a.newton_tol == b.newton_tol &&
-         a.precision == b.precision;
+         a.precision == b.precision && a.integrator == b.integrator;
 }
 
 int run_faces(harmrad_ctx* c, bool fresh) {
@@ -194,8 +196,51 @@ int run_faces(harmrad_ctx* c, bool fresh) {
 int run_cfl(harmrad_ctx* c) {
   return c->dp.metric == 1 ? hr::Run<hr::KS>::cfl(c) : hr::Run<hr::MINK>::cfl(c);
 }
-int run_solve(harmrad_ctx* c, int s) {
-  return c->dp.metric == 1 ? hr::Run<hr::KS>::solve(c, s) : hr::Run<hr::MINK>::solve(c, s);
+int run_solve(harmrad_ctx* c, int s, const hr::ImexStage& im) {
+  return c->dp.metric == 1 ? hr::Run<hr::KS>::solve(c, s, im) : hr::Run<hr::MINK>::solve(c, s, im);
+}
+
+// Sub-steps of a time integrator (Sec. 4.1): RK3 and IMEX2 have 3, IMEX2B 4,
+// IMEX3 5 (its 4 implicit stages and the final combination).
+int n_substeps(int integrator) { return integrator == 2 ? 4 : (integrator == 3 ? 5 : 3); }
+
+// Sub-step k of an IMEX scheme as printed in Sec. 4.1 (Eqs. IMEX2, IMEX2B,
+// IMEX3), one row {an, ap, d, c0, c1, c2, c3, g} per stage:
+// U* = an U^n + ap U(P_prev) + d dt F(P_prev) + dt sum_j c_j M^j, solved with
+// the implicit step g dt.
+hr::ImexStage imex_stage(int integrator, int k) {
+  hr::ImexStage s{};
+  if (integrator == 0) return s;
+  double row[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  if (integrator == 1) {
+    const double y = 1.0 - 1.0 / sqrt(2.0);  // gamma
+    const double t[3][8] = {{1, 0, 0, 0, 0, 0, 0, y},
+                            {(3 * y - 1) / y, (1 - 2 * y) / y, 1, 0, 0, 0, 0, y},
+                            {0.5, 0.5, 0.5, y, (1 - y) / 2, 0, 0, 0}};
+    memcpy(row, t[k], sizeof(row));
+  } else if (integrator == 2) {
+    const double t[4][8] = {{1, 0, 0, 0, 0, 0, 0, 0.25},
+                            {1, 0, 0.5, 0, 0, 0, 0, 0.25},
+                            {0, 1, 0.5, 1.0 / 3, 1.0 / 12, 0, 0, 1.0 / 3},
+                            {1.0 / 3, 2.0 / 3, 1.0 / 3, 1.0 / 9, 1.0 / 9, 1.0 / 9, 0, 0}};
+    memcpy(row, t[k], sizeof(row));
+  } else {
+    const double a = 0.24169426078821, b = 0.06042356519705, e = 0.12915286960590;  // alpha, beta, eta
+    const double t[5][8] = {
+        {1, 0, 0, 0, 0, 0, 0, a},
+        {2, -1, 0, 0, 0, 0, 0, a},
+        {1, 0, 1, 0, 1 - a, 0, 0, a},
+        {0.75, 0.25, 0.25, b, (-1 + a + 4 * e) / 4, (2 - 5 * a - 4 * (b + e)) / 4, 0, a},
+        {1.0 / 3, 2.0 / 3, 2.0 / 3, -2 * b / 3, (1 - 4 * e) / 6, (-1 + 4 * a + 4 * (b + e)) / 6, 4 * (1 - a) / 6, 0}};
+    memcpy(row, t[k], sizeof(row));
+  }
+  s.an = row[0];
+  s.ap = row[1];
+  s.d = row[2];
+  for (int j = 0; j < 4; ++j) s.c[j] = row[3 + j];
+  s.g = row[7];
+  s.on = 1;
+  return s;
 }
 
 // Enqueue one full step.  with_cfl: the time step comes from the CFL pass of
@@ -214,12 +259,17 @@ int enqueue_step(harmrad_ctx* c, bool with_cfl) {
     if ((r = run_cfl(c)) < 0) return r;
     nk += r;
   }
-  for (int s = 0; s < 3; ++s) {
-    if (!(s == 0 && with_cfl)) {
-      if ((r = run_faces(c, s == 0)) < 0) return r;
-      nk += r;
+  bool first = true;  // the first sub-step with fluxes restarts the flattener's maximum
+  for (int s = 0; s < n_substeps(c->dp.integrator); ++s) {
+    const hr::ImexStage im = imex_stage(c->dp.integrator, s);
+    if (!im.on || im.d != 0.0) {
+      if (!(s == 0 && with_cfl)) {
+        if ((r = run_faces(c, first)) < 0) return r;
+        nk += r;
+      }
+      first = false;
     }
-    if ((r = run_solve(c, s)) < 0) return r;
+    if ((r = run_solve(c, s, im)) < 0) return r;
     nk += r;
   }
   return nk;
@@ -298,7 +348,8 @@ void free_all(harmrad_ctx* c) {
   void* ptrs[] = {c->P, c->K, c->geotab, c->Un, c->F[0], c->F[1], c->F[2], c->spd[0], c->spd[1], c->spd[2],
                   c->aux, c->flat[0], c->flat[1], c->flat[2], c->emf, c->edges, c->slope, c->dt, c->status,
                   c->iters, c->failed, c->qcount, c->czone, c->cbox, c->cdata, c->qzone, c->qbox, c->qdata, c->fzone, c->fbox,
-                  c->ftmp, c->stats, c->dtmin, c->stage_buf, c->flag, c->dboxes};
+                  c->ftmp, c->stats, c->dtmin, c->stage_buf, c->flag, c->dboxes, c->imex_ust, c->imex_psol,
+                  c->imex_M};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (c->host_dt) cudaFreeHost(c->host_dt);
@@ -415,6 +466,11 @@ int create(const harmrad_params* p, int count, void* stream, harmrad_ctx** out) 
   rc = rc ? rc : dalloc(&c->stats, 8 * sizeof(unsigned long long));
   rc = rc ? rc : dalloc(&c->dtmin, count * sizeof(unsigned long long));
   rc = rc ? rc : dalloc(&c->stage_buf, 12 * na * sizeof(double));
+  if (dp.integrator != 0) {  // IMEX: U*, the implicit solutions and the stages' sources
+    rc = rc ? rc : dalloc(&c->imex_ust, 12 * na * sizeof(double));
+    rc = rc ? rc : dalloc(&c->imex_psol, 12 * na * sizeof(double));
+    rc = rc ? rc : dalloc(&c->imex_M, 16 * na * sizeof(double));
+  }
   rc = rc ? rc : dalloc(&c->flag, sizeof(int));
   if (!rc && cudaMallocHost((void**)&c->host_dt, count * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
@@ -710,7 +766,7 @@ int harmrad_adjoint_enable(harmrad_ctx* c, int on) {
     free_adjoint(c);
     return HARMRAD_OK;
   }
-  if (c->nbox != 1 || c->real_size != 8) return HARMRAD_E_ARG;
+  if (c->nbox != 1 || c->real_size != 8 || c->dp.integrator != 0) return HARMRAD_E_ARG;
   if (c->adj) return HARMRAD_OK;
   c->adj = new hr::AdjBufs();
   memset(c->adj, 0, sizeof(hr::AdjBufs));

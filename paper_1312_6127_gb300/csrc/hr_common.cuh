@@ -7,6 +7,15 @@ namespace hr {
 enum { ST_PMHD = 0, ST_URAD = 1, ST_BACKUP = 2, ST_SOLVES = 3, ST_ITERS = 4 };
 constexpr int QSTRIDE = 18;
 
+// Coefficients of one sub-step of an IMEX scheme (Sec. 4.1, Eqs. IMEX2,
+// IMEX2B, IMEX3) in its bracket form: U* = an U^n + ap U(P) + d dt F(P)
+// + dt sum_j c_j M^j, then the implicit solve with step g dt (g = 0: the
+// final combination, inverted only).  on = 0: the RK3 stage coefficients.
+struct ImexStage {
+  double an, ap, d, c[4], g;
+  int on;
+};
+
 // Index of cell (i, j, k) (active indices, ghosts negative or >= n) within
 // its grid's block of a cell-indexed array.
 __host__ __device__ __forceinline__ long long cell_index(const BoxGeo& b, int i, int j, int k) {

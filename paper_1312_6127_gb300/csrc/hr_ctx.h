@@ -64,6 +64,9 @@ struct harmrad_ctx {
   double* rec_ust;
   unsigned char* rec_meth;
   double* rec_psol;
+  double* imex_ust;   // IMEX: [12][nact] U* of the current stage
+  double* imex_psol;  // IMEX: [12][nact] implicit solution of the current stage (before floors)
+  double* imex_M;     // IMEX: [4 stages][4 gas rows][nact] implicit sources M^j
   // launch shapes of the heavy kernels (threads per block, resident-block cap
   // per SM of the grid-stride grid); chosen by harmrad_autotune
   harmrad_tuning tune;
@@ -98,7 +101,7 @@ template <int MET>
 struct Run {
   static int faces(harmrad_ctx* c, bool fresh);     // ghosts, prep, flattener, fluxes, flux-CT
   static int cfl(harmrad_ctx* c);                   // faces(fresh) + reduction into *dt
-  static int solve(harmrad_ctx* c, int stage);      // update + implicit, retry, back-up
+  static int solve(harmrad_ctx* c, int stage, const ImexStage& im);  // update + implicit, retry, back-up
   // reverse sweep of the last step: gPout (device, active layout) -> gPin, gk
   static int adjoint(harmrad_ctx* c, const double* gPout, double* gPin, double* gk);
   static int zone_physics(const DevParams& dp, const BoxGeo& bg, int n, const double* x,

@@ -44,12 +44,15 @@ struct Bufs {
   double* cdata;          // [nact][CSTRIDE] continuation payload: U*, Newton state
   unsigned long long* stats;  // [8] counters
   unsigned long long* dtmin;  // [nbox] CFL minimum (ordered bits of a positive double)
-  // records for the adjoint's recomputation of a step (null otherwise):
   const double* geo;          // metric tables of Kerr-Schild grids (null otherwise)
+  // records of the sub-step for the adjoint's recomputation of a step and for
+  // the IMEX sources (null otherwise); planes per grid, grid b at 12 aoff_b:
   double* ust_rec;            // [12][nact] U* of every zone of the sub-step
   unsigned char* meth_rec;    // [nact] outcome of every zone of the sub-step
   double* psol_rec;           // [12][nact] solution of every zone before the floors
+  double* imexM;              // IMEX: [4 stages][4 gas rows][nact] per grid, grid b at 16 aoff_b
 };
+
 
 // Counter update aggregated over the converged lanes of a warp.
 __device__ __forceinline__ void warp_add(unsigned long long* dst, unsigned v) {
@@ -1027,7 +1030,7 @@ __device__ __forceinline__ bool pmhd_finish(const DevParams& p, const BoxGeo& bx
     double Pn[NPR];
     pmhd_final<MET>(p, s, best_x, Pn);
     if (b.psol_rec)
-      for (int q = 0; q < NPR; ++q) b.psol_rec[q * bx.nact + z] = Pn[q];
+      for (int q = 0; q < NPR; ++q) b.psol_rec[12 * bx.aoff + q * bx.nact + z] = Pn[q];
     apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn);
 #pragma unroll
     for (int q = 0; q < NPR; ++q) P[q * bx.ntot + t] = Pn[q];
@@ -1054,9 +1057,9 @@ __device__ __forceinline__ bool pmhd_finish(const DevParams& p, const BoxGeo& bx
 // update X = -sum_d dF_d/dx_d + SM, the RK3 combination
 // U* = a_s U^n + b_s (U(P_s) + dt X) (Sec. 4.1), the PMHD Newton solve, floors.
 // Zones whose PMHD error exceeds 1e-9 go to the retry queue.
-template <int MET, typename R, bool CONT>
+template <int MET, typename R, bool CONT, bool IMEX>
 __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx, int bi, const Bufs& b,
-                                           int stage, int split) {
+                                           int stage, int split, const ImexStage& im) {
   const double A = stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0);
   const double Bc = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
   {
@@ -1091,10 +1094,11 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
       const double kz = kfield(p, K, t);
       double Us[NPR], X[NPR];
       cons_source<MET, double>(p, g, x1, x2, Ps, Us, X, tab ? &mdt : nullptr);
-      // flux divergence
+      // flux divergence (an IMEX stage without flux term reads no fluxes)
+      const bool rhs = !IMEX || im.d != 0.0;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        if (!p.act[d]) continue;
+        if (!p.act[d] || !rhs) continue;
         const long long s = bx.str[d];
         const double idx_ = 1.0 / bx.dx[d];
 #pragma unroll
@@ -1113,14 +1117,32 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
         } else {
           un = Un[q * bx.nact + z];
         }
-        Ust[q] = A * un + Bc * (Us[q] + dt * X[q]);
+        if constexpr (IMEX)
+          Ust[q] = im.an * un + im.ap * Us[q] + im.d * dt * X[q];
+        else
+          Ust[q] = A * un + Bc * (Us[q] + dt * X[q]);
+      }
+      if (IMEX && stage > 0) {
+        // earlier stages' implicit sources: +M on the gas rows, -M on the radiation rows
+        const double* M = b.imexM + 16 * bx.aoff + z;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (j >= stage) break;
+          const double cj = im.c[j];
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            const double m = M[(4 * j + r) * bx.nact];
+            Ust[UU + r] += dt * cj * m;
+            Ust[ER + r] -= dt * cj * m;
+          }
+        }
       }
       if (b.ust_rec) {
 #pragma unroll
-        for (int q = 0; q < NPR; ++q) b.ust_rec[q * bx.nact + z] = Ust[q];
+        for (int q = 0; q < NPR; ++q) b.ust_rec[12 * bx.aoff + q * bx.nact + z] = Ust[q];
       }
       // implicit solve
-      const double h = Bc * dt;
+      const double h = IMEX ? im.g * dt : Bc * dt;
       ImpSys<MET> s;
       build_sys<MET>(p, g, Ust, h, kz, s);
       double x0[4] = {Ps[UU], Ps[U1], Ps[U2], Ps[U3]};
@@ -1181,8 +1203,7 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
 // uninterrupted iteration) and finishes the zone as the update kernel would.
 template <int MET>
 __global__ void __launch_bounds__(128) k_newton_cont(DevParams p, const BoxGeo* __restrict__ boxes, Bufs b,
-                                                     int stage) {
-  const double Bc = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
+                                                     double hfac) {
   const int nq = b.qcount[2];
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nq; e += gridDim.x * blockDim.x) {
     const int bi = b.cbox[e];
@@ -1201,7 +1222,7 @@ __global__ void __launch_bounds__(128) k_newton_cont(DevParams p, const BoxGeo* 
     for (int q = 0; q < NPR; ++q) Ust[q] = cd[q];
     NewtonState ns;
     newton_state_load(cd + NPR, ns);
-    const double h = Bc * b.dt[bi];
+    const double h = hfac * b.dt[bi];  // the sub-step's implicit step fraction
     ImpSys<MET> s;
     build_sys<MET>(p, g, Ust, h, kfield(p, b.K + bx.coff, t), s);
     newton_pmhd_run<MET>(p, s, ns, 1 << 30);
@@ -1212,18 +1233,48 @@ __global__ void __launch_bounds__(128) k_newton_cont(DevParams p, const BoxGeo* 
   }
 }
 
+// IMEX: the sub-step of an IMEX scheme with coefficients im (otherwise RK3).
 // ONE: a single grid whose geometry travels in the kernel's parameter space
 // (no registers held for it across the Newton solve); otherwise the boxes of
 // a batch, read from the device table.  CONT: PMHD iterations beyond `split`
 // continue in k_newton_cont (the queue costs registers; it pays where the
 // iteration counts are heavy-tailed, which the autotuner measures).
-template <int MET, typename R, bool ONE, bool CONT>
+template <int MET, typename R, bool ONE, bool CONT, bool IMEX>
 __global__ void __launch_bounds__(128) k_update(DevParams p, BoxGeo one, const BoxGeo* __restrict__ boxes,
-                                                int nbox, Bufs b, int stage, int split) {
+                                                int nbox, Bufs b, int stage, int split, ImexStage im) {
   if constexpr (ONE) {
-    update_box<MET, R, CONT>(p, one, 0, b, stage, split);
+    update_box<MET, R, CONT, IMEX>(p, one, 0, b, stage, split, im);
   } else {
-    for (int bi = 0; bi < nbox; ++bi) update_box<MET, R, CONT>(p, boxes[bi], bi, b, stage, split);
+    for (int bi = 0; bi < nbox; ++bi) update_box<MET, R, CONT, IMEX>(p, boxes[bi], bi, b, stage, split, im);
+  }
+}
+
+// IMEX: the implicit source of stage j on the gas rows,
+// M^j = (U(P) - U*) / (g dt), with P the stage's implicit solution before the
+// floors (the change the implicit stage made, Sec. 4.8); the radiation rows
+// take -M^j, so gas plus radiation stays conserved.
+template <int MET>
+__global__ void k_imex_store(DevParams p, const BoxGeo* __restrict__ boxes, int nbox, Bufs b, int j, double gj) {
+  for (int bi = 0; bi < nbox; ++bi) {
+    const BoxGeo& bx = boxes[bi];
+    const double h = gj * b.dt[bi];
+    const double* Ps = b.psol_rec + 12 * bx.aoff;
+    const double* Us = b.ust_rec + 12 * bx.aoff;
+    double* M = b.imexM + 16 * bx.aoff;
+    for (long long z = HR_TID; z < bx.nact; z += HR_STRIDE) {
+      long long r = z;
+      const int i = (int)(r % bx.n[0]);
+      r /= bx.n[0];
+      const int jj = (int)(r % bx.n[1]);
+      const double x1 = xcen(bx, 0, i), x2 = xcen(bx, 1, jj);
+      const Geo<MET, double> g = geo_centre<MET, double>(p, bx, b.geo, i, jj);
+      double Pz[NPR], Uz[NPR], Xz[NPR];
+#pragma unroll
+      for (int q = 0; q < NPR; ++q) Pz[q] = Ps[q * bx.nact + z];
+      cons_source<MET, double>(p, g, x1, x2, Pz, Uz, Xz, nullptr);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) M[(4 * j + q) * bx.nact + z] = (Uz[UU + q] - Us[(UU + q) * bx.nact + z]) / h;
+    }
   }
 }
 
@@ -1324,7 +1375,7 @@ __global__ void __launch_bounds__(128) k_retry(DevParams p, const BoxGeo* __rest
     }
     if (eT > 1e-7) method = ST_BACKUP;
     if (b.psol_rec)
-      for (int q = 0; q < NPR; ++q) b.psol_rec[q * bx.nact + z] = Pn[q];
+      for (int q = 0; q < NPR; ++q) b.psol_rec[12 * bx.aoff + q * bx.nact + z] = Pn[q];
     apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn);
     for (int q = 0; q < NPR; ++q) P[q * bx.ntot + t] = Pn[q];
     unsigned char m = (unsigned char)method;

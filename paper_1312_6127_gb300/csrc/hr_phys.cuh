@@ -37,6 +37,7 @@ struct DevParams {
   int newton_max;
   double newton_tol;
   int precision;
+  int integrator;  // 0 RK3, 1 IMEX2, 2 IMEX2B, 3 IMEX3 (Sec. 4.1)
 };
 
 // Geometry of one grid of a context: sizes, ghost depth, strides, internal
@@ -442,7 +443,7 @@ __device__ __forceinline__ int rad_invert(const DevParams& p, const Geo<MET, T>&
       out[1] = out[2] = out[3] = T(0.0);
       return negE;
     }
-    y = Utsq / (Erad * Erad);
+    y = Utsq > 0.0 ? Utsq / (Erad * Erad) : T(0.0);  // no momentum: y = 0 (Erad^2 may underflow)
     if (y < 0.0) {
       y = T(0.0);
       Ut[0] = Ut[1] = Ut[2] = T(0.0);
@@ -455,7 +456,7 @@ __device__ __forceinline__ int rad_invert(const DevParams& p, const Geo<MET, T>&
       y = T(ymax);
     }
   } else {
-    y = Erad > 0.0 ? Utsq / (Erad * Erad) : T(HUGE_VAL);
+    y = Erad > 0.0 ? (Utsq > 0.0 ? Utsq / (Erad * Erad) : T(0.0)) : T(HUGE_VAL);
     if (Erad <= 0.0 || y > ymax) {
       Erad = T(1e-150) + sqrt(Utsq / T(ymax));
       y = Utsq / (Erad * Erad);

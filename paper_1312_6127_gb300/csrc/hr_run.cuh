@@ -38,6 +38,11 @@ inline Bufs make_bufs(harmrad_ctx* c) {
   b.ust_rec = c->rec_ust;
   b.meth_rec = c->rec_meth;
   b.psol_rec = c->rec_psol;
+  if (c->imex_M) {  // IMEX contexts record U* and the solutions for the stage sources
+    b.ust_rec = c->imex_ust;
+    b.psol_rec = c->imex_psol;
+  }
+  b.imexM = c->imex_M;
   return b;
 }
 
@@ -193,7 +198,7 @@ int cfl_impl(harmrad_ctx* c) {
 }
 
 template <int MET, typename R>
-int solve_impl(harmrad_ctx* c, int stage) {
+int solve_impl(harmrad_ctx* c, int stage, const ImexStage& im) {
   const DevParams& p = c->dp;
   cudaStream_t st = c->stream;
   if (cudaMemsetAsync(c->qcount, 0, 4 * sizeof(int), st) != cudaSuccess) return HARMRAD_E_CUDA;
@@ -204,25 +209,45 @@ int solve_impl(harmrad_ctx* c, int stage) {
   const int gu = grid_for(c->maxact, c->sms, bu, c->tune.update_blocks_per_sm);
   const int split = c->tune.newton_split;
   const bool one = c->nbox == 1;
-  if (one && split == 0)
-    k_update<MET, R, true, false><<<gu, bu, 0, st>>>(p, c->boxes[0], c->dboxes, 1, b, stage, 0);
-  else if (one)
-    k_update<MET, R, true, true><<<gu, bu, 0, st>>>(p, c->boxes[0], c->dboxes, 1, b, stage, split);
-  else if (split == 0)
-    k_update<MET, R, false, false><<<gu, bu, 0, st>>>(p, c->boxes[0], c->dboxes, c->nbox, b, stage, 0);
-  else
-    k_update<MET, R, false, true><<<gu, bu, 0, st>>>(p, c->boxes[0], c->dboxes, c->nbox, b, stage, split);
+  const BoxGeo& b0 = c->boxes[0];
+  const BoxGeo* bt = c->dboxes;
+  const int nb = c->nbox;
+  if (!im.on) {
+    if (one && split == 0)
+      k_update<MET, R, true, false, false><<<gu, bu, 0, st>>>(p, b0, bt, 1, b, stage, 0, im);
+    else if (one)
+      k_update<MET, R, true, true, false><<<gu, bu, 0, st>>>(p, b0, bt, 1, b, stage, split, im);
+    else if (split == 0)
+      k_update<MET, R, false, false, false><<<gu, bu, 0, st>>>(p, b0, bt, nb, b, stage, 0, im);
+    else
+      k_update<MET, R, false, true, false><<<gu, bu, 0, st>>>(p, b0, bt, nb, b, stage, split, im);
+  } else {
+    if (one && split == 0)
+      k_update<MET, R, true, false, true><<<gu, bu, 0, st>>>(p, b0, bt, 1, b, stage, 0, im);
+    else if (one)
+      k_update<MET, R, true, true, true><<<gu, bu, 0, st>>>(p, b0, bt, 1, b, stage, split, im);
+    else if (split == 0)
+      k_update<MET, R, false, false, true><<<gu, bu, 0, st>>>(p, b0, bt, nb, b, stage, 0, im);
+    else
+      k_update<MET, R, false, true, true><<<gu, bu, 0, st>>>(p, b0, bt, nb, b, stage, split, im);
+  }
   mark(c, HARMRAD_K_UPDATE);
   int nk = 4;
   if (split > 0) {
     // the continuation queue, the retry queue and the back-up list are
     // short: one persistent wave of blocks each
-    k_newton_cont<MET><<<c->sms * 2, 128, 0, st>>>(p, c->dboxes, b, stage);
+    const double hfac = im.on ? im.g : (stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0));
+    k_newton_cont<MET><<<c->sms * 2, 128, 0, st>>>(p, c->dboxes, b, hfac);
     mark(c, HARMRAD_K_UPDATE);
     ++nk;
   }
   k_retry<MET><<<c->sms * 2, 128, 0, st>>>(p, c->dboxes, b);
   mark(c, HARMRAD_K_RETRY);
+  if (im.on && im.g > 0.0) {
+    k_imex_store<MET><<<grid_for(c->maxact, c->sms, 256), 256, 0, st>>>(p, c->dboxes, c->nbox, b, stage, im.g);
+    mark(c, HARMRAD_K_UPDATE);
+    ++nk;
+  }
   k_backup_avg<<<c->sms, 128, 0, st>>>(p, c->dboxes, b);
   mark(c, HARMRAD_K_BACKUP);
   k_backup_apply<MET><<<c->sms, 128, 0, st>>>(p, c->dboxes, b);
@@ -375,8 +400,8 @@ int Run<MET>::cfl(harmrad_ctx* c) {
   return c->real_size == 8 ? cfl_impl<MET, double>(c) : cfl_impl<MET, float>(c);
 }
 template <int MET>
-int Run<MET>::solve(harmrad_ctx* c, int stage) {
-  return c->real_size == 8 ? solve_impl<MET, double>(c, stage) : solve_impl<MET, float>(c, stage);
+int Run<MET>::solve(harmrad_ctx* c, int stage, const ImexStage& im) {
+  return c->real_size == 8 ? solve_impl<MET, double>(c, stage, im) : solve_impl<MET, float>(c, stage, im);
 }
 template <int MET>
 int Run<MET>::zone_physics(const DevParams& dp, const BoxGeo& bg, int n, const double* x,

@@ -18,6 +18,7 @@ OK, W_BACKUP_USED = 0, 1
 ZONE_PMHD, ZONE_URAD, ZONE_BACKUP = 0, 1, 2
 PREC_FP64, PREC_SPLIT = 0, 1
 OPAC_CONST, OPAC_KRAMERS, OPAC_FIELD = 0, 1, 2
+INT_RK3, INT_IMEX2, INT_IMEX2B, INT_IMEX3 = 0, 1, 2, 3
 
 EXPORTS = [
     "harmrad_init", "harmrad_init_batch", "harmrad_destroy", "harmrad_set_opacity_field", "harmrad_set_prims", "harmrad_get_prims",
@@ -64,6 +65,7 @@ class Params(ctypes.Structure):
         ("newton_max", ctypes.c_int),
         ("newton_tol", ctypes.c_double),
         ("precision", ctypes.c_int),
+        ("integrator", ctypes.c_int),
     ]
 
 
@@ -153,6 +155,8 @@ def make_params(cfg, precision=None):
     for name, ctype in Params._fields_:
         if name == "precision":
             v = cfg.get("precision", PREC_FP64) if precision is None else precision
+        elif name == "integrator":
+            v = cfg.get("integrator", INT_RK3)
         else:
             if name not in cfg:
                 raise KeyError("missing parameter %s" % name)

@@ -3,16 +3,20 @@ tests/golden/radiative_shocks.json) on the CUDA step.
 
 Parity: 800 zones over [-20, 20] with zero-gradient ends that let the inflow
 in (HARMRAD_BC_COPY), 20 steps of CUDA and oracle from the printed left/right
-states; tests 1 (non-relativistic, radiation 1e-4 of the gas energy: many
-URAD zones), 3b (upstream u^x = 10, optically thick) and 4a (radiation
-pressure dominated).
+states; tests 1 (non-relativistic, radiation 1e-4 of the gas energy: half the
+zones take URAD, whose Newton stops at e_T < 1e-9, so the two sides may stop
+at different iterates inside that tolerance in each of the 60 solves: 1e-6
+per zone), 3b (upstream u^x = 10, optically thick) and 4a (radiation pressure
+dominated), 1e-8 per zone.
 
 Stationary shocks: tests 2, 3b and 4b run on the GPU to t = 300 (the time
 the paper evolves them to).  The printed states are the asymptotic states of
-a shock at rest, so the run must settle with the far states unchanged and the
-total flux of rest mass, energy and momentum the same in every zone (a steady
-state of a conservative scheme); the tolerance is the jump-condition rounding
-of the printed states plus the smoothing of the shock by the scheme.
+a shock at rest, so the run must settle into a steady state of the
+conservative scheme: the same total face flux of rest mass, energy and
+momentum through every face (the face fluxes of the library's Riemann
+solver, gas plus radiation), equal to the flux of the printed left state,
+and the far states unchanged.  The tolerance allows the jump-condition
+rounding of the printed states (2e-3) and a slow drift of the shock.
 """
 import json
 import os
@@ -32,21 +36,14 @@ pytestmark = pytest.mark.gpu
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "radiative_shocks.json")))
 
 
-def zone_total_flux(cfg, P12):
-    """Total x-fluxes (rest mass, energy incl. rest mass, x-momentum) of the
-    primitives of one zone, from the oracle's flux function."""
-    F, _ = O.flux(O.make_params(cfg), [0.5, 0.5, 0.5], 1, P12)
-    return np.array([F[0], F[1] + F[8], F[2] + F[9]])
-
-
 def state(name):
     st = dict(GOLD["tests"][name])
     st["gam"] = float(Fraction(st["gam"]))
     return st
 
 
-@pytest.mark.parametrize("name", ["1", "3b", "4a"])
-def test_shock_tube_matches_oracle(name):
+@pytest.mark.parametrize("name,tol", [("1", 1e-6), ("3b", 1e-8), ("4a", 1e-8)])
+def test_shock_tube_matches_oracle(name, tol):
     cfg, P = W.shock_tube(state(name))
     g = H.Grid(cfg)
     g.set_prims(P)
@@ -64,9 +61,7 @@ def test_shock_tube_matches_oracle(name):
     ok = ~urad
     print("test %s: PMHD zones %.4e (%d), URAD/back-up zones %.4e (%d)"
           % (name, e[:, ok].max() if ok.any() else 0, ok.sum(), e[:, urad].max() if urad.any() else 0, urad.sum()))
-    assert e[:, ok].max() < 1e-8, e[:, ok].reshape(12, -1).max(axis=1)
-    if urad.any():
-        assert e[:, urad].max() < 1e-6
+    assert e.max() < tol, e.reshape(12, -1).max(axis=1)
 
 
 @pytest.mark.parametrize("name", ["2", "3b", "4b"])
@@ -83,10 +78,12 @@ def test_shock_stands_still(name):
     Q = g.get_prims()
     assert np.isfinite(Q).all()
     sig = float(st["sigma"])
-    F = np.array([zone_total_flux(cfg, Q[:, 0, 0, i]) for i in range(Q.shape[-1])])
+    F = g.fluxes(1)[:, 0, 0, :]
+    tot = np.stack([F[0], F[1] + F[8], F[2] + F[9]], axis=1)
     FL = total_flux(st["gam"], sig, [float(v) for v in st["L"]])
-    dev = np.abs(F - FL).max(axis=0) / np.abs(FL)
-    far = np.abs(Q[:, 0, 0, :40] - P[:, 0, 0, :40]).max(axis=1)
-    print("test %s: flux deviation %s; far-left drift rho %.2e ug %.2e ux %.2e E %.2e"
+    dev = np.abs(tot - FL).max(axis=0) / np.abs(FL)
+    far = np.abs(Q[:, 0, 0, :40] - P[:, 0, 0, :40]).max(axis=1) / np.abs(P[:, 0, 0, 0]).clip(1e-300)
+    print("test %s: face-flux deviation %s; far-left relative drift rho %.2e ug %.2e ux %.2e E %.2e"
           % (name, dev, far[0], far[1], far[2], far[8]))
-    assert dev.max() < 2e-2
+    assert dev.max() < 1e-2
+    assert max(far[0], far[1], far[2], far[8]) < 1e-3
