@@ -123,8 +123,13 @@ int    orc_rad_invert(const orc_params* p, const double* x, const double* Rt,
  * writes prims 0..4 of Pout and copies B. Returns 0 on success. */
 int    orc_gas_invert(const orc_params* p, const double* x, const double* U,
                       const double* Pg, double tol, double* Pout);
+/* Sec. 4.10 sub-dominance test of one zone: 1 if the radiation is extremely
+ * sub-dominant (URAD first in the grid step).  Un may be NULL. */
+int    orc_radiation_subdominant(const orc_params* p, const double* x, const double* Ustar,
+                                 const double* Un, const double* Ps);
 /* Implicit four-force solve of one zone: U* (12, densitised), guess P_s,
- * h = b_s*dt.  Writes the new prims and info. */
+ * h = b_s*dt, PMHD-first sequence (no sub-dominance test: no U^n here).
+ * Writes the new prims and info. */
 void   orc_implicit_zone(const orc_params* p, const double* x, const double* Ustar,
                          const double* Ps, double h, double* Pout,
                          orc_implicit_info* info);

@@ -118,6 +118,8 @@ def lib():
         L.orc_gas_invert.restype = ctypes.c_int
         L.orc_gas_invert.argtypes = [pp, dp, dp, dp, ctypes.c_double, dp]
         L.orc_implicit_zone.argtypes = [pp, dp, dp, dp, ctypes.c_double, dp, ctypes.POINTER(OrcInfo)]
+        L.orc_radiation_subdominant.argtypes = [pp, dp, dp, dp, dp]
+        L.orc_radiation_subdominant.restype = ctypes.c_int
         L.orc_pmhd_residual.argtypes = [pp, dp, dp, ctypes.c_double, dp, dp, dp, dp]
         L.orc_face_flux_stencil.argtypes = [pp, ctypes.c_int, dp, dp, dp, dp, dp]
         L.orc_levermore_xi.restype = ctypes.c_double
@@ -291,6 +293,14 @@ def implicit_zone(p, x, Ustar, Ps, h):
     lib().orc_implicit_zone(ctypes.byref(p), _dp(x), _dp(Ustar), _dp(Ps), float(h), _dp(out),
                             ctypes.byref(info))
     return out, info
+
+
+def radiation_subdominant(p, x, Ustar, Un, Ps):
+    """Sec. 4.10 sub-dominance test of one zone (Un may be None)."""
+    x, Us, Pz = _vec(x), _vec(Ustar), _vec(Ps)
+    una = _vec(Un) if Un is not None else None
+    un = _dp(una) if una is not None else None
+    return bool(lib().orc_radiation_subdominant(ctypes.byref(p), _dp(x), _dp(Us), un, _dp(Pz)))
 
 
 def pmhd_residual(p, x, Ustar, h, xg):

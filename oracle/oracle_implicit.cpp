@@ -383,13 +383,41 @@ void pmhd_residual_public(const orc_params& p, const Geom& G, const double* Usta
   *eI = r.eI;
 }
 
+// Sec. 4.10: the radiation is in the "extreme sub-dominant regime" when, on
+// the energy row, its conserved value, or its relative change over the
+// explicit update, or its fluid-frame energy density is below 10 eps_m of the
+// gas's (u_g for the last).  Then the round-off of the gas quantities from
+// which PMHD recovers the radiation would swamp it, and URAD goes first.  Un
+// may be null (no previous state): the relative-change test is then skipped.
+bool radiation_subdominant(const Geom& G, const double* Ustar, const double* Un, const double* Ps) {
+  const double tiny = 10.0 * 2.220446049250313e-16;
+  if (std::fabs(Ustar[ER]) < tiny * std::fabs(Ustar[UU])) return true;
+  if (Un) {
+    double dg = std::fabs(Ustar[UU] - Un[UU]), sg = std::fabs(Ustar[UU]) + std::fabs(Un[UU]);
+    double dr = std::fabs(Ustar[ER] - Un[ER]), sr = std::fabs(Ustar[ER]) + std::fabs(Un[ER]);
+    if (sg > 0.0 && sr > 0.0 && dr / sr < tiny * (dg / sg)) return true;
+  }
+  // Ehat = R^{mu nu} u_mu u_nu = Ebar (4/3 gamma_rel^2 - 1/3), gamma_rel = -u_rad . u
+  FourVel u, ur;
+  double ut[3] = {Ps[U1], Ps[U2], Ps[U3]}, utr[3] = {Ps[UR1], Ps[UR2], Ps[UR3]};
+  fourvel(G, ut, u);
+  fourvel(G, utr, ur);
+  double grel = 0.0;
+  for (int m = 0; m < 4; ++m) grel -= ur.ucon[m] * u.ucov[m];
+  double Ehat = Ps[ER] * ((4.0 / 3.0) * grel * grel - 1.0 / 3.0);
+  return Ehat < tiny * Ps[UU];
+}
+
 // Method sequence (Sec. 4.10-4.11): PMHD first, guessed from P_s or, where the
 // cell is optically thin (tau < 2/3), from a gas inversion of U*; URAD if PMHD
-// leaves e_T > 1e-9; the lower-error solution is kept; e_T > 1e-7 marks the
-// zone for the neighbour-average back-up.  A solution that hit the TYPE2
-// negative-energy branch has its radiation re-inverted with the BASIC limiter.
+// leaves e_T > 1e-9; the lower-error solution is kept.  With the radiation
+// extremely sub-dominant URAD goes first, from P_s, and PMHD (which would lose
+// that radiation in the gas's round-off) is not tried; the paper's next
+// method there, PRAD, is not built.  e_T > 1e-7 marks the zone for the
+// neighbour-average back-up.  A solution that hit the TYPE2 negative-energy
+// branch has its radiation re-inverted with the BASIC limiter.
 void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, const double* Ps,
-                   double h, double* Pout, orc_implicit_info* info) {
+                   double h, double* Pout, orc_implicit_info* info, bool subdominant) {
   Sys s;
   build_sys(p, G, Ustar, h, s);
   double x0[4] = {Ps[UU], Ps[U1], Ps[U2], Ps[U3]};
@@ -408,22 +436,35 @@ void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, cons
       x0[3] = Pt[U3];
     }
   }
-  Res bp;
-  info->iters_pmhd = newton_pmhd(s, x0, bp);
-  info->iters_urad = 0;
-  Res best = bp;
-  int method = ORC_OK_PMHD;
-  if (!(bp.ok && bp.eT < 1e-9)) {
-    const double* Pg = (bp.ok && bp.eT < 1e-4) ? bp.P : Ps;
+  Res best;
+  int method;
+  if (!subdominant) {
+    Res bp;
+    info->iters_pmhd = newton_pmhd(s, x0, bp);
+    info->iters_urad = 0;
+    best = bp;
+    method = ORC_OK_PMHD;
+    if (!(bp.ok && bp.eT < 1e-9)) {
+      const double* Pg = (bp.ok && bp.eT < 1e-4) ? bp.P : Ps;
+      double Tc[4], Rc[4];
+      tt_row(p, G, Pg, Tc, Rc, nullptr, nullptr);
+      double xr[4] = {Rc[0], Rc[1], Rc[2], Rc[3]};
+      Res br;
+      info->iters_urad = newton_urad(s, xr, Pg, br);
+      if (br.ok && (!best.ok || br.eT < best.eT)) {
+        best = br;
+        method = ORC_OK_URAD;
+      }
+    }
+  } else {
     double Tc[4], Rc[4];
-    tt_row(p, G, Pg, Tc, Rc, nullptr, nullptr);
+    tt_row(p, G, Ps, Tc, Rc, nullptr, nullptr);
     double xr[4] = {Rc[0], Rc[1], Rc[2], Rc[3]};
     Res br;
-    info->iters_urad = newton_urad(s, xr, Pg, br);
-    if (br.ok && (!best.ok || br.eT < best.eT)) {
-      best = br;
-      method = ORC_OK_URAD;
-    }
+    info->iters_urad = newton_urad(s, xr, Ps, br);
+    info->iters_pmhd = 0;
+    best = br;
+    method = ORC_OK_URAD;
   }
   if (!best.ok) {
     for (int q = 0; q < NP; ++q) Pout[q] = Ps[q];

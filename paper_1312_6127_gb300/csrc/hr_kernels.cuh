@@ -1049,6 +1049,26 @@ __device__ __forceinline__ bool pmhd_finish(const DevParams& p, const BoxGeo& bx
   return accept;
 }
 
+// The radiation of a zone is "extremely sub-dominant" (Sec. 4.10) when, on the
+// energy row, its conserved value in U*, or its relative change from U^n to
+// U*, or its fluid-frame energy density Ehat = Ebar (4/3 gamma_rel^2 - 1/3)
+// is below 10 eps_m of the gas's (u_g for Ehat).  PMHD recovers the radiation
+// from the gas's round-off there, so such zones start with URAD.
+template <int MET>
+__device__ __forceinline__ bool radiation_subdominant(const Geo<MET, double>& g, const double Ust[NPR],
+                                                      double un_gas, double un_rad, const double Ps[NPR]) {
+  const double tiny = 10.0 * 2.220446049250313e-16;
+  if (fabs(Ust[ER]) < tiny * fabs(Ust[UU])) return true;
+  const double dg = fabs(Ust[UU] - un_gas), sg = fabs(Ust[UU]) + fabs(un_gas);
+  const double dr = fabs(Ust[ER] - un_rad), sr = fabs(Ust[ER]) + fabs(un_rad);
+  if (sg > 0.0 && sr > 0.0 && dr / sr < tiny * (dg / sg)) return true;
+  double uc[4], uv[4], gm, rc[4], rv[4], gr;
+  fourvel<MET, double>(g, Ps[U1], Ps[U2], Ps[U3], uc, uv, &gm);
+  fourvel<MET, double>(g, Ps[UR1], Ps[UR2], Ps[UR3], rc, rv, &gr);
+  const double grel = -(rc[0] * uv[0] + rc[1] * uv[1] + rc[2] * uv[2] + rc[3] * uv[3]);
+  return Ps[ER] * ((4.0 / 3.0) * grel * grel - 1.0 / 3.0) < tiny * Ps[UU];
+}
+
 // ------------------------------------------------------- update + implicit
 // One thread per active zone: U(P_s), the geometric source
 // SM_nu = 1/2 sqrt(-g) T^{mu kappa} d_nu g_{mu kappa}  (equal to
@@ -1056,7 +1076,8 @@ __device__ __forceinline__ bool pmhd_finish(const DevParams& p, const BoxGeo& bx
 // only for nu = x1, x2 on the stationary axisymmetric metric), the explicit
 // update X = -sum_d dF_d/dx_d + SM, the RK3 combination
 // U* = a_s U^n + b_s (U(P_s) + dt X) (Sec. 4.1), the PMHD Newton solve, floors.
-// Zones whose PMHD error exceeds 1e-9 go to the retry queue.
+// Zones whose PMHD error exceeds 1e-9 go to the retry queue, and so do zones
+// whose radiation is extremely sub-dominant (URAD only, Sec. 4.10).
 template <int MET, typename R, bool CONT, bool IMEX>
 __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx, int bi, const Bufs& b,
                                            int stage, int split, const ImexStage& im) {
@@ -1107,7 +1128,7 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
           X[q] -= double(df) * idx_;
         }
       }
-      double Ust[NPR];
+      double Ust[NPR], un_gas = 0.0, un_rad = 0.0;
 #pragma unroll
       for (int q = 0; q < NPR; ++q) {
         double un;
@@ -1117,6 +1138,8 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
         } else {
           un = Un[q * bx.nact + z];
         }
+        if (q == UU) un_gas = un;
+        if (q == ER) un_rad = un;
         if constexpr (IMEX)
           Ust[q] = im.an * un + im.ap * Us[q] + im.d * dt * X[q];
         else
@@ -1143,6 +1166,20 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
       }
       // implicit solve
       const double h = IMEX ? im.g * dt : Bc * dt;
+      if (radiation_subdominant<MET>(g, Ust, un_gas, un_rad, Ps)) {
+        // URAD first, in the retry kernel (a negative PMHD error marks the entry)
+        const int slot = atomicAdd(&b.qcount[0], 1);
+        b.qzone[slot] = (int)z;
+        b.qbox[slot] = bi;
+        double* qd = b.qdata + (long long)slot * QSTRIDE;
+#pragma unroll
+        for (int q = 0; q < NPR; ++q) qd[q] = Ust[q];
+        for (int q = 0; q < 4; ++q) qd[12 + q] = 0.0;
+        qd[16] = -1.0;
+        qd[17] = h;
+        warp_add(&b.stats[ST_SOLVES], 1u);
+        continue;
+      }
       ImpSys<MET> s;
       build_sys<MET>(p, g, Ust, h, kz, s);
       double x0[4] = {Ps[UU], Ps[U1], Ps[U2], Ps[U3]};
@@ -1308,7 +1345,10 @@ __global__ void __launch_bounds__(128) k_retry(DevParams p, const BoxGeo* __rest
       Ps[q] = P[q * bx.ntot + t];
     }
     for (int q = 0; q < 4; ++q) px[q] = qd[12 + q];
-    const double peT = qd[16], h = qd[17];
+    // qd[16] < 0: radiation extremely sub-dominant, URAD only (no PMHD iterate)
+    const bool subdom = qd[16] < 0.0;
+    const double peT = subdom ? HUGE_VAL : qd[16];
+    const double h = qd[17];
     ImpSys<MET> s;
     build_sys<MET>(p, g, Ust, h, kfield(p, K, t), s);
     // PMHD iterate as the error function left it (TYPE2 radiation)

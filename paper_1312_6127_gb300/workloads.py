@@ -359,6 +359,44 @@ def thin_pulse(n=(32, 32, 32), L=100.0, w=5.0, T_a=1e6):
     return cfg, P
 
 
+def thick_pulse(n1=100, L=100.0, w=5.0, kappa_es=1e3, T_a=1e6, a_rad=8.77e-12):
+    """Optically thick planar radiation pulse (Sec. 5, 1D): radiation
+    temperature T_a (1 + 100 exp(-x^2/w^2)) on n1 zones over [-L/2, L/2)
+    (periodic), scattering opacity kappa_es per unit length at rho0 = 1, no
+    absorption, gas at rest at temperature T_a (K, converted to m_b c^2 / k_b),
+    a_rad = 8.77e-12 in these units (the paper's value).  The radiation energy is
+    25 orders below the gas energy, so it diffuses as a test field with
+    D = 1/(3 kappa_es)."""
+    cfg = base_params()
+    cfg.update(n=[n1, 1, 1], x0=[-L / 2, 0.0, 0.0], dx=[L / n1, 1.0, 1.0],
+               opacity=OPAC_CONST, kappa_abs0=0.0, kappa_es0=kappa_es, a_rad=a_rad)
+    Tg = T_a / 1.0888e13
+    x = cfg["x0"][0] + (np.arange(n1) + 0.5) * cfg["dx"][0]
+    P = np.zeros((NP, 1, 1, n1))
+    P[RHO] = 1.0
+    P[UU] = Tg / (cfg["gam"] - 1.0)
+    P[ER] = cfg["a_rad"] * (Tg * (1.0 + 100.0 * np.exp(-x ** 2 / w ** 2))) ** 4
+    return cfg, P
+
+
+def thick_pulse_exact(x, t, L=100.0, w=5.0, kappa_es=1e3, T_a=1e6, a_rad=8.77e-12, images=2):
+    """Solution of dE/dt = D d2E/dx2, D = 1/(3 kappa_es), from the thick
+    pulse's initial radiation energy: its binomial expansion
+    a T^4 sum_m C(4,m) 100^m exp(-m x^2/w^2) is a sum of Gaussians that each
+    spread on their own (periodic images included)."""
+    D = 1.0 / (3.0 * kappa_es)
+    Tg = T_a / 1.0888e13
+    x = np.asarray(x, dtype=float)
+    E = np.ones_like(x)
+    for m in range(1, 5):
+        t0 = w * w / (4.0 * m * D)
+        s = np.zeros_like(x)
+        for k in range(-images, images + 1):
+            s += np.exp(-(x - k * L) ** 2 / (4.0 * D * (t + t0)))
+        E += math.comb(4, m) * 100.0 ** m * math.sqrt(t0 / (t + t0)) * s
+    return a_rad * Tg ** 4 * E
+
+
 def shock_tube(state, n1=800, xlim=(-20.0, 20.0), recon=PPM, flux=LAXF):
     """1D radiative shock tube (Sec. 5, HD radiative shocks): the left and
     right states (rho0, p_g, u^x, Ehat) of ``state`` (keys L, R, gam, sigma,
