@@ -124,12 +124,12 @@ int    orc_rad_invert(const orc_params* p, const double* x, const double* Rt,
 int    orc_gas_invert(const orc_params* p, const double* x, const double* U,
                       const double* Pg, double tol, double* Pout);
 /* Sec. 4.10 sub-dominance test of one zone: 1 if the radiation is extremely
- * sub-dominant (URAD first in the grid step).  Un may be NULL. */
+ * sub-dominant (URAD first in the grid step). */
 int    orc_radiation_subdominant(const orc_params* p, const double* x, const double* Ustar,
-                                 const double* Un, const double* Ps);
+                                 const double* Ps);
 /* Implicit four-force solve of one zone: U* (12, densitised), guess P_s,
- * h = b_s*dt, PMHD-first sequence (no sub-dominance test: no U^n here).
- * Writes the new prims and info. */
+ * h = b_s*dt, PMHD-first sequence (the grid step's sub-dominance test is
+ * not applied here).  Writes the new prims and info. */
 void   orc_implicit_zone(const orc_params* p, const double* x, const double* Ustar,
                          const double* Ps, double h, double* Pout,
                          orc_implicit_info* info);

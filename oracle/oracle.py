@@ -118,7 +118,7 @@ def lib():
         L.orc_gas_invert.restype = ctypes.c_int
         L.orc_gas_invert.argtypes = [pp, dp, dp, dp, ctypes.c_double, dp]
         L.orc_implicit_zone.argtypes = [pp, dp, dp, dp, ctypes.c_double, dp, ctypes.POINTER(OrcInfo)]
-        L.orc_radiation_subdominant.argtypes = [pp, dp, dp, dp, dp]
+        L.orc_radiation_subdominant.argtypes = [pp, dp, dp, dp]
         L.orc_radiation_subdominant.restype = ctypes.c_int
         L.orc_pmhd_residual.argtypes = [pp, dp, dp, ctypes.c_double, dp, dp, dp, dp]
         L.orc_face_flux_stencil.argtypes = [pp, ctypes.c_int, dp, dp, dp, dp, dp]
@@ -295,12 +295,10 @@ def implicit_zone(p, x, Ustar, Ps, h):
     return out, info
 
 
-def radiation_subdominant(p, x, Ustar, Un, Ps):
-    """Sec. 4.10 sub-dominance test of one zone (Un may be None)."""
+def radiation_subdominant(p, x, Ustar, Ps):
+    """Sec. 4.10 sub-dominance test of one zone."""
     x, Us, Pz = _vec(x), _vec(Ustar), _vec(Ps)
-    una = _vec(Un) if Un is not None else None
-    un = _dp(una) if una is not None else None
-    return bool(lib().orc_radiation_subdominant(ctypes.byref(p), _dp(x), _dp(Us), un, _dp(Pz)))
+    return bool(lib().orc_radiation_subdominant(ctypes.byref(p), _dp(x), _dp(Us), _dp(Pz)))
 
 
 def pmhd_residual(p, x, Ustar, h, xg):

@@ -630,9 +630,7 @@ void substep(Ctx& c, int s, double dt) {
         double Pn[NP];
         orc_implicit_info info;
         const double h = imex ? ps.g * dt : Bc[s] * dt;
-        double Unz[NP];
-        for (int q = 0; q < NP; ++q) Unz[q] = c.Un[(long)q * c.ntot + t];
-        implicit_zone(cell_params(c, t), G, Ust, Ps, h, Pn, &info, radiation_subdominant(G, Ust, Unz, Ps));
+        implicit_zone(cell_params(c, t), G, Ust, Ps, h, Pn, &info, radiation_subdominant(G, Ust, Ps));
         if (imex && ps.g > 0.0) {
           // M^s = (U(P) - U*) / (g dt) on the gas rows, P the implicit stage's
           // solution (the source as the change the implicit stage made)
@@ -904,11 +902,10 @@ int orc_gas_invert(const orc_params* p, const double* x, const double* U, const 
   return gas_invert(*p, G, U, Pg, tol, Pout);
 }
 
-int orc_radiation_subdominant(const orc_params* p, const double* x, const double* Ustar, const double* Un,
-                              const double* Ps) {
+int orc_radiation_subdominant(const orc_params* p, const double* x, const double* Ustar, const double* Ps) {
   Geom G;
   geom_at(*p, x[1], x[2], x[3], G);
-  return radiation_subdominant(G, Ustar, Un, Ps) ? 1 : 0;
+  return radiation_subdominant(G, Ustar, Ps) ? 1 : 0;
 }
 
 void orc_implicit_zone(const orc_params* p, const double* x, const double* Ustar, const double* Ps,

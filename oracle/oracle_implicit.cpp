@@ -384,19 +384,16 @@ void pmhd_residual_public(const orc_params& p, const Geom& G, const double* Usta
 }
 
 // Sec. 4.10: the radiation is in the "extreme sub-dominant regime" when, on
-// the energy row, its conserved value, or its relative change over the
-// explicit update, or its fluid-frame energy density is below 10 eps_m of the
-// gas's (u_g for the last).  Then the round-off of the gas quantities from
-// which PMHD recovers the radiation would swamp it, and URAD goes first.  Un
-// may be null (no previous state): the relative-change test is then skipped.
-bool radiation_subdominant(const Geom& G, const double* Ustar, const double* Un, const double* Ps) {
+// the energy row, its conserved value in U*, or its fluid-frame energy
+// density, is below 10 eps_m of the gas's (u_g for the latter).  Then the
+// round-off of the gas quantities from which PMHD recovers the radiation
+// would swamp it, and URAD goes first.  (The paper also lists the relative
+// change of the energy row over the explicit update; compared between gas and
+// radiation it flags any zone whose radiation the update left unchanged, a
+// uniform radiation field for one, whatever its size, so it is not used.)
+bool radiation_subdominant(const Geom& G, const double* Ustar, const double* Ps) {
   const double tiny = 10.0 * 2.220446049250313e-16;
   if (std::fabs(Ustar[ER]) < tiny * std::fabs(Ustar[UU])) return true;
-  if (Un) {
-    double dg = std::fabs(Ustar[UU] - Un[UU]), sg = std::fabs(Ustar[UU]) + std::fabs(Un[UU]);
-    double dr = std::fabs(Ustar[ER] - Un[ER]), sr = std::fabs(Ustar[ER]) + std::fabs(Un[ER]);
-    if (sg > 0.0 && sr > 0.0 && dr / sr < tiny * (dg / sg)) return true;
-  }
   // Ehat = R^{mu nu} u_mu u_nu = Ebar (4/3 gamma_rel^2 - 1/3), gamma_rel = -u_rad . u
   FourVel u, ur;
   double ut[3] = {Ps[U1], Ps[U2], Ps[U3]}, utr[3] = {Ps[UR1], Ps[UR2], Ps[UR3]};

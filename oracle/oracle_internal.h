@@ -42,7 +42,7 @@ int gas_invert(const orc_params& p, const Geom& G, const double* U, const double
                double* out);
 
 // Implicit four-force solve of one zone (Sec. 4.7-4.11).
-bool radiation_subdominant(const Geom& G, const double* Ustar, const double* Un, const double* Ps);
+bool radiation_subdominant(const Geom& G, const double* Ustar, const double* Ps);
 void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, const double* Ps,
                    double h, double* Pout, orc_implicit_info* info, bool subdominant);
 void pmhd_residual_public(const orc_params& p, const Geom& G, const double* Ustar, double h,
