@@ -1025,7 +1025,7 @@ __device__ __forceinline__ bool pmhd_finish(const DevParams& p, const BoxGeo& bx
                                             double beT, int steps, double* P, const Bufs& b) {
   const long long zg = bx.aoff + z;
   b.iters[zg] += steps;
-  const bool accept = beT < 1e-9;
+  const bool accept = beT >= 0.0 && beT < 1e-9;  // beT < 0: sub-dominant radiation, URAD first
   if (accept) {
     double Pn[NPR];
     pmhd_final<MET>(p, s, best_x, Pn);
@@ -1164,20 +1164,9 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
       }
       // implicit solve
       const double h = IMEX ? im.g * dt : Bc * dt;
-      if (radiation_subdominant<MET>(g, Ust, Ps)) {
-        // URAD first, in the retry kernel (a negative PMHD error marks the entry)
-        const int slot = atomicAdd(&b.qcount[0], 1);
-        b.qzone[slot] = (int)z;
-        b.qbox[slot] = bi;
-        double* qd = b.qdata + (long long)slot * QSTRIDE;
-#pragma unroll
-        for (int q = 0; q < NPR; ++q) qd[q] = Ust[q];
-        for (int q = 0; q < 4; ++q) qd[12 + q] = 0.0;
-        qd[16] = -1.0;
-        qd[17] = h;
-        warp_add(&b.stats[ST_SOLVES], 1u);
-        continue;
-      }
+      // extremely sub-dominant radiation: no PMHD attempt; the zone goes to
+      // the retry queue for URAD with a negative PMHD error as the mark
+      const bool subdom = radiation_subdominant<MET>(g, Ust, Ps);
       ImpSys<MET> s;
       build_sys<MET>(p, g, Ust, h, kz, s);
       double x0[4] = {Ps[UU], Ps[U1], Ps[U2], Ps[U3]};
@@ -1202,8 +1191,8 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
       bool accept = false;
       unsigned done_steps = 0;
       if constexpr (!CONT) {
-        double bxn[4], beT;
-        const int steps = newton_pmhd<MET>(p, s, x0, bxn, &beT);
+        double bxn[4] = {0.0, 0.0, 0.0, 0.0}, beT = -1.0;
+        const int steps = subdom ? 0 : newton_pmhd<MET>(p, s, x0, bxn, &beT);
         accept = pmhd_finish<MET>(p, bx, bi, z, t, x1, g, s, Ust, h, bxn, beT, steps, P, b);
         done_steps = (unsigned)steps;
       } else {
@@ -1212,7 +1201,8 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
         // heavy tail of iteration counts runs in full warps
         NewtonState ns;
         newton_pmhd_init(x0, ns);
-        if (newton_pmhd_run<MET>(p, s, ns, split)) {
+        if (subdom) ns.best_eT = -1.0;
+        if (subdom || newton_pmhd_run<MET>(p, s, ns, split)) {
           accept = pmhd_finish<MET>(p, bx, bi, z, t, x1, g, s, Ust, h, ns.best_x, ns.best_eT, ns.steps, P, b);
           done_steps = (unsigned)ns.steps;
         } else {
