@@ -34,6 +34,7 @@ UNIT = "zone-cycles/s"
 # clock x 2 flops x 2.07 GHz = 1.26 TFLOP/s (the nominal 1.25 TFLOP/s).
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 PROFILE_JSON = os.path.join(ROOT, "profiles", "k_update_counters.json")
+INTEGRATORS = {"rk3": 0, "imex2": 1, "imex2b": 2, "imex3": 3}
 KERNEL_SOURCES = ["hr_phys.cuh", "hr_implicit.cuh", "hr_kernels.cuh"]
 
 
@@ -120,11 +121,12 @@ class OracleRun:
     zone and face loops on `threads` host threads (the result does not depend
     on the thread count)."""
 
-    def __init__(self, n, threads):
+    def __init__(self, n, threads, integrator=0):
         os.environ["ORACLE_THREADS"] = str(threads)
         from oracle import oracle as O
         from paper_1312_6127_gb300 import workloads as W
         cfg, P = W.torus(n, seed=12345)
+        cfg["integrator"] = integrator
         self.o = O.Oracle(cfg)
         self.o.set_prims(P)
         self.zones = n[0] * n[1] * n[2]
@@ -143,7 +145,7 @@ def run_reference(args, ws, rank):
         return 0
     n = tuple(int(x) for x in args.size.split(","))
     cores = os.cpu_count() or 1
-    run = OracleRun(n, cores)
+    run = OracleRun(n, cores, INTEGRATORS[args.integrator])
     for _ in range(args.warmup):
         run.step()
     t_all = 0.0
@@ -156,7 +158,7 @@ def run_reference(args, ws, rank):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": "KS torus a=0.9375 %dx%dx%d (PPM, LAXF, flux-CT, PMHD/URAD)" % n,
-                   "precision": "fp64", "zones": run.zones},
+                   "precision": "fp64", "integrator": args.integrator, "zones": run.zones},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": "each step: one CFL step of the whole %dx%dx%d torus, FP64 oracle "
                                    "with its zone and face loops on %d host threads" % (n + (cores,))},
@@ -177,6 +179,8 @@ def main():
     ap.add_argument("--workload", default="torus", choices=["torus", "batch48"],
                     help="torus: the Kerr-Schild torus (default); batch48: 48 uneven Minkowski "
                          "boxes with a per-zone absorption field in one batched context")
+    ap.add_argument("--integrator", default="rk3", choices=list(INTEGRATORS),
+                    help="time integrator (Sec. 4.1): the paper's RK3 or one of its IMEX schemes")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
@@ -200,8 +204,10 @@ def main():
     n = tuple(int(x) for x in args.size.split(","))
     prec = H.PREC_SPLIT if args.precision == "split" else H.PREC_FP64
     stream = torch.cuda.current_stream()
+    integ = INTEGRATORS[args.integrator]
     if args.workload == "torus":
         cfg, P = W.torus(n, seed=12345 + rank)
+        cfg["integrator"] = integ
         nact = n[0] * n[1] * n[2]
         g = H.Grid(cfg, precision=prec, stream=stream)
         g.set_prims(P)
@@ -209,6 +215,7 @@ def main():
         size_key, prof_key = list(n), args.precision
     else:
         cfgs, Ps, Ks = W.box_batch(seed=4242 + rank)
+        cfgs = [dict(c, integrator=integ) for c in cfgs]
         g = H.Batch(cfgs, precision=prec, stream=stream)
         g.set_prims(Ps)
         g.set_opacity_field(Ks)
@@ -260,7 +267,9 @@ def main():
         except (OSError, ValueError):
             prof = {}
         entry = prof.get(prof_key, {})
-        fresh = entry.get("kernel_hash") == kernel_hash() and entry.get("size") == size_key
+        # the counters are those of the RK3 update kernel
+        fresh = (entry.get("kernel_hash") == kernel_hash() and entry.get("size") == size_key
+                 and integ == 0)
         flops_per_zone = entry.get("fp64_flops_per_zone_stage")
         traffic = entry.get("dram_bytes_per_launch") if fresh else None
         if flops_per_zone and fresh:
@@ -277,7 +286,8 @@ def main():
                         "unit": "TFLOP/s", "frac": None, "traffic": traffic,
                         "kernel": "k_update", "kernel_ms": avg_ms,
                         "note": "FP64 op count per zone not captured for this kernel build "
-                                "(profiles/k_update_counters.json kernel_hash differs)"}
+                                "(profiles/k_update_counters.json kernel_hash differs)" if integ == 0 else
+                                "FP64 op counts are captured for the RK3 update kernel only"}
         # HBM view of the whole step: algorithmic bytes per zone-cycle
         hbm = measured_peaks().get("hbm_gbs")
         step_ms = ms / args.steps
@@ -308,7 +318,7 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu and args.workload == "torus":
         cores = os.cpu_count() or 1
-        run = OracleRun(n, cores)
+        run = OracleRun(n, cores, integ)
         v, t = run.step()
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "one CFL step of the same seeded %dx%dx%d torus, FP64 oracle with its zone "
@@ -322,7 +332,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == H.PREC_FP64 else "f64+f32",
             "data": "synthetic",
             "config": {"workload": wl,
-                       "precision": args.precision, "zones": nact,
+                       "precision": args.precision, "integrator": args.integrator, "zones": nact,
                        "l2": "working set > L2 (129 MB); no flush needed",
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "launch_shapes": {k: v for k, v in tuning.items() if not k.endswith("_ms")},
