@@ -119,6 +119,8 @@ def lib():
         L.orc_gas_invert.argtypes = [pp, dp, dp, dp, ctypes.c_double, dp]
         L.orc_implicit_zone.argtypes = [pp, dp, dp, dp, ctypes.c_double, dp, ctypes.POINTER(OrcInfo)]
         L.orc_radiation_subdominant.argtypes = [pp, dp, dp, dp]
+        L.orc_method_zone.argtypes = [pp, dp, dp, dp, ctypes.c_double, ctypes.c_int, dp, dp,
+                                      ctypes.POINTER(ctypes.c_int)]
         L.orc_radiation_subdominant.restype = ctypes.c_int
         L.orc_pmhd_residual.argtypes = [pp, dp, dp, ctypes.c_double, dp, dp, dp, dp]
         L.orc_face_flux_stencil.argtypes = [pp, ctypes.c_int, dp, dp, dp, dp, dp]
@@ -293,6 +295,17 @@ def implicit_zone(p, x, Ustar, Ps, h):
     lib().orc_implicit_zone(ctypes.byref(p), _dp(x), _dp(Ustar), _dp(Ps), float(h), _dp(out),
                             ctypes.byref(info))
     return out, info
+
+
+def method_zone(p, x, Ustar, Ps, h, method):
+    """One Newton method alone (0 PMHD, 1 URAD, 2 PRAD): (P, e_T, steps)."""
+    x, Us, Pz = _vec(x), _vec(Ustar), _vec(Ps)
+    out = np.empty(NP)
+    eT = ctypes.c_double()
+    it = ctypes.c_int()
+    lib().orc_method_zone(ctypes.byref(p), _dp(x), _dp(Us), _dp(Pz), float(h), int(method), _dp(out),
+                          ctypes.byref(eT), ctypes.byref(it))
+    return out, eT.value, it.value
 
 
 def radiation_subdominant(p, x, Ustar, Ps):

@@ -182,6 +182,53 @@ bool urad_res(const Sys& s, const double x[4], const double* Pguess, double tol_
   return r.ok;
 }
 
+// PRAD error function: iterate the radiation primitives (Ebar, u~^i_rad);
+// radiation R^t_nu from them in closed form; gas from total energy-momentum
+// conservation through the 1D_W inversion; all conserved quantities
+// recomputed from the primitives before forming E_q (Sec. 4.8).
+bool prad_res(const Sys& s, const double x[4], const double* Pguess, double tol_inv, Res& r) {
+  const orc_params& p = *s.p;
+  const Geom& G = *s.G;
+  double P[NP];
+  for (int q = 0; q < NP; ++q) P[q] = Pguess[q];
+  P[ER] = x[0];
+  P[UR1] = x[1];
+  P[UR2] = x[2];
+  P[UR3] = x[3];
+  double R[4][4];
+  FourVel ur;
+  rad_stress(G, P, R, ur);
+  double Rx[4];
+  for (int k = 0; k < 4; ++k) Rx[k] = R[0][k];
+  double gd = G.gdet;
+  double U[NP];
+  U[0] = gd * s.Dlab;
+  for (int k = 0; k < 4; ++k) U[1 + k] = gd * (s.Tstar[k] - (Rx[k] - s.Rstar[k]));
+  for (int i = 0; i < 3; ++i) U[5 + i] = gd * s.B[i];
+  for (int k = 0; k < 4; ++k) U[8 + k] = gd * Rx[k];
+  double Pg[NP];
+  if (gas_invert(p, G, U, Pguess, tol_inv, Pg) != 0) {
+    r.ok = false;
+    return false;
+  }
+  for (int q = 0; q < ER; ++q) P[q] = Pg[q];
+  for (int k = 0; k < 4; ++k) r.Rt_pre[k] = Rx[k];
+  r.negE = 0;
+  double Tc[4], Rc[4];
+  FourVel u;
+  tt_row(p, G, P, Tc, Rc, &u, nullptr);
+  double Gc[4];
+  four_force(p, G, P[RHO], P[UU], u, R, Gc);
+  for (int k = 0; k < 4; ++k) {
+    r.Eg[k] = Tc[k] - s.Tstar[k] - s.h * Gc[k];
+    r.Er[k] = Rc[k] - s.Rstar[k] + s.h * Gc[k];
+  }
+  normalise(s, Tc, Rc, Gc, false, r);
+  std::memcpy(r.P, P, sizeof(P));
+  r.ok = std::isfinite(r.eT);
+  return r.ok;
+}
+
 // Solve A z = b (4x4) by Gaussian elimination with partial pivoting.
 bool solve4(double A[4][4], double b[4], double z[4]) {
   double M[4][5];
@@ -306,10 +353,20 @@ int newton_urad(const Sys& s, const double x0[4], const double* Pg0, Res& best) 
   int steps = 0, ninv = 0;
   const int inv_budget = 20 * 6;
   double eps = 1e-8;
+  double xprev[4];
+  bool have_prev = false;
   for (int k = 0;; ++k) {
     Res r;
-    ++ninv;
-    if (!urad_res(s, x, Pg, 1e-13, r)) break;
+    // an inversion error at a new iterate backs the step up half-way, up to
+    // 20 times (Sec. 4.10)
+    bool ok = false;
+    for (int back = 0;; ++back) {
+      ++ninv;
+      ok = urad_res(s, x, Pg, 1e-13, r);
+      if (ok || !have_prev || back >= 20 || ninv >= inv_budget) break;
+      for (int i = 0; i < 4; ++i) x[i] = 0.5 * (x[i] + xprev[i]);
+    }
+    if (!ok) break;
     std::memcpy(Pg, r.P, sizeof(Pg));
     if (r.eT < best.eT) best = r;
     hs.eT[k] = r.eT;
@@ -344,6 +401,8 @@ int newton_urad(const Sys& s, const double x0[4], const double* Pg0, Res& best) 
     for (int i = 0; i < 4; ++i) xn[i] = x[i] - dx[i];
     // R^t_t must stay negative (positive lab energy): reflect to half its size.
     if (xn[0] > 0.0) xn[0] = -0.5 * std::fabs(xn[0]);
+    for (int i = 0; i < 4; ++i) xprev[i] = x[i];
+    have_prev = true;
     bool tiny = true;
     for (int i = 0; i < 4; ++i)
       if (std::fabs(xn[i] - x[i]) > 10.0 * EPSM * std::fabs(x[i])) tiny = false;
@@ -353,6 +412,93 @@ int newton_urad(const Sys& s, const double x0[4], const double* Pg0, Res& best) 
       Res rf;
       ++ninv;
       if (urad_res(s, x, Pg, 1e-13, rf) && rf.eT < best.eT) best = rf;
+      break;
+    }
+  }
+  return steps;
+}
+
+// PRAD Newton (Sec. 4.8-4.10): iterate the radiation primitives (Ebar,
+// u~^i_rad) with the URAD controls (one-sided Jacobian retried x10 up to 0.3
+// on an inversion failure, tolerance 1e-9, 20 x 6 gas inversions, half-step
+// back-off); offsets eps |Ebar| and eps max(1, |u~_rad|) / sqrt(g_jj) (the
+// PMHD form for velocities); Ebar < 0 after a step -> |Ebar| / 2.
+int newton_prad(const Sys& s, const double x0[4], const double* Pg0, Res& best) {
+  const orc_params& p = *s.p;
+  const Geom& G = *s.G;
+  const double tol = 1e-9;
+  double x[4] = {x0[0], x0[1], x0[2], x0[3]};
+  double Pg[NP];
+  std::memcpy(Pg, Pg0, sizeof(Pg));
+  History hs;
+  best.eT = HUGE_VAL;
+  best.ok = false;
+  int steps = 0, ninv = 0;
+  const int inv_budget = 20 * 6;
+  double eps = 1e-8;
+  double xprev[4];
+  bool have_prev = false;
+  for (int k = 0;; ++k) {
+    Res r;
+    // an inversion error at a new iterate backs the step up half-way, up to
+    // 20 times (Sec. 4.10)
+    bool ok = false;
+    for (int back = 0;; ++back) {
+      ++ninv;
+      ok = prad_res(s, x, Pg, 1e-13, r);
+      if (ok || !have_prev || back >= 20 || ninv >= inv_budget) break;
+      for (int i = 0; i < 4; ++i) x[i] = 0.5 * (x[i] + xprev[i]);
+    }
+    if (!ok) break;
+    std::memcpy(Pg, r.P, sizeof(Pg));
+    if (r.eT < best.eT) best = r;
+    hs.eT[k] = r.eT;
+    hs.eI[k] = r.eI;
+    if (r.eT < tol) break;
+    if (stalled(hs, k)) break;
+    if (k >= p.newton_max || ninv >= inv_budget) break;
+    if (r.eI < 1e-9) eps = 1e-10;
+    double J[4][4];
+    bool jok = true;
+    for (int j = 0; j < 4 && jok; ++j) {
+      double umag = 0.0;
+      for (int a = 1; a < 4; ++a)
+        for (int c = 1; c < 4; ++c) umag += G.gcov[a][c] * x[a] * x[c];
+      umag = std::max(1.0, std::sqrt(std::max(umag, 0.0)));
+      double scale = j == 0 ? std::fabs(x[0]) : umag / std::sqrt(G.gcov[j][j]);
+      bool done = false;
+      for (double e = eps; e <= 0.3 && !done; e *= 10.0) {
+        double dj = e * scale;
+        if (dj == 0.0) break;
+        double xp[4] = {x[0], x[1], x[2], x[3]};
+        xp[j] += dj;
+        Res rp;
+        ++ninv;
+        if (prad_res(s, xp, Pg, 1e-2 * e, rp)) {
+          for (int i = 0; i < 4; ++i) J[i][j] = (rp.Er[i] - r.Er[i]) / dj;
+          done = true;
+        }
+      }
+      if (!done) jok = false;
+    }
+    if (!jok) break;
+    double dx[4], E[4] = {r.Er[0], r.Er[1], r.Er[2], r.Er[3]};
+    if (!solve4(J, E, dx)) break;
+    double xn[4];
+    for (int i = 0; i < 4; ++i) xn[i] = x[i] - dx[i];
+    // Ebar must stay positive: reflect to half its size (Sec. 4.10)
+    if (xn[0] < 0.0) xn[0] = 0.5 * std::fabs(xn[0]);
+    for (int i = 0; i < 4; ++i) xprev[i] = x[i];
+    have_prev = true;
+    bool tiny = true;
+    for (int i = 0; i < 4; ++i)
+      if (std::fabs(xn[i] - x[i]) > 10.0 * EPSM * std::fabs(x[i])) tiny = false;
+    for (int i = 0; i < 4; ++i) x[i] = xn[i];
+    ++steps;
+    if (tiny) {
+      Res rf;
+      ++ninv;
+      if (prad_res(s, x, Pg, 1e-13, rf) && rf.eT < best.eT) best = rf;
       break;
     }
   }
@@ -371,6 +517,26 @@ void build_sys(const orc_params& p, const Geom& G, const double* Ustar, double h
 }
 
 }  // namespace
+
+void method_zone(const orc_params& p, const Geom& G, const double* Ustar, const double* Ps, double h,
+                 int method, double* Pout, double* eT, int* iters) {
+  Sys s;
+  build_sys(p, G, Ustar, h, s);
+  Res b;
+  if (method == 0) {
+    double x0[4] = {Ps[UU], Ps[U1], Ps[U2], Ps[U3]};
+    *iters = newton_pmhd(s, x0, b);
+  } else if (method == 1) {
+    double Tc[4], Rc[4];
+    tt_row(p, G, Ps, Tc, Rc, nullptr, nullptr);
+    *iters = newton_urad(s, Rc, Ps, b);
+  } else {
+    double x0[4] = {Ps[ER], Ps[UR1], Ps[UR2], Ps[UR3]};
+    *iters = newton_prad(s, x0, Ps, b);
+  }
+  *eT = b.ok ? b.eT : HUGE_VAL;
+  for (int q = 0; q < NP; ++q) Pout[q] = b.ok ? b.P[q] : Ps[q];
+}
 
 void pmhd_residual_public(const orc_params& p, const Geom& G, const double* Ustar, double h,
                           const double* xg, double* E4, double* eT, double* eI) {
@@ -407,12 +573,12 @@ bool radiation_subdominant(const Geom& G, const double* Ustar, const double* Ps)
 
 // Method sequence (Sec. 4.10-4.11): PMHD first, guessed from P_s or, where the
 // cell is optically thin (tau < 2/3), from a gas inversion of U*; URAD if PMHD
-// leaves e_T > 1e-9; the lower-error solution is kept.  With the radiation
-// extremely sub-dominant URAD goes first, from P_s, and PMHD (which would lose
-// that radiation in the gas's round-off) is not tried; the paper's next
-// method there, PRAD, is not built.  e_T > 1e-7 marks the zone for the
-// neighbour-average back-up.  A solution that hit the TYPE2 negative-energy
-// branch has its radiation re-inverted with the BASIC limiter.
+// leaves e_T > 1e-9; PRAD if both do; the lowest-error solution is kept.  With
+// the radiation extremely sub-dominant URAD goes first, from P_s, then PRAD,
+// and PMHD (which would lose that radiation in the gas's round-off) is not
+// tried.  e_T > 1e-7 marks the zone for the neighbour-average back-up.  A
+// solution that hit the TYPE2 negative-energy branch has its radiation
+// re-inverted with the BASIC limiter.
 void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, const double* Ps,
                    double h, double* Pout, orc_implicit_info* info, bool subdominant) {
   Sys s;
@@ -462,6 +628,28 @@ void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, cons
     info->iters_pmhd = 0;
     best = br;
     method = ORC_OK_URAD;
+  }
+  if (!(best.ok && best.eT < 1e-9)) {
+    // PRAD (Sec. 4.10), guessed from the best earlier solution if its
+    // e_T < 1e-4, else from the optically thin limit (the M1 inversion of U*,
+    // no source) where tau < 2/3, else from P_s; its outcome counts as URAD's
+    // (a retry method solved the zone)
+    double xq[4];
+    const double* Pq = Ps;
+    if (best.ok && best.eT < 1e-4) {
+      Pq = best.P;
+      for (int i = 0; i < 4; ++i) xq[i] = best.P[ER + i];
+    } else if (tau < 2.0 / 3.0) {
+      rad_invert(p, G, s.Rstar, LIM_TYPE2, xq);
+    } else {
+      for (int i = 0; i < 4; ++i) xq[i] = Ps[ER + i];
+    }
+    Res bq;
+    info->iters_urad += newton_prad(s, xq, Pq, bq);
+    if (bq.ok && (!best.ok || bq.eT < best.eT)) {
+      best = bq;
+      method = ORC_OK_URAD;
+    }
   }
   if (!best.ok) {
     for (int q = 0; q < NP; ++q) Pout[q] = Ps[q];

@@ -463,24 +463,99 @@ __device__ __forceinline__ bool urad_res(const DevParams& p, const ImpSys<MET>& 
   return r.ok;
 }
 
-// URAD Newton: one-sided Jacobian, tolerance 1e-9, at most 20 x 6 gas
-// inversions; inversion failures in a Jacobian column retried with offsets
-// x10 up to 0.3.  Pg (gas guess: rho, u_g, u~^i) is updated by every
-// successful residual.  best_x / best_Pg / best_eT hold the best iterate.
+// PRAD error function: iterate the radiation primitives (Ebar, u~^i_rad);
+// R^t_nu from them in closed form; gas from 1D_W inversion of
+// T^t_nu = T*^t_nu - (R^t_nu - R*^t_nu) (Sec. 4.8).
 template <int MET>
-__device__ int newton_urad(const DevParams& p, const ImpSys<MET>& s, const double x0[4], double Pg[5],
-                           double best_x[4], double best_Pg[5], double* best_eT) {
+__device__ __forceinline__ bool prad_res(const DevParams& p, const ImpSys<MET>& s, const double x[4],
+                                         const double Pg[5], double tol_inv, ImpRes& r,
+                                         double gas_out[5], double Rx[4], bool norm) {
+  const auto& g = s.g;
+  double urc[4], urv[4], gr;
+  fourvel<MET, double>(g, x[1], x[2], x[3], urc, urv, &gr);
+  const double e43 = (4.0 / 3.0) * x[0];
+  Rx[0] = e43 * urc[0] * urv[0] + x[0] * (1.0 / 3.0);
+#pragma unroll
+  for (int k = 1; k < 4; ++k) Rx[k] = e43 * urc[0] * urv[k];
+  double Tt[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) Tt[k] = s.Ts[k] - (Rx[k] - s.Rs[k]);
+  double Pg12[12];
+  Pg12[UU] = Pg[1];
+  Pg12[U1] = Pg[2];
+  Pg12[U2] = Pg[3];
+  Pg12[U3] = Pg[4];
+  double T3[3] = {Tt[1], Tt[2], Tt[3]};
+  if (gas_invert<MET>(p, g, s.Dlab, Tt[0], T3, s.B, Pg12, tol_inv, gas_out) != 0) {
+    r.ok = false;
+    return false;
+  }
+  r.negE = 0;
+  double ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq;
+  fourvel<MET, double>(g, gas_out[2], gas_out[3], gas_out[4], ucon, ucov, &gm);
+  bvec<MET, double>(g, ucon, ucov, s.B[0], s.B[1], s.B[2], bcon, bcov, &bsq);
+  double rho = gas_out[0], ug = gas_out[1];
+  double pg = (p.gam - 1.0) * ug;
+  double wb = rho + ug + pg + bsq, pt = pg + 0.5 * bsq;
+  double Tc[4];
+  Tc[0] = wb * ucon[0] * ucov[0] + pt - bcon[0] * bcov[0] + rho * ucon[0];
+#pragma unroll
+  for (int k = 1; k < 4; ++k) Tc[k] = wb * ucon[0] * ucov[k] - bcon[0] * bcov[k];
+  double G[4];
+  four_force_rad<MET>(p, rho, (p.gam - 1.0) * ug / rho, s.kf, s.ks, ucon, ucov, urc, urv, x[0], G);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    r.Eg[k] = Tc[k] - s.Ts[k] - s.h * G[k];
+    r.Er[k] = Rx[k] - s.Rs[k] + s.h * G[k];
+  }
+  if (norm) {
+    normalise<MET>(s, Tc, Rx, G, false, r);
+    r.ok = isfinite(r.eT);
+  } else {
+    r.ok = true;
+  }
+  return r.ok;
+}
+
+// Radiation-side Newton iterations (Sec. 4.8-4.10).  URAD (PRAD = false)
+// iterates x = R^t_nu with offsets eps |R^t_t| (times sqrt(g_jj) for j > 0);
+// PRAD iterates x = (Ebar, u~^i_rad) with offsets eps |Ebar| and
+// eps max(1, |u~_rad|) / sqrt(g_jj).  Both: one-sided Jacobian of the
+// radiation rows, offsets retried x10 up to 0.3 on an inversion failure,
+// tolerance 1e-9, at most 20 x 6 gas inversions; an inversion error at a new
+// iterate backs the step up half-way, up to 20 times; after a step URAD
+// reflects R^t_t > 0 and PRAD Ebar < 0 to half their size.  Pg (gas guess:
+// rho, u_g, u~^i) is updated by every successful residual.  best_x / best_Pg
+// / best_eT hold the best iterate.
+template <int MET, bool PRAD>
+__device__ int newton_rad(const DevParams& p, const ImpSys<MET>& s, const double x0[4], double Pg[5],
+                          double best_x[4], double best_Pg[5], double* best_eT) {
   double x[4] = {x0[0], x0[1], x0[2], x0[3]};
+  double xprev[4] = {x0[0], x0[1], x0[2], x0[3]};
+  bool have_prev = false;
   Hist hs = {HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, 0};
   *best_eT = HUGE_VAL;
   int steps = 0, ninv = 0;
   const int budget = 20 * 6;
   double eps = 1e-8;
+  auto res = [&](const double* xx, double tol, ImpRes& rr, double* go, bool norm) {
+    double aux[4];
+    return PRAD ? prad_res<MET>(p, s, xx, Pg, tol, rr, go, aux, norm)
+                : urad_res<MET>(p, s, xx, Pg, tol, rr, go, aux, norm);
+  };
   for (int k = 0;; ++k) {
     ImpRes r;
-    double go[5], Pr[4];
-    ++ninv;
-    if (!urad_res<MET>(p, s, x, Pg, 1e-13, r, go, Pr, true)) break;
+    double go[5];
+    bool ok = false;
+#pragma unroll 1
+    for (int back = 0;; ++back) {
+      ++ninv;
+      ok = res(x, 1e-13, r, go, true);
+      if (ok || !have_prev || back >= 20 || ninv >= budget) break;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) x[i] = 0.5 * (x[i] + xprev[i]);
+    }
+    if (!ok) break;
 #pragma unroll
     for (int i = 0; i < 5; ++i) Pg[i] = go[i];
     if (r.eT < *best_eT) {
@@ -496,9 +571,14 @@ __device__ int newton_urad(const DevParams& p, const ImpSys<MET>& s, const doubl
     if (r.eI < 1e-9) eps = 1e-10;
     double J[4][4];
     bool jok = true;
+    const double umag = PRAD ? fmax(1.0, sqrt(fmax(s.g.sq3(x[1], x[2], x[3]), 0.0))) : 0.0;
 #pragma unroll 1
     for (int j = 0; j < 4 && jok; ++j) {
-      double scale = fabs(x[0]) * (j == 0 ? 1.0 : sqrt(s.g.gdd(j)));
+      double scale;
+      if (PRAD)
+        scale = j == 0 ? fabs(x[0]) : umag / sqrt(s.g.gdd(j));
+      else
+        scale = fabs(x[0]) * (j == 0 ? 1.0 : sqrt(s.g.gdd(j)));
       bool done = false;
 #pragma unroll 1
       for (double e = eps; e <= 0.3 && !done; e *= 10.0) {
@@ -507,9 +587,9 @@ __device__ int newton_urad(const DevParams& p, const ImpSys<MET>& s, const doubl
         double xp[4] = {x[0], x[1], x[2], x[3]};
         xp[j] += dj;
         ImpRes rp;
-        double go2[5], Pr2[4];
+        double go2[5];
         ++ninv;
-        if (urad_res<MET>(p, s, xp, Pg, 1e-2 * e, rp, go2, Pr2, false)) {
+        if (res(xp, 1e-2 * e, rp, go2, false)) {
           double id = 1.0 / dj;
 #pragma unroll
           for (int i = 0; i < 4; ++i) J[i][j] = (rp.Er[i] - r.Er[i]) * id;
@@ -524,19 +604,27 @@ __device__ int newton_urad(const DevParams& p, const ImpSys<MET>& s, const doubl
     double xn[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) xn[i] = x[i] - dx[i];
-    if (xn[0] > 0.0) xn[0] = -0.5 * fabs(xn[0]);
+    if (PRAD) {
+      if (xn[0] < 0.0) xn[0] = 0.5 * fabs(xn[0]);
+    } else {
+      if (xn[0] > 0.0) xn[0] = -0.5 * fabs(xn[0]);
+    }
     bool tiny = true;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
       if (fabs(xn[i] - x[i]) > 10.0 * 2.220446049250313e-16 * fabs(x[i])) tiny = false;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) x[i] = xn[i];
+    for (int i = 0; i < 4; ++i) {
+      xprev[i] = x[i];
+      x[i] = xn[i];
+    }
+    have_prev = true;
     ++steps;
     if (tiny) {
       ImpRes rf;
-      double go3[5], Pr3[4];
+      double go3[5];
       ++ninv;
-      if (urad_res<MET>(p, s, x, Pg, 1e-13, rf, go3, Pr3, true) && rf.eT < *best_eT) {
+      if (res(x, 1e-13, rf, go3, true) && rf.eT < *best_eT) {
         *best_eT = rf.eT;
 #pragma unroll
         for (int i = 0; i < 4; ++i) best_x[i] = x[i];
@@ -547,6 +635,12 @@ __device__ int newton_urad(const DevParams& p, const ImpSys<MET>& s, const doubl
     }
   }
   return steps;
+}
+
+template <int MET>
+__device__ __forceinline__ int newton_urad(const DevParams& p, const ImpSys<MET>& s, const double x0[4],
+                                           double Pg[5], double best_x[4], double best_Pg[5], double* best_eT) {
+  return newton_rad<MET, false>(p, s, x0, Pg, best_x, best_Pg, best_eT);
 }
 
 template <int MET, typename T = double>

@@ -826,6 +826,116 @@ __device__ __forceinline__ void pmhd_final(const DevParams& p, const ImpSysT<MET
   P[UR3] = Pr[3];
 }
 
+// Optical depth of a cell along its longest active proper edge, from the
+// primitives P (the tau < 2/3 guess rules of Sec. 4.10).
+template <int MET>
+__device__ __forceinline__ double zone_tau(const DevParams& p, const Geo<MET, double>& g, const double dx[3],
+                                           const double P[NPR], double kf) {
+  double kabs, ksca;
+  opacity<double>(p, P[RHO], P[UU], kf, &kabs, &ksca);
+  double dl = 0.0;
+#pragma unroll
+  for (int d = 1; d <= 3; ++d)
+    if (p.act[d - 1]) dl = fmax(dl, sqrt(g.gdd(d)) * dx[d - 1]);
+  return (kabs + ksca) * dl;
+}
+
+// The retry methods after PMHD (Sec. 4.10-4.11).  URAD from the PMHD iterate
+// where its e_T < 1e-4, else from P_s; then PRAD if neither reached 1e-9,
+// guessed from the better earlier solution where its e_T < 1e-4, else from
+// the optically thin limit (the M1 inversion of R*, no source) where
+// tau < 2/3, else from P_s.  The lowest-error solution wins (the earlier
+// method on ties); its primitives before the floors go to Pn.  px / peT: the
+// PMHD iterate and its error (inf if none).  Returns the outcome: ST_PMHD,
+// ST_URAD (URAD or PRAD), or ST_BACKUP when no residual was finite or the
+// best e_T exceeds 1e-7; *eT_out its error, *steps_out the Newton steps.
+template <int MET>
+__device__ int retry_sequence(const DevParams& p, const Geo<MET, double>& g, const ImpSys<MET>& s,
+                              const double Ps[NPR], const double px[4], double peT, double tau, double Pn[NPR],
+                              double* eT_out, int* steps_out) {
+  const bool pfin = isfinite(peT);
+  double Pb[NPR];
+  if (pfin) {  // the PMHD iterate as its error function left it (TYPE2 radiation)
+    ImpRes rr;
+    ImpState stt;
+    pmhd_res<MET>(p, s, px, rr, &stt, false);
+    Pb[RHO] = stt.rho;
+    Pb[UU] = px[0];
+    Pb[U1] = px[1];
+    Pb[U2] = px[2];
+    Pb[U3] = px[3];
+    Pb[B1] = s.B[0];
+    Pb[B2] = s.B[1];
+    Pb[B3] = s.B[2];
+    for (int q = 0; q < 4; ++q) Pb[ER + q] = stt.Pr[q];
+  }
+  const double* Pg = (pfin && peT < 1e-4) ? Pb : Ps;
+  double urc[4], urv[4], gr;
+  fourvel<MET, double>(g, Pg[UR1], Pg[UR2], Pg[UR3], urc, urv, &gr);
+  const double e43 = (4.0 / 3.0) * Pg[ER];
+  double xr[4];
+  xr[0] = e43 * urc[0] * urv[0] + Pg[ER] * (1.0 / 3.0);
+  for (int n = 1; n < 4; ++n) xr[n] = e43 * urc[0] * urv[n];
+  double gas[5] = {Pg[RHO], Pg[UU], Pg[U1], Pg[U2], Pg[U3]};
+  double ux[4], ugas[5], ueT;
+  int steps = newton_urad<MET>(p, s, xr, gas, ux, ugas, &ueT);
+  int best = pfin ? 0 : -1;
+  double beT = pfin ? peT : HUGE_VAL;
+  if (isfinite(ueT) && (best < 0 || ueT < beT)) {
+    best = 1;
+    beT = ueT;
+  }
+  double qx[4], qgas[5], qeT = HUGE_VAL;
+  if (!(beT < 1e-9)) {
+    double xq[4], gq[5];
+    if (best >= 0 && beT < 1e-4) {
+      if (best == 0) {
+        for (int q = 0; q < 4; ++q) xq[q] = Pb[ER + q];
+        for (int q = 0; q < 5; ++q) gq[q] = Pb[q];
+      } else {
+        rad_invert<MET>(p, g, ux, 2, xq);
+        for (int q = 0; q < 5; ++q) gq[q] = ugas[q];
+      }
+    } else {
+      if (tau < 2.0 / 3.0) {
+        rad_invert<MET>(p, g, s.Rs, 2, xq);
+      } else {
+        for (int q = 0; q < 4; ++q) xq[q] = Ps[ER + q];
+      }
+      for (int q = 0; q < 5; ++q) gq[q] = Ps[q];
+    }
+    steps += newton_rad<MET, true>(p, s, xq, gq, qx, qgas, &qeT);
+    if (isfinite(qeT) && (best < 0 || qeT < beT)) {
+      best = 2;
+      beT = qeT;
+    }
+  }
+  int method = ST_URAD;
+  if (best == 0) {
+    pmhd_final<MET>(p, s, px, Pn);
+    method = ST_PMHD;
+  } else if (best == 1) {
+    for (int q = 0; q < 5; ++q) Pn[q] = ugas[q];
+    double Pr[4];
+    if (rad_invert<MET>(p, g, ux, 2, Pr)) rad_invert<MET>(p, g, ux, 0, Pr);
+    for (int q = 0; q < 4; ++q) Pn[ER + q] = Pr[q];
+  } else if (best == 2) {
+    for (int q = 0; q < 5; ++q) Pn[q] = qgas[q];
+    for (int q = 0; q < 4; ++q) Pn[ER + q] = qx[q];
+  } else {
+    for (int q = 0; q < NPR; ++q) Pn[q] = Ps[q];
+    method = ST_BACKUP;
+    beT = HUGE_VAL;
+  }
+  Pn[B1] = s.B[0];
+  Pn[B2] = s.B[1];
+  Pn[B3] = s.B[2];
+  if (beT > 1e-7) method = ST_BACKUP;
+  *eT_out = beT;
+  *steps_out = steps;
+  return method;
+}
+
 // Metric derivatives for the geometric source: forward-mode pair (d/dx1, d/dx2).
 struct D2 {
   double v, a, b;
@@ -1305,10 +1415,9 @@ __global__ void k_imex_store(DevParams p, const BoxGeo* __restrict__ boxes, int 
 
 // ----------------------------------------------------------- retry (URAD)
 // Persistent grid over the retry queue (its length is read on the device, so
-// the launch needs no host round trip and can live in a CUDA graph).  URAD is
-// guessed from the PMHD solution when that reached e_T < 1e-4, else from P_s;
-// the lower-error of the two solutions is kept; e_T > 1e-7 sends the zone to
-// the neighbour-average back-up.
+// the launch needs no host round trip and can live in a CUDA graph): URAD,
+// then PRAD (retry_sequence); e_T > 1e-7 sends the zone to the
+// neighbour-average back-up.
 template <int MET>
 __global__ void __launch_bounds__(128) k_retry(DevParams p, const BoxGeo* __restrict__ boxes, Bufs b) {
   const int nq = b.qcount[0];
@@ -1339,69 +1448,12 @@ __global__ void __launch_bounds__(128) k_retry(DevParams p, const BoxGeo* __rest
     const double h = qd[17];
     ImpSys<MET> s;
     build_sys<MET>(p, g, Ust, h, kfield(p, K, t), s);
-    // PMHD iterate as the error function left it (TYPE2 radiation)
-    double Pb[NPR];
-    if (isfinite(peT)) {
-      ImpRes rr;
-      ImpState stt;
-      pmhd_res<MET>(p, s, px, rr, &stt, false);
-      Pb[RHO] = stt.rho;
-      Pb[UU] = px[0];
-      Pb[U1] = px[1];
-      Pb[U2] = px[2];
-      Pb[U3] = px[3];
-      Pb[B1] = s.B[0];
-      Pb[B2] = s.B[1];
-      Pb[B3] = s.B[2];
-      for (int q = 0; q < 4; ++q) Pb[ER + q] = stt.Pr[q];
-    }
-    const double* Pg = (isfinite(peT) && peT < 1e-4) ? Pb : Ps;
-    // R^t_nu of the guess radiation state
-    double urc[4], urv[4], gr;
-    fourvel<MET, double>(g, Pg[UR1], Pg[UR2], Pg[UR3], urc, urv, &gr);
-    double e43 = (4.0 / 3.0) * Pg[ER];
-    double xr[4];
-    xr[0] = e43 * urc[0] * urv[0] + Pg[ER] * (1.0 / 3.0);
-    for (int n = 1; n < 4; ++n) xr[n] = e43 * urc[0] * urv[n];
-    double gas[5] = {Pg[RHO], Pg[UU], Pg[U1], Pg[U2], Pg[U3]};
-    double bxn[4], bgas[5], beT;
-    int steps = newton_urad<MET>(p, s, xr, gas, bxn, bgas, &beT);
     const long long zg = bx.aoff + z;
+    double Pn[NPR], eT;
+    int steps;
+    const double tau = zone_tau<MET>(p, g, bx.dx, Ps, kfield(p, K, t));
+    const int method = retry_sequence<MET>(p, g, s, Ps, px, peT, tau, Pn, &eT, &steps);
     b.iters[zg] += steps;
-    double Pn[NPR];
-    int method;
-    double eT;
-    if (isfinite(beT) && (!isfinite(peT) || beT < peT)) {
-      Pn[RHO] = bgas[0];
-      Pn[UU] = bgas[1];
-      Pn[U1] = bgas[2];
-      Pn[U2] = bgas[3];
-      Pn[U3] = bgas[4];
-      Pn[B1] = s.B[0];
-      Pn[B2] = s.B[1];
-      Pn[B3] = s.B[2];
-      double Pr[4];
-      int neg = rad_invert<MET>(p, g, bxn, 2, Pr);
-      if (neg) rad_invert<MET>(p, g, bxn, 0, Pr);
-      Pn[ER] = Pr[0];
-      Pn[UR1] = Pr[1];
-      Pn[UR2] = Pr[2];
-      Pn[UR3] = Pr[3];
-      method = ST_URAD;
-      eT = beT;
-    } else if (isfinite(peT)) {
-      pmhd_final<MET>(p, s, px, Pn);
-      method = ST_PMHD;
-      eT = peT;
-    } else {
-      for (int q = 0; q < NPR; ++q) Pn[q] = Ps[q];
-      Pn[B1] = s.B[0];
-      Pn[B2] = s.B[1];
-      Pn[B3] = s.B[2];
-      method = ST_BACKUP;
-      eT = HUGE_VAL;
-    }
-    if (eT > 1e-7) method = ST_BACKUP;
     if (b.psol_rec)
       for (int q = 0; q < NPR; ++q) b.psol_rec[12 * bx.aoff + q * bx.nact + z] = Pn[q];
     apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn);

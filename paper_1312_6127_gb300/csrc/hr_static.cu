@@ -120,7 +120,7 @@ __global__ void k_zi_pmhd(hr::DevParams p, hr::BoxGeo bg, int n, const double* _
 }
 
 template <int MET>
-__global__ void k_zi_urad(hr::DevParams p, const double* __restrict__ x,
+__global__ void k_zi_urad(hr::DevParams p, hr::BoxGeo bg, const double* __restrict__ x,
                           const double* __restrict__ Us, const double* __restrict__ Ps,
                           const double* __restrict__ hh, double* Pout, double* eTo, int* itso,
                           unsigned char* meth, void* base) {
@@ -136,56 +136,10 @@ __global__ void k_zi_urad(hr::DevParams p, const double* __restrict__ x,
     zi_setup<MET>(p, z, x, Us, Ps, hh, g, s, P0);
     double bx[4] = {r[0], r[1], r[2], r[3]};
     const double beT = r[4];
-    double Pb[NPR];
-    if (isfinite(beT)) {
-      ImpRes rr;
-      ImpState stt;
-      pmhd_res<MET>(p, s, bx, rr, &stt, false);
-      Pb[RHO] = stt.rho;
-      Pb[UU] = bx[0];
-      Pb[U1] = bx[1];
-      Pb[U2] = bx[2];
-      Pb[U3] = bx[3];
-      for (int q = 0; q < 4; ++q) Pb[ER + q] = stt.Pr[q];
-    }
-    const double* Pg = (isfinite(beT) && beT < 1e-4) ? Pb : P0;
-    double urc[4], urv[4], gr;
-    fourvel<MET, double>(g, Pg[UR1], Pg[UR2], Pg[UR3], urc, urv, &gr);
-    double e43 = (4.0 / 3.0) * Pg[ER];
-    double xr[4];
-    xr[0] = e43 * urc[0] * urv[0] + Pg[ER] * (1.0 / 3.0);
-    for (int m = 1; m < 4; ++m) xr[m] = e43 * urc[0] * urv[m];
-    double gas[5] = {Pg[RHO], Pg[UU], Pg[U1], Pg[U2], Pg[U3]};
-    double ux[4], ugas[5], ueT;
-    int steps = newton_urad<MET>(p, s, xr, gas, ux, ugas, &ueT);
-    double Pn[NPR];
-    int method = 0;
-    double eT = beT;
-    if (isfinite(ueT) && (!isfinite(beT) || ueT < beT)) {
-      Pn[RHO] = ugas[0];
-      Pn[UU] = ugas[1];
-      Pn[U1] = ugas[2];
-      Pn[U2] = ugas[3];
-      Pn[U3] = ugas[4];
-      Pn[B1] = s.B[0];
-      Pn[B2] = s.B[1];
-      Pn[B3] = s.B[2];
-      double Pr[4];
-      int neg = rad_invert<MET>(p, g, ux, 2, Pr);
-      if (neg) rad_invert<MET>(p, g, ux, 0, Pr);
-      for (int q = 0; q < 4; ++q) Pn[ER + q] = Pr[q];
-      method = 1;
-      eT = ueT;
-    } else if (isfinite(beT)) {
-      pmhd_final<MET>(p, s, bx, Pn);
-    } else {
-      for (int q = 0; q < NPR; ++q) Pn[q] = P0[q];
-      Pn[B1] = s.B[0];
-      Pn[B2] = s.B[1];
-      Pn[B3] = s.B[2];
-      method = 2;
-    }
-    if (eT > 1e-7) method = 2;
+    double Pn[NPR], eT;
+    int steps;
+    const int method =
+        retry_sequence<MET>(p, g, s, P0, bx, beT, zone_tau<MET>(p, g, bg.dx, P0, 1.0), Pn, &eT, &steps);
     for (int q = 0; q < NPR; ++q) Pout[NPR * z + q] = Pn[q];
     if (eTo) eTo[z] = eT;
     if (itso) itso[z] += steps;
@@ -245,10 +199,10 @@ extern "C" int harmrad_zone_implicit_static(const harmrad_params* prm, int n, co
   int grid = hr::grid_for(n, sms, 128);
   if (dp.metric == 1) {
     k_zi_pmhd<hr::KS><<<grid, 128, 0, st>>>(dp, bg, n, x, Us, Ps, h, Pout, eT, iters, method, base);
-    k_zi_urad<hr::KS><<<sms * 2, 128, 0, st>>>(dp, x, Us, Ps, h, Pout, eT, iters, method, base);
+    k_zi_urad<hr::KS><<<sms * 2, 128, 0, st>>>(dp, bg, x, Us, Ps, h, Pout, eT, iters, method, base);
   } else {
     k_zi_pmhd<hr::MINK><<<grid, 128, 0, st>>>(dp, bg, n, x, Us, Ps, h, Pout, eT, iters, method, base);
-    k_zi_urad<hr::MINK><<<sms * 2, 128, 0, st>>>(dp, x, Us, Ps, h, Pout, eT, iters, method, base);
+    k_zi_urad<hr::MINK><<<sms * 2, 128, 0, st>>>(dp, bg, x, Us, Ps, h, Pout, eT, iters, method, base);
   }
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
     cudaGetLastError();
