@@ -4,7 +4,9 @@
 // equations T^t_nu(i+1) - T^t_nu(i) = h G_nu(i+1) (Eq. source3) with
 // rho0 u^t and B fixed, solved by a 4D Newton-Raphson (Eq. newton) with a
 // finite-difference Jacobian, first iterating the gas primitives (PMHD), then,
-// if the error is not acceptable, the radiation conserved quantities (URAD).
+// if the error is not acceptable, the radiation conserved quantities (URAD),
+// then the radiation primitives (PRAD); URAD first where the radiation is
+// extremely sub-dominant (Sec. 4.10).
 #include <algorithm>
 #include <cmath>
 #include <cstring>

@@ -4,7 +4,8 @@
 // Solves T^t_nu(x) - T*^t_nu = h G_nu(x) (Eq. source3) with rho0 u^t and B
 // fixed and the radiation taken from total energy-momentum conservation.
 // PMHD iterates the gas primitives x = (u_g, u~^i); URAD iterates x = R^t_nu
-// and recovers the gas from a 1D_W inversion inside every residual.  Newton
+// and PRAD x = (Ebar, u~^i_rad), both recovering the gas from a 1D_W
+// inversion inside every residual.  Newton
 // steps follow Eq. newton with D = 1 and a finite-difference Jacobian
 // (one-sided; the paper's two-sided PMHD differences belong to its staged
 // scheme, which is not used), normalised offset 1e-8, switching
