@@ -338,17 +338,18 @@ def wave_amplitude(rho, k):
     return 2.0 / N * np.sum((rho.ravel() - rho.mean()) * np.exp(1j * k * x))
 
 
-def thin_pulse(n=(32, 32, 32), L=100.0, w=5.0, T_a=1e6):
-    """Optically thin 3D radiation pulse (Sec. 5.3): kappa = 0, rho0 = 1,
-    gas temperature T_a, Ebar = a_rad T_a^4 (1 + 100 exp(-r^2/w^2))^4 in
-    radiation temperature, centred in a periodic box of side L.
-    Temperatures are in code units of m_b c^2/k_b."""
+def thin_pulse(n=(50, 50, 50), L=100.0, w=5.0, T_a=1e6, a_rad=8.77e-12):
+    """Optically thin 3D radiation pulse (Sec. 5, 3D Cartesian Minkowski):
+    kappa = 0, rho0 = 1, gas temperature T_a, radiation temperature
+    T_a (1 + 100 exp(-r^2/w^2)), Ebar = a_rad T_rad^4, centred in a periodic
+    box [-L/2, L/2)^3 of n zones per side.  Temperatures are in code units of
+    m_b c^2/k_b; a_rad = 8.77e-12 in these units as the paper gives it."""
     cfg = base_params()
     n1, n2, n3 = n
     cfg.update(n=list(n), x0=[-L / 2] * 3, dx=[L / n1, L / n2, L / n3],
                opacity=OPAC_CONST, kappa_abs0=0.0, kappa_es0=0.0)
     Tg = T_a / 1.0888e13  # K -> m_b c^2 / k_b
-    cfg["a_rad"] = 1.0
+    cfg["a_rad"] = a_rad
     zc = [cfg["x0"][i] + (np.arange(m) + 0.5) * cfg["dx"][i] for i, m in enumerate(n)]
     R2 = zc[2][:, None, None] ** 2 + zc[1][None, :, None] ** 2 + zc[0][None, None, :] ** 2
     P = np.zeros((NP, n3, n2, n1))

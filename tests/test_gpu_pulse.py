@@ -4,7 +4,9 @@ sub-dominant (Sec. 4.10) and the update kernel hands it to URAD in the retry
 kernel.  Against the oracle over 20 steps (radiation energy to 1e-6 of the
 peak, radiation velocity to 1e-6 of its largest value: URAD stops at
 e_T < 1e-9 on both sides), and against the closed-form diffusion solution at
-the times of the paper's figure as the oracle is (tests/test_oracle_pulse.py).
+the times of the paper's figure as the oracle is (tests/test_oracle_pulse.py);
+and the optically thin 3D pulse against the paper's printed peaks and the
+oracle.
 """
 import numpy as np
 
@@ -56,3 +58,40 @@ def test_thick_pulse_follows_diffusion_on_gpu():
         err = np.abs(E - Ex).max() / (Ex.max() - Ex.min())
         print("t = %.2f: err/peak %.3e" % (t, err))
         assert err < 3e-2
+
+
+def test_thin_pulse_matches_paper_and_oracle():
+    """The optically thin 3D pulse at 50^3 (Sec. 5; the paper's contour
+    ranges in tests/golden/thin_pulse.json): the CUDA step's peak -R^t_t
+    after free streaming to t = 15.21 and 35.01 is the paper's within 3 % and
+    7 % (the oracle's is 2.1 % and 5.4 % below), and at t = 15.21 it matches
+    the oracle zone by zone (URAD everywhere: 1e-6 of the peak)."""
+    import os
+    from tests.test_oracle_pulse import THIN, lab_energy
+    os.environ["ORACLE_THREADS"] = str(os.cpu_count() or 1)
+    cfg, P = W.thin_pulse()
+    g = H.Grid(cfg)
+    g.set_prims(P)
+    o = O.Oracle(cfg)
+    o.set_prims(P)
+    t = 0.0
+    c1, c2 = THIN["contours"][1], THIN["contours"][2]
+    while t < c1["t"] - 1e-9:
+        dt = min(o.cfl_dt(), c1["t"] - t)
+        assert g.cfl_dt() == pytest.approx(o.cfl_dt(), rel=1e-7)
+        o.step(dt)
+        g.step(dt)
+        t += dt
+    Eg, Eo = lab_energy(g.get_prims()), lab_energy(o.get_prims())
+    d = np.abs(Eg - Eo).max() / Eo.max()
+    print("t = %.2f: GPU peak %.4e, oracle %.4e, paper %.4e, max difference %.2e of the peak"
+          % (t, Eg.max(), Eo.max(), c1["max"], d))
+    assert d < 1e-6
+    assert abs(Eg.max() / c1["max"] - 1.0) < 0.03
+    while t < c2["t"] - 1e-9:
+        dt = min(g.cfl_dt(), c2["t"] - t)
+        g.step(dt)
+        t += dt
+    Eg = lab_energy(g.get_prims())
+    print("t = %.2f: GPU peak %.4e, paper %.4e" % (t, Eg.max(), c2["max"]))
+    assert abs(Eg.max() / c2["max"] - 1.0) < 0.07
