@@ -116,11 +116,14 @@ typedef struct harmrad_params {
   int integrator;      /* HARMRAD_INT_* */
 } harmrad_params;
 
-/* Per-zone outcome codes written by harmrad_get_status (worst over the three
- * stages of the last step). */
+/* Per-zone outcome codes written by harmrad_get_status (worst over the
+ * sub-steps of the last step).  Method sequence (Sec. 4.10): PMHD, then URAD,
+ * then PRAD, the lowest-error solution kept; a zone whose radiation is
+ * extremely sub-dominant (below 10 eps_m of the gas in conserved or
+ * fluid-frame energy) starts with URAD and skips PMHD. */
 #define HARMRAD_ZONE_PMHD 0    /* PMHD Newton accepted */
-#define HARMRAD_ZONE_URAD 1    /* URAD Newton accepted after PMHD */
-#define HARMRAD_ZONE_BACKUP 2  /* neither reached e_T <= 1e-7: neighbour average */
+#define HARMRAD_ZONE_URAD 1    /* a retry method (URAD or PRAD) gave the accepted solution */
+#define HARMRAD_ZONE_BACKUP 2  /* no method reached e_T <= 1e-7: neighbour average */
 
 typedef struct harmrad_stats {
   double dt;                   /* time step used by the last harmrad_step */
@@ -177,13 +180,14 @@ int harmrad_get_prims(harmrad_ctx* ctx, double* P, int on_device);
  * speed on the two d-faces of the zone (Sec. 4.4, last paragraph). */
 int harmrad_cfl_dt(harmrad_ctx* ctx, double* dt);
 
-/* Advance one full RK3 step.  dt <= 0 selects the CFL step of the current
+/* Advance one full step of the context's integrator (RK3 or an IMEX scheme).
+ * dt <= 0 selects the CFL step of the current
  * state (computed on the device).  The call only enqueues work on the
  * context's stream and does not wait for it; solver outcomes (back-up use,
  * iteration counts) are read afterwards with harmrad_get_stats. */
 int harmrad_step(harmrad_ctx* ctx, double dt);
 
-/* Advance one full RK3 step with host input and output: copies P_in (host,
+/* Advance one full step with host input and output: copies P_in (host,
  * active zones) to the device, steps with dt (<= 0: CFL), copies the result to
  * P_out (host).  P_in and P_out may alias. */
 int harmrad_step_host(harmrad_ctx* ctx, const double* P_in, double* P_out, double dt);
@@ -216,7 +220,8 @@ int harmrad_zone_physics(const harmrad_params* p, int n, const double* x, const 
 /* Implicit four-force solve of n independent zones (device pointers):
  * x[n][4], Ustar[n][12] explicit conserved state, Ps[n][12] guess primitives,
  * h[n] = b_s dt -> Pout[n][12], eT[n], iters[n], method[n] (HARMRAD_ZONE_*).
- * Same solver as harmrad_step (Sec. 4.7-4.11). */
+ * Same solver as harmrad_step (Sec. 4.7-4.11): PMHD, URAD, PRAD (the
+ * sub-dominance test needs no U^n but is not applied here: PMHD goes first). */
 int harmrad_zone_implicit(const harmrad_params* p, int n, const double* x, const double* Ustar,
                           const double* Ps, const double* h, double* Pout, double* eT, int* iters,
                           unsigned char* method, void* stream);
@@ -226,7 +231,7 @@ int harmrad_zone_implicit(const harmrad_params* p, int n, const double* x, const
  * framework's caching pool, a fixed-budget service) and may not call
  * cudaMalloc or cudaFree, whose implicit synchronisation they also cannot
  * afford.  The paper has no counterpart; this is a deployment variant.
- * The zones that PMHD does not accept are queued for URAD in a fixed array in
+ * The zones that PMHD does not accept are queued for URAD/PRAD in a fixed array in
  * the library's static device memory (about 2.9 MB per device that loads the
  * library, kept until the process exits); the call makes no device
  * allocation.  n must not exceed 65536 (HARMRAD_E_ARG otherwise).  The first
@@ -248,7 +253,7 @@ int harmrad_zone_implicit_static(const harmrad_params* p, int n, const double* x
 #define HARMRAD_K_FACE 3      /* face physics + Riemann flux */
 #define HARMRAD_K_CT 4        /* flux-CT EMFs */
 #define HARMRAD_K_UPDATE 5    /* update + geometric source + PMHD implicit solve */
-#define HARMRAD_K_RETRY 6     /* URAD retry queue */
+#define HARMRAD_K_RETRY 6     /* retry queue (URAD, PRAD) */
 #define HARMRAD_K_BACKUP 7    /* neighbour-average back-up */
 #define HARMRAD_K_CFL 8       /* CFL reduction */
 #define HARMRAD_K_OTHER 9     /* memsets, time-step upload */
