@@ -220,8 +220,7 @@ int harmrad_zone_physics(const harmrad_params* p, int n, const double* x, const 
 /* Implicit four-force solve of n independent zones (device pointers):
  * x[n][4], Ustar[n][12] explicit conserved state, Ps[n][12] guess primitives,
  * h[n] = b_s dt -> Pout[n][12], eT[n], iters[n], method[n] (HARMRAD_ZONE_*).
- * Same solver as harmrad_step (Sec. 4.7-4.11): PMHD, URAD, PRAD (the
- * sub-dominance test needs no U^n but is not applied here: PMHD goes first). */
+ * Same solver and method sequence as harmrad_step (Sec. 4.7-4.11). */
 int harmrad_zone_implicit(const harmrad_params* p, int n, const double* x, const double* Ustar,
                           const double* Ps, const double* h, double* Pout, double* eT, int* iters,
                           unsigned char* method, void* stream);

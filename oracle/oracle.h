@@ -128,8 +128,7 @@ int    orc_gas_invert(const orc_params* p, const double* x, const double* U,
 int    orc_radiation_subdominant(const orc_params* p, const double* x, const double* Ustar,
                                  const double* Ps);
 /* Implicit four-force solve of one zone: U* (12, densitised), guess P_s,
- * h = b_s*dt, PMHD-first sequence (the grid step's sub-dominance test is
- * not applied here).  Writes the new prims and info. */
+ * h = b_s*dt, the grid step's method sequence.  Writes the new prims and info. */
 void   orc_implicit_zone(const orc_params* p, const double* x, const double* Ustar,
                          const double* Ps, double h, double* Pout,
                          orc_implicit_info* info);

@@ -912,7 +912,7 @@ void orc_implicit_zone(const orc_params* p, const double* x, const double* Ustar
                        double h, double* Pout, orc_implicit_info* info) {
   Geom G;
   geom_at(*p, x[1], x[2], x[3], G);
-  implicit_zone(*p, G, Ustar, Ps, h, Pout, info, false);
+  implicit_zone(*p, G, Ustar, Ps, h, Pout, info, radiation_subdominant(G, Ustar, Ps));
 }
 
 void orc_method_zone(const orc_params* p, const double* x, const double* Ustar, const double* Ps, double h,

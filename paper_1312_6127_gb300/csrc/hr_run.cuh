@@ -328,8 +328,9 @@ __global__ void k_zone_implicit(DevParams p, BoxGeo bg, int n, const double* __r
         x0[3] = go[4];
       }
     }
-    double bx[4], beT;
-    int steps = newton_pmhd<MET>(p, s, x0, bx, &beT);
+    double bx[4] = {0.0, 0.0, 0.0, 0.0}, beT = HUGE_VAL;
+    // extremely sub-dominant radiation (Sec. 4.10): no PMHD attempt
+    int steps = radiation_subdominant<MET>(g, Ust, P0) ? 0 : newton_pmhd<MET>(p, s, x0, bx, &beT);
     double Pn[NPR];
     int method = 0;
     double eT = beT;

@@ -100,8 +100,9 @@ __global__ void k_zi_pmhd(hr::DevParams p, hr::BoxGeo bg, int n, const double* _
         x0[3] = go[4];
       }
     }
-    double bx[4], beT;
-    int steps = newton_pmhd<MET>(p, s, x0, bx, &beT);
+    double bx[4] = {0.0, 0.0, 0.0, 0.0}, beT = HUGE_VAL;
+    // extremely sub-dominant radiation (Sec. 4.10): no PMHD attempt
+    int steps = radiation_subdominant<MET>(g, Us + NPR * (size_t)z, P0) ? 0 : newton_pmhd<MET>(p, s, x0, bx, &beT);
     if (itso) itso[z] = steps;
     if (beT < 1e-9) {
       double Pn[NPR];
