@@ -109,6 +109,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def job_time_ms(ms_local, dist, device):
+    """The job's timed-region length: the maximum over ranks of each rank's
+    milliseconds (every rank receives it); ms_local itself on one process."""
+    if dist is None:
+        return ms_local
+    import torch
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, steps, ws, ms):
+    """Whole-job zone-cycles/s: the units all ranks advanced (each rank runs
+    its own replica of the workload) over the max-over-ranks time."""
+    return units_per_rank * steps * ws / (ms / 1e3)
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -246,12 +263,9 @@ def main():
         dist.barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = job_time_ms(ms, dist, "cuda")
     st = g.stats()
-    value = nact * args.steps * ws / (ms / 1e3)
+    value = job_throughput(nact, args.steps, ws, ms)
 
     # per-kernel device times of one eager step (events on the launching stream)
     roofline = None
