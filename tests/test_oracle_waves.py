@@ -68,3 +68,16 @@ def test_oracle_linear_wave_omega(case):
           % (case, w_re, w_im, mode["omega"][0], mode["omega"][1], e_re, e_im))
     assert e_re < 1e-4
     assert e_im < 2e-2
+
+
+@pytest.mark.parametrize("integrator", [W.IMEX2, W.IMEX2B, W.IMEX3])
+@pytest.mark.parametrize("case", ["a_sound", "a_fast", "a_slow", "c_sound", "b_sound"])
+def test_oracle_linear_wave_omega_imex(case, integrator):
+    """The printed eigenvalues with the IMEX integrators of Sec. 4.1 in place
+    of RK3: the same tolerances (at 128 zones the spatial error dominates)."""
+    mode = GOLD["cases"][case]
+    cfg, P = W.linear_wave(N, GOLD["background"], mode)
+    cfg["integrator"] = integrator
+    w_re, w_im = measure_omega(OracleStepper(cfg, P), cfg, P, mode["omega"][0])
+    assert abs(w_re / mode["omega"][0] - 1) < 1e-4
+    assert abs(w_im / mode["omega"][1] - 1) < 2e-2
