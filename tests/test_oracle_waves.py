@@ -25,6 +25,16 @@ from paper_1312_6127_gb300 import workloads as W
 
 GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "linear_waves.json")))
 N = 128
+CASES = list(GOLD["cases"])
+
+
+def tolerance(case):
+    """Relative tolerances on (Re omega, Im omega) at 128 zones: 1e-4 and 2e-2;
+    3e-3 and 2e-2 for panel (d), optically thick and radiation dominated,
+    whose modes lose 60-78 % of their amplitude in one period, so that the
+    measured phase carries the scheme's damping error too (the oracle's
+    errors there are 2e-4 to 1.8e-3)."""
+    return (3e-3, 2e-2) if case.startswith("d_") else (1e-4, 2e-2)
 
 
 def measure_omega(stepper, cfg, P, omega_re):
@@ -57,7 +67,7 @@ class OracleStepper:
         return self.o.get_prims()[0]
 
 
-@pytest.mark.parametrize("case", ["a_sound", "a_fast", "a_slow", "c_sound", "b_sound"])
+@pytest.mark.parametrize("case", CASES)
 def test_oracle_linear_wave_omega(case):
     mode = GOLD["cases"][case]
     cfg, P = W.linear_wave(N, GOLD["background"], mode)
@@ -66,8 +76,9 @@ def test_oracle_linear_wave_omega(case):
     e_im = abs(w_im / mode["omega"][1] - 1)
     print("%s: omega %.6f + %.6f i (paper %.6f + %.6f i): rel err %.1e, %.1e"
           % (case, w_re, w_im, mode["omega"][0], mode["omega"][1], e_re, e_im))
-    assert e_re < 1e-4
-    assert e_im < 2e-2
+    t_re, t_im = tolerance(case)
+    assert e_re < t_re
+    assert e_im < t_im
 
 
 @pytest.mark.parametrize("integrator", [W.IMEX2, W.IMEX2B, W.IMEX3])
