@@ -92,3 +92,21 @@ def test_oracle_linear_wave_omega_imex(case, integrator):
     w_re, w_im = measure_omega(OracleStepper(cfg, P), cfg, P, mode["omega"][0])
     assert abs(w_re / mode["omega"][0] - 1) < 1e-4
     assert abs(w_im / mode["omega"][1] - 1) < 2e-2
+
+
+@pytest.mark.parametrize("case,order", [("a_sound", 2.0), ("c_fast", 2.0), ("d_sound", 0.9)])
+def test_oracle_spatial_convergence(case, order):
+    """Error of the measured omega against the printed one at 32, 64 and 128
+    zones: the optically thin modes converge at least at second order (PPM on
+    a smooth wave), the optically thick radiation-dominated mode at first
+    order (the paper: the stiff terms are first order in space for optically
+    thick waves, and its convergence figure shows both slopes)."""
+    mode = GOLD["cases"][case]
+    errs = []
+    for n in (32, 64, 128):
+        cfg, P = W.linear_wave(n, GOLD["background"], mode)
+        w_re, w_im = measure_omega(OracleStepper(cfg, P), cfg, P, mode["omega"][0])
+        errs.append(abs(complex(w_re, w_im) - complex(*mode["omega"])) / abs(complex(*mode["omega"])))
+    p = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    print(case, errs, p)
+    assert np.all(p > order), p
