@@ -9,9 +9,12 @@ state is resident in HBM; its working set (primitives, fluxes, scratch) is far
 larger than the 129 MB L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|split]
-                  [--impl harmrad|reference]
+                  [--workload torus|batch48] [--impl harmrad|reference]
 
-Prints one JSON line.  The reference arm times the FP64 CPU oracle (the plain
+Prints one JSON line.  The default run (FP64 torus, one GPU) also times split
+precision on the same torus ("split", with its conserved totals against FP64)
+and the batch of 48 uneven boxes ("batch48"), each with its own clocks and
+roofline.  The reference arm times the FP64 CPU oracle (the plain
 restatement of the method used by the tests) on the host cores.
 """
 import argparse
@@ -31,7 +34,8 @@ sys.path.insert(0, ROOT)
 METRIC = "GRRMHD+M1 zone-cycles/s at 256x128x64 (FP64 vs split); frac of HBM roofline"
 UNIT = "zone-cycles/s"
 # FP64 peak of a GB300 from its unit counts and clock: 152 SMs x 2 FP64 FMA per
-# clock x 2 flops x 2.07 GHz = 1.26 TFLOP/s (the nominal 1.25 TFLOP/s).
+# clock x 2 flops x 2.07 GHz = 1.26 TFLOP/s (the nominal 1.25 TFLOP/s); the
+# roofline divides by the rate measured live, this figure is reported beside it.
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 PROFILE_JSON = os.path.join(ROOT, "profiles", "k_update_counters.json")
 INTEGRATORS = {"rk3": 0, "imex2": 1, "imex2b": 2, "imex3": 3}
@@ -185,6 +189,144 @@ def run_reference(args, ws, rank):
     return 0
 
 
+def fp64_peak(H):
+    """FP64 peak for the roofline: the device's FMA rate measured live by the
+    library's FMA-chain kernel (harmrad_fp64_fma_rate), best of 5 launches."""
+    try:
+        return H.fp64_fma_rate(5), "measured: harmrad_fp64_fma_rate (independent DFMA chains, best of 5)"
+    except Exception as ex:  # the derived figure is reported instead, and said so
+        return FP64_PEAK_GFLOPS / 1e3, "derived from unit counts (probe failed: %s)" % ex
+
+
+def make_context(args, H, W, workload, prec, stream, rank, integ):
+    """The workload's context with its state loaded: (grid, active zones,
+    workload text, counters key)."""
+    n = tuple(int(x) for x in args.size.split(","))
+    pname = "split" if prec == H.PREC_SPLIT else "fp64"
+    if workload == "torus":
+        cfg, P = W.torus(n, seed=12345 + rank)
+        cfg["integrator"] = integ
+        g = H.Grid(cfg, precision=prec, stream=stream)
+        g.set_prims(P)
+        g.cfg_init, g.P_init = cfg, P
+        wl = "KS torus a=0.9375 %dx%dx%d (PPM, LAXF, flux-CT, PMHD/URAD)" % n
+        return g, n[0] * n[1] * n[2], wl, (list(n), pname)
+    cfgs, Ps, Ks = W.box_batch(seed=4242 + rank)
+    cfgs = [dict(c, integrator=integ) for c in cfgs]
+    g = H.Batch(cfgs, precision=prec, stream=stream)
+    g.set_prims(Ps)
+    g.set_opacity_field(Ks)
+    wl = ("48 periodic Minkowski boxes, edges log-uniform 32..128 (%d zones), per-zone "
+          "absorption with optical depth per cell log-uniform 1e-4..1e6, one batched context" % g.nact)
+    return g, g.nact, wl, ("batch48", "batch48_" + pname)
+
+
+def time_steps(g, args, stream, dist, local):
+    """W warm-up steps, then K timed CUDA-graph steps bracketed by a barrier
+    and a synchronize; clocks sampled during the timed region."""
+    import torch
+    for _ in range(args.warmup):
+        g.step(0.0)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        g.step(0.0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    return ms, clocks.stop()
+
+
+def kernel_roofline(g, nact, key, integ, peak_tf, peak_note, ms, steps):
+    """Roofline of the dominant kernel (the update kernel: update, geometric
+    source and PMHD Newton) from one eager step timed per kernel with CUDA
+    events on the context's stream, and the HBM view of the whole step."""
+    kt = g.profile_step(0.0)
+    upd_ms, upd_n = kt["update"]
+    avg_ms = upd_ms / max(upd_n, 1)
+    try:
+        with open(PROFILE_JSON) as fh:
+            prof = json.load(fh)
+    except (OSError, ValueError):
+        prof = {}
+    size_key, prof_key = key
+    entry = prof.get(prof_key, {})
+    # the counters are those of the RK3 update kernel of this build
+    fresh = (entry.get("kernel_hash") == kernel_hash() and entry.get("size") == size_key and integ == 0)
+    flops_per_zone = entry.get("fp64_flops_per_zone_stage")
+    traffic = entry.get("dram_bytes_per_launch") if fresh else None
+    derived = FP64_PEAK_GFLOPS / 1e3
+    roof = {"bound": "alu", "achieved": None, "peak": peak_tf, "unit": "TFLOP/s", "frac": None,
+            "traffic": traffic, "kernel": "k_update (update + geometric source + PMHD Newton)",
+            "kernel_ms": avg_ms, "kernel_share": upd_ms / max(sum(v[0] for v in kt.values()), 1e-30),
+            "counters_fresh": fresh, "peak_note": peak_note,
+            "peak_derived": derived}
+    if flops_per_zone and fresh:
+        achieved = flops_per_zone * nact / (avg_ms / 1e3) / 1e12
+        roof.update(achieved=achieved, frac=achieved / peak_tf, frac_of_derived=achieved / derived,
+                    fp64_flops_per_zone_stage=flops_per_zone,
+                    fp64_pipe_active_pct=entry.get("fp64_pipe_active_pct"),
+                    counters_captured_size=entry.get("captured_size"),
+                    achieved_note="(2 DFMA + DMUL + DADD) thread instructions per zone-stage from ncu x "
+                                  "zones / CUDA-event launch time")
+    else:
+        roof["note"] = ("FP64 op counts of this kernel build are not in profiles/k_update_counters.json"
+                        if integ == 0 else "FP64 op counts are captured for the RK3 update kernel only")
+    hbm = measured_peaks().get("hbm_gbs")
+    step_ms = ms / steps
+    gbs = 960.0 * nact / (step_ms / 1e3) / 1e9
+    roof["step_hbm"] = {"algorithmic_bytes_per_zone_cycle": 960, "achieved_gbs": gbs, "peak_gbs": hbm,
+                        "frac": gbs / hbm if hbm else None}
+    return roof, kt
+
+
+def conserved_totals(H, cfg, Pd):
+    """Mass, total energy and total momenta (gas + radiation) of a state,
+    with the absolute sums they are measured against (point-wise physics
+    entry of the library)."""
+    import torch
+    n1, n2, n3 = cfg["n"]
+    kk, jj, ii = np.meshgrid(np.arange(n3), np.arange(n2), np.arange(n1), indexing="ij")
+    x = np.zeros((n3 * n2 * n1, 4))
+    x[:, 1] = cfg["x0"][0] + (ii.ravel() + 0.5) * cfg["dx"][0]
+    x[:, 2] = cfg["x0"][1] + (jj.ravel() + 0.5) * cfg["dx"][1]
+    x[:, 3] = cfg["x0"][2] + (kk.ravel() + 0.5) * cfg["dx"][2]
+    U = H.zone_physics(cfg, x, Pd.reshape(12, -1).T.cpu().numpy())[0]
+    tot, ab = U.sum(axis=0), np.abs(U).sum(axis=0)
+    pick = lambda t: np.array([t[0], t[1] + t[8], t[2] + t[9], t[3] + t[10], t[4] + t[11]])
+    return pick(tot), pick(ab)
+
+
+def split_total_errors(H, g64, g32, steps):
+    """Both precisions from the same initial state with the FP64 run's CFL
+    steps: each conserved total of split precision against FP64, relative to
+    the total's absolute sum (outside any timed region)."""
+    cfg, P = g64.cfg_init, g64.P_init
+    g64.set_prims(P)
+    g32.set_prims(P)
+    dts = []
+    for _ in range(steps):
+        g64.step(0.0)
+        dts.append(g64.stats()["dt"])
+    for dt in dts:
+        g32.step(dt)
+    t64, s64 = conserved_totals(H, cfg, g64.get_prims(device=True))
+    t32, _ = conserved_totals(H, cfg, g32.get_prims(device=True))
+    rel = np.abs(t32 - t64) / s64
+    return {"steps": steps, "quantities": ["mass", "energy", "momentum_1", "momentum_2", "momentum_3"],
+            "rel_to_abs_sum": [float(v) for v in rel], "max": float(rel.max())}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -202,6 +344,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the split-precision and batch48 sub-measurements of the default run")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -222,93 +366,17 @@ def main():
     prec = H.PREC_SPLIT if args.precision == "split" else H.PREC_FP64
     stream = torch.cuda.current_stream()
     integ = INTEGRATORS[args.integrator]
-    if args.workload == "torus":
-        cfg, P = W.torus(n, seed=12345 + rank)
-        cfg["integrator"] = integ
-        nact = n[0] * n[1] * n[2]
-        g = H.Grid(cfg, precision=prec, stream=stream)
-        g.set_prims(P)
-        wl = "KS torus a=0.9375 %dx%dx%d (PPM, LAXF, flux-CT, PMHD/URAD)" % n
-        size_key, prof_key = list(n), args.precision
-    else:
-        cfgs, Ps, Ks = W.box_batch(seed=4242 + rank)
-        cfgs = [dict(c, integrator=integ) for c in cfgs]
-        g = H.Batch(cfgs, precision=prec, stream=stream)
-        g.set_prims(Ps)
-        g.set_opacity_field(Ks)
-        nact = g.nact
-        del Ps, Ks
-        wl = ("48 periodic Minkowski boxes, edges log-uniform 32..128 (%d zones), per-zone "
-              "absorption with optical depth per cell log-uniform 1e-4..1e6, one batched context"
-              % nact)
-        size_key, prof_key = "batch48", "batch48_" + args.precision
+    peak_tf, peak_note = fp64_peak(H)
+    g, nact, wl, key = make_context(args, H, W, args.workload, prec, stream, rank, integ)
     tuning = g.tuning() if args.no_autotune else g.autotune(reps=1)
-    for _ in range(args.warmup):
-        g.step(0.0)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clocks = ClockSampler(local)
-    clocks.start()
-    time.sleep(0.3)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
-        g.step(0.0)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ms = e0.elapsed_time(e1)
-    clk = clocks.stop()
+    ms, clk = time_steps(g, args, stream, dist, local)
     ms = job_time_ms(ms, dist, "cuda")
     st = g.stats()
     value = job_throughput(nact, args.steps, ws, ms)
 
-    # per-kernel device times of one eager step (events on the launching stream)
-    roofline = None
-    kt = None
+    roofline, kt = None, None
     if not args.no_profile:
-        kt = g.profile_step(0.0)
-        upd_ms, upd_n = kt["update"]
-        avg_ms = upd_ms / max(upd_n, 1)
-        prof = {}
-        try:
-            with open(PROFILE_JSON) as fh:
-                prof = json.load(fh)
-        except (OSError, ValueError):
-            prof = {}
-        entry = prof.get(prof_key, {})
-        # the counters are those of the RK3 update kernel
-        fresh = (entry.get("kernel_hash") == kernel_hash() and entry.get("size") == size_key
-                 and integ == 0)
-        flops_per_zone = entry.get("fp64_flops_per_zone_stage")
-        traffic = entry.get("dram_bytes_per_launch") if fresh else None
-        if flops_per_zone and fresh:
-            achieved = flops_per_zone * nact / (avg_ms / 1e3) / 1e12
-            roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS / 1e3,
-                        "unit": "TFLOP/s", "frac": achieved / (FP64_PEAK_GFLOPS / 1e3),
-                        "traffic": traffic, "kernel": "k_update (update + PMHD Newton)",
-                        "kernel_ms": avg_ms, "counters_fresh": fresh,
-                        "fp64_pipe_active_pct": entry.get("fp64_pipe_active_pct"),
-                        "peak_note": "FP64 from unit counts: 152 SM x 2 DFMA/clk x 2 x 2.07 GHz; "
-                                     "achieved counts DFMA/DMUL/DADD only"}
-        else:
-            roofline = {"bound": "alu", "achieved": None, "peak": FP64_PEAK_GFLOPS / 1e3,
-                        "unit": "TFLOP/s", "frac": None, "traffic": traffic,
-                        "kernel": "k_update", "kernel_ms": avg_ms,
-                        "note": "FP64 op count per zone not captured for this kernel build "
-                                "(profiles/k_update_counters.json kernel_hash differs)" if integ == 0 else
-                                "FP64 op counts are captured for the RK3 update kernel only"}
-        # HBM view of the whole step: algorithmic bytes per zone-cycle
-        hbm = measured_peaks().get("hbm_gbs")
-        step_ms = ms / args.steps
-        alg_bytes = 960.0 * nact
-        roofline["step_hbm"] = {"algorithmic_bytes_per_zone_cycle": 960, "achieved_gbs":
-                                alg_bytes / (step_ms / 1e3) / 1e9, "peak_gbs": hbm,
-                                "frac": (alg_bytes / (step_ms / 1e3) / 1e9) / hbm if hbm else None}
+        roofline, kt = kernel_roofline(g, nact, key, integ, peak_tf, peak_note, ms, args.steps)
 
     # end to end through the C ABI with host buffers: H2D + step + D2H per step
     e2e = None
@@ -328,6 +396,33 @@ def main():
         nbytes = size * 8
         e2e = {"value": nact * args.steps * ws / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes}
+
+    # the default run also measures split precision on the same torus and the
+    # batch of 48 boxes (same steps and warm-up, each timed on its own)
+    extras = {}
+    default_run = (args.workload == "torus" and prec == H.PREC_FP64 and integ == 0 and ws == 1)
+    if default_run and not args.no_extras:
+        for name, wk, pr in (("split", "torus", H.PREC_SPLIT), ("batch48", "batch48", H.PREC_FP64)):
+            gx, nx, wlx, keyx = make_context(args, H, W, wk, pr, stream, rank, integ)
+            tx = gx.tuning() if args.no_autotune else gx.autotune(reps=1)
+            msx, clkx = time_steps(gx, args, stream, None, local)
+            stx = gx.stats()
+            sub = {"value": job_throughput(nx, args.steps, 1, msx), "unit": UNIT,
+                   "ms_per_step": msx / args.steps, "workload": wlx, "zones": nx,
+                   "dtype": "f64+f32" if pr == H.PREC_SPLIT else "f64", "clocks": clkx,
+                   "launch_shapes": {k: v for k, v in tx.items() if not k.endswith("_ms")},
+                   "solver": {"newton_iters_per_solve": stx["newton_iters"] / max(stx["zone_stages"], 1),
+                              "pmhd": stx["pmhd_ok"], "urad": stx["urad_ok"], "backup": stx["backup"]}}
+            if not args.no_profile:
+                sub["roofline"], ktx = kernel_roofline(gx, nx, keyx, integ, peak_tf, peak_note, msx,
+                                                       args.steps)
+                sub["kernel_ms"] = {k: round(v[0], 4) for k, v in ktx.items()}
+            if name == "split":
+                sub["vs_fp64"] = value and sub["value"] / value
+                sub["conserved_totals_vs_fp64"] = split_total_errors(H, g, gx, args.steps)
+            extras[name] = sub
+            del gx
+            torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu and args.workload == "torus":
@@ -362,6 +457,7 @@ def main():
         }
         if kt:
             line["kernel_ms"] = {k: round(v[0], 4) for k, v in kt.items()}
+        line.update(extras)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -235,7 +235,9 @@ int harmrad_zone_implicit(const harmrad_params* p, int n, const double* x, const
  * library, kept until the process exits); the call makes no device
  * allocation.  n must not exceed 65536 (HARMRAD_E_ARG otherwise).  The first
  * call on a device looks up that array's device address, so make it before
- * any stream capture.  The array is shared by every call on the device and
+ * any stream capture; the address is kept per device together with the id of
+ * the CUDA context it belongs to, and looked up again by the first call in a
+ * new context (after a device reset).  The array is shared by every call on the device and
  * keeps the last call's contents (each call clears its queue counter first):
  * calls whose work overlaps on the GPU race, so serialise them, e.g. on one
  * stream.  Arguments, layouts and outputs as for harmrad_zone_implicit; the
@@ -324,6 +326,15 @@ int harmrad_autotune(harmrad_ctx* ctx, int reps, harmrad_tuning* out);
  * HARMRAD_E_ARG; the captured graphs are dropped). */
 int harmrad_get_tuning(harmrad_ctx* ctx, harmrad_tuning* out);
 int harmrad_set_tuning(harmrad_ctx* ctx, const harmrad_tuning* t);
+
+/* FP64 fused multiply-add rate of the current device in TFLOP/s (2 flops per
+ * FMA), measured on the given stream by a kernel of independent FMA chains
+ * (8 per thread, 8 blocks of 256 threads per SM, 4096 rounds): the best of
+ * reps timed launches after one warm-up, CUDA events around each.  It is the
+ * FP64 peak that the roofline fraction of the FP64-bound kernels divides by;
+ * no step of the method uses it.  Allocates and frees a small scratch buffer;
+ * synchronises the stream.  HARMRAD_E_ARG unless 1 <= reps <= 100. */
+int harmrad_fp64_fma_rate(int reps, double* tflops, void* stream);
 
 /* Human-readable text of a return code. */
 const char* harmrad_strerror(int code);

@@ -12,6 +12,7 @@
 #include <math.h>
 
 #include <atomic>
+#include <mutex>
 
 #include "../../include/harmrad.h"
 #include "hr_common.cuh"
@@ -33,10 +34,47 @@ constexpr size_t kScratchBytes = kHeader + kIdxBytes + kRecBytes;  // about 2.9 
 
 static __device__ __align__(256) unsigned char g_zi_scratch[kScratchBytes];
 
-// Device address of g_zi_scratch, looked up once per device (host code may
-// not use the symbol itself: on the host it names a stand-in, not device memory).
+// Device address of g_zi_scratch, looked up once per device and context (host
+// code may not use the symbol itself: on the host it names a stand-in, not
+// device memory).  The address belongs to the module loaded in the device's
+// current context; a device reset destroys that context and the next one
+// loads the module again, possibly elsewhere.  So each entry remembers the
+// unique id of the context it was looked up in, and a call made in another
+// context looks the address up again.
 constexpr int kMaxDevices = 64;
-std::atomic<void*> g_scratch_addr[kMaxDevices];
+struct ScratchAddr {
+  std::atomic<unsigned long long> ctx_id{0};  // 0: not looked up yet
+  std::atomic<void*> addr{nullptr};
+};
+ScratchAddr g_scratch_addr[kMaxDevices];
+std::mutex g_scratch_mu;
+
+// Driver entry points for the current context's id, reached through the
+// runtime (no link against the driver library).
+using PfnCtxGetCurrent = int (*)(void**);
+using PfnCtxGetId = int (*)(void*, unsigned long long*);
+
+int current_context_id(unsigned long long* id) {
+  static PfnCtxGetCurrent get_current = nullptr;
+  static PfnCtxGetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = (PfnCtxGetCurrent)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = (PfnCtxGetId)f;
+    cudaGetLastError();
+  });
+  void* ctx = nullptr;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, id) != 0 || *id == 0)
+    return HARMRAD_E_CUDA;
+  return HARMRAD_OK;
+}
 
 struct QueueView {
   int* count;
@@ -148,7 +186,8 @@ __global__ void k_zi_urad(hr::DevParams p, hr::BoxGeo bg, const double* __restri
   }
 }
 
-// Device address of the static queue on the current device (set-up on first use).
+// Device address of the static queue on the current device (set-up on the
+// first call in each context of the device).
 int scratch_address(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -156,15 +195,29 @@ int scratch_address(void** out) {
     return HARMRAD_E_CUDA;
   }
   if (dev < 0 || dev >= kMaxDevices) return HARMRAD_E_ARG;
-  void* a = g_scratch_addr[dev].load(std::memory_order_acquire);
-  if (!a) {
-    if (cudaGetSymbolAddress(&a, g_zi_scratch) != cudaSuccess || !a) {
-      cudaGetLastError();
-      return HARMRAD_E_CUDA;
-    }
-    g_scratch_addr[dev].store(a, std::memory_order_release);
+  // bind the device's primary context to this thread (it exists already: the
+  // caller's buffers live in it), so that the driver reports it as current
+  if (cudaSetDevice(dev) != cudaSuccess) {
+    cudaGetLastError();
+    return HARMRAD_E_CUDA;
   }
-  *out = a;
+  unsigned long long id = 0;
+  int rc = current_context_id(&id);
+  if (rc) return rc;
+  ScratchAddr& e = g_scratch_addr[dev];
+  if (e.ctx_id.load(std::memory_order_acquire) != id) {
+    std::lock_guard<std::mutex> lk(g_scratch_mu);
+    if (e.ctx_id.load(std::memory_order_acquire) != id) {
+      void* a = nullptr;
+      if (cudaGetSymbolAddress(&a, g_zi_scratch) != cudaSuccess || !a) {
+        cudaGetLastError();
+        return HARMRAD_E_CUDA;
+      }
+      e.addr.store(a, std::memory_order_release);
+      e.ctx_id.store(id, std::memory_order_release);
+    }
+  }
+  *out = e.addr.load(std::memory_order_acquire);
   return HARMRAD_OK;
 }
 

@@ -26,7 +26,7 @@ EXPORTS = [
     "harmrad_get_status", "harmrad_get_iters", "harmrad_compute_fluxes",
     "harmrad_zone_physics", "harmrad_zone_implicit", "harmrad_zone_implicit_static",
     "harmrad_profile_step", "harmrad_autotune", "harmrad_get_tuning", "harmrad_set_tuning",
-    "harmrad_adjoint_enable", "harmrad_step_adjoint",
+    "harmrad_adjoint_enable", "harmrad_step_adjoint", "harmrad_fp64_fma_rate",
     "harmrad_strerror",
 ]
 KERNEL_CLASSES = ["bc", "prep", "flatten", "face", "ct", "update", "retry", "backup", "cfl", "other",
@@ -138,6 +138,7 @@ def load(path=LIB_PATH):
     L.harmrad_autotune.argtypes = [vp, ip, ctypes.POINTER(Tuning)]
     L.harmrad_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
     L.harmrad_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+    L.harmrad_fp64_fma_rate.argtypes = [ip, dp, vp]
     L.harmrad_strerror.restype = ctypes.c_char_p
     L.harmrad_strerror.argtypes = [ip]
     _lib = L
@@ -398,6 +399,14 @@ class Batch(Grid):
 def _dev(a):
     import torch
     return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def fp64_fma_rate(reps=5, stream=None):
+    """Measured FP64 FMA rate of the current device, TFLOP/s."""
+    t = ctypes.c_double()
+    _check(load().harmrad_fp64_fma_rate(int(reps), ctypes.byref(t), _stream_ptr(stream)),
+           "fp64_fma_rate")
+    return t.value
 
 
 def zone_physics(cfg, x, P):

@@ -3,8 +3,8 @@ cannot allocate device memory (their device memory belongs to another
 allocator, so they may not call cudaMalloc/cudaFree).  It keeps its retry
 queue in a fixed array of the library's static device memory.  Called here
 through the C ABI and checked against harmrad_zone_implicit, twice in a row
-with different inputs (the shared queue must start empty every call), and
-for its size limit.  The file name sorts last so that a stop at the first
+with different inputs (the shared queue must start empty every call),
+against the oracle's point-wise solve, and for its size limit.  The file name sorts last so that a stop at the first
 failure has run every other test already."""
 import ctypes
 
@@ -70,6 +70,8 @@ def test_static_variant_matches_allocating_entry(metric):
         got = _call(L.harmrad_zone_implicit_static, cfg, x, Ust, Ps, h)
         same = got[3] == ref[3]
         assert (~same).sum() <= 0.01 * len(x), ("method differs", call, int((~same).sum()))
+        if metric == 1:  # no zone of the Kerr-Schild inputs is near a method threshold
+            assert same.all(), ("method differs", call, int((~same).sum()))
         queued += int(np.sum(~(ref[1] < 1e-9)))  # zones that went through the retry queue
         eg, ea = [], []
         for k in np.nonzero(same & (ref[3] != 2))[0]:
@@ -81,6 +83,38 @@ def test_static_variant_matches_allocating_entry(metric):
         assert ea.max() < 1e-6, (call, ea.max())
     if metric == 1:
         assert queued > 0
+
+
+def test_static_variant_matches_oracle():
+    """The no-allocation entry against the oracle's point-wise implicit solve
+    (Sec. 4.7-4.11), not only against the other GPU entry: 300 Kerr-Schild
+    zones, among them zones that PMHD leaves to the retry queue (the oracle
+    solves 253 by PMHD, 28 by a retry method and sends 19 to the back-up).
+    The outcome (PMHD, retry, back-up) may differ only for zones whose error
+    lies at a method threshold (at most 2 %); PMHD solutions agree to
+    1e-10 in the per-zone measure (radiation in conserved form, which PMHD
+    recovers from total conservation), retry solutions to the retry
+    tolerance (e_T < 1e-9 bounds the residual: 1e-6 in the per-zone measure)."""
+    L = H.load()
+    cfg, x, Ust, Ps, h = _inputs(300, 401, 1)
+    p = O.make_params(cfg)
+    Pout, eT, it, meth = _call(L.harmrad_zone_implicit_static, cfg, x, Ust, Ps, h)
+    n_pmhd = n_retry = differ = 0
+    for k in range(len(x)):
+        Po, info = O.implicit_zone(p, x[k], Ust[k], Ps[k], h[k])
+        if info.method != meth[k]:
+            differ += 1
+            continue
+        e = point_errors(cfg, x[k], Pout[k], Po, cfg["gam"], rad_conserved=True)
+        if meth[k] == 0:
+            n_pmhd += 1
+            assert e.max() < 1e-10 or e[8:].max() < 1e-10 and e.max() < 1e-7, (k, e)
+        elif meth[k] == 1:
+            n_retry += 1
+            assert e.max() < 1e-6, (k, e)
+    print("static entry vs oracle: %d PMHD, %d retry zones, %d differ in outcome" % (n_pmhd, n_retry, differ))
+    assert differ <= 0.02 * len(x)
+    assert n_pmhd > 200 and n_retry >= 5
 
 
 def test_static_variant_rejects_too_many_zones():
