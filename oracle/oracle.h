@@ -25,10 +25,16 @@
  * modes, optically thin and thick, gas- and radiation-dominated), by
  * tests/test_oracle_shocks.py (the jump conditions of the radiative shock-tube
  * states of Table t.radtube) and by tests/test_oracle_imex.py (the orders of
- * accuracy of the IMEX integrators on stiff relaxation).  Parity unpinned:
- * the PPM shock flattener (its constants beyond SP0 = 0.75 are not in the
- * paper), the polar-axis ghost rule and the floor procedure are readings of
- * the paper that only oracle-versus-library agreement checks.
+ * accuracy of the IMEX integrators on stiff relaxation).  The readings of
+ * the paper where it points to sources that are not in it are pinned by
+ * tests/test_oracle_readings.py: the polar-axis ghost rule (a smooth
+ * Cartesian field continued across the axis), the floors (the bounds they
+ * establish, the velocity and field they keep, idempotence), the PPM edge
+ * values (exact for a parabola, fourth order on smooth data, a monotone
+ * limited parabola) and the Kerr-Schild signal speeds (velocity addition in
+ * the normal observer's frame).  Parity unpinned: the constants of the PPM
+ * shock flattener beyond SP0 = 0.75 (not in the paper), which only
+ * oracle-versus-library agreement checks.
  */
 #ifndef HARMRAD_ORACLE_H
 #define HARMRAD_ORACLE_H
@@ -151,6 +157,14 @@ void   orc_pmhd_residual(const orc_params* p, const double* x, const double* Ust
  * max signal speed.  Test hook for sampled faces of large grids. */
 void   orc_face_flux_stencil(const orc_params* p, int d, const double* S, const double* xc,
                              const double* xf, double* F, double* speed);
+/* Floors of the grid step applied to the primitives P (12, in place) of a
+ * zone at x (test hook). */
+void   orc_apply_floors(const orc_params* p, const double* x, double* P);
+/* PPM reconstruction of the centre cell of the 5-cell stencil s5 (Sec. 4.3):
+ * edge values aL, aR with flattener chi (test hook). */
+void   orc_ppm_cell(const double* s5, double chi, double* aL, double* aR);
+/* Monotonised-central slope of the centre cell (test hook). */
+double orc_mc_slope(double qm, double q0, double qp);
 /* Levermore Eddington factor xi(f) (Sec. 3.1). */
 double orc_levermore_xi(double f);
 

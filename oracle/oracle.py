@@ -124,6 +124,10 @@ def lib():
         L.orc_radiation_subdominant.restype = ctypes.c_int
         L.orc_pmhd_residual.argtypes = [pp, dp, dp, ctypes.c_double, dp, dp, dp, dp]
         L.orc_face_flux_stencil.argtypes = [pp, ctypes.c_int, dp, dp, dp, dp, dp]
+        L.orc_apply_floors.argtypes = [pp, dp, dp]
+        L.orc_ppm_cell.argtypes = [dp, ctypes.c_double, dp, dp]
+        L.orc_mc_slope.restype = ctypes.c_double
+        L.orc_mc_slope.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_double]
         L.orc_levermore_xi.restype = ctypes.c_double
         L.orc_levermore_xi.argtypes = [ctypes.c_double]
     return _lib
@@ -331,6 +335,25 @@ def face_flux_stencil(p, d, S, xc, xf):
     sp = ctypes.c_double()
     lib().orc_face_flux_stencil(ctypes.byref(p), int(d), _dp(S), _dp(xc), _dp(xf), _dp(F), ctypes.byref(sp))
     return F, sp.value
+
+
+def apply_floors(p, x, P):
+    """The grid step's floors applied to one zone's primitives (copy returned)."""
+    Q = _vec(P).copy()
+    lib().orc_apply_floors(ctypes.byref(p), _dp(_vec(x)), _dp(Q))
+    return Q
+
+
+def ppm_cell(s5, chi=0.0):
+    """PPM edge values (aL, aR) of the centre cell of a 5-cell stencil."""
+    s = _vec(s5)
+    aL, aR = ctypes.c_double(), ctypes.c_double()
+    lib().orc_ppm_cell(_dp(s), float(chi), ctypes.byref(aL), ctypes.byref(aR))
+    return aL.value, aR.value
+
+
+def mc_slope(qm, q0, qp):
+    return lib().orc_mc_slope(float(qm), float(q0), float(qp))
 
 
 def levermore_xi(f):

@@ -944,6 +944,16 @@ void orc_face_flux_stencil(const orc_params* p, int d, const double* S, const do
   face_flux(*p, d - 1, P8, geo, Gf, nullptr, nullptr, F, speed);
 }
 
+void orc_apply_floors(const orc_params* p, const double* x, double* P) {
+  Geom G;
+  geom_at(*p, x[1], x[2], x[3], G);
+  apply_floors(*p, G, P);
+}
+
+void orc_ppm_cell(const double* s5, double chi, double* aL, double* aR) { ppm_cell(s5, chi, aL, aR); }
+
+double orc_mc_slope(double qm, double q0, double qp) { return mc_slope(qm, q0, qp); }
+
 double orc_levermore_xi(double f) {
   double f2 = f * f;
   return (3.0 + 4.0 * f2) / (5.0 + 2.0 * std::sqrt(4.0 - 3.0 * f2));
