@@ -299,6 +299,15 @@ int harmrad_adjoint_enable(harmrad_ctx* ctx, int on);
 int harmrad_step_adjoint(harmrad_ctx* ctx, const double* gP_out, double* gP_in, double* g_kappa,
                          int on_device);
 
+/* Make P (active layout, host or device per on_device) with time step dt > 0
+ * the step that the next harmrad_step_adjoint differentiates, without running
+ * that step: P becomes the context's primitives and the adjoint's saved input,
+ * exactly as harmrad_step(ctx, dt) from P would record them (the adjoint
+ * recomputes the step itself).  For checkpointed reverse sweeps that already
+ * hold every step's input.  HARMRAD_E_STATE unless the adjoint is enabled,
+ * HARMRAD_E_ARG for dt <= 0; HARMRAD_E_NAN_INPUT as for harmrad_set_prims. */
+int harmrad_adjoint_set_input(harmrad_ctx* ctx, const double* P, double dt, int on_device);
+
 /* Launch shapes of the three heaviest kernels: threads per block and the cap
  * on blocks per SM of their grid-stride grids (the grid is the smaller of the
  * work and sms x cap blocks).  Shapes change no result: every zone and face

@@ -534,9 +534,11 @@ Pass imex_pass(int integrator, int k) {
     if (k == 0) {  // U^0 = [U^n] + alpha dt M^0
       s.an = 1.0;
       s.g = al;
-    } else if (k == 1) {  // U^1 = [2U^n - U^0] + alpha dt M^1
-      s.an = 2.0;
-      s.ap = -1.0;
+    } else if (k == 1) {  // U^1 = [2U^n - U^0] + alpha dt M^1, with the bracket taken as
+                          // [U^n - alpha dt M^0]: equal by the first stage, but free of
+                          // the floors' additions to U^0, which 2U^n - U^0 would subtract
+      s.an = 1.0;
+      s.c[0] = -al;
       s.g = al;
     } else if (k == 2) {  // U^2 = [U^n + dt F^1 + (1-alpha) dt M^1] + alpha dt M^2
       s.an = 1.0;

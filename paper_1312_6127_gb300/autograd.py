@@ -7,7 +7,10 @@ of the initial primitives ``P0`` and of the global opacity scale
 backward pass uses the library's hand-written adjoint of one step
 (``harmrad_step_adjoint``) with checkpointing: the forward keeps the state
 every ``checkpoint`` steps; the backward re-runs each segment from its
-checkpoint to recover the steps' inputs and sweeps the segment in reverse.
+checkpoint to recover the steps' inputs and sweeps the segment in reverse,
+handing each step's input to the adjoint (which recomputes that step once
+with recording on): per segment of n steps, n - 1 forward steps of replay
+and the adjoints' n recomputations.
 The time steps are those of the forward run (held fixed, not differentiated).
 All arithmetic runs in the library's kernels; torch holds device memory.
 """
@@ -50,8 +53,8 @@ class _Steps(torch.autograd.Function):
                 if j < n - 1:
                     grid.step(ctx.dts[i0 + j])
             for j in reversed(range(n)):
-                grid.set_prims(inputs[j])
-                grid.step(ctx.dts[i0 + j])
+                # the adjoint recomputes the step from its recorded input
+                grid.adjoint_set_input(inputs[j], ctx.dts[i0 + j])
                 g, gkj = grid.step_adjoint(g)
                 gk += gkj
         return g, torch.tensor(gk, dtype=torch.float64), None, None, None, None

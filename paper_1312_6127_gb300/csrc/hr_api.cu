@@ -228,7 +228,9 @@ hr::ImexStage imex_stage(int integrator, int k) {
     const double a = 0.24169426078821, b = 0.06042356519705, e = 0.12915286960590;  // alpha, beta, eta
     const double t[5][8] = {
         {1, 0, 0, 0, 0, 0, 0, a},
-        {2, -1, 0, 0, 0, 0, 0, a},
+        // [2U^n - U^0] as [U^n - alpha dt M^0]: the same by the first stage,
+        // without subtracting the floors' additions to U^0
+        {1, 0, 0, -a, 0, 0, 0, a},
         {1, 0, 1, 0, 1 - a, 0, 0, a},
         {0.75, 0.25, 0.25, b, (-1 + a + 4 * e) / 4, (2 - 5 * a - 4 * (b + e)) / 4, 0, a},
         {1.0 / 3, 2.0 / 3, 2.0 / 3, -2 * b / 3, (1 - 4 * e) / 6, (-1 + 4 * a + 4 * (b + e)) / 6, 4 * (1 - a) / 6, 0}};
@@ -798,6 +800,21 @@ int harmrad_adjoint_enable(harmrad_ctx* c, int on) {
   if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = HARMRAD_E_CUDA;
   if (rc) free_adjoint(c);
   return rc;
+}
+
+int harmrad_adjoint_set_input(harmrad_ctx* c, const double* P, double dt, int on_device) {
+  if (!c || !P || !(dt > 0.0)) return HARMRAD_E_ARG;
+  if (!c->adj) return HARMRAD_E_STATE;
+  int rc = harmrad_set_prims(c, P, on_device);
+  if (rc) return rc;
+  // what harmrad_step records for the adjoint: its input and its time step
+  HR_CHECK(cudaMemcpyAsync(c->adj_Pn, c->P, 12 * (size_t)c->ncell * sizeof(double), cudaMemcpyDeviceToDevice,
+                           c->stream));
+  k_set_dt<<<1, 128, 0, c->stream>>>(c->dt, c->nbox, dt);
+  HR_CHECK(cudaGetLastError());
+  c->last_dt = dt;
+  c->adj_ready = true;
+  return HARMRAD_OK;
 }
 
 int harmrad_step_adjoint(harmrad_ctx* c, const double* gP_out, double* gP_in, double* g_kappa, int on_device) {

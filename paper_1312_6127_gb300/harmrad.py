@@ -26,7 +26,8 @@ EXPORTS = [
     "harmrad_get_status", "harmrad_get_iters", "harmrad_compute_fluxes",
     "harmrad_zone_physics", "harmrad_zone_implicit", "harmrad_zone_implicit_static",
     "harmrad_profile_step", "harmrad_autotune", "harmrad_get_tuning", "harmrad_set_tuning",
-    "harmrad_adjoint_enable", "harmrad_step_adjoint", "harmrad_fp64_fma_rate",
+    "harmrad_adjoint_enable", "harmrad_step_adjoint", "harmrad_adjoint_set_input",
+    "harmrad_fp64_fma_rate",
     "harmrad_strerror",
 ]
 KERNEL_CLASSES = ["bc", "prep", "flatten", "face", "ct", "update", "retry", "backup", "cfl", "other",
@@ -138,6 +139,7 @@ def load(path=LIB_PATH):
     L.harmrad_autotune.argtypes = [vp, ip, ctypes.POINTER(Tuning)]
     L.harmrad_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
     L.harmrad_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
+    L.harmrad_adjoint_set_input.argtypes = [vp, vp, ctypes.c_double, ip]
     L.harmrad_fp64_fma_rate.argtypes = [ip, dp, vp]
     L.harmrad_strerror.restype = ctypes.c_char_p
     L.harmrad_strerror.argtypes = [ip]
@@ -255,6 +257,13 @@ class Grid:
     def adjoint_enable(self, on=True):
         """Keep each step's input so that step_adjoint can differentiate it."""
         _check(load().harmrad_adjoint_enable(self._h, 1 if on else 0), "adjoint_enable")
+
+    def adjoint_set_input(self, P, dt):
+        """Record P (float64 CUDA tensor, active layout) and dt as the input of
+        the step that the next step_adjoint differentiates (no step is run)."""
+        P = P.contiguous()
+        _check(load().harmrad_adjoint_set_input(self._h, ctypes.c_void_p(P.data_ptr()), float(dt), 1),
+               "adjoint_set_input")
 
     def step_adjoint(self, gP_out):
         """Reverse-mode derivative of the last step: dL/dP^{n+1} -> (dL/dP^n,

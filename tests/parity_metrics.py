@@ -76,6 +76,17 @@ def zone_errors(cfg, A, R):
     return E
 
 
+def plain_relative(A, R):
+    """Plain relative errors |A - R| / |R| of u_g and Ebar per zone (the
+    unconditioned companions of the per-zone measure above), as (max, p99)
+    of each."""
+    out = {}
+    for q, name in ((1, "u_g"), (8, "Ebar")):
+        e = (np.abs(A[q] - R[q]) / np.abs(R[q])).ravel()
+        out[name] = (float(e.max()), float(np.quantile(e, 0.99)))
+    return out
+
+
 def energy_scale(cfg, R):
     """|T^t_t + rho0 u^t| per zone from the oracle's conserved variables."""
     p = O.make_params(cfg)

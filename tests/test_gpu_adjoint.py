@@ -13,9 +13,11 @@
   (exact agreement expected) and on the 128x64x32 torus with 64 seeded
   directions.
 
-The checks solve the implicit step to round-off (Newton tolerance 1e-15
+Most checks solve the implicit step to round-off (Newton tolerance 1e-15
 instead of 1e-12): the adjoint differentiates the exact root, and a root
-known only to 1e-12 would put noise of 1e-12/h into every difference.
+known only to 1e-12 would put noise of 1e-12/h into every difference.  Two
+one-step cases run at the default tolerance 1e-12 (Newton's last step
+usually lands far below it) and are held to the same 1e-6.
 
 A finite difference only measures the derivative if P +- hv crosses none of
 the step's kinks (slope-limiter switches, wave-speed maxima, floors).  The
@@ -80,6 +82,11 @@ def cases():
     out["ks_random_ppm_laxf_kramers"] = (dict(cfg, newton_tol=TOL), P)
     cfg, P = W.ks_random_state((32, 16, 8), seed=9, tau=10.0)
     out["ks_random_stiff_urad"] = (dict(cfg, newton_tol=TOL), P)
+    # the default Newton tolerance (1e-12), as users run the step
+    cfg, P = W.minkowski_box((8, 8, 8), seed=6, recon=W.PPM, flux=W.HLL)
+    out["mink_ppm_hll_default_tol"] = (cfg, P)
+    cfg, P = W.ks_random_state((32, 16, 8), seed=9, tau=1.0)
+    out["ks_random_ppm_laxf_default_tol"] = (cfg, P)
     return out
 
 
@@ -127,6 +134,28 @@ def test_step_adjoint_against_finite_differences(name):
         print("%s kappa_scale, h %.0e: adjoint %.10e fd %.10e rel %.2e" % (name, h, gk, fd, eks[-1]))
     assert worst < 1e-6
     assert min(eks) < KAPPA_TOL.get(name, 1e-6)
+
+
+def test_adjoint_set_input_equals_a_recorded_step():
+    """harmrad_adjoint_set_input records a step's input and time step without
+    running it: the adjoint that follows equals, bit for bit, the adjoint
+    after running that step, and leaves the step's result as the primitives."""
+    cfg, P = W.ks_random_state((32, 16, 8), seed=9, tau=1.0)
+    rng = W.rng(303)
+    w = torch.tensor(rng.standard_normal(P.shape), device="cuda")
+    g = H.Grid(cfg)
+    g.adjoint_enable(True)
+    g.set_prims(P)
+    dt = g.cfl_dt()
+    g.step(dt)
+    after_step = g.get_prims(device=True)
+    gA, kA = g.step_adjoint(w)
+    g2 = H.Grid(cfg)
+    g2.adjoint_enable(True)
+    g2.adjoint_set_input(torch.tensor(P, device="cuda"), dt)
+    gB, kB = g2.step_adjoint(w)
+    assert torch.equal(gA, gB) and kA == kB
+    assert torch.equal(g2.get_prims(device=True), after_step)
 
 
 def test_step_adjoint_against_oracle_differences():

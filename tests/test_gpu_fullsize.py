@@ -13,7 +13,7 @@ import torch
 from oracle import oracle as O
 from paper_1312_6127_gb300 import harmrad as H
 from paper_1312_6127_gb300 import workloads as W
-from tests.parity_metrics import GROUPS, zone_errors
+from tests.parity_metrics import GROUPS, plain_relative, zone_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -183,7 +183,8 @@ def test_fullsize_against_oracle_twenty_steps(torus_full):
     """256x128x64, 20 CFL steps of the oracle (on all host cores: its zone
     loops are independent, so the thread count does not change its result)
     and of the CUDA step in FP64 and in split precision with the oracle's
-    time steps: per-zone errors and conserved totals against the oracle."""
+    time steps: per-zone errors and conserved totals against the oracle.
+    FP64: the largest per-zone error of all 2,097,152 zones below 1e-8."""
     cfg, P = torus_full
     old = os.environ.get("ORACLE_THREADS")
     os.environ["ORACLE_THREADS"] = str(os.cpu_count() or 1)
@@ -212,13 +213,16 @@ def test_fullsize_against_oracle_twenty_steps(torus_full):
         A = g.get_prims()
         tA, _ = conserved_totals(cfg, torch.as_tensor(A, device="cuda"))
         e = zone_errors(cfg, A, R).max(0)
-        res[prec] = (np.abs(tA - tR) / sR, np.median(e), np.quantile(e, 0.99), e.max())
+        res[prec] = (np.abs(tA - tR) / sR, np.median(e), np.quantile(e, 0.99), e.max(),
+                     plain_relative(A, R), int((g.status() != 0).sum()))
         del g
     for prec, name in ((H.PREC_FP64, "FP64"), (H.PREC_SPLIT, "split")):
-        rel, med, p99, mx = res[prec]
-        print("%s vs oracle after 20 steps: totals %s; per-zone error median %.2e p99 %.2e max %.2e"
-              % (name, np.array2string(rel, precision=2), med, p99, mx))
+        rel, med, p99, mx, plain, nret = res[prec]
+        print("%s vs oracle after 20 steps: totals %s; per-zone error median %.2e p99 %.2e max %.2e; "
+              "plain relative (max, p99) %s; zones that took a retry or back-up in the last step: %d"
+              % (name, np.array2string(rel, precision=2), med, p99, mx, plain, nret))
     print("oracle solver counts:", counts)
     assert res[H.PREC_FP64][0].max() < 1e-10
-    assert res[H.PREC_FP64][1] < 1e-9
+    # every zone within the ten-step bound of 1e-8 (1.2e-10 measured)
+    assert res[H.PREC_FP64][3] < 1e-8
     assert res[H.PREC_SPLIT][0].max() < 1e-5
