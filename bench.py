@@ -39,7 +39,7 @@ UNIT = "zone-cycles/s"
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 PROFILE_JSON = os.path.join(ROOT, "profiles", "k_update_counters.json")
 INTEGRATORS = {"rk3": 0, "imex2": 1, "imex2b": 2, "imex3": 3}
-KERNEL_SOURCES = ["hr_phys.cuh", "hr_implicit.cuh", "hr_kernels.cuh"]
+KERNEL_SOURCES = ["hr_phys.cuh", "hr_implicit.cuh", "hr_tangent.cuh", "hr_kernels.cuh"]
 
 
 def kernel_hash():

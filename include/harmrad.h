@@ -57,6 +57,8 @@ extern "C" {
 #define HARMRAD_BC_OUTFLOW 1   /* copy the edge zone; the normal velocities may not point inward */
 #define HARMRAD_BC_POLAR 2     /* theta direction of the Kerr-Schild grid only */
 #define HARMRAD_BC_COPY 3      /* copy the edge zone (zero gradient), inflow allowed (shock tubes) */
+#define HARMRAD_BC_FIXED 4     /* the ghost zones keep the values given by harmrad_set_prims_ghosts
+                                  (a fixed inflow state, e.g. the base of the static atmosphere) */
 
 #define HARMRAD_METRIC_MINKOWSKI 0
 #define HARMRAD_METRIC_KS 1
@@ -163,6 +165,17 @@ void harmrad_destroy(harmrad_ctx* ctx);
  * P is a device pointer, else host memory.  Returns HARMRAD_E_NAN_INPUT if any
  * value is not finite, or if rho0, u_g or Ebar is not positive. */
 int harmrad_set_prims(harmrad_ctx* ctx, const double* P, int on_device);
+
+/* Load the primitives of every cell of a single-grid context, ghost zones
+ * included: layout [12][N3][N2][N1] with N_d = n_d + 8 for an active
+ * direction (4 ghosts per side) and N_d = 1 for a degenerate one.  The ghost
+ * zones of faces with HARMRAD_BC_FIXED keep these values through every later
+ * step (the fixed boundary states of the paper's static atmosphere, Sec. 5);
+ * all other ghosts are refilled by their boundary condition at every
+ * sub-step.  A later harmrad_set_prims changes the active zones only.
+ * HARMRAD_E_ARG for a batch; HARMRAD_E_NAN_INPUT as for harmrad_set_prims,
+ * over every cell. */
+int harmrad_set_prims_ghosts(harmrad_ctx* ctx, const double* P, int on_device);
 
 /* Load the per-zone absorption field K (active zones, [n3][n2][n1] FP64 per
  * box, boxes concatenated) of a context created with opacity =
@@ -278,7 +291,7 @@ int harmrad_profile_step(harmrad_ctx* ctx, double dt, harmrad_kernel_times* out)
  * harmrad_adjoint_enable(ctx, 1) allocates the adjoint's workspace (about 40
  * doubles per cell) and makes every later harmrad_step keep a copy of its
  * input; 0 releases it.  HARMRAD_E_ARG for a batch, split precision or an
- * IMEX integrator.
+ * IMEX integrator, or a context with a HARMRAD_BC_FIXED face.
  *
  * harmrad_step_adjoint(ctx, gP_out, gP_in, g_kappa, on_device) differentiates
  * the last harmrad_step of the context: given gP_out = dL/dP^{n+1} (active

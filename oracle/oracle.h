@@ -48,7 +48,8 @@ typedef struct {
   int metric;             /* 0 Minkowski Cartesian, 1 Kerr-Schild + MSP map */
   double a_spin, R0, hslope;
   int bc[6];              /* lower/upper per direction: 0 periodic, 1 outflow, 2 polar,
-                             3 zero gradient with inflow allowed */
+                             3 zero gradient with inflow allowed, 4 fixed (ghosts as set
+                             by orc_set_prims_with_ghosts) */
   double gam, a_rad, courant;
   int opacity;            /* 0 kappa = k0*rho (per length), 1 Kramers k0*rho^2*T^-3.5,
                              2 per-zone field K (orc_set_opacity_field), kappa = K */
@@ -99,6 +100,9 @@ void   orc_get_counts(void* ctx, long long* c);
  * prims and copies F for faces [0..n_d] x active transverse range,
  * layout [12][n3'][n2'][n1'] where n_d' = n_d + 1. */
 void   orc_compute_fluxes(void* ctx, int dir, double* F);
+/* Set every cell, ghosts included (layout [12][N3][N2][N1], N = n + 8 for an
+ * active direction); ghosts of fixed faces (bc 4) keep these values. */
+void   orc_set_prims_with_ghosts(void* ctx, const double* P);
 /* Ghost-inclusive prim copy (layout [12][N3][N2][N1]); debug/test hook. */
 void   orc_get_prims_with_ghosts(void* ctx, double* P, int fill_ghosts);
 

@@ -99,6 +99,7 @@ def lib():
         L.orc_get_prims.argtypes = [ctypes.c_void_p, dp]
         L.orc_set_opacity_field.argtypes = [ctypes.c_void_p, dp]
         L.orc_get_prims_with_ghosts.argtypes = [ctypes.c_void_p, dp, ctypes.c_int]
+        L.orc_set_prims_with_ghosts.argtypes = [ctypes.c_void_p, dp]
         L.orc_cfl_dt.restype = ctypes.c_double
         L.orc_cfl_dt.argtypes = [ctypes.c_void_p]
         L.orc_step.restype = ctypes.c_double
@@ -218,6 +219,13 @@ class Oracle:
         F = np.empty((NP, m[2], m[1], m[0]))
         lib().orc_compute_fluxes(self._h, d, _dp(F))
         return F
+
+    def set_prims_with_ghosts(self, P):
+        """Every cell, ghosts included ([12, N3, N2, N1]); fixed faces keep their ghosts."""
+        ng = [4 if x > 1 else 0 for x in self.n]
+        N = [self.n[i] + 2 * ng[i] for i in range(3)]
+        P = _vec(P).reshape((NP, N[2], N[1], N[0]))
+        lib().orc_set_prims_with_ghosts(self._h, _dp(P))
 
     def prims_with_ghosts(self, fill=True):
         ng = [4 if x > 1 else 0 for x in self.n]

@@ -71,7 +71,8 @@ inline double xf(const Ctx& c, int d, int i) { return c.p.x0[d] + i * c.p.dx[d];
 // from already-filled data.  Periodic: wrap.  Outflow: copy the last active
 // zone and clamp the normal velocities so nothing flows in from the ghost.
 // Polar (direction 2 only): mirror across the axis, taking the zone on the
-// opposite side in phi (shift n3/2) and negating the theta components.  The
+// opposite side in phi (shift n3/2) and negating the theta components.
+// Fixed: the ghosts are left as set (orc_set_prims_with_ghosts).  The
 // absorption field (opacity mode 2) is copied from the same source zone.
 void fill_ghosts(Ctx& c, std::vector<double>& P) {
   for (int d = 0; d < 3; ++d) {
@@ -88,6 +89,7 @@ void fill_ghosts(Ctx& c, std::vector<double>& P) {
     }
     for (int side = 0; side < 2; ++side) {
       int bc = c.p.bc[2 * d + side];
+      if (bc == 4) continue;  // fixed: the ghosts keep the values they were given
       for (int g = 0; g < c.ng[d]; ++g) {
         int gi = side == 0 ? -1 - g : c.n[d] + g;
         int a0 = d == 0 ? 0 : lo[0], a1 = d == 0 ? 1 : hi[0];
@@ -763,6 +765,11 @@ void orc_set_prims(void* ctx, const double* P) {
       for (int j = 0; j < c.n[1]; ++j)
         for (int i = 0; i < c.n[0]; ++i)
           c.P[(long)q * c.ntot + idx(c, i, j, k)] = P[(long)q * na + aidx(c, i, j, k)];
+}
+
+void orc_set_prims_with_ghosts(void* ctx, const double* P) {
+  Ctx& c = *static_cast<Ctx*>(ctx);
+  for (long m = 0; m < (long)NP * c.ntot; ++m) c.P[m] = P[m];
 }
 
 void orc_set_opacity_field(void* ctx, const double* K) {

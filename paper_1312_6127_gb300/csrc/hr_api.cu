@@ -86,6 +86,17 @@ __global__ void k_validate(const BoxGeo* __restrict__ boxes, int nbox, int nv,
   }
 }
 
+// Finite primitives with positive rho0, u_g and Ebar in every cell of a
+// ghost-inclusive single-grid array [12][ncell].
+__global__ void k_validate_cells(long long ncell, const double* __restrict__ P, int* flag) {
+  for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < 12 * ncell;
+       id += (long long)gridDim.x * blockDim.x) {
+    const double v = P[id];
+    const long long q = id / ncell;
+    if (!isfinite(v) || ((q == hr::RHO || q == hr::UU || q == hr::ER) && !(v > 0.0))) atomicOr(flag, 1);
+  }
+}
+
 __global__ void k_set_dt(double* dt, int nbox, double v) {
   for (int i = threadIdx.x; i < nbox; i += blockDim.x) dt[i] = v;
 }
@@ -166,7 +177,7 @@ int fill_geometry(const harmrad_params* p, BoxGeo& b) {
   b.str[2] = (long long)b.N[0] * b.N[1];
   for (int s = 0; s < 6; ++s) {
     int bc = p->bc[s];
-    if (bc < 0 || bc > 3) return HARMRAD_E_ARG;
+    if (bc < 0 || bc > 4) return HARMRAD_E_ARG;
     if (bc == 2 && (s / 2 != 1 || p->metric != 1)) return HARMRAD_E_ARG;
     b.bc[s] = bc;
   }
@@ -560,6 +571,22 @@ int harmrad_set_prims(harmrad_ctx* c, const double* P, int on_device) {
   return HARMRAD_OK;
 }
 
+int harmrad_set_prims_ghosts(harmrad_ctx* c, const double* P, int on_device) {
+  if (!c || !P || c->nbox != 1) return HARMRAD_E_ARG;
+  const size_t bytes = 12 * (size_t)c->ncell * sizeof(double);
+  HR_CHECK(cudaMemcpyAsync(c->P, P, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           c->stream));
+  HR_CHECK(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+  k_validate_cells<<<hr::grid_for(c->ncell, c->sms, 256), 256, 0, c->stream>>>(c->ncell, c->P, c->flag);
+  HR_CHECK(cudaGetLastError());
+  int flag = 0;
+  HR_CHECK(cudaMemcpyAsync(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  HR_CHECK(cudaStreamSynchronize(c->stream));
+  if (flag) return HARMRAD_E_NAN_INPUT;
+  c->has_prims = true;
+  return HARMRAD_OK;
+}
+
 int harmrad_set_opacity_field(harmrad_ctx* c, const double* kabs, int on_device) {
   if (!c || !kabs) return HARMRAD_E_ARG;
   if (c->dp.opacity != HARMRAD_OPAC_FIELD) return HARMRAD_E_ARG;
@@ -769,6 +796,8 @@ int harmrad_adjoint_enable(harmrad_ctx* c, int on) {
     return HARMRAD_OK;
   }
   if (c->nbox != 1 || c->real_size != 8 || c->dp.integrator != 0) return HARMRAD_E_ARG;
+  for (int f = 0; f < 6; ++f)
+    if (c->boxes[0].bc[f] == HARMRAD_BC_FIXED) return HARMRAD_E_ARG;
   if (c->adj) return HARMRAD_OK;
   c->adj = new hr::AdjBufs();
   memset(c->adj, 0, sizeof(hr::AdjBufs));

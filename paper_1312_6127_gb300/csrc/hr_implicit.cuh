@@ -6,18 +6,23 @@
 // PMHD iterates the gas primitives x = (u_g, u~^i); URAD iterates x = R^t_nu
 // and PRAD x = (Ebar, u~^i_rad), both recovering the gas from a 1D_W
 // inversion inside every residual.  Newton
-// steps follow Eq. newton with D = 1 and a finite-difference Jacobian
-// (one-sided; the paper's two-sided PMHD differences belong to its staged
-// scheme, which is not used), normalised offset 1e-8, switching
-// to 1e-10 once e_I < 1e-9; the stopping rules of Sec. 4.10 (tolerance,
-// stalled error, repeated rises, tiny step, step limit) and the best-error
-// bookkeeping are applied.
+// steps follow Eq. newton with D = 1.  The PMHD Jacobian is the exact
+// derivative of the error function evaluated on the FP32 pipe
+// (hr_tangent.cuh); it falls back to the paper's finite differences (FP64,
+// one-sided; the paper's two-sided PMHD differences belong to its staged
+// scheme, which is not used; normalised offset 1e-8, switching to 1e-10 once
+// e_I < 1e-9) for the rest of a solve when the FP32 Jacobian is not finite or
+// singular, or when a step taken with it did not halve e_T.  URAD and PRAD
+// use the finite differences.  The error, and with it every stopping rule of
+// Sec. 4.10 (tolerance, stalled error, repeated rises, tiny step, step limit)
+// and the best-error bookkeeping, is FP64.
 //
 // The four-force uses the rank-one-plus-isotropic form of the M1 tensor:
 // R^mu_a u^a = 4/3 Ebar (u_r.u) u_r^mu + 1/3 Ebar u^mu, so G_nu (Eq. Gcov) is a
 // combination of u_r_nu and u_nu and needs no 4x4 contraction.
 #pragma once
 #include "hr_phys.cuh"
+#include "hr_tangent.cuh"
 
 namespace hr {
 
@@ -258,6 +263,7 @@ struct NewtonState {
   double eps;
   int k;      // index of the next iteration
   int steps;  // Newton steps taken
+  int jac32;  // 1 while the FP32 tangent Jacobian is in use, 0 after a fall-back
 };
 
 __device__ __forceinline__ void newton_pmhd_init(const double x0[4], NewtonState& st) {
@@ -271,6 +277,51 @@ __device__ __forceinline__ void newton_pmhd_init(const double x0[4], NewtonState
   st.eps = 1e-8;
   st.k = 0;
   st.steps = 0;
+  st.jac32 = 1;
+}
+
+// Finite-difference PMHD Jacobian (one-sided, the paper's numerical
+// Jacobian): column j from the error at x + dj e_j, dj = eps |u_g| for j = 0
+// and eps max(1, |u~|)/sqrt(g_jj) for the velocities.
+template <int MET>
+__device__ __forceinline__ void pmhd_jacobian_fd(const DevParams& p, const ImpSys<MET>& s, const double x[4],
+                                                 const ImpRes& r, double eps, double J[4][4]) {
+  double umag = fmax(1.0, sqrt(s.g.sq3(x[1], x[2], x[3])));
+#pragma unroll 1
+  for (int j = 0; j < 4; ++j) {
+    double dj = (j == 0) ? eps * fabs(x[0]) : eps * umag / sqrt(s.g.gdd(j));
+    double xp[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) xp[i] = x[i] + (i == j ? dj : 0.0);
+    ImpRes rp;
+    pmhd_res<MET>(p, s, xp, rp, nullptr, false);
+    double id = 1.0 / dj;
+    // column j of J, written through compile-time indices
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+        if (c == j) J[i][c] = (rp.Eg[i] - r.Eg[i]) * id;
+  }
+}
+
+// Newton step dx = J^-1 E at x: the FP32 tangent Jacobian while *jac32, else
+// (or when it is not finite or singular, which clears *jac32) the
+// finite-difference one.  Returns false if no Jacobian could be solved.
+template <int MET>
+__device__ __forceinline__ bool pmhd_newton_dx(const DevParams& p, const ImpSys<MET>& s, const double x[4],
+                                               const ImpRes& r, const double Rt[4], double eps, int* jac32,
+                                               double dx[4]) {
+  if (*jac32) {
+    double J[4][4];
+    double E[4] = {r.Eg[0], r.Eg[1], r.Eg[2], r.Eg[3]};
+    if (pmhd_jacobian_fp32<MET>(p, s, x, Rt, J) && solve4(J, E, dx)) return true;
+    *jac32 = 0;
+  }
+  double J[4][4];
+  pmhd_jacobian_fd<MET>(p, s, x, r, eps, J);
+  double E[4] = {r.Eg[0], r.Eg[1], r.Eg[2], r.Eg[3]};
+  return solve4(J, E, dx);
 }
 
 // PMHD Newton iterations from the state st until a stopping rule ends the
@@ -283,7 +334,8 @@ __device__ __forceinline__ bool newton_pmhd_run(const DevParams& p, const ImpSys
   for (;; ++st.k) {
     if (st.k >= kstop) return false;
     ImpRes r;
-    pmhd_res<MET>(p, s, st.x, r, nullptr, true);
+    ImpState ist;
+    pmhd_res<MET>(p, s, st.x, r, &ist, true);
     if (!r.ok) break;
     if (r.eT < st.best_eT) {
       st.best_eT = r.eT;
@@ -291,30 +343,14 @@ __device__ __forceinline__ bool newton_pmhd_run(const DevParams& p, const ImpSys
       for (int i = 0; i < 4; ++i) st.best_x[i] = st.x[i];
     }
     if (r.eT < p.newton_tol) break;
+    // a step with the FP32 Jacobian that did not halve e_T: finite
+    // differences for the rest of the solve
+    if (st.jac32 && r.eT > 0.5 * st.hs.t1) st.jac32 = 0;
     if (stalled(st.hs, st.k, r.eT, r.eI)) break;
     if (st.k >= p.newton_max) break;
     if (r.eI < 1e-9) st.eps = 1e-10;
-    const double eps = st.eps;
-    double umag = fmax(1.0, sqrt(s.g.sq3(st.x[1], st.x[2], st.x[3])));
-    double J[4][4];
-#pragma unroll 1
-    for (int j = 0; j < 4; ++j) {
-      double dj = (j == 0) ? eps * fabs(st.x[0]) : eps * umag / sqrt(s.g.gdd(j));
-      double xp[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) xp[i] = st.x[i] + (i == j ? dj : 0.0);
-      ImpRes rp;
-      pmhd_res<MET>(p, s, xp, rp, nullptr, false);
-      double id = 1.0 / dj;
-      // column j of J, written through compile-time indices
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (c == j) J[i][c] = (rp.Eg[i] - r.Eg[i]) * id;
-    }
-    double E[4] = {r.Eg[0], r.Eg[1], r.Eg[2], r.Eg[3]}, dx[4];
-    if (!solve4(J, E, dx)) break;
+    double dx[4];
+    if (!pmhd_newton_dx<MET>(p, s, st.x, r, ist.Rt_pre, st.eps, &st.jac32, dx)) break;
     double xn[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) xn[i] = st.x[i] - dx[i];
@@ -352,9 +388,11 @@ __device__ int newton_pmhd(const DevParams& p, const ImpSys<MET>& s, const doubl
   *best_eT = HUGE_VAL;
   int steps = 0;
   double eps = 1e-8;
+  int jac32 = 1;
   for (int k = 0;; ++k) {
     ImpRes r;
-    pmhd_res<MET>(p, s, x, r, nullptr, true);
+    ImpState ist;
+    pmhd_res<MET>(p, s, x, r, &ist, true);
     if (!r.ok) break;
     if (r.eT < *best_eT) {
       *best_eT = r.eT;
@@ -362,29 +400,14 @@ __device__ int newton_pmhd(const DevParams& p, const ImpSys<MET>& s, const doubl
       for (int i = 0; i < 4; ++i) best_x[i] = x[i];
     }
     if (r.eT < p.newton_tol) break;
+    // a step with the FP32 Jacobian that did not halve e_T: finite
+    // differences for the rest of the solve
+    if (jac32 && r.eT > 0.5 * hs.t1) jac32 = 0;
     if (stalled(hs, k, r.eT, r.eI)) break;
     if (k >= p.newton_max) break;
     if (r.eI < 1e-9) eps = 1e-10;
-    double umag = fmax(1.0, sqrt(s.g.sq3(x[1], x[2], x[3])));
-    double J[4][4];
-#pragma unroll 1
-    for (int j = 0; j < 4; ++j) {
-      double dj = (j == 0) ? eps * fabs(x[0]) : eps * umag / sqrt(s.g.gdd(j));
-      double xp[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) xp[i] = x[i] + (i == j ? dj : 0.0);
-      ImpRes rp;
-      pmhd_res<MET>(p, s, xp, rp, nullptr, false);
-      double id = 1.0 / dj;
-      // column j of J, written through compile-time indices
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int i = 0; i < 4; ++i)
-          if (c == j) J[i][c] = (rp.Eg[i] - r.Eg[i]) * id;
-    }
-    double E[4] = {r.Eg[0], r.Eg[1], r.Eg[2], r.Eg[3]}, dx[4];
-    if (!solve4(J, E, dx)) break;
+    double dx[4];
+    if (!pmhd_newton_dx<MET>(p, s, x, r, ist.Rt_pre, eps, &jac32, dx)) break;
     double xn[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) xn[i] = x[i] - dx[i];

@@ -200,6 +200,7 @@ static __global__ void k_bc_fill(DevParams p, const BoxGeo* __restrict__ boxes, 
       int g = c[d];
       int dst[3] = {c[0], c[1], c[2]}, src[3] = {c[0], c[1], c[2]};
       int bc = bx.bc[2 * d + side];
+      if (bc == 4) continue;  // fixed ghosts keep the values they were given
       dst[d] = side == 0 ? -1 - g : bx.n[d] + g;
       double sgn = 1.0;
       int clamp = 0;
@@ -1084,7 +1085,7 @@ __device__ __forceinline__ void cons_source(const DevParams& p, const Geo<MET, T
   (void)x2;
 }
 
-constexpr int CSTRIDE = NPR + 21;  // continuation queue record: U*, Newton state
+constexpr int CSTRIDE = NPR + 22;  // continuation queue record: U*, Newton state
 
 __device__ __forceinline__ void newton_state_store(const NewtonState& st, double* d) {
   for (int i = 0; i < 4; ++i) {
@@ -1104,6 +1105,7 @@ __device__ __forceinline__ void newton_state_store(const NewtonState& st, double
   d[18] = (double)st.hs.rises;
   d[19] = (double)st.k;
   d[20] = (double)st.steps;
+  d[21] = (double)st.jac32;
 }
 
 __device__ __forceinline__ void newton_state_load(const double* d, NewtonState& st) {
@@ -1124,6 +1126,7 @@ __device__ __forceinline__ void newton_state_load(const double* d, NewtonState& 
   st.hs.rises = (int)d[18];
   st.k = (int)d[19];
   st.steps = (int)d[20];
+  st.jac32 = (int)d[21];
 }
 
 // End of a zone's PMHD solve: accept (e_T < 1e-9: final primitives, floors,

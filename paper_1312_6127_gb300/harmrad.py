@@ -21,7 +21,8 @@ OPAC_CONST, OPAC_KRAMERS, OPAC_FIELD = 0, 1, 2
 INT_RK3, INT_IMEX2, INT_IMEX2B, INT_IMEX3 = 0, 1, 2, 3
 
 EXPORTS = [
-    "harmrad_init", "harmrad_init_batch", "harmrad_destroy", "harmrad_set_opacity_field", "harmrad_set_prims", "harmrad_get_prims",
+    "harmrad_init", "harmrad_init_batch", "harmrad_destroy", "harmrad_set_opacity_field", "harmrad_set_prims",
+    "harmrad_set_prims_ghosts", "harmrad_get_prims",
     "harmrad_cfl_dt", "harmrad_step", "harmrad_step_host", "harmrad_get_stats",
     "harmrad_get_status", "harmrad_get_iters", "harmrad_compute_fluxes",
     "harmrad_zone_physics", "harmrad_zone_implicit", "harmrad_zone_implicit_static",
@@ -122,6 +123,7 @@ def load(path=LIB_PATH):
     L.harmrad_destroy.argtypes = [vp]
     L.harmrad_destroy.restype = None
     L.harmrad_set_prims.argtypes = [vp, vp, ip]
+    L.harmrad_set_prims_ghosts.argtypes = [vp, vp, ip]
     L.harmrad_get_prims.argtypes = [vp, vp, ip]
     L.harmrad_cfl_dt.argtypes = [vp, dp]
     L.harmrad_step.argtypes = [vp, ctypes.c_double]
@@ -218,6 +220,13 @@ class Grid:
         else:
             P = np.ascontiguousarray(P, dtype=np.float64).reshape(self.shape)
             _check(load().harmrad_set_prims(self._h, P.ctypes.data_as(ctypes.c_void_p), 0), "set_prims")
+
+    def set_prims_ghosts(self, P):
+        """Every cell, ghosts included ([12, N3, N2, N1], numpy); the ghosts of
+        HARMRAD_BC_FIXED faces keep these values."""
+        P = np.ascontiguousarray(P, dtype=np.float64)
+        _check(load().harmrad_set_prims_ghosts(self._h, P.ctypes.data_as(ctypes.c_void_p), 0),
+               "set_prims_ghosts")
 
     def set_opacity_field(self, K):
         """Per-zone absorption field K ([n3,n2,n1]; kappa_abs = kappa_scale K)."""

@@ -22,7 +22,7 @@ import numpy as np
 
 NP = 12
 RHO, UU, U1, U2, U3, B1, B2, B3, ER, UR1, UR2, UR3 = range(12)
-PERIODIC, OUTFLOW, POLAR, COPY = 0, 1, 2, 3
+PERIODIC, OUTFLOW, POLAR, COPY, FIXED = 0, 1, 2, 3, 4
 PPM, MC = 0, 1
 LAXF, HLL = 0, 1
 OPAC_CONST, OPAC_KRAMERS, OPAC_FIELD = 0, 1, 2
@@ -422,6 +422,86 @@ def shock_tube(state, n1=800, xlim=(-20.0, 20.0), recon=PPM, flux=LAXF):
         P[ER][..., sel] = E
         P[UR1][..., sel] = ux
     return cfg, P
+
+
+# CGS constants for the static atmosphere's physical units
+_G, _C, _MSUN = 6.67430e-8, 2.99792458e10, 1.98847e33
+_MP, _KB, _ARAD = 1.67262192e-24, 1.380649e-16, 7.5657e-15
+
+
+def _m1_from_flux(E, F):
+    """Radiation-frame energy density and Lorentz factor of an M1 field with
+    lab (observer-frame) energy density E and flux F along one axis:
+    E = Ebar (4 g^2 - 1)/3, F = 4/3 Ebar g^2 v (Sec. 3, Eq. Rlab), so
+    F/E = 4 g^2 v / (4 g^2 - 1), solved for g by bisection."""
+    ratio = F / E
+    lo, hi = 1.0, 1e4
+    for _ in range(200):
+        g = math.sqrt(lo * hi)
+        v = math.sqrt(1.0 - 1.0 / (g * g))
+        if 4 * g * g * v / (4 * g * g - 1) > ratio:
+            hi = g
+        else:
+            lo = g
+    g = math.sqrt(lo * hi)
+    return E * 3.0 / (4 * g * g - 1), g
+
+
+def static_atmosphere(f, n1=40, r_in=1e6, r_out=1.4e6, rho_in_cgs=1e-15, T_in_K=1e6, flux_ratio=0.99999):
+    """The static radiative atmosphere of the paper's Sec. 5 ("Static
+    Radiative Atmosphere in 1D Spherical Polar Minkowski"): a polytropic
+    atmosphere p = K rho0^Gamma on a Schwarzschild grid (Kerr-Schild, a = 0)
+    from r = 1e6 to 1.4e6, one equatorial theta cell (0.99 to 1.01 pi/2), held
+    up by gravity, its pressure gradient and the radiation force of a flux
+    F = F_in (r_in/r)^2 with F_in = f F_Edd, F_Edd = 1/(kappa_es r_in^2);
+    scattering only (kappa_abs = 0, kappa_es = 0.4 cm^2/g), M = 1 solar mass,
+    rho0 = 1e-15 g/cm^3 and T = 1e6 K at r_in, E = F/0.99999.  Both radial
+    boundaries are fixed at the analytic state (Eqs. rho, f); velocities start
+    at zero.  The radial cells are uniform in ln r (the grid's map), not in r.
+    The gas is fully ionised hydrogen (mean molecular weight 1/2, so
+    p = 2 rho0 k T / m_p): with weight 1 the analytic atmospheres of the two
+    lowest luminosities would end inside the grid (rho0 -> 0 at r = 1.30e6
+    and 1.34e6), which the paper's runs cannot have done.
+
+    Returns (cfg, P, info): P holds every cell including the 4 ghosts per
+    radial side ([12, 1, 1, n1 + 8], for harmrad_set_prims_ghosts); info the
+    cell radii, the analytic density and ZAMO-frame radial flux, and the unit
+    conversions."""
+    cfg = base_params()
+    L = _G * _MSUN / _C ** 2                      # length unit GM/c^2
+    rho_u = _MSUN / L ** 3                        # density unit
+    T_u = _MP * _C ** 2 / _KB                     # temperature unit m_p c^2 / k_B
+    kes = 0.4 * rho_u * L                         # kappa_es per length per unit density
+    a_rad = _ARAD * T_u ** 4 / (rho_u * _C ** 2)
+    gam = 5.0 / 3.0
+    rho_in, T_in = rho_in_cgs / rho_u, 2.0 * T_in_K / T_u   # p/rho0 = 2 k T / (m_p c^2)
+    K = rho_in * T_in / rho_in ** gam             # p = rho0 T at r_in
+    x1a, x1b = math.log(r_in), math.log(r_out)
+    dx1 = (x1b - x1a) / n1
+    cfg.update(n=[n1, 1, 1], x0=[x1a, 0.495, 0.0], dx=[dx1, 0.01, 1.0], metric=1, a_spin=0.0, R0=0.0,
+               hslope=1.0, bc=[FIXED, FIXED, PERIODIC, PERIODIC, PERIODIC, PERIODIC], gam=gam,
+               a_rad=a_rad, opacity=OPAC_CONST, kappa_abs0=0.0, kappa_es0=kes, gamma_rad_max=200.0,
+               floor_rho0=1e-60, floor_u0=1e-70)
+    F_edd = 1.0 / (kes * r_in ** 2)
+    C = gam * K / (gam - 1.0) * rho_in ** (gam - 1.0) - (1.0 - f) / r_in
+    ng = 4
+    ii = np.arange(-ng, n1 + ng)
+    r = np.exp(x1a + (ii + 0.5) * dx1)
+    rho = ((gam - 1.0) / (gam * K) * (C + (1.0 - f) / r)) ** (1.0 / (gam - 1.0))
+    Fz = f * F_edd * (r_in / r) ** 2
+    P = np.zeros((NP, 1, 1, len(ii)))
+    P[RHO, 0, 0] = rho
+    P[UU, 0, 0] = K * rho ** gam / (gam - 1.0)
+    for m in range(len(ii)):
+        Ez = Fz[m] / flux_ratio
+        Ebar, g = _m1_from_flux(Ez, Fz[m])
+        # u~^r in the internal chart: orthonormal g v over sqrt(g_{x1 x1}),
+        # g_{x1 x1} = (1 + 2/r) r^2 for Kerr-Schild with a = 0 and r = e^x1
+        P[ER, 0, 0, m] = Ebar
+        P[UR1, 0, 0, m] = math.sqrt(g * g - 1.0) / math.sqrt((1.0 + 2.0 / r[m]) * r[m] ** 2)
+    info = {"r": r, "rho": rho, "Fz": Fz, "F_edd": F_edd, "K": K, "kes": kes, "ng": ng,
+            "units": {"length_cm": L, "density_gcc": rho_u, "temperature_K": T_u}}
+    return cfg, P, info
 
 
 def random_states(n, seed=3, metric=0, gamma_max=50.0, magnetised=True, gamma_rad_max=20.0):

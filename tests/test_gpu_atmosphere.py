@@ -1,0 +1,55 @@
+"""The static radiative atmosphere (Sec. 5, Eqs. atm1, rho, f) on the CUDA
+step: fixed radial boundaries (HARMRAD_BC_FIXED, loaded with
+harmrad_set_prims_ghosts), a Schwarzschild grid with one equatorial theta
+cell.  Against the oracle zone by zone, and against the analytic atmosphere
+after 1000 steps with the bounds the oracle meets
+(tests/test_oracle_atmosphere.py)."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1312_6127_gb300 import harmrad as H
+from paper_1312_6127_gb300 import workloads as W
+from tests.parity_metrics import zone_errors
+from tests.test_oracle_atmosphere import STEPS, measures
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("f", [0.1, 1.0])
+def test_atmosphere_matches_oracle(f):
+    """Ten steps with the oracle's time steps: every zone within 1e-8."""
+    cfg, P, info = W.static_atmosphere(f, flux_ratio=0.99)
+    g = H.Grid(cfg)
+    g.set_prims_ghosts(P)
+    o = O.Oracle(cfg)
+    o.set_prims_with_ghosts(P)
+    for _ in range(10):
+        dt = o.cfl_dt()
+        assert g.cfl_dt() == pytest.approx(dt, rel=1e-12)
+        o.step(dt)
+        g.step(dt)
+        assert np.array_equal(g.status(), o.status())
+    e = zone_errors(cfg, g.get_prims(), o.get_prims())
+    print("f = %.1f, 10 steps: per-zone error %.2e" % (f, e.max()))
+    assert e.max() < 1e-8
+
+
+@pytest.mark.parametrize("f", [0.1, 0.5, 1.0])
+def test_atmosphere_holds_on_gpu(f):
+    cfg, P, info = W.static_atmosphere(f, flux_ratio=0.99)
+    g = H.Grid(cfg)
+    g.set_prims_ghosts(P)
+    for _ in range(STEPS):
+        g.step(0.0)
+    drho, v, spread = measures(cfg, info, g.get_prims())
+    print("GPU f = %.1f: density %.2e, velocity %.2e, flux spread %.2e" % (f, drho, v, spread))
+    assert drho < 1e-4 and v < 1e-6 and spread < 0.03
+
+
+def test_fixed_boundary_rejected_by_the_adjoint():
+    cfg, P, _ = W.static_atmosphere(0.5, flux_ratio=0.99)
+    g = H.Grid(cfg)
+    g.set_prims_ghosts(P)
+    with pytest.raises(H.HarmradError):
+        g.adjoint_enable(True)

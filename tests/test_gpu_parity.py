@@ -63,11 +63,14 @@ def test_zone_implicit_matches_oracle(metric):
         Ps[n, 8] *= 1.0 + 0.3 * g.uniform(-1, 1)
     Pout, eT, it, meth = H.zone_implicit(cfg, x, Ust, Ps, h)
     nsame = 0
+    it_gpu, it_orc = [], []
     for n in range(len(x)):
         Po, info = O.implicit_zone(p, x[n], Ust[n], Ps[n], h[n])
         if info.method != 0 or meth[n] != 0:
             continue
         nsame += 1
+        it_gpu.append(it[n])
+        it_orc.append(info.iters_pmhd)
         e = point_errors(cfg, x[n], Pout[n], Po, cfg["gam"], rad_conserved=True)
         assert e[8:].max() < 1e-10, (n, e)
         if e[:8].max() >= 1e-10:
@@ -75,6 +78,11 @@ def test_zone_implicit_matches_oracle(metric):
             _, eT_o, _ = O.pmhd_residual(p, x[n], Ust[n], h[n], xg)
             assert eT_o < 2.0 * max(eT[n], 1e-9) and e.max() < 1e-7, (n, e, eT_o, eT[n])
     assert nsame > 240
+    # the library's Jacobian (FP32 tangents) against the oracle's finite
+    # differences: Newton steps per PMHD solve, on average
+    mg, mo = float(np.mean(it_gpu)), float(np.mean(it_orc))
+    print("PMHD Newton steps per solve: library %.3f, oracle %.3f" % (mg, mo))
+    assert mg < 1.15 * mo + 0.1
 
 
 @pytest.mark.parametrize("metric", [0, 1])
