@@ -71,6 +71,7 @@ def test_invalid_params_rejected_on_host(lib):
     assert L.harmrad_zone_physics(ctypes.byref(H.make_params(polar_bad)), 0, None, None, None, None,
                                   None, None, None) == -1
     for over, rc in ((dict(integrator=3), 0), (dict(integrator=4), -1), (dict(integrator=-1), -1),
-                     (dict(bc=[3, 3, 0, 0, 0, 0]), 0), (dict(bc=[4, 4, 0, 0, 0, 0]), -1)):
+                     (dict(bc=[3, 3, 0, 0, 0, 0]), 0), (dict(bc=[4, 4, 0, 0, 0, 0]), 0),
+                     (dict(bc=[5, 5, 0, 0, 0, 0]), -1)):
         q = H.make_params(dict(cfg, **over))
         assert L.harmrad_zone_physics(ctypes.byref(q), 0, None, None, None, None, None, None, None) == rc, over
