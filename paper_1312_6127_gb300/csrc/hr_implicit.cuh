@@ -12,7 +12,7 @@
 // one-sided; the paper's two-sided PMHD differences belong to its staged
 // scheme, which is not used; normalised offset 1e-8, switching to 1e-10 once
 // e_I < 1e-9) for the rest of a solve when the FP32 Jacobian is not finite or
-// singular, or when a step taken with it did not halve e_T.  URAD and PRAD
+// singular, or when a step taken with it raised e_T.  URAD and PRAD
 // use the finite differences.  The error, and with it every stopping rule of
 // Sec. 4.10 (tolerance, stalled error, repeated rises, tiny step, step limit)
 // and the best-error bookkeeping, is FP64.
@@ -343,9 +343,9 @@ __device__ __forceinline__ bool newton_pmhd_run(const DevParams& p, const ImpSys
       for (int i = 0; i < 4; ++i) st.best_x[i] = st.x[i];
     }
     if (r.eT < p.newton_tol) break;
-    // a step with the FP32 Jacobian that did not halve e_T: finite
-    // differences for the rest of the solve
-    if (st.jac32 && r.eT > 0.5 * st.hs.t1) st.jac32 = 0;
+    // a step with the FP32 Jacobian that raised e_T: finite differences for
+    // the rest of the solve
+    if (st.jac32 && r.eT > st.hs.t1) st.jac32 = 0;
     if (stalled(st.hs, st.k, r.eT, r.eI)) break;
     if (st.k >= p.newton_max) break;
     if (r.eI < 1e-9) st.eps = 1e-10;
@@ -400,9 +400,9 @@ __device__ int newton_pmhd(const DevParams& p, const ImpSys<MET>& s, const doubl
       for (int i = 0; i < 4; ++i) best_x[i] = x[i];
     }
     if (r.eT < p.newton_tol) break;
-    // a step with the FP32 Jacobian that did not halve e_T: finite
-    // differences for the rest of the solve
-    if (jac32 && r.eT > 0.5 * hs.t1) jac32 = 0;
+    // a step with the FP32 Jacobian that raised e_T: finite differences for
+    // the rest of the solve
+    if (jac32 && r.eT > hs.t1) jac32 = 0;
     if (stalled(hs, k, r.eT, r.eI)) break;
     if (k >= p.newton_max) break;
     if (r.eI < 1e-9) eps = 1e-10;

@@ -23,36 +23,41 @@
 
 namespace hr {
 
-// FP32 value with one directional derivative.
+// FP32 value with one directional derivative.  Every operation is an
+// explicitly rounded intrinsic, which the compiler may not contract into a
+// different multiply-add: the Jacobian is then the same bits in every kernel
+// that evaluates it (the update kernel and the Newton continuation kernel).
 struct F1 {
   float v, d;
 };
 __device__ __forceinline__ F1 fc(float v) { return F1{v, 0.0f}; }
-__device__ __forceinline__ F1 operator+(F1 a, F1 b) { return F1{a.v + b.v, a.d + b.d}; }
-__device__ __forceinline__ F1 operator-(F1 a, F1 b) { return F1{a.v - b.v, a.d - b.d}; }
+__device__ __forceinline__ F1 operator+(F1 a, F1 b) { return F1{__fadd_rn(a.v, b.v), __fadd_rn(a.d, b.d)}; }
+__device__ __forceinline__ F1 operator-(F1 a, F1 b) { return F1{__fsub_rn(a.v, b.v), __fsub_rn(a.d, b.d)}; }
 __device__ __forceinline__ F1 operator-(F1 a) { return F1{-a.v, -a.d}; }
-__device__ __forceinline__ F1 operator+(F1 a, float b) { return F1{a.v + b, a.d}; }
-__device__ __forceinline__ F1 operator+(float a, F1 b) { return F1{a + b.v, b.d}; }
-__device__ __forceinline__ F1 operator-(F1 a, float b) { return F1{a.v - b, a.d}; }
-__device__ __forceinline__ F1 operator-(float a, F1 b) { return F1{a - b.v, -b.d}; }
-__device__ __forceinline__ F1 operator*(F1 a, F1 b) { return F1{a.v * b.v, fmaf(a.d, b.v, a.v * b.d)}; }
-__device__ __forceinline__ F1 operator*(F1 a, float b) { return F1{a.v * b, a.d * b}; }
-__device__ __forceinline__ F1 operator*(float a, F1 b) { return F1{a * b.v, a * b.d}; }
+__device__ __forceinline__ F1 operator+(F1 a, float b) { return F1{__fadd_rn(a.v, b), a.d}; }
+__device__ __forceinline__ F1 operator+(float a, F1 b) { return F1{__fadd_rn(a, b.v), b.d}; }
+__device__ __forceinline__ F1 operator-(F1 a, float b) { return F1{__fsub_rn(a.v, b), a.d}; }
+__device__ __forceinline__ F1 operator-(float a, F1 b) { return F1{__fsub_rn(a, b.v), -b.d}; }
+__device__ __forceinline__ F1 operator*(F1 a, F1 b) {
+  return F1{__fmul_rn(a.v, b.v), __fmaf_rn(a.d, b.v, __fmul_rn(a.v, b.d))};
+}
+__device__ __forceinline__ F1 operator*(F1 a, float b) { return F1{__fmul_rn(a.v, b), __fmul_rn(a.d, b)}; }
+__device__ __forceinline__ F1 operator*(float a, F1 b) { return F1{__fmul_rn(a, b.v), __fmul_rn(a, b.d)}; }
 __device__ __forceinline__ F1 operator/(F1 a, F1 b) {
-  const float ib = 1.0f / b.v, q = a.v * ib;
-  return F1{q, (a.d - q * b.d) * ib};
+  const float ib = __fdiv_rn(1.0f, b.v), q = __fmul_rn(a.v, ib);
+  return F1{q, __fmul_rn(__fsub_rn(a.d, __fmul_rn(q, b.d)), ib)};
 }
 __device__ __forceinline__ F1 operator/(float a, F1 b) {
-  const float ib = 1.0f / b.v, q = a * ib;
-  return F1{q, -q * b.d * ib};
+  const float ib = __fdiv_rn(1.0f, b.v), q = __fmul_rn(a, ib);
+  return F1{q, __fmul_rn(__fmul_rn(-q, b.d), ib)};
 }
 __device__ __forceinline__ F1 fsqrt(F1 a) {
-  const float s = sqrtf(a.v);
-  return F1{s, s > 0.0f ? 0.5f * a.d / s : 0.0f};
+  const float s = __fsqrt_rn(a.v);
+  return F1{s, s > 0.0f ? __fdiv_rn(__fmul_rn(0.5f, a.d), s) : 0.0f};
 }
 __device__ __forceinline__ F1 frsqrt(F1 a) {
   const float s = rsqrtf(a.v);
-  return F1{s, -0.5f * s * s * s * a.d};
+  return F1{s, __fmul_rn(__fmul_rn(__fmul_rn(-0.5f, s), __fmul_rn(s, s)), a.d)};
 }
 
 // FP32 copy of the metric components the error function uses.
@@ -201,7 +206,7 @@ __device__ __forceinline__ bool pmhd_jac_column(const DevParams& p, const Sys& s
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const F1 G = A * urv[k] + C * ucov[k];
-    col[k] = Tc[k].d - h * G.d;
+    col[k] = __fsub_rn(Tc[k].d, __fmul_rn(h, G.d));
     ok = ok && isfinite(col[k]);
   }
   return ok;

@@ -93,8 +93,9 @@ def cases():
 # Tolerance of the kappa_scale derivative.  kappa_scale moves every zone at
 # once; in the stiff case about 4 % of the zone-stages are solved by URAD,
 # whose tolerance is 1e-9 (not the PMHD one), and the implicit-function
-# derivative is exact only at an exact root.
-KAPPA_TOL = {"ks_random_stiff_urad": 1e-5}
+# derivative is exact only at an exact root; at the default Newton tolerance
+# the roots of the differenced runs are known to 1e-12 only.
+KAPPA_TOL = {"ks_random_stiff_urad": 1e-5, "mink_ppm_hll_default_tol": 1e-5, "ks_random_ppm_laxf_default_tol": 1e-5}
 
 
 CASES = cases()
@@ -138,8 +139,10 @@ def test_step_adjoint_against_finite_differences(name):
 
 def test_adjoint_set_input_equals_a_recorded_step():
     """harmrad_adjoint_set_input records a step's input and time step without
-    running it: the adjoint that follows equals, bit for bit, the adjoint
-    after running that step, and leaves the step's result as the primitives."""
+    running it: the adjoint that follows equals the adjoint after running that
+    step (to the round-off of the adjoint's atomic accumulation of stencil
+    cotangents, whose order varies), and leaves the step's result, bit for
+    bit, as the primitives."""
     cfg, P = W.ks_random_state((32, 16, 8), seed=9, tau=1.0)
     rng = W.rng(303)
     w = torch.tensor(rng.standard_normal(P.shape), device="cuda")
@@ -154,7 +157,8 @@ def test_adjoint_set_input_equals_a_recorded_step():
     g2.adjoint_enable(True)
     g2.adjoint_set_input(torch.tensor(P, device="cuda"), dt)
     gB, kB = g2.step_adjoint(w)
-    assert torch.equal(gA, gB) and kA == kB
+    assert float((gA - gB).abs().max()) <= 1e-12 * float(gA.abs().max())
+    assert kA == pytest.approx(kB, rel=1e-12)
     assert torch.equal(g2.get_prims(device=True), after_step)
 
 
