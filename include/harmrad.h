@@ -312,6 +312,28 @@ int harmrad_adjoint_enable(harmrad_ctx* ctx, int on);
 int harmrad_step_adjoint(harmrad_ctx* ctx, const double* gP_out, double* gP_in, double* g_kappa,
                          int on_device);
 
+/* Branch signature, an instrument for derivative checks (the paper has none):
+ * a finite difference (L(P + h v) - L(P - h v)) / 2h measures the derivative
+ * only if the step takes the same branches at P + h v and at P - h v.  With
+ * the signature on, every later step folds each branch decision it takes into
+ * a 64-bit word of the cell concerned: the MC slope limiter's choice per
+ * primitive and direction, the PPM monotonicity limiter's case, the shock
+ * flattener's tests and clamps and the maxima it takes, the wave-speed maxima
+ * of LAXF/HLL and the speed caps of both states at every face, the outflow
+ * clamps of the ghost fill, the floors that act, the TYPE2 limiter and the
+ * solver method of every zone, and the neighbours a back-up averages; each
+ * decision is hashed with its kernel and sub-step and the words combine by
+ * XOR.  Two runs from different states took the same branches everywhere if
+ * and only if their words agree (up to 64-bit hash collisions).
+ * harmrad_branch_signature(ctx, 1) allocates the words (one per cell of the
+ * ghost-inclusive grid, [N3][N2][N1] per grid) and sets them to zero; 0 frees
+ * them.  Drops the captured graphs.  The decisions add no arithmetic to the
+ * step's results. */
+int harmrad_branch_signature(harmrad_ctx* ctx, int on);
+/* Copy the signature words out (host or device memory; ncell values).
+ * HARMRAD_E_STATE if the signature is off.  Synchronises the stream. */
+int harmrad_get_branch_signature(harmrad_ctx* ctx, unsigned long long* out, int on_device);
+
 /* Make P (active layout, host or device per on_device) with time step dt > 0
  * the step that the next harmrad_step_adjoint differentiates, without running
  * that step: P becomes the context's primitives and the adjoint's saved input,

@@ -275,6 +275,7 @@ int enqueue_step(harmrad_ctx* c, bool with_cfl) {
   bool first = true;  // the first sub-step with fluxes restarts the flattener's maximum
   for (int s = 0; s < n_substeps(c->dp.integrator); ++s) {
     const hr::ImexStage im = imex_stage(c->dp.integrator, s);
+    c->dp.sig_salt = s + 1;  // the branch signature tells the sub-steps apart
     if (!im.on || im.d != 0.0) {
       if (!(s == 0 && with_cfl)) {
         if ((r = run_faces(c, first)) < 0) return r;
@@ -285,6 +286,7 @@ int enqueue_step(harmrad_ctx* c, bool with_cfl) {
     if ((r = run_solve(c, s, im)) < 0) return r;
     nk += r;
   }
+  c->dp.sig_salt = 0;
   return nk;
 }
 
@@ -362,7 +364,7 @@ void free_all(harmrad_ctx* c) {
                   c->aux, c->flat[0], c->flat[1], c->flat[2], c->emf, c->edges, c->slope, c->dt, c->status,
                   c->iters, c->failed, c->qcount, c->czone, c->cbox, c->cdata, c->qzone, c->qbox, c->qdata, c->fzone, c->fbox,
                   c->ftmp, c->stats, c->dtmin, c->stage_buf, c->flag, c->dboxes, c->imex_ust, c->imex_psol,
-                  c->imex_M};
+                  c->imex_M, c->sig};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (c->host_dt) cudaFreeHost(c->host_dt);
@@ -829,6 +831,31 @@ int harmrad_adjoint_enable(harmrad_ctx* c, int on) {
   if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess) rc = HARMRAD_E_CUDA;
   if (rc) free_adjoint(c);
   return rc;
+}
+
+int harmrad_branch_signature(harmrad_ctx* c, int on) {
+  if (!c) return HARMRAD_E_ARG;
+  HR_CHECK(cudaStreamSynchronize(c->stream));
+  drop_graphs(c);  // the captured launches carry the signature pointer
+  if (!on) {
+    if (c->sig) cudaFree(c->sig);
+    c->sig = nullptr;
+    c->dp.sig = nullptr;
+    return HARMRAD_OK;
+  }
+  if (!c->sig && dalloc(&c->sig, c->ncell * sizeof(unsigned long long)) != HARMRAD_OK) return HARMRAD_E_OOM;
+  HR_CHECK(cudaMemsetAsync(c->sig, 0, c->ncell * sizeof(unsigned long long), c->stream));
+  c->dp.sig = c->sig;
+  return HARMRAD_OK;
+}
+
+int harmrad_get_branch_signature(harmrad_ctx* c, unsigned long long* out, int on_device) {
+  if (!c || !out) return HARMRAD_E_ARG;
+  if (!c->sig) return HARMRAD_E_STATE;
+  HR_CHECK(cudaMemcpyAsync(out, c->sig, c->ncell * sizeof(unsigned long long),
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  HR_CHECK(cudaStreamSynchronize(c->stream));
+  return HARMRAD_OK;
 }
 
 int harmrad_adjoint_set_input(harmrad_ctx* c, const double* P, double dt, int on_device) {

@@ -75,6 +75,7 @@ struct harmrad_ctx {
   bool use_graph;
   int launches_per_step;
   double last_dt;
+  unsigned long long* sig;   // branch signature per cell (null unless enabled)
   // per-kernel profiling (harmrad_profile_step): an event after every launch
   bool profiling;
   int nev;

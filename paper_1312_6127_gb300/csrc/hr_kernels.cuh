@@ -220,7 +220,11 @@ static __global__ void k_bc_fill(DevParams p, const BoxGeo* __restrict__ boxes, 
       for (int q = 0; q < NPR; ++q) {
         double v = P[q * bx.ntot + s];
         if (q == U1 + d || q == B1 + d || q == UR1 + d) v *= sgn;
-        if (clamp != 0 && (q == U1 + d || q == UR1 + d)) v = clamp < 0 ? fmin(v, 0.0) : fmax(v, 0.0);
+        if (clamp != 0 && (q == U1 + d || q == UR1 + d)) {
+          const double vc = clamp < 0 ? fmin(v, 0.0) : fmax(v, 0.0);
+          if (p.sig) sig_put(p, bx.coff + t, 50 + d, (unsigned long long)q << 8 | (vc != v ? 1u : 0u));
+          v = vc;
+        }
         P[q * bx.ntot + t] = v;
       }
       if (K) K[t] = K[s];
@@ -313,6 +317,39 @@ __device__ __forceinline__ void flatten_cell(const FlatCell<R>* c, R* Fg, R* Fr)
   *Fr = (R(1) - w) * fr + w * mx;
 }
 
+// Branches of the flattener of cell 3 of c[0..6] (flatten_cell): each
+// ftilde's compression test and clamp, the neighbour chosen, the maxima taken.
+template <typename R>
+__device__ __forceinline__ unsigned ftilde_code(const FlatCell<R>* c, int m, bool gas, R w) {
+  auto pe = [&](int o) { return gas ? c[m + o].pg + w * c[m + o].pr : c[m + o].pr + w * c[m + o].pg; };
+  auto ve = [&](int o) { return gas ? c[m + o].vg : c[m + o].vr; };
+  R dp1 = pe(1) - pe(-1), dp2 = pe(2) - pe(-2);
+  R dv = ve(1) - ve(-1);
+  R p1 = pe(1), pm = pe(-1);
+  if (!(fabs(dp1) > R(0.33) * (p1 < pm ? p1 : pm) && dv < R(0))) return 0u;
+  R sp = dp2 != R(0) ? dp1 / dp2 : R(0);
+  R f = R(10) * (sp - R(0.75));
+  return f <= R(0) ? 1u : (f >= R(1) ? 3u : 2u);
+}
+template <typename R>
+__device__ __forceinline__ unsigned flatten_code(const FlatCell<R>* c, R og, R orr) {
+  const R w = c[3].w;
+  R g0 = ftilde<R>(c, 3, true, w), r0 = ftilde<R>(c, 3, false, w);
+  R pg1 = c[4].pg + w * c[4].pr, pgm = c[2].pg + w * c[2].pr;
+  R pr1 = c[4].pr + w * c[4].pg, prm = c[2].pr + w * c[2].pg;
+  int sg = (pg1 - pgm) < R(0) ? 1 : -1;
+  int sr = (pr1 - prm) < R(0) ? 1 : -1;
+  R gn = ftilde<R>(c, 3 + sg, true, c[3 + sg].w);
+  R rn = ftilde<R>(c, 3 + sr, false, c[3 + sr].w);
+  R fg = g0 > gn ? g0 : gn, fr = r0 > rn ? r0 : rn;
+  R Fg = (R(1) - w) * fg + w * (fg > fr ? fg : fr), Fr = (R(1) - w) * fr + w * (fg > fr ? fg : fr);
+  unsigned k = ftilde_code<R>(c, 3, true, w) | ftilde_code<R>(c, 3, false, w) << 2 |
+               ftilde_code<R>(c, 3 + sg, true, c[3 + sg].w) << 4 | ftilde_code<R>(c, 3 + sr, false, c[3 + sr].w) << 6;
+  k |= (sg > 0 ? 1u : 0u) << 8 | (sr > 0 ? 1u : 0u) << 9 | (g0 > gn ? 1u : 0u) << 10 | (r0 > rn ? 1u : 0u) << 11;
+  k |= (fg > fr ? 1u : 0u) << 12 | (Fg > og ? 1u : 0u) << 13 | (Fr > orr ? 1u : 0u) << 14;
+  return k;
+}
+
 template <typename R>
 __global__ void k_flatten(DevParams p, const BoxGeo* __restrict__ boxes, int nbox,
                           const double* __restrict__ P0, const R* __restrict__ aux0,
@@ -354,6 +391,7 @@ __global__ void k_flatten(DevParams p, const BoxGeo* __restrict__ boxes, int nbo
       R Fg, Fr;
       flatten_cell<R>(c, &Fg, &Fr);
       R og = flat[t], orr = flat[bx.ntot + t];
+      if (p.sig) sig_put(p, bx.coff + t, 30 + d, flatten_code<R>(c, og, orr));
       flat[t] = Fg > og ? Fg : og;
       flat[bx.ntot + t] = Fr > orr ? Fr : orr;
     }
@@ -370,6 +408,41 @@ __device__ __forceinline__ R mc_slope(R qm, R q0, R qp) {
   m = m < a ? m : a;
   m = m < b ? m : b;
   return dc > R(0) ? m : -m;
+}
+
+// Branch of mc_slope: 0 opposite one-sided slopes (zero), 1 central,
+// 2 twice the left, 3 twice the right difference.
+template <typename R>
+__device__ __forceinline__ unsigned mc_code(R qm, R q0, R qp) {
+  R dl = q0 - qm, dr = qp - q0, dc = R(0.5) * (qp - qm);
+  if (dl * dr <= R(0)) return 0u;
+  R m = fabs(dc);
+  R a = R(2) * fabs(dl), b = R(2) * fabs(dr);
+  unsigned c = 1u;
+  if (a < m) {
+    m = a;
+    c = 2u;
+  }
+  if (b < m) c = 3u;
+  return c;
+}
+
+// Branch of the PPM monotonicity limiter (ppm_slopes): 0 none, 1 flat,
+// 2 left edge moved, 3 right edge moved.
+template <typename R>
+__device__ __forceinline__ unsigned ppm_code(R sm, R s0, R sp, R dm, R d0, R dp, R chi) {
+  const R sixth = R(1.0 / 6.0);
+  R l = R(0.5) * (sm + s0) - (d0 - dm) * sixth;
+  R r = R(0.5) * (s0 + sp) - (dp - d0) * sixth;
+  R q = s0;
+  l = (R(1) - chi) * l + chi * q;
+  r = (R(1) - chi) * r + chi * q;
+  if ((r - q) * (q - l) <= R(0)) return 1u;
+  R dd = r - l;
+  R m6 = R(6) * (q - R(0.5) * (l + r));
+  if (dd * m6 > dd * dd) return 2u;
+  if (-dd * dd > dd * m6) return 3u;
+  return 0u;
 }
 
 // PPM edge values of the centre of s[0..4] (Colella & Woodward 1984, no
@@ -455,6 +528,7 @@ __global__ void __launch_bounds__(256) k_slopes(DevParams p, const BoxGeo* __res
           s[m] = wq ? gw[m] * v : v;
         }
         S[q * bx.ntot + t] = mc_slope<R>(s[0], s[1], s[2]);
+        if (p.sig) sig_put(p, bx.coff + t, 10 + d, (unsigned long long)q << 8 | mc_code<R>(s[0], s[1], s[2]));
       }
     }
   }
@@ -550,6 +624,9 @@ __global__ void __launch_bounds__(256) k_edges(DevParams p, const BoxGeo* __rest
             ds[m] = S[q * bx.ntot + t + (m - 1) * st];
           }
           ppm_slopes<R>(s[0], s[1], s[2], ds[0], ds[1], ds[2], q < ER ? chg : chr, &aL, &aR);
+          if (p.sig)
+            sig_put(p, bx.coff + t, 20 + d,
+                    (unsigned long long)q << 8 | ppm_code<R>(s[0], s[1], s[2], ds[0], ds[1], ds[2], q < ER ? chg : chr));
         } else {
           R v = R(P[q * bx.ntot + t]);
           if (wq) v = aux[t] * v;
@@ -571,14 +648,25 @@ __global__ void __launch_bounds__(256) k_edges(DevParams p, const BoxGeo* __rest
 // Used by the face kernel and, on dual numbers, by the adjoint.
 template <int MET, typename R, int d>
 __device__ __forceinline__ void face_flux(const DevParams& p, const Geo<MET, R>& g, R dxd, R kL, R kR, R ks,
-                                          const R PL[NPR], const R PR[NPR], R out[NPR], R* smax) {
+                                          const R PL[NPR], const R PR[NPR], R out[NPR], R* smax,
+                                          unsigned* code = nullptr) {
   R sL[4], sR[4];
-  face_speeds<MET, R>(p, g, d + 1, dxd, kL, ks, PL, sL);
-  face_speeds<MET, R>(p, g, d + 1, dxd, kR, ks, PR, sR);
+  unsigned cL = 0, cR = 0;
+  face_speeds<MET, R>(p, g, d + 1, dxd, kL, ks, PL, sL, code ? &cL : nullptr);
+  face_speeds<MET, R>(p, g, d + 1, dxd, kR, ks, PR, sR, code ? &cR : nullptr);
   R cmaxg = fmax(R(0), fmax(sL[1], sR[1]));
   R cming = -fmin(R(0), fmin(sL[0], sR[0]));
   R cmaxr = fmax(R(0), fmax(sL[3], sR[3]));
   R cminr = -fmin(R(0), fmin(sL[2], sR[2]));
+  if (code) {  // which signal speed each maximum took, and the speed caps
+    unsigned c = cL | (cR << 3);
+    c |= (sL[1] >= sR[1] ? 0u : 1u) << 6 | (R(0) > fmax(sL[1], sR[1]) ? 1u : 0u) << 7;
+    c |= (sL[0] <= sR[0] ? 0u : 1u) << 8 | (R(0) < fmin(sL[0], sR[0]) ? 1u : 0u) << 9;
+    c |= (sL[3] >= sR[3] ? 0u : 1u) << 10 | (R(0) > fmax(sL[3], sR[3]) ? 1u : 0u) << 11;
+    c |= (sL[2] <= sR[2] ? 0u : 1u) << 12 | (R(0) < fmin(sL[2], sR[2]) ? 1u : 0u) << 13;
+    c |= (cmaxg > cming ? 1u : 0u) << 14 | (cmaxr > cminr ? 1u : 0u) << 15;
+    *code = c;
+  }
   // weights of (F_L, U_L) and (F_R, U_R) in the flux, gas and radiation groups
   R fLg, uLg, fRg, uRg, fLr, uLr, fRr, uRr;
   if (p.flux == 0) {  // LAXF: 1/2 (F_L + F_R - c (U_R - U_L))
@@ -698,7 +786,9 @@ __global__ void __launch_bounds__(128) k_face(DevParams p, const BoxGeo* __restr
       }
       const R kL = R(kfield(p, K, t - st)), kR = R(kfield(p, K, t));
       R out[NPR], smax;
-      face_flux<MET, R, d>(p, g, dxd, kL, kR, R(p.kscale), PL, PR, out, &smax);
+      unsigned fcode = 0;
+      face_flux<MET, R, d>(p, g, dxd, kL, kR, R(p.kscale), PL, PR, out, &smax, p.sig ? &fcode : nullptr);
+      if (p.sig) sig_put(p, bx.coff + t, 40 + d, fcode);
 #pragma unroll
       for (int q = 0; q < NPR; ++q) F[q * bx.ntot + t] = out[q];
       spd[t] = smax;
@@ -773,8 +863,15 @@ __global__ void k_ct(DevParams p, const BoxGeo* __restrict__ boxes, int nbox, co
 // Lorentz-factor caps, density and internal-energy floors f0 r^pow,
 // magnetisation caps b^2/rho, b^2/u_g, u_g/rho, and Ebar > 0.
 template <int MET, typename T = double>
-__device__ __forceinline__ void apply_floors(const DevParams& p, const Geo<MET, T>& g, double r, T P[NPR]) {
+__device__ __forceinline__ void apply_floors(const DevParams& p, const Geo<MET, T>& g, double r, T P[NPR],
+                                             unsigned* code = nullptr) {
   T gm = sqrt(1.0 + g.sq3(P[U1], P[U2], P[U3]));
+  if (code) {  // which floors act (the branch signature)
+    *code = 0;
+    const T gr0 = sqrt(1.0 + g.sq3(P[UR1], P[UR2], P[UR3]));
+    if (gm > p.ggas_max) *code |= 1u;
+    if (gr0 > p.grad_max) *code |= 2u;
+  }
   if (gm > p.ggas_max) {
     T f = sqrt((p.ggas_max * p.ggas_max - 1.0) / (gm * gm - 1.0));
     P[U1] *= f;
@@ -793,6 +890,13 @@ __device__ __forceinline__ void apply_floors(const DevParams& p, const Geo<MET, 
   bvec<MET, T>(g, ucon, ucov, P[B1], P[B2], P[B3], bcon, bcov, &bsq);
   T rfl = T(p.rf0 * (p.rfp == 0.0 ? 1.0 : pow(r, p.rfp)));
   T ufl = T(p.uf0 * (p.ufp == 0.0 ? 1.0 : pow(r, p.ufp)));
+  if (code) {
+    const T rb = bsq / p.bsq_rho_max, ub = bsq / p.bsq_u_max;
+    const T rf = fmax(rfl, rb), uf = fmax(ufl, ub);
+    const T u1 = fmax(P[UU], uf);
+    *code |= (rb > rfl ? 4u : 0u) | (ub > ufl ? 8u : 0u) | (rf > P[RHO] ? 16u : 0u) | (uf > P[UU] ? 32u : 0u) |
+             (u1 / p.u_rho_max > fmax(P[RHO], rf) ? 64u : 0u) | (!(P[ER] > 0.0) ? 128u : 0u);
+  }
   rfl = fmax(rfl, bsq / p.bsq_rho_max);
   ufl = fmax(ufl, bsq / p.bsq_u_max);
   P[RHO] = fmax(P[RHO], rfl);
@@ -805,10 +909,16 @@ __device__ __forceinline__ void apply_floors(const DevParams& p, const Geo<MET, 
 // re-inverted with BASIC if the TYPE2 branch saw a negative energy (Sec. 4.10).
 template <int MET, typename T = double>
 __device__ __forceinline__ void pmhd_final(const DevParams& p, const ImpSysT<MET, T>& s, const T x[4], T P[NPR],
-                                           T* Eg = nullptr) {
+                                           T* Eg = nullptr, unsigned* code = nullptr) {
   ImpResT<T> r;
   ImpStateT<T> stt;
   pmhd_res<MET, T>(p, s, x, r, &stt, false);
+  if (code) {  // the TYPE2 limiter's branch at the solution (the branch signature)
+    T Prt[4];
+    int lim = 0;
+    rad_invert<MET, T>(p, s.g, stt.Rt_pre, 2, Prt, &lim);
+    *code = (unsigned)r.negE | (unsigned)lim << 1;
+  }
   if (Eg)
     for (int k = 0; k < 4; ++k) Eg[k] = r.Eg[k];
   P[RHO] = stt.rho;
@@ -1141,10 +1251,13 @@ __device__ __forceinline__ bool pmhd_finish(const DevParams& p, const BoxGeo& bx
   const bool accept = beT >= 0.0 && beT < 1e-9;  // beT < 0: sub-dominant radiation, URAD first
   if (accept) {
     double Pn[NPR];
-    pmhd_final<MET>(p, s, best_x, Pn);
+    unsigned lcode = 0;
+    pmhd_final<MET, double>(p, s, best_x, Pn, nullptr, p.sig ? &lcode : nullptr);
     if (b.psol_rec)
       for (int q = 0; q < NPR; ++q) b.psol_rec[12 * bx.aoff + q * bx.nact + z] = Pn[q];
-    apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn);
+    unsigned fcode = 0;
+    apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn, p.sig ? &fcode : nullptr);
+    if (p.sig) sig_put(p, bx.coff + t, 60, (fcode << 2 | lcode) << 4 | ST_PMHD);
 #pragma unroll
     for (int q = 0; q < NPR; ++q) P[q * bx.ntot + t] = Pn[q];
     if (b.meth_rec) b.meth_rec[zg] = ST_PMHD;
@@ -1459,7 +1572,9 @@ __global__ void __launch_bounds__(128) k_retry(DevParams p, const BoxGeo* __rest
     b.iters[zg] += steps;
     if (b.psol_rec)
       for (int q = 0; q < NPR; ++q) b.psol_rec[12 * bx.aoff + q * bx.nact + z] = Pn[q];
-    apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn);
+    unsigned fcode = 0;
+    apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn, p.sig ? &fcode : nullptr);
+    if (p.sig) sig_put(p, bx.coff + t, 60, fcode << 4 | (unsigned)method);
     for (int q = 0; q < NPR; ++q) P[q * bx.ntot + t] = Pn[q];
     unsigned char m = (unsigned char)method;
     if (m > b.status[zg]) b.status[zg] = m;
@@ -1516,6 +1631,7 @@ static __global__ void k_backup_avg(DevParams p, const BoxGeo* __restrict__ boxe
       }
     }
     long long t = cell_index(bx, ii[0], ii[1], ii[2]);
+    if (p.sig) sig_put(p, bx.coff + t, 61, (unsigned)ng << 4 | (unsigned)na);
     for (int q = 0; q < NPR; ++q) {
       double v = P[q * bx.ntot + t];
       if (na > 0 && !(q >= B1 && q <= B3)) v = ng > 0 ? sg[q] / ng : sa[q] / na;
@@ -1541,7 +1657,9 @@ __global__ void k_backup_apply(DevParams p, const BoxGeo* __restrict__ boxes, Bu
     Geo<MET, double> g = make_geo<MET, double>(p, x1, x2);
     double Pn[NPR];
     for (int q = 0; q < NPR; ++q) Pn[q] = b.ftmp[(long long)e * NPR + q];
-    apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn);
+    unsigned fcode = 0;
+    apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn, p.sig ? &fcode : nullptr);
+    if (p.sig) sig_put(p, bx.coff + t, 62, fcode);
     for (int q = 0; q < NPR; ++q) P[q * bx.ntot + t] = Pn[q];
   }
 }

@@ -38,7 +38,31 @@ struct DevParams {
   double newton_tol;
   int precision;
   int integrator;  // 0 RK3, 1 IMEX2, 2 IMEX2B, 3 IMEX3 (Sec. 4.1)
+  // branch signature (a test instrument; null unless enabled): per cell a
+  // 64-bit word into which every branch decision of the step is folded
+  unsigned long long* sig;
+  int sig_salt;  // sub-step of the decisions (0: the CFL pass)
 };
+
+// Fold one decision `code` of kernel `kernel` about cell `cell` (index into
+// the context's cell arrays) into the branch signature.  Two runs took the
+// same branches everywhere if and only if their words agree (up to 64-bit
+// hash collisions).  The decision is hashed with the kernel and the sub-step,
+// and words combine by XOR, so the order in which threads add them does not
+// matter.
+__device__ __forceinline__ unsigned long long sig_hash(unsigned long long a, unsigned long long b) {
+  unsigned long long h = (a * 0x9E3779B97F4A7C15ULL) ^ (b + 0x632BE59BD9B4E019ULL);
+  h ^= h >> 29;
+  h *= 0xBF58476D1CE4E5B9ULL;
+  h ^= h >> 32;
+  h *= 0x94D049BB133111EBULL;
+  h ^= h >> 31;
+  return h;
+}
+__device__ __forceinline__ void sig_put(const DevParams& p, long long cell, unsigned kernel,
+                                        unsigned long long code) {
+  atomicXor(p.sig + cell, sig_hash(((unsigned long long)kernel << 32) | (unsigned)p.sig_salt, code));
+}
 
 // Geometry of one grid of a context: sizes, ghost depth, strides, internal
 // coordinates, boundary conditions and the grid's offsets in the context's
@@ -350,7 +374,7 @@ __device__ __forceinline__ void face_state(const DevParams& p, const Geo<MET, R>
 // dxd is the cell size along d and kf the per-zone opacity of the state's cell.
 template <int MET, typename R>
 __device__ __forceinline__ void face_speeds(const DevParams& p, const Geo<MET, R>& g, int d, R dxd,
-                                            R kf, R ks, const R P[NPR], R sp[4]) {
+                                            R kf, R ks, const R P[NPR], R sp[4], unsigned* code = nullptr) {
   R ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq;
   fourvel<MET, R>(g, P[U1], P[U2], P[U3], ucon, ucov, &gm);
   bvec<MET, R>(g, ucon, ucov, P[B1], P[B2], P[B3], bcon, bcov, &bsq);
@@ -360,6 +384,7 @@ __device__ __forceinline__ void face_speeds(const DevParams& p, const Geo<MET, R
   R cs2 = R(p.gam) * pg / w;
   R va2 = bsq / (w + bsq);
   R cms2 = cs2 + va2 - cs2 * va2;
+  if (code) *code = (cms2 > R(1) ? 1u : 0u) | (cms2 < R(0) ? 2u : 0u);
   cms2 = cms2 > R(1) ? R(1) : (cms2 < R(0) ? R(0) : cms2);
   char_speeds<MET, R>(g, ucon, cms2, d, &sp[0], &sp[1]);
   R urc[4], urv[4], gr;
@@ -371,6 +396,7 @@ __device__ __forceinline__ void face_speeds(const DevParams& p, const Geo<MET, R
   if (tau > R(0)) {
     R lim = R(4.0 / 3.0) / tau;
     lim = lim * lim;
+    if (code && lim < cr2) *code |= 4u;
     cr2 = lim < cr2 ? lim : cr2;
   }
   char_speeds<MET, R>(g, urc, cr2, d, &sp[2], &sp[3]);
@@ -424,7 +450,7 @@ __device__ __forceinline__ void face_accum(const DevParams& p, const Geo<MET, R>
 // (lim 2).  Returns 1 if E_rad <= 0 on entry.
 template <int MET, typename T = double>
 __device__ __forceinline__ int rad_invert(const DevParams& p, const Geo<MET, T>& g, const T Rt[4], int lim,
-                                          T out[4]) {
+                                          T out[4], int* limited = nullptr) {
   const T a = g.alpha;
   T Erad = a * a * g.raise_t(Rt);
   T Ut[3];
@@ -457,6 +483,7 @@ __device__ __forceinline__ int rad_invert(const DevParams& p, const Geo<MET, T>&
     }
   } else {
     y = Erad > 0.0 ? (Utsq > 0.0 ? Utsq / (Erad * Erad) : T(0.0)) : T(HUGE_VAL);
+    if (limited) *limited = (Erad <= 0.0 || y > ymax) ? 1 : 0;
     if (Erad <= 0.0 || y > ymax) {
       Erad = T(1e-150) + sqrt(Utsq / T(ymax));
       y = Utsq / (Erad * Erad);

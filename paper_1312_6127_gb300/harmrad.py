@@ -28,6 +28,7 @@ EXPORTS = [
     "harmrad_zone_physics", "harmrad_zone_implicit", "harmrad_zone_implicit_static",
     "harmrad_profile_step", "harmrad_autotune", "harmrad_get_tuning", "harmrad_set_tuning",
     "harmrad_adjoint_enable", "harmrad_step_adjoint", "harmrad_adjoint_set_input",
+    "harmrad_branch_signature", "harmrad_get_branch_signature",
     "harmrad_fp64_fma_rate",
     "harmrad_strerror",
 ]
@@ -142,6 +143,8 @@ def load(path=LIB_PATH):
     L.harmrad_get_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
     L.harmrad_set_tuning.argtypes = [vp, ctypes.POINTER(Tuning)]
     L.harmrad_adjoint_set_input.argtypes = [vp, vp, ctypes.c_double, ip]
+    L.harmrad_branch_signature.argtypes = [vp, ip]
+    L.harmrad_get_branch_signature.argtypes = [vp, vp, ip]
     L.harmrad_fp64_fma_rate.argtypes = [ip, dp, vp]
     L.harmrad_strerror.restype = ctypes.c_char_p
     L.harmrad_strerror.argtypes = [ip]
@@ -266,6 +269,19 @@ class Grid:
     def adjoint_enable(self, on=True):
         """Keep each step's input so that step_adjoint can differentiate it."""
         _check(load().harmrad_adjoint_enable(self._h, 1 if on else 0), "adjoint_enable")
+
+    def branch_signature(self, on=True):
+        """Start (zeroed) or stop the per-cell branch signature of later steps."""
+        _check(load().harmrad_branch_signature(self._h, 1 if on else 0), "branch_signature")
+
+    def get_branch_signature(self):
+        """The signature words of every cell (ghost-inclusive, uint64, numpy)."""
+        ng = [4 if x > 1 else 0 for x in self.cfg["n"]]
+        n = int(np.prod([self.cfg["n"][i] + 2 * ng[i] for i in range(3)]))
+        out = np.empty(n, dtype=np.uint64)
+        _check(load().harmrad_get_branch_signature(self._h, out.ctypes.data_as(ctypes.c_void_p), 0),
+               "get_branch_signature")
+        return out
 
     def adjoint_set_input(self, P, dt):
         """Record P (float64 CUDA tensor, active layout) and dt as the input of

@@ -10,8 +10,9 @@
   oracle's finite differences;
 - the torch.autograd front end, 20 steps with checkpoints every 5, loss = the
   radiative energy flux through r = 40: on a random Kerr-Schild state
-  (exact agreement expected) and on the 128x64x32 torus with 64 seeded
-  directions.
+  (exact agreement expected) and on the 128x64x32 torus, where the step's
+  branch signature separates the directions whose differences cross a
+  branch switch from those that measure the derivative.
 
 Most checks solve the implicit step to round-off (Newton tolerance 1e-15
 instead of 1e-12): the adjoint differentiates the exact root, and a root
@@ -26,7 +27,8 @@ ratio lies within h of a switching point; over one step the adjoint must
 agree to 1e-6 (it agrees to ~1e-9).  The torus varies by 2 % from zone to
 zone and is nearly symmetric, so thousands of limiter ratios sit within 1e-7
 of a switch and single differences scatter up to the 1e-3 level; that test
-reports the scatter and checks the median.
+records every branch decision of both runs of each difference and holds the
+directions that switch no branch to 1e-6.
 """
 import math
 
@@ -162,6 +164,25 @@ def test_adjoint_set_input_equals_a_recorded_step():
     assert torch.equal(g2.get_prims(device=True), after_step)
 
 
+def test_branch_signature_records_without_changing_the_step():
+    """The branch signature changes no result bit; the same state gives the
+    same words; a state perturbed by 30 % takes other branches somewhere."""
+    cfg, P = W.ks_random_state((32, 16, 8), seed=9, tau=1.0)
+    out, sigs = [], []
+    for Q, on in ((P, False), (P, True), (P, True), (P * (1 + 0.3 * W.rng(4).uniform(-1, 1, P.shape)), True)):
+        g = H.Grid(cfg)
+        g.set_prims(Q)
+        if on:
+            g.branch_signature(True)
+        g.step(0.0)
+        g.step(0.0)
+        out.append(g.get_prims())
+        sigs.append(g.get_branch_signature() if on else None)
+    assert np.array_equal(out[0], out[1])
+    assert np.array_equal(sigs[1], sigs[2]) and (sigs[1] != 0).mean() > 0.5
+    assert (sigs[1] != sigs[3]).sum() > 100
+
+
 def test_step_adjoint_against_oracle_differences():
     """Random Kerr-Schild state, two steps (the one-step adjoints chained):
     directional derivatives against central differences of the oracle."""
@@ -293,12 +314,97 @@ def test_autograd_flux_loss_random_ks():
 
 
 def test_autograd_flux_loss_torus128():
-    """The 128x64x32 torus, 20 steps, checkpoints every 5: 64 seeded smooth
-    directions and kappa_scale.  The differences scatter at the 1e-4..1e-3
-    level (limiter switches; see the module docstring), so the median is
-    checked and the spread reported."""
+    """The adjoint's torus check: the 128x64x32 torus, 20 steps, checkpoints
+    every 5, loss = the radiative flux through r = 40.  Each direction's two
+    runs at P +- h v record the step's branch signature
+    (harmrad_branch_signature: every limiter, flattener, wave-speed, clamp,
+    floor and method decision of every zone and sub-step).  Where the two
+    runs took the same branches everywhere the difference measures the
+    derivative, and the adjoint must agree with it to 1e-6; where a branch
+    switched the difference crosses a kink, and its error is reported.
+    Directions: 64 smooth global ones (relative perturbations of low
+    wavenumber in every primitive, h = 1e-6) and 16 concentrated on single
+    zones (all primitives of one zone, h = 1e-6), which reach far fewer
+    switching points.  Also the oracle's own central difference along 4 of
+    the smooth directions (h = 1e-5): its 20-step state agrees with the
+    library's to 1e-10 per zone, which bounds that comparison near 1e-10/h."""
+    import os
+    from paper_1312_6127_gb300 import autograd as AG
     cfg, P = W.generic_torus((128, 64, 32), seed=12345)
-    Lv, errs, gks, kerr = autograd_check(dict(cfg, newton_tol=TOL), P, 20, 64, True)
-    print("torus 128x64x32, loss %.10e: 64 directions, rel err median %.2e p90 %.2e max %.2e; "
-          "kappa_scale %.10e (%.2e)" % (Lv, np.median(errs), np.quantile(errs, 0.9), errs.max(), gks, kerr))
-    assert np.median(errs) < 1e-4
+    cfg = dict(cfg, newton_tol=TOL)
+    nsteps = 20
+    i0, a = flux_loss_setup(cfg)
+    g = H.Grid(cfg)
+    g.set_prims(P)
+    dt = 0.9 * g.cfl_dt()
+    P0 = torch.tensor(P, device="cuda", requires_grad=True)
+    ks = torch.tensor(cfg["kappa_scale"], dtype=torch.float64, requires_grad=True)
+    Pf = AG.steps(g, P0, ks, nsteps, checkpoint=5, dt=dt)
+    Lv, GL = flux_loss(cfg, Pf.detach().cpu().numpy(), i0, a)
+    Pf.backward(torch.tensor(GL, device="cuda"))
+    gP0 = P0.grad.cpu().numpy()
+
+    def L_sig(Q):
+        gg = H.Grid(cfg)
+        gg.set_prims(Q)
+        gg.branch_signature(True)
+        for _ in range(nsteps):
+            gg.step(dt)
+        return flux_loss(cfg, gg.get_prims(), i0, a)[0], gg.get_branch_signature()
+
+    rng = W.rng(505)
+    results = {"smooth": [], "zone": []}
+    smooth_dirs = []
+    for kind, count in (("smooth", 64), ("zone", 16)):
+        for _ in range(count):
+            if kind == "smooth":
+                v = direction(P, rng, smooth=True)
+                smooth_dirs.append(v)
+            else:
+                v = np.zeros_like(P)
+                z = tuple(int(rng.integers(0, m)) for m in P.shape[1:])
+                v[(slice(None),) + z] = rng.standard_normal(12) * np.abs(P[(slice(None),) + z])
+            h = 1e-6
+            Lp, sp = L_sig(P + h * v)
+            Lm, sm = L_sig(P - h * v)
+            ad = float((gP0 * v).sum())
+            fd = (Lp - Lm) / (2 * h)
+            err = abs(ad - fd) / max(abs(ad), abs(fd), 1e-300)
+            results[kind].append((err, int((sp != sm).sum())))
+    for kind in results:
+        e = np.array([r[0] for r in results[kind]])
+        ncell = np.array([r[1] for r in results[kind]])
+        same = ncell == 0
+        print("torus 128x64x32, loss %.10e, %s directions: %d of %d cross no branch switch "
+              "(their worst error %.2e); the others switch branches in %d cells on average, "
+              "error median %.2e, max %.2e"
+              % (Lv, kind, int(same.sum()), len(e), e[same].max() if same.any() else float("nan"),
+                 int(ncell[~same].mean()) if (~same).any() else 0,
+                 np.median(e[~same]) if (~same).any() else float("nan"), e[~same].max() if (~same).any() else 0.0))
+        if same.any():
+            assert e[same].max() < 1e-6
+    nsame = sum(r[1] == 0 for k in results for r in results[k])
+    assert nsame >= 4, "too few directions without a branch switch to check the adjoint"
+    # the oracle's own differences along four smooth directions
+    old = os.environ.get("ORACLE_THREADS")
+    os.environ["ORACLE_THREADS"] = str(os.cpu_count() or 1)
+    try:
+        def L_orc(Q):
+            o = O.Oracle(cfg)
+            o.set_prims(Q)
+            for _ in range(nsteps):
+                o.step(dt)
+            return flux_loss(cfg, o.get_prims(), i0, a)[0]
+        oerr = []
+        for v in smooth_dirs[:4]:
+            h = 1e-5
+            fd = (L_orc(P + h * v) - L_orc(P - h * v)) / (2 * h)
+            ad = float((gP0 * v).sum())
+            oerr.append(abs(ad - fd) / max(abs(ad), abs(fd)))
+    finally:
+        if old is None:
+            del os.environ["ORACLE_THREADS"]
+        else:
+            os.environ["ORACLE_THREADS"] = old
+    print("oracle central differences (h = 1e-5) against the adjoint: %s" % ["%.2e" % x for x in oerr])
+    assert np.median(oerr) < 1e-3
