@@ -64,6 +64,8 @@ typedef struct {
   int integrator;         /* 0 RK3 with the same coefficients for the explicit and
                              implicit parts (the paper's runs), 1 IMEX2, 2 IMEX2B,
                              3 IMEX3 (Sec. 4.1, Eqs. IMEX2, IMEX2B, IMEX3) */
+  int implicit_eq;        /* 0 energy equations, the entropy equation as back-up (RK3);
+                             1 the entropy equation in every zone (RK3) */
 } orc_params;
 
 /* Per-zone solver outcome codes (same meaning as the library's status byte). */
@@ -75,6 +77,7 @@ typedef struct {
   int iters_urad;  /* Newton iterations taken by the URAD attempt (0 if none) */
   int method;      /* ORC_OK_PMHD, ORC_OK_URAD or ORC_BACKUP */
   int neg_erad;    /* 1 if the accepted solution hit the TYPE2 negative-energy branch */
+  int entropy;     /* 1 if the entropy equation gave the accepted solution */
 } orc_implicit_info;
 
 /* --- grid-level driver --------------------------------------------------- */
@@ -93,7 +96,8 @@ void   orc_get_status(void* ctx, unsigned char* st);
 /* Per-zone Newton iteration totals summed over the three stages of the last step. */
 void   orc_get_iters(void* ctx, int* it);
 /* Counts over the last step: [0] PMHD-accepted, [1] URAD-accepted, [2] back-up,
- * [3] total Newton iterations, [4] zone-stages solved. */
+ * [3] total Newton iterations, [4] zone-stages solved, [5] zone-stages whose
+ * accepted solution came from the entropy equation. */
 void   orc_get_counts(void* ctx, long long* c);
 /* Face fluxes of one direction after the last call to orc_compute_fluxes
  * (debug/test hook): computes ghost fill + fluxes (+flux-CT) for the current
@@ -137,10 +141,11 @@ int    orc_gas_invert(const orc_params* p, const double* x, const double* U,
  * sub-dominant (URAD first in the grid step). */
 int    orc_radiation_subdominant(const orc_params* p, const double* x, const double* Ustar,
                                  const double* Ps);
-/* Implicit four-force solve of one zone: U* (12, densitised), guess P_s,
+/* Implicit four-force solve of one zone: U* (12, densitised), the explicit
+ * entropy S* = sqrt(-g) S u^t (NULL: no entropy back-up), guess P_s,
  * h = b_s*dt, the grid step's method sequence.  Writes the new prims and info. */
 void   orc_implicit_zone(const orc_params* p, const double* x, const double* Ustar,
-                         const double* Ps, double h, double* Pout,
+                         const double* Sstar, const double* Ps, double h, double* Pout,
                          orc_implicit_info* info);
 /* One Newton method alone on one zone (test hook): method 0 PMHD (guess the
  * gas of Ps), 1 URAD (guess R^t_nu of Ps), 2 PRAD (guess the radiation of Ps).

@@ -53,6 +53,7 @@ class OrcParams(ctypes.Structure):
         ("newton_max", ctypes.c_int),
         ("newton_tol", ctypes.c_double),
         ("integrator", ctypes.c_int),
+        ("implicit_eq", ctypes.c_int),
     ]
 
 
@@ -63,6 +64,7 @@ class OrcInfo(ctypes.Structure):
         ("iters_urad", ctypes.c_int),
         ("method", ctypes.c_int),
         ("neg_erad", ctypes.c_int),
+        ("entropy", ctypes.c_int),
     ]
 
 
@@ -118,7 +120,7 @@ def lib():
         L.orc_rad_invert.argtypes = [pp, dp, dp, ctypes.c_int, dp]
         L.orc_gas_invert.restype = ctypes.c_int
         L.orc_gas_invert.argtypes = [pp, dp, dp, dp, ctypes.c_double, dp]
-        L.orc_implicit_zone.argtypes = [pp, dp, dp, dp, ctypes.c_double, dp, ctypes.POINTER(OrcInfo)]
+        L.orc_implicit_zone.argtypes = [pp, dp, dp, dp, dp, ctypes.c_double, dp, ctypes.POINTER(OrcInfo)]
         L.orc_radiation_subdominant.argtypes = [pp, dp, dp, dp]
         L.orc_method_zone.argtypes = [pp, dp, dp, dp, ctypes.c_double, ctypes.c_int, dp, dp,
                                       ctypes.POINTER(ctypes.c_int)]
@@ -208,10 +210,10 @@ class Oracle:
         return it
 
     def counts(self):
-        c = np.zeros(5, dtype=np.int64)
+        c = np.zeros(6, dtype=np.int64)
         lib().orc_get_counts(self._h, c.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)))
         return {"pmhd": int(c[0]), "urad": int(c[1]), "backup": int(c[2]),
-                "iters": int(c[3]), "solves": int(c[4])}
+                "iters": int(c[3]), "solves": int(c[4]), "entropy": int(c[5])}
 
     def fluxes(self, d):
         m = list(self.n)
@@ -300,11 +302,17 @@ def gas_invert(p, x, U, Pg, tol=1e-14):
     return out, rc
 
 
-def implicit_zone(p, x, Ustar, Ps, h):
+def implicit_zone(p, x, Ustar, Ps, h, Sstar=None):
+    """Implicit solve of one zone; Sstar = sqrt(-g) S u^t of the explicit
+    update enables the entropy back-up (None: energy methods only)."""
     x, Ustar, Ps = _vec(x), _vec(Ustar), _vec(Ps)
     out = np.empty(NP)
     info = OrcInfo()
-    lib().orc_implicit_zone(ctypes.byref(p), _dp(x), _dp(Ustar), _dp(Ps), float(h), _dp(out),
+    sp = None
+    if Sstar is not None:
+        sv = ctypes.c_double(float(Sstar))
+        sp = ctypes.pointer(sv)
+    lib().orc_implicit_zone(ctypes.byref(p), _dp(x), _dp(Ustar), sp, _dp(Ps), float(h), _dp(out),
                             ctypes.byref(info))
     return out, info
 

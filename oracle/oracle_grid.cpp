@@ -46,7 +46,9 @@ struct Ctx {
   std::vector<double> gam;     // cell-centre connection [ntot][64] (KS only)
   std::vector<unsigned char> status;  // active zones
   std::vector<int> iters;             // active zones
-  long long counts[5];
+  std::vector<double> FS[3];  // face fluxes of the entropy S u^j [ntot] (RK3)
+  std::vector<double> Sn;     // sqrt(-g) S u^t of the step's initial state [ntot]
+  long long counts[6];
   std::vector<double> M[4];  // IMEX: implicit source of stage j, gas rows [4][ntot]
 };
 
@@ -210,7 +212,7 @@ void flattener(const FlatIn* c, int m, double* fg, double* fr) {
 // else nullptr): the stencil cells' absorption field; a reconstructed face
 // state takes the value of the cell it was reconstructed from.
 void face_flux(const orc_params& p, int d, const double P8[8][NP], const Geom* geo[8], const Geom& Gf,
-               const double* K8, double* stored[2][2], double F[NP], double* speed) {
+               const double* K8, double* stored[2][2], double F[NP], double* speed, double* FS = nullptr) {
   auto at = [&](int m) {
     orc_params q = p;
     if (K8) q.kappa_abs0 = K8[m];
@@ -293,6 +295,20 @@ void face_flux(const orc_params& p, int d, const double P8[8][NP], const Geom* g
     F[q] = fl;
   }
   *speed = std::max(std::max(cmaxg, cming), std::max(cmaxr, cminr));
+  if (FS) {
+    // entropy flux sqrt(-g) S u^d = s_gas F_rho and conserved s_gas U_rho of
+    // each state (Sec. 4 list of U_q, F_q), with the gas signal speeds
+    const double sL = entropy_per_baryon(at(3), PL[RHO], PL[UU]);
+    const double sR = entropy_per_baryon(at(4), PR[RHO], PR[UU]);
+    const double fL = sL * FL[RHO], fR = sR * FR[RHO], uL = sL * UL[RHO], uR = sR * UR[RHO];
+    if (p.flux == 0) {
+      *FS = 0.5 * (fL + fR - std::max(cmaxg, cming) * (uR - uL));
+    } else if (cmaxg + cming > 0.0) {
+      *FS = (cming * fR + cmaxg * fL - cming * cmaxg * (uR - uL)) / (cming + cmaxg);
+    } else {
+      *FS = 0.5 * (fL + fR);
+    }
+  }
 }
 
 // Face fluxes along direction d (0-based) for every face that the update or
@@ -340,10 +356,12 @@ void compute_fluxes(Ctx& c, int d, bool use_stored) {
     geom_at(p, x[0], x[1], x[2], G);
     double* st[2][2] = {{&c.flat[d][t - str], &c.flat[d][c.ntot + t - str]},
                         {&c.flat[d][t], &c.flat[d][c.ntot + t]}};
-    double Fq[NP], sp;
-    face_flux(p, d, P8, geo, G, c.K.empty() ? nullptr : K8, use_stored ? st : nullptr, Fq, &sp);
+    double Fq[NP], sp, fs = 0.0;
+    face_flux(p, d, P8, geo, G, c.K.empty() ? nullptr : K8, use_stored ? st : nullptr, Fq, &sp,
+              p.integrator == 0 ? &fs : nullptr);
     for (int q = 0; q < NP; ++q) F[(long)q * c.ntot + t] = Fq[q];
     c.spd[d][t] = sp;
+    c.FS[d][t] = fs;
   };
   // a face writes the flattener of the two cells beside it: the parallel
   // loop runs over an index other than d, so neighbours along d stay on one
@@ -587,9 +605,9 @@ void substep(Ctx& c, int s, double dt) {
   std::vector<double> Pnew((size_t)NP * c.ntot);
   std::memcpy(Pnew.data(), c.P.data(), sizeof(double) * NP * c.ntot);
   std::vector<unsigned char> failed((size_t)c.n[0] * c.n[1] * c.n[2], 0);
-  long long n_pmhd = 0, n_urad = 0, n_back = 0, n_iter = 0, n_solve = 0;
+  long long n_pmhd = 0, n_urad = 0, n_back = 0, n_iter = 0, n_solve = 0, n_ent = 0;
 #pragma omp parallel for num_threads(orc_threads()) schedule(dynamic, 1) \
-    reduction(+ : n_pmhd, n_urad, n_back, n_iter, n_solve)
+    reduction(+ : n_pmhd, n_urad, n_back, n_iter, n_solve, n_ent)
   for (int k = 0; k < c.n[2]; ++k)
     for (int j = 0; j < c.n[1]; ++j)
       for (int i = 0; i < c.n[0]; ++i) {
@@ -631,10 +649,26 @@ void substep(Ctx& c, int s, double dt) {
             Ust[q] = v;
           }
         }
+        // RK3: the explicit entropy S* = a_s S^n + b_s (S(P_s) + dt X_S), the
+        // conserved entropy sqrt(-g) S u^t = U_rho s_gas (Sec. 2, Eq. S), for the
+        // entropy equation of the implicit solve (Sec. 4.7, 4.11)
+        double Sst = 0.0;
+        if (!imex) {
+          const double Su = Us[RHO] * entropy_per_baryon(c.p, Ps[RHO], Ps[UU]);
+          if (s == 0) c.Sn[t] = Su;
+          double divS = 0.0;
+          for (int d = 0; d < 3; ++d) {
+            if (c.n[d] == 1) continue;
+            long st = d == 0 ? 1 : (d == 1 ? c.N[0] : (long)c.N[0] * c.N[1]);
+            divS += (c.FS[d][t + st] - c.FS[d][t]) / c.p.dx[d];
+          }
+          Sst = A[s] * c.Sn[t] + Bc[s] * (Su - dt * divS);
+        }
         double Pn[NP];
         orc_implicit_info info;
         const double h = imex ? ps.g * dt : Bc[s] * dt;
-        implicit_zone(cell_params(c, t), G, Ust, Ps, h, Pn, &info, radiation_subdominant(G, Ust, Ps));
+        implicit_zone(cell_params(c, t), G, Ust, imex ? nullptr : &Sst, Ps, h, Pn, &info,
+                      radiation_subdominant(G, Ust, Ps));
         if (imex && ps.g > 0.0) {
           // M^s = (U(P) - U*) / (g dt) on the gas rows, P the implicit stage's
           // solution (the source as the change the implicit stage made)
@@ -647,6 +681,7 @@ void substep(Ctx& c, int s, double dt) {
         c.iters[a] += info.iters_pmhd + info.iters_urad;
         n_iter += info.iters_pmhd + info.iters_urad;
         n_solve += 1;
+        n_ent += info.entropy;
         if (info.method == ORC_OK_PMHD) n_pmhd++;
         else if (info.method == ORC_OK_URAD) n_urad++;
         else n_back++;
@@ -659,6 +694,7 @@ void substep(Ctx& c, int s, double dt) {
   c.counts[2] += n_back;
   c.counts[3] += n_iter;
   c.counts[4] += n_solve;
+  c.counts[5] += n_ent;
   // Back-up (Sec. 4.11): replace failed zones by the average of their good
   // active face neighbours (all active neighbours if none is good); B keeps
   // its constrained-transport value.  Every solution was floored above, and
@@ -727,9 +763,11 @@ void* orc_create(const orc_params* p) {
   c->P.assign((size_t)NP * c->ntot, 0.0);
   if (p->opacity == 2) c->K.assign((size_t)c->ntot, 0.0);
   c->Un.assign((size_t)NP * c->ntot, 0.0);
+  c->Sn.assign((size_t)c->ntot, 0.0);
   for (int d = 0; d < 3; ++d) {
     c->F[d].assign((size_t)NP * c->ntot, 0.0);
     c->spd[d].assign((size_t)c->ntot, 0.0);
+    c->FS[d].assign((size_t)c->ntot, 0.0);
     c->flat[d].assign((size_t)2 * c->ntot, 0.0);
   }
   if (c->p.integrator < 0 || c->p.integrator > 3) c->p.integrator = 0;
@@ -751,7 +789,7 @@ void* orc_create(const orc_params* p) {
   long na = (long)c->n[0] * c->n[1] * c->n[2];
   c->status.assign(na, 0);
   c->iters.assign(na, 0);
-  for (int i = 0; i < 5; ++i) c->counts[i] = 0;
+  for (int i = 0; i < 6; ++i) c->counts[i] = 0;
   return c;
 }
 
@@ -804,7 +842,7 @@ double orc_step(void* ctx, double dt) {
   for (int d = 0; d < 3; ++d) std::fill(c.flat[d].begin(), c.flat[d].end(), 0.0);
   std::fill(c.iters.begin(), c.iters.end(), 0);
   std::fill(c.status.begin(), c.status.end(), 0);
-  for (int i = 0; i < 5; ++i) c.counts[i] = 0;
+  for (int i = 0; i < 6; ++i) c.counts[i] = 0;
   for (int s = 0; s < n_passes(c.p.integrator); ++s) substep(c, s, dt);
   return dt;
 }
@@ -821,7 +859,7 @@ void orc_get_iters(void* ctx, int* it) {
 
 void orc_get_counts(void* ctx, long long* out) {
   Ctx& c = *static_cast<Ctx*>(ctx);
-  for (int i = 0; i < 5; ++i) out[i] = c.counts[i];
+  for (int i = 0; i < 6; ++i) out[i] = c.counts[i];
 }
 
 void orc_compute_fluxes(void* ctx, int dir, double* Fout) {
@@ -917,11 +955,11 @@ int orc_radiation_subdominant(const orc_params* p, const double* x, const double
   return radiation_subdominant(G, Ustar, Ps) ? 1 : 0;
 }
 
-void orc_implicit_zone(const orc_params* p, const double* x, const double* Ustar, const double* Ps,
-                       double h, double* Pout, orc_implicit_info* info) {
+void orc_implicit_zone(const orc_params* p, const double* x, const double* Ustar, const double* Sstar,
+                       const double* Ps, double h, double* Pout, orc_implicit_info* info) {
   Geom G;
   geom_at(*p, x[1], x[2], x[3], G);
-  implicit_zone(*p, G, Ustar, Ps, h, Pout, info, radiation_subdominant(G, Ustar, Ps));
+  implicit_zone(*p, G, Ustar, Sstar, Ps, h, Pout, info, radiation_subdominant(G, Ustar, Ps));
 }
 
 void orc_method_zone(const orc_params* p, const double* x, const double* Ustar, const double* Ps, double h,

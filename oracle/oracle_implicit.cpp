@@ -25,6 +25,8 @@ struct Sys {
   double Rstar[4];  // explicit R^t_nu
   double B[3];      // lab field (fixed)
   double h;         // b_s dt
+  bool entropy;     // solve the entropy equation in place of the gas energy row
+  double Sstar;     // explicit S u^t (entropy density times u^t)
 };
 
 struct Res {
@@ -137,6 +139,31 @@ void pmhd_res(const Sys& s, const double x[4], Res& r) {
     r.Er[k] = Rc[k] - s.Rstar[k] + s.h * Gc[k];
   }
   normalise(s, Tc, Rc, Gc, true, r);
+  if (s.entropy) {
+    // Eq. source6 in place of the gas energy row: S u^t(x) - S* = h G_S with
+    // S u^t = rho0 u^t s_gas, s_gas = log(p^n / rho0^(n+1)), n = 1/(Gamma-1)
+    // (Sec. 2, Eq. S), and G_S = -G_mu u^mu / T, T = p/rho0 (Eq. GS).  The
+    // radiation keeps total energy-momentum conservation (Sec. 4.7), so its
+    // energy row only mirrors the gas energy equation that is not solved:
+    // both energy rows leave e_T and e_I.
+    const double pg = (p.gam - 1.0) * P[UU];
+    const double sg = entropy_per_baryon(p, P[RHO], P[UU]);
+    double Gu = 0.0;
+    for (int m = 0; m < 4; ++m) Gu += Gc[m] * u.ucon[m];
+    const double GS = -Gu / (pg / P[RHO]);
+    const double Su = s.Dlab * sg;
+    r.Eg[0] = Su - s.Sstar - s.h * GS;
+    const double d0 = std::fabs(Su) + std::fabs(s.Sstar) + s.h * std::fabs(GS);
+    r.eg[0] = d0 > 0.0 ? std::fabs(r.Eg[0]) / d0 : 0.0;
+    r.er[0] = 0.0;
+    double sT = r.eg[0], sI = r.eg[0];
+    for (int k = 1; k < 4; ++k) {
+      sT += std::max(r.eg[k], r.er[k]);
+      sI += r.eg[k];
+    }
+    r.eT = 0.25 * sT;
+    r.eI = 0.25 * sI;
+  }
   std::memcpy(r.P, P, sizeof(P));
   r.ok = std::isfinite(r.eT);
 }
@@ -510,6 +537,8 @@ int newton_prad(const Sys& s, const double x0[4], const double* Pg0, Res& best) 
 void build_sys(const orc_params& p, const Geom& G, const double* Ustar, double h, Sys& s) {
   s.p = &p;
   s.G = &G;
+  s.entropy = false;
+  s.Sstar = 0.0;
   double gd = G.gdet;
   s.Dlab = Ustar[0] / gd;
   for (int k = 0; k < 4; ++k) s.Tstar[k] = Ustar[1 + k] / gd;
@@ -573,18 +602,49 @@ bool radiation_subdominant(const Geom& G, const double* Ustar, const double* Ps)
   return Ehat < tiny * Ps[UU];
 }
 
+// Final primitives of a solve: the best iterate (B from U*), its radiation
+// re-inverted with the BASIC limiter if the TYPE2 branch saw a negative
+// energy; e_T > 1e-7 (or no finite iterate) is no solution: the back-up.
+void finish_solution(const orc_params& p, const Geom& G, const Sys& s, const Res& best, const double* Ps,
+                     double* Pout, orc_implicit_info* info, int method) {
+  if (!best.ok) {
+    for (int q = 0; q < NP; ++q) Pout[q] = Ps[q];
+    for (int i = 0; i < 3; ++i) Pout[B1 + i] = s.B[i];
+    info->e_T = HUGE_VAL;
+    info->method = ORC_BACKUP;
+    info->neg_erad = 0;
+    return;
+  }
+  for (int q = 0; q < NP; ++q) Pout[q] = best.P[q];
+  if (best.negE) {
+    double Pr[4];
+    rad_invert(p, G, best.Rt_pre, LIM_BASIC, Pr);
+    Pout[ER] = Pr[0];
+    Pout[UR1] = Pr[1];
+    Pout[UR2] = Pr[2];
+    Pout[UR3] = Pr[3];
+  }
+  info->e_T = best.eT;
+  info->neg_erad = best.negE;
+  info->method = (best.eT > 1e-7) ? ORC_BACKUP : method;
+}
+
 // Method sequence (Sec. 4.10-4.11): PMHD first, guessed from P_s or, where the
 // cell is optically thin (tau < 2/3), from a gas inversion of U*; URAD if PMHD
 // leaves e_T > 1e-9; PRAD if both do; the lowest-error solution is kept.  With
 // the radiation extremely sub-dominant URAD goes first, from P_s, then PRAD,
 // and PMHD (which would lose that radiation in the gas's round-off) is not
-// tried.  e_T > 1e-7 marks the zone for the neighbour-average back-up.  A
-// solution that hit the TYPE2 negative-energy branch has its radiation
-// re-inverted with the BASIC limiter.
-void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, const double* Ps,
-                   double h, double* Pout, orc_implicit_info* info, bool subdominant) {
+// tried.  When no energy-based method reaches e_T <= 1e-7 and the explicit
+// entropy S* is given (RK3), the entropy-based PMHD follows (Sec. 4.11); its
+// solution counts as a retry method's.  e_T > 1e-7 after that marks the zone
+// for the neighbour-average back-up.  A solution that hit the TYPE2
+// negative-energy branch has its radiation re-inverted with the BASIC
+// limiter.  With implicit_eq = 1 every zone solves the entropy equation.
+void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, const double* Sstar,
+                   const double* Ps, double h, double* Pout, orc_implicit_info* info, bool subdominant) {
   Sys s;
   build_sys(p, G, Ustar, h, s);
+  info->entropy = 0;
   double x0[4] = {Ps[UU], Ps[U1], Ps[U2], Ps[U3]};
   double kabs, ksca;
   opacity(p, Ps[RHO], Ps[UU], &kabs, &ksca);
@@ -603,6 +663,17 @@ void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, cons
   }
   Res best;
   int method;
+  if (p.implicit_eq == 1 && Sstar) {
+    // entropy equation for every zone (Eq. source6), PMHD iterates
+    Sys se = s;
+    se.entropy = true;
+    se.Sstar = *Sstar / G.gdet;
+    info->iters_pmhd = newton_pmhd(se, x0, best);
+    info->iters_urad = 0;
+    finish_solution(p, G, se, best, Ps, Pout, info, ORC_OK_PMHD);
+    info->entropy = best.ok && best.eT <= 1e-7;
+    return;
+  }
   if (!subdominant) {
     Res bp;
     info->iters_pmhd = newton_pmhd(s, x0, bp);
@@ -653,26 +724,22 @@ void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, cons
       method = ORC_OK_URAD;
     }
   }
-  if (!best.ok) {
-    for (int q = 0; q < NP; ++q) Pout[q] = Ps[q];
-    for (int i = 0; i < 3; ++i) Pout[B1 + i] = s.B[i];
-    info->e_T = HUGE_VAL;
-    info->method = ORC_BACKUP;
-    info->neg_erad = 0;
-    return;
+  if (Sstar && !(best.ok && best.eT <= 1e-7)) {
+    // no energy-based solution: the entropy equation replaces the gas energy
+    // equation (Sec. 4.7, Eq. source6; Sec. 4.11), PMHD iterates, the same
+    // guess as the energy PMHD
+    Sys se = s;
+    se.entropy = true;
+    se.Sstar = *Sstar / G.gdet;
+    Res bs;
+    info->iters_urad += newton_pmhd(se, x0, bs);
+    if (bs.ok && bs.eT <= 1e-7) {
+      finish_solution(p, G, se, bs, Ps, Pout, info, ORC_OK_URAD);
+      info->entropy = 1;
+      return;
+    }
   }
-  for (int q = 0; q < NP; ++q) Pout[q] = best.P[q];
-  if (best.negE) {
-    double Pr[4];
-    rad_invert(p, G, best.Rt_pre, LIM_BASIC, Pr);
-    Pout[ER] = Pr[0];
-    Pout[UR1] = Pr[1];
-    Pout[UR2] = Pr[2];
-    Pout[UR3] = Pr[3];
-  }
-  info->e_T = best.eT;
-  info->neg_erad = best.negE;
-  info->method = (best.eT > 1e-7) ? ORC_BACKUP : method;
+  finish_solution(p, G, s, best, Ps, Pout, info, method);
 }
 
 }  // namespace orc

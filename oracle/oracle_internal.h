@@ -38,12 +38,14 @@ void char_speeds(const Geom& G, const double ucon[4], double c2, int d, double* 
 void face_state(const orc_params& p, const Geom& G, int d, const double* P, double* U, double* F,
                 double sp[4]);
 int rad_invert(const orc_params& p, const Geom& G, const double Rt[4], int limiter, double out[4]);
+double entropy_per_baryon(const orc_params& p, double rho, double ug);
 int gas_invert(const orc_params& p, const Geom& G, const double* U, const double* Pg, double tol,
                double* out);
 
 // Implicit four-force solve of one zone (Sec. 4.7-4.11).
 bool radiation_subdominant(const Geom& G, const double* Ustar, const double* Ps);
-void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, const double* Ps,
+void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, const double* Sstar,
+                   const double* Ps,
                    double h, double* Pout, orc_implicit_info* info, bool subdominant);
 void method_zone(const orc_params& p, const Geom& G, const double* Ustar, const double* Ps, double h,
                  int method, double* Pout, double* eT, int* iters);

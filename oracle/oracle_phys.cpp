@@ -441,6 +441,13 @@ int rad_invert(const orc_params& p, const Geom& G, const double Rt[4], int limit
   return negE;
 }
 
+// Specific entropy of the gas (Sec. 2, Eq. S): s = log(p^n / rho0^(n+1))
+// with n = 1/(Gamma - 1), p = (Gamma - 1) u_g; the entropy density is rho0 s.
+double entropy_per_baryon(const orc_params& p, double rho, double ug) {
+  const double n = 1.0 / (p.gam - 1.0);
+  return n * std::log((p.gam - 1.0) * ug) - (n + 1.0) * std::log(rho);
+}
+
 // ---------------------------------------------------------------------------
 // Gas 1D_W inversion (Sec. 4.5): Newton on the energy equation Eq. EMHD in the
 // unknown W' = W - D, with v~^2 from Eq. vsqeq and v~^i from Eq. tveq.

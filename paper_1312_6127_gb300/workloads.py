@@ -45,7 +45,7 @@ def base_params():
         gamma_rad_max=100.0, gamma_gas_max=50.0,
         floor_rho0=1e-10, floor_rho_pow=0.0, floor_u0=1e-12, floor_u_pow=0.0,
         bsq_rho_max=200.0, bsq_u_max=1e5, u_rho_max=1e10,
-        newton_max=20, newton_tol=1e-12, integrator=0,
+        newton_max=20, newton_tol=1e-12, integrator=0, implicit_eq=0,
     )
 
 
