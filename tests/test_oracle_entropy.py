@@ -1,0 +1,149 @@
+"""Pins of the oracle's entropy equation (Sec. 2, Eq. S: the conserved
+entropy S u^t with S = rho0 log(p^n / rho0^(n+1)), n = 1/(Gamma - 1); Eq. GS
+for its radiation source) and of its use in the implicit solve (Sec. 4.7,
+Eq. source6; Sec. 4.11: the back-up when the energy equations have no
+solution).  The paper states that this form of the entropy is conserved to
+machine round-off; the pins check that, that the entropy and energy forms
+agree on smooth adiabatic flow, and that the back-up finds the solution the
+energy methods cannot."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1312_6127_gb300 import workloads as W
+
+RHO, UU = 0, 1
+
+
+def total_entropy(cfg, P):
+    """sum over zones of sqrt(-g) S u^t = U_rho s (and of its absolute value)."""
+    p = O.make_params(cfg)
+    gam = cfg["gam"]
+    n = 1.0 / (gam - 1.0)
+    nz = cfg["n"]
+    tot = ab = 0.0
+    for k in range(nz[2]):
+        for j in range(nz[1]):
+            for i in range(nz[0]):
+                x = [0.0] + [cfg["x0"][e] + ((i, j, k)[e] + 0.5) * cfg["dx"][e] for e in range(3)]
+                U, _ = O.prim_to_cons(p, x, P[:, k, j, i])
+                s = n * math.log((gam - 1.0) * P[UU, k, j, i]) - (n + 1.0) * math.log(P[RHO, k, j, i])
+                tot += U[0] * s
+                ab += abs(U[0] * s)
+    return tot, ab
+
+
+def test_entropy_equation_conserves_total_entropy():
+    """A random periodic box (field, velocities up to 0.3 c, no gas-radiation
+    coupling) stepped with the entropy equation in every zone keeps its total
+    entropy to round-off over five steps; with the energy equations (the
+    default) the same box, whose zones are not smooth, raises it by 15 %."""
+    cfg, P = W.minkowski_box((12, 10, 8), seed=3)
+    cfg.update(kappa_abs0=0.0, kappa_es0=0.0)
+    out = {}
+    for eq in (0, 1):
+        c = dict(cfg, implicit_eq=eq)
+        o = O.Oracle(c)
+        o.set_prims(P)
+        S0, a0 = total_entropy(c, P)
+        for _ in range(5):
+            o.step(0.0)
+        S1, _ = total_entropy(c, o.get_prims())
+        out[eq] = ((S1 - S0) / a0, o.counts())
+    print("relative change of the total entropy: energy %.2e, entropy %.2e" % (out[0][0], out[1][0]))
+    assert abs(out[1][0]) < 1e-10
+    assert out[1][1]["entropy"] == out[1][1]["solves"]
+    assert out[0][0] > 1e-2
+
+
+def test_entropy_and_energy_forms_agree_on_smooth_flow():
+    """A small-amplitude sound wave (periodic 1D, adiabatic, no coupling):
+    after 40 steps the entropy-form and energy-form solutions differ by far
+    less than the wave's amplitude (the two equations agree on smooth flow
+    to truncation error)."""
+    n1 = 64
+    cfg = W.base_params()
+    cfg.update(n=[n1, 1, 1], dx=[1.0 / n1, 1, 1], kappa_abs0=0.0, kappa_es0=0.0, a_rad=1.0)
+    x = (np.arange(n1) + 0.5) / n1
+    gam = cfg["gam"]
+    rho0, u0, amp = 1.0, 0.1, 1e-3
+    p0 = (gam - 1) * u0
+    cs = math.sqrt(gam * p0 / (rho0 + u0 + p0))
+    P = np.zeros((12, 1, 1, n1))
+    d = amp * np.sin(2 * np.pi * x)
+    P[RHO] = rho0 * (1 + d)
+    P[UU] = u0 * (1 + gam * d)
+    P[2] = cs * d
+    P[8] = 1e-6
+    res = {}
+    for eq in (0, 1):
+        o = O.Oracle(dict(cfg, implicit_eq=eq))
+        o.set_prims(P)
+        for _ in range(40):
+            o.step(0.0)
+        res[eq] = o.get_prims()
+    diff = np.abs(res[1][:2] - res[0][:2]).max() / u0
+    print("entropy vs energy form after 40 steps: %.2e (wave amplitude %.0e)" % (diff, amp))
+    assert diff < 1e-2 * amp
+
+
+def deficit_zone():
+    """One zone whose explicit update took more energy from the gas than it
+    has (T^t_t + rho0 u^t raised by ten times u_g) while the radiation holds
+    much more: with a weak coupling (h = 1e-10) no energy-based method can
+    solve it, and the entropy equation, which moves the deficit to the
+    radiation through total conservation, can."""
+    cfg, x, P = W.random_states(1, seed=17, metric=0, gamma_max=2.0, gamma_rad_max=1.5)
+    cfg.update(kappa_abs0=1.0, kappa_es0=0.4)
+    p = O.make_params(cfg)
+    Pz = P[0].copy()
+    Pz[UU] = 1e-3 * Pz[RHO]
+    Pz[8] = 100.0 * Pz[UU]
+    U, _ = O.prim_to_cons(p, x[0], Pz)
+    gam = cfg["gam"]
+    n = 1.0 / (gam - 1.0)
+    Sstar = U[0] * (n * math.log((gam - 1) * Pz[UU]) - (n + 1) * math.log(Pz[RHO]))
+    Ust = U.copy()
+    Ust[1] += 10.0 * Pz[UU]
+    return cfg, p, x[0], Pz, Ust, Sstar
+
+
+def test_entropy_backup_solves_a_zone_the_energy_methods_cannot():
+    cfg, p, x, Pz, Ust, Sstar = deficit_zone()
+    h = 1e-10
+    _, info_e = O.implicit_zone(p, x, Ust, Pz, h)
+    Po, info = O.implicit_zone(p, x, Ust, Pz, h, Sstar=Sstar)
+    print("energy methods: outcome %d (e_T %.2e); with the entropy back-up: outcome %d, entropy %d, e_T %.2e"
+          % (info_e.method, info_e.e_T, info.method, info.entropy, info.e_T))
+    assert info_e.method == 2
+    assert info.method == 1 and info.entropy == 1 and info.e_T < 1e-9
+    # the solution keeps the zone's entropy (weak coupling) and its momentum,
+    # and the radiation took the energy deficit
+    gam = cfg["gam"]
+    n = 1.0 / (gam - 1.0)
+    U, _ = O.prim_to_cons(p, x, Po)
+    s = n * math.log((gam - 1) * Po[UU]) - (n + 1) * math.log(Po[RHO])
+    assert U[0] * s == pytest.approx(Sstar, rel=1e-9)
+    assert Po[UU] == pytest.approx(Pz[UU], rel=1e-6)
+    for k in range(3):
+        assert U[2 + k] + U[9 + k] == pytest.approx(Ust[2 + k] + Ust[9 + k], rel=1e-9, abs=1e-12)
+    assert U[1] + U[8] == pytest.approx(Ust[1] + Ust[8], rel=1e-9)
+
+
+def test_cold_fast_flow_takes_the_entropy_backup():
+    """A cold (u_g = 1e-7 rho0), fast (up to 0.6 c) random box: the explicit
+    update leaves some zones with less energy than their kinetic energy,
+    which the energy equations cannot invert; the entropy back-up solves
+    most of them (the rest take the neighbour average)."""
+    cfg, P = W.minkowski_box((12, 10, 8), seed=3, vmax=0.6)
+    P[UU] = 1e-7 * P[RHO]
+    cfg.update(kappa_abs0=1.0)
+    o = O.Oracle(cfg)
+    o.set_prims(P)
+    o.step(0.0)
+    c = o.counts()
+    print("cold fast box, first step:", c)
+    assert c["entropy"] > 10 and c["entropy"] > c["backup"]
+    assert np.isfinite(o.get_prims()).all()
