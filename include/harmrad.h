@@ -86,6 +86,21 @@ extern "C" {
  * their final combination has no implicit term, and its conserved state is
  * inverted by the same Newton solve with a zero source step.  A stage whose
  * explicit bracket holds no flux term runs no reconstruction or flux kernel. */
+/* Gas equation of the implicit solve (Sec. 4.7, Eqs. source3-source6).
+ * ENERGY: the energy-momentum equations, PMHD then URAD then PRAD; with RK3 a
+ * zone that none of them solves (e_T > 1e-7) tries the entropy equation
+ * (Eq. source6: [S u^t] - [S u^t]* = dt G_S, S = rho0 log(p^n/rho0^(n+1)),
+ * Sec. 2) in place of the gas energy equation before the neighbour average
+ * (Sec. 4.11); the radiation keeps total energy-momentum conservation.
+ * ENTROPY: the entropy equation in every zone (PMHD iterates; RK3 only), which
+ * conserves the total entropy to round-off where the gas and radiation do not
+ * exchange energy.  The entropy S u^t is carried as a 13th conserved quantity
+ * with its own face fluxes (RK3 contexts).  The point-wise entries
+ * (harmrad_zone_implicit, harmrad_zone_implicit_static) solve the energy
+ * equations only. */
+#define HARMRAD_EQ_ENERGY 0
+#define HARMRAD_EQ_ENTROPY 1
+
 #define HARMRAD_INT_RK3 0
 #define HARMRAD_INT_IMEX2 1
 #define HARMRAD_INT_IMEX2B 2
@@ -116,6 +131,7 @@ typedef struct harmrad_params {
   double newton_tol;   /* PMHD tolerance on e_T (Sec. 4.10) */
   int precision;       /* HARMRAD_PREC_* */
   int integrator;      /* HARMRAD_INT_* */
+  int implicit_eq;     /* HARMRAD_EQ_*: which gas equation the implicit solve uses */
 } harmrad_params;
 
 /* Per-zone outcome codes written by harmrad_get_status (worst over the
@@ -124,7 +140,8 @@ typedef struct harmrad_params {
  * extremely sub-dominant (below 10 eps_m of the gas in conserved or
  * fluid-frame energy) starts with URAD and skips PMHD. */
 #define HARMRAD_ZONE_PMHD 0    /* PMHD Newton accepted */
-#define HARMRAD_ZONE_URAD 1    /* a retry method (URAD or PRAD) gave the accepted solution */
+#define HARMRAD_ZONE_URAD 1    /* a retry method (URAD, PRAD or the entropy equation) gave the
+                                  accepted solution */
 #define HARMRAD_ZONE_BACKUP 2  /* no method reached e_T <= 1e-7: neighbour average */
 
 typedef struct harmrad_stats {
@@ -134,6 +151,9 @@ typedef struct harmrad_stats {
   long long newton_iters;      /* Newton steps summed over all solves */
   int kernel_launches;         /* kernels one harmrad_step launches */
   int graph;                   /* 1 if the step is replayed as a CUDA graph */
+  long long entropy_ok;        /* solves whose accepted solution came from the entropy
+                                  equation (counted in urad_ok as well, or in pmhd_ok with
+                                  implicit_eq = 1) */
 } harmrad_stats;
 
 typedef struct harmrad_ctx harmrad_ctx;

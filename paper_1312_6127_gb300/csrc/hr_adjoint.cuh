@@ -28,7 +28,7 @@ struct AdjBufs {
   double* Pst;          // [4][12][ntot] sub-step inputs P_0, P_1, P_2 and the result P^{n+1}
   double* chi;          // [3][3][2][ntot] flattener after sub-step s, per direction (PPM)
   double* Ust;          // [3][12][nact] U* of every zone and sub-step
-  unsigned char* meth;  // [3][nact] outcome per sub-step: 0 PMHD, 1 URAD, 2 back-up
+  unsigned char* meth;  // [3][nact] outcome per sub-step: 0 PMHD, 1 URAD, 2 back-up, 3 entropy
   double* Psol;         // [3][12][nact] solution of every zone before the floors
   double* gP;           // [12][ntot] cotangent of the current sub-step's input (ghosts included)
   double* gN;           // [12][nact] cotangent of the current sub-step's output
@@ -135,7 +135,10 @@ __global__ void ka_implicit(DevParams p, BoxGeo bx, AdjBufs a, int s, double dt,
     }
     (void)Pnext;
     const double kz = kfield(p, K, t);
-    if (m == 2) {  // back-up: only B = U*[B] / sqrt(-g) is the zone's own
+    if (m == 2 || m == METH_ENTROPY) {
+      // back-up: only B = U*[B] / sqrt(-g) is the zone's own; a zone solved by
+      // the entropy equation is held constant the same way (its error
+      // function differs from the energy one the transposed solve uses)
       for (int c = 0; c < 3; ++c) a.gU[(B1 + c) * bx.nact + z] = gq[B1 + c] * igd;
       continue;
     }

@@ -148,6 +148,11 @@ int fill_physics(const harmrad_params* p, DevParams& d) {
   d.newton_tol = p->newton_tol;
   if (p->precision != 0 && p->precision != 1) return HARMRAD_E_ARG;
   d.precision = p->precision;
+  // the entropy equation needs the RK3 stages (the IMEX sources cover the
+  // energy-momentum rows only)
+  if (p->implicit_eq != 0 && p->implicit_eq != 1) return HARMRAD_E_ARG;
+  if (p->implicit_eq == 1 && p->integrator != 0) return HARMRAD_E_ARG;
+  d.implicit_eq = p->implicit_eq;
   if (p->integrator < 0 || p->integrator > 3) return HARMRAD_E_ARG;
   d.integrator = p->integrator;
   return HARMRAD_OK;
@@ -364,7 +369,7 @@ void free_all(harmrad_ctx* c) {
                   c->aux, c->flat[0], c->flat[1], c->flat[2], c->emf, c->edges, c->slope, c->dt, c->status,
                   c->iters, c->failed, c->qcount, c->czone, c->cbox, c->cdata, c->qzone, c->qbox, c->qdata, c->fzone, c->fbox,
                   c->ftmp, c->stats, c->dtmin, c->stage_buf, c->flag, c->dboxes, c->imex_ust, c->imex_psol,
-                  c->imex_M, c->sig};
+                  c->imex_M, c->sig, c->Sn, c->FS[0], c->FS[1], c->FS[2]};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (c->host_dt) cudaFreeHost(c->host_dt);
@@ -454,9 +459,11 @@ int create(const harmrad_params* p, int count, void* stream, harmrad_ctx** out) 
   rc = rc ? rc : dalloc(&c->K, nk * sizeof(double));
   if (goff > 0) rc = rc ? rc : dalloc(&c->geotab, goff * sizeof(double));
   rc = rc ? rc : dalloc(&c->Un, 12 * na * sizeof(double));
+  if (dp.integrator == 0) rc = rc ? rc : dalloc(&c->Sn, na * sizeof(double));
   for (int d = 0; d < 3; ++d) {
     size_t fn = dp.act[d] ? nt : 0;
     rc = rc ? rc : dalloc(&c->F[d], 12 * fn * rs);
+    if (dp.integrator == 0 && fn) rc = rc ? rc : dalloc(&c->FS[d], fn * rs);
     rc = rc ? rc : dalloc(&c->spd[d], fn * rs);
     rc = rc ? rc : dalloc(&c->flat[d], 2 * fn * rs);
   }
@@ -503,6 +510,7 @@ int create(const harmrad_params* p, int count, void* stream, harmrad_ctx** out) 
       rc = HARMRAD_E_CUDA;
     for (int d = 0; d < 3 && !rc; ++d) {
       size_t fn = dp.act[d] ? nt : 0;
+      if (fn && c->FS[d] && cudaMemsetAsync(c->FS[d], 0, fn * rs, c->stream) != cudaSuccess) rc = HARMRAD_E_CUDA;
       if (fn && (cudaMemsetAsync(c->F[d], 0, 12 * fn * rs, c->stream) != cudaSuccess ||
                  cudaMemsetAsync(c->spd[d], 0, fn * rs, c->stream) != cudaSuccess ||
                  cudaMemsetAsync(c->flat[d], 0, 2 * fn * rs, c->stream) != cudaSuccess))
@@ -689,6 +697,7 @@ int harmrad_get_stats(harmrad_ctx* c, harmrad_stats* s) {
   s->backup = (long long)h[hr::ST_BACKUP];
   s->zone_stages = (long long)h[hr::ST_SOLVES];
   s->newton_iters = (long long)h[hr::ST_ITERS];
+  s->entropy_ok = (long long)h[hr::ST_ENTROPY];
   s->kernel_launches = c->launches_per_step;
   s->graph = c->use_graph ? 1 : 0;
   return s->backup > 0 ? HARMRAD_W_BACKUP_USED : HARMRAD_OK;
@@ -797,7 +806,7 @@ int harmrad_adjoint_enable(harmrad_ctx* c, int on) {
     free_adjoint(c);
     return HARMRAD_OK;
   }
-  if (c->nbox != 1 || c->real_size != 8 || c->dp.integrator != 0) return HARMRAD_E_ARG;
+  if (c->nbox != 1 || c->real_size != 8 || c->dp.integrator != 0 || c->dp.implicit_eq != 0) return HARMRAD_E_ARG;
   for (int f = 0; f < 6; ++f)
     if (c->boxes[0].bc[f] == HARMRAD_BC_FIXED) return HARMRAD_E_ARG;
   if (c->adj) return HARMRAD_OK;

@@ -28,6 +28,8 @@ struct harmrad_ctx {
   double* K;
   double* geotab;  // metric tables of Kerr-Schild grids (null for Minkowski)
   double* Un;
+  double* Sn;   // [nact] conserved entropy sqrt(-g) S u^t at the start of the step (RK3)
+  void* FS[3];  // [ntot] entropy face fluxes of each active direction (RK3; null otherwise)
   void* F[3];
   void* spd[3];
   void* aux;

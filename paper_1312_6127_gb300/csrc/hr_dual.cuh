@@ -73,6 +73,7 @@ struct Dn {
     const double s = ::rsqrt(a.v);
     return chain(a, s, -0.5 * s * s * s);
   }
+  friend __device__ __forceinline__ Dn log(const Dn& a) { return chain(a, ::log(a.v), 1.0 / a.v); }
   friend __device__ __forceinline__ Dn exp(const Dn& a) {
     const double e = ::exp(a.v);
     return chain(a, e, e);

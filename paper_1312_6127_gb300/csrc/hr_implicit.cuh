@@ -40,6 +40,8 @@ struct ImpSysT {
   T kf;     // the zone's absorption opacity when it is a per-zone field
   T ks;     // global opacity scale kappa_scale
   T sgk[3]; // sqrt(gamma^{kk}) of the ZAMO slice
+  bool entropy;  // the entropy equation replaces the gas energy row (Eq. source6)
+  T Sstar;       // explicit S u^t (the conserved entropy over sqrt(-g))
 };
 template <int MET>
 using ImpSys = ImpSysT<MET, double>;
@@ -85,7 +87,7 @@ __device__ __forceinline__ void four_force_rad(const DevParams& p, T rho, T Tg, 
 
 template <int MET, typename T = double>
 __device__ __forceinline__ void normalise(const ImpSysT<MET, T>& s, const T Tc[4], const T Rc[4],
-                                          const T G[4], bool iter_gas, ImpResT<T>& r) {
+                                          const T G[4], bool iter_gas, ImpResT<T>& r, T eS = T(-1.0)) {
   T dg0 = fabs(Tc[0]) + fabs(s.Ts[0]) + s.h * fabs(G[0]);
   T dr0 = fabs(Rc[0]) + fabs(s.Rs[0]) + s.h * fabs(G[0]);
   T dgs = T(0.0), drs = T(0.0);
@@ -108,6 +110,10 @@ __device__ __forceinline__ void normalise(const ImpSysT<MET, T>& s, const T Tc[4
     er[k] = fabs(r.Er[k]) * s.sgk[k - 1] * idrs;
   }
   if (r.negE) eg[0] = er[0] = T(0.0);
+  if (eS >= 0.0) {  // entropy row in place of the gas energy row; the radiation energy row drops
+    eg[0] = eS;
+    er[0] = T(0.0);
+  }
   T sT = T(0.0), sI = T(0.0);
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -153,6 +159,20 @@ __device__ __forceinline__ void pmhd_res(const DevParams& p, const ImpSysT<MET, 
                          urv, Pr[0], G);
 #pragma unroll
   for (int k = 0; k < 4; ++k) r.Eg[k] = Tc[k] - s.Ts[k] - s.h * G[k];
+  T eS = T(-1.0);
+  if (s.entropy) {
+    // Eq. source6: S u^t(x) - S* = h G_S, S u^t = rho0 u^t s_gas, G_S = -G_mu u^mu / T
+    // (Eq. GS), T = p/rho0; the radiation keeps total conservation (Sec. 4.7)
+    const T Tg = (p.gam - 1.0) * x[0] / rho;
+    const T Gu = G[0] * ucon[0] + G[1] * ucon[1] + G[2] * ucon[2] + G[3] * ucon[3];
+    const T GS = -Gu / Tg;
+    const T Su = s.Dlab * entropy_per_baryon<T>(p, rho, x[0]);
+    r.Eg[0] = Su - s.Sstar - s.h * GS;
+    if (norm) {
+      const T d0 = fabs(Su) + fabs(s.Sstar) + s.h * fabs(GS);
+      eS = d0 > 0.0 ? fabs(r.Eg[0]) / d0 : T(0.0);
+    }
+  }
   if (norm) {
     T e43 = (4.0 / 3.0) * Pr[0];
     T Rc[4];
@@ -161,7 +181,7 @@ __device__ __forceinline__ void pmhd_res(const DevParams& p, const ImpSysT<MET, 
     for (int k = 1; k < 4; ++k) Rc[k] = e43 * urc[0] * urv[k];
 #pragma unroll
     for (int k = 0; k < 4; ++k) r.Er[k] = Rc[k] - s.Rs[k] + s.h * G[k];
-    normalise<MET, T>(s, Tc, Rc, G, true, r);
+    normalise<MET, T>(s, Tc, Rc, G, true, r, eS);
     r.ok = isfinite(r.eT);
   } else {
     r.ok = true;
@@ -388,7 +408,7 @@ __device__ int newton_pmhd(const DevParams& p, const ImpSys<MET>& s, const doubl
   *best_eT = HUGE_VAL;
   int steps = 0;
   double eps = 1e-8;
-  int jac32 = 1;
+  int jac32 = s.entropy ? 0 : 1;  // the FP32 tangents differentiate the energy row
   for (int k = 0;; ++k) {
     ImpRes r;
     ImpState ist;
@@ -689,6 +709,8 @@ __device__ __forceinline__ void build_sys(const DevParams& p, const Geo<MET, T>&
   // on the slice, inside the horizon too
 #pragma unroll
   for (int k = 1; k < 4; ++k) s.sgk[k - 1] = sqrt(g.Gdd(k) - g.Gt(k) * g.Gt(k) / g.Gtt());
+  s.entropy = false;
+  s.Sstar = T(0.0);
   (void)p;
 }
 

@@ -22,7 +22,9 @@ struct Bufs {
   double* P;       // [12][ntot] primitives, ghosts included (per grid)
   double* K;       // [ntot] per-zone absorption opacity (opacity field mode), ghosts included
   double* Un;      // [12][nact] conserved state at the start of the step
+  double* Sn;      // [nact] conserved entropy at the start of the step (RK3; null otherwise)
   void* F[3];      // [12][ntot] face fluxes (real type of the precision mode)
+  void* FS[3];     // [ntot] entropy face fluxes (RK3; null otherwise)
   void* spd[3];    // [ntot] per-face max signal speed
   void* aux;       // [10][ntot] per-cell gdet, sqrt(-g) u^d gas/rad, tau weights
   void* flat[3];   // [2][ntot] flattener, max over the sub-steps of the step
@@ -35,7 +37,7 @@ struct Bufs {
   int* qcount;            // [4] retry queue, back-up list, Newton continuation queue lengths
   int* qzone;             // [nact] retry queue: zone index within its grid
   int* qbox;              // [nact] retry queue: grid of the entry
-  double* qdata;          // [nact][18] retry queue payload: U*, PMHD best x, e_T, h
+  double* qdata;          // [nact][19] retry queue payload: U*, PMHD best x, e_T, h, S*
   int* fzone;             // [nact] back-up list: zone index within its grid
   int* fbox;              // [nact] back-up list: grid of the entry
   double* ftmp;           // [nact][12] averaged primitives of back-up zones
@@ -649,7 +651,7 @@ __global__ void __launch_bounds__(256) k_edges(DevParams p, const BoxGeo* __rest
 template <int MET, typename R, int d>
 __device__ __forceinline__ void face_flux(const DevParams& p, const Geo<MET, R>& g, R dxd, R kL, R kR, R ks,
                                           const R PL[NPR], const R PR[NPR], R out[NPR], R* smax,
-                                          unsigned* code = nullptr) {
+                                          unsigned* code = nullptr, R* fs = nullptr) {
   R sL[4], sR[4];
   unsigned cL = 0, cR = 0;
   face_speeds<MET, R>(p, g, d + 1, dxd, kL, ks, PL, sL, code ? &cL : nullptr);
@@ -701,8 +703,9 @@ __device__ __forceinline__ void face_flux(const DevParams& p, const Geo<MET, R>&
   }
 #pragma unroll
   for (int q = 0; q < NPR; ++q) out[q] = R(0);
-  face_accum<MET, R>(p, g, d + 1, PL, fLg, uLg, fLr, uLr, out);
-  face_accum<MET, R>(p, g, d + 1, PR, fRg, uRg, fRr, uRr, out);
+  if (fs) *fs = R(0);
+  face_accum<MET, R>(p, g, d + 1, PL, fLg, uLg, fLr, uLr, out, fs);
+  face_accum<MET, R>(p, g, d + 1, PR, fRg, uRg, fRr, uRr, out, fs);
   out[B1 + d] = R(0);
   *smax = fmax(fmax(cmaxg, cming), fmax(cmaxr, cminr));
 }
@@ -719,7 +722,7 @@ template <int MET, typename R, int d>
 __global__ void __launch_bounds__(128) k_face(DevParams p, const BoxGeo* __restrict__ boxes, int nbox,
                                               const R* __restrict__ E0, const double* __restrict__ K0,
                                               R* __restrict__ F0, R* __restrict__ spd0,
-                                              const double* __restrict__ geo0) {
+                                              const double* __restrict__ geo0, R* __restrict__ FS0) {
   const bool weighted = (MET == KS) && (d != 1);
   for (int bi = 0; bi < nbox; ++bi) {
     const BoxGeo& bx = boxes[bi];
@@ -727,6 +730,7 @@ __global__ void __launch_bounds__(128) k_face(DevParams p, const BoxGeo* __restr
     const double* K = K0 + bx.coff;
     R* F = F0 + 12 * bx.coff;
     R* spd = spd0 + bx.coff;
+    R* FS = FS0 ? FS0 + bx.coff : nullptr;
     int len[3], off[3];
     for (int e = 0; e < 3; ++e) {
       if (e == d) {
@@ -756,6 +760,7 @@ __global__ void __launch_bounds__(128) k_face(DevParams p, const BoxGeo* __restr
 #pragma unroll
         for (int q = 0; q < NPR; ++q) F[q * bx.ntot + t] = R(0);
         spd[t] = R(0);
+        if (FS) FS[t] = R(0);
         continue;
       }
       Geo<MET, R> g;
@@ -787,8 +792,11 @@ __global__ void __launch_bounds__(128) k_face(DevParams p, const BoxGeo* __restr
       const R kL = R(kfield(p, K, t - st)), kR = R(kfield(p, K, t));
       R out[NPR], smax;
       unsigned fcode = 0;
-      face_flux<MET, R, d>(p, g, dxd, kL, kR, R(p.kscale), PL, PR, out, &smax, p.sig ? &fcode : nullptr);
+      R fsv;
+      face_flux<MET, R, d>(p, g, dxd, kL, kR, R(p.kscale), PL, PR, out, &smax, p.sig ? &fcode : nullptr,
+                           FS ? &fsv : nullptr);
       if (p.sig) sig_put(p, bx.coff + t, 40 + d, fcode);
+      if (FS) FS[t] = fsv;
 #pragma unroll
       for (int q = 0; q < NPR; ++q) F[q * bx.ntot + t] = out[q];
       spd[t] = smax;
@@ -1195,7 +1203,7 @@ __device__ __forceinline__ void cons_source(const DevParams& p, const Geo<MET, T
   (void)x2;
 }
 
-constexpr int CSTRIDE = NPR + 22;  // continuation queue record: U*, Newton state
+constexpr int CSTRIDE = NPR + 23;  // continuation queue record: U*, Newton state, S*
 
 __device__ __forceinline__ void newton_state_store(const NewtonState& st, double* d) {
   for (int i = 0; i < 4; ++i) {
@@ -1245,10 +1253,11 @@ template <int MET>
 __device__ __forceinline__ bool pmhd_finish(const DevParams& p, const BoxGeo& bx, int bi, long long z, long long t,
                                             double x1, const Geo<MET, double>& g, const ImpSys<MET>& s,
                                             const double Ust[NPR], double h, const double best_x[4],
-                                            double beT, int steps, double* P, const Bufs& b) {
+                                            double beT, int steps, double* P, const Bufs& b, double Sst,
+                                            double acc_tol = 1e-9) {
   const long long zg = bx.aoff + z;
   b.iters[zg] += steps;
-  const bool accept = beT >= 0.0 && beT < 1e-9;  // beT < 0: sub-dominant radiation, URAD first
+  const bool accept = beT >= 0.0 && beT < acc_tol;  // beT < 0: sub-dominant radiation, URAD first
   if (accept) {
     double Pn[NPR];
     unsigned lcode = 0;
@@ -1271,6 +1280,7 @@ __device__ __forceinline__ bool pmhd_finish(const DevParams& p, const BoxGeo& bx
     for (int q = 0; q < 4; ++q) qd[12 + q] = isfinite(beT) ? best_x[q] : 0.0;
     qd[16] = beT;
     qd[17] = h;
+    qd[18] = Sst;
   }
   return accept;
 }
@@ -1388,6 +1398,29 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
 #pragma unroll
         for (int q = 0; q < NPR; ++q) b.ust_rec[12 * bx.aoff + q * bx.nact + z] = Ust[q];
       }
+      // RK3: the explicit entropy S* = a_s S^n + b_s (S(P_s) + dt X_S), the
+      // conserved entropy sqrt(-g) S u^t = U_rho s_gas (Sec. 2, Eq. S), for the
+      // entropy equation of the implicit solve (Sec. 4.7, 4.11); NaN: none
+      double Sst = NAN;
+      if (!IMEX && b.Sn) {
+        const double Su = Us[RHO] * entropy_per_baryon<double>(p, Ps[RHO], Ps[UU]);
+        double* Sn = b.Sn + bx.aoff;
+        double sn;
+        if (stage == 0) {
+          Sn[z] = Su;
+          sn = Su;
+        } else {
+          sn = Sn[z];
+        }
+        double divS = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          if (!p.act[d]) continue;
+          const R* FSd = (const R*)b.FS[d] + bx.coff;
+          divS += double(FSd[t + bx.str[d]] - FSd[t]) / bx.dx[d];
+        }
+        Sst = A * sn + Bc * (Su - dt * divS);
+      }
       // implicit solve
       const double h = IMEX ? im.g * dt : Bc * dt;
       // extremely sub-dominant radiation: no PMHD attempt; the zone goes to
@@ -1416,10 +1449,20 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
       }
       bool accept = false;
       unsigned done_steps = 0;
-      if constexpr (!CONT) {
+      if (p.implicit_eq == 1) {
+        // the entropy equation in every zone (Eq. source6), PMHD iterates;
+        // no solution (e_T > 1e-7) is the neighbour-average back-up
+        s.entropy = true;
+        s.Sstar = Sst / g.gdet;
+        double bxn[4] = {0.0, 0.0, 0.0, 0.0}, beT = HUGE_VAL;
+        const int steps = newton_pmhd<MET>(p, s, x0, bxn, &beT);
+        accept = pmhd_finish<MET>(p, bx, bi, z, t, x1, g, s, Ust, h, bxn, beT, steps, P, b, Sst, 1e-7 * (1 + 1e-15));
+        done_steps = (unsigned)steps;
+        warp_add(&b.stats[ST_ENTROPY], accept ? 1u : 0u);
+      } else if constexpr (!CONT) {
         double bxn[4] = {0.0, 0.0, 0.0, 0.0}, beT = -1.0;
         const int steps = subdom ? 0 : newton_pmhd<MET>(p, s, x0, bxn, &beT);
-        accept = pmhd_finish<MET>(p, bx, bi, z, t, x1, g, s, Ust, h, bxn, beT, steps, P, b);
+        accept = pmhd_finish<MET>(p, bx, bi, z, t, x1, g, s, Ust, h, bxn, beT, steps, P, b, Sst);
         done_steps = (unsigned)steps;
       } else {
         // the first `split` iterations here; a zone that needs more
@@ -1429,7 +1472,7 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
         newton_pmhd_init(x0, ns);
         if (subdom) ns.best_eT = -1.0;
         if (subdom || newton_pmhd_run<MET>(p, s, ns, split)) {
-          accept = pmhd_finish<MET>(p, bx, bi, z, t, x1, g, s, Ust, h, ns.best_x, ns.best_eT, ns.steps, P, b);
+          accept = pmhd_finish<MET>(p, bx, bi, z, t, x1, g, s, Ust, h, ns.best_x, ns.best_eT, ns.steps, P, b, Sst);
           done_steps = (unsigned)ns.steps;
         } else {
           const int slot = atomicAdd(&b.qcount[2], 1);
@@ -1439,6 +1482,7 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
 #pragma unroll
           for (int q = 0; q < NPR; ++q) cd[q] = Ust[q];
           newton_state_store(ns, cd + NPR);
+          cd[NPR + 22] = Sst;
         }
       }
       warp_add(&b.stats[ST_PMHD], accept ? 1u : 0u);
@@ -1477,8 +1521,8 @@ __global__ void __launch_bounds__(128) k_newton_cont(DevParams p, const BoxGeo* 
     ImpSys<MET> s;
     build_sys<MET>(p, g, Ust, h, kfield(p, b.K + bx.coff, t), s);
     newton_pmhd_run<MET>(p, s, ns, 1 << 30);
-    const bool accept =
-        pmhd_finish<MET>(p, bx, bi, z, t, x1, g, s, Ust, h, ns.best_x, ns.best_eT, ns.steps, b.P + 12 * bx.coff, b);
+    const bool accept = pmhd_finish<MET>(p, bx, bi, z, t, x1, g, s, Ust, h, ns.best_x, ns.best_eT, ns.steps,
+                                         b.P + 12 * bx.coff, b, cd[NPR + 22]);
     if (accept) atomicAdd(&b.stats[ST_PMHD], 1ULL);
     atomicAdd(&b.stats[ST_ITERS], (unsigned long long)ns.steps);
   }
@@ -1568,7 +1612,41 @@ __global__ void __launch_bounds__(128) k_retry(DevParams p, const BoxGeo* __rest
     double Pn[NPR], eT;
     int steps;
     const double tau = zone_tau<MET>(p, g, bx.dx, Ps, kfield(p, K, t));
-    const int method = retry_sequence<MET>(p, g, s, Ps, px, peT, tau, Pn, &eT, &steps);
+    int method;
+    bool by_entropy = false;
+    const double Sst = qd[18];
+    if (p.implicit_eq == 1) {  // the entropy solve already failed: back-up
+      for (int q = 0; q < NPR; ++q) Pn[q] = Ps[q];
+      for (int c = 0; c < 3; ++c) Pn[B1 + c] = s.B[c];
+      eT = HUGE_VAL;
+      steps = 0;
+      method = ST_BACKUP;
+    } else {
+      method = retry_sequence<MET>(p, g, s, Ps, px, peT, tau, Pn, &eT, &steps);
+      if (method == ST_BACKUP && isfinite(Sst)) {
+        // no energy-based solution: the entropy equation in place of the gas
+        // energy equation (Sec. 4.7, Eq. source6; Sec. 4.11), PMHD iterates
+        // from the energy PMHD's guess (P_s, or where tau < 2/3 the gas
+        // inversion of U*)
+        double x0[4] = {Ps[UU], Ps[U1], Ps[U2], Ps[U3]};
+        if (tau < 2.0 / 3.0) {
+          double go[5], T3[3] = {s.Ts[1], s.Ts[2], s.Ts[3]};
+          if (gas_invert<MET>(p, g, s.Dlab, s.Ts[0], T3, s.B, Ps, 1e-9, go) == 0)
+            for (int c = 0; c < 4; ++c) x0[c] = go[1 + c];
+        }
+        ImpSys<MET> se = s;
+        se.entropy = true;
+        se.Sstar = Sst / g.gdet;
+        double bxe[4] = {0.0, 0.0, 0.0, 0.0}, beT = HUGE_VAL;
+        steps += newton_pmhd<MET>(p, se, x0, bxe, &beT);
+        if (beT <= 1e-7) {
+          pmhd_final<MET>(p, se, bxe, Pn);
+          eT = beT;
+          method = ST_URAD;
+          by_entropy = true;
+        }
+      }
+    }
     b.iters[zg] += steps;
     if (b.psol_rec)
       for (int q = 0; q < NPR; ++q) b.psol_rec[12 * bx.aoff + q * bx.nact + z] = Pn[q];
@@ -1578,7 +1656,8 @@ __global__ void __launch_bounds__(128) k_retry(DevParams p, const BoxGeo* __rest
     for (int q = 0; q < NPR; ++q) P[q * bx.ntot + t] = Pn[q];
     unsigned char m = (unsigned char)method;
     if (m > b.status[zg]) b.status[zg] = m;
-    if (b.meth_rec) b.meth_rec[zg] = m;
+    if (b.meth_rec) b.meth_rec[zg] = by_entropy ? METH_ENTROPY : m;
+    if (by_entropy) atomicAdd(&b.stats[ST_ENTROPY], 1ULL);
     if (method == ST_BACKUP) {
       b.failed[zg] = 1;
       int slot = atomicAdd(&b.qcount[1], 1);

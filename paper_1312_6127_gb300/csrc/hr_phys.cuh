@@ -38,6 +38,7 @@ struct DevParams {
   double newton_tol;
   int precision;
   int integrator;  // 0 RK3, 1 IMEX2, 2 IMEX2B, 3 IMEX3 (Sec. 4.1)
+  int implicit_eq;  // 0 energy equations (entropy as back-up, RK3), 1 entropy in every zone
   // branch signature (a test instrument; null unless enabled): per cell a
   // 64-bit word into which every branch decision of the step is folded
   unsigned long long* sig;
@@ -248,6 +249,14 @@ __device__ __forceinline__ void bvec(const Geo<MET, R>& g, const R ucon[4], cons
   bvec_iut<MET, R>(g, ucon, ucov, R(1) / ucon[0], Bx, By, Bz, bcon, bcov, bsq);
 }
 
+// Specific entropy of the gas (Sec. 2, Eq. S): s = log(p^n / rho0^(n+1)),
+// n = 1/(Gamma - 1); the conserved entropy sqrt(-g) S u^t is sqrt(-g) rho0 u^t s.
+template <typename R>
+__device__ __forceinline__ R entropy_per_baryon(const DevParams& p, R rho, R ug) {
+  const R n = R(1.0 / (p.gam - 1.0));
+  return n * log(R(p.gam - 1.0) * ug) - (n + R(1)) * log(rho);
+}
+
 // Opacities per length at density rho and gas temperature T; kf is the
 // zone's absorption opacity when the opacity is a per-zone field; ks the
 // global opacity scale (kappa_scale; a separate argument so that the adjoint
@@ -408,7 +417,8 @@ __device__ __forceinline__ void face_speeds(const DevParams& p, const Geo<MET, R
 // share and the two states' U and F never need to be held together.
 template <int MET, typename R>
 __device__ __forceinline__ void face_accum(const DevParams& p, const Geo<MET, R>& g, int d,
-                                           const R P[NPR], R aFg, R aUg, R aFr, R aUr, R out[NPR]) {
+                                           const R P[NPR], R aFg, R aUg, R aFr, R aUr, R out[NPR],
+                                           R* fs = nullptr) {
   R ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq;
   fourvel<MET, R>(g, P[U1], P[U2], P[U3], ucon, ucov, &gm);
   const R iut = g.alpha / gm;
@@ -419,6 +429,8 @@ __device__ __forceinline__ void face_accum(const DevParams& p, const Geo<MET, R>
   const R gd = g.gdet;
   const R mt = rho * ucon[0], md = rho * ucon[d];
   out[0] += gd * (aFg * md + aUg * mt);
+  // entropy flux sqrt(-g) S u^d = s_gas times the mass flux (Sec. 2, Eq. S)
+  if (fs) *fs += entropy_per_baryon<R>(p, rho, ug) * (gd * (aFg * md + aUg * mt));
   out[1] += gd * (aFg * (wb * ucon[d] * ucov[0] - bcon[d] * bcov[0] + md) +
                   aUg * (wb * ucon[0] * ucov[0] + pt - bcon[0] * bcov[0] + mt));
 #pragma unroll

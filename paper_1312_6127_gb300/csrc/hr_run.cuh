@@ -10,8 +10,10 @@ inline Bufs make_bufs(harmrad_ctx* c) {
   b.P = c->P;
   b.K = c->K;
   b.Un = c->Un;
+  b.Sn = c->Sn;
   for (int d = 0; d < 3; ++d) {
     b.F[d] = c->F[d];
+    b.FS[d] = c->FS[d];
     b.spd[d] = c->spd[d];
     b.flat[d] = c->flat[d];
   }
@@ -131,7 +133,7 @@ int faces_impl(harmrad_ctx* c, bool fresh) {
       }
       k_edges<MET, R, 0><<<ge, be, 0, st>>>(p, bt, nb, c->P, aux, fl, Sl, Ed);
       mark(c, HARMRAD_K_EDGE);
-      k_face<MET, R, 0><<<g, bf, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd, c->geotab);
+      k_face<MET, R, 0><<<g, bf, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd, c->geotab, (R*)c->FS[0]);
     } else if (d == 1) {
       if (Sl) {
         k_slopes<MET, R, 1><<<gs, be, 0, st>>>(p, bt, nb, c->P, aux, Sl);
@@ -140,7 +142,7 @@ int faces_impl(harmrad_ctx* c, bool fresh) {
       }
       k_edges<MET, R, 1><<<ge, be, 0, st>>>(p, bt, nb, c->P, aux, fl, Sl, Ed);
       mark(c, HARMRAD_K_EDGE);
-      k_face<MET, R, 1><<<g, bf, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd, c->geotab);
+      k_face<MET, R, 1><<<g, bf, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd, c->geotab, (R*)c->FS[1]);
     } else {
       if (Sl) {
         k_slopes<MET, R, 2><<<gs, be, 0, st>>>(p, bt, nb, c->P, aux, Sl);
@@ -149,7 +151,7 @@ int faces_impl(harmrad_ctx* c, bool fresh) {
       }
       k_edges<MET, R, 2><<<ge, be, 0, st>>>(p, bt, nb, c->P, aux, fl, Sl, Ed);
       mark(c, HARMRAD_K_EDGE);
-      k_face<MET, R, 2><<<g, bf, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd, c->geotab);
+      k_face<MET, R, 2><<<g, bf, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd, c->geotab, (R*)c->FS[2]);
     }
     mark(c, HARMRAD_K_FACE);
     nk += 2;

@@ -19,6 +19,7 @@ ZONE_PMHD, ZONE_URAD, ZONE_BACKUP = 0, 1, 2
 PREC_FP64, PREC_SPLIT = 0, 1
 OPAC_CONST, OPAC_KRAMERS, OPAC_FIELD = 0, 1, 2
 INT_RK3, INT_IMEX2, INT_IMEX2B, INT_IMEX3 = 0, 1, 2, 3
+EQ_ENERGY, EQ_ENTROPY = 0, 1
 
 EXPORTS = [
     "harmrad_init", "harmrad_init_batch", "harmrad_destroy", "harmrad_set_opacity_field", "harmrad_set_prims",
@@ -69,6 +70,7 @@ class Params(ctypes.Structure):
         ("newton_tol", ctypes.c_double),
         ("precision", ctypes.c_int),
         ("integrator", ctypes.c_int),
+        ("implicit_eq", ctypes.c_int),
     ]
 
 
@@ -82,6 +84,7 @@ class Stats(ctypes.Structure):
         ("newton_iters", ctypes.c_longlong),
         ("kernel_launches", ctypes.c_int),
         ("graph", ctypes.c_int),
+        ("entropy_ok", ctypes.c_longlong),
     ]
 
 

@@ -1,0 +1,85 @@
+"""The entropy equation on the CUDA step (Sec. 2, Eq. S; Sec. 4.7, Eq.
+source6; Sec. 4.11) against the oracle: the all-zone entropy mode
+(HARMRAD_EQ_ENTROPY) zone by zone and in its round-off conservation of the
+total entropy, and the entropy back-up of the energy mode on a cold, fast
+box whose explicit update leaves zones without an energy-based solution."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1312_6127_gb300 import harmrad as H
+from paper_1312_6127_gb300 import workloads as W
+from tests.parity_metrics import zone_errors
+from tests.test_oracle_entropy import total_entropy
+
+pytestmark = pytest.mark.gpu
+
+
+def run_pair(cfg, P, steps):
+    g = H.Grid(cfg)
+    g.set_prims(P)
+    o = O.Oracle(cfg)
+    o.set_prims(P)
+    for _ in range(steps):
+        dt = o.cfl_dt()
+        assert g.cfl_dt() == pytest.approx(dt, rel=1e-12)
+        o.step(dt)
+        g.step(dt)
+        assert np.array_equal(g.status(), o.status())
+    return g, o
+
+
+@pytest.mark.parametrize("steps,tol", [(1, 1e-10), (5, 1e-8)])
+def test_entropy_mode_matches_oracle_and_conserves_entropy(steps, tol):
+    cfg, P = W.minkowski_box((12, 10, 8), seed=3)
+    cfg.update(kappa_abs0=0.0, kappa_es0=0.0, implicit_eq=H.EQ_ENTROPY)
+    g, o = run_pair(cfg, P, steps)
+    A, R = g.get_prims(), o.get_prims()
+    e = zone_errors(cfg, A, R)
+    st = g.stats()
+    S0, a0 = total_entropy(cfg, P)
+    S1, _ = total_entropy(cfg, A)
+    print("entropy mode, %d steps: per-zone error %.2e; total entropy change %.2e; entropy solves %d of %d"
+          % (steps, e.max(), (S1 - S0) / a0, st["entropy_ok"], st["zone_stages"]))
+    assert e.max() < tol
+    assert abs(S1 - S0) < 1e-10 * a0
+    assert st["entropy_ok"] == st["zone_stages"]
+
+
+def test_entropy_mode_torus_matches_oracle():
+    cfg, P = W.torus((32, 16, 8), seed=12345)
+    cfg["implicit_eq"] = H.EQ_ENTROPY
+    g, o = run_pair(cfg, P, 1)
+    e = zone_errors(cfg, g.get_prims(), o.get_prims())
+    print("entropy mode, torus, 1 step: per-zone error %.2e" % e.max())
+    assert e.max() < 1e-10
+
+
+def test_entropy_backup_matches_oracle():
+    """The cold (u_g = 1e-7 rho0), fast (up to 0.6 c) box: the same zones
+    fall back to the entropy equation on both sides (the same number of
+    entropy solutions, the same outcome per zone), and every zone agrees to
+    1e-10 except URAD/PRAD and back-up zones (the retry tolerance)."""
+    cfg, P = W.minkowski_box((12, 10, 8), seed=3, vmax=0.6)
+    P[1] = 1e-7 * P[0]
+    cfg.update(kappa_abs0=1.0)
+    g, o = run_pair(cfg, P, 1)
+    gs, oc = g.stats(), o.counts()
+    A, R = g.get_prims(), o.get_prims()
+    e = zone_errors(cfg, A, R)
+    st = o.status()
+    print("cold fast box: entropy solutions GPU %d, oracle %d; outcomes %s; errors: PMHD %.2e, retry %.2e"
+          % (gs["entropy_ok"], oc["entropy"], np.bincount(st.ravel(), minlength=3),
+             e[:, st == 0].max(), e[:, st == 1].max() if (st == 1).any() else 0.0))
+    assert gs["entropy_ok"] == oc["entropy"] > 10
+    assert e[:, st == 0].max() < 1e-10
+    assert e[:, st == 1].max() < 1e-6
+
+
+def test_adjoint_rejects_entropy_mode():
+    cfg, P = W.minkowski_box((8, 8, 8), seed=5)
+    cfg["implicit_eq"] = H.EQ_ENTROPY
+    g = H.Grid(cfg)
+    g.set_prims(P)
+    with pytest.raises(H.HarmradError):
+        g.adjoint_enable(True)
