@@ -42,6 +42,12 @@ struct AdjBufs {
   double* gaux;         // [3][ntot] cotangent of sqrt(-g) u^d (gas, rad) and w_d of one direction
   double* gemf;         // [ntot] cotangent of the edge EMFs of one pair of directions
   double* gk;           // [1] cotangent of kappa_scale
+  // the entropy (Sec. 2, Eq. S), for zones solved by the entropy equation
+  double* Sst;          // [3][nact] explicit entropy S* of every zone and sub-step
+  double* gS;           // [nact] cotangent of S*
+  double* gSn;          // [nact] cotangent of S^n, the step's initial conserved entropy
+  double* gXS;          // [nact] cotangent of the entropy's explicit rate X_S = -div F_S
+  double* gFS[3];       // [ntot] cotangent of the entropy face fluxes
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -120,6 +126,7 @@ __global__ void ka_implicit(DevParams p, BoxGeo bx, AdjBufs a, int s, double dt,
       any = any || gq[q] != 0.0;
       a.gU[q * bx.nact + z] = 0.0;
     }
+    a.gS[z] = 0.0;
     if (!any) continue;
     int i, j, k;
     zone_ijk(bx, z, i, j, k);
@@ -135,13 +142,14 @@ __global__ void ka_implicit(DevParams p, BoxGeo bx, AdjBufs a, int s, double dt,
     }
     (void)Pnext;
     const double kz = kfield(p, K, t);
-    if (m == 2 || m == METH_ENTROPY) {
-      // back-up: only B = U*[B] / sqrt(-g) is the zone's own; a zone solved by
-      // the entropy equation is held constant the same way (its error
-      // function differs from the energy one the transposed solve uses)
+    if (m == 2) {  // back-up: only B = U*[B] / sqrt(-g) is the zone's own
       for (int c = 0; c < 3; ++c) a.gU[(B1 + c) * bx.nact + z] = gq[B1 + c] * igd;
       continue;
     }
+    // a zone solved by the entropy equation: the same transposed solve on the
+    // entropy system (Eq. source6), which also depends on S*
+    const bool ent = m == METH_ENTROPY;
+    const double Sz = ent ? a.Sst[(long long)s * bx.nact + z] : 0.0;
     const Geo<MET, D4> g4 = geo_cast<D4>(g);
     {  // floors: gq <- (d floors / d P)^T gq at the solution
       const double rr = p.metric == KS ? p.R0 + exp(x1) : 1.0;
@@ -166,6 +174,8 @@ __global__ void ka_implicit(DevParams p, BoxGeo bx, AdjBufs a, int s, double dt,
       for (int q = 0; q < NPR; ++q) UsD[q] = D4(Us[q]);
       ImpSysT<MET, D4> sys;
       build_sys<MET, D4>(p, g4, UsD, h, D4(kz), sys);
+      sys.entropy = ent;
+      sys.Sstar = D4(Sz * igd);
       pmhd_final<MET, D4>(p, sys, xs, PsD, Eg);
       for (int r = 0; r < 4; ++r)
         for (int c = 0; c < 4; ++c) J[c][r] = Eg[r].d[c];  // transposed
@@ -181,6 +191,8 @@ __global__ void ka_implicit(DevParams p, BoxGeo bx, AdjBufs a, int s, double dt,
       for (int q = 0; q < NPR; ++q) UsD[q] = D4::seed(Us[q], q - 4 * ch);
       ImpSysT<MET, D4> sys;
       build_sys<MET, D4>(p, g4, UsD, h, D4(kz), sys);
+      sys.entropy = ent;
+      sys.Sstar = D4(Sz * igd);
       pmhd_final<MET, D4>(p, sys, xs, PsD, Eg);
       for (int c = 0; c < 4; ++c) {
         double v = 0.0;
@@ -197,10 +209,14 @@ __global__ void ka_implicit(DevParams p, BoxGeo bx, AdjBufs a, int s, double dt,
       ImpSysT<MET, D1> sys;
       build_sys<MET, D1>(p, g1, UsD, h, D1(kz), sys);
       sys.ks = D1::seed(p.kscale, 0);
+      sys.entropy = ent;
+      sys.Sstar = D1(Sz * igd);
       pmhd_final<MET, D1>(p, sys, xs, PsD, Eg);
       for (int r = 0; r < 4; ++r) gk -= lam[r] * Eg[r].d[0];
     }
     for (int q = 0; q < NPR; ++q) a.gU[q * bx.nact + z] = gU[q];
+    // S* enters the entropy row only, E_0 = S u^t(x) - S*/sqrt(-g) - h G_S
+    if (ent) a.gS[z] = lam[0] * igd;
   }
   warp_atomic_add(a.gk, gk);
 }
@@ -221,6 +237,11 @@ __global__ void ka_update(DevParams p, BoxGeo bx, AdjBufs a, int s, double dt, c
       if (s > 0) a.gUn[q * bx.nact + z] += A * gq[q];
       a.gX[q * bx.nact + z] = Bc * dt * gq[q];
     }
+    // S* = A S^n + Bc (S(P_s) + dt X_S), S(P) = U_rho(P) s_gas(P)
+    const double gs = a.gS[z];
+    any = any || gs != 0.0;
+    if (s > 0) a.gSn[z] += A * gs;
+    a.gXS[z] = Bc * dt * gs;
     int i, j, k;
     zone_ijk(bx, z, i, j, k);
     const long long t = cell_index(bx, i, j, k);
@@ -234,8 +255,9 @@ __global__ void ka_update(DevParams p, BoxGeo bx, AdjBufs a, int s, double dt, c
       D4 PsD[NPR], UsD[NPR], XD[NPR];
       for (int q = 0; q < NPR; ++q) PsD[q] = D4::seed(Ps0[q * bx.ntot + t], q - 4 * ch);
       cons_source<MET, D4>(p, g4, x1, x2, PsD, UsD, XD);
+      const D4 Su = gs != 0.0 ? UsD[RHO] * entropy_per_baryon<D4>(p, PsD[RHO], PsD[UU]) : D4(0.0);
       for (int c = 0; c < 4; ++c) {
-        double v = 0.0;
+        double v = gs * Su.d[c];
         for (int q = 0; q < NPR; ++q) v += gq[q] * (UsD[q].d[c] + dt * XD[q].d[c]);
         a.gP[(4 * ch + c) * bx.ntot + t] = Bc * v;
       }
@@ -254,6 +276,8 @@ __global__ void ka_un(DevParams p, BoxGeo bx, AdjBufs a, const double* __restric
       gq[q] = a.gUn[q * bx.nact + z];
       any = any || gq[q] != 0.0;
     }
+    const double gs = a.gSn[z];  // S^n = U_rho(P^n) s_gas(P^n)
+    any = any || gs != 0.0;
     if (!any) continue;
     int i, j, k;
     zone_ijk(bx, z, i, j, k);
@@ -264,8 +288,9 @@ __global__ void ka_un(DevParams p, BoxGeo bx, AdjBufs a, const double* __restric
       D4 PsD[NPR], UsD[NPR], XD[NPR];
       for (int q = 0; q < NPR; ++q) PsD[q] = D4::seed(P0[q * bx.ntot + t], q - 4 * ch);
       cons_source<MET, D4>(p, g4, x1, x2, PsD, UsD, XD);
+      const D4 Su = gs != 0.0 ? UsD[RHO] * entropy_per_baryon<D4>(p, PsD[RHO], PsD[UU]) : D4(0.0);
       for (int c = 0; c < 4; ++c) {
-        double v = 0.0;
+        double v = gs * Su.d[c];
         for (int q = 0; q < NPR; ++q) v += gq[q] * UsD[q].d[c];
         a.gN[(4 * ch + c) * bx.nact + z] += v;
       }
@@ -277,7 +302,8 @@ __global__ void ka_un(DevParams p, BoxGeo bx, AdjBufs a, const double* __restric
 // Face range of the face kernel of direction d; the flux at cell t is the
 // flux through t's lower face: +1/dx in X of zone t, -1/dx in X of zone t-s_d.
 template <int d>
-__global__ void ka_fluxgrad(BoxGeo bx, const double* __restrict__ gX, double* __restrict__ gF) {
+__global__ void ka_fluxgrad(BoxGeo bx, const double* __restrict__ gX, double* __restrict__ gF,
+                            const double* __restrict__ gXS, double* __restrict__ gFS) {
   int len[3], off[3];
   for (int e = 0; e < 3; ++e) {
     if (e == d) {
@@ -316,6 +342,12 @@ __global__ void ka_fluxgrad(BoxGeo bx, const double* __restrict__ gX, double* __
       if (up) v += gX[q * bx.nact + zu] * idx_;
       if (dn) v -= gX[q * bx.nact + zd] * idx_;
       gF[q * bx.ntot + t] = v;
+    }
+    if (gFS) {  // the entropy flux, X_S = -div F_S
+      double v = 0.0;
+      if (up) v += gXS[zu] * idx_;
+      if (dn) v -= gXS[zd] * idx_;
+      gFS[t] = v;
     }
   }
 }
@@ -405,7 +437,8 @@ __global__ void ka_ct_T(BoxGeo bx, const double* __restrict__ gemf, double* __re
 template <int MET, int d>
 __global__ void __launch_bounds__(128) ka_face(DevParams p, BoxGeo bx, const double* __restrict__ E,
                                                const double* __restrict__ K, const double* __restrict__ gF,
-                                               double* __restrict__ gE, double* gk_out) {
+                                               double* __restrict__ gE, double* gk_out,
+                                               const double* __restrict__ gFS) {
   typedef Dn<5> D5;
   const bool weighted = (MET == KS) && (d != 1);
   int len[3], off[3];
@@ -440,6 +473,8 @@ __global__ void __launch_bounds__(128) ka_face(DevParams p, BoxGeo bx, const dou
       gq[q] = gF[q * bx.ntot + t];
       any = any || gq[q] != 0.0;
     }
+    const double gfs = gFS ? gFS[t] : 0.0;
+    any = any || gfs != 0.0;
     if (!any) continue;
     double xf[3];
     for (int e = 0; e < 3; ++e) xf[e] = bx.x0[e] + (ii[e] + (e == d ? 0.0 : 0.5)) * bx.dx[e];
@@ -464,9 +499,11 @@ __global__ void __launch_bounds__(128) ka_face(DevParams p, BoxGeo bx, const dou
         PRd[q] = D5::seed(PR[q], NPR + q - 5 * ch);
       }
       const D5 ks = D5::seed(p.kscale, 24 - 5 * ch);
-      face_flux<MET, D5, d>(p, g5, D5(bx.dx[d]), D5(kL), D5(kR), ks, PLd, PRd, out, &smax);
+      D5 fs;
+      face_flux<MET, D5, d>(p, g5, D5(bx.dx[d]), D5(kL), D5(kR), ks, PLd, PRd, out, &smax, nullptr,
+                            gfs != 0.0 ? &fs : nullptr);
       for (int c = 0; c < 5; ++c) {
-        double v = 0.0;
+        double v = gfs != 0.0 ? gfs * fs.d[c] : 0.0;
         for (int q = 0; q < NPR; ++q) v += gq[q] * out[q].d[c];
         gin[5 * ch + c] = v;
       }

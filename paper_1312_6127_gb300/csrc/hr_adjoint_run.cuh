@@ -40,10 +40,12 @@ int Run<MET>::adjoint(harmrad_ctx* c, const double* gPout, double* gPin, double*
     c->rec_ust = a.Ust + (size_t)s * 12 * na;
     c->rec_meth = a.meth + (size_t)s * na;
     c->rec_psol = a.Psol + (size_t)s * 12 * na;
+    c->rec_sst = a.Sst + (size_t)s * na;
     r = solve_impl<MET, double>(c, s, ImexStage{});
     c->rec_ust = nullptr;
     c->rec_meth = nullptr;
     c->rec_psol = nullptr;
+    c->rec_sst = nullptr;
     if (r < 0) return r;
   }
   HR_ACHECK(cudaMemcpyAsync(a.Pst + (size_t)3 * 12 * nt, c->P, pbytes, cudaMemcpyDeviceToDevice, st));
@@ -53,6 +55,7 @@ int Run<MET>::adjoint(harmrad_ctx* c, const double* gPout, double* gPin, double*
   HR_ACHECK(cudaMemsetAsync(a.gUn, 0, 12 * (size_t)na * sizeof(double), st));
   HR_ACHECK(cudaMemsetAsync(a.carry, 0, 6 * (size_t)nt * sizeof(double), st));
   HR_ACHECK(cudaMemsetAsync(a.gk, 0, sizeof(double), st));
+  HR_ACHECK(cudaMemsetAsync(a.gSn, 0, (size_t)na * sizeof(double), st));
   double dt = 0.0;
   HR_ACHECK(cudaMemcpyAsync(&dt, c->dt, sizeof(double), cudaMemcpyDeviceToHost, st));
   HR_ACHECK(cudaStreamSynchronize(st));
@@ -81,9 +84,9 @@ int Run<MET>::adjoint(harmrad_ctx* c, const double* gPout, double* gPin, double*
       if (!p.act[d]) continue;
       long long w = 1;
       for (int e = 0; e < 3; ++e) w *= (e == d) ? bx.n[e] + 1 : (bx.n[e] > 1 ? bx.n[e] + 2 : 1);
-      if (d == 0) ka_fluxgrad<0><<<G(w), 128, 0, st>>>(bx, a.gX, a.gF[0]);
-      if (d == 1) ka_fluxgrad<1><<<G(w), 128, 0, st>>>(bx, a.gX, a.gF[1]);
-      if (d == 2) ka_fluxgrad<2><<<G(w), 128, 0, st>>>(bx, a.gX, a.gF[2]);
+      if (d == 0) ka_fluxgrad<0><<<G(w), 128, 0, st>>>(bx, a.gX, a.gF[0], a.gXS, a.gFS[0]);
+      if (d == 1) ka_fluxgrad<1><<<G(w), 128, 0, st>>>(bx, a.gX, a.gF[1], a.gXS, a.gFS[1]);
+      if (d == 2) ka_fluxgrad<2><<<G(w), 128, 0, st>>>(bx, a.gX, a.gF[2], a.gXS, a.gFS[2]);
     }
     for (int pa = 0; pa < 3; ++pa)
       for (int pb = pa + 1; pb < 3; ++pb) {
@@ -122,7 +125,7 @@ int Run<MET>::adjoint(harmrad_ctx* c, const double* gPout, double* gPin, double*
       if (d == 0) {
         k_slopes<MET, double, 0><<<G(ws), 128, 0, st>>>(p, c->dboxes, 1, Pg, aux, (double*)c->slope);
         k_edges<MET, double, 0><<<G(wc), 128, 0, st>>>(p, c->dboxes, 1, Pg, aux, flat, (double*)c->slope, E);
-        ka_face<MET, 0><<<G(wf), 128, 0, st>>>(p, bx, E, K, a.gF[0], a.gE, a.gk);
+        ka_face<MET, 0><<<G(wf), 128, 0, st>>>(p, bx, E, K, a.gF[0], a.gE, a.gk, a.gFS[0]);
         ka_edges<MET, 0><<<G(wc), 128, 0, st>>>(p, bx, Pg, aux, flat, a.gE, a.gP, a.gchi);
         if (p.recon == 0) {
           ka_flatten<0><<<G(wc), 128, 0, st>>>(p, bx, Pg, aux, chi_prev, a.gchi, carry, a.gP, a.gaux);
@@ -131,7 +134,7 @@ int Run<MET>::adjoint(harmrad_ctx* c, const double* gPout, double* gPin, double*
       } else if (d == 1) {
         k_slopes<MET, double, 1><<<G(ws), 128, 0, st>>>(p, c->dboxes, 1, Pg, aux, (double*)c->slope);
         k_edges<MET, double, 1><<<G(wc), 128, 0, st>>>(p, c->dboxes, 1, Pg, aux, flat, (double*)c->slope, E);
-        ka_face<MET, 1><<<G(wf), 128, 0, st>>>(p, bx, E, K, a.gF[1], a.gE, a.gk);
+        ka_face<MET, 1><<<G(wf), 128, 0, st>>>(p, bx, E, K, a.gF[1], a.gE, a.gk, a.gFS[1]);
         ka_edges<MET, 1><<<G(wc), 128, 0, st>>>(p, bx, Pg, aux, flat, a.gE, a.gP, a.gchi);
         if (p.recon == 0) {
           ka_flatten<1><<<G(wc), 128, 0, st>>>(p, bx, Pg, aux, chi_prev, a.gchi, carry, a.gP, a.gaux);
@@ -140,7 +143,7 @@ int Run<MET>::adjoint(harmrad_ctx* c, const double* gPout, double* gPin, double*
       } else {
         k_slopes<MET, double, 2><<<G(ws), 128, 0, st>>>(p, c->dboxes, 1, Pg, aux, (double*)c->slope);
         k_edges<MET, double, 2><<<G(wc), 128, 0, st>>>(p, c->dboxes, 1, Pg, aux, flat, (double*)c->slope, E);
-        ka_face<MET, 2><<<G(wf), 128, 0, st>>>(p, bx, E, K, a.gF[2], a.gE, a.gk);
+        ka_face<MET, 2><<<G(wf), 128, 0, st>>>(p, bx, E, K, a.gF[2], a.gE, a.gk, a.gFS[2]);
         ka_edges<MET, 2><<<G(wc), 128, 0, st>>>(p, bx, Pg, aux, flat, a.gE, a.gP, a.gchi);
         if (p.recon == 0) {
           ka_flatten<2><<<G(wc), 128, 0, st>>>(p, bx, Pg, aux, chi_prev, a.gchi, carry, a.gP, a.gaux);

@@ -353,7 +353,8 @@ void free_adjoint(harmrad_ctx* c) {
   if (c->adj) {
     hr::AdjBufs& a = *c->adj;
     void* ptrs[] = {a.Pst, a.chi, a.Ust, a.meth, a.Psol, a.gP, a.gN, a.gUn, a.gU, a.gX, a.gF[0], a.gF[1], a.gF[2],
-                    a.gE, a.gchi, a.carry, a.gaux, a.gemf, a.gk};
+                    a.gE, a.gchi, a.carry, a.gaux, a.gemf, a.gk, a.Sst, a.gS, a.gSn, a.gXS, a.gFS[0],
+                    a.gFS[1], a.gFS[2]};
     for (void* q : ptrs)
       if (q) cudaFree(q);
     delete c->adj;
@@ -833,6 +834,11 @@ int harmrad_adjoint_enable(harmrad_ctx* c, int on) {
   rc = rc ? rc : dalloc(&a.gaux, 3 * nt * D);
   rc = rc ? rc : dalloc(&a.gemf, nt * D);
   rc = rc ? rc : dalloc(&a.gk, D);
+  rc = rc ? rc : dalloc(&a.Sst, 3 * na * D);
+  rc = rc ? rc : dalloc(&a.gS, na * D);
+  rc = rc ? rc : dalloc(&a.gSn, na * D);
+  rc = rc ? rc : dalloc(&a.gXS, na * D);
+  for (int d = 0; d < 3; ++d) rc = rc ? rc : dalloc(&a.gFS[d], nt * D);
   if (!rc && cudaMemsetAsync(a.chi, 0, 3 * 3 * 2 * nt * D, c->stream) != cudaSuccess) rc = HARMRAD_E_CUDA;
   if (!rc && cudaMemsetAsync(a.gF[0], 0, 12 * nt * D, c->stream) != cudaSuccess) rc = HARMRAD_E_CUDA;
   if (!rc && cudaMemsetAsync(a.gF[1], 0, 12 * nt * D, c->stream) != cudaSuccess) rc = HARMRAD_E_CUDA;

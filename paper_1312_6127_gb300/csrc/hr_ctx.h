@@ -66,6 +66,7 @@ struct harmrad_ctx {
   double* rec_ust;
   unsigned char* rec_meth;
   double* rec_psol;
+  double* rec_sst;
   double* imex_ust;   // IMEX: [12][nact] U* of the current stage
   double* imex_psol;  // IMEX: [12][nact] implicit solution of the current stage (before floors)
   double* imex_M;     // IMEX: [4 stages][4 gas rows][nact] implicit sources M^j

@@ -52,6 +52,7 @@ struct Bufs {
   double* ust_rec;            // [12][nact] U* of every zone of the sub-step
   unsigned char* meth_rec;    // [nact] outcome of every zone of the sub-step
   double* psol_rec;           // [12][nact] solution of every zone before the floors
+  double* sst_rec;            // [nact] explicit entropy S* of every zone of the sub-step
   double* imexM;              // IMEX: [4 stages][4 gas rows][nact] per grid, grid b at 16 aoff_b
 };
 
@@ -1420,6 +1421,7 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
           divS += double(FSd[t + bx.str[d]] - FSd[t]) / bx.dx[d];
         }
         Sst = A * sn + Bc * (Su - dt * divS);
+        if (b.sst_rec) b.sst_rec[bx.aoff + z] = Sst;
       }
       // implicit solve
       const double h = IMEX ? im.g * dt : Bc * dt;

@@ -40,6 +40,7 @@ inline Bufs make_bufs(harmrad_ctx* c) {
   b.ust_rec = c->rec_ust;
   b.meth_rec = c->rec_meth;
   b.psol_rec = c->rec_psol;
+  b.sst_rec = c->rec_sst;
   if (c->imex_M) {  // IMEX contexts record U* and the solutions for the stage sources
     b.ust_rec = c->imex_ust;
     b.psol_rec = c->imex_psol;

@@ -84,6 +84,12 @@ def cases():
     out["ks_random_ppm_laxf_kramers"] = (dict(cfg, newton_tol=TOL), P)
     cfg, P = W.ks_random_state((32, 16, 8), seed=9, tau=10.0)
     out["ks_random_stiff_urad"] = (dict(cfg, newton_tol=TOL), P)
+    # a cold (u_g = 1e-7 rho0), fast box whose explicit update leaves zones
+    # without an energy-based solution: the entropy back-up solves them, and
+    # the adjoint differentiates that solve too
+    cfg, P = W.minkowski_box((8, 8, 8), seed=3, vmax=0.6)
+    P[W.UU] = 1e-7 * P[W.RHO]
+    out["mink_cold_entropy_backup"] = (dict(cfg, kappa_abs0=1.0, newton_tol=TOL), P)
     # the default Newton tolerance (1e-12), as users run the step
     cfg, P = W.minkowski_box((8, 8, 8), seed=6, recon=W.PPM, flux=W.HLL)
     out["mink_ppm_hll_default_tol"] = (cfg, P)
@@ -113,7 +119,10 @@ def test_step_adjoint_against_finite_differences(name):
     g.adjoint_enable(True)
     g.step(dt)
     st = g.stats()
-    print("%s: %d PMHD, %d URAD, %d back-up zone-stages" % (name, st["pmhd_ok"], st["urad_ok"], st["backup"]))
+    print("%s: %d PMHD, %d URAD (%d by the entropy equation), %d back-up zone-stages"
+          % (name, st["pmhd_ok"], st["urad_ok"], st["entropy_ok"], st["backup"]))
+    if name == "mink_cold_entropy_backup":
+        assert st["entropy_ok"] > 0
     w = rng.standard_normal(P.shape)
     gin, gk = g.step_adjoint(w)
     L = lambda Q: float((w * Q).sum())
