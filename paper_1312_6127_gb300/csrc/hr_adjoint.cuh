@@ -152,7 +152,7 @@ __global__ void ka_implicit(DevParams p, BoxGeo bx, AdjBufs a, int s, double dt,
     const double Sz = ent ? a.Sst[(long long)s * bx.nact + z] : 0.0;
     const Geo<MET, D4> g4 = geo_cast<D4>(g);
     {  // floors: gq <- (d floors / d P)^T gq at the solution
-      const double rr = p.metric == KS ? p.R0 + exp(x1) : 1.0;
+      const double rr = log_r<MET>(p, x1);
       double gs[NPR];
       for (int ch = 0; ch < 3; ++ch) {
         D4 PD[NPR];

@@ -871,8 +871,16 @@ __global__ void k_ct(DevParams p, const BoxGeo* __restrict__ boxes, int nbox, co
 // ----------------------------------------------------------------- floors
 // Lorentz-factor caps, density and internal-energy floors f0 r^pow,
 // magnetisation caps b^2/rho, b^2/u_g, u_g/rho, and Ebar > 0.
+// ln r of the cell centre at x1 (0 on the Minkowski grid, where the floors
+// take r = 1): x1 itself when r = e^x1 (R0 = 0).
+template <int MET>
+__device__ __forceinline__ double log_r(const DevParams& p, double x1) {
+  if constexpr (MET == KS) return p.R0 == 0.0 ? x1 : log(p.R0 + exp(x1));
+  else return 0.0;
+}
+
 template <int MET, typename T = double>
-__device__ __forceinline__ void apply_floors(const DevParams& p, const Geo<MET, T>& g, double r, T P[NPR],
+__device__ __forceinline__ void apply_floors(const DevParams& p, const Geo<MET, T>& g, double lr, T P[NPR],
                                              unsigned* code = nullptr) {
   T gm = sqrt(1.0 + g.sq3(P[U1], P[U2], P[U3]));
   if (code) {  // which floors act (the branch signature)
@@ -897,8 +905,10 @@ __device__ __forceinline__ void apply_floors(const DevParams& p, const Geo<MET, 
   T ucon[4], ucov[4], bcon[4], bcov[4], bsq;
   fourvel<MET, T>(g, P[U1], P[U2], P[U3], ucon, ucov, &gm);
   bvec<MET, T>(g, ucon, ucov, P[B1], P[B2], P[B3], bcon, bcov, &bsq);
-  T rfl = T(p.rf0 * (p.rfp == 0.0 ? 1.0 : pow(r, p.rfp)));
-  T ufl = T(p.uf0 * (p.ufp == 0.0 ? 1.0 : pow(r, p.ufp)));
+  // f0 r^pow as exp(pow ln r): the floor needs ln r only (x1 itself on the
+  // Kerr-Schild grid with R0 = 0, where r = e^x1)
+  T rfl = T(p.rf0 * (p.rfp == 0.0 ? 1.0 : exp(p.rfp * lr)));
+  T ufl = T(p.uf0 * (p.ufp == 0.0 ? 1.0 : exp(p.ufp * lr)));
   if (code) {
     const T rb = bsq / p.bsq_rho_max, ub = bsq / p.bsq_u_max;
     const T rf = fmax(rfl, rb), uf = fmax(ufl, ub);
@@ -1266,7 +1276,7 @@ __device__ __forceinline__ bool pmhd_finish(const DevParams& p, const BoxGeo& bx
     if (b.psol_rec)
       for (int q = 0; q < NPR; ++q) b.psol_rec[12 * bx.aoff + q * bx.nact + z] = Pn[q];
     unsigned fcode = 0;
-    apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn, p.sig ? &fcode : nullptr);
+    apply_floors<MET>(p, g, log_r<MET>(p, x1), Pn, p.sig ? &fcode : nullptr);
     if (p.sig) sig_put(p, bx.coff + t, 60, (fcode << 2 | lcode) << 4 | ST_PMHD);
 #pragma unroll
     for (int q = 0; q < NPR; ++q) P[q * bx.ntot + t] = Pn[q];
@@ -1653,7 +1663,7 @@ __global__ void __launch_bounds__(128) k_retry(DevParams p, const BoxGeo* __rest
     if (b.psol_rec)
       for (int q = 0; q < NPR; ++q) b.psol_rec[12 * bx.aoff + q * bx.nact + z] = Pn[q];
     unsigned fcode = 0;
-    apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn, p.sig ? &fcode : nullptr);
+    apply_floors<MET>(p, g, log_r<MET>(p, x1), Pn, p.sig ? &fcode : nullptr);
     if (p.sig) sig_put(p, bx.coff + t, 60, fcode << 4 | (unsigned)method);
     for (int q = 0; q < NPR; ++q) P[q * bx.ntot + t] = Pn[q];
     unsigned char m = (unsigned char)method;
@@ -1739,7 +1749,7 @@ __global__ void k_backup_apply(DevParams p, const BoxGeo* __restrict__ boxes, Bu
     double Pn[NPR];
     for (int q = 0; q < NPR; ++q) Pn[q] = b.ftmp[(long long)e * NPR + q];
     unsigned fcode = 0;
-    apply_floors<MET>(p, g, p.metric == KS ? p.R0 + exp(x1) : 1.0, Pn, p.sig ? &fcode : nullptr);
+    apply_floors<MET>(p, g, log_r<MET>(p, x1), Pn, p.sig ? &fcode : nullptr);
     if (p.sig) sig_put(p, bx.coff + t, 62, fcode);
     for (int q = 0; q < NPR; ++q) P[q * bx.ntot + t] = Pn[q];
   }

