@@ -140,8 +140,8 @@ typedef struct harmrad_params {
  * extremely sub-dominant (below 10 eps_m of the gas in conserved or
  * fluid-frame energy) starts with URAD and skips PMHD. */
 #define HARMRAD_ZONE_PMHD 0    /* PMHD Newton accepted */
-#define HARMRAD_ZONE_URAD 1    /* a retry method (URAD, PRAD or the entropy equation) gave the
-                                  accepted solution */
+#define HARMRAD_ZONE_URAD 1    /* a retry method (URAD, PRAD, the entropy or the cold-MHD
+                                  equations) gave the accepted solution */
 #define HARMRAD_ZONE_BACKUP 2  /* no method reached e_T <= 1e-7: neighbour average */
 
 typedef struct harmrad_stats {
@@ -154,6 +154,9 @@ typedef struct harmrad_stats {
   long long entropy_ok;        /* solves whose accepted solution came from the entropy
                                   equation (counted in urad_ok as well, or in pmhd_ok with
                                   implicit_eq = 1) */
+  long long cold_ok;           /* solves whose accepted solution came from the cold-MHD
+                                  equations (counted in urad_ok as well); their u_g is the
+                                  neighbours' average */
 } harmrad_stats;
 
 typedef struct harmrad_ctx harmrad_ctx;
@@ -250,13 +253,34 @@ int harmrad_compute_fluxes(harmrad_ctx* ctx, int dir, double* F_host);
 int harmrad_zone_physics(const harmrad_params* p, int n, const double* x, const double* P,
                          double* U, double* SM, double* F, double* speeds, void* stream);
 
+/* Method codes of the zone-level solves below: HARMRAD_ZONE_PMHD,
+ * HARMRAD_ZONE_URAD (URAD or PRAD) and HARMRAD_ZONE_BACKUP (no method reached
+ * e_T <= 1e-7; Pout holds the guess with B of U*), and, for the back-up
+ * equations of Sec. 4.11: */
+#define HARMRAD_ZONE_ENTROPY 3 /* the entropy equation (Eq. source6) in place of the energy equation */
+#define HARMRAD_ZONE_COLD 4    /* the cold-MHD equations: momentum only, u_g held at the guess */
+
 /* Implicit four-force solve of n independent zones (device pointers):
  * x[n][4], Ustar[n][12] explicit conserved state, Ps[n][12] guess primitives,
- * h[n] = b_s dt -> Pout[n][12], eT[n], iters[n], method[n] (HARMRAD_ZONE_*).
- * Same solver and method sequence as harmrad_step (Sec. 4.7-4.11). */
+ * h[n] = b_s dt -> Pout[n][12], eT[n], iters[n], method[n] (the codes above).
+ * Same solver and method sequence as harmrad_step (Sec. 4.7-4.11) without the
+ * explicit entropy: PMHD, URAD, PRAD, then the cold-MHD equations for a cold,
+ * momentum-dominated zone.  The grid step then replaces a cold-MHD zone's u_g
+ * by its neighbours' average; a single zone has no neighbours, so Pout keeps
+ * the solve's u_g (the guess's). */
 int harmrad_zone_implicit(const harmrad_params* p, int n, const double* x, const double* Ustar,
                           const double* Ps, const double* h, double* Pout, double* eT, int* iters,
                           unsigned char* method, void* stream);
+
+/* As harmrad_zone_implicit with the explicit entropy Sstar[n] (device, may be
+ * NULL) = sqrt(-g) S u^t of the zone after the explicit update, S u^t =
+ * rho0 u^t s_gas (Sec. 2, Eq. S): a zone that the energy methods leave without
+ * a solution tries the entropy equation (HARMRAD_ZONE_ENTROPY) before the
+ * cold-MHD equations, as in harmrad_step's RK3 stages.  A non-finite Sstar[i]
+ * skips the entropy equation for that zone. */
+int harmrad_zone_implicit_full(const harmrad_params* p, int n, const double* x, const double* Ustar,
+                               const double* Sstar, const double* Ps, const double* h, double* Pout,
+                               double* eT, int* iters, unsigned char* method, void* stream);
 
 /* Same solve as harmrad_zone_implicit, for callers that cannot allocate device
  * memory: processes whose device memory is owned by another allocator (a
@@ -326,8 +350,11 @@ int harmrad_profile_step(harmrad_ctx* ctx, double dt, harmrad_kernel_times* out)
  * Jacobian.  Branches (limiters, wave-speed maxima, flattener clamps, outflow
  * clamps) take the derivative of the branch the step took.  Zones whose
  * solution a floor changed are constant except for B; back-up zones pass
- * their cotangent to the neighbours they averaged.  The paper has no adjoint;
- * this is an extension.  HARMRAD_E_STATE if no step ran since enabling. */
+ * their cotangent to the neighbours they averaged.  Zones solved by the
+ * entropy equation take the transposed solve of that system.  The paper has
+ * no adjoint; this is an extension.  HARMRAD_E_STATE if no step ran since
+ * enabling; HARMRAD_E_ARG if a zone of the step was solved by the cold-MHD
+ * equations (its u_g, the neighbours' average, has no adjoint here). */
 int harmrad_adjoint_enable(harmrad_ctx* ctx, int on);
 int harmrad_step_adjoint(harmrad_ctx* ctx, const double* gP_out, double* gP_in, double* g_kappa,
                          int on_device);

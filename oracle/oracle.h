@@ -78,6 +78,7 @@ typedef struct {
   int method;      /* ORC_OK_PMHD, ORC_OK_URAD or ORC_BACKUP */
   int neg_erad;    /* 1 if the accepted solution hit the TYPE2 negative-energy branch */
   int entropy;     /* 1 if the entropy equation gave the accepted solution */
+  int cold;        /* 1 if the cold-MHD equations gave it (u_g held at the guess) */
 } orc_implicit_info;
 
 /* --- grid-level driver --------------------------------------------------- */
@@ -97,7 +98,8 @@ void   orc_get_status(void* ctx, unsigned char* st);
 void   orc_get_iters(void* ctx, int* it);
 /* Counts over the last step: [0] PMHD-accepted, [1] URAD-accepted, [2] back-up,
  * [3] total Newton iterations, [4] zone-stages solved, [5] zone-stages whose
- * accepted solution came from the entropy equation. */
+ * accepted solution came from the entropy equation, [6] from the cold-MHD
+ * equations. */
 void   orc_get_counts(void* ctx, long long* c);
 /* Face fluxes of one direction after the last call to orc_compute_fluxes
  * (debug/test hook): computes ghost fill + fluxes (+flux-CT) for the current
@@ -141,6 +143,10 @@ int    orc_gas_invert(const orc_params* p, const double* x, const double* U,
  * sub-dominant (URAD first in the grid step). */
 int    orc_radiation_subdominant(const orc_params* p, const double* x, const double* Ustar,
                                  const double* Ps);
+/* Sec. 4.11 test of one zone for the cold-MHD back-up: 1 if the guess Ps is
+ * cold (u_g < 0.1 rho0 u~^i u~_i) and both the gas t^t_mu and the radiation
+ * R^t_mu of U* are momentum-dominated (|t_t t^t| < 0.1 |t_i t^i|). */
+int    orc_cold_allowed(const orc_params* p, const double* x, const double* Ustar, const double* Ps);
 /* Implicit four-force solve of one zone: U* (12, densitised), the explicit
  * entropy S* = sqrt(-g) S u^t (NULL: no entropy back-up), guess P_s,
  * h = b_s*dt, the grid step's method sequence.  Writes the new prims and info. */

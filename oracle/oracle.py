@@ -65,6 +65,7 @@ class OrcInfo(ctypes.Structure):
         ("method", ctypes.c_int),
         ("neg_erad", ctypes.c_int),
         ("entropy", ctypes.c_int),
+        ("cold", ctypes.c_int),
     ]
 
 
@@ -122,6 +123,8 @@ def lib():
         L.orc_gas_invert.argtypes = [pp, dp, dp, dp, ctypes.c_double, dp]
         L.orc_implicit_zone.argtypes = [pp, dp, dp, dp, dp, ctypes.c_double, dp, ctypes.POINTER(OrcInfo)]
         L.orc_radiation_subdominant.argtypes = [pp, dp, dp, dp]
+        L.orc_cold_allowed.argtypes = [pp, dp, dp, dp]
+        L.orc_cold_allowed.restype = ctypes.c_int
         L.orc_method_zone.argtypes = [pp, dp, dp, dp, ctypes.c_double, ctypes.c_int, dp, dp,
                                       ctypes.POINTER(ctypes.c_int)]
         L.orc_radiation_subdominant.restype = ctypes.c_int
@@ -210,10 +213,10 @@ class Oracle:
         return it
 
     def counts(self):
-        c = np.zeros(6, dtype=np.int64)
+        c = np.zeros(7, dtype=np.int64)
         lib().orc_get_counts(self._h, c.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)))
         return {"pmhd": int(c[0]), "urad": int(c[1]), "backup": int(c[2]),
-                "iters": int(c[3]), "solves": int(c[4]), "entropy": int(c[5])}
+                "iters": int(c[3]), "solves": int(c[4]), "entropy": int(c[5]), "cold": int(c[6])}
 
     def fluxes(self, d):
         m = list(self.n)
@@ -304,7 +307,8 @@ def gas_invert(p, x, U, Pg, tol=1e-14):
 
 def implicit_zone(p, x, Ustar, Ps, h, Sstar=None):
     """Implicit solve of one zone; Sstar = sqrt(-g) S u^t of the explicit
-    update enables the entropy back-up (None: energy methods only)."""
+    update enables the entropy back-up (None: energy methods, then the
+    cold-MHD equations)."""
     x, Ustar, Ps = _vec(x), _vec(Ustar), _vec(Ps)
     out = np.empty(NP)
     info = OrcInfo()
@@ -332,6 +336,12 @@ def radiation_subdominant(p, x, Ustar, Ps):
     """Sec. 4.10 sub-dominance test of one zone."""
     x, Us, Pz = _vec(x), _vec(Ustar), _vec(Ps)
     return bool(lib().orc_radiation_subdominant(ctypes.byref(p), _dp(x), _dp(Us), _dp(Pz)))
+
+
+def cold_allowed(p, x, Ustar, Ps):
+    """Sec. 4.11 test of one zone for the cold-MHD back-up."""
+    x, Us, Pz = _vec(x), _vec(Ustar), _vec(Ps)
+    return bool(lib().orc_cold_allowed(ctypes.byref(p), _dp(x), _dp(Us), _dp(Pz)))
 
 
 def pmhd_residual(p, x, Ustar, h, xg):

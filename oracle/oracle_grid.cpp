@@ -48,7 +48,7 @@ struct Ctx {
   std::vector<int> iters;             // active zones
   std::vector<double> FS[3];  // face fluxes of the entropy S u^j [ntot] (RK3)
   std::vector<double> Sn;     // sqrt(-g) S u^t of the step's initial state [ntot]
-  long long counts[6];
+  long long counts[7];
   std::vector<double> M[4];  // IMEX: implicit source of stage j, gas rows [4][ntot]
 };
 
@@ -605,9 +605,9 @@ void substep(Ctx& c, int s, double dt) {
   std::vector<double> Pnew((size_t)NP * c.ntot);
   std::memcpy(Pnew.data(), c.P.data(), sizeof(double) * NP * c.ntot);
   std::vector<unsigned char> failed((size_t)c.n[0] * c.n[1] * c.n[2], 0);
-  long long n_pmhd = 0, n_urad = 0, n_back = 0, n_iter = 0, n_solve = 0, n_ent = 0;
+  long long n_pmhd = 0, n_urad = 0, n_back = 0, n_iter = 0, n_solve = 0, n_ent = 0, n_cold = 0;
 #pragma omp parallel for num_threads(orc_threads()) schedule(dynamic, 1) \
-    reduction(+ : n_pmhd, n_urad, n_back, n_iter, n_solve, n_ent)
+    reduction(+ : n_pmhd, n_urad, n_back, n_iter, n_solve, n_ent, n_cold)
   for (int k = 0; k < c.n[2]; ++k)
     for (int j = 0; j < c.n[1]; ++j)
       for (int i = 0; i < c.n[0]; ++i) {
@@ -682,10 +682,11 @@ void substep(Ctx& c, int s, double dt) {
         n_iter += info.iters_pmhd + info.iters_urad;
         n_solve += 1;
         n_ent += info.entropy;
+        n_cold += info.cold;
         if (info.method == ORC_OK_PMHD) n_pmhd++;
         else if (info.method == ORC_OK_URAD) n_urad++;
         else n_back++;
-        failed[a] = info.method == ORC_BACKUP;
+        failed[a] = info.method == ORC_BACKUP ? 1 : (info.cold ? 2 : 0);
         apply_floors(c.p, G, Pn);
         for (int q = 0; q < NP; ++q) Pnew[(long)q * c.ntot + t] = Pn[q];
       }
@@ -695,10 +696,14 @@ void substep(Ctx& c, int s, double dt) {
   c.counts[3] += n_iter;
   c.counts[4] += n_solve;
   c.counts[5] += n_ent;
+  c.counts[6] += n_cold;
   // Back-up (Sec. 4.11): replace failed zones by the average of their good
   // active face neighbours (all active neighbours if none is good); B keeps
-  // its constrained-transport value.  Every solution was floored above, and
-  // the floors are applied once more after averaging (they are idempotent).
+  // its constrained-transport value.  A zone solved by the cold-MHD equations
+  // has only its u_g replaced by that average, and counts as not good for its
+  // neighbours.  All averages are taken from the solutions before any is
+  // replaced.  Every solution was floored above, and the floors are applied
+  // once more after averaging (they are idempotent).
   std::vector<double> Pavg = Pnew;
   for (int k = 0; k < c.n[2]; ++k)
     for (int j = 0; j < c.n[1]; ++j)
@@ -725,8 +730,10 @@ void substep(Ctx& c, int s, double dt) {
           }
         }
         if (nall == 0) continue;
+        const bool cold = failed[aidx(c, i, j, k)] == 2;
         for (int q = 0; q < NP; ++q) {
           if (q >= B1 && q <= B3) continue;
+          if (cold && q != UU) continue;
           Pavg[(long)q * c.ntot + t] = ngood > 0 ? sum_good[q] / ngood : sum_all[q] / nall;
         }
       }
@@ -789,7 +796,7 @@ void* orc_create(const orc_params* p) {
   long na = (long)c->n[0] * c->n[1] * c->n[2];
   c->status.assign(na, 0);
   c->iters.assign(na, 0);
-  for (int i = 0; i < 6; ++i) c->counts[i] = 0;
+  for (int i = 0; i < 7; ++i) c->counts[i] = 0;
   return c;
 }
 
@@ -842,7 +849,7 @@ double orc_step(void* ctx, double dt) {
   for (int d = 0; d < 3; ++d) std::fill(c.flat[d].begin(), c.flat[d].end(), 0.0);
   std::fill(c.iters.begin(), c.iters.end(), 0);
   std::fill(c.status.begin(), c.status.end(), 0);
-  for (int i = 0; i < 6; ++i) c.counts[i] = 0;
+  for (int i = 0; i < 7; ++i) c.counts[i] = 0;
   for (int s = 0; s < n_passes(c.p.integrator); ++s) substep(c, s, dt);
   return dt;
 }
@@ -859,7 +866,7 @@ void orc_get_iters(void* ctx, int* it) {
 
 void orc_get_counts(void* ctx, long long* out) {
   Ctx& c = *static_cast<Ctx*>(ctx);
-  for (int i = 0; i < 6; ++i) out[i] = c.counts[i];
+  for (int i = 0; i < 7; ++i) out[i] = c.counts[i];
 }
 
 void orc_compute_fluxes(void* ctx, int dir, double* Fout) {
@@ -953,6 +960,12 @@ int orc_radiation_subdominant(const orc_params* p, const double* x, const double
   Geom G;
   geom_at(*p, x[1], x[2], x[3], G);
   return radiation_subdominant(G, Ustar, Ps) ? 1 : 0;
+}
+
+int orc_cold_allowed(const orc_params* p, const double* x, const double* Ustar, const double* Ps) {
+  Geom G;
+  geom_at(*p, x[1], x[2], x[3], G);
+  return cold_allowed(G, Ustar, Ps) ? 1 : 0;
 }
 
 void orc_implicit_zone(const orc_params* p, const double* x, const double* Ustar, const double* Sstar,

@@ -27,6 +27,7 @@ struct Sys {
   double h;         // b_s dt
   bool entropy;     // solve the entropy equation in place of the gas energy row
   double Sstar;     // explicit S u^t (entropy density times u^t)
+  bool cold;        // cold MHD: u_g held, momentum rows only (Sec. 4.11)
 };
 
 struct Res {
@@ -163,6 +164,17 @@ void pmhd_res(const Sys& s, const double x[4], Res& r) {
     }
     r.eT = 0.25 * sT;
     r.eI = 0.25 * sI;
+  }
+  if (s.cold) {
+    // cold MHD (Sec. 4.8, 4.11): energy and entropy errors are ignored, the
+    // errors average the three momentum rows
+    double sT = 0.0, sI = 0.0;
+    for (int k = 1; k < 4; ++k) {
+      sT += std::max(r.eg[k], r.er[k]);
+      sI += r.eg[k];
+    }
+    r.eT = sT / 3.0;
+    r.eI = sI / 3.0;
   }
   std::memcpy(r.P, P, sizeof(P));
   r.ok = std::isfinite(r.eT);
@@ -310,7 +322,8 @@ bool stalled(History& hs, int k) {
 // PMHD Newton (Sec. 4.9-4.10): undamped, one-sided FD Jacobian (the paper
 // takes two-sided differences for PMHD only in its staged scheme, which is not
 // used here) with a normalised offset of 1e-8 (1e-10 once e_I < 1e-9),
-// u_g < 0 reset to |u_g|/2.
+// u_g < 0 reset to |u_g|/2.  The cold-MHD system iterates the three momentum
+// unknowns only (the reduced 3D method of Sec. 4.9): u_g keeps its guess.
 int newton_pmhd(const Sys& s, const double x0[4], Res& best) {
   const orc_params& p = *s.p;
   const Geom& G = *s.G;
@@ -338,6 +351,10 @@ int newton_pmhd(const Sys& s, const double x0[4], Res& best) {
     double umag = std::max(1.0, std::sqrt(usq));
     double J[4][4];
     for (int j = 0; j < 4; ++j) {
+      if (s.cold && j == 0) {
+        for (int i = 0; i < 4; ++i) J[i][0] = i == 0 ? 1.0 : 0.0;
+        continue;
+      }
       double dj = (j == 0) ? eps * std::fabs(x[0]) : eps * umag / std::sqrt(G.gcov[j][j]);
       double xp[4];
       for (int i = 0; i < 4; ++i) xp[i] = x[i];
@@ -347,6 +364,11 @@ int newton_pmhd(const Sys& s, const double x0[4], Res& best) {
       for (int i = 0; i < 4; ++i) J[i][j] = (rp.Eg[i] - r.Eg[i]) / dj;
     }
     double dx[4], E[4] = {r.Eg[0], r.Eg[1], r.Eg[2], r.Eg[3]};
+    if (s.cold) {
+      // the 3x3 momentum block: the u_g row and column become the identity
+      for (int j = 1; j < 4; ++j) J[0][j] = 0.0;
+      E[0] = 0.0;
+    }
     if (!solve4(J, E, dx)) break;
     double xn[4];
     for (int i = 0; i < 4; ++i) xn[i] = x[i] - dx[i];
@@ -539,6 +561,7 @@ void build_sys(const orc_params& p, const Geom& G, const double* Ustar, double h
   s.G = &G;
   s.entropy = false;
   s.Sstar = 0.0;
+  s.cold = false;
   double gd = G.gdet;
   s.Dlab = Ustar[0] / gd;
   for (int k = 0; k < 4; ++k) s.Tstar[k] = Ustar[1 + k] / gd;
@@ -602,6 +625,31 @@ bool radiation_subdominant(const Geom& G, const double* Ustar, const double* Ps)
   return Ehat < tiny * Ps[UU];
 }
 
+// Sec. 4.11: the cold-MHD equations are tried only for a cold, momentum-
+// dominated zone: u_g < 0.1 rho0 u~^i u~_i (guess primitives), and for both
+// the gas t^t_mu = T^t_mu + rho0 u^t delta^t_mu and the radiation R^t_mu of
+// U*, the time part of the covector's square, |t_t t^t| with
+// t^t = g^{t mu} t_mu, below 0.1 of its spatial part |sum_i t_i t^i|.
+bool cold_allowed(const Geom& G, const double* Ustar, const double* Ps) {
+  double usq = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) usq += G.gcov[i + 1][j + 1] * Ps[U1 + i] * Ps[U1 + j];
+  if (!(Ps[UU] < 0.1 * Ps[RHO] * usq)) return false;
+  for (int w = 0; w < 2; ++w) {
+    const double* c = Ustar + (w == 0 ? UU : ER);
+    double t[4], tup[4];
+    for (int m = 0; m < 4; ++m) t[m] = c[m] / G.gdet;
+    for (int m = 0; m < 4; ++m) {
+      tup[m] = 0.0;
+      for (int n = 0; n < 4; ++n) tup[m] += G.gcon[m][n] * t[n];
+    }
+    double at = std::fabs(t[0] * tup[0]);
+    double as = std::fabs(t[1] * tup[1] + t[2] * tup[2] + t[3] * tup[3]);
+    if (!(at < 0.1 * as)) return false;
+  }
+  return true;
+}
+
 // Final primitives of a solve: the best iterate (B from U*), its radiation
 // re-inverted with the BASIC limiter if the TYPE2 branch saw a negative
 // energy; e_T > 1e-7 (or no finite iterate) is no solution: the back-up.
@@ -629,6 +677,25 @@ void finish_solution(const orc_params& p, const Geom& G, const Sys& s, const Res
   info->method = (best.eT > 1e-7) ? ORC_BACKUP : method;
 }
 
+// The cold-MHD back-up (Sec. 4.11): when cold_allowed, the PMHD method on
+// the three momentum equations alone, u_g held at the guess x0's value; the
+// gas and radiation energy equations are dropped, the radiation still takes
+// total energy-momentum conservation.  Accepted at e_T <= 1e-7 (a retry
+// method's solution, info->cold = 1); returns false otherwise.
+bool try_cold(const orc_params& p, const Geom& G, const Sys& s, const double* Ustar, const double* Ps,
+              const double x0[4], double* Pout, orc_implicit_info* info) {
+  if (!cold_allowed(G, Ustar, Ps)) return false;
+  Sys sc = s;
+  sc.entropy = false;
+  sc.cold = true;
+  Res bc;
+  info->iters_urad += newton_pmhd(sc, x0, bc);
+  if (!(bc.ok && bc.eT <= 1e-7)) return false;
+  finish_solution(p, G, sc, bc, Ps, Pout, info, ORC_OK_URAD);
+  info->cold = 1;
+  return true;
+}
+
 // Method sequence (Sec. 4.10-4.11): PMHD first, guessed from P_s or, where the
 // cell is optically thin (tau < 2/3), from a gas inversion of U*; URAD if PMHD
 // leaves e_T > 1e-9; PRAD if both do; the lowest-error solution is kept.  With
@@ -640,11 +707,15 @@ void finish_solution(const orc_params& p, const Geom& G, const Sys& s, const Res
 // for the neighbour-average back-up.  A solution that hit the TYPE2
 // negative-energy branch has its radiation re-inverted with the BASIC
 // limiter.  With implicit_eq = 1 every zone solves the entropy equation.
+// When neither the energy nor the entropy equation gives a solution, a cold,
+// momentum-dominated zone (cold_allowed) tries the cold-MHD equations before
+// the back-up; the grid step then replaces its u_g by the neighbour average.
 void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, const double* Sstar,
                    const double* Ps, double h, double* Pout, orc_implicit_info* info, bool subdominant) {
   Sys s;
   build_sys(p, G, Ustar, h, s);
   info->entropy = 0;
+  info->cold = 0;
   double x0[4] = {Ps[UU], Ps[U1], Ps[U2], Ps[U3]};
   double kabs, ksca;
   opacity(p, Ps[RHO], Ps[UU], &kabs, &ksca);
@@ -670,6 +741,7 @@ void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, cons
     se.Sstar = *Sstar / G.gdet;
     info->iters_pmhd = newton_pmhd(se, x0, best);
     info->iters_urad = 0;
+    if (!(best.ok && best.eT <= 1e-7) && try_cold(p, G, s, Ustar, Ps, x0, Pout, info)) return;
     finish_solution(p, G, se, best, Ps, Pout, info, ORC_OK_PMHD);
     info->entropy = best.ok && best.eT <= 1e-7;
     return;
@@ -739,6 +811,7 @@ void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, cons
       return;
     }
   }
+  if (!(best.ok && best.eT <= 1e-7) && try_cold(p, G, s, Ustar, Ps, x0, Pout, info)) return;
   finish_solution(p, G, s, best, Ps, Pout, info, method);
 }
 

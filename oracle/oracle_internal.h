@@ -44,6 +44,7 @@ int gas_invert(const orc_params& p, const Geom& G, const double* U, const double
 
 // Implicit four-force solve of one zone (Sec. 4.7-4.11).
 bool radiation_subdominant(const Geom& G, const double* Ustar, const double* Ps);
+bool cold_allowed(const Geom& G, const double* Ustar, const double* Ps);
 void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, const double* Sstar,
                    const double* Ps,
                    double h, double* Pout, orc_implicit_info* info, bool subdominant);

@@ -75,6 +75,12 @@ __device__ __forceinline__ long long zone_of(const BoxGeo& bx, int i, int j, int
   return ((long long)k * bx.n[1] + j) * bx.n[0] + i;
 }
 
+// Sets *flag when any of the n method records equals m.
+static __global__ void ka_find_meth(const unsigned char* __restrict__ meth, long long n, unsigned char m, int* flag) {
+  for (long long z = HR_TID; z < n; z += HR_STRIDE)
+    if (meth[z] == m) *flag = 1;
+}
+
 // ------------------------------------------------------------ back-up (T)
 // A back-up zone's non-B primitives are the average of its good neighbours'
 // solutions: its cotangent moves to those neighbours.

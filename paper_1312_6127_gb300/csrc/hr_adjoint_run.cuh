@@ -56,9 +56,16 @@ int Run<MET>::adjoint(harmrad_ctx* c, const double* gPout, double* gPin, double*
   HR_ACHECK(cudaMemsetAsync(a.carry, 0, 6 * (size_t)nt * sizeof(double), st));
   HR_ACHECK(cudaMemsetAsync(a.gk, 0, sizeof(double), st));
   HR_ACHECK(cudaMemsetAsync(a.gSn, 0, (size_t)na * sizeof(double), st));
+  // a zone solved by the cold-MHD equations (its u_g the neighbours'
+  // average) has no adjoint here: the step is refused
+  HR_ACHECK(cudaMemsetAsync(c->flag, 0, sizeof(int), st));
+  ka_find_meth<<<G(3 * na), 128, 0, st>>>(a.meth, 3 * na, METH_COLD, c->flag);
   double dt = 0.0;
+  int cold = 0;
   HR_ACHECK(cudaMemcpyAsync(&dt, c->dt, sizeof(double), cudaMemcpyDeviceToHost, st));
+  HR_ACHECK(cudaMemcpyAsync(&cold, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
   HR_ACHECK(cudaStreamSynchronize(st));
+  if (cold) return HARMRAD_E_ARG;
   const double* K = c->K;
   double* aux = (double*)c->aux;
   double* Pg = c->P;

@@ -699,6 +699,7 @@ int harmrad_get_stats(harmrad_ctx* c, harmrad_stats* s) {
   s->zone_stages = (long long)h[hr::ST_SOLVES];
   s->newton_iters = (long long)h[hr::ST_ITERS];
   s->entropy_ok = (long long)h[hr::ST_ENTROPY];
+  s->cold_ok = (long long)h[hr::ST_COLD];
   s->kernel_launches = c->launches_per_step;
   s->graph = c->use_graph ? 1 : 0;
   return s->backup > 0 ? HARMRAD_W_BACKUP_USED : HARMRAD_OK;
@@ -775,9 +776,9 @@ int harmrad_zone_physics(const harmrad_params* prm, int n, const double* x, cons
   return HARMRAD_OK;
 }
 
-int harmrad_zone_implicit(const harmrad_params* prm, int n, const double* x, const double* Us,
-                          const double* Ps, const double* h, double* Pout, double* eT, int* iters,
-                          unsigned char* method, void* stream) {
+static int zone_implicit_impl(const harmrad_params* prm, int n, const double* x, const double* Us,
+                              const double* Ss, const double* Ps, const double* h, double* Pout, double* eT,
+                              int* iters, unsigned char* method, void* stream) {
   if (!prm || n < 0 || (n > 0 && (!x || !Us || !Ps || !h || !Pout))) return HARMRAD_E_ARG;
   DevParams dp;
   BoxGeo bg;
@@ -791,11 +792,23 @@ int harmrad_zone_implicit(const harmrad_params* prm, int n, const double* x, con
   HR_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   cudaStream_t st = (cudaStream_t)stream;
   int r = dp.metric == 1
-              ? hr::Run<hr::KS>::zone_implicit(dp, bg, n, x, Us, Ps, h, Pout, eT, iters, method, st, sms)
-              : hr::Run<hr::MINK>::zone_implicit(dp, bg, n, x, Us, Ps, h, Pout, eT, iters, method, st, sms);
+              ? hr::Run<hr::KS>::zone_implicit(dp, bg, n, x, Us, Ss, Ps, h, Pout, eT, iters, method, st, sms)
+              : hr::Run<hr::MINK>::zone_implicit(dp, bg, n, x, Us, Ss, Ps, h, Pout, eT, iters, method, st, sms);
   if (r < 0) return r;
   HR_CHECK(cudaStreamSynchronize(st));
   return HARMRAD_OK;
+}
+
+int harmrad_zone_implicit(const harmrad_params* prm, int n, const double* x, const double* Us,
+                          const double* Ps, const double* h, double* Pout, double* eT, int* iters,
+                          unsigned char* method, void* stream) {
+  return zone_implicit_impl(prm, n, x, Us, nullptr, Ps, h, Pout, eT, iters, method, stream);
+}
+
+int harmrad_zone_implicit_full(const harmrad_params* prm, int n, const double* x, const double* Us,
+                               const double* Sstar, const double* Ps, const double* h, double* Pout,
+                               double* eT, int* iters, unsigned char* method, void* stream) {
+  return zone_implicit_impl(prm, n, x, Us, Sstar, Ps, h, Pout, eT, iters, method, stream);
 }
 
 int harmrad_adjoint_enable(harmrad_ctx* c, int on) {

@@ -4,10 +4,12 @@
 
 namespace hr {
 
-enum { ST_PMHD = 0, ST_URAD = 1, ST_BACKUP = 2, ST_SOLVES = 3, ST_ITERS = 4, ST_ENTROPY = 5 };
-// record code of a zone solved by the entropy equation (adjoint records only;
-// its status byte is ST_URAD, a retry method)
+enum { ST_PMHD = 0, ST_URAD = 1, ST_BACKUP = 2, ST_SOLVES = 3, ST_ITERS = 4, ST_ENTROPY = 5, ST_COLD = 6 };
+// record codes of a zone solved by the entropy equation or by the cold-MHD
+// equations (adjoint records only; their status byte is ST_URAD, a retry
+// method)
 constexpr unsigned char METH_ENTROPY = 3;
+constexpr unsigned char METH_COLD = 4;
 constexpr int QSTRIDE = 19;
 
 // Coefficients of one sub-step of an IMEX scheme (Sec. 4.1, Eqs. IMEX2,

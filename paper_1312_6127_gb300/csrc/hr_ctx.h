@@ -112,8 +112,9 @@ struct Run {
                           const double* P, double* U, double* SM, double* F, double* speeds,
                           cudaStream_t st, int sms);
   static int zone_implicit(const DevParams& dp, const BoxGeo& bg, int n, const double* x,
-                           const double* Us, const double* Ps, const double* h, double* Pout,
-                           double* eT, int* iters, unsigned char* method, cudaStream_t st, int sms);
+                           const double* Us, const double* Ss, const double* Ps, const double* h,
+                           double* Pout, double* eT, int* iters, unsigned char* method, cudaStream_t st,
+                           int sms);
 };
 
 }  // namespace hr

@@ -42,6 +42,7 @@ struct ImpSysT {
   T sgk[3]; // sqrt(gamma^{kk}) of the ZAMO slice
   bool entropy;  // the entropy equation replaces the gas energy row (Eq. source6)
   T Sstar;       // explicit S u^t (the conserved entropy over sqrt(-g))
+  bool cold;     // cold MHD (Sec. 4.11): u_g held, the momentum rows only
 };
 template <int MET>
 using ImpSys = ImpSysT<MET, double>;
@@ -61,6 +62,7 @@ template <typename T = double>
 struct ImpStateT {
   T rho, ug, Pr[4];
   T Rt_pre[4];
+  int negE;  // the TYPE2 inversion saw E_rad <= 0
 };
 using ImpState = ImpStateT<double>;
 
@@ -113,6 +115,17 @@ __device__ __forceinline__ void normalise(const ImpSysT<MET, T>& s, const T Tc[4
   if (eS >= 0.0) {  // entropy row in place of the gas energy row; the radiation energy row drops
     eg[0] = eS;
     er[0] = T(0.0);
+  }
+  if (s.cold) {  // cold MHD: energy and entropy ignored, the mean of the momentum rows
+    T cT = T(0.0), cI = T(0.0);
+#pragma unroll
+    for (int k = 1; k < 4; ++k) {
+      cT += fmax(eg[k], er[k]);
+      cI += eg[k];
+    }
+    r.eT = cT / 3.0;
+    r.eI = cI / 3.0;
+    return;
   }
   T sT = T(0.0), sI = T(0.0);
 #pragma unroll
@@ -187,6 +200,7 @@ __device__ __forceinline__ void pmhd_res(const DevParams& p, const ImpSysT<MET, 
     r.ok = true;
   }
   if (st) {
+    st->negE = r.negE;
     st->rho = rho;
     st->ug = x[0];
 #pragma unroll
@@ -341,6 +355,14 @@ __device__ __forceinline__ bool pmhd_newton_dx(const DevParams& p, const ImpSys<
   double J[4][4];
   pmhd_jacobian_fd<MET>(p, s, x, r, eps, J);
   double E[4] = {r.Eg[0], r.Eg[1], r.Eg[2], r.Eg[3]};
+  if (s.cold) {  // the 3x3 momentum block; u_g's row and column become the identity
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      J[0][i] = i == 0 ? 1.0 : 0.0;
+      J[i][0] = i == 0 ? 1.0 : 0.0;
+    }
+    E[0] = 0.0;
+  }
   return solve4(J, E, dx);
 }
 
@@ -402,13 +424,13 @@ __device__ __forceinline__ bool newton_pmhd_run(const DevParams& p, const ImpSys
 // residual was finite).
 template <int MET>
 __device__ int newton_pmhd(const DevParams& p, const ImpSys<MET>& s, const double x0[4],
-                           double best_x[4], double* best_eT) {
+                           double best_x[4], double* best_eT, ImpState* best_st = nullptr) {
   double x[4] = {x0[0], x0[1], x0[2], x0[3]};
   Hist hs = {HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, 0};
   *best_eT = HUGE_VAL;
   int steps = 0;
   double eps = 1e-8;
-  int jac32 = s.entropy ? 0 : 1;  // the FP32 tangents differentiate the energy row
+  int jac32 = (s.entropy || s.cold) ? 0 : 1;  // the FP32 tangents differentiate the energy system
   for (int k = 0;; ++k) {
     ImpRes r;
     ImpState ist;
@@ -418,6 +440,7 @@ __device__ int newton_pmhd(const DevParams& p, const ImpSys<MET>& s, const doubl
       *best_eT = r.eT;
 #pragma unroll
       for (int i = 0; i < 4; ++i) best_x[i] = x[i];
+      if (best_st) *best_st = ist;
     }
     if (r.eT < p.newton_tol) break;
     // a step with the FP32 Jacobian that raised e_T: finite differences for
@@ -441,11 +464,13 @@ __device__ int newton_pmhd(const DevParams& p, const ImpSys<MET>& s, const doubl
     ++steps;
     if (tiny) {
       ImpRes rf;
-      pmhd_res<MET>(p, s, x, rf, nullptr, true);
+      ImpState stf;
+      pmhd_res<MET>(p, s, x, rf, best_st ? &stf : nullptr, true);
       if (rf.ok && rf.eT < *best_eT) {
         *best_eT = rf.eT;
 #pragma unroll
         for (int i = 0; i < 4; ++i) best_x[i] = x[i];
+        if (best_st) *best_st = stf;
       }
       break;
     }
@@ -710,6 +735,7 @@ __device__ __forceinline__ void build_sys(const DevParams& p, const Geo<MET, T>&
 #pragma unroll
   for (int k = 1; k < 4; ++k) s.sgk[k - 1] = sqrt(g.Gdd(k) - g.Gt(k) * g.Gt(k) / g.Gtt());
   s.entropy = false;
+  s.cold = false;
   s.Sstar = T(0.0);
   (void)p;
 }

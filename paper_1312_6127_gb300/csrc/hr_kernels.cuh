@@ -926,6 +926,28 @@ __device__ __forceinline__ void apply_floors(const DevParams& p, const Geo<MET, 
 
 // Final primitives of an accepted PMHD iterate: gas from x, B fixed, radiation
 // re-inverted with BASIC if the TYPE2 branch saw a negative energy (Sec. 4.10).
+// Final primitives from the error function's state at x (pmhd_res), without
+// evaluating it again: gas from x, B fixed, radiation re-inverted with BASIC
+// if the TYPE2 branch saw a negative energy (Sec. 4.10).
+template <int MET>
+__device__ __forceinline__ void pmhd_final_state(const DevParams& p, const ImpSys<MET>& s, const double x[4],
+                                                 const ImpState& st, double P[NPR]) {
+  P[RHO] = st.rho;
+  P[UU] = x[0];
+  P[U1] = x[1];
+  P[U2] = x[2];
+  P[U3] = x[3];
+  P[B1] = s.B[0];
+  P[B2] = s.B[1];
+  P[B3] = s.B[2];
+  double Pr[4] = {st.Pr[0], st.Pr[1], st.Pr[2], st.Pr[3]};
+  if (st.negE) rad_invert<MET, double>(p, s.g, st.Rt_pre, 0, Pr);
+  P[ER] = Pr[0];
+  P[UR1] = Pr[1];
+  P[UR2] = Pr[2];
+  P[UR3] = Pr[3];
+}
+
 template <int MET, typename T = double>
 __device__ __forceinline__ void pmhd_final(const DevParams& p, const ImpSysT<MET, T>& s, const T x[4], T P[NPR],
                                            T* Eg = nullptr, unsigned* code = nullptr) {
@@ -1265,14 +1287,17 @@ __device__ __forceinline__ bool pmhd_finish(const DevParams& p, const BoxGeo& bx
                                             double x1, const Geo<MET, double>& g, const ImpSys<MET>& s,
                                             const double Ust[NPR], double h, const double best_x[4],
                                             double beT, int steps, double* P, const Bufs& b, double Sst,
-                                            double acc_tol = 1e-9) {
+                                            double acc_tol = 1e-9, const ImpState* bst = nullptr) {
   const long long zg = bx.aoff + z;
   b.iters[zg] += steps;
   const bool accept = beT >= 0.0 && beT < acc_tol;  // beT < 0: sub-dominant radiation, URAD first
   if (accept) {
     double Pn[NPR];
     unsigned lcode = 0;
-    pmhd_final<MET, double>(p, s, best_x, Pn, nullptr, p.sig ? &lcode : nullptr);
+    if (bst && !p.sig)  // the state the Newton loop kept for its best iterate
+      pmhd_final_state<MET>(p, s, best_x, *bst, Pn);
+    else
+      pmhd_final<MET, double>(p, s, best_x, Pn, nullptr, p.sig ? &lcode : nullptr);
     if (b.psol_rec)
       for (int q = 0; q < NPR; ++q) b.psol_rec[12 * bx.aoff + q * bx.nact + z] = Pn[q];
     unsigned fcode = 0;
@@ -1314,6 +1339,68 @@ __device__ __forceinline__ bool radiation_subdominant(const Geo<MET, double>& g,
   fourvel<MET, double>(g, Ps[UR1], Ps[UR2], Ps[UR3], rc, rv, &gr);
   const double grel = -(rc[0] * uv[0] + rc[1] * uv[1] + rc[2] * uv[2] + rc[3] * uv[3]);
   return Ps[ER] * ((4.0 / 3.0) * grel * grel - 1.0 / 3.0) < tiny * Ps[UU];
+}
+
+// Sec. 4.11: the cold-MHD equations are tried only for a cold, momentum-
+// dominated zone: u_g < 0.1 rho0 u~^i u~_i of the guess primitives, and for
+// the gas t^t_mu = T^t_mu + rho0 u^t delta^t_mu and the radiation R^t_mu of
+// U* alike, |t_t t^t| < 0.1 |sum_i t_i t^i| with t^mu = g^{mu nu} t_nu.
+template <int MET>
+__device__ __forceinline__ bool cold_allowed(const Geo<MET, double>& g, const double Ust[NPR],
+                                             const double Ps[NPR]) {
+  if (!(Ps[UU] < 0.1 * Ps[RHO] * g.sq3(Ps[U1], Ps[U2], Ps[U3]))) return false;
+  const double igd = 1.0 / g.gdet;
+#pragma unroll
+  for (int w = 0; w < 2; ++w) {
+    const int o = w == 0 ? UU : ER;
+    const double t[4] = {Ust[o] * igd, Ust[o + 1] * igd, Ust[o + 2] * igd, Ust[o + 3] * igd};
+    double up[3];
+    g.raise3(t, up);
+    const double at = fabs(t[0] * g.raise_t(t));
+    const double as = fabs(t[1] * up[0] + t[2] * up[1] + t[3] * up[2]);
+    if (!(at < 0.1 * as)) return false;
+  }
+  return true;
+}
+
+// The back-up equations of Sec. 4.11 for a zone that the energy methods left
+// without a solution.  First the entropy equation (Eq. source6) in place of
+// the gas energy equation, where the explicit S* (sqrt(-g) S u^t) is finite
+// and with_entropy; then, for a cold momentum-dominated zone (cold_allowed),
+// the cold-MHD equations: PMHD on the three momentum equations with u_g held
+// at the guess.  Both start from the energy PMHD's guess (P_s, or where
+// tau < 2/3 the gas inversion of U*) and are accepted at e_T <= 1e-7.
+// Returns METH_ENTROPY or METH_COLD with Pn and *eT set, 0 if neither
+// gives a solution; adds the Newton steps to *steps.
+template <int MET>
+__device__ int backup_equations(const DevParams& p, const Geo<MET, double>& g, const ImpSys<MET>& s,
+                                const double Ust[NPR], const double Ps[NPR], double Sst, bool with_entropy,
+                                double tau, double Pn[NPR], double* eT, int* steps) {
+  const bool ent = with_entropy && isfinite(Sst);
+  const bool cold = cold_allowed<MET>(g, Ust, Ps);
+  if (!ent && !cold) return 0;
+  double x0[4] = {Ps[UU], Ps[U1], Ps[U2], Ps[U3]};
+  if (tau < 2.0 / 3.0) {
+    double go[5], T3[3] = {s.Ts[1], s.Ts[2], s.Ts[3]};
+    if (gas_invert<MET>(p, g, s.Dlab, s.Ts[0], T3, s.B, Ps, 1e-9, go) == 0)
+      for (int c = 0; c < 4; ++c) x0[c] = go[1 + c];
+  }
+#pragma unroll 1
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 0 ? !ent : !cold) continue;
+    ImpSys<MET> se = s;
+    se.entropy = pass == 0;
+    se.cold = pass == 1;
+    se.Sstar = pass == 0 ? Sst / g.gdet : 0.0;
+    double bxe[4] = {0.0, 0.0, 0.0, 0.0}, beT = HUGE_VAL;
+    *steps += newton_pmhd<MET>(p, se, x0, bxe, &beT);
+    if (beT <= 1e-7) {
+      pmhd_final<MET>(p, se, bxe, Pn);
+      *eT = beT;
+      return pass == 0 ? METH_ENTROPY : METH_COLD;
+    }
+  }
+  return 0;
 }
 
 // ------------------------------------------------------- update + implicit
@@ -1473,8 +1560,10 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
         warp_add(&b.stats[ST_ENTROPY], accept ? 1u : 0u);
       } else if constexpr (!CONT) {
         double bxn[4] = {0.0, 0.0, 0.0, 0.0}, beT = -1.0;
-        const int steps = subdom ? 0 : newton_pmhd<MET>(p, s, x0, bxn, &beT);
-        accept = pmhd_finish<MET>(p, bx, bi, z, t, x1, g, s, Ust, h, bxn, beT, steps, P, b, Sst);
+        ImpState bst;
+        const int steps = subdom ? 0 : newton_pmhd<MET>(p, s, x0, bxn, &beT, &bst);
+        accept = pmhd_finish<MET>(p, bx, bi, z, t, x1, g, s, Ust, h, bxn, beT, steps, P, b, Sst, 1e-9,
+                                  subdom ? nullptr : &bst);
         done_steps = (unsigned)steps;
       } else {
         // the first `split` iterations here; a zone that needs more
@@ -1625,9 +1714,8 @@ __global__ void __launch_bounds__(128) k_retry(DevParams p, const BoxGeo* __rest
     int steps;
     const double tau = zone_tau<MET>(p, g, bx.dx, Ps, kfield(p, K, t));
     int method;
-    bool by_entropy = false;
     const double Sst = qd[18];
-    if (p.implicit_eq == 1) {  // the entropy solve already failed: back-up
+    if (p.implicit_eq == 1) {  // the entropy solve already failed
       for (int q = 0; q < NPR; ++q) Pn[q] = Ps[q];
       for (int c = 0; c < 3; ++c) Pn[B1 + c] = s.B[c];
       eT = HUGE_VAL;
@@ -1635,29 +1723,12 @@ __global__ void __launch_bounds__(128) k_retry(DevParams p, const BoxGeo* __rest
       method = ST_BACKUP;
     } else {
       method = retry_sequence<MET>(p, g, s, Ps, px, peT, tau, Pn, &eT, &steps);
-      if (method == ST_BACKUP && isfinite(Sst)) {
-        // no energy-based solution: the entropy equation in place of the gas
-        // energy equation (Sec. 4.7, Eq. source6; Sec. 4.11), PMHD iterates
-        // from the energy PMHD's guess (P_s, or where tau < 2/3 the gas
-        // inversion of U*)
-        double x0[4] = {Ps[UU], Ps[U1], Ps[U2], Ps[U3]};
-        if (tau < 2.0 / 3.0) {
-          double go[5], T3[3] = {s.Ts[1], s.Ts[2], s.Ts[3]};
-          if (gas_invert<MET>(p, g, s.Dlab, s.Ts[0], T3, s.B, Ps, 1e-9, go) == 0)
-            for (int c = 0; c < 4; ++c) x0[c] = go[1 + c];
-        }
-        ImpSys<MET> se = s;
-        se.entropy = true;
-        se.Sstar = Sst / g.gdet;
-        double bxe[4] = {0.0, 0.0, 0.0, 0.0}, beT = HUGE_VAL;
-        steps += newton_pmhd<MET>(p, se, x0, bxe, &beT);
-        if (beT <= 1e-7) {
-          pmhd_final<MET>(p, se, bxe, Pn);
-          eT = beT;
-          method = ST_URAD;
-          by_entropy = true;
-        }
-      }
+    }
+    // no energy-based solution: the entropy, then the cold-MHD equations
+    int by = 0;
+    if (method == ST_BACKUP) {
+      by = backup_equations<MET>(p, g, s, Ust, Ps, Sst, p.implicit_eq != 1, tau, Pn, &eT, &steps);
+      if (by) method = ST_URAD;
     }
     b.iters[zg] += steps;
     if (b.psol_rec)
@@ -1668,13 +1739,19 @@ __global__ void __launch_bounds__(128) k_retry(DevParams p, const BoxGeo* __rest
     for (int q = 0; q < NPR; ++q) P[q * bx.ntot + t] = Pn[q];
     unsigned char m = (unsigned char)method;
     if (m > b.status[zg]) b.status[zg] = m;
-    if (b.meth_rec) b.meth_rec[zg] = by_entropy ? METH_ENTROPY : m;
-    if (by_entropy) atomicAdd(&b.stats[ST_ENTROPY], 1ULL);
-    if (method == ST_BACKUP) {
-      b.failed[zg] = 1;
+    if (b.meth_rec) b.meth_rec[zg] = by ? (unsigned char)by : m;
+    if (by == METH_ENTROPY) atomicAdd(&b.stats[ST_ENTROPY], 1ULL);
+    if (by == METH_COLD) atomicAdd(&b.stats[ST_COLD], 1ULL);
+    if (method == ST_BACKUP || by == METH_COLD) {
+      // the back-up average: all primitives but B, or u_g alone for a
+      // cold-MHD solution (Sec. 4.11); either counts as not good for its
+      // neighbours' averages
+      b.failed[zg] = method == ST_BACKUP ? 1 : 2;
       int slot = atomicAdd(&b.qcount[1], 1);
       b.fzone[slot] = (int)z;
       b.fbox[slot] = bi;
+    }
+    if (method == ST_BACKUP) {
       atomicAdd(&b.stats[ST_BACKUP], 1ULL);
     } else if (method == ST_URAD) {
       atomicAdd(&b.stats[ST_URAD], 1ULL);
@@ -1687,7 +1764,9 @@ __global__ void __launch_bounds__(128) k_retry(DevParams p, const BoxGeo* __rest
 
 // ------------------------------------------------------------- back-up
 // Average of the good active face neighbours (all active neighbours if none
-// is good); B keeps its constrained-transport value (Sec. 4.11).
+// is good); B keeps its constrained-transport value, and a zone solved by the
+// cold-MHD equations takes the average for u_g alone (Sec. 4.11).  All
+// averages are formed before any is written back (k_backup_apply).
 static __global__ void k_backup_avg(DevParams p, const BoxGeo* __restrict__ boxes, Bufs b) {
   const int nf = b.qcount[1];
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nf; e += gridDim.x * blockDim.x) {
@@ -1723,9 +1802,10 @@ static __global__ void k_backup_avg(DevParams p, const BoxGeo* __restrict__ boxe
     }
     long long t = cell_index(bx, ii[0], ii[1], ii[2]);
     if (p.sig) sig_put(p, bx.coff + t, 61, (unsigned)ng << 4 | (unsigned)na);
+    const bool cold = b.failed[bx.aoff + z] == 2;
     for (int q = 0; q < NPR; ++q) {
       double v = P[q * bx.ntot + t];
-      if (na > 0 && !(q >= B1 && q <= B3)) v = ng > 0 ? sg[q] / ng : sa[q] / na;
+      if (na > 0 && !(q >= B1 && q <= B3) && (!cold || q == UU)) v = ng > 0 ? sg[q] / ng : sa[q] / na;
       b.ftmp[(long long)e * NPR + q] = v;
     }
   }

@@ -304,8 +304,8 @@ __global__ void k_zone_physics(DevParams p, BoxGeo bg, int n, const double* __re
 template <int MET>
 __global__ void k_zone_implicit(DevParams p, BoxGeo bg, int n, const double* __restrict__ x,
                                 const double* __restrict__ Us, const double* __restrict__ Ps,
-                                const double* __restrict__ hh, double* Pout, double* eTo, int* itso,
-                                unsigned char* meth) {
+                                const double* __restrict__ hh, const double* __restrict__ Sst, double* Pout,
+                                double* eTo, int* itso, unsigned char* meth) {
   for (int z = blockIdx.x * blockDim.x + threadIdx.x; z < n; z += gridDim.x * blockDim.x) {
     double x1 = x[4 * z + 1], x2 = x[4 * z + 2];
     Geo<MET, double> g = make_geo<MET, double>(p, x1, x2);
@@ -341,8 +341,13 @@ __global__ void k_zone_implicit(DevParams p, BoxGeo bg, int n, const double* __r
       pmhd_final<MET>(p, s, bx, Pn);
     } else {
       int rs;
-      method = retry_sequence<MET>(p, g, s, P0, bx, beT, zone_tau<MET>(p, g, bg.dx, P0, 1.0), Pn, &eT, &rs);
+      const double tau = zone_tau<MET>(p, g, bg.dx, P0, 1.0);
+      method = retry_sequence<MET>(p, g, s, P0, bx, beT, tau, Pn, &eT, &rs);
       steps += rs;
+      if (method == ST_BACKUP) {  // the entropy (S* given), then the cold-MHD equations
+        const int by = backup_equations<MET>(p, g, s, Ust, P0, Sst ? Sst[z] : NAN, true, tau, Pn, &eT, &steps);
+        if (by) method = by;
+      }
     }
     for (int q = 0; q < NPR; ++q) Pout[NPR * z + q] = Pn[q];
     if (eTo) eTo[z] = eT;
@@ -372,9 +377,10 @@ int Run<MET>::zone_physics(const DevParams& dp, const BoxGeo& bg, int n, const d
 }
 template <int MET>
 int Run<MET>::zone_implicit(const DevParams& dp, const BoxGeo& bg, int n, const double* x,
-                            const double* Us, const double* Ps, const double* h, double* Pout,
-                            double* eT, int* iters, unsigned char* method, cudaStream_t st, int sms) {
-  k_zone_implicit<MET><<<grid_for(n, sms, 128), 128, 0, st>>>(dp, bg, n, x, Us, Ps, h, Pout, eT, iters,
+                            const double* Us, const double* Ss, const double* Ps, const double* h,
+                            double* Pout, double* eT, int* iters, unsigned char* method, cudaStream_t st,
+                            int sms) {
+  k_zone_implicit<MET><<<grid_for(n, sms, 128), 128, 0, st>>>(dp, bg, n, x, Us, Ps, h, Ss, Pout, eT, iters,
                                                               method);
   return cudaGetLastError() == cudaSuccess ? 1 : HARMRAD_E_CUDA;
 }

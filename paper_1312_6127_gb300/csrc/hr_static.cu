@@ -177,8 +177,12 @@ __global__ void k_zi_urad(hr::DevParams p, hr::BoxGeo bg, const double* __restri
     const double beT = r[4];
     double Pn[NPR], eT;
     int steps;
-    const int method =
-        retry_sequence<MET>(p, g, s, P0, bx, beT, zone_tau<MET>(p, g, bg.dx, P0, 1.0), Pn, &eT, &steps);
+    const double tau = zone_tau<MET>(p, g, bg.dx, P0, 1.0);
+    int method = retry_sequence<MET>(p, g, s, P0, bx, beT, tau, Pn, &eT, &steps);
+    if (method == ST_BACKUP) {  // the cold-MHD equations (no explicit entropy here)
+      const int by = backup_equations<MET>(p, g, s, Us + NPR * (size_t)z, P0, NAN, false, tau, Pn, &eT, &steps);
+      if (by) method = by;
+    }
     for (int q = 0; q < NPR; ++q) Pout[NPR * z + q] = Pn[q];
     if (eTo) eTo[z] = eT;
     if (itso) itso[z] += steps;

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libharmrad.so")
 NPRIM = 12
 
 OK, W_BACKUP_USED = 0, 1
-ZONE_PMHD, ZONE_URAD, ZONE_BACKUP = 0, 1, 2
+ZONE_PMHD, ZONE_URAD, ZONE_BACKUP, ZONE_ENTROPY, ZONE_COLD = 0, 1, 2, 3, 4
 PREC_FP64, PREC_SPLIT = 0, 1
 OPAC_CONST, OPAC_KRAMERS, OPAC_FIELD = 0, 1, 2
 INT_RK3, INT_IMEX2, INT_IMEX2B, INT_IMEX3 = 0, 1, 2, 3
@@ -26,7 +26,8 @@ EXPORTS = [
     "harmrad_set_prims_ghosts", "harmrad_get_prims",
     "harmrad_cfl_dt", "harmrad_step", "harmrad_step_host", "harmrad_get_stats",
     "harmrad_get_status", "harmrad_get_iters", "harmrad_compute_fluxes",
-    "harmrad_zone_physics", "harmrad_zone_implicit", "harmrad_zone_implicit_static",
+    "harmrad_zone_physics", "harmrad_zone_implicit", "harmrad_zone_implicit_full",
+    "harmrad_zone_implicit_static",
     "harmrad_profile_step", "harmrad_autotune", "harmrad_get_tuning", "harmrad_set_tuning",
     "harmrad_adjoint_enable", "harmrad_step_adjoint", "harmrad_adjoint_set_input",
     "harmrad_branch_signature", "harmrad_get_branch_signature",
@@ -85,6 +86,7 @@ class Stats(ctypes.Structure):
         ("kernel_launches", ctypes.c_int),
         ("graph", ctypes.c_int),
         ("entropy_ok", ctypes.c_longlong),
+        ("cold_ok", ctypes.c_longlong),
     ]
 
 
@@ -138,6 +140,7 @@ def load(path=LIB_PATH):
     L.harmrad_compute_fluxes.argtypes = [vp, ip, vp]
     L.harmrad_zone_physics.argtypes = [pp, ip, vp, vp, vp, vp, vp, vp, vp]
     L.harmrad_zone_implicit.argtypes = [pp, ip, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.harmrad_zone_implicit_full.argtypes = [pp, ip, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.harmrad_zone_implicit_static.argtypes = [pp, ip, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.harmrad_profile_step.argtypes = [vp, ctypes.c_double, ctypes.POINTER(KernelTimes)]
     L.harmrad_adjoint_enable.argtypes = [vp, ip]
@@ -462,8 +465,10 @@ def zone_physics(cfg, x, P):
     return U.cpu().numpy(), SM.cpu().numpy(), F.cpu().numpy(), S.cpu().numpy()
 
 
-def zone_implicit(cfg, x, Ustar, Ps, h):
-    """Implicit four-force solve of n independent zones (numpy in, numpy out)."""
+def zone_implicit(cfg, x, Ustar, Ps, h, Sstar=None):
+    """Implicit four-force solve of n independent zones (numpy in, numpy out).
+    Sstar (n values of sqrt(-g) S u^t after the explicit update) adds the
+    entropy equation to the back-up equations (harmrad_zone_implicit_full)."""
     import torch
     n = len(x)
     xd, Ud, Pd, hd = _dev(x), _dev(Ustar), _dev(Ps), _dev(np.broadcast_to(h, (n,)))
@@ -473,6 +478,12 @@ def zone_implicit(cfg, x, Ustar, Ps, h):
     meth = torch.empty(n, dtype=torch.uint8, device="cuda")
     p = make_params(cfg)
     vp = lambda t: ctypes.c_void_p(t.data_ptr())
-    _check(load().harmrad_zone_implicit(ctypes.byref(p), n, vp(xd), vp(Ud), vp(Pd), vp(hd), vp(Pout),
-                                        vp(eT), vp(it), vp(meth), _stream_ptr(None)), "zone_implicit")
+    if Sstar is None:
+        _check(load().harmrad_zone_implicit(ctypes.byref(p), n, vp(xd), vp(Ud), vp(Pd), vp(hd), vp(Pout),
+                                            vp(eT), vp(it), vp(meth), _stream_ptr(None)), "zone_implicit")
+    else:
+        Sd = _dev(np.broadcast_to(Sstar, (n,)))
+        _check(load().harmrad_zone_implicit_full(ctypes.byref(p), n, vp(xd), vp(Ud), vp(Sd), vp(Pd), vp(hd),
+                                                 vp(Pout), vp(eT), vp(it), vp(meth), _stream_ptr(None)),
+               "zone_implicit_full")
     return Pout.cpu().numpy(), eT.cpu().numpy(), it.cpu().numpy(), meth.cpu().numpy()

@@ -10,7 +10,7 @@ import pytest
 from oracle import oracle as O
 from paper_1312_6127_gb300 import harmrad as H
 from paper_1312_6127_gb300 import workloads as W
-from tests.parity_metrics import point_errors, zone_errors
+from tests.parity_metrics import flux_errors, point_errors, zone_errors
 from tests.test_oracle_atmosphere import STEPS, measures
 
 pytestmark = pytest.mark.gpu
@@ -42,6 +42,44 @@ def test_atmosphere_matches_oracle(f):
     print("f = %.1f, 10 steps: per-zone error, gas %.2e, radiation (conserved) %.2e, radiation primitives %.2e"
           % (f, e[:8].max(), er, e[8:].max()))
     assert e[:8].max() < 1e-8 and er < 1e-8
+
+
+@pytest.mark.parametrize("f", [0.1, 1.0])
+def test_atmosphere_first_step_matches_oracle(f):
+    """The pieces of the first step separately: the point physics (U, the
+    geometric source, the radial flux, the signal speeds) at every cell
+    centre, the radial face fluxes of the initial state, then the state after
+    one step, each against the oracle."""
+    cfg, P, info = W.static_atmosphere(f, flux_ratio=0.99)
+    n1 = cfg["n"][0]
+    xs = np.array([[0.0, cfg["x0"][0] + (i + 0.5) * cfg["dx"][0], 0.5, 0.5] for i in range(-4, n1 + 4)])
+    Pc = P[:, 0, 0, :].T.copy()
+    U, SM, F, S = H.zone_physics(cfg, xs, Pc)
+    p = O.make_params(cfg)
+    eu = esm = ef = es = 0.0
+    for z in range(len(xs)):
+        Uo, SMo = O.prim_to_cons(p, xs[z], Pc[z])
+        Fo, So = O.flux(p, xs[z], 1, Pc[z])
+        eu = max(eu, np.abs(U[z] - Uo).max() / max(np.abs(Uo).max(), 1e-300))
+        esm = max(esm, np.abs(SM[z] - SMo).max() / max(np.abs(SMo).max(), 1e-300))
+        ef = max(ef, np.abs(F[z, 0] - Fo).max() / max(np.abs(Fo).max(), 1e-300))
+        es = max(es, np.abs(S[z, 0] - So).max())
+    g = H.Grid(cfg)
+    g.set_prims_ghosts(P)
+    o = O.Oracle(cfg)
+    o.set_prims_with_ghosts(P)
+    Fo1 = o.fluxes(1)
+    eF = flux_errors(g.fluxes(1), Fo1)
+    dt = o.cfl_dt()
+    o.step(dt)
+    g.step(dt)
+    e = zone_errors(cfg, g.get_prims(), o.get_prims())
+    worst = e.reshape(12, -1).max(axis=1)
+    print("f = %.1f: point U %.1e SM %.1e F %.1e speeds %.1e; face fluxes %s; one step %s (worst zone %d)"
+          % (f, eu, esm, ef, es, ["%.0e" % v for v in eF.reshape(12, -1).max(axis=1)],
+             ["%.0e" % v for v in worst], int(np.argmax(e.max(axis=0)))))
+    assert eF.max() < 1e-12
+    assert e.max() < 1e-10
 
 
 @pytest.mark.parametrize("f", [0.1, 0.5, 1.0])
