@@ -95,11 +95,32 @@ extern "C" {
  * ENTROPY: the entropy equation in every zone (PMHD iterates; RK3 only), which
  * conserves the total entropy to round-off where the gas and radiation do not
  * exchange energy.  The entropy S u^t is carried as a 13th conserved quantity
- * with its own face fluxes (RK3 contexts).  The point-wise entries
- * (harmrad_zone_implicit, harmrad_zone_implicit_static) solve the energy
- * equations only. */
+ * with its own face fluxes (RK3 contexts).  A zone that neither the energy
+ * nor the entropy equation solves tries the cold-MHD equations (Sec. 4.11)
+ * when it is cold and momentum-dominated.  The point-wise entries
+ * harmrad_zone_implicit and harmrad_zone_implicit_static have no explicit
+ * entropy: the energy methods, then the cold-MHD equations;
+ * harmrad_zone_implicit_full takes the entropy too. */
 #define HARMRAD_EQ_ENERGY 0
 #define HARMRAD_EQ_ENTROPY 1
+
+/* Magnetic field transport (Sec. 4.2 steps viii-x).
+ * FLUXCT: cell-centred B; the edge EMFs are the averages of the four face
+ * fluxes of B around each edge and replace them (flux-CT, Toth 2000), which
+ * keeps the corner-centred divergence of B at its initial value.
+ * UCT: the paper's staggered field: sqrt(-g) B^d lives on the d-faces and is
+ * advanced by the curl of edge EMFs from a 4-state upwind (HLL, or LAXF)
+ * solution (Del Zanna et al. 2007): B^d of the faces interpolated to the edge
+ * across d (MC-limited linear), the 3-velocities v^i = u^i/u^t of the four
+ * cells around the edge extrapolated to it with MC-limited slopes, and signal
+ * speeds averaged from the gas speeds of the two faces beside the edge.  The
+ * face divergence sum_d (Bf_d(+) - Bf_d(-))/dx_d of every zone keeps its
+ * initial value to round-off.  A zone's cell-centred B is the average of its
+ * two faces' sqrt(-g) B^d over the centre's sqrt(-g).  harmrad_set_prims
+ * initialises each face from the two cells beside it (and then the centres
+ * from the faces); harmrad_set_face_fields sets the faces directly. */
+#define HARMRAD_EMF_FLUXCT 0
+#define HARMRAD_EMF_UCT 1
 
 #define HARMRAD_INT_RK3 0
 #define HARMRAD_INT_IMEX2 1
@@ -132,6 +153,7 @@ typedef struct harmrad_params {
   int precision;       /* HARMRAD_PREC_* */
   int integrator;      /* HARMRAD_INT_* */
   int implicit_eq;     /* HARMRAD_EQ_*: which gas equation the implicit solve uses */
+  int emf;             /* HARMRAD_EMF_*: magnetic field transport */
 } harmrad_params;
 
 /* Per-zone outcome codes written by harmrad_get_status (worst over the
@@ -199,6 +221,17 @@ int harmrad_set_prims(harmrad_ctx* ctx, const double* P, int on_device);
  * HARMRAD_E_ARG for a batch; HARMRAD_E_NAN_INPUT as for harmrad_set_prims,
  * over every cell. */
 int harmrad_set_prims_ghosts(harmrad_ctx* ctx, const double* P, int on_device);
+
+/* Staggered field (HARMRAD_EMF_UCT contexts of one grid; HARMRAD_E_ARG
+ * otherwise): sqrt(-g) B^d on the d-faces, three arrays one after another,
+ * direction d of shape [n3'][n2'][n1'] (FP64) with n_d' = n_d + 1 faces along
+ * d when n_d > 1 (1 otherwise) and n_e' = n_e across.  On a periodic
+ * direction the last face is the image of the first: set ignores it, get
+ * returns the image.  Set makes the cell-centred B of every zone the average
+ * of its faces; call it after harmrad_set_prims (which initialises the faces
+ * from the cell-centred B). */
+int harmrad_set_face_fields(harmrad_ctx* ctx, const double* Bf, int on_device);
+int harmrad_get_face_fields(harmrad_ctx* ctx, double* Bf, int on_device);
 
 /* Load the per-zone absorption field K (active zones, [n3][n2][n1] FP64 per
  * box, boxes concatenated) of a context created with opacity =

@@ -66,6 +66,9 @@ typedef struct {
                              3 IMEX3 (Sec. 4.1, Eqs. IMEX2, IMEX2B, IMEX3) */
   int implicit_eq;        /* 0 energy equations, the entropy equation as back-up (RK3);
                              1 the entropy equation in every zone (RK3) */
+  int emf;                /* 0 flux-CT: cell-centred B, edge EMFs averaged from the face
+                             fluxes; 1 staggered B on faces with the 4-state upwind EMF
+                             (Sec. 4.2 steps viii-ix) */
 } orc_params;
 
 /* Per-zone solver outcome codes (same meaning as the library's status byte). */
@@ -94,6 +97,14 @@ double orc_cfl_dt(void* ctx);
 double orc_step(void* ctx, double dt);
 /* Per-zone status bytes of the last step, worst over its three stages ([n3][n2][n1]). */
 void   orc_get_status(void* ctx, unsigned char* st);
+/* Staggered field (emf = 1): sqrt(-g) B^d on the d-faces, three arrays one
+ * after another, direction d of shape [n3'][n2'][n1'] with n_d' = n_d + 1
+ * faces along d when n_d > 1 (1 otherwise) and n_e' = n_e across.  On a
+ * periodic direction the last face is the first one's image: set ignores it,
+ * get returns the image.  Set also makes the cell-centred B of every active
+ * zone the average of its two faces (sqrt(-g) B averaged). */
+void   orc_set_face_fields(void* ctx, const double* Bf);
+void   orc_get_face_fields(void* ctx, double* Bf);
 /* Per-zone Newton iteration totals summed over the three stages of the last step. */
 void   orc_get_iters(void* ctx, int* it);
 /* Counts over the last step: [0] PMHD-accepted, [1] URAD-accepted, [2] back-up,

@@ -54,6 +54,7 @@ class OrcParams(ctypes.Structure):
         ("newton_tol", ctypes.c_double),
         ("integrator", ctypes.c_int),
         ("implicit_eq", ctypes.c_int),
+        ("emf", ctypes.c_int),
     ]
 
 
@@ -103,6 +104,8 @@ def lib():
         L.orc_set_opacity_field.argtypes = [ctypes.c_void_p, dp]
         L.orc_get_prims_with_ghosts.argtypes = [ctypes.c_void_p, dp, ctypes.c_int]
         L.orc_set_prims_with_ghosts.argtypes = [ctypes.c_void_p, dp]
+        L.orc_set_face_fields.argtypes = [ctypes.c_void_p, dp]
+        L.orc_get_face_fields.argtypes = [ctypes.c_void_p, dp]
         L.orc_cfl_dt.restype = ctypes.c_double
         L.orc_cfl_dt.argtypes = [ctypes.c_void_p]
         L.orc_step.restype = ctypes.c_double
@@ -224,6 +227,32 @@ class Oracle:
         F = np.empty((NP, m[2], m[1], m[0]))
         lib().orc_compute_fluxes(self._h, d, _dp(F))
         return F
+
+    def face_shapes(self):
+        """Shapes [n3', n2', n1'] of the three face-field arrays (staggered field)."""
+        out = []
+        for d in range(3):
+            m = list(self.n)
+            if m[d] > 1:
+                m[d] += 1
+            out.append((m[2], m[1], m[0]))
+        return out
+
+    def set_face_fields(self, Bf):
+        """sqrt(-g) B^d on the d-faces (three arrays of face_shapes())."""
+        flat = np.concatenate([np.ascontiguousarray(b, dtype=np.float64).ravel() for b in Bf])
+        lib().orc_set_face_fields(self._h, _dp(flat))
+
+    def get_face_fields(self):
+        shapes = self.face_shapes()
+        flat = np.empty(sum(int(np.prod(s)) for s in shapes))
+        lib().orc_get_face_fields(self._h, _dp(flat))
+        out, off = [], 0
+        for s in shapes:
+            m = int(np.prod(s))
+            out.append(flat[off:off + m].reshape(s))
+            off += m
+        return out
 
     def set_prims_with_ghosts(self, P):
         """Every cell, ghosts included ([12, N3, N2, N1]); fixed faces keep their ghosts."""

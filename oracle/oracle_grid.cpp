@@ -50,6 +50,10 @@ struct Ctx {
   std::vector<double> Sn;     // sqrt(-g) S u^t of the step's initial state [ntot]
   long long counts[7];
   std::vector<double> M[4];  // IMEX: implicit source of stage j, gas rows [4][ntot]
+  // staggered field (emf = 1): sqrt(-g) B^d on the lower d-face of each cell
+  // [ntot], its value at the start of the step, and the gas signal speeds
+  // (v_max, v_min) of each d-face [2][ntot]
+  std::vector<double> Bf[3], Bfn[3], gsp[3];
 };
 
 inline long idx(const Ctx& c, int i, int j, int k) {
@@ -212,7 +216,8 @@ void flattener(const FlatIn* c, int m, double* fg, double* fr) {
 // else nullptr): the stencil cells' absorption field; a reconstructed face
 // state takes the value of the cell it was reconstructed from.
 void face_flux(const orc_params& p, int d, const double P8[8][NP], const Geom* geo[8], const Geom& Gf,
-               const double* K8, double* stored[2][2], double F[NP], double* speed, double* FS = nullptr) {
+               const double* K8, double* stored[2][2], double F[NP], double* speed, double* FS = nullptr,
+               double* gas_speeds = nullptr) {
   auto at = [&](int m) {
     orc_params q = p;
     if (K8) q.kappa_abs0 = K8[m];
@@ -295,6 +300,10 @@ void face_flux(const orc_params& p, int d, const double P8[8][NP], const Geom* g
     F[q] = fl;
   }
   *speed = std::max(std::max(cmaxg, cming), std::max(cmaxr, cminr));
+  if (gas_speeds) {
+    gas_speeds[0] = cmaxg;
+    gas_speeds[1] = cming;
+  }
   if (FS) {
     // entropy flux sqrt(-g) S u^d = s_gas F_rho and conserved s_gas U_rho of
     // each state (Sec. 4 list of U_q, F_q), with the gas signal speeds
@@ -356,12 +365,16 @@ void compute_fluxes(Ctx& c, int d, bool use_stored) {
     geom_at(p, x[0], x[1], x[2], G);
     double* st[2][2] = {{&c.flat[d][t - str], &c.flat[d][c.ntot + t - str]},
                         {&c.flat[d][t], &c.flat[d][c.ntot + t]}};
-    double Fq[NP], sp, fs = 0.0;
+    double Fq[NP], sp, fs = 0.0, gs[2];
     face_flux(p, d, P8, geo, G, c.K.empty() ? nullptr : K8, use_stored ? st : nullptr, Fq, &sp,
-              p.integrator == 0 ? &fs : nullptr);
+              p.integrator == 0 ? &fs : nullptr, gs);
     for (int q = 0; q < NP; ++q) F[(long)q * c.ntot + t] = Fq[q];
     c.spd[d][t] = sp;
     c.FS[d][t] = fs;
+    if (!c.gsp[d].empty()) {
+      c.gsp[d][t] = gs[0];
+      c.gsp[d][c.ntot + t] = gs[1];
+    }
   };
   // a face writes the flattener of the two cells beside it: the parallel
   // loop runs over an index other than d, so neighbours along d stay on one
@@ -433,6 +446,256 @@ void flux_ct(Ctx& c) {
     double* Fd = &c.F[d][(long)(B1 + d) * c.ntot];
     for (long t = 0; t < c.ntot; ++t) Fd[t] = 0.0;
   }
+}
+
+// ------------------------------------------------------- staggered field
+// With emf = 1 the magnetic field is evolved on cell faces (Sec. 4, the list
+// of quantities; Sec. 4.2 steps viii-x): Bf[d] holds sqrt(-g) B^d on the
+// lower d-face of each cell, the EMFs sit on the cell edges, and the
+// cell-centred B of a zone is the average of its two faces' sqrt(-g) B^d
+// divided by the centre's sqrt(-g).  A direction with one zone has one face
+// per cell, the cell itself.
+
+inline long stride(const Ctx& c, int d) { return d == 0 ? 1 : (d == 1 ? c.N[0] : (long)c.N[0] * c.N[1]); }
+inline bool periodic(const Ctx& c, int d) { return c.p.bc[2 * d] == 0 && c.p.bc[2 * d + 1] == 0; }
+// position of a cell's lower d-face along d (the centre when n_d = 1)
+inline double xface(const Ctx& c, int d, int i) { return c.n[d] > 1 ? xf(c, d, i) : xc(c, d, i); }
+
+// Index ranges of the evolved faces of direction d: along d, faces 0..n_d
+// (0..n_d-1 when d is periodic: face n_d is face 0's image); across, the
+// active zones.
+void face_range(const Ctx& c, int d, int lo[3], int hi[3]) {
+  for (int e = 0; e < 3; ++e) {
+    lo[e] = 0;
+    hi[e] = c.n[e];
+  }
+  if (c.n[d] > 1 && !periodic(c, d)) hi[d] = c.n[d] + 1;
+}
+
+// Faces outside the evolved ranges: the periodic image where one exists,
+// else the average of the two cells beside the face of sqrt(-g) B^d (the
+// ghost cells hold the boundary conditions' B), or the one cell inside the
+// array on its outermost layer.
+void fill_face_ghosts(Ctx& c) {
+  for (int d = 0; d < 3; ++d) {
+    int lo[3], hi[3];
+    face_range(c, d, lo, hi);
+    const long sd = stride(c, d);
+    for (int k = -c.ng[2]; k < c.n[2] + c.ng[2]; ++k)
+      for (int j = -c.ng[1]; j < c.n[1] + c.ng[1]; ++j)
+        for (int i = -c.ng[0]; i < c.n[0] + c.ng[0]; ++i) {
+          int ii[3] = {i, j, k};
+          bool inside = true;
+          for (int e = 0; e < 3; ++e) inside = inside && ii[e] >= lo[e] && ii[e] < hi[e];
+          if (inside) continue;
+          const long t = idx(c, i, j, k);
+          int w[3] = {i, j, k};
+          bool image = true;
+          for (int e = 0; e < 3; ++e) {
+            if (w[e] >= lo[e] && w[e] < hi[e]) continue;
+            if (periodic(c, e) && c.n[e] > 1) w[e] = ((w[e] % c.n[e]) + c.n[e]) % c.n[e];
+            else image = false;
+          }
+          if (image) {
+            c.Bf[d][t] = c.Bf[d][idx(c, w[0], w[1], w[2])];
+            continue;
+          }
+          const double bt = c.geo[t].gdet * c.P[(long)(B1 + d) * c.ntot + t];
+          if (c.n[d] == 1 || ii[d] == -c.ng[d]) {
+            c.Bf[d][t] = bt;
+          } else {
+            const double bm = c.geo[t - sd].gdet * c.P[(long)(B1 + d) * c.ntot + t - sd];
+            c.Bf[d][t] = 0.5 * (bm + bt);
+          }
+        }
+  }
+}
+
+// sqrt(-g) B^d at the centre of cell t from its faces.
+inline double centre_flux(const Ctx& c, int d, long t) {
+  return c.n[d] > 1 ? 0.5 * (c.Bf[d][t] + c.Bf[d][t + stride(c, d)]) : c.Bf[d][t];
+}
+
+// Cell-centred B of the active zones from the faces.
+void centre_B_from_faces(Ctx& c) {
+  for (int k = 0; k < c.n[2]; ++k)
+    for (int j = 0; j < c.n[1]; ++j)
+      for (int i = 0; i < c.n[0]; ++i) {
+        long t = idx(c, i, j, k);
+        for (int d = 0; d < 3; ++d) c.P[(long)(B1 + d) * c.ntot + t] = centre_flux(c, d, t) / c.geo[t].gdet;
+      }
+}
+
+// Faces from the cell-centred B: sqrt(-g) B^d averaged over the two cells
+// beside each evolved face (after the ghost fill), then the centres from the
+// faces.
+void faces_from_centres(Ctx& c) {
+  fill_ghosts(c, c.P);
+  for (int d = 0; d < 3; ++d) {
+    const long sd = stride(c, d);
+    for (int k = -c.ng[2]; k < c.n[2] + c.ng[2]; ++k)
+      for (int j = -c.ng[1]; j < c.n[1] + c.ng[1]; ++j)
+        for (int i = -c.ng[0]; i < c.n[0] + c.ng[0]; ++i) {
+          const int ii[3] = {i, j, k};
+          const long t = idx(c, i, j, k);
+          const double bt = c.geo[t].gdet * c.P[(long)(B1 + d) * c.ntot + t];
+          if (c.n[d] == 1 || ii[d] == -c.ng[d]) c.Bf[d][t] = bt;
+          else c.Bf[d][t] = 0.5 * (c.geo[t - sd].gdet * c.P[(long)(B1 + d) * c.ntot + t - sd] + bt);
+        }
+  }
+  fill_face_ghosts(c);
+  centre_B_from_faces(c);
+}
+
+// 4-state upwind EMF (Sec. 4.2 steps viii-ix, after Del Zanna et al. 2007)
+// for every pair a < b of directions of which one has more than one zone, on
+// the edges (lower a-face, lower b-face) of the cells:
+//   emf_ab = sqrt(-g) (B^b v^a - B^a v^b), the flux of sqrt(-g) B^b along a
+//   and minus that of sqrt(-g) B^a along b.
+// The field components come from the faces: B^b from the b-faces on either
+// side of the edge along a, interpolated to the edge along a (MC-limited
+// linear), and B^a likewise along b.  The velocities v^i = u^i/u^t of the
+// four cells around the edge are extrapolated to it with MC-limited slopes.
+// The signal speeds along a at the edge interpolate (average) the gas
+// speeds v_max, v_min of the two a-faces beside it, and likewise along b.
+// The four states are combined by the 2D HLL (or, with LAXF, by weights
+// v_tot), with the dissipation of each direction's 1D HLL/LAXF flux
+// (Eqs. hll, lax).  Edges on the polar axis carry no EMF.
+void uct_emfs(Ctx& c, std::vector<double> emf[3]) {
+  const orc_params& p = c.p;
+  // v^i of every cell
+  std::vector<double> V((size_t)3 * c.ntot, 0.0);
+  for (long t = 0; t < c.ntot; ++t) {
+    double ut[3] = {c.P[(long)U1 * c.ntot + t], c.P[(long)U2 * c.ntot + t], c.P[(long)U3 * c.ntot + t]};
+    FourVel u;
+    fourvel(c.geo[t], ut, u);
+    for (int i = 0; i < 3; ++i) V[(long)i * c.ntot + t] = u.ucon[i + 1] / u.ucon[0];
+  }
+  for (int a = 0; a < 3; ++a)
+    for (int b = a + 1; b < 3; ++b) {
+      const int e = 3 - a - b;
+      std::vector<double>& E = emf[e];
+      E.assign((size_t)c.ntot, 0.0);
+      if (c.n[a] == 1 && c.n[b] == 1) continue;
+      const long sa = stride(c, a), sb = stride(c, b);
+      const bool aa = c.n[a] > 1, ab = c.n[b] > 1;
+      int hi[3];
+      for (int z = 0; z < 3; ++z) hi[z] = c.n[z];
+      if (aa) hi[a] = c.n[a] + 1;
+      if (ab) hi[b] = c.n[b] + 1;
+      // face primitive B^d = Bf / sqrt(-g) at the face position
+      auto Bface = [&](int d, long t, int i, int j, int k) {
+        double x[3] = {xc(c, 0, i), xc(c, 1, j), xc(c, 2, k)};
+        int ii[3] = {i, j, k};
+        x[d] = xface(c, d, ii[d]);
+        Geom G;
+        geom_at(p, x[0], x[1], x[2], G);
+        return c.Bf[d][t] / G.gdet;
+      };
+      for (int k = 0; k < hi[2]; ++k)
+        for (int j = 0; j < hi[1]; ++j)
+          for (int i = 0; i < hi[0]; ++i) {
+            const long t = idx(c, i, j, k);
+            const int ii[3] = {i, j, k};
+            if (p.metric == 1 && (a == 1 || b == 1) &&
+                ((j == 0 && p.bc[2] == 2) || (j == c.n[1] && p.bc[3] == 2)))
+              continue;  // polar axis
+            double x[3] = {xc(c, 0, i), xc(c, 1, j), xc(c, 2, k)};
+            x[a] = xface(c, a, ii[a]);
+            x[b] = xface(c, b, ii[b]);
+            Geom Ge;
+            geom_at(p, x[0], x[1], x[2], Ge);
+            // B^b along a (sides - and + of the edge), B^a along b
+            // face value B^d of the cell offset by o along direction m
+            auto Bat = [&](int d, int m, int o) {
+              int q[3] = {i, j, k};
+              q[m] += o;
+              return Bface(d, t + o * stride(c, m), q[0], q[1], q[2]);
+            };
+            double Bb[2], Ba[2];
+            {
+              const double b0 = Bat(b, a, 0);
+              if (aa) {
+                const double bmm = Bat(b, a, -2), bm = Bat(b, a, -1), bp = Bat(b, a, 1);
+                Bb[0] = bm + 0.5 * mc_slope(bmm, bm, b0);
+                Bb[1] = b0 - 0.5 * mc_slope(bm, b0, bp);
+              } else {
+                Bb[0] = Bb[1] = b0;
+              }
+            }
+            {
+              const double b0 = Bat(a, b, 0);
+              if (ab) {
+                const double bmm = Bat(a, b, -2), bm = Bat(a, b, -1), bp = Bat(a, b, 1);
+                Ba[0] = bm + 0.5 * mc_slope(bmm, bm, b0);
+                Ba[1] = b0 - 0.5 * mc_slope(bm, b0, bp);
+              } else {
+                Ba[0] = Ba[1] = b0;
+              }
+            }
+            // the four corner states: side sa_ (0: -, 1: +) along a, sb_ along b
+            double es[2][2];
+            for (int s1 = 0; s1 < 2; ++s1)
+              for (int s2 = 0; s2 < 2; ++s2) {
+                const long tc = t - (s1 == 0 && aa ? sa : 0) - (s2 == 0 && ab ? sb : 0);
+                double v[2];
+                const int comp[2] = {a, b};
+                for (int m = 0; m < 2; ++m) {
+                  const double* Vm = &V[(long)comp[m] * c.ntot];
+                  double val = Vm[tc];
+                  if (aa) val += (s1 == 0 ? 0.5 : -0.5) * mc_slope(Vm[tc - sa], Vm[tc], Vm[tc + sa]);
+                  if (ab) val += (s2 == 0 ? 0.5 : -0.5) * mc_slope(Vm[tc - sb], Vm[tc], Vm[tc + sb]);
+                  v[m] = val;
+                }
+                es[s1][s2] = Ge.gdet * (Bb[s1] * v[0] - Ba[s2] * v[1]);
+              }
+            // signal speeds at the edge and the weights of each side
+            double wa[2] = {0.0, 0.0}, wb[2] = {0.0, 0.0};
+            if (aa) {
+              const long f0 = ab ? t - sb : t;
+              const double vmax = 0.5 * (c.gsp[a][f0] + c.gsp[a][t]);
+              const double vmin = 0.5 * (c.gsp[a][c.ntot + f0] + c.gsp[a][c.ntot + t]);
+              if (p.flux == 0) wa[0] = wa[1] = std::max(vmax, vmin);
+              else {
+                wa[0] = vmax;
+                wa[1] = vmin;
+              }
+            }
+            if (ab) {
+              const long f0 = aa ? t - sa : t;
+              const double vmax = 0.5 * (c.gsp[b][f0] + c.gsp[b][t]);
+              const double vmin = 0.5 * (c.gsp[b][c.ntot + f0] + c.gsp[b][c.ntot + t]);
+              if (p.flux == 0) wb[0] = wb[1] = std::max(vmax, vmin);
+              else {
+                wb[0] = vmax;
+                wb[1] = vmin;
+              }
+            }
+            double Wa = wa[0] + wa[1], Wb = wb[0] + wb[1];
+            double da = 0.0, db = 0.0;
+            if (Wa > 0.0) da = wa[0] * wa[1] / Wa;
+            else wa[0] = wa[1] = Wa = 1.0;
+            if (Wb > 0.0) db = wb[0] * wb[1] / Wb;
+            else wb[0] = wb[1] = Wb = 1.0;
+            double sum = 0.0;
+            for (int s1 = 0; s1 < 2; ++s1)
+              for (int s2 = 0; s2 < 2; ++s2) sum += wa[s1] * wb[s2] * es[s1][s2];
+            E[t] = sum / (Wa * Wb) - da * Ge.gdet * (Bb[1] - Bb[0]) + db * Ge.gdet * (Ba[1] - Ba[0]);
+          }
+    }
+}
+
+// Right-hand side of the evolved face fields from the edge EMFs:
+// d(sqrt(-g) B^d)/dt = - sum_{a != d} d_a emf_{a d}, emf_{a d} = -emf_{d a}.
+void face_rhs(const Ctx& c, const std::vector<double> emf[3], int d, long t, double* rhs) {
+  double r = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    if (a == d || c.n[a] == 1) continue;
+    const int e = 3 - a - d;
+    const double sgn = a < d ? 1.0 : -1.0;  // emf[e] holds emf_{min(a,d) max(a,d)}
+    r -= sgn * (emf[e][t + stride(c, a)] - emf[e][t]) / c.p.dx[a];
+  }
+  *rhs = r;
 }
 
 // Floors (Sec. 2 and Sec. 4.11; values from the configuration): Lorentz
@@ -596,11 +859,34 @@ void substep(Ctx& c, int s, double dt) {
   const Pass ps = imex_pass(c.p.integrator, s);
   // an IMEX stage without an explicit right-hand side needs no fluxes
   const bool rhs = !imex || ps.d != 0.0;
+  const bool uct = c.p.emf == 1;
+  std::vector<double> emf[3];
   if (rhs) {
     fill_ghosts(c, c.P);
+    if (uct) fill_face_ghosts(c);
     for (int d = 0; d < 3; ++d)
       if (c.n[d] > 1) compute_fluxes(c, d, c.p.recon == 0);
-    flux_ct(c);
+    if (uct) uct_emfs(c, emf);
+    else flux_ct(c);
+  }
+  if (uct) {
+    // the staggered field's stage (Sec. 4.2 step x): the same combination as
+    // the cell-centred conserved quantities, with the EMFs' curl for X
+    for (int d = 0; d < 3; ++d) {
+      if (s == 0) c.Bfn[d] = c.Bf[d];
+      int lo[3], hi[3];
+      face_range(c, d, lo, hi);
+      for (int k = lo[2]; k < hi[2]; ++k)
+        for (int j = lo[1]; j < hi[1]; ++j)
+          for (int i = lo[0]; i < hi[0]; ++i) {
+            const long t = idx(c, i, j, k);
+            double r = 0.0;
+            if (rhs) face_rhs(c, emf, d, t, &r);
+            const double bn = c.Bfn[d][t], bs = c.Bf[d][t];
+            c.Bf[d][t] = !imex ? A[s] * bn + Bc[s] * (bs + dt * r) : ps.an * bn + ps.ap * bs + ps.d * dt * r;
+          }
+    }
+    fill_face_ghosts(c);
   }
   std::vector<double> Pnew((size_t)NP * c.ntot);
   std::memcpy(Pnew.data(), c.P.data(), sizeof(double) * NP * c.ntot);
@@ -630,7 +916,9 @@ void substep(Ctx& c, int s, double dt) {
             }
             X[q] = -div + SM[q];
           }
-          if (!imex) {
+          if (uct && q >= B1 && q <= B3) {
+            Ust[q] = centre_flux(c, q - B1, t);  // the field from the evolved faces
+          } else if (!imex) {
             Ust[q] = A[s] * c.Un[(long)q * c.ntot + t] + Bc[s] * (Us[q] + dt * X[q]);
           } else {
             double v = ps.an * c.Un[(long)q * c.ntot + t] + ps.ap * Us[q] + ps.d * dt * X[q];
@@ -778,6 +1066,14 @@ void* orc_create(const orc_params* p) {
     c->flat[d].assign((size_t)2 * c->ntot, 0.0);
   }
   if (c->p.integrator < 0 || c->p.integrator > 3) c->p.integrator = 0;
+  if (c->p.emf == 1)
+    for (int d = 0; d < 3; ++d) {
+      c->Bf[d].assign((size_t)c->ntot, 0.0);
+      c->Bfn[d].assign((size_t)c->ntot, 0.0);
+      c->gsp[d].assign((size_t)2 * c->ntot, 0.0);
+    }
+  else
+    c->p.emf = 0;
   if (c->p.integrator != 0)
     for (int j = 0; j < 4; ++j) c->M[j].assign((size_t)4 * c->ntot, 0.0);
   c->geo.resize(c->ntot);
@@ -810,11 +1106,51 @@ void orc_set_prims(void* ctx, const double* P) {
       for (int j = 0; j < c.n[1]; ++j)
         for (int i = 0; i < c.n[0]; ++i)
           c.P[(long)q * c.ntot + idx(c, i, j, k)] = P[(long)q * na + aidx(c, i, j, k)];
+  if (c.p.emf == 1) faces_from_centres(c);
 }
 
 void orc_set_prims_with_ghosts(void* ctx, const double* P) {
   Ctx& c = *static_cast<Ctx*>(ctx);
   for (long m = 0; m < (long)NP * c.ntot; ++m) c.P[m] = P[m];
+  if (c.p.emf == 1) faces_from_centres(c);
+}
+
+// Active face layout of direction d: [n3'][n2'][n1'], n_d' = n_d + 1 if
+// n_d > 1 (else 1), n_e' = n_e across.
+static void face_dims(const Ctx& c, int d, int m[3]) {
+  for (int e = 0; e < 3; ++e) m[e] = c.n[e];
+  if (c.n[d] > 1) m[d] = c.n[d] + 1;
+}
+
+void orc_set_face_fields(void* ctx, const double* Bf) {
+  Ctx& c = *static_cast<Ctx*>(ctx);
+  if (c.p.emf != 1) return;
+  fill_ghosts(c, c.P);
+  long off = 0;
+  for (int d = 0; d < 3; ++d) {
+    int m[3];
+    face_dims(c, d, m);
+    for (int k = 0; k < m[2]; ++k)
+      for (int j = 0; j < m[1]; ++j)
+        for (int i = 0; i < m[0]; ++i) c.Bf[d][idx(c, i, j, k)] = Bf[off + ((long)k * m[1] + j) * m[0] + i];
+    off += (long)m[0] * m[1] * m[2];
+  }
+  fill_face_ghosts(c);
+  centre_B_from_faces(c);
+}
+
+void orc_get_face_fields(void* ctx, double* Bf) {
+  Ctx& c = *static_cast<Ctx*>(ctx);
+  if (c.p.emf != 1) return;
+  long off = 0;
+  for (int d = 0; d < 3; ++d) {
+    int m[3];
+    face_dims(c, d, m);
+    for (int k = 0; k < m[2]; ++k)
+      for (int j = 0; j < m[1]; ++j)
+        for (int i = 0; i < m[0]; ++i) Bf[off + ((long)k * m[1] + j) * m[0] + i] = c.Bf[d][idx(c, i, j, k)];
+    off += (long)m[0] * m[1] * m[2];
+  }
 }
 
 void orc_set_opacity_field(void* ctx, const double* K) {

@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libharmrad.so")
 SOURCES = ["hr_api.cu", "hr_run_mink.cu", "hr_run_ks.cu", "hr_static.cu", "hr_adj_ks.cu", "hr_adj_mink.cu",
            "hr_probe.cu"]
-HEADERS = ["hr_common.cuh", "hr_dual.cuh", "hr_phys.cuh", "hr_implicit.cuh", "hr_tangent.cuh", "hr_kernels.cuh", "hr_run.cuh",
+HEADERS = ["hr_common.cuh", "hr_dual.cuh", "hr_phys.cuh", "hr_implicit.cuh", "hr_tangent.cuh", "hr_kernels.cuh", "hr_uct.cuh", "hr_run.cuh",
            "hr_ctx.h", "hr_adjoint.cuh", "hr_adjoint_run.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -11,6 +11,7 @@
 
 #include "hr_adjoint.cuh"
 #include "hr_ctx.h"
+#include "hr_uct.cuh"
 
 using hr::BoxGeo;
 using hr::DevParams;
@@ -155,6 +156,8 @@ int fill_physics(const harmrad_params* p, DevParams& d) {
   d.implicit_eq = p->implicit_eq;
   if (p->integrator < 0 || p->integrator > 3) return HARMRAD_E_ARG;
   d.integrator = p->integrator;
+  if (p->emf != 0 && p->emf != 1) return HARMRAD_E_ARG;
+  d.emf = p->emf;
   return HARMRAD_OK;
 }
 
@@ -370,7 +373,9 @@ void free_all(harmrad_ctx* c) {
                   c->aux, c->flat[0], c->flat[1], c->flat[2], c->emf, c->edges, c->slope, c->dt, c->status,
                   c->iters, c->failed, c->qcount, c->czone, c->cbox, c->cdata, c->qzone, c->qbox, c->qdata, c->fzone, c->fbox,
                   c->ftmp, c->stats, c->dtmin, c->stage_buf, c->flag, c->dboxes, c->imex_ust, c->imex_psol,
-                  c->imex_M, c->sig, c->Sn, c->FS[0], c->FS[1], c->FS[2]};
+                  c->imex_M, c->sig, c->Sn, c->FS[0], c->FS[1], c->FS[2], c->Bf[0], c->Bf[1], c->Bf[2],
+                  c->Bfn[0], c->Bfn[1], c->Bfn[2], c->gsp[0], c->gsp[1], c->gsp[2], c->vel, c->emf3[0],
+                  c->emf3[1], c->emf3[2]};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   if (c->host_dt) cudaFreeHost(c->host_dt);
@@ -470,6 +475,15 @@ int create(const harmrad_params* p, int count, void* stream, harmrad_ctx** out) 
   }
   rc = rc ? rc : dalloc(&c->aux, 10 * nt * rs);
   rc = rc ? rc : dalloc(&c->emf, nt * rs);
+  if (dp.emf == 1) {  // staggered field
+    for (int d = 0; d < 3; ++d) {
+      rc = rc ? rc : dalloc(&c->Bf[d], nt * sizeof(double));
+      rc = rc ? rc : dalloc(&c->Bfn[d], nt * sizeof(double));
+      rc = rc ? rc : dalloc(&c->gsp[d], 2 * nt * rs);
+      rc = rc ? rc : dalloc(&c->emf3[d], nt * rs);
+    }
+    rc = rc ? rc : dalloc(&c->vel, 3 * nt * rs);
+  }
   rc = rc ? rc : dalloc(&c->edges, 24 * nt * rs);
   rc = rc ? rc : dalloc(&c->slope, 12 * nt * rs);
   rc = rc ? rc : dalloc(&c->dt, count * sizeof(double));
@@ -574,11 +588,66 @@ void harmrad_destroy(harmrad_ctx* c) {
   free(c);
 }
 
+// Staggered field: the faces from the cell-centred B just set (or, with
+// from_centres false, the ghost faces and centres from the faces just set).
+static int init_faces(harmrad_ctx* c, bool from_centres) {
+  if (c->dp.emf != 1) return HARMRAD_OK;
+  int r = c->dp.metric == 1 ? hr::Run<hr::KS>::init_faces(c, from_centres)
+                            : hr::Run<hr::MINK>::init_faces(c, from_centres);
+  if (r < 0) return r;
+  HR_CHECK(cudaStreamSynchronize(c->stream));
+  return HARMRAD_OK;
+}
+
 int harmrad_set_prims(harmrad_ctx* c, const double* P, int on_device) {
   if (!c || !P) return HARMRAD_E_ARG;
   int rc = upload_planes(c, 12, P, on_device, c->P);
   if (rc) return rc;
+  if ((rc = init_faces(c, true))) return rc;
   c->has_prims = true;
+  return HARMRAD_OK;
+}
+
+int harmrad_set_face_fields(harmrad_ctx* c, const double* Bf, int on_device) {
+  if (!c || !Bf || c->dp.emf != 1 || c->nbox != 1) return HARMRAD_E_ARG;
+  const hr::BoxGeo& b = c->boxes[0];
+  size_t n = 0;
+  for (int d = 0; d < 3; ++d) {
+    size_t m = 1;
+    for (int e = 0; e < 3; ++e) m *= b.n[e] + ((e == d && b.n[d] > 1) ? 1 : 0);
+    n += m;
+  }
+  // host data stage through the [12][nact] staging buffer: the face count
+  // of a grid, at most 3 (n1+1)(n2+1)(n3+1) <= 12 n1 n2 n3 when every n >= 1
+  double* src = (double*)Bf;
+  if (!on_device) {
+    HR_CHECK(cudaMemcpyAsync(c->stage_buf, Bf, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    src = c->stage_buf;
+  }
+  hr::FaceSet fs;
+  for (int d = 0; d < 3; ++d) fs.f[d] = c->Bf[d];
+  hr::k_face_pack<<<hr::grid_for((long long)n, c->sms, 256), 256, 0, c->stream>>>(c->dboxes, src, fs, true);
+  HR_CHECK(cudaGetLastError());
+  return init_faces(c, false);
+}
+
+int harmrad_get_face_fields(harmrad_ctx* c, double* Bf, int on_device) {
+  if (!c || !Bf || c->dp.emf != 1 || c->nbox != 1) return HARMRAD_E_ARG;
+  const hr::BoxGeo& b = c->boxes[0];
+  size_t n = 0;
+  for (int d = 0; d < 3; ++d) {
+    size_t m = 1;
+    for (int e = 0; e < 3; ++e) m *= b.n[e] + ((e == d && b.n[d] > 1) ? 1 : 0);
+    n += m;
+  }
+  double* dst = on_device ? Bf : c->stage_buf;
+  hr::FaceSet fs;
+  for (int d = 0; d < 3; ++d) fs.f[d] = c->Bf[d];
+  hr::k_face_pack<<<hr::grid_for((long long)n, c->sms, 256), 256, 0, c->stream>>>(c->dboxes, dst, fs, false);
+  HR_CHECK(cudaGetLastError());
+  if (!on_device)
+    HR_CHECK(cudaMemcpyAsync(Bf, c->stage_buf, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  HR_CHECK(cudaStreamSynchronize(c->stream));
   return HARMRAD_OK;
 }
 
@@ -594,6 +663,8 @@ int harmrad_set_prims_ghosts(harmrad_ctx* c, const double* P, int on_device) {
   HR_CHECK(cudaMemcpyAsync(&flag, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   HR_CHECK(cudaStreamSynchronize(c->stream));
   if (flag) return HARMRAD_E_NAN_INPUT;
+  int rc = init_faces(c, true);
+  if (rc) return rc;
   c->has_prims = true;
   return HARMRAD_OK;
 }
@@ -820,7 +891,8 @@ int harmrad_adjoint_enable(harmrad_ctx* c, int on) {
     free_adjoint(c);
     return HARMRAD_OK;
   }
-  if (c->nbox != 1 || c->real_size != 8 || c->dp.integrator != 0 || c->dp.implicit_eq != 0) return HARMRAD_E_ARG;
+  if (c->nbox != 1 || c->real_size != 8 || c->dp.integrator != 0 || c->dp.implicit_eq != 0 || c->dp.emf != 0)
+    return HARMRAD_E_ARG;
   for (int f = 0; f < 6; ++f)
     if (c->boxes[0].bc[f] == HARMRAD_BC_FIXED) return HARMRAD_E_ARG;
   if (c->adj) return HARMRAD_OK;

@@ -35,6 +35,15 @@ struct harmrad_ctx {
   void* aux;
   void* flat[3];
   void* emf;
+  // staggered field (emf mode 1; null otherwise): sqrt(-g) B^d on the d-faces
+  // and its value at the start of the step [ntot] each, gas signal speeds of
+  // the faces [2][ntot] per direction, cell 3-velocities [3][ntot] and the
+  // three edge EMFs [ntot] each (real type of the precision mode)
+  double* Bf[3];
+  double* Bfn[3];
+  void* gsp[3];
+  void* vel;
+  void* emf3[3];
   void* edges;  // [2][12][ntot] reconstructed edge values of one direction
   void* slope;  // [12][ntot] MC slopes of one direction
   double* dt;
@@ -111,6 +120,10 @@ struct Run {
   static int zone_physics(const DevParams& dp, const BoxGeo& bg, int n, const double* x,
                           const double* P, double* U, double* SM, double* F, double* speeds,
                           cudaStream_t st, int sms);
+  // staggered field: the faces from the cell-centred B (from_centres: after
+  // a set of the primitives), then the ghost faces and the cell-centred B of
+  // the active zones from the evolved faces
+  static int init_faces(harmrad_ctx* c, bool from_centres);
   static int zone_implicit(const DevParams& dp, const BoxGeo& bg, int n, const double* x,
                            const double* Us, const double* Ss, const double* Ps, const double* h,
                            double* Pout, double* eT, int* iters, unsigned char* method, cudaStream_t st,

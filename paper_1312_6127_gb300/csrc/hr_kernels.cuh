@@ -54,6 +54,7 @@ struct Bufs {
   double* psol_rec;           // [12][nact] solution of every zone before the floors
   double* sst_rec;            // [nact] explicit entropy S* of every zone of the sub-step
   double* imexM;              // IMEX: [4 stages][4 gas rows][nact] per grid, grid b at 16 aoff_b
+  double* Bf[3];              // staggered field: sqrt(-g) B^d on the d-faces [ntot] (null: flux-CT)
 };
 
 
@@ -652,7 +653,7 @@ __global__ void __launch_bounds__(256) k_edges(DevParams p, const BoxGeo* __rest
 template <int MET, typename R, int d>
 __device__ __forceinline__ void face_flux(const DevParams& p, const Geo<MET, R>& g, R dxd, R kL, R kR, R ks,
                                           const R PL[NPR], const R PR[NPR], R out[NPR], R* smax,
-                                          unsigned* code = nullptr, R* fs = nullptr) {
+                                          unsigned* code = nullptr, R* fs = nullptr, R* gas = nullptr) {
   R sL[4], sR[4];
   unsigned cL = 0, cR = 0;
   face_speeds<MET, R>(p, g, d + 1, dxd, kL, ks, PL, sL, code ? &cL : nullptr);
@@ -709,6 +710,10 @@ __device__ __forceinline__ void face_flux(const DevParams& p, const Geo<MET, R>&
   face_accum<MET, R>(p, g, d + 1, PR, fRg, uRg, fRr, uRr, out, fs);
   out[B1 + d] = R(0);
   *smax = fmax(fmax(cmaxg, cming), fmax(cmaxr, cminr));
+  if (gas) {
+    gas[0] = cmaxg;
+    gas[1] = cming;
+  }
 }
 
 // ----------------------------------------------------------------- fluxes
@@ -723,7 +728,8 @@ template <int MET, typename R, int d>
 __global__ void __launch_bounds__(128) k_face(DevParams p, const BoxGeo* __restrict__ boxes, int nbox,
                                               const R* __restrict__ E0, const double* __restrict__ K0,
                                               R* __restrict__ F0, R* __restrict__ spd0,
-                                              const double* __restrict__ geo0, R* __restrict__ FS0) {
+                                              const double* __restrict__ geo0, R* __restrict__ FS0,
+                                              R* __restrict__ gsp0 = nullptr) {
   const bool weighted = (MET == KS) && (d != 1);
   for (int bi = 0; bi < nbox; ++bi) {
     const BoxGeo& bx = boxes[bi];
@@ -732,6 +738,7 @@ __global__ void __launch_bounds__(128) k_face(DevParams p, const BoxGeo* __restr
     R* F = F0 + 12 * bx.coff;
     R* spd = spd0 + bx.coff;
     R* FS = FS0 ? FS0 + bx.coff : nullptr;
+    R* gsp = gsp0 ? gsp0 + 2 * bx.coff : nullptr;  // gas v_max, v_min per face (staggered field)
     int len[3], off[3];
     for (int e = 0; e < 3; ++e) {
       if (e == d) {
@@ -762,6 +769,7 @@ __global__ void __launch_bounds__(128) k_face(DevParams p, const BoxGeo* __restr
         for (int q = 0; q < NPR; ++q) F[q * bx.ntot + t] = R(0);
         spd[t] = R(0);
         if (FS) FS[t] = R(0);
+        if (gsp) gsp[t] = gsp[bx.ntot + t] = R(0);
         continue;
       }
       Geo<MET, R> g;
@@ -793,11 +801,15 @@ __global__ void __launch_bounds__(128) k_face(DevParams p, const BoxGeo* __restr
       const R kL = R(kfield(p, K, t - st)), kR = R(kfield(p, K, t));
       R out[NPR], smax;
       unsigned fcode = 0;
-      R fsv;
+      R fsv, gs[2];
       face_flux<MET, R, d>(p, g, dxd, kL, kR, R(p.kscale), PL, PR, out, &smax, p.sig ? &fcode : nullptr,
-                           FS ? &fsv : nullptr);
+                           FS ? &fsv : nullptr, gs);
       if (p.sig) sig_put(p, bx.coff + t, 40 + d, fcode);
       if (FS) FS[t] = fsv;
+      if (gsp) {
+        gsp[t] = gs[0];
+        gsp[bx.ntot + t] = gs[1];
+      }
 #pragma unroll
       for (int q = 0; q < NPR; ++q) F[q * bx.ntot + t] = out[q];
       spd[t] = smax;
@@ -1476,6 +1488,13 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
           Ust[q] = im.an * un + im.ap * Us[q] + im.d * dt * X[q];
         else
           Ust[q] = A * un + Bc * (Us[q] + dt * X[q]);
+      }
+      if (b.Bf[0]) {  // staggered field: B from the evolved faces (average of the two)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const double* Bfd = b.Bf[d] + bx.coff;
+          Ust[B1 + d] = p.act[d] ? 0.5 * (Bfd[t] + Bfd[t + bx.str[d]]) : Bfd[t];
+        }
       }
       if (IMEX && stage > 0) {
         // earlier stages' implicit sources: +M on the gas rows, -M on the radiation rows

@@ -39,6 +39,7 @@ struct DevParams {
   int precision;
   int integrator;  // 0 RK3, 1 IMEX2, 2 IMEX2B, 3 IMEX3 (Sec. 4.1)
   int implicit_eq;  // 0 energy equations (entropy as back-up, RK3), 1 entropy in every zone
+  int emf;          // 0 flux-CT, 1 staggered field with the 4-state upwind EMF
   // branch signature (a test instrument; null unless enabled): per cell a
   // 64-bit word into which every branch decision of the step is folded
   unsigned long long* sig;

@@ -2,6 +2,7 @@
 #pragma once
 #include "hr_ctx.h"
 #include "hr_kernels.cuh"
+#include "hr_uct.cuh"
 
 namespace hr {
 
@@ -46,6 +47,7 @@ inline Bufs make_bufs(harmrad_ctx* c) {
     b.psol_rec = c->imex_psol;
   }
   b.imexM = c->imex_M;
+  for (int d = 0; d < 3; ++d) b.Bf[d] = c->dp.emf == 1 ? c->Bf[d] : nullptr;
   return b;
 }
 
@@ -60,12 +62,27 @@ inline long long max_work(const harmrad_ctx* c, Fn work) {
   return m;
 }
 
-template <int MET, typename R>
-int faces_impl(harmrad_ctx* c, bool fresh) {
+inline FaceSet face_set(double* const f[3]) {
+  FaceSet s;
+  for (int d = 0; d < 3; ++d) s.f[d] = f[d];
+  return s;
+}
+
+// Staggered field: the faces outside the evolved ranges (periodic images,
+// else from the ghost cells' B; after the ghost fill of P).
+template <int MET>
+int face_ghosts(harmrad_ctx* c) {
+  for (int d = 0; d < 3; ++d) {
+    k_face_ghosts<MET><<<grid_for(c->maxcell, c->sms, 256), 256, 0, c->stream>>>(c->dp, c->dboxes, c->nbox, c->P,
+                                                                                 face_set(c->Bf), d);
+    mark(c, HARMRAD_K_CT);
+  }
+  return 3;
+}
+
+// Ghost fill of P in every active direction.
+inline int fill_ghost_cells(harmrad_ctx* c) {
   const DevParams& p = c->dp;
-  cudaStream_t st = c->stream;
-  const BoxGeo* bt = c->dboxes;
-  const int nb = c->nbox;
   double* K = p.opacity == 2 ? c->K : nullptr;
   int nk = 0;
   for (int d = 0; d < 3; ++d) {
@@ -76,10 +93,21 @@ int faces_impl(harmrad_ctx* c, bool fresh) {
         if (e != d) w *= (e < d) ? b.N[e] : b.n[e];
       return w;
     });
-    k_bc_fill<<<grid_for(work, c->sms, 256), 256, 0, st>>>(p, bt, nb, c->P, K, d);
+    k_bc_fill<<<grid_for(work, c->sms, 256), 256, 0, c->stream>>>(p, c->dboxes, c->nbox, c->P, K, d);
     mark(c, HARMRAD_K_BC);
     ++nk;
   }
+  return nk;
+}
+
+template <int MET, typename R>
+int faces_impl(harmrad_ctx* c, bool fresh) {
+  const DevParams& p = c->dp;
+  cudaStream_t st = c->stream;
+  const BoxGeo* bt = c->dboxes;
+  const int nb = c->nbox;
+  int nk = fill_ghost_cells(c);
+  if (p.emf == 1) nk += face_ghosts<MET>(c);
   k_prep<MET, R><<<grid_for(c->maxcell, c->sms, 256), 256, 0, st>>>(p, bt, nb, c->P, c->K, (R*)c->aux,
                                                                      c->geotab);
   mark(c, HARMRAD_K_PREP);
@@ -134,7 +162,8 @@ int faces_impl(harmrad_ctx* c, bool fresh) {
       }
       k_edges<MET, R, 0><<<ge, be, 0, st>>>(p, bt, nb, c->P, aux, fl, Sl, Ed);
       mark(c, HARMRAD_K_EDGE);
-      k_face<MET, R, 0><<<g, bf, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd, c->geotab, (R*)c->FS[0]);
+      k_face<MET, R, 0><<<g, bf, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd, c->geotab, (R*)c->FS[0],
+                                           (R*)c->gsp[0]);
     } else if (d == 1) {
       if (Sl) {
         k_slopes<MET, R, 1><<<gs, be, 0, st>>>(p, bt, nb, c->P, aux, Sl);
@@ -143,7 +172,8 @@ int faces_impl(harmrad_ctx* c, bool fresh) {
       }
       k_edges<MET, R, 1><<<ge, be, 0, st>>>(p, bt, nb, c->P, aux, fl, Sl, Ed);
       mark(c, HARMRAD_K_EDGE);
-      k_face<MET, R, 1><<<g, bf, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd, c->geotab, (R*)c->FS[1]);
+      k_face<MET, R, 1><<<g, bf, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd, c->geotab, (R*)c->FS[1],
+                                           (R*)c->gsp[1]);
     } else {
       if (Sl) {
         k_slopes<MET, R, 2><<<gs, be, 0, st>>>(p, bt, nb, c->P, aux, Sl);
@@ -152,10 +182,32 @@ int faces_impl(harmrad_ctx* c, bool fresh) {
       }
       k_edges<MET, R, 2><<<ge, be, 0, st>>>(p, bt, nb, c->P, aux, fl, Sl, Ed);
       mark(c, HARMRAD_K_EDGE);
-      k_face<MET, R, 2><<<g, bf, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd, c->geotab, (R*)c->FS[2]);
+      k_face<MET, R, 2><<<g, bf, 0, st>>>(p, bt, nb, Ed, c->K, Fd, sd, c->geotab, (R*)c->FS[2],
+                                           (R*)c->gsp[2]);
     }
     mark(c, HARMRAD_K_FACE);
     nk += 2;
+  }
+  if (p.emf == 1) {  // staggered field: the 4-state upwind EMFs on the edges
+    k_vel<MET, R><<<grid_for(c->maxcell, c->sms, 256), 256, 0, st>>>(p, bt, nb, c->P, (R*)c->vel);
+    mark(c, HARMRAD_K_CT);
+    ++nk;
+    for (int a = 0; a < 3; ++a)
+      for (int b = a + 1; b < 3; ++b) {
+        if (!p.act[a] && !p.act[b]) continue;
+        long long we = max_work(c, [a, b](const BoxGeo& x) {
+          long long w = 1;
+          for (int e = 0; e < 3; ++e) w *= x.n[e] + (((e == a || e == b) && x.n[e] > 1) ? 1 : 0);
+          return w;
+        });
+        k_uct_emf<MET, R><<<grid_for(we, c->sms, 128), 128, 0, st>>>(
+            p, bt, nb, face_set(c->Bf), (const R*)c->vel, (const R*)c->gsp[a], (const R*)c->gsp[b],
+            (R*)c->emf3[3 - a - b], a, b);
+        mark(c, HARMRAD_K_CT);
+        ++nk;
+      }
+    if (cudaGetLastError() != cudaSuccess) return HARMRAD_E_CUDA;
+    return nk;
   }
   for (int a = 0; a < 3; ++a)
     for (int b = a + 1; b < 3; ++b) {
@@ -215,6 +267,23 @@ int solve_impl(harmrad_ctx* c, int stage, const ImexStage& im) {
   const BoxGeo& b0 = c->boxes[0];
   const BoxGeo* bt = c->dboxes;
   const int nb = c->nbox;
+  int nf = 0;
+  if (p.emf == 1) {  // the staggered field's stage, then its periodic images
+    EmfSet es;
+    for (int e = 0; e < 3; ++e) es.e[e] = c->emf3[e];
+    const bool rhs = !im.on || im.d != 0.0;
+    for (int d = 0; d < 3; ++d) {
+      long long wf = max_work(c, [d](const BoxGeo& x) {
+        long long w = 1;
+        for (int e = 0; e < 3; ++e) w *= (e == d && x.n[e] > 1) ? x.n[e] + 1 : x.n[e];
+        return w;
+      });
+      k_face_update<R><<<grid_for(wf, c->sms, 256), 256, 0, st>>>(p, bt, nb, face_set(c->Bf), face_set(c->Bfn), es,
+                                                                  c->dt, stage, im, rhs, d);
+      mark(c, HARMRAD_K_CT);
+    }
+    nf = 3 + face_ghosts<MET>(c);
+  }
   if (!im.on) {
     if (one && split == 0)
       k_update<MET, R, true, false, false><<<gu, bu, 0, st>>>(p, b0, bt, 1, b, stage, 0, im);
@@ -235,7 +304,7 @@ int solve_impl(harmrad_ctx* c, int stage, const ImexStage& im) {
       k_update<MET, R, false, true, true><<<gu, bu, 0, st>>>(p, b0, bt, nb, b, stage, split, im);
   }
   mark(c, HARMRAD_K_UPDATE);
-  int nk = 4;
+  int nk = 4 + nf;
   if (split > 0) {
     // the continuation queue, the retry queue and the back-up list are
     // short: one persistent wave of blocks each
@@ -356,6 +425,17 @@ __global__ void k_zone_implicit(DevParams p, BoxGeo bg, int n, const double* __r
   }
 }
 
+template <int MET>
+int Run<MET>::init_faces(harmrad_ctx* c, bool from_centres) {
+  fill_ghost_cells(c);
+  if (from_centres)
+    k_faces_from_centres<MET><<<grid_for(c->maxcell, c->sms, 256), 256, 0, c->stream>>>(c->dp, c->dboxes, c->nbox,
+                                                                                        c->P, face_set(c->Bf));
+  face_ghosts<MET>(c);
+  k_centre_B<MET><<<grid_for(c->maxact, c->sms, 256), 256, 0, c->stream>>>(c->dp, c->dboxes, c->nbox, c->P,
+                                                                           face_set(c->Bf));
+  return cudaGetLastError() == cudaSuccess ? 0 : HARMRAD_E_CUDA;
+}
 template <int MET>
 int Run<MET>::faces(harmrad_ctx* c, bool fresh) {
   return c->real_size == 8 ? faces_impl<MET, double>(c, fresh) : faces_impl<MET, float>(c, fresh);

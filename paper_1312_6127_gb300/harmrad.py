@@ -20,10 +20,11 @@ PREC_FP64, PREC_SPLIT = 0, 1
 OPAC_CONST, OPAC_KRAMERS, OPAC_FIELD = 0, 1, 2
 INT_RK3, INT_IMEX2, INT_IMEX2B, INT_IMEX3 = 0, 1, 2, 3
 EQ_ENERGY, EQ_ENTROPY = 0, 1
+EMF_FLUXCT, EMF_UCT = 0, 1
 
 EXPORTS = [
     "harmrad_init", "harmrad_init_batch", "harmrad_destroy", "harmrad_set_opacity_field", "harmrad_set_prims",
-    "harmrad_set_prims_ghosts", "harmrad_get_prims",
+    "harmrad_set_prims_ghosts", "harmrad_get_prims", "harmrad_set_face_fields", "harmrad_get_face_fields",
     "harmrad_cfl_dt", "harmrad_step", "harmrad_step_host", "harmrad_get_stats",
     "harmrad_get_status", "harmrad_get_iters", "harmrad_compute_fluxes",
     "harmrad_zone_physics", "harmrad_zone_implicit", "harmrad_zone_implicit_full",
@@ -72,6 +73,7 @@ class Params(ctypes.Structure):
         ("precision", ctypes.c_int),
         ("integrator", ctypes.c_int),
         ("implicit_eq", ctypes.c_int),
+        ("emf", ctypes.c_int),
     ]
 
 
@@ -131,6 +133,8 @@ def load(path=LIB_PATH):
     L.harmrad_set_prims.argtypes = [vp, vp, ip]
     L.harmrad_set_prims_ghosts.argtypes = [vp, vp, ip]
     L.harmrad_get_prims.argtypes = [vp, vp, ip]
+    L.harmrad_set_face_fields.argtypes = [vp, vp, ip]
+    L.harmrad_get_face_fields.argtypes = [vp, vp, ip]
     L.harmrad_cfl_dt.argtypes = [vp, dp]
     L.harmrad_step.argtypes = [vp, ctypes.c_double]
     L.harmrad_step_host.argtypes = [vp, vp, vp, ctypes.c_double]
@@ -236,6 +240,32 @@ class Grid:
         P = np.ascontiguousarray(P, dtype=np.float64)
         _check(load().harmrad_set_prims_ghosts(self._h, P.ctypes.data_as(ctypes.c_void_p), 0),
                "set_prims_ghosts")
+
+    def face_shapes(self):
+        """Shapes [n3', n2', n1'] of the three face-field arrays (staggered field)."""
+        out = []
+        for d in range(3):
+            m = list(self.n)
+            if m[d] > 1:
+                m[d] += 1
+            out.append((m[2], m[1], m[0]))
+        return out
+
+    def set_face_fields(self, Bf):
+        """sqrt(-g) B^d on the d-faces: three arrays of face_shapes()."""
+        flat = np.concatenate([np.ascontiguousarray(b, dtype=np.float64).ravel() for b in Bf])
+        _check(load().harmrad_set_face_fields(self._h, flat.ctypes.data_as(ctypes.c_void_p), 0), "set_face_fields")
+
+    def get_face_fields(self):
+        shapes = self.face_shapes()
+        flat = np.empty(sum(int(np.prod(s)) for s in shapes))
+        _check(load().harmrad_get_face_fields(self._h, flat.ctypes.data_as(ctypes.c_void_p), 0), "get_face_fields")
+        out, off = [], 0
+        for s in shapes:
+            m = int(np.prod(s))
+            out.append(flat[off:off + m].reshape(s))
+            off += m
+        return out
 
     def set_opacity_field(self, K):
         """Per-zone absorption field K ([n3,n2,n1]; kappa_abs = kappa_scale K)."""

@@ -45,7 +45,7 @@ def base_params():
         gamma_rad_max=100.0, gamma_gas_max=50.0,
         floor_rho0=1e-10, floor_rho_pow=0.0, floor_u0=1e-12, floor_u_pow=0.0,
         bsq_rho_max=200.0, bsq_u_max=1e5, u_rho_max=1e10,
-        newton_max=20, newton_tol=1e-12, integrator=0, implicit_eq=0,
+        newton_max=20, newton_tol=1e-12, integrator=0, implicit_eq=0, emf=0,
     )
 
 
@@ -87,7 +87,7 @@ def _gaussian_torus(r, th):
     return np.exp(-((r - 15.0) / 4.0) ** 2 - (np.cos(th) / 0.3) ** 2)
 
 
-def torus(n=(64, 32, 16), seed=12345, b_background=0.0):
+def torus(n=(64, 32, 16), seed=12345, b_background=0.0, faces=False):
     """Seeded Kerr-Schild torus, a = 0.9375, r in [1.2, 50] log-spaced,
     theta concentrated toward the equator (h = 0.3):
     rho = max(G(r, theta) (1 + 0.02 sin phi_k), 1e-6 r^-1.5) with G a Gaussian
@@ -98,7 +98,12 @@ def torus(n=(64, 32, 16), seed=12345, b_background=0.0):
     electron scattering; B from A_phi ~ max(rho - 0.2, 0) scaled so that
     max p_gas / max p_mag = 100.  b_background > 0 adds the field of
     A_phi = b_background (r sin theta)^2 (a weak vertical field threading the
-    whole grid)."""
+    whole grid).  faces=True also returns the staggered field of the same
+    potential, sqrt(-g) B^d on the d-faces as (x-faces [n3, n2, n1+1],
+    y-faces [n3, n2+1, n1], z-faces [n3+1, n2, n1]): sqrt(-g) B^1 =
+    d A_phi / dx2 and sqrt(-g) B^2 = -d A_phi / dx1 by differences of the
+    corner values along the face, whose two-face averages are the
+    cell-centred B."""
     cfg = _ks_setup(n)
     n1, n2, n3 = n
     a, h = cfg["a_spin"], cfg["hslope"]
@@ -138,10 +143,12 @@ def torus(n=(64, 32, 16), seed=12345, b_background=0.0):
     P = np.zeros((NP, n3, n2, n1))
     P[RHO] = rho
     P[UU] = ug
+    Atot = scale * A
     if b_background > 0.0:
         Ab = b_background * (rf * np.sin(thf)) ** 2
         B1c = scale * B1c + (Ab[1:, :-1] + Ab[1:, 1:] - Ab[:-1, :-1] - Ab[:-1, 1:]) / (2 * cfg["dx"][1] * gdet)
         B2c = scale * B2c - (Ab[:-1, 1:] + Ab[1:, 1:] - Ab[:-1, :-1] - Ab[1:, :-1]) / (2 * cfg["dx"][0] * gdet)
+        Atot = Atot + Ab
         scale = 1.0
     P[B1] = (scale * B1c)[None, :, :]
     P[B2] = (scale * B2c)[None, :, :]
@@ -151,6 +158,12 @@ def torus(n=(64, 32, 16), seed=12345, b_background=0.0):
     cfg.update(a_rad=a_rad, opacity=OPAC_KRAMERS, kappa_abs0=kK, kappa_es0=0.4,
                T_kappa_min=1e-3 * T0,
                floor_rho0=1e-6, floor_rho_pow=-1.5, floor_u0=1e-8, floor_u_pow=-2.5)
+    if faces:
+        f1 = (Atot[1:, :] - Atot[:-1, :]) / cfg["dx"][1]           # [n2, n1+1]
+        f2 = -(Atot[:, 1:] - Atot[:, :-1]) / cfg["dx"][0]          # [n2+1, n1]
+        Bf = (np.broadcast_to(f1, (n3, n2, n1 + 1)).copy(), np.broadcast_to(f2, (n3, n2 + 1, n1)).copy(),
+              np.zeros((n3 + 1, n2, n1)))
+        return cfg, P, Bf
     return cfg, P
 
 

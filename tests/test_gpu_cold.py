@@ -5,7 +5,9 @@ kinetic energy of the motion, momentum-dominated radiation).
 
 - harmrad_zone_implicit (no explicit entropy) and the no-allocation entry
   solve every zone with the cold-MHD equations: method HARMRAD_ZONE_COLD,
-  u_g equal to the guess's, every primitive within 1e-12 of the oracle's;
+  u_g equal to the guess's, every primitive within 1e-10 of the oracle's
+  (both Newton solves stop once e_T < 1e-12, Sec. 4.10, which leaves their
+  roots up to about 1e-11 apart);
 - harmrad_zone_implicit_full with the true state's entropy solves the zones
   with the entropy equation first (HARMRAD_ZONE_ENTROPY), with an entropy no
   u_g > 0 reaches with the cold-MHD equations, and a zone whose radiation is
@@ -47,7 +49,7 @@ def test_cold_zones_match_oracle(B_amp):
     assert np.array_equal(Pg[:, UU], Ps[:, UU])
     err = max(_rel(Pg[k], ref[k][0]).max() for k in range(len(cases)))
     print("cold-MHD zones, B amplitude %.2f: worst relative error %.2e, e_T up to %.1e" % (B_amp, err, eT.max()))
-    assert err < 1e-12 and eT.max() < 1e-12
+    assert err < 1e-10 and eT.max() < 1e-12
 
 
 def test_cold_zones_static_entry():
@@ -74,7 +76,7 @@ def test_cold_zones_static_entry():
     meth, Pg = me.cpu().numpy(), Pout.cpu().numpy()
     assert np.all(meth == H.ZONE_COLD)
     err = max(_rel(Pg[k], O.implicit_zone(p, X, U[k], Ps[k], 0.1)[0]).max() for k in range(n))
-    assert err < 1e-12, err
+    assert err < 1e-10, err
 
 
 def test_backup_order_matches_oracle():
