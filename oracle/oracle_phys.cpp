@@ -105,12 +105,26 @@ static void ks_msp_gcov(const orc_params& p, const S X[4], S g[4][4]) {
     for (int n = 0; n < 4; ++n) g[m][n] = ks[m][n] * J[m] * J[n];
 }
 
-// Gauss-Jordan inverse with partial pivoting; returns the determinant.
-static double invert4(const double a_in[4][4], double inv[4][4]) {
+// Inverse of a symmetric 4x4 matrix by Gauss-Jordan elimination with partial
+// pivoting, after symmetric equilibration: with D = diag(1/sqrt(max_j
+// |a_ij|)), g^-1 = D (D g D)^-1 D and det g = det(D g D) / det(D)^2.  In the
+// internal coordinates the metric's entries span many decades (g_11 ~ r^2
+// dr/dx1^2 ~ 1e12 at r = 1e6 against g_00 ~ 1), and eliminating on the raw
+// entries leaves the small entries of the inverse (g^{t1} ~ 2/r^2) with a
+// relative error of order 1e-16 times that spread; on the equilibrated
+// matrix every entry of the inverse keeps round-off accuracy.  Returns the
+// determinant.
+static double invert4(const double g_in[4][4], double inv[4][4]) {
+  double D[4];
+  for (int i = 0; i < 4; ++i) {
+    double m = 0.0;
+    for (int j = 0; j < 4; ++j) m = std::max(m, std::fabs(g_in[i][j]));
+    D[i] = m > 0.0 ? 1.0 / std::sqrt(m) : 1.0;
+  }
   double a[4][8];
   for (int i = 0; i < 4; ++i)
     for (int j = 0; j < 4; ++j) {
-      a[i][j] = a_in[i][j];
+      a[i][j] = D[i] * g_in[i][j] * D[j];
       a[i][j + 4] = (i == j) ? 1.0 : 0.0;
     }
   double det = 1.0;
@@ -133,7 +147,8 @@ static double invert4(const double a_in[4][4], double inv[4][4]) {
     }
   }
   for (int i = 0; i < 4; ++i)
-    for (int j = 0; j < 4; ++j) inv[i][j] = a[i][j + 4];
+    for (int j = 0; j < 4; ++j) inv[i][j] = D[i] * a[i][j + 4] * D[j];
+  for (int i = 0; i < 4; ++i) det /= D[i] * D[i];
   return det;
 }
 

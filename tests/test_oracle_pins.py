@@ -47,6 +47,36 @@ def test_metric_inverse_and_gdet_closed_form():
         assert alpha == pytest.approx(1.0 / math.sqrt(1.0 + 2.0 * r / Sig), rel=1e-13)
 
 
+@pytest.mark.parametrize("a,h", [(0.9375, 0.3), (0.0, 1.0)])
+def test_inverse_metric_entries_closed_form(a, h):
+    """Every entry of g^{mu nu} against the textbook Kerr-Schild inverse
+    (g^tt = -(1 + 2r/S), g^tr = 2r/S, g^rr = Delta/S, g^rphi = a/S,
+    g^thth = 1/S, g^phph = 1/(S sin^2 th), S = r^2 + a^2 cos^2 th) divided by
+    the internal-coordinate Jacobians J_mu J_nu, each entry to 1e-13 of
+    itself, from the horizon out to r = 1e6 (the static atmosphere's radius,
+    where the covariant entries span thirteen decades)."""
+    p = O.make_params(ks_params(a=a, h=h))
+    for r in (1.2, 1.5, 3.0, 15.0, 50.0, 1e4, 1e6, 1.4e6):
+        for x2 in (0.07, 0.3, 0.5, 0.77):
+            gcov, gcon, gdet, alpha = O.metric(p, [0.0, math.log(r), x2, 0.3])
+            th = math.pi * x2 + 0.5 * (1 - h) * math.sin(2 * math.pi * x2)
+            S = r * r + a * a * math.cos(th) ** 2
+            D = r * r - 2 * r + a * a
+            J = [1.0, r, math.pi * (1 + (1 - h) * math.cos(2 * math.pi * x2)), 2 * math.pi]
+            ks = np.zeros((4, 4))
+            ks[0, 0] = -(1 + 2 * r / S)
+            ks[0, 1] = ks[1, 0] = 2 * r / S
+            ks[1, 1] = D / S
+            ks[1, 3] = ks[3, 1] = a / S
+            ks[2, 2] = 1 / S
+            ks[3, 3] = 1 / (S * math.sin(th) ** 2)
+            want = ks / np.outer(J, J)
+            nz = want != 0.0
+            err = np.abs(gcon[nz] - want[nz]) / np.abs(want[nz])
+            assert err.max() < 1e-13, (r, x2, err.max())
+            assert np.all(gcon[~nz] == 0.0) or np.abs(gcon[~nz]).max() < 1e-16 * np.abs(gcon).max()
+
+
 def test_ks_grr_vanishes_on_horizon():
     # g^{rr} = Delta/Sigma in Kerr-Schild; in code coordinates divided by (dr/dx1)^2.
     a = 0.9375
