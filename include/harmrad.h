@@ -315,6 +315,21 @@ int harmrad_zone_implicit_full(const harmrad_params* p, int n, const double* x, 
                                const double* Sstar, const double* Ps, const double* h, double* Pout,
                                double* eT, int* iters, unsigned char* method, void* stream);
 
+/* One Newton method of the implicit solve alone on n independent zones
+ * (device pointers; for testing each method against its restatement):
+ * method 0 PMHD from the gas of Ps, 1 URAD from R^t_nu of Ps, 2 PRAD from the
+ * radiation of Ps (Sec. 4.8-4.10), 3 the staged PMHD of Sec. 4.10 (one
+ * momentum-only step damped by 1/2, energy-only steps, then the full 4D
+ * Newton with its first step damped by 1/4, two-sided differences) from the
+ * gas of Ps with u_g from the explicit entropy Sstar (device, may be NULL).
+ * Pout[n][12]: the best iterate's primitives as its error function forms them
+ * (radiation through the TYPE2 limiter; Ps where no residual was finite),
+ * eT[n] its total error (inf if none), iters[n] the Newton steps.
+ * HARMRAD_E_ARG for another method or a per-zone opacity field. */
+int harmrad_zone_method(const harmrad_params* p, int n, const double* x, const double* Ustar,
+                        const double* Sstar, const double* Ps, const double* h, int method, double* Pout,
+                        double* eT, int* iters, void* stream);
+
 /* Same solve as harmrad_zone_implicit, for callers that cannot allocate device
  * memory: processes whose device memory is owned by another allocator (a
  * framework's caching pool, a fixed-budget service) and may not call

@@ -165,12 +165,14 @@ void   orc_implicit_zone(const orc_params* p, const double* x, const double* Ust
                          const double* Sstar, const double* Ps, double h, double* Pout,
                          orc_implicit_info* info);
 /* One Newton method alone on one zone (test hook): method 0 PMHD (guess the
- * gas of Ps), 1 URAD (guess R^t_nu of Ps), 2 PRAD (guess the radiation of Ps).
- * Writes the best iterate's prims (Ps if none), its e_T (inf if none) and the
- * Newton steps taken. */
+ * gas of Ps), 1 URAD (guess R^t_nu of Ps), 2 PRAD (guess the radiation of Ps),
+ * 3 staged PMHD (Sec. 4.10; guess the gas of Ps with u_g from the explicit
+ * entropy Sstar = sqrt(-g) S u^t when Sstar is not NULL).  Writes the best
+ * iterate's prims (Ps if none), its e_T (inf if none) and the Newton steps
+ * taken. */
 void   orc_method_zone(const orc_params* p, const double* x, const double* Ustar,
-                       const double* Ps, double h, int method, double* Pout,
-                       double* eT, int* iters);
+                       const double* Sstar, const double* Ps, double h, int method,
+                       double* Pout, double* eT, int* iters);
 /* Residual of the PMHD system at gas unknowns xg = (u_g, u~^i):
  * E[4] (gas rows), eT, eI.  Test hook. */
 void   orc_pmhd_residual(const orc_params* p, const double* x, const double* Ustar,

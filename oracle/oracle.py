@@ -128,7 +128,7 @@ def lib():
         L.orc_radiation_subdominant.argtypes = [pp, dp, dp, dp]
         L.orc_cold_allowed.argtypes = [pp, dp, dp, dp]
         L.orc_cold_allowed.restype = ctypes.c_int
-        L.orc_method_zone.argtypes = [pp, dp, dp, dp, ctypes.c_double, ctypes.c_int, dp, dp,
+        L.orc_method_zone.argtypes = [pp, dp, dp, dp, dp, ctypes.c_double, ctypes.c_int, dp, dp,
                                       ctypes.POINTER(ctypes.c_int)]
         L.orc_radiation_subdominant.restype = ctypes.c_int
         L.orc_pmhd_residual.argtypes = [pp, dp, dp, ctypes.c_double, dp, dp, dp, dp]
@@ -350,13 +350,18 @@ def implicit_zone(p, x, Ustar, Ps, h, Sstar=None):
     return out, info
 
 
-def method_zone(p, x, Ustar, Ps, h, method):
-    """One Newton method alone (0 PMHD, 1 URAD, 2 PRAD): (P, e_T, steps)."""
+def method_zone(p, x, Ustar, Ps, h, method, Sstar=None):
+    """One Newton method alone (0 PMHD, 1 URAD, 2 PRAD, 3 staged PMHD with
+    u_g from the explicit entropy Sstar if given): (P, e_T, steps)."""
     x, Us, Pz = _vec(x), _vec(Ustar), _vec(Ps)
     out = np.empty(NP)
     eT = ctypes.c_double()
     it = ctypes.c_int()
-    lib().orc_method_zone(ctypes.byref(p), _dp(x), _dp(Us), _dp(Pz), float(h), int(method), _dp(out),
+    sp = None
+    if Sstar is not None:
+        sv = ctypes.c_double(float(Sstar))
+        sp = ctypes.pointer(sv)
+    lib().orc_method_zone(ctypes.byref(p), _dp(x), _dp(Us), sp, _dp(Pz), float(h), int(method), _dp(out),
                           ctypes.byref(eT), ctypes.byref(it))
     return out, eT.value, it.value
 

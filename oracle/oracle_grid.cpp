@@ -1311,11 +1311,11 @@ void orc_implicit_zone(const orc_params* p, const double* x, const double* Ustar
   implicit_zone(*p, G, Ustar, Sstar, Ps, h, Pout, info, radiation_subdominant(G, Ustar, Ps));
 }
 
-void orc_method_zone(const orc_params* p, const double* x, const double* Ustar, const double* Ps, double h,
-                     int method, double* Pout, double* eT, int* iters) {
+void orc_method_zone(const orc_params* p, const double* x, const double* Ustar, const double* Sstar,
+                     const double* Ps, double h, int method, double* Pout, double* eT, int* iters) {
   Geom G;
   geom_at(*p, x[1], x[2], x[3], G);
-  method_zone(*p, G, Ustar, Ps, h, method, Pout, eT, iters);
+  method_zone(*p, G, Ustar, Sstar, Ps, h, method, Pout, eT, iters);
 }
 
 void orc_pmhd_residual(const orc_params* p, const double* x, const double* Ustar, double h,

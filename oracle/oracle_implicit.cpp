@@ -388,6 +388,118 @@ int newton_pmhd(const Sys& s, const double x0[4], Res& best) {
   return steps;
 }
 
+// One damped Newton step of the PMHD system on a subset of its unknowns
+// (Sec. 4.9-4.10, the staged scheme): the unknowns not in `mask` (bit j for
+// x_j) and their error rows drop out (identity row and column, zero error),
+// the Jacobian columns come from two-sided differences with the PMHD
+// offsets, and x_new = x - D J^-1 E.  Returns false if the system is
+// singular.
+bool pmhd_damped_step(const Sys& s, const double x[4], const Res& r, unsigned mask, double D, double eps,
+                      double xn[4]) {
+  const Geom& G = *s.G;
+  double usq = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) usq += G.gcov[i + 1][j + 1] * x[1 + i] * x[1 + j];
+  const double umag = std::max(1.0, std::sqrt(usq));
+  double J[4][4], E[4];
+  for (int j = 0; j < 4; ++j) {
+    if (!(mask >> j & 1u)) {
+      for (int i = 0; i < 4; ++i) J[i][j] = J[j][i] = i == j ? 1.0 : 0.0;
+      continue;
+    }
+    const double dj = (j == 0) ? eps * std::fabs(x[0]) : eps * umag / std::sqrt(G.gcov[j][j]);
+    double xp[4], xm[4];
+    for (int i = 0; i < 4; ++i) xp[i] = xm[i] = x[i];
+    xp[j] += dj;
+    xm[j] -= dj;
+    Res rp, rm;
+    pmhd_res(s, xp, rp);
+    pmhd_res(s, xm, rm);
+    for (int i = 0; i < 4; ++i)
+      if (mask >> i & 1u) J[i][j] = (rp.Eg[i] - rm.Eg[i]) / (2.0 * dj);
+  }
+  for (int i = 0; i < 4; ++i) E[i] = (mask >> i & 1u) ? r.Eg[i] : 0.0;
+  double dx[4];
+  if (!solve4(J, E, dx)) return false;
+  for (int i = 0; i < 4; ++i) xn[i] = x[i] - D * dx[i];
+  return true;
+}
+
+// Staged PMHD (Sec. 4.10), for zones whose radiation is extremely
+// sub-dominant, after the plain methods: stage 1, one momentum-only step
+// (u_g held) damped by D = 1/2; stage 2, energy-only steps (velocities held),
+// the first damped by 1/2, until the energy row's normalised error is below
+// the tolerance, stops falling, or newton_max steps; stage 3, the full 4D
+// Newton, its first step damped by 1/4, at most 40 steps, with the stopping
+// rules of the plain method.  Two-sided differences throughout.  A step that
+// leaves u_g < 0 sets it to |u_g|/2; the second such reset in stage 1 or 2
+// restores the prior iterate and ends the stage.  The lowest-e_T iterate of
+// all stages is kept.
+int newton_pmhd_staged(const Sys& s, const double x0[4], Res& best) {
+  const orc_params& p = *s.p;
+  double x[4] = {x0[0], x0[1], x0[2], x0[3]};
+  best.eT = HUGE_VAL;
+  best.ok = false;
+  int steps = 0;
+  double eps = 1e-8;
+  auto eval = [&](Res& r) {
+    pmhd_res(s, x, r);
+    if (r.ok && r.eT < best.eT) best = r;
+    return r.ok;
+  };
+  // stages 1 and 2
+  for (int stage = 1; stage <= 2; ++stage) {
+    const unsigned mask = stage == 1 ? 0xEu : 0x1u;
+    const int max_steps = stage == 1 ? 1 : p.newton_max;
+    int resets = 0, rises = 0;
+    double prev = HUGE_VAL;
+    for (int k = 0; k < max_steps; ++k) {
+      Res r;
+      if (!eval(r)) return steps;
+      if (stage == 2) {
+        if (r.eg[0] < p.newton_tol) break;
+        if (r.eg[0] >= prev && ++rises >= 5) break;
+        prev = r.eg[0];
+      }
+      if (r.eI < 1e-9) eps = 1e-10;
+      double xn[4];
+      if (!pmhd_damped_step(s, x, r, mask, k == 0 ? 0.5 : 1.0, eps, xn)) break;
+      ++steps;
+      if (xn[0] < 0.0) {
+        if (++resets >= 2) break;  // hold the prior iterate, next stage
+        xn[0] = 0.5 * std::fabs(xn[0]);
+      }
+      for (int i = 0; i < 4; ++i) x[i] = xn[i];
+    }
+  }
+  // stage 3: full 4D
+  History hs;
+  for (int k = 0;; ++k) {
+    Res r;
+    if (!eval(r)) break;
+    hs.eT[k] = r.eT;
+    hs.eI[k] = r.eI;
+    if (r.eT < p.newton_tol) break;
+    if (stalled(hs, k)) break;
+    if (k >= 40) break;
+    if (r.eI < 1e-9) eps = 1e-10;
+    double xn[4];
+    if (!pmhd_damped_step(s, x, r, 0xFu, k == 0 ? 0.25 : 1.0, eps, xn)) break;
+    if (xn[0] < 0.0) xn[0] = 0.5 * std::fabs(xn[0]);
+    bool tiny = true;
+    for (int i = 0; i < 4; ++i)
+      if (std::fabs(xn[i] - x[i]) > 10.0 * EPSM * std::fabs(x[i])) tiny = false;
+    for (int i = 0; i < 4; ++i) x[i] = xn[i];
+    ++steps;
+    if (tiny) {
+      Res rf;
+      eval(rf);
+      break;
+    }
+  }
+  return steps;
+}
+
 // URAD Newton (Sec. 4.8-4.10): one-sided FD Jacobian, tolerance 1e-9, at most
 // 20 x 6 gas inversions, inversion failures inside the Jacobian retried with
 // larger offsets up to 0.3.
@@ -572,8 +684,25 @@ void build_sys(const orc_params& p, const Geom& G, const double* Ustar, double h
 
 }  // namespace
 
-void method_zone(const orc_params& p, const Geom& G, const double* Ustar, const double* Ps, double h,
-                 int method, double* Pout, double* eT, int* iters) {
+// Guess of the staged PMHD (Sec. 4.10): the gas of the lowest-error earlier
+// solution if its e_T < 1e-4, else of P_s; u_g then from the specific
+// entropy of U*, s_gas = S* / (rho0 u^t)*, at the density of P_s (where the
+// explicit entropy S* is given).
+void staged_guess(const orc_params& p, const Sys& s, const double* Ustar, const double* Sstar, const double* Ps,
+                  const Res& best, double xs[4]) {
+  const double* Pg = (best.ok && best.eT < 1e-4) ? best.P : Ps;
+  for (int i = 0; i < 4; ++i) xs[i] = Pg[UU + i];
+  if (Sstar && std::isfinite(*Sstar) && Ustar[RHO] != 0.0) {
+    const double n = 1.0 / (p.gam - 1.0);
+    const double sg = *Sstar / Ustar[RHO];
+    const double pg = std::exp((sg + (n + 1.0) * std::log(Ps[RHO])) / n);
+    if (std::isfinite(pg) && pg > 0.0) xs[0] = pg / (p.gam - 1.0);
+  }
+  (void)s;
+}
+
+void method_zone(const orc_params& p, const Geom& G, const double* Ustar, const double* Sstar, const double* Ps,
+                 double h, int method, double* Pout, double* eT, int* iters) {
   Sys s;
   build_sys(p, G, Ustar, h, s);
   Res b;
@@ -584,9 +713,15 @@ void method_zone(const orc_params& p, const Geom& G, const double* Ustar, const 
     double Tc[4], Rc[4];
     tt_row(p, G, Ps, Tc, Rc, nullptr, nullptr);
     *iters = newton_urad(s, Rc, Ps, b);
-  } else {
+  } else if (method == 2) {
     double x0[4] = {Ps[ER], Ps[UR1], Ps[UR2], Ps[UR3]};
     *iters = newton_prad(s, x0, Ps, b);
+  } else {
+    Res none;
+    none.ok = false;
+    double xs[4];
+    staged_guess(p, s, Ustar, Sstar, Ps, none, xs);
+    *iters = newton_pmhd_staged(s, xs, b);
   }
   *eT = b.ok ? b.eT : HUGE_VAL;
   for (int q = 0; q < NP; ++q) Pout[q] = b.ok ? b.P[q] : Ps[q];
@@ -701,7 +836,7 @@ bool try_cold(const orc_params& p, const Geom& G, const Sys& s, const double* Us
 // leaves e_T > 1e-9; PRAD if both do; the lowest-error solution is kept.  With
 // the radiation extremely sub-dominant URAD goes first, from P_s, then PRAD,
 // and PMHD (which would lose that radiation in the gas's round-off) is not
-// tried.  When no energy-based method reaches e_T <= 1e-7 and the explicit
+// tried; if they leave e_T >= 1e-9, the staged PMHD follows.  When no energy-based method reaches e_T <= 1e-7 and the explicit
 // entropy S* is given (RK3), the entropy-based PMHD follows (Sec. 4.11); its
 // solution counts as a retry method's.  e_T > 1e-7 after that marks the zone
 // for the neighbour-average back-up.  A solution that hit the TYPE2
@@ -793,6 +928,17 @@ void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, cons
     info->iters_urad += newton_prad(s, xq, Pq, bq);
     if (bq.ok && (!best.ok || bq.eT < best.eT)) {
       best = bq;
+      method = ORC_OK_URAD;
+    }
+  }
+  if (subdominant && !(best.ok && best.eT < 1e-9)) {
+    // staged PMHD (Sec. 4.10), for the extremely sub-dominant radiation only
+    double xs[4];
+    staged_guess(p, s, Ustar, Sstar, Ps, best, xs);
+    Res bs;
+    info->iters_urad += newton_pmhd_staged(s, xs, bs);
+    if (bs.ok && (!best.ok || bs.eT < best.eT)) {
+      best = bs;
       method = ORC_OK_URAD;
     }
   }

@@ -48,8 +48,8 @@ bool cold_allowed(const Geom& G, const double* Ustar, const double* Ps);
 void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, const double* Sstar,
                    const double* Ps,
                    double h, double* Pout, orc_implicit_info* info, bool subdominant);
-void method_zone(const orc_params& p, const Geom& G, const double* Ustar, const double* Ps, double h,
-                 int method, double* Pout, double* eT, int* iters);
+void method_zone(const orc_params& p, const Geom& G, const double* Ustar, const double* Sstar, const double* Ps,
+                 double h, int method, double* Pout, double* eT, int* iters);
 void pmhd_residual_public(const orc_params& p, const Geom& G, const double* Ustar, double h,
                           const double* xg, double* E4, double* eT, double* eI);
 

@@ -876,6 +876,31 @@ int harmrad_zone_implicit(const harmrad_params* prm, int n, const double* x, con
   return zone_implicit_impl(prm, n, x, Us, nullptr, Ps, h, Pout, eT, iters, method, stream);
 }
 
+int harmrad_zone_method(const harmrad_params* prm, int n, const double* x, const double* Us, const double* Sstar,
+                        const double* Ps, const double* h, int method, double* Pout, double* eT, int* iters,
+                        void* stream) {
+  if (!prm || n < 0 || method < 0 || method > 3 ||
+      (n > 0 && (!x || !Us || !Ps || !h || !Pout || !eT || !iters)))
+    return HARMRAD_E_ARG;
+  DevParams dp;
+  BoxGeo bg;
+  int rc = fill_physics(prm, dp);
+  if (!rc) rc = fill_geometry(prm, bg);
+  if (rc) return rc;
+  if (dp.opacity == HARMRAD_OPAC_FIELD) return HARMRAD_E_ARG;
+  if (n == 0) return HARMRAD_OK;
+  int dev, sms;
+  HR_CHECK(cudaGetDevice(&dev));
+  HR_CHECK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  cudaStream_t st = (cudaStream_t)stream;
+  int r = dp.metric == 1
+              ? hr::Run<hr::KS>::zone_method(dp, bg, n, x, Us, Sstar, Ps, h, method, Pout, eT, iters, st, sms)
+              : hr::Run<hr::MINK>::zone_method(dp, bg, n, x, Us, Sstar, Ps, h, method, Pout, eT, iters, st, sms);
+  if (r < 0) return r;
+  HR_CHECK(cudaStreamSynchronize(st));
+  return HARMRAD_OK;
+}
+
 int harmrad_zone_implicit_full(const harmrad_params* prm, int n, const double* x, const double* Us,
                                const double* Sstar, const double* Ps, const double* h, double* Pout,
                                double* eT, int* iters, unsigned char* method, void* stream) {

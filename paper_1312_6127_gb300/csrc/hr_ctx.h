@@ -124,6 +124,9 @@ struct Run {
   // a set of the primitives), then the ghost faces and the cell-centred B of
   // the active zones from the evolved faces
   static int init_faces(harmrad_ctx* c, bool from_centres);
+  static int zone_method(const DevParams& dp, const BoxGeo& bg, int n, const double* x, const double* Us,
+                         const double* Ss, const double* Ps, const double* h, int method, double* Pout,
+                         double* eT, int* iters, cudaStream_t st, int sms);
   static int zone_implicit(const DevParams& dp, const BoxGeo& bg, int n, const double* x,
                            const double* Us, const double* Ss, const double* Ps, const double* h,
                            double* Pout, double* eT, int* iters, unsigned char* method, cudaStream_t st,

@@ -51,6 +51,7 @@ template <typename T = double>
 struct ImpResT {
   T Eg[4], Er[4];
   T eT, eI;
+  T eg0;  // normalised error of the gas energy (or entropy) row alone
   int negE;
   bool ok;
 };
@@ -116,6 +117,7 @@ __device__ __forceinline__ void normalise(const ImpSysT<MET, T>& s, const T Tc[4
     eg[0] = eS;
     er[0] = T(0.0);
   }
+  r.eg0 = eg[0];
   if (s.cold) {  // cold MHD: energy and entropy ignored, the mean of the momentum rows
     T cT = T(0.0), cI = T(0.0);
 #pragma unroll
@@ -472,6 +474,117 @@ __device__ int newton_pmhd(const DevParams& p, const ImpSys<MET>& s, const doubl
         for (int i = 0; i < 4; ++i) best_x[i] = x[i];
         if (best_st) *best_st = stf;
       }
+      break;
+    }
+  }
+  return steps;
+}
+
+// One damped Newton step of the PMHD system on a subset of its unknowns
+// (the staged scheme of Sec. 4.9-4.10): unknowns not in `mask` (bit j for x_j)
+// and their error rows drop out (identity row and column, zero error); the
+// Jacobian columns come from two-sided differences with the PMHD offsets;
+// x_new = x - D J^-1 E.  Returns false if the system is singular.
+template <int MET>
+__device__ bool pmhd_damped_step(const DevParams& p, const ImpSys<MET>& s, const double x[4], const ImpRes& r,
+                                 unsigned mask, double D, double eps, double xn[4]) {
+  const double umag = fmax(1.0, sqrt(s.g.sq3(x[1], x[2], x[3])));
+  double J[4][4], E[4];
+#pragma unroll 1
+  for (int j = 0; j < 4; ++j) {
+    if (!(mask >> j & 1u)) {
+      for (int i = 0; i < 4; ++i) J[i][j] = J[j][i] = i == j ? 1.0 : 0.0;
+      continue;
+    }
+    const double dj = (j == 0) ? eps * fabs(x[0]) : eps * umag / sqrt(s.g.gdd(j));
+    double xp[4], xm[4];
+    for (int i = 0; i < 4; ++i) xp[i] = xm[i] = x[i];
+    xp[j] += dj;
+    xm[j] -= dj;
+    ImpRes rp, rm;
+    pmhd_res<MET>(p, s, xp, rp, nullptr, false);
+    pmhd_res<MET>(p, s, xm, rm, nullptr, false);
+    for (int i = 0; i < 4; ++i)
+      if (mask >> i & 1u) J[i][j] = (rp.Eg[i] - rm.Eg[i]) / (2.0 * dj);
+  }
+  for (int i = 0; i < 4; ++i) E[i] = (mask >> i & 1u) ? r.Eg[i] : 0.0;
+  double dx[4];
+  if (!solve4(J, E, dx)) return false;
+  for (int i = 0; i < 4; ++i) xn[i] = x[i] - D * dx[i];
+  return true;
+}
+
+// Staged PMHD (Sec. 4.10) for zones whose radiation is extremely
+// sub-dominant, after the plain methods: stage 1, one momentum-only step
+// (u_g held) damped by 1/2; stage 2, energy-only steps (velocities held), the
+// first damped by 1/2, until the energy row's normalised error is below the
+// tolerance, has risen five times, or newton_max steps; stage 3, the full 4D
+// Newton, its first step damped by 1/4, at most 40 steps, with the stopping
+// rules of the plain method.  Two-sided differences throughout.  u_g < 0
+// after a step becomes |u_g|/2; the second such reset in stage 1 or 2 keeps
+// the prior iterate and ends the stage.  best_x / best_eT: the lowest-e_T
+// iterate of all stages (inf if no residual was finite).  Returns the steps.
+template <int MET>
+__device__ int newton_pmhd_staged(const DevParams& p, const ImpSys<MET>& s, const double x0[4], double best_x[4],
+                                  double* best_eT) {
+  double x[4] = {x0[0], x0[1], x0[2], x0[3]};
+  *best_eT = HUGE_VAL;
+  int steps = 0;
+  double eps = 1e-8;
+  auto eval = [&](ImpRes& r) {
+    pmhd_res<MET>(p, s, x, r, nullptr, true);
+    if (r.ok && r.eT < *best_eT) {
+      *best_eT = r.eT;
+      for (int i = 0; i < 4; ++i) best_x[i] = x[i];
+    }
+    return r.ok;
+  };
+#pragma unroll 1
+  for (int stage = 1; stage <= 2; ++stage) {
+    const unsigned mask = stage == 1 ? 0xEu : 0x1u;
+    const int max_steps = stage == 1 ? 1 : p.newton_max;
+    int resets = 0, rises = 0;
+    double prev = HUGE_VAL;
+#pragma unroll 1
+    for (int k = 0; k < max_steps; ++k) {
+      ImpRes r;
+      if (!eval(r)) return steps;
+      if (stage == 2) {
+        if (r.eg0 < p.newton_tol) break;
+        if (r.eg0 >= prev && ++rises >= 5) break;
+        prev = r.eg0;
+      }
+      if (r.eI < 1e-9) eps = 1e-10;
+      double xn[4];
+      if (!pmhd_damped_step<MET>(p, s, x, r, mask, k == 0 ? 0.5 : 1.0, eps, xn)) break;
+      ++steps;
+      if (xn[0] < 0.0) {
+        if (++resets >= 2) break;
+        xn[0] = 0.5 * fabs(xn[0]);
+      }
+      for (int i = 0; i < 4; ++i) x[i] = xn[i];
+    }
+  }
+  Hist hs = {HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, 0};
+#pragma unroll 1
+  for (int k = 0;; ++k) {
+    ImpRes r;
+    if (!eval(r)) break;
+    if (r.eT < p.newton_tol) break;
+    if (stalled(hs, k, r.eT, r.eI)) break;
+    if (k >= 40) break;
+    if (r.eI < 1e-9) eps = 1e-10;
+    double xn[4];
+    if (!pmhd_damped_step<MET>(p, s, x, r, 0xFu, k == 0 ? 0.25 : 1.0, eps, xn)) break;
+    if (xn[0] < 0.0) xn[0] = 0.5 * fabs(xn[0]);
+    bool tiny = true;
+    for (int i = 0; i < 4; ++i)
+      if (fabs(xn[i] - x[i]) > 10.0 * 2.220446049250313e-16 * fabs(x[i])) tiny = false;
+    for (int i = 0; i < 4; ++i) x[i] = xn[i];
+    ++steps;
+    if (tiny) {
+      ImpRes rf;
+      eval(rf);
       break;
     }
   }

@@ -1016,7 +1016,7 @@ __device__ __forceinline__ double zone_tau(const DevParams& p, const Geo<MET, do
 template <int MET>
 __device__ int retry_sequence(const DevParams& p, const Geo<MET, double>& g, const ImpSys<MET>& s,
                               const double Ps[NPR], const double px[4], double peT, double tau, double Pn[NPR],
-                              double* eT_out, int* steps_out) {
+                              double* eT_out, int* steps_out, bool subdom = false, double Sst = NAN) {
   const bool pfin = isfinite(peT);
   double Pb[NPR];
   if (pfin) {  // the PMHD iterate as its error function left it (TYPE2 radiation)
@@ -1074,6 +1074,27 @@ __device__ int retry_sequence(const DevParams& p, const Geo<MET, double>& g, con
       beT = qeT;
     }
   }
+  double sx[4];
+  if (subdom && !(beT < 1e-9)) {
+    // staged PMHD (Sec. 4.10): guessed from the gas of the best earlier
+    // solution if its e_T < 1e-4 (else P_s), u_g from the specific entropy
+    // S* / (rho0 u^t)* at the density of P_s where S* is given
+    const double* gsrc = Ps;
+    if (best >= 0 && beT < 1e-4) gsrc = best == 0 ? Pb : (best == 1 ? ugas : qgas);
+    double xs[4] = {gsrc[UU], gsrc[U1], gsrc[U2], gsrc[U3]};
+    if (isfinite(Sst) && s.Dlab != 0.0) {
+      const double n = 1.0 / (p.gam - 1.0);
+      const double sg = Sst / (s.Dlab * g.gdet);
+      const double pg = exp((sg + (n + 1.0) * log(Ps[RHO])) / n);
+      if (isfinite(pg) && pg > 0.0) xs[0] = pg / (p.gam - 1.0);
+    }
+    double seT;
+    steps += newton_pmhd_staged<MET>(p, s, xs, sx, &seT);
+    if (isfinite(seT) && (best < 0 || seT < beT)) {
+      best = 3;
+      beT = seT;
+    }
+  }
   int method = ST_URAD;
   if (best == 0) {
     pmhd_final<MET>(p, s, px, Pn);
@@ -1086,6 +1107,8 @@ __device__ int retry_sequence(const DevParams& p, const Geo<MET, double>& g, con
   } else if (best == 2) {
     for (int q = 0; q < 5; ++q) Pn[q] = qgas[q];
     for (int q = 0; q < 4; ++q) Pn[ER + q] = qx[q];
+  } else if (best == 3) {
+    pmhd_final<MET>(p, s, sx, Pn);
   } else {
     for (int q = 0; q < NPR; ++q) Pn[q] = Ps[q];
     method = ST_BACKUP;
@@ -1741,7 +1764,7 @@ __global__ void __launch_bounds__(128) k_retry(DevParams p, const BoxGeo* __rest
       steps = 0;
       method = ST_BACKUP;
     } else {
-      method = retry_sequence<MET>(p, g, s, Ps, px, peT, tau, Pn, &eT, &steps);
+      method = retry_sequence<MET>(p, g, s, Ps, px, peT, tau, Pn, &eT, &steps, subdom, Sst);
     }
     // no energy-based solution: the entropy, then the cold-MHD equations
     int by = 0;

@@ -402,7 +402,8 @@ __global__ void k_zone_implicit(DevParams p, BoxGeo bg, int n, const double* __r
     }
     double bx[4] = {0.0, 0.0, 0.0, 0.0}, beT = HUGE_VAL;
     // extremely sub-dominant radiation (Sec. 4.10): no PMHD attempt
-    int steps = radiation_subdominant<MET>(g, Ust, P0) ? 0 : newton_pmhd<MET>(p, s, x0, bx, &beT);
+    const bool subdom = radiation_subdominant<MET>(g, Ust, P0);
+    int steps = subdom ? 0 : newton_pmhd<MET>(p, s, x0, bx, &beT);
     double Pn[NPR];
     int method = 0;
     double eT = beT;
@@ -411,10 +412,11 @@ __global__ void k_zone_implicit(DevParams p, BoxGeo bg, int n, const double* __r
     } else {
       int rs;
       const double tau = zone_tau<MET>(p, g, bg.dx, P0, 1.0);
-      method = retry_sequence<MET>(p, g, s, P0, bx, beT, tau, Pn, &eT, &rs);
+      const double sz = Sst ? Sst[z] : NAN;
+      method = retry_sequence<MET>(p, g, s, P0, bx, beT, tau, Pn, &eT, &rs, subdom, sz);
       steps += rs;
       if (method == ST_BACKUP) {  // the entropy (S* given), then the cold-MHD equations
-        const int by = backup_equations<MET>(p, g, s, Ust, P0, Sst ? Sst[z] : NAN, true, tau, Pn, &eT, &steps);
+        const int by = backup_equations<MET>(p, g, s, Ust, P0, sz, true, tau, Pn, &eT, &steps);
         if (by) method = by;
       }
     }
@@ -423,6 +425,81 @@ __global__ void k_zone_implicit(DevParams p, BoxGeo bg, int n, const double* __r
     if (itso) itso[z] = steps;
     if (meth) meth[z] = (unsigned char)method;
   }
+}
+
+// One Newton method alone on each of n independent zones (test hook, the
+// counterpart of the oracle's method hook): 0 PMHD from the gas of Ps, 1 URAD
+// from R^t_nu of Ps, 2 PRAD from the radiation of Ps, 3 staged PMHD from the
+// gas of Ps with u_g from the explicit entropy Sst (if given).  Writes the
+// best iterate's primitives as its error function forms them (TYPE2
+// radiation; Ps if none), its e_T (inf if none) and the Newton steps.
+template <int MET>
+__global__ void k_zone_method(DevParams p, BoxGeo bg, int n, const double* __restrict__ x,
+                              const double* __restrict__ Us, const double* __restrict__ Ps,
+                              const double* __restrict__ hh, const double* __restrict__ Sst, int method,
+                              double* Pout, double* eTo, int* itso) {
+  for (int z = blockIdx.x * blockDim.x + threadIdx.x; z < n; z += gridDim.x * blockDim.x) {
+    const Geo<MET, double> g = make_geo<MET, double>(p, x[4 * z + 1], x[4 * z + 2]);
+    double Ust[NPR], P0[NPR], Pn[NPR];
+    for (int q = 0; q < NPR; ++q) {
+      Ust[q] = Us[NPR * z + q];
+      P0[q] = Pn[q] = Ps[NPR * z + q];
+    }
+    ImpSys<MET> s;
+    build_sys<MET>(p, g, Ust, hh[z], 1.0, s);
+    double eT = HUGE_VAL;
+    int steps = 0;
+    if (method == 0 || method == 3) {
+      double x0[4] = {P0[UU], P0[U1], P0[U2], P0[U3]}, bx[4];
+      if (method == 3 && Sst && isfinite(Sst[z]) && s.Dlab != 0.0) {
+        const double nn = 1.0 / (p.gam - 1.0);
+        const double pg = exp((Sst[z] / (s.Dlab * g.gdet) + (nn + 1.0) * log(P0[RHO])) / nn);
+        if (isfinite(pg) && pg > 0.0) x0[0] = pg / (p.gam - 1.0);
+      }
+      steps = method == 0 ? newton_pmhd<MET>(p, s, x0, bx, &eT) : newton_pmhd_staged<MET>(p, s, x0, bx, &eT);
+      if (isfinite(eT)) {
+        ImpRes rr;
+        ImpState st;
+        pmhd_res<MET>(p, s, bx, rr, &st, false);
+        Pn[RHO] = st.rho;
+        for (int c = 0; c < 4; ++c) Pn[UU + c] = bx[c];
+        for (int c = 0; c < 4; ++c) Pn[ER + c] = st.Pr[c];
+        for (int c = 0; c < 3; ++c) Pn[B1 + c] = s.B[c];
+      }
+    } else {
+      double gas[5] = {P0[RHO], P0[UU], P0[U1], P0[U2], P0[U3]}, bx[4], bgas[5];
+      if (method == 1) {
+        double urc[4], urv[4], gr;
+        fourvel<MET, double>(g, P0[UR1], P0[UR2], P0[UR3], urc, urv, &gr);
+        const double e43 = (4.0 / 3.0) * P0[ER];
+        double xr[4];
+        xr[0] = e43 * urc[0] * urv[0] + P0[ER] * (1.0 / 3.0);
+        for (int c = 1; c < 4; ++c) xr[c] = e43 * urc[0] * urv[c];
+        steps = newton_urad<MET>(p, s, xr, gas, bx, bgas, &eT);
+        if (isfinite(eT)) rad_invert<MET>(p, g, bx, 2, Pn + ER);
+      } else {
+        double xq[4] = {P0[ER], P0[UR1], P0[UR2], P0[UR3]};
+        steps = newton_rad<MET, true>(p, s, xq, gas, bx, bgas, &eT);
+        if (isfinite(eT))
+          for (int c = 0; c < 4; ++c) Pn[ER + c] = bx[c];
+      }
+      if (isfinite(eT)) {
+        for (int c = 0; c < 5; ++c) Pn[c] = bgas[c];
+        for (int c = 0; c < 3; ++c) Pn[B1 + c] = s.B[c];
+      }
+    }
+    for (int q = 0; q < NPR; ++q) Pout[NPR * z + q] = Pn[q];
+    eTo[z] = eT;
+    itso[z] = steps;
+  }
+}
+
+template <int MET>
+int Run<MET>::zone_method(const DevParams& dp, const BoxGeo& bg, int n, const double* x, const double* Us,
+                          const double* Ss, const double* Ps, const double* h, int method, double* Pout,
+                          double* eT, int* iters, cudaStream_t st, int sms) {
+  k_zone_method<MET><<<grid_for(n, sms, 128), 128, 0, st>>>(dp, bg, n, x, Us, Ps, h, Ss, method, Pout, eT, iters);
+  return cudaGetLastError() == cudaSuccess ? 1 : HARMRAD_E_CUDA;
 }
 
 template <int MET>

@@ -178,7 +178,8 @@ __global__ void k_zi_urad(hr::DevParams p, hr::BoxGeo bg, const double* __restri
     double Pn[NPR], eT;
     int steps;
     const double tau = zone_tau<MET>(p, g, bg.dx, P0, 1.0);
-    int method = retry_sequence<MET>(p, g, s, P0, bx, beT, tau, Pn, &eT, &steps);
+    const bool subdom = radiation_subdominant<MET>(g, Us + NPR * (size_t)z, P0);
+    int method = retry_sequence<MET>(p, g, s, P0, bx, beT, tau, Pn, &eT, &steps, subdom);
     if (method == ST_BACKUP) {  // the cold-MHD equations (no explicit entropy here)
       const int by = backup_equations<MET>(p, g, s, Us + NPR * (size_t)z, P0, NAN, false, tau, Pn, &eT, &steps);
       if (by) method = by;

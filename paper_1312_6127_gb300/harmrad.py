@@ -27,7 +27,7 @@ EXPORTS = [
     "harmrad_set_prims_ghosts", "harmrad_get_prims", "harmrad_set_face_fields", "harmrad_get_face_fields",
     "harmrad_cfl_dt", "harmrad_step", "harmrad_step_host", "harmrad_get_stats",
     "harmrad_get_status", "harmrad_get_iters", "harmrad_compute_fluxes",
-    "harmrad_zone_physics", "harmrad_zone_implicit", "harmrad_zone_implicit_full",
+    "harmrad_zone_physics", "harmrad_zone_implicit", "harmrad_zone_implicit_full", "harmrad_zone_method",
     "harmrad_zone_implicit_static",
     "harmrad_profile_step", "harmrad_autotune", "harmrad_get_tuning", "harmrad_set_tuning",
     "harmrad_adjoint_enable", "harmrad_step_adjoint", "harmrad_adjoint_set_input",
@@ -145,6 +145,7 @@ def load(path=LIB_PATH):
     L.harmrad_zone_physics.argtypes = [pp, ip, vp, vp, vp, vp, vp, vp, vp]
     L.harmrad_zone_implicit.argtypes = [pp, ip, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.harmrad_zone_implicit_full.argtypes = [pp, ip, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.harmrad_zone_method.argtypes = [pp, ip, vp, vp, vp, vp, vp, ip, vp, vp, vp, vp]
     L.harmrad_zone_implicit_static.argtypes = [pp, ip, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     L.harmrad_profile_step.argtypes = [vp, ctypes.c_double, ctypes.POINTER(KernelTimes)]
     L.harmrad_adjoint_enable.argtypes = [vp, ip]
@@ -517,3 +518,20 @@ def zone_implicit(cfg, x, Ustar, Ps, h, Sstar=None):
                                                  vp(Pout), vp(eT), vp(it), vp(meth), _stream_ptr(None)),
                "zone_implicit_full")
     return Pout.cpu().numpy(), eT.cpu().numpy(), it.cpu().numpy(), meth.cpu().numpy()
+
+
+def zone_method(cfg, x, Ustar, Ps, h, method, Sstar=None):
+    """One Newton method alone on n zones (0 PMHD, 1 URAD, 2 PRAD, 3 staged
+    PMHD): (P[n][12], e_T[n], steps[n]) as numpy arrays."""
+    import torch
+    n = len(x)
+    xd, Ud, Pd, hd = _dev(x), _dev(Ustar), _dev(Ps), _dev(np.broadcast_to(h, (n,)))
+    Sd = _dev(np.broadcast_to(Sstar, (n,))) if Sstar is not None else None
+    Pout = torch.empty((n, 12), dtype=torch.float64, device="cuda")
+    eT = torch.empty(n, dtype=torch.float64, device="cuda")
+    it = torch.empty(n, dtype=torch.int32, device="cuda")
+    p = make_params(cfg)
+    vp = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None
+    _check(load().harmrad_zone_method(ctypes.byref(p), n, vp(xd), vp(Ud), vp(Sd), vp(Pd), vp(hd), int(method),
+                                      vp(Pout), vp(eT), vp(it), _stream_ptr(None)), "zone_method")
+    return Pout.cpu().numpy(), eT.cpu().numpy(), it.cpu().numpy()
