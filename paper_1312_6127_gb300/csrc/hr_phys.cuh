@@ -254,6 +254,14 @@ __device__ __forceinline__ void bvec(const Geo<MET, R>& g, const R ucon[4], cons
 // n = 1/(Gamma - 1); the conserved entropy sqrt(-g) S u^t is sqrt(-g) rho0 u^t s.
 template <typename R>
 __device__ __forceinline__ R entropy_per_baryon(const DevParams& p, R rho, R ug) {
+  if constexpr (std::is_same<R, double>::value) {
+    // n = 3/2: p^n / rho^(n+1) = x sqrt(x) / rho with x = p / rho, one
+    // logarithm (FP64 only: the product would leave FP32's range first)
+    if (p.gam == 5.0 / 3.0) {
+      const R x = R(2.0 / 3.0) * ug / rho;
+      return log(x * sqrt(x) / rho);
+    }
+  }
   const R n = R(1.0 / (p.gam - 1.0));
   return n * log(R(p.gam - 1.0) * ug) - (n + R(1)) * log(rho);
 }

@@ -16,9 +16,20 @@ from tests.test_oracle_atmosphere import STEPS, measures
 pytestmark = pytest.mark.gpu
 
 
+def ug_bound(P, steps):
+    """Parity bound of u_g after `steps` steps.  The gas energy row of U is
+    sqrt(-g)(T^t_t + rho0 u^t): for gas nearly at rest at r = 1e6 it is the
+    difference of two terms of size rho0 (the rest mass and its potential
+    energy, 1 - 1/alpha ~ 1e-6) against u_g ~ 2.5e-7 rho0, so one evaluation
+    resolves u_g only to about eps rho0 / u_g (4e-10 here); the implicit solve
+    of each of the 3 sub-steps inherits that."""
+    return 3 * steps * 2.220446049250313e-16 * float(np.max(P[W.RHO] / P[W.UU]))
+
+
 @pytest.mark.parametrize("f", [0.1, 1.0])
 def test_atmosphere_matches_oracle(f):
-    """Ten steps with the oracle's time steps: every zone within 1e-8.  The
+    """Ten steps with the oracle's time steps: every zone within 1e-8 but u_g,
+    which is within ug_bound (the conditioning of its energy equation).  The
     two CFL steps agree to 1e-9: at r = 1e6 the metric components in the
     internal chart reach 1e12, and the signal speeds carry that round-off."""
     cfg, P, info = W.static_atmosphere(f, flux_ratio=0.99)
@@ -39,9 +50,11 @@ def test_atmosphere_matches_oracle(f):
     # Ebar by about eps / (1 - F/E))
     er = max(point_errors(cfg, [0.0, cfg["x0"][0] + (i + 0.5) * cfg["dx"][0], 0.5, 0.5], A[:, 0, 0, i],
                           R[:, 0, 0, i], cfg["gam"], rad_conserved=True)[8:].max() for i in range(cfg["n"][0]))
-    print("f = %.1f, 10 steps: per-zone error, gas %.2e, radiation (conserved) %.2e, radiation primitives %.2e"
-          % (f, e[:8].max(), er, e[8:].max()))
-    assert e[:8].max() < 1e-8 and er < 1e-8
+    ub = ug_bound(P, 10)
+    gas = np.delete(e[:8], W.UU, axis=0)
+    print("f = %.1f, 10 steps: per-zone error, gas but u_g %.2e, u_g %.2e (bound %.1e), radiation (conserved) "
+          "%.2e, radiation primitives %.2e" % (f, gas.max(), e[W.UU].max(), ub, er, e[8:].max()))
+    assert gas.max() < 1e-8 and e[W.UU].max() < ub and er < 1e-8
 
 
 @pytest.mark.parametrize("f", [0.1, 1.0])
@@ -79,7 +92,7 @@ def test_atmosphere_first_step_matches_oracle(f):
           % (f, eu, esm, ef, es, ["%.0e" % v for v in eF.reshape(12, -1).max(axis=1)],
              ["%.0e" % v for v in worst], int(np.argmax(e.max(axis=0)))))
     assert eF.max() < 1e-12
-    assert e.max() < 1e-10
+    assert np.delete(e, W.UU, axis=0).max() < 1e-10 and e[W.UU].max() < ug_bound(P, 1)
 
 
 @pytest.mark.parametrize("f", [0.1, 0.5, 1.0])
