@@ -656,8 +656,9 @@ __device__ __forceinline__ void face_flux(const DevParams& p, const Geo<MET, R>&
                                           unsigned* code = nullptr, R* fs = nullptr, R* gas = nullptr) {
   R sL[4], sR[4];
   unsigned cL = 0, cR = 0;
-  face_speeds<MET, R>(p, g, d + 1, dxd, kL, ks, PL, sL, code ? &cL : nullptr);
-  face_speeds<MET, R>(p, g, d + 1, dxd, kR, ks, PR, sR, code ? &cR : nullptr);
+  R lL[2], lR[2];  // Lorentz factors of the states, for face_accum
+  face_speeds<MET, R>(p, g, d + 1, dxd, kL, ks, PL, sL, code ? &cL : nullptr, lL);
+  face_speeds<MET, R>(p, g, d + 1, dxd, kR, ks, PR, sR, code ? &cR : nullptr, lR);
   R cmaxg = fmax(R(0), fmax(sL[1], sR[1]));
   R cming = -fmin(R(0), fmin(sL[0], sR[0]));
   R cmaxr = fmax(R(0), fmax(sL[3], sR[3]));
@@ -706,8 +707,8 @@ __device__ __forceinline__ void face_flux(const DevParams& p, const Geo<MET, R>&
 #pragma unroll
   for (int q = 0; q < NPR; ++q) out[q] = R(0);
   if (fs) *fs = R(0);
-  face_accum<MET, R>(p, g, d + 1, PL, fLg, uLg, fLr, uLr, out, fs);
-  face_accum<MET, R>(p, g, d + 1, PR, fRg, uRg, fRr, uRr, out, fs);
+  face_accum<MET, R>(p, g, d + 1, PL, fLg, uLg, fLr, uLr, out, fs, lL);
+  face_accum<MET, R>(p, g, d + 1, PR, fRg, uRg, fRr, uRr, out, fs, lR);
   out[B1 + d] = R(0);
   *smax = fmax(fmax(cmaxg, cming), fmax(cmaxr, cminr));
   if (gas) {

@@ -212,6 +212,23 @@ __device__ __forceinline__ Geo<MET, R> make_geo(const DevParams& p, R x1, R x2) 
 
 // ------------------------------------------------------------- 4-vectors
 // u^t = gamma/alpha, u^i = u~^i - gamma alpha g^{ti}, gamma^2 = 1 + g_ij u~^i u~^j.
+// The same with the Lorentz factor gamma of (q1, q2, q3) already known.
+template <int MET, typename R>
+__device__ __forceinline__ void fourvel_g(const Geo<MET, R>& g, R q1, R q2, R q3, R gm, R ucon[4], R ucov[4]) {
+  if constexpr (MET == MINK) {
+    ucon[0] = gm;
+    ucon[1] = q1;
+    ucon[2] = q2;
+    ucon[3] = q3;
+  } else {
+    ucon[0] = gm * g.ialpha;
+    ucon[1] = q1 - gm * g.alpha * g.G01;
+    ucon[2] = q2;
+    ucon[3] = q3;
+  }
+  g.lower(ucon, ucov);
+}
+
 template <int MET, typename R>
 __device__ __forceinline__ void fourvel(const Geo<MET, R>& g, R q1, R q2, R q3, R ucon[4],
                                         R ucov[4], R* gamma) {
@@ -390,12 +407,18 @@ __device__ __forceinline__ void face_state(const DevParams& p, const Geo<MET, R>
 
 // Gas and radiation signal speeds (vmin, vmax) of one reconstructed state;
 // dxd is the cell size along d and kf the per-zone opacity of the state's cell.
+// lor (optional) returns the gas and radiation Lorentz factors for
+// face_accum.  b^2 = (B^i B_i + (B^i u_i)^2) / (u^t)^2 (the identity behind
+// b^t = B^i u_i, b^i = (B^i + b^t u^i)/u^t), without forming b^mu.
 template <int MET, typename R>
 __device__ __forceinline__ void face_speeds(const DevParams& p, const Geo<MET, R>& g, int d, R dxd,
-                                            R kf, R ks, const R P[NPR], R sp[4], unsigned* code = nullptr) {
-  R ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq;
+                                            R kf, R ks, const R P[NPR], R sp[4], unsigned* code = nullptr,
+                                            R* lor = nullptr) {
+  R ucon[4], ucov[4], gm;
   fourvel<MET, R>(g, P[U1], P[U2], P[U3], ucon, ucov, &gm);
-  bvec<MET, R>(g, ucon, ucov, P[B1], P[B2], P[B3], bcon, bcov, &bsq);
+  const R Bu = P[B1] * ucov[1] + P[B2] * ucov[2] + P[B3] * ucov[3];
+  const R iut = g.alpha / gm;
+  const R bsq = (g.sq3(P[B1], P[B2], P[B3]) + Bu * Bu) * iut * iut;
   const R rho = P[RHO], ug = P[UU];
   const R pg = R(p.gam - 1.0) * ug;
   const R w = rho + ug + pg;
@@ -407,6 +430,10 @@ __device__ __forceinline__ void face_speeds(const DevParams& p, const Geo<MET, R
   char_speeds<MET, R>(g, ucon, cms2, d, &sp[0], &sp[1]);
   R urc[4], urv[4], gr;
   fourvel<MET, R>(g, P[UR1], P[UR2], P[UR3], urc, urv, &gr);
+  if (lor) {
+    lor[0] = gm;
+    lor[1] = gr;
+  }
   R kabs, ksca;
   opacity<R>(p, rho, ug, kf, &kabs, &ksca, ks);
   R tau = (kabs + ksca) * sqrt(g.gdd(d)) * dxd;
@@ -427,9 +454,14 @@ __device__ __forceinline__ void face_speeds(const DevParams& p, const Geo<MET, R
 template <int MET, typename R>
 __device__ __forceinline__ void face_accum(const DevParams& p, const Geo<MET, R>& g, int d,
                                            const R P[NPR], R aFg, R aUg, R aFr, R aUr, R out[NPR],
-                                           R* fs = nullptr) {
+                                           R* fs = nullptr, const R* lor = nullptr) {
   R ucon[4], ucov[4], gm, bcon[4], bcov[4], bsq;
-  fourvel<MET, R>(g, P[U1], P[U2], P[U3], ucon, ucov, &gm);
+  if (lor) {
+    gm = lor[0];
+    fourvel_g<MET, R>(g, P[U1], P[U2], P[U3], gm, ucon, ucov);
+  } else {
+    fourvel<MET, R>(g, P[U1], P[U2], P[U3], ucon, ucov, &gm);
+  }
   const R iut = g.alpha / gm;
   bvec_iut<MET, R>(g, ucon, ucov, iut, P[B1], P[B2], P[B3], bcon, bcov, &bsq);
   const R rho = P[RHO], ug = P[UU];
@@ -454,7 +486,8 @@ __device__ __forceinline__ void face_accum(const DevParams& p, const Geo<MET, R>
     out[4 + i] += gd * (aFg * f + aUg * P[B1 + i - 1]);
   }
   R urc[4], urv[4], gr;
-  fourvel<MET, R>(g, P[UR1], P[UR2], P[UR3], urc, urv, &gr);
+  if (lor) fourvel_g<MET, R>(g, P[UR1], P[UR2], P[UR3], lor[1], urc, urv);
+  else fourvel<MET, R>(g, P[UR1], P[UR2], P[UR3], urc, urv, &gr);
   const R E = P[ER];
   const R e43 = R(4.0 / 3.0) * E, e13 = E * R(1.0 / 3.0);
 #pragma unroll
