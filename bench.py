@@ -9,13 +9,14 @@ state is resident in HBM; its working set (primitives, fluxes, scratch) is far
 larger than the 129 MB L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|split]
-                  [--workload torus|batch48] [--impl harmrad|reference]
+                  [--workload torus|torus_uct|batch48] [--impl harmrad|reference]
 
 Prints one JSON line.  The default run (FP64 torus, one GPU) also times split
-precision on the same torus ("split", with its conserved totals against FP64)
-and the batch of 48 uneven boxes ("batch48"), each with its own clocks and
-roofline.  The reference arm times the FP64 CPU oracle (the plain
-restatement of the method used by the tests) on the host cores.
+precision on the same torus ("split", with its conserved totals against FP64),
+the batch of 48 uneven boxes ("batch48") and the torus with the staggered
+field and 4-state EMF ("uct"), each with its own clocks and roofline.  The
+reference arm times the FP64 CPU oracle (the plain restatement of the method
+used by the tests) on the host cores.
 """
 import argparse
 import hashlib
@@ -203,14 +204,19 @@ def make_context(args, H, W, workload, prec, stream, rank, integ):
     workload text, counters key)."""
     n = tuple(int(x) for x in args.size.split(","))
     pname = "split" if prec == H.PREC_SPLIT else "fp64"
-    if workload == "torus":
-        cfg, P = W.torus(n, seed=12345 + rank)
+    if workload in ("torus", "torus_uct"):
+        cfg, P, Bf = W.torus(n, seed=12345 + rank, faces=True)
         cfg["integrator"] = integ
+        uct = workload == "torus_uct"
+        cfg["emf"] = H.EMF_UCT if uct else H.EMF_FLUXCT
         g = H.Grid(cfg, precision=prec, stream=stream)
         g.set_prims(P)
+        if uct:
+            g.set_face_fields(Bf)
         g.cfg_init, g.P_init = cfg, P
-        wl = "KS torus a=0.9375 %dx%dx%d (PPM, LAXF, flux-CT, PMHD/URAD)" % n
-        return g, n[0] * n[1] * n[2], wl, (list(n), pname)
+        wl = "KS torus a=0.9375 %dx%dx%d (PPM, LAXF, %s, PMHD/URAD)" % (n + ("staggered B, 4-state EMF" if uct
+                                                                             else "flux-CT",))
+        return g, n[0] * n[1] * n[2], wl, (list(n), pname + ("_uct" if uct else ""))
     cfgs, Ps, Ks = W.box_batch(seed=4242 + rank)
     cfgs = [dict(c, integrator=integ) for c in cfgs]
     g = H.Batch(cfgs, precision=prec, stream=stream)
@@ -342,9 +348,10 @@ def main():
     ap.add_argument("--impl", default="harmrad", choices=["harmrad", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "split"])
     ap.add_argument("--size", default="256,128,64")
-    ap.add_argument("--workload", default="torus", choices=["torus", "batch48"],
-                    help="torus: the Kerr-Schild torus (default); batch48: 48 uneven Minkowski "
-                         "boxes with a per-zone absorption field in one batched context")
+    ap.add_argument("--workload", default="torus", choices=["torus", "torus_uct", "batch48"],
+                    help="torus: the Kerr-Schild torus (default, flux-CT); torus_uct: the same torus with "
+                         "the staggered field and 4-state EMF; batch48: 48 uneven Minkowski boxes with a "
+                         "per-zone absorption field in one batched context")
     ap.add_argument("--integrator", default="rk3", choices=list(INTEGRATORS),
                     help="time integrator (Sec. 4.1): the paper's RK3 or one of its IMEX schemes")
     ap.add_argument("--no-e2e", action="store_true")
@@ -352,7 +359,8 @@ def main():
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the split-precision and batch48 sub-measurements of the default run")
+                    help="skip the split-precision, batch48 and staggered-field sub-measurements of the "
+                         "default run")
     args = ap.parse_args()
     ws, rank, local = dist_setup()
     if args.impl == "reference":
@@ -404,12 +412,14 @@ def main():
         e2e = {"value": nact * args.steps * ws / te, "unit": UNIT, "h2d_bytes_per_step": nbytes,
                "d2h_bytes_per_step": nbytes}
 
-    # the default run also measures split precision on the same torus and the
-    # batch of 48 boxes (same steps and warm-up, each timed on its own)
+    # the default run also measures split precision on the same torus, the
+    # batch of 48 boxes and the torus with the staggered field (same steps and
+    # warm-up, each timed on its own)
     extras = {}
     default_run = (args.workload == "torus" and prec == H.PREC_FP64 and integ == 0 and ws == 1)
     if default_run and not args.no_extras:
-        for name, wk, pr in (("split", "torus", H.PREC_SPLIT), ("batch48", "batch48", H.PREC_FP64)):
+        for name, wk, pr in (("split", "torus", H.PREC_SPLIT), ("batch48", "batch48", H.PREC_FP64),
+                             ("uct", "torus_uct", H.PREC_FP64)):
             gx, nx, wlx, keyx = make_context(args, H, W, wk, pr, stream, rank, integ)
             tx = gx.tuning() if args.no_autotune else gx.autotune(reps=1)
             msx, clkx = time_steps(gx, args, stream, None, local)
@@ -424,8 +434,9 @@ def main():
                 sub["roofline"], ktx = kernel_roofline(gx, nx, keyx, integ, peak_tf, peak_note, msx,
                                                        args.steps)
                 sub["kernel_ms"] = {k: round(v[0], 4) for k, v in ktx.items()}
-            if name == "split":
+            if name in ("split", "uct"):
                 sub["vs_fp64"] = value and sub["value"] / value
+            if name == "split":
                 sub["conserved_totals_vs_fp64"] = split_total_errors(H, g, gx, args.steps)
             extras[name] = sub
             del gx

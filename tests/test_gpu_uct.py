@@ -6,7 +6,8 @@ Sec. 4.2 steps viii-x) on the CUDA step, against the oracle:
   face fields within 1e-10 of the field scale;
 - the Kerr-Schild torus with its potential's face field: 1e-10 after one step,
   1e-8 after ten (zones that took URAD or the back-up on either side excluded,
-  as in the flux-CT parity tests), faces alike;
+  as in the flux-CT parity tests), faces alike; one IMEX2 and one IMEX3 step
+  at 1e-10;
 - the face divergence keeps its initial value to round-off over 20 steps of
   the torus on the GPU;
 - a batch of boxes initialised from cell-centred fields equals its single-grid
@@ -87,6 +88,24 @@ def test_torus_matches_oracle(steps, tol):
           % (steps, int(bad.sum()), bad.size, e[:, ~bad].max(), ef))
     assert (~bad).mean() > 0.9
     assert e[:, ~bad].max() < tol and ef < tol
+
+
+@pytest.mark.parametrize("integrator", [W.IMEX2, W.IMEX3])
+def test_torus_imex_matches_oracle(integrator):
+    """The face fields take the IMEX brackets' combinations (Sec. 4.1): one
+    IMEX step of the torus against the oracle, 1e-10 per zone and face."""
+    cfg, P, Bf = W.torus((64, 32, 16), seed=12345, faces=True)
+    cfg.update(emf=H.EMF_UCT, integrator=integrator)
+    g, o = pair(cfg, P, Bf)
+    d = o.cfl_dt()
+    o.step(d)
+    g.step(d)
+    bad = (o.status() != 0) | (g.status() != 0)
+    e = zone_errors(cfg, g.get_prims(), o.get_prims())
+    ef = face_error(g.get_face_fields(), o.get_face_fields())
+    print("UCT torus, IMEX %d, 1 step: excluded zones %d, worst zone %.2e, faces %.2e"
+          % (integrator, int(bad.sum()), e[:, ~bad].max(), ef))
+    assert (~bad).mean() > 0.9 and e[:, ~bad].max() < 1e-10 and ef < 1e-10
 
 
 def test_face_divergence_on_gpu():
