@@ -158,6 +158,12 @@ int fill_physics(const harmrad_params* p, DevParams& d) {
   d.integrator = p->integrator;
   if (p->emf != 0 && p->emf != 1) return HARMRAD_E_ARG;
   d.emf = p->emf;
+  d.gm1f = (float)(d.gam - 1.0);
+  d.ymaxf = (float)d.ymax_rad;
+  d.Tminf = (float)d.Tmin;
+  d.kabs0f = (float)d.kabs0;
+  d.kes0f = (float)d.kes0;
+  d.aradf = (float)d.a_rad;
   return HARMRAD_OK;
 }
 

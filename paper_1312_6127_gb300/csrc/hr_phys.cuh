@@ -40,6 +40,9 @@ struct DevParams {
   int integrator;  // 0 RK3, 1 IMEX2, 2 IMEX2B, 3 IMEX3 (Sec. 4.1)
   int implicit_eq;  // 0 energy equations (entropy as back-up, RK3), 1 entropy in every zone
   int emf;          // 0 flux-CT, 1 staggered field with the 4-state upwind EMF
+  // FP32 copies of the parameters the FP32 tangent pass reads (converted once
+  // on the host, not per use on the device)
+  float gm1f, ymaxf, Tminf, kabs0f, kes0f, aradf;
   // branch signature (a test instrument; null unless enabled): per cell a
   // 64-bit word into which every branch decision of the step is folded
   unsigned long long* sig;

@@ -106,22 +106,27 @@ __device__ __forceinline__ void fourvel_t(const GeoF<MET>& g, F1 q1, F1 q2, F1 q
   g.lower(ucon, ucov);
 }
 
-// Column j of the PMHD Jacobian dE_gas/dx at x.  Rt64: R^t_nu of the FP64
-// error function at the same x (its values); Sys: the zone's implicit system
-// (ImpSys: rho0 u^t, B, the step h, opacity inputs).  Returns false if a
-// value is not finite.
-template <int MET, class Sys>
-__device__ __forceinline__ bool pmhd_jac_column(const DevParams& p, const Sys& s, const GeoF<MET>& g,
-                                                const double x[4], const double Rt64[4], int j, float col[4]) {
+// FP32 inputs of the tangent passes of one Jacobian, converted once: the
+// unknowns x, R^t_nu of the FP64 error function (values), and the zone's
+// rho0 u^t, 1/(rho0 u^t), B, step h and opacity inputs.
+struct TanIn {
+  float x[4], rt[4], Dlab, iDlab, B[3], h, ks, kf;
+};
+
+// Column j of the PMHD Jacobian dE_gas/dx at x (inputs in ti).  Returns false
+// if a value is not finite.
+template <int MET>
+__device__ __forceinline__ bool pmhd_jac_column(const DevParams& p, const TanIn& ti, const GeoF<MET>& g, int j,
+                                                float col[4]) {
   F1 X[4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i) X[i] = F1{(float)x[i], i == j ? 1.0f : 0.0f};
-  const float gm1 = (float)(p.gam - 1.0);
+  for (int i = 0; i < 4; ++i) X[i] = F1{ti.x[i], i == j ? 1.0f : 0.0f};
+  const float gm1 = p.gm1f;
   F1 ucon[4], ucov[4], gm;
   fourvel_t<MET>(g, X[1], X[2], X[3], ucon, ucov, &gm);
   const F1 iut = (MET == MINK ? 1.0f : g.alpha) / gm;
-  const F1 rho = (float)s.Dlab * iut;
-  const float B1 = (float)s.B[0], B2 = (float)s.B[1], B3 = (float)s.B[2];
+  const F1 rho = ti.Dlab * iut;
+  const float B1 = ti.B[0], B2 = ti.B[1], B3 = ti.B[2];
   F1 bcon[4], bcov[4];
   const F1 bt = B1 * ucov[1] + B2 * ucov[2] + B3 * ucov[3];
   bcon[0] = bt;
@@ -139,7 +144,7 @@ __device__ __forceinline__ bool pmhd_jac_column(const DevParams& p, const Sys& s
   // R^t_nu = R*^t_nu - (T^t_nu(x) - T*^t_nu): FP64 value, derivative -dT
   F1 Rt[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) Rt[k] = F1{(float)Rt64[k], -Tc[k].d};
+  for (int k = 0; k < 4; ++k) Rt[k] = F1{ti.rt[k], -Tc[k].d};
   // TYPE2 M1 inversion (Sec. 4.6)
   F1 Erad, Ut[3];
   if constexpr (MET == MINK) {
@@ -155,7 +160,7 @@ __device__ __forceinline__ bool pmhd_jac_column(const DevParams& p, const Sys& s
     Ut[2] = a * (g.G13 * Rt[1] + g.G33 * Rt[3]);
   }
   const F1 Utsq = g.sq3(Ut[0], Ut[1], Ut[2]);
-  const float ymax = (float)p.ymax_rad;
+  const float ymax = p.ymaxf;
   F1 y;
   if (Erad.v > 0.0f) {
     // y = U~^2 / E_rad^2 from the ratios (E_rad^2 can underflow in FP32)
@@ -177,31 +182,31 @@ __device__ __forceinline__ bool pmhd_jac_column(const DevParams& p, const Sys& s
   F1 urc[4], urv[4], gr;
   fourvel_t<MET>(g, f * Ut[0], f * Ut[1], f * Ut[2], urc, urv, &gr);
   // gas temperature T = (gamma-1) u_g u^t / (rho0 u^t)
-  const F1 Tg = (gm1 * (float)s.iDlab) * (X[0] * ucon[0]);
+  const F1 Tg = (gm1 * ti.iDlab) * (X[0] * ucon[0]);
   // opacities (opacity_ks)
-  const float ks = (float)s.ks;
+  const float ks = ti.ks;
   F1 kabs;
   if (p.opacity == 2) {
-    kabs = fc(ks * (float)s.kf);
+    kabs = fc(ks * ti.kf);
   } else if (p.opacity == 1) {
-    const float Tmin = (float)p.Tmin;
+    const float Tmin = p.Tminf;
     const F1 Tcl = Tg.v > Tmin ? Tg : fc(Tmin);
     const F1 t35 = frsqrt(Tcl) / (Tcl * Tcl * Tcl);  // T^-3.5 without forming T^7
-    kabs = (ks * (float)p.kabs0) * (rho * rho) * t35;
+    kabs = (ks * p.kabs0f) * (rho * rho) * t35;
   } else {
-    kabs = (ks * (float)p.kabs0) * rho;
+    kabs = (ks * p.kabs0f) * rho;
   }
-  const F1 ksca = (ks * (float)p.kes0) * rho;
+  const F1 ksca = (ks * p.kes0f) * rho;
   // four-force (four_force_rad)
   const F1 T2 = Tg * Tg;
-  const F1 lam = kabs * (float)p.a_rad * (T2 * T2);
+  const F1 lam = kabs * p.aradf * (T2 * T2);
   const F1 uru = urv[0] * ucon[0] + urv[1] * ucon[1] + urv[2] * ucon[2] + urv[3] * ucon[3];
   const F1 c1 = (4.0f / 3.0f) * E * uru, c2 = E * (1.0f / 3.0f);
   const F1 uRu = c1 * uru - c2;
   const F1 kt = kabs + ksca;
   const F1 A = -(kt * c1);
   const F1 C = -(kt * c2 + lam + ksca * uRu);
-  const float h = (float)s.h;
+  const float h = ti.h;
   bool ok = true;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
@@ -217,11 +222,24 @@ template <int MET, class Sys>
 __device__ __forceinline__ bool pmhd_jacobian_fp32(const DevParams& p, const Sys& s, const double x[4],
                                                    const double Rt64[4], double J[4][4]) {
   const GeoF<MET> g(s.g);
+  TanIn ti;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    ti.x[i] = (float)x[i];
+    ti.rt[i] = (float)Rt64[i];
+  }
+  ti.Dlab = (float)s.Dlab;
+  ti.iDlab = (float)s.iDlab;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) ti.B[i] = (float)s.B[i];
+  ti.h = (float)s.h;
+  ti.ks = (float)s.ks;
+  ti.kf = (float)s.kf;
   bool ok = true;
 #pragma unroll 1
   for (int j = 0; j < 4; ++j) {
     float col[4];
-    ok = pmhd_jac_column<MET, Sys>(p, s, g, x, Rt64, j, col) && ok;
+    ok = pmhd_jac_column<MET>(p, ti, g, j, col) && ok;
     // column j written through compile-time indices
 #pragma unroll
     for (int c = 0; c < 4; ++c)
