@@ -74,7 +74,7 @@ template <int MET>
 int face_ghosts(harmrad_ctx* c) {
   for (int d = 0; d < 3; ++d) {
     k_face_ghosts<MET><<<grid_for(c->maxcell, c->sms, 256), 256, 0, c->stream>>>(c->dp, c->dboxes, c->nbox, c->P,
-                                                                                 face_set(c->Bf), d);
+                                                                                 face_set(c->Bf), d, c->geotab);
     mark(c, HARMRAD_K_CT);
   }
   return 3;
@@ -189,7 +189,7 @@ int faces_impl(harmrad_ctx* c, bool fresh) {
     nk += 2;
   }
   if (p.emf == 1) {  // staggered field: the 4-state upwind EMFs on the edges
-    k_vel<MET, R><<<grid_for(c->maxcell, c->sms, 256), 256, 0, st>>>(p, bt, nb, c->P, (R*)c->vel);
+    k_vel<MET, R><<<grid_for(c->maxcell, c->sms, 256), 256, 0, st>>>(p, bt, nb, c->P, (R*)c->vel, c->geotab);
     mark(c, HARMRAD_K_CT);
     ++nk;
     for (int a = 0; a < 3; ++a)
@@ -202,7 +202,7 @@ int faces_impl(harmrad_ctx* c, bool fresh) {
         });
         k_uct_emf<MET, R><<<grid_for(we, c->sms, 128), 128, 0, st>>>(
             p, bt, nb, face_set(c->Bf), (const R*)c->vel, (const R*)c->gsp[a], (const R*)c->gsp[b],
-            (R*)c->emf3[3 - a - b], a, b);
+            (R*)c->emf3[3 - a - b], a, b, c->geotab);
         mark(c, HARMRAD_K_CT);
         ++nk;
       }
@@ -506,11 +506,11 @@ template <int MET>
 int Run<MET>::init_faces(harmrad_ctx* c, bool from_centres) {
   fill_ghost_cells(c);
   if (from_centres)
-    k_faces_from_centres<MET><<<grid_for(c->maxcell, c->sms, 256), 256, 0, c->stream>>>(c->dp, c->dboxes, c->nbox,
-                                                                                        c->P, face_set(c->Bf));
+    k_faces_from_centres<MET><<<grid_for(c->maxcell, c->sms, 256), 256, 0, c->stream>>>(
+        c->dp, c->dboxes, c->nbox, c->P, face_set(c->Bf), c->geotab);
   face_ghosts<MET>(c);
   k_centre_B<MET><<<grid_for(c->maxact, c->sms, 256), 256, 0, c->stream>>>(c->dp, c->dboxes, c->nbox, c->P,
-                                                                           face_set(c->Bf));
+                                                                           face_set(c->Bf), c->geotab);
   return cudaGetLastError() == cudaSuccess ? 0 : HARMRAD_E_CUDA;
 }
 template <int MET>

@@ -36,6 +36,28 @@ __device__ __forceinline__ double gdet_at(const DevParams& p, double x1, double 
   }
 }
 
+// sqrt(-g) at a cell position (q0, q1) of the grid (ghosts included) whose
+// x1 (f0) and/or x2 (f1) coordinate sits on the cell's lower face: from the
+// Kerr-Schild metric tables (centres, x1 faces, x2 faces) where the context
+// has them, else from the closed form.
+template <int MET>
+__device__ __forceinline__ double gdet_pos(const DevParams& p, const double* geo, const BoxGeo& bx, bool f0, bool f1,
+                                           int q0, int q1) {
+  f0 = f0 && bx.n[0] > 1;
+  f1 = f1 && bx.n[1] > 1;
+  if constexpr (MET == KS) {
+    if (geo && bx.goff >= 0 && !(f0 && f1)) {
+      const GeoTab T = geotab(geo, bx);
+      if (f0) return __ldg(T.F0 + 13 * T.sF0 + gidx_f0(bx, q0, q1));
+      if (f1) return __ldg(T.F1 + 13 * T.sF1 + gidx_f1(bx, q0, q1));
+      return __ldg(T.C + 13 * T.sC + gidx_c(bx, q0, q1));
+    }
+  }
+  const double x1 = f0 ? bx.x0[0] + q0 * bx.dx[0] : xcen(bx, 0, q0);
+  const double x2 = f1 ? bx.x0[1] + q1 * bx.dx[1] : xcen(bx, 1, q1);
+  return gdet_at<MET>(p, x1, x2);
+}
+
 __device__ __forceinline__ bool periodic_dir(const BoxGeo& bx, int d) {
   return bx.bc[2 * d] == 0 && bx.bc[2 * d + 1] == 0;
 }
@@ -58,7 +80,7 @@ struct FaceSet {
 // array on the outermost layer.  Run after the ghost fill of P.
 template <int MET>
 __global__ void k_face_ghosts(DevParams p, const BoxGeo* __restrict__ boxes, int nbox, const double* __restrict__ P0,
-                              FaceSet F, int d) {
+                              FaceSet F, int d, const double* __restrict__ geo) {
   for (int bi = 0; bi < nbox; ++bi) {
     const BoxGeo& bx = boxes[bi];
     const double* P = P0 + 12 * bx.coff;
@@ -85,13 +107,13 @@ __global__ void k_face_ghosts(DevParams p, const BoxGeo* __restrict__ boxes, int
         Bf[t] = Bf[cell_index(bx, w[0], w[1], w[2])];
         continue;
       }
-      const double bt = gdet_at<MET>(p, xcen(bx, 0, ii[0]), xcen(bx, 1, ii[1])) * P[(B1 + d) * bx.ntot + t];
+      const double bt = gdet_pos<MET>(p, geo, bx, false, false, ii[0], ii[1]) * P[(B1 + d) * bx.ntot + t];
       if (bx.n[d] == 1 || ii[d] == -bx.ng[d]) {
         Bf[t] = bt;
       } else {
         int m[3] = {ii[0], ii[1], ii[2]};
         m[d] -= 1;
-        Bf[t] = 0.5 * (gdet_at<MET>(p, xcen(bx, 0, m[0]), xcen(bx, 1, m[1])) * P[(B1 + d) * bx.ntot + t - sd] + bt);
+        Bf[t] = 0.5 * (gdet_pos<MET>(p, geo, bx, false, false, m[0], m[1]) * P[(B1 + d) * bx.ntot + t - sd] + bt);
       }
     }
   }
@@ -102,7 +124,7 @@ __global__ void k_face_ghosts(DevParams p, const BoxGeo* __restrict__ boxes, int
 // fill of P; k_face_ghosts and k_centre_B follow.
 template <int MET>
 __global__ void k_faces_from_centres(DevParams p, const BoxGeo* __restrict__ boxes, int nbox,
-                                     const double* __restrict__ P0, FaceSet F) {
+                                     const double* __restrict__ P0, FaceSet F, const double* __restrict__ geo) {
   for (int bi = 0; bi < nbox; ++bi) {
     const BoxGeo& bx = boxes[bi];
     const double* P = P0 + 12 * bx.coff;
@@ -113,14 +135,14 @@ __global__ void k_faces_from_centres(DevParams p, const BoxGeo* __restrict__ box
       r /= bx.N[0];
       ii[1] = (int)(r % bx.N[1]) - bx.ng[1];
       ii[2] = (int)(r / bx.N[1]) - bx.ng[2];
-      const double gt = gdet_at<MET>(p, xcen(bx, 0, ii[0]), xcen(bx, 1, ii[1]));
+      const double gt = gdet_pos<MET>(p, geo, bx, false, false, ii[0], ii[1]);
       for (int d = 0; d < 3; ++d) {
         const double bt = gt * P[(B1 + d) * bx.ntot + t];
         double v = bt;
         if (bx.n[d] > 1 && ii[d] > -bx.ng[d]) {
           int m[3] = {ii[0], ii[1], ii[2]};
           m[d] -= 1;
-          v = 0.5 * (gdet_at<MET>(p, xcen(bx, 0, m[0]), xcen(bx, 1, m[1])) * P[(B1 + d) * bx.ntot + t - bx.str[d]] + bt);
+          v = 0.5 * (gdet_pos<MET>(p, geo, bx, false, false, m[0], m[1]) * P[(B1 + d) * bx.ntot + t - bx.str[d]] + bt);
         }
         F.f[d][bx.coff + t] = v;
       }
@@ -131,7 +153,7 @@ __global__ void k_faces_from_centres(DevParams p, const BoxGeo* __restrict__ box
 // Cell-centred B of the active zones from their faces.
 template <int MET>
 __global__ void k_centre_B(DevParams p, const BoxGeo* __restrict__ boxes, int nbox, double* __restrict__ P0,
-                           FaceSet F) {
+                           FaceSet F, const double* __restrict__ geo) {
   for (int bi = 0; bi < nbox; ++bi) {
     const BoxGeo& bx = boxes[bi];
     double* P = P0 + 12 * bx.coff;
@@ -142,7 +164,7 @@ __global__ void k_centre_B(DevParams p, const BoxGeo* __restrict__ boxes, int nb
       const int j = (int)(r % bx.n[1]);
       const int k = (int)(r / bx.n[1]);
       const long long t = cell_index(bx, i, j, k);
-      const double ig = 1.0 / gdet_at<MET>(p, xcen(bx, 0, i), xcen(bx, 1, j));
+      const double ig = 1.0 / gdet_pos<MET>(p, geo, bx, false, false, i, j);
       for (int d = 0; d < 3; ++d) {
         const double* Bf = F.f[d] + bx.coff;
         const double c = bx.n[d] > 1 ? 0.5 * (Bf[t] + Bf[t + bx.str[d]]) : Bf[t];
@@ -155,7 +177,7 @@ __global__ void k_centre_B(DevParams p, const BoxGeo* __restrict__ boxes, int nb
 // Lab-frame 3-velocity v^i = u^i / u^t of every cell, ghosts included.
 template <int MET, typename R>
 __global__ void k_vel(DevParams p, const BoxGeo* __restrict__ boxes, int nbox, const double* __restrict__ P0,
-                      R* __restrict__ V0) {
+                      R* __restrict__ V0, const double* __restrict__ geo) {
   for (int bi = 0; bi < nbox; ++bi) {
     const BoxGeo& bx = boxes[bi];
     const double* P = P0 + 12 * bx.coff;
@@ -165,7 +187,16 @@ __global__ void k_vel(DevParams p, const BoxGeo* __restrict__ boxes, int nbox, c
       const int i = (int)(r % bx.N[0]) - bx.ng[0];
       r /= bx.N[0];
       const int j = (int)(r % bx.N[1]) - bx.ng[1];
-      const Geo<MET, double> g = make_geo<MET, double>(p, xcen(bx, 0, i), xcen(bx, 1, j));
+      Geo<MET, double> g;
+      bool tab = false;
+      if constexpr (MET == KS) {
+        if (geo && bx.goff >= 0) {
+          const GeoTab T = geotab(geo, bx);
+          g = geo_load<MET>(T.C, T.sC, gidx_c(bx, i, j));
+          tab = true;
+        }
+      }
+      if (!tab) g = make_geo<MET, double>(p, xcen(bx, 0, i), xcen(bx, 1, j));
       double ucon[4], ucov[4], gm;
       fourvel<MET, double>(g, P[U1 * bx.ntot + t], P[U2 * bx.ntot + t], P[U3 * bx.ntot + t], ucon, ucov, &gm);
       const double iut = 1.0 / ucon[0];
@@ -188,7 +219,7 @@ __global__ void k_vel(DevParams p, const BoxGeo* __restrict__ boxes, int nbox, c
 template <int MET, typename R>
 __global__ void k_uct_emf(DevParams p, const BoxGeo* __restrict__ boxes, int nbox, FaceSet F,
                           const R* __restrict__ V0, const R* __restrict__ gsa0, const R* __restrict__ gsb0,
-                          R* __restrict__ emf0, int a, int b) {
+                          R* __restrict__ emf0, int a, int b, const double* __restrict__ geo) {
   for (int bi = 0; bi < nbox; ++bi) {
     const BoxGeo& bx = boxes[bi];
     const bool aa = bx.n[a] > 1, ab = bx.n[b] > 1;
@@ -220,9 +251,7 @@ __global__ void k_uct_emf(DevParams p, const BoxGeo* __restrict__ boxes, int nbo
       auto Bat = [&](const double* Fd, int d, int m, int o) {
         int q[3] = {ii[0], ii[1], ii[2]};
         q[m] += o;
-        double x[3] = {xcen(bx, 0, q[0]), xcen(bx, 1, q[1]), xcen(bx, 2, q[2])};
-        x[d] = xface(bx, d, q[d]);
-        return Fd[t + o * bx.str[m]] / gdet_at<MET>(p, x[0], x[1]);
+        return Fd[t + o * bx.str[m]] / gdet_pos<MET>(p, geo, bx, d == 0, d == 1, q[0], q[1]);
       };
       double Bb[2], Ba[2];
       {
@@ -245,10 +274,7 @@ __global__ void k_uct_emf(DevParams p, const BoxGeo* __restrict__ boxes, int nbo
           Ba[0] = Ba[1] = b0;
         }
       }
-      double xe[3] = {xcen(bx, 0, ii[0]), xcen(bx, 1, ii[1]), xcen(bx, 2, ii[2])};
-      xe[a] = xface(bx, a, ii[a]);
-      xe[b] = xface(bx, b, ii[b]);
-      const double ge = gdet_at<MET>(p, xe[0], xe[1]);
+      const double ge = gdet_pos<MET>(p, geo, bx, a == 0 || b == 0, a == 1 || b == 1, ii[0], ii[1]);
       double es[2][2];
 #pragma unroll
       for (int s1 = 0; s1 < 2; ++s1)
