@@ -321,7 +321,9 @@ int harmrad_zone_implicit_full(const harmrad_params* p, int n, const double* x, 
  * radiation of Ps (Sec. 4.8-4.10), 3 the staged PMHD of Sec. 4.10 (one
  * momentum-only step damped by 1/2, energy-only steps, then the full 4D
  * Newton with its first step damped by 1/4, two-sided differences) from the
- * gas of Ps with u_g from the explicit entropy Sstar (device, may be NULL).
+ * gas of Ps with u_g from the explicit entropy Sstar (device, may be NULL),
+ * 4 the staged URAD and 5 the staged PRAD (the same stages on the radiation
+ * unknowns with the plain methods' one-sided differences; guesses as 1, 2).
  * Pout[n][12]: the best iterate's primitives as its error function forms them
  * (radiation through the TYPE2 limiter; Ps where no residual was finite),
  * eT[n] its total error (inf if none), iters[n] the Newton steps.

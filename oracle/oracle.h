@@ -167,7 +167,8 @@ void   orc_implicit_zone(const orc_params* p, const double* x, const double* Ust
 /* One Newton method alone on one zone (test hook): method 0 PMHD (guess the
  * gas of Ps), 1 URAD (guess R^t_nu of Ps), 2 PRAD (guess the radiation of Ps),
  * 3 staged PMHD (Sec. 4.10; guess the gas of Ps with u_g from the explicit
- * entropy Sstar = sqrt(-g) S u^t when Sstar is not NULL).  Writes the best
+ * entropy Sstar = sqrt(-g) S u^t when Sstar is not NULL), 4 staged URAD,
+ * 5 staged PRAD (guesses as 1 and 2).  Writes the best
  * iterate's prims (Ps if none), its e_T (inf if none) and the Newton steps
  * taken. */
 void   orc_method_zone(const orc_params* p, const double* x, const double* Ustar,

@@ -668,6 +668,147 @@ int newton_prad(const Sys& s, const double x0[4], const double* Pg0, Res& best) 
   return steps;
 }
 
+// Staged URAD (prad = false) or PRAD (prad = true) (Sec. 4.10), after the
+// plain methods for extremely sub-dominant radiation: the stages of the
+// staged PMHD on the radiation unknowns -- one momentum-only step damped by
+// 1/2, energy-only steps (the first damped by 1/2) until the radiation energy
+// row's normalised error is below 1e-9, has risen five times or newton_max
+// steps, then the full 4D Newton with its first step damped by 1/4, at most
+// 40 steps -- with the plain method's controls: one-sided Jacobian columns
+// retried with offsets x10 up to 0.3 on an inversion failure, an iterate
+// whose inversion fails backed up half-way (up to 20 times), tolerance 1e-9,
+// and 40 x 6 gas inversions in all (the staged budget).  A step that leaves
+// the energy unknown on the wrong side (R^t_t > 0, Ebar < 0) reflects it to
+// half its size; the second such reflection in stage 1 or 2 keeps the prior
+// iterate and ends the stage.
+int newton_rad_staged(const Sys& s, const double x0[4], const double* Pg0, bool prad, Res& best) {
+  const orc_params& p = *s.p;
+  const Geom& G = *s.G;
+  const double tol = 1e-9;
+  double x[4] = {x0[0], x0[1], x0[2], x0[3]};
+  double Pg[NP];
+  std::memcpy(Pg, Pg0, sizeof(Pg));
+  best.eT = HUGE_VAL;
+  best.ok = false;
+  int steps = 0, ninv = 0;
+  const int inv_budget = 40 * 6;
+  double eps = 1e-8;
+  double xprev[4];
+  bool have_prev = false;
+  auto res = [&](const double* xx, double tinv, Res& r) {
+    ++ninv;
+    return prad ? prad_res(s, xx, Pg, tinv, r) : urad_res(s, xx, Pg, tinv, r);
+  };
+  // the iterate's residual, backing the last step up half-way on an inversion failure
+  auto eval = [&](Res& r) {
+    bool ok = false;
+    for (int back = 0;; ++back) {
+      ok = res(x, 1e-13, r);
+      if (ok || !have_prev || back >= 20 || ninv >= inv_budget) break;
+      for (int i = 0; i < 4; ++i) x[i] = 0.5 * (x[i] + xprev[i]);
+    }
+    if (!ok) return false;
+    std::memcpy(Pg, r.P, sizeof(Pg));
+    if (r.eT < best.eT) best = r;
+    return true;
+  };
+  // one damped step on the unknowns of mask
+  auto step = [&](const Res& r, unsigned mask, double D, double xn[4]) {
+    double J[4][4], E[4];
+    for (int j = 0; j < 4; ++j) {
+      if (!(mask >> j & 1u)) {
+        for (int i = 0; i < 4; ++i) J[i][j] = J[j][i] = i == j ? 1.0 : 0.0;
+        continue;
+      }
+      double scale;
+      if (prad) {
+        double umag = 0.0;
+        for (int a = 1; a < 4; ++a)
+          for (int c = 1; c < 4; ++c) umag += G.gcov[a][c] * x[a] * x[c];
+        umag = std::max(1.0, std::sqrt(std::max(umag, 0.0)));
+        scale = j == 0 ? std::fabs(x[0]) : umag / std::sqrt(G.gcov[j][j]);
+      } else {
+        scale = std::fabs(x[0]) * (j == 0 ? 1.0 : std::sqrt(G.gcov[j][j]));
+      }
+      bool done = false;
+      for (double e = eps; e <= 0.3 && !done; e *= 10.0) {
+        const double dj = e * scale;
+        if (dj == 0.0) break;
+        double xp[4] = {x[0], x[1], x[2], x[3]};
+        xp[j] += dj;
+        Res rp;
+        if (res(xp, 1e-2 * e, rp)) {
+          for (int i = 0; i < 4; ++i)
+            if (mask >> i & 1u) J[i][j] = (rp.Er[i] - r.Er[i]) / dj;
+          done = true;
+        }
+      }
+      if (!done) return false;
+    }
+    for (int i = 0; i < 4; ++i) E[i] = (mask >> i & 1u) ? r.Er[i] : 0.0;
+    double dx[4];
+    if (!solve4(J, E, dx)) return false;
+    for (int i = 0; i < 4; ++i) xn[i] = x[i] - D * dx[i];
+    return true;
+  };
+  auto wrong_side = [&](double v) { return prad ? v < 0.0 : v > 0.0; };
+  auto reflect = [&](double v) { return prad ? 0.5 * std::fabs(v) : -0.5 * std::fabs(v); };
+  for (int stage = 1; stage <= 2; ++stage) {
+    const unsigned mask = stage == 1 ? 0xEu : 0x1u;
+    const int max_steps = stage == 1 ? 1 : p.newton_max;
+    int resets = 0, rises = 0;
+    double prev = HUGE_VAL;
+    for (int k = 0; k < max_steps; ++k) {
+      Res r;
+      if (!eval(r)) return steps;
+      if (stage == 2) {
+        if (r.er[0] < tol) break;
+        if (r.er[0] >= prev && ++rises >= 5) break;
+        prev = r.er[0];
+      }
+      if (ninv >= inv_budget) return steps;
+      if (r.eI < 1e-9) eps = 1e-10;
+      double xn[4];
+      if (!step(r, mask, k == 0 ? 0.5 : 1.0, xn)) break;
+      ++steps;
+      if (wrong_side(xn[0])) {
+        if (++resets >= 2) break;
+        xn[0] = reflect(xn[0]);
+      }
+      for (int i = 0; i < 4; ++i) xprev[i] = x[i];
+      have_prev = true;
+      for (int i = 0; i < 4; ++i) x[i] = xn[i];
+    }
+  }
+  History hs;
+  for (int k = 0;; ++k) {
+    Res r;
+    if (!eval(r)) break;
+    hs.eT[k] = r.eT;
+    hs.eI[k] = r.eI;
+    if (r.eT < tol) break;
+    if (stalled(hs, k)) break;
+    if (k >= 40 || ninv >= inv_budget) break;
+    if (r.eI < 1e-9) eps = 1e-10;
+    double xn[4];
+    if (!step(r, 0xFu, k == 0 ? 0.25 : 1.0, xn)) break;
+    if (wrong_side(xn[0])) xn[0] = reflect(xn[0]);
+    for (int i = 0; i < 4; ++i) xprev[i] = x[i];
+    have_prev = true;
+    bool tiny = true;
+    for (int i = 0; i < 4; ++i)
+      if (std::fabs(xn[i] - x[i]) > 10.0 * EPSM * std::fabs(x[i])) tiny = false;
+    for (int i = 0; i < 4; ++i) x[i] = xn[i];
+    ++steps;
+    if (tiny) {
+      Res rf;
+      if (res(x, 1e-13, rf) && rf.eT < best.eT) best = rf;
+      break;
+    }
+  }
+  return steps;
+}
+
 void build_sys(const orc_params& p, const Geom& G, const double* Ustar, double h, Sys& s) {
   s.p = &p;
   s.G = &G;
@@ -716,12 +857,19 @@ void method_zone(const orc_params& p, const Geom& G, const double* Ustar, const 
   } else if (method == 2) {
     double x0[4] = {Ps[ER], Ps[UR1], Ps[UR2], Ps[UR3]};
     *iters = newton_prad(s, x0, Ps, b);
-  } else {
+  } else if (method == 3) {
     Res none;
     none.ok = false;
     double xs[4];
     staged_guess(p, s, Ustar, Sstar, Ps, none, xs);
     *iters = newton_pmhd_staged(s, xs, b);
+  } else if (method == 4) {
+    double Tc[4], Rc[4];
+    tt_row(p, G, Ps, Tc, Rc, nullptr, nullptr);
+    *iters = newton_rad_staged(s, Rc, Ps, false, b);
+  } else {
+    double x0[4] = {Ps[ER], Ps[UR1], Ps[UR2], Ps[UR3]};
+    *iters = newton_rad_staged(s, x0, Ps, true, b);
   }
   *eT = b.ok ? b.eT : HUGE_VAL;
   for (int q = 0; q < NP; ++q) Pout[q] = b.ok ? b.P[q] : Ps[q];
@@ -932,7 +1080,9 @@ void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, cons
     }
   }
   if (subdominant && !(best.ok && best.eT < 1e-9)) {
-    // staged PMHD (Sec. 4.10), for the extremely sub-dominant radiation only
+    // the staged PMHD, URAD and PRAD (Sec. 4.10), for the extremely
+    // sub-dominant radiation only, each from the lowest-error solution so far
+    // if its e_T < 1e-4, else from P_s
     double xs[4];
     staged_guess(p, s, Ustar, Sstar, Ps, best, xs);
     Res bs;
@@ -940,6 +1090,22 @@ void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, cons
     if (bs.ok && (!best.ok || bs.eT < best.eT)) {
       best = bs;
       method = ORC_OK_URAD;
+    }
+    for (int prad = 0; prad < 2 && !(best.ok && best.eT < 1e-9); ++prad) {
+      const double* Pg = (best.ok && best.eT < 1e-4) ? best.P : Ps;
+      double xr[4];
+      if (prad) {
+        for (int i = 0; i < 4; ++i) xr[i] = Pg[ER + i];
+      } else {
+        double Tc[4];
+        tt_row(p, G, Pg, Tc, xr, nullptr, nullptr);
+      }
+      Res br;
+      info->iters_urad += newton_rad_staged(s, xr, Pg, prad == 1, br);
+      if (br.ok && (!best.ok || br.eT < best.eT)) {
+        best = br;
+        method = ORC_OK_URAD;
+      }
     }
   }
   if (Sstar && !(best.ok && best.eT <= 1e-7)) {

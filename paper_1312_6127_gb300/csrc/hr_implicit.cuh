@@ -52,6 +52,7 @@ struct ImpResT {
   T Eg[4], Er[4];
   T eT, eI;
   T eg0;  // normalised error of the gas energy (or entropy) row alone
+  T er0;  // normalised error of the radiation energy row alone
   int negE;
   bool ok;
 };
@@ -118,6 +119,7 @@ __device__ __forceinline__ void normalise(const ImpSysT<MET, T>& s, const T Tc[4
     er[0] = T(0.0);
   }
   r.eg0 = eg[0];
+  r.er0 = er[0];
   if (s.cold) {  // cold MHD: energy and entropy ignored, the mean of the momentum rows
     T cT = T(0.0), cI = T(0.0);
 #pragma unroll
@@ -811,6 +813,152 @@ __device__ int newton_rad(const DevParams& p, const ImpSys<MET>& s, const double
 #pragma unroll
         for (int i = 0; i < 4; ++i) best_x[i] = x[i];
 #pragma unroll
+        for (int i = 0; i < 5; ++i) best_Pg[i] = go3[i];
+      }
+      break;
+    }
+  }
+  return steps;
+}
+
+// Staged URAD (PRAD = false) or PRAD (Sec. 4.10), after the plain methods for
+// extremely sub-dominant radiation: one momentum-only step damped by 1/2,
+// energy-only steps (the first damped by 1/2) until the radiation energy
+// row's normalised error is below 1e-9, has risen five times or newton_max
+// steps, then the full 4D Newton with its first step damped by 1/4, at most
+// 40 steps; the plain method's controls otherwise (one-sided columns retried
+// x10 up to 0.3, half-step back-off on an inversion failure, tolerance 1e-9),
+// with 40 x 6 gas inversions in all.  The energy unknown reflected to half
+// its size when a step puts it on the wrong side; the second reflection in
+// stage 1 or 2 keeps the prior iterate and ends the stage.
+template <int MET, bool PRAD>
+__device__ int newton_rad_staged(const DevParams& p, const ImpSys<MET>& s, const double x0[4], double Pg[5],
+                                 double best_x[4], double best_Pg[5], double* best_eT) {
+  double x[4] = {x0[0], x0[1], x0[2], x0[3]};
+  double xprev[4] = {x0[0], x0[1], x0[2], x0[3]};
+  bool have_prev = false;
+  *best_eT = HUGE_VAL;
+  int steps = 0, ninv = 0;
+  const int budget = 40 * 6;
+  double eps = 1e-8;
+  auto res = [&](const double* xx, double tol, ImpRes& rr, double* go, bool norm) {
+    double aux[4];
+    ++ninv;
+    return PRAD ? prad_res<MET>(p, s, xx, Pg, tol, rr, go, aux, norm)
+                : urad_res<MET>(p, s, xx, Pg, tol, rr, go, aux, norm);
+  };
+  auto eval = [&](ImpRes& r) {
+    double go[5];
+    bool ok = false;
+#pragma unroll 1
+    for (int back = 0;; ++back) {
+      ok = res(x, 1e-13, r, go, true);
+      if (ok || !have_prev || back >= 20 || ninv >= budget) break;
+      for (int i = 0; i < 4; ++i) x[i] = 0.5 * (x[i] + xprev[i]);
+    }
+    if (!ok) return false;
+    for (int i = 0; i < 5; ++i) Pg[i] = go[i];
+    if (r.eT < *best_eT) {
+      *best_eT = r.eT;
+      for (int i = 0; i < 4; ++i) best_x[i] = x[i];
+      for (int i = 0; i < 5; ++i) best_Pg[i] = go[i];
+    }
+    return true;
+  };
+  auto step = [&](const ImpRes& r, unsigned mask, double D, double xn[4]) {
+    double J[4][4], E[4];
+    const double umag = PRAD ? fmax(1.0, sqrt(fmax(s.g.sq3(x[1], x[2], x[3]), 0.0))) : 0.0;
+#pragma unroll 1
+    for (int j = 0; j < 4; ++j) {
+      if (!(mask >> j & 1u)) {
+        for (int i = 0; i < 4; ++i) J[i][j] = J[j][i] = i == j ? 1.0 : 0.0;
+        continue;
+      }
+      const double scale = PRAD ? (j == 0 ? fabs(x[0]) : umag / sqrt(s.g.gdd(j)))
+                                : fabs(x[0]) * (j == 0 ? 1.0 : sqrt(s.g.gdd(j)));
+      bool done = false;
+#pragma unroll 1
+      for (double e = eps; e <= 0.3 && !done; e *= 10.0) {
+        const double dj = e * scale;
+        if (dj == 0.0) break;
+        double xp[4] = {x[0], x[1], x[2], x[3]};
+        xp[j] += dj;
+        ImpRes rp;
+        double go2[5];
+        if (res(xp, 1e-2 * e, rp, go2, false)) {
+          for (int i = 0; i < 4; ++i)
+            if (mask >> i & 1u) J[i][j] = (rp.Er[i] - r.Er[i]) / dj;
+          done = true;
+        }
+      }
+      if (!done) return false;
+    }
+    for (int i = 0; i < 4; ++i) E[i] = (mask >> i & 1u) ? r.Er[i] : 0.0;
+    double dx[4];
+    if (!solve4(J, E, dx)) return false;
+    for (int i = 0; i < 4; ++i) xn[i] = x[i] - D * dx[i];
+    return true;
+  };
+  auto wrong_side = [](double v) { return PRAD ? v < 0.0 : v > 0.0; };
+  auto reflect = [](double v) { return PRAD ? 0.5 * fabs(v) : -0.5 * fabs(v); };
+#pragma unroll 1
+  for (int stage = 1; stage <= 2; ++stage) {
+    const unsigned mask = stage == 1 ? 0xEu : 0x1u;
+    const int max_steps = stage == 1 ? 1 : p.newton_max;
+    int resets = 0, rises = 0;
+    double prev = HUGE_VAL;
+#pragma unroll 1
+    for (int k = 0; k < max_steps; ++k) {
+      ImpRes r;
+      if (!eval(r)) return steps;
+      if (stage == 2) {
+        if (r.er0 < 1e-9) break;
+        if (r.er0 >= prev && ++rises >= 5) break;
+        prev = r.er0;
+      }
+      if (ninv >= budget) return steps;
+      if (r.eI < 1e-9) eps = 1e-10;
+      double xn[4];
+      if (!step(r, mask, k == 0 ? 0.5 : 1.0, xn)) break;
+      ++steps;
+      if (wrong_side(xn[0])) {
+        if (++resets >= 2) break;
+        xn[0] = reflect(xn[0]);
+      }
+      for (int i = 0; i < 4; ++i) {
+        xprev[i] = x[i];
+        x[i] = xn[i];
+      }
+      have_prev = true;
+    }
+  }
+  Hist hs = {HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, HUGE_VAL, 0};
+#pragma unroll 1
+  for (int k = 0;; ++k) {
+    ImpRes r;
+    if (!eval(r)) break;
+    if (r.eT < 1e-9) break;
+    if (stalled(hs, k, r.eT, r.eI)) break;
+    if (k >= 40 || ninv >= budget) break;
+    if (r.eI < 1e-9) eps = 1e-10;
+    double xn[4];
+    if (!step(r, 0xFu, k == 0 ? 0.25 : 1.0, xn)) break;
+    if (wrong_side(xn[0])) xn[0] = reflect(xn[0]);
+    bool tiny = true;
+    for (int i = 0; i < 4; ++i)
+      if (fabs(xn[i] - x[i]) > 10.0 * 2.220446049250313e-16 * fabs(x[i])) tiny = false;
+    for (int i = 0; i < 4; ++i) {
+      xprev[i] = x[i];
+      x[i] = xn[i];
+    }
+    have_prev = true;
+    ++steps;
+    if (tiny) {
+      ImpRes rf;
+      double go3[5];
+      if (res(x, 1e-13, rf, go3, true) && rf.eT < *best_eT) {
+        *best_eT = rf.eT;
+        for (int i = 0; i < 4; ++i) best_x[i] = x[i];
         for (int i = 0; i < 5; ++i) best_Pg[i] = go3[i];
       }
       break;

@@ -1096,6 +1096,51 @@ __device__ int retry_sequence(const DevParams& p, const Geo<MET, double>& g, con
       beT = seT;
     }
   }
+  // then the staged URAD and PRAD, each from the primitives of the
+  // lowest-error solution so far if its e_T < 1e-4 (as its error function
+  // formed them), else from P_s
+  double tx[2][4], tgas[2][5];
+#pragma unroll 1
+  for (int pr = 0; pr < 2 && subdom && !(beT < 1e-9); ++pr) {
+    double Pq[NPR];
+    for (int q = 0; q < NPR; ++q) Pq[q] = Ps[q];
+    if (best >= 0 && beT < 1e-4) {
+      if (best == 0 || best == 3) {
+        ImpRes rr;
+        ImpState stt;
+        const double* bx = best == 0 ? px : sx;
+        pmhd_res<MET>(p, s, bx, rr, &stt, false);
+        Pq[RHO] = stt.rho;
+        for (int c = 0; c < 4; ++c) Pq[UU + c] = bx[c];
+        for (int c = 0; c < 4; ++c) Pq[ER + c] = stt.Pr[c];
+      } else if (best == 1 || best == 4) {
+        const double* gg = best == 1 ? ugas : tgas[0];
+        for (int c = 0; c < 5; ++c) Pq[c] = gg[c];
+        rad_invert<MET>(p, g, best == 1 ? ux : tx[0], 2, Pq + ER);
+      } else {
+        const double* gg = best == 2 ? qgas : tgas[1];
+        const double* xx = best == 2 ? qx : tx[1];
+        for (int c = 0; c < 5; ++c) Pq[c] = gg[c];
+        for (int c = 0; c < 4; ++c) Pq[ER + c] = xx[c];
+      }
+    }
+    double gq[5] = {Pq[RHO], Pq[UU], Pq[U1], Pq[U2], Pq[U3]}, x4[4], reT;
+    if (pr == 1) {
+      for (int c = 0; c < 4; ++c) x4[c] = Pq[ER + c];
+      steps += newton_rad_staged<MET, true>(p, s, x4, gq, tx[1], tgas[1], &reT);
+    } else {
+      double urc2[4], urv2[4], gr2;
+      fourvel<MET, double>(g, Pq[UR1], Pq[UR2], Pq[UR3], urc2, urv2, &gr2);
+      const double e43q = (4.0 / 3.0) * Pq[ER];
+      x4[0] = e43q * urc2[0] * urv2[0] + Pq[ER] * (1.0 / 3.0);
+      for (int c = 1; c < 4; ++c) x4[c] = e43q * urc2[0] * urv2[c];
+      steps += newton_rad_staged<MET, false>(p, s, x4, gq, tx[0], tgas[0], &reT);
+    }
+    if (isfinite(reT) && (best < 0 || reT < beT)) {
+      best = 4 + pr;
+      beT = reT;
+    }
+  }
   int method = ST_URAD;
   if (best == 0) {
     pmhd_final<MET>(p, s, px, Pn);
@@ -1110,6 +1155,14 @@ __device__ int retry_sequence(const DevParams& p, const Geo<MET, double>& g, con
     for (int q = 0; q < 4; ++q) Pn[ER + q] = qx[q];
   } else if (best == 3) {
     pmhd_final<MET>(p, s, sx, Pn);
+  } else if (best == 4) {
+    for (int q = 0; q < 5; ++q) Pn[q] = tgas[0][q];
+    double Pr[4];
+    if (rad_invert<MET>(p, g, tx[0], 2, Pr)) rad_invert<MET>(p, g, tx[0], 0, Pr);
+    for (int q = 0; q < 4; ++q) Pn[ER + q] = Pr[q];
+  } else if (best == 5) {
+    for (int q = 0; q < 5; ++q) Pn[q] = tgas[1][q];
+    for (int q = 0; q < 4; ++q) Pn[ER + q] = tx[1][q];
   } else {
     for (int q = 0; q < NPR; ++q) Pn[q] = Ps[q];
     method = ST_BACKUP;

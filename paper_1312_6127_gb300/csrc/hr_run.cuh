@@ -430,7 +430,8 @@ __global__ void k_zone_implicit(DevParams p, BoxGeo bg, int n, const double* __r
 // One Newton method alone on each of n independent zones (test hook, the
 // counterpart of the oracle's method hook): 0 PMHD from the gas of Ps, 1 URAD
 // from R^t_nu of Ps, 2 PRAD from the radiation of Ps, 3 staged PMHD from the
-// gas of Ps with u_g from the explicit entropy Sst (if given).  Writes the
+// gas of Ps with u_g from the explicit entropy Sst (if given), 4 staged URAD,
+// 5 staged PRAD (guesses as 1 and 2).  Writes the
 // best iterate's primitives as its error function forms them (TYPE2
 // radiation; Ps if none), its e_T (inf if none) and the Newton steps.
 template <int MET>
@@ -468,18 +469,20 @@ __global__ void k_zone_method(DevParams p, BoxGeo bg, int n, const double* __res
       }
     } else {
       double gas[5] = {P0[RHO], P0[UU], P0[U1], P0[U2], P0[U3]}, bx[4], bgas[5];
-      if (method == 1) {
+      if (method == 1 || method == 4) {
         double urc[4], urv[4], gr;
         fourvel<MET, double>(g, P0[UR1], P0[UR2], P0[UR3], urc, urv, &gr);
         const double e43 = (4.0 / 3.0) * P0[ER];
         double xr[4];
         xr[0] = e43 * urc[0] * urv[0] + P0[ER] * (1.0 / 3.0);
         for (int c = 1; c < 4; ++c) xr[c] = e43 * urc[0] * urv[c];
-        steps = newton_urad<MET>(p, s, xr, gas, bx, bgas, &eT);
+        steps = method == 1 ? newton_urad<MET>(p, s, xr, gas, bx, bgas, &eT)
+                            : newton_rad_staged<MET, false>(p, s, xr, gas, bx, bgas, &eT);
         if (isfinite(eT)) rad_invert<MET>(p, g, bx, 2, Pn + ER);
       } else {
         double xq[4] = {P0[ER], P0[UR1], P0[UR2], P0[UR3]};
-        steps = newton_rad<MET, true>(p, s, xq, gas, bx, bgas, &eT);
+        steps = method == 2 ? newton_rad<MET, true>(p, s, xq, gas, bx, bgas, &eT)
+                            : newton_rad_staged<MET, true>(p, s, xq, gas, bx, bgas, &eT);
         if (isfinite(eT))
           for (int c = 0; c < 4; ++c) Pn[ER + c] = bx[c];
       }
