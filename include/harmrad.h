@@ -323,7 +323,10 @@ int harmrad_zone_implicit_full(const harmrad_params* p, int n, const double* x, 
  * Newton with its first step damped by 1/4, two-sided differences) from the
  * gas of Ps with u_g from the explicit entropy Sstar (device, may be NULL),
  * 4 the staged URAD and 5 the staged PRAD (the same stages on the radiation
- * unknowns with the plain methods' one-sided differences; guesses as 1, 2).
+ * unknowns with the plain methods' one-sided differences; guesses as 1, 2),
+ * 6, 7, 8 the entropy-based PMHD, URAD, PRAD (the entropy equation, Eq.
+ * source6, in place of the energy equation with Sstar, which these require;
+ * guesses as 0, 1, 2).
  * Pout[n][12]: the best iterate's primitives as its error function forms them
  * (radiation through the TYPE2 limiter; Ps where no residual was finite),
  * eT[n] its total error (inf if none), iters[n] the Newton steps.

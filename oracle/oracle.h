@@ -168,7 +168,9 @@ void   orc_implicit_zone(const orc_params* p, const double* x, const double* Ust
  * gas of Ps), 1 URAD (guess R^t_nu of Ps), 2 PRAD (guess the radiation of Ps),
  * 3 staged PMHD (Sec. 4.10; guess the gas of Ps with u_g from the explicit
  * entropy Sstar = sqrt(-g) S u^t when Sstar is not NULL), 4 staged URAD,
- * 5 staged PRAD (guesses as 1 and 2).  Writes the best
+ * 5 staged PRAD (guesses as 1 and 2), 6, 7, 8 the entropy-based PMHD, URAD,
+ * PRAD (Eq. source6 with the explicit entropy Sstar; guesses as 0, 1, 2).
+ * Writes the best
  * iterate's prims (Ps if none), its e_T (inf if none) and the Newton steps
  * taken. */
 void   orc_method_zone(const orc_params* p, const double* x, const double* Ustar,

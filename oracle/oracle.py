@@ -353,7 +353,8 @@ def implicit_zone(p, x, Ustar, Ps, h, Sstar=None):
 def method_zone(p, x, Ustar, Ps, h, method, Sstar=None):
     """One Newton method alone (0 PMHD, 1 URAD, 2 PRAD, 3 staged PMHD with
     u_g from the explicit entropy Sstar if given, 4 staged URAD, 5 staged
-    PRAD): (P, e_T, steps)."""
+    PRAD, 6/7/8 the entropy-based PMHD/URAD/PRAD with the explicit entropy
+    Sstar): (P, e_T, steps)."""
     x, Us, Pz = _vec(x), _vec(Ustar), _vec(Ps)
     out = np.empty(NP)
     eT = ctypes.c_double()

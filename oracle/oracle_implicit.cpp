@@ -155,7 +155,9 @@ void pmhd_res(const Sys& s, const double x[4], Res& r) {
     const double Su = s.Dlab * sg;
     r.Eg[0] = Su - s.Sstar - s.h * GS;
     const double d0 = std::fabs(Su) + std::fabs(s.Sstar) + s.h * std::fabs(GS);
-    r.eg[0] = d0 > 0.0 ? std::fabs(r.Eg[0]) / d0 : 0.0;
+    // a TYPE2 inversion that met a negative energy excludes the entropy term
+    // from the error (Sec. 4.10)
+    r.eg[0] = (d0 > 0.0 && !r.negE) ? std::fabs(r.Eg[0]) / d0 : 0.0;
     r.er[0] = 0.0;
     double sT = r.eg[0], sI = r.eg[0];
     for (int k = 1; k < 4; ++k) {
@@ -178,6 +180,36 @@ void pmhd_res(const Sys& s, const double x[4], Res& r) {
   }
   std::memcpy(r.P, P, sizeof(P));
   r.ok = std::isfinite(r.eT);
+}
+
+// The entropy equation's row for the radiation methods (Sec. 4.8: the
+// entropy-based URAD and PRAD take the entropy row and the three radiation
+// momentum rows as their error function; the energy rows are ignored): at the
+// iterate's primitives P, E_S = S u^t(P) - S* - h G_S (Eq. source6, G_S of
+// Eq. GS) replaces the radiation energy row of the Newton error vector, and
+// e_T, e_I are formed as for the entropy PMHD with the radiation rows iterated.
+void entropy_rad_rows(const Sys& s, const double* P, const FourVel& u, const double Gc[4], Res& r) {
+  const orc_params& p = *s.p;
+  const double pg = (p.gam - 1.0) * P[UU];
+  const double sg = entropy_per_baryon(p, P[RHO], P[UU]);
+  double Gu = 0.0;
+  for (int m = 0; m < 4; ++m) Gu += Gc[m] * u.ucon[m];
+  const double GS = -Gu / (pg / P[RHO]);
+  const double Su = s.Dlab * sg;
+  r.Er[0] = Su - s.Sstar - s.h * GS;
+  const double d0 = std::fabs(Su) + std::fabs(s.Sstar) + s.h * std::fabs(GS);
+  // a TYPE2 inversion that met a negative energy excludes the entropy term
+  // from the error (Sec. 4.10)
+  const double eS = (d0 > 0.0 && !r.negE) ? std::fabs(r.Er[0]) / d0 : 0.0;
+  r.eg[0] = 0.0;
+  r.er[0] = eS;
+  double sT = eS, sI = eS;
+  for (int k = 1; k < 4; ++k) {
+    sT += std::max(r.eg[k], r.er[k]);
+    sI += r.er[k];
+  }
+  r.eT = 0.25 * sT;
+  r.eI = 0.25 * sI;
 }
 
 // URAD error function: iterate R^t_nu; gas from conservation through the
@@ -218,6 +250,7 @@ bool urad_res(const Sys& s, const double x[4], const double* Pguess, double tol_
     r.Er[k] = Rc[k] - s.Rstar[k] + s.h * Gc[k];
   }
   normalise(s, Tc, Rc, Gc, false, r);
+  if (s.entropy) entropy_rad_rows(s, P, u, Gc, r);
   std::memcpy(r.P, P, sizeof(P));
   r.ok = std::isfinite(r.eT);
   return r.ok;
@@ -265,6 +298,7 @@ bool prad_res(const Sys& s, const double x[4], const double* Pguess, double tol_
     r.Er[k] = Rc[k] - s.Rstar[k] + s.h * Gc[k];
   }
   normalise(s, Tc, Rc, Gc, false, r);
+  if (s.entropy) entropy_rad_rows(s, P, u, Gc, r);
   std::memcpy(r.P, P, sizeof(P));
   r.ok = std::isfinite(r.eT);
   return r.ok;
@@ -867,9 +901,25 @@ void method_zone(const orc_params& p, const Geom& G, const double* Ustar, const 
     double Tc[4], Rc[4];
     tt_row(p, G, Ps, Tc, Rc, nullptr, nullptr);
     *iters = newton_rad_staged(s, Rc, Ps, false, b);
-  } else {
+  } else if (method == 5) {
     double x0[4] = {Ps[ER], Ps[UR1], Ps[UR2], Ps[UR3]};
     *iters = newton_rad_staged(s, x0, Ps, true, b);
+  } else {
+    // the entropy-based PMHD, URAD, PRAD (Eq. source6 in place of the energy equation)
+    Sys se = s;
+    se.entropy = true;
+    se.Sstar = Sstar ? *Sstar / G.gdet : 0.0;
+    if (method == 6) {
+      double x0[4] = {Ps[UU], Ps[U1], Ps[U2], Ps[U3]};
+      *iters = newton_pmhd(se, x0, b);
+    } else if (method == 7) {
+      double Tc[4], Rc[4];
+      tt_row(p, G, Ps, Tc, Rc, nullptr, nullptr);
+      *iters = newton_urad(se, Rc, Ps, b);
+    } else {
+      double x0[4] = {Ps[ER], Ps[UR1], Ps[UR2], Ps[UR3]};
+      *iters = newton_prad(se, x0, Ps, b);
+    }
   }
   *eT = b.ok ? b.eT : HUGE_VAL;
   for (int q = 0; q < NP; ++q) Pout[q] = b.ok ? b.P[q] : Ps[q];
@@ -960,6 +1010,29 @@ void finish_solution(const orc_params& p, const Geom& G, const Sys& s, const Res
   info->method = (best.eT > 1e-7) ? ORC_BACKUP : method;
 }
 
+// After the entropy PMHD (bs), the entropy URAD and then the entropy PRAD
+// while the best entropy solution has e_T >= 1e-9 (the energy methods'
+// sequence, Sec. 4.11), each from the primitives of the best entropy solution
+// if its e_T < 1e-4, else from P_s.  bs ends as the lowest-error entropy
+// solution; returns the Newton steps.
+int entropy_radiation_methods(const orc_params& p, const Geom& G, const Sys& se, const double* Ps, Res& bs) {
+  int steps = 0;
+  for (int prad = 0; prad < 2 && !(bs.ok && bs.eT < 1e-9); ++prad) {
+    const double* Pg = (bs.ok && bs.eT < 1e-4) ? bs.P : Ps;
+    double xr[4];
+    if (prad) {
+      for (int i = 0; i < 4; ++i) xr[i] = Pg[ER + i];
+    } else {
+      double Tc[4];
+      tt_row(p, G, Pg, Tc, xr, nullptr, nullptr);
+    }
+    Res br;
+    steps += prad ? newton_prad(se, xr, Pg, br) : newton_urad(se, xr, Pg, br);
+    if (br.ok && (!bs.ok || br.eT < bs.eT)) bs = br;
+  }
+  return steps;
+}
+
 // The cold-MHD back-up (Sec. 4.11): when cold_allowed, the PMHD method on
 // the three momentum equations alone, u_g held at the guess x0's value; the
 // gas and radiation energy equations are dropped, the radiation still takes
@@ -1023,7 +1096,7 @@ void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, cons
     se.entropy = true;
     se.Sstar = *Sstar / G.gdet;
     info->iters_pmhd = newton_pmhd(se, x0, best);
-    info->iters_urad = 0;
+    info->iters_urad = entropy_radiation_methods(p, G, se, Ps, best);
     if (!(best.ok && best.eT <= 1e-7) && try_cold(p, G, s, Ustar, Ps, x0, Pout, info)) return;
     finish_solution(p, G, se, best, Ps, Pout, info, ORC_OK_PMHD);
     info->entropy = best.ok && best.eT <= 1e-7;
@@ -1117,6 +1190,7 @@ void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, cons
     se.Sstar = *Sstar / G.gdet;
     Res bs;
     info->iters_urad += newton_pmhd(se, x0, bs);
+    info->iters_urad += entropy_radiation_methods(p, G, se, Ps, bs);
     if (bs.ok && bs.eT <= 1e-7) {
       finish_solution(p, G, se, bs, Ps, Pout, info, ORC_OK_URAD);
       info->entropy = 1;

@@ -885,7 +885,7 @@ int harmrad_zone_implicit(const harmrad_params* prm, int n, const double* x, con
 int harmrad_zone_method(const harmrad_params* prm, int n, const double* x, const double* Us, const double* Sstar,
                         const double* Ps, const double* h, int method, double* Pout, double* eT, int* iters,
                         void* stream) {
-  if (!prm || n < 0 || method < 0 || method > 5 ||
+  if (!prm || n < 0 || method < 0 || method > 8 || (method >= 6 && !Sstar) ||
       (n > 0 && (!x || !Us || !Ps || !h || !Pout || !eT || !iters)))
     return HARMRAD_E_ARG;
   DevParams dp;

@@ -91,7 +91,8 @@ __device__ __forceinline__ void four_force_rad(const DevParams& p, T rho, T Tg, 
 
 template <int MET, typename T = double>
 __device__ __forceinline__ void normalise(const ImpSysT<MET, T>& s, const T Tc[4], const T Rc[4],
-                                          const T G[4], bool iter_gas, ImpResT<T>& r, T eS = T(-1.0)) {
+                                          const T G[4], bool iter_gas, ImpResT<T>& r, T eS = T(-1.0),
+                                          T eSr = T(-1.0)) {
   T dg0 = fabs(Tc[0]) + fabs(s.Ts[0]) + s.h * fabs(G[0]);
   T dr0 = fabs(Rc[0]) + fabs(s.Rs[0]) + s.h * fabs(G[0]);
   T dgs = T(0.0), drs = T(0.0);
@@ -115,8 +116,12 @@ __device__ __forceinline__ void normalise(const ImpSysT<MET, T>& s, const T Tc[4
   }
   if (r.negE) eg[0] = er[0] = T(0.0);
   if (eS >= 0.0) {  // entropy row in place of the gas energy row; the radiation energy row drops
-    eg[0] = eS;
+    eg[0] = r.negE ? T(0.0) : eS;  // excluded after a TYPE2 negative energy (Sec. 4.10)
     er[0] = T(0.0);
+  }
+  if (eSr >= 0.0) {  // the radiation methods' entropy row (the energy rows drop)
+    eg[0] = T(0.0);
+    er[0] = r.negE ? T(0.0) : eSr;
   }
   r.eg0 = eg[0];
   r.er0 = er[0];
@@ -593,6 +598,22 @@ __device__ int newton_pmhd_staged(const DevParams& p, const ImpSys<MET>& s, cons
   return steps;
 }
 
+// The entropy-based URAD and PRAD (Sec. 4.8: their error function takes the
+// entropy row and the three radiation momentum rows; the energy rows drop):
+// E_S = S u^t(P) - S* - h G_S (Eq. source6, G_S of Eq. GS) in place of the
+// radiation energy row; returns its normalised error (for normalise).
+template <int MET>
+__device__ __forceinline__ double entropy_rad_row(const DevParams& p, const ImpSys<MET>& s, double rho, double ug,
+                                                  const double ucon[4], const double G[4], ImpRes& r) {
+  const double Tg = (p.gam - 1.0) * ug / rho;
+  const double Gu = G[0] * ucon[0] + G[1] * ucon[1] + G[2] * ucon[2] + G[3] * ucon[3];
+  const double GS = -Gu / Tg;
+  const double Su = s.Dlab * entropy_per_baryon<double>(p, rho, ug);
+  r.Er[0] = Su - s.Sstar - s.h * GS;
+  const double d0 = fabs(Su) + fabs(s.Sstar) + s.h * fabs(GS);
+  return d0 > 0.0 ? fabs(r.Er[0]) / d0 : 0.0;
+}
+
 // URAD error function: iterate R^t_nu; gas from 1D_W inversion of
 // T^t_nu = T*^t_nu - (x - R*^t_nu); radiation from the M1 inversion of x.
 template <int MET>
@@ -638,8 +659,9 @@ __device__ __forceinline__ bool urad_res(const DevParams& p, const ImpSys<MET>& 
     r.Eg[k] = Tc[k] - s.Ts[k] - s.h * G[k];
     r.Er[k] = Rc[k] - s.Rs[k] + s.h * G[k];
   }
+  const double eSr = s.entropy ? entropy_rad_row<MET>(p, s, rho, ug, ucon, G, r) : -1.0;
   if (norm) {
-    normalise<MET>(s, Tc, Rc, G, false, r);
+    normalise<MET>(s, Tc, Rc, G, false, r, -1.0, eSr);
     r.ok = isfinite(r.eT);
   } else {
     r.ok = true;
@@ -692,8 +714,9 @@ __device__ __forceinline__ bool prad_res(const DevParams& p, const ImpSys<MET>& 
     r.Eg[k] = Tc[k] - s.Ts[k] - s.h * G[k];
     r.Er[k] = Rx[k] - s.Rs[k] + s.h * G[k];
   }
+  const double eSr = s.entropy ? entropy_rad_row<MET>(p, s, rho, ug, ucon, G, r) : -1.0;
   if (norm) {
-    normalise<MET>(s, Tc, Rx, G, false, r);
+    normalise<MET>(s, Tc, Rx, G, false, r, -1.0, eSr);
     r.ok = isfinite(r.eT);
   } else {
     r.ok = true;

@@ -1454,18 +1454,23 @@ __device__ __forceinline__ bool cold_allowed(const Geo<MET, double>& g, const do
 
 // The back-up equations of Sec. 4.11 for a zone that the energy methods left
 // without a solution.  First the entropy equation (Eq. source6) in place of
-// the gas energy equation, where the explicit S* (sqrt(-g) S u^t) is finite
-// and with_entropy; then, for a cold momentum-dominated zone (cold_allowed),
-// the cold-MHD equations: PMHD on the three momentum equations with u_g held
-// at the guess.  Both start from the energy PMHD's guess (P_s, or where
-// tau < 2/3 the gas inversion of U*) and are accepted at e_T <= 1e-7.
-// Returns METH_ENTROPY or METH_COLD with Pn and *eT set, 0 if neither
-// gives a solution; adds the Newton steps to *steps.
+// the gas energy equation, where the explicit S* (sqrt(-g) S u^t) is finite,
+// by the energy methods' sequence: PMHD (emode 1; with emode 2 the update
+// kernel ran it already and px / peT are its best iterate and error), then
+// URAD and PRAD while the best entropy solution has e_T >= 1e-9, each from the
+// primitives of that solution if its e_T < 1e-4, else from P_s.  Then, for a
+// cold momentum-dominated zone (cold_allowed), the cold-MHD equations: PMHD
+// on the three momentum equations with u_g held at the guess.  The PMHD
+// attempts start from the energy PMHD's guess (P_s, or where tau < 2/3 the
+// gas inversion of U*); a solution is accepted at e_T <= 1e-7.  Returns
+// METH_ENTROPY or METH_COLD with Pn and *eT set, 0 if none gives a solution;
+// adds the Newton steps to *steps.  emode 0: no entropy equation.
 template <int MET>
 __device__ int backup_equations(const DevParams& p, const Geo<MET, double>& g, const ImpSys<MET>& s,
-                                const double Ust[NPR], const double Ps[NPR], double Sst, bool with_entropy,
-                                double tau, double Pn[NPR], double* eT, int* steps) {
-  const bool ent = with_entropy && isfinite(Sst);
+                                const double Ust[NPR], const double Ps[NPR], double Sst, int emode,
+                                double tau, double Pn[NPR], double* eT, int* steps,
+                                const double* px = nullptr, double peT = HUGE_VAL) {
+  const bool ent = emode != 0 && isfinite(Sst);
   const bool cold = cold_allowed<MET>(g, Ust, Ps);
   if (!ent && !cold) return 0;
   double x0[4] = {Ps[UU], Ps[U1], Ps[U2], Ps[U3]};
@@ -1474,19 +1479,85 @@ __device__ int backup_equations(const DevParams& p, const Geo<MET, double>& g, c
     if (gas_invert<MET>(p, g, s.Dlab, s.Ts[0], T3, s.B, Ps, 1e-9, go) == 0)
       for (int c = 0; c < 4; ++c) x0[c] = go[1 + c];
   }
-#pragma unroll 1
-  for (int pass = 0; pass < 2; ++pass) {
-    if (pass == 0 ? !ent : !cold) continue;
+  if (ent) {
     ImpSys<MET> se = s;
-    se.entropy = pass == 0;
-    se.cold = pass == 1;
-    se.Sstar = pass == 0 ? Sst / g.gdet : 0.0;
+    se.entropy = true;
+    se.Sstar = Sst / g.gdet;
     double bxe[4] = {0.0, 0.0, 0.0, 0.0}, beT = HUGE_VAL;
-    *steps += newton_pmhd<MET>(p, se, x0, bxe, &beT);
+    int who = -1;  // 0 PMHD, 1 URAD, 2 PRAD
+    if (emode == 1) {
+      *steps += newton_pmhd<MET>(p, se, x0, bxe, &beT);
+    } else if (px && isfinite(peT)) {
+      for (int c = 0; c < 4; ++c) bxe[c] = px[c];
+      beT = peT;
+    }
+    if (isfinite(beT)) who = 0;
+    double rx[2][4], rgas[2][5];
+#pragma unroll 1
+    for (int pr = 0; pr < 2 && !(beT < 1e-9); ++pr) {
+      double Pq[NPR];
+      for (int q = 0; q < NPR; ++q) Pq[q] = Ps[q];
+      if (who >= 0 && beT < 1e-4) {
+        if (who == 0) {
+          ImpRes rr;
+          ImpState stt;
+          pmhd_res<MET>(p, se, bxe, rr, &stt, false);
+          Pq[RHO] = stt.rho;
+          for (int c = 0; c < 4; ++c) Pq[UU + c] = bxe[c];
+          for (int c = 0; c < 4; ++c) Pq[ER + c] = stt.Pr[c];
+        } else if (who == 1) {
+          for (int c = 0; c < 5; ++c) Pq[c] = rgas[0][c];
+          rad_invert<MET>(p, g, rx[0], 2, Pq + ER);
+        } else {
+          for (int c = 0; c < 5; ++c) Pq[c] = rgas[1][c];
+          for (int c = 0; c < 4; ++c) Pq[ER + c] = rx[1][c];
+        }
+      }
+      double gq[5] = {Pq[RHO], Pq[UU], Pq[U1], Pq[U2], Pq[U3]}, x4[4], reT;
+      if (pr == 1) {
+        for (int c = 0; c < 4; ++c) x4[c] = Pq[ER + c];
+        *steps += newton_rad<MET, true>(p, se, x4, gq, rx[1], rgas[1], &reT);
+      } else {
+        double urc2[4], urv2[4], gr2;
+        fourvel<MET, double>(g, Pq[UR1], Pq[UR2], Pq[UR3], urc2, urv2, &gr2);
+        const double e43q = (4.0 / 3.0) * Pq[ER];
+        x4[0] = e43q * urc2[0] * urv2[0] + Pq[ER] * (1.0 / 3.0);
+        for (int c = 1; c < 4; ++c) x4[c] = e43q * urc2[0] * urv2[c];
+        *steps += newton_rad<MET, false>(p, se, x4, gq, rx[0], rgas[0], &reT);
+      }
+      if (isfinite(reT) && (who < 0 || reT < beT)) {
+        who = 1 + pr;
+        beT = reT;
+      }
+    }
     if (beT <= 1e-7) {
-      pmhd_final<MET>(p, se, bxe, Pn);
+      if (who == 0) {
+        pmhd_final<MET>(p, se, bxe, Pn);
+      } else {
+        for (int q = 0; q < 5; ++q) Pn[q] = rgas[who - 1][q];
+        if (who == 1) {
+          double Pr[4];
+          if (rad_invert<MET>(p, g, rx[0], 2, Pr)) rad_invert<MET>(p, g, rx[0], 0, Pr);
+          for (int q = 0; q < 4; ++q) Pn[ER + q] = Pr[q];
+        } else {
+          for (int q = 0; q < 4; ++q) Pn[ER + q] = rx[1][q];
+        }
+        for (int c = 0; c < 3; ++c) Pn[B1 + c] = s.B[c];
+      }
       *eT = beT;
-      return pass == 0 ? METH_ENTROPY : METH_COLD;
+      return METH_ENTROPY;
+    }
+  }
+  if (cold) {
+    ImpSys<MET> sc = s;
+    sc.entropy = false;
+    sc.cold = true;
+    double bxc[4] = {0.0, 0.0, 0.0, 0.0}, beT = HUGE_VAL;
+    *steps += newton_pmhd<MET>(p, sc, x0, bxc, &beT);
+    if (beT <= 1e-7) {
+      pmhd_final<MET>(p, sc, bxc, Pn);
+      *eT = beT;
+      return METH_COLD;
     }
   }
   return 0;
@@ -1811,7 +1882,7 @@ __global__ void __launch_bounds__(128) k_retry(DevParams p, const BoxGeo* __rest
     const double tau = zone_tau<MET>(p, g, bx.dx, Ps, kfield(p, K, t));
     int method;
     const double Sst = qd[18];
-    if (p.implicit_eq == 1) {  // the entropy solve already failed
+    if (p.implicit_eq == 1) {  // the entropy PMHD of the update kernel left no solution
       for (int q = 0; q < NPR; ++q) Pn[q] = Ps[q];
       for (int c = 0; c < 3; ++c) Pn[B1 + c] = s.B[c];
       eT = HUGE_VAL;
@@ -1823,7 +1894,8 @@ __global__ void __launch_bounds__(128) k_retry(DevParams p, const BoxGeo* __rest
     // no energy-based solution: the entropy, then the cold-MHD equations
     int by = 0;
     if (method == ST_BACKUP) {
-      by = backup_equations<MET>(p, g, s, Ust, Ps, Sst, p.implicit_eq != 1, tau, Pn, &eT, &steps);
+      by = p.implicit_eq == 1 ? backup_equations<MET>(p, g, s, Ust, Ps, Sst, 2, tau, Pn, &eT, &steps, px, peT)
+                              : backup_equations<MET>(p, g, s, Ust, Ps, Sst, 1, tau, Pn, &eT, &steps);
       if (by) method = ST_URAD;
     }
     b.iters[zg] += steps;

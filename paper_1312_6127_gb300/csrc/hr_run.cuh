@@ -416,7 +416,7 @@ __global__ void k_zone_implicit(DevParams p, BoxGeo bg, int n, const double* __r
       method = retry_sequence<MET>(p, g, s, P0, bx, beT, tau, Pn, &eT, &rs, subdom, sz);
       steps += rs;
       if (method == ST_BACKUP) {  // the entropy (S* given), then the cold-MHD equations
-        const int by = backup_equations<MET>(p, g, s, Ust, P0, sz, true, tau, Pn, &eT, &steps);
+        const int by = backup_equations<MET>(p, g, s, Ust, P0, sz, 1, tau, Pn, &eT, &steps);
         if (by) method = by;
       }
     }
@@ -431,7 +431,8 @@ __global__ void k_zone_implicit(DevParams p, BoxGeo bg, int n, const double* __r
 // counterpart of the oracle's method hook): 0 PMHD from the gas of Ps, 1 URAD
 // from R^t_nu of Ps, 2 PRAD from the radiation of Ps, 3 staged PMHD from the
 // gas of Ps with u_g from the explicit entropy Sst (if given), 4 staged URAD,
-// 5 staged PRAD (guesses as 1 and 2).  Writes the
+// 5 staged PRAD (guesses as 1 and 2), 6, 7, 8 the entropy-based PMHD, URAD,
+// PRAD (the entropy equation with the explicit entropy Sst; guesses as 0-2).  Writes the
 // best iterate's primitives as its error function forms them (TYPE2
 // radiation; Ps if none), its e_T (inf if none) and the Newton steps.
 template <int MET>
@@ -448,6 +449,11 @@ __global__ void k_zone_method(DevParams p, BoxGeo bg, int n, const double* __res
     }
     ImpSys<MET> s;
     build_sys<MET>(p, g, Ust, hh[z], 1.0, s);
+    if (method >= 6) {  // the entropy-based PMHD, URAD, PRAD
+      s.entropy = true;
+      s.Sstar = Sst ? Sst[z] / g.gdet : 0.0;
+      method -= 6;
+    }
     double eT = HUGE_VAL;
     int steps = 0;
     if (method == 0 || method == 3) {

@@ -181,7 +181,7 @@ __global__ void k_zi_urad(hr::DevParams p, hr::BoxGeo bg, const double* __restri
     const bool subdom = radiation_subdominant<MET>(g, Us + NPR * (size_t)z, P0);
     int method = retry_sequence<MET>(p, g, s, P0, bx, beT, tau, Pn, &eT, &steps, subdom);
     if (method == ST_BACKUP) {  // the cold-MHD equations (no explicit entropy here)
-      const int by = backup_equations<MET>(p, g, s, Us + NPR * (size_t)z, P0, NAN, false, tau, Pn, &eT, &steps);
+      const int by = backup_equations<MET>(p, g, s, Us + NPR * (size_t)z, P0, NAN, 0, tau, Pn, &eT, &steps);
       if (by) method = by;
     }
     for (int q = 0; q < NPR; ++q) Pout[NPR * z + q] = Pn[q];

@@ -522,8 +522,8 @@ def zone_implicit(cfg, x, Ustar, Ps, h, Sstar=None):
 
 def zone_method(cfg, x, Ustar, Ps, h, method, Sstar=None):
     """One Newton method alone on n zones (0 PMHD, 1 URAD, 2 PRAD, 3 staged
-    PMHD, 4 staged URAD, 5 staged PRAD): (P[n][12], e_T[n], steps[n]) as
-    numpy arrays."""
+    PMHD, 4 staged URAD, 5 staged PRAD, 6/7/8 the entropy-based PMHD, URAD,
+    PRAD, which need Sstar): (P[n][12], e_T[n], steps[n]) as numpy arrays."""
     import torch
     n = len(x)
     xd, Ud, Pd, hd = _dev(x), _dev(Ustar), _dev(Ps), _dev(np.broadcast_to(h, (n,)))

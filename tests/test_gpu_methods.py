@@ -1,7 +1,9 @@
 """Each Newton method of the implicit solve alone on the CUDA path
 (harmrad_zone_method) against the oracle's restatement of it (the seeded
 random states of tests/test_oracle_methods.py, Minkowski and Kerr-Schild):
-PMHD, URAD, PRAD (Sec. 4.8-4.10) and the staged PMHD, URAD and PRAD (Sec. 4.10).  The two
+PMHD, URAD, PRAD (Sec. 4.8-4.10), the staged PMHD, URAD and PRAD (Sec. 4.10) and
+the entropy-based PMHD, URAD and PRAD (Sec. 4.8, 4.11; the explicit entropy of
+the true state).  The two
 sides converge (e_T < 1e-9) on the same states up to a few near the
 threshold, and where both converge their roots agree to 1e-10 in the median;
 at worst to 1e-7 for PMHD and the staged PMHD (which stop at e_T < 1e-12) and
@@ -22,7 +24,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("metric", [0, 1])
-@pytest.mark.parametrize("method", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("method", [0, 1, 2, 3, 4, 5, 6, 7, 8])
 def test_method_matches_oracle(metric, method):
     cfg, x, P = W.random_states(120, seed=201 + metric, metric=metric, gamma_max=5.0, gamma_rad_max=3.0)
     cfg.update(kappa_abs0=3.0, kappa_es0=1.0)
@@ -38,9 +40,10 @@ def test_method_matches_oracle(metric, method):
     # the explicit entropy of the true state, S* = U_rho (n log p - (n + 1) log rho0)
     nad = 1.0 / (cfg["gam"] - 1.0)
     S = U[:, W.RHO] * (nad * np.log((cfg["gam"] - 1.0) * P[:, W.UU]) - (nad + 1.0) * np.log(P[:, W.RHO]))
-    ref = [O.method_zone(p, x[n], U[n], Ps[n], h[n], method, Sstar=S[n] if method == 3 else None)
+    use_s = method == 3 or method >= 6
+    ref = [O.method_zone(p, x[n], U[n], Ps[n], h[n], method, Sstar=S[n] if use_s else None)
            for n in range(len(x))]
-    Pg, eT, it = H.zone_method(cfg, x, U, Ps, h, method, Sstar=S if method == 3 else None)
+    Pg, eT, it = H.zone_method(cfg, x, U, Ps, h, method, Sstar=S if use_s else None)
     co = np.array([r[1] < 1e-9 for r in ref])
     cg = eT < 1e-9
     both = co & cg
@@ -50,4 +53,4 @@ def test_method_matches_oracle(metric, method):
           % (metric, method, co.sum(), cg.sum(), both.sum(), np.median(d), d.max()))
     assert abs(int(co.sum()) - int(cg.sum())) <= 0.05 * len(x)
     assert both.sum() > 0.5 * len(x)
-    assert np.median(d) < 1e-10 and d.max() < (1e-5 if method in (1, 2, 4, 5) else 1e-7)
+    assert np.median(d) < 1e-10 and d.max() < (1e-5 if method in (1, 2, 4, 5, 7, 8) else 1e-7)

@@ -147,3 +147,37 @@ def test_cold_fast_flow_takes_the_entropy_backup():
     print("cold fast box, first step:", c)
     assert c["entropy"] > 10 and c["entropy"] > c["backup"]
     assert np.isfinite(o.get_prims()).all()
+
+
+@pytest.mark.parametrize("metric", [0, 1])
+def test_entropy_radiation_methods_reach_the_entropy_root(metric):
+    """The entropy-based URAD and PRAD (Sec. 4.8: the entropy row and the three
+    radiation momentum rows as the error, the gas from total energy-momentum
+    conservation through the 1D_W inversion) solve the same equations as the
+    entropy PMHD (total conservation, the momentum equations and Eq. source6):
+    where both converge they reach its root, to 1e-9 in the median and 5e-5 at
+    worst (their tolerance is e_T < 1e-9, which bounds the residual, not each
+    primitive), on seeded states with the explicit entropy of the true state."""
+    cfg, x, P = W.random_states(120, seed=301 + metric, metric=metric, gamma_max=5.0, gamma_rad_max=3.0)
+    cfg.update(kappa_abs0=3.0, kappa_es0=1.0)
+    p = O.make_params(cfg)
+    g = W.rng(7)
+    h = 10 ** g.uniform(-3, 0, len(x))
+    nad = 1.0 / (cfg["gam"] - 1.0)
+    conv, diffs = np.zeros(3, dtype=int), {7: [], 8: []}
+    for n in range(len(x)):
+        U, _ = O.prim_to_cons(p, x[n], P[n])
+        S = U[RHO] * (nad * math.log((cfg["gam"] - 1.0) * P[n][UU]) - (nad + 1.0) * math.log(P[n][RHO]))
+        Ps = P[n].copy()
+        Ps[UU] *= 1.0 + 0.3 * g.uniform(-1, 1)
+        Ps[W.ER] *= 1.0 + 0.3 * g.uniform(-1, 1)
+        res = {m: O.method_zone(p, x[n], U, Ps, h[n], m, Sstar=S) for m in (6, 7, 8)}
+        conv += [res[m][1] < 1e-9 for m in (6, 7, 8)]
+        for m in (7, 8):
+            if res[6][1] < 1e-10 and res[m][1] < 1e-9:
+                idx = [RHO, UU, W.ER]
+                diffs[m].append(np.max(np.abs(res[m][0][idx] - res[6][0][idx]) / np.abs(res[6][0][idx])))
+    print("entropy PMHD/URAD/PRAD converged", conv, {m: (np.median(d), np.max(d)) for m, d in diffs.items()})
+    for m in (7, 8):
+        assert len(diffs[m]) > 0.5 * len(x)
+        assert np.median(diffs[m]) < 1e-9 and np.max(diffs[m]) < 5e-5
