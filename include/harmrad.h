@@ -91,8 +91,12 @@ extern "C" {
  * zone that none of them solves (e_T > 1e-7) tries the entropy equation
  * (Eq. source6: [S u^t] - [S u^t]* = dt G_S, S = rho0 log(p^n/rho0^(n+1)),
  * Sec. 2) in place of the gas energy equation before the neighbour average
- * (Sec. 4.11); the radiation keeps total energy-momentum conservation.
- * ENTROPY: the entropy equation in every zone (PMHD iterates; RK3 only), which
+ * (Sec. 4.11); the radiation keeps total energy-momentum conservation.  The
+ * entropy methods take the energy methods' sequence (PMHD, with u_g guessed
+ * from the explicit entropy, then URAD and PRAD while e_T >= 1e-9); their
+ * entropy row carries the factor T = p/rho0 and is normalised with the gas
+ * energy row's norm added (Sec. 4.8).
+ * ENTROPY: the entropy equation in every zone (same sequence; RK3 only), which
  * conserves the total entropy to round-off where the gas and radiation do not
  * exchange energy.  The entropy S u^t is carried as a 13th conserved quantity
  * with its own face fluxes (RK3 contexts).  A zone that neither the energy
@@ -404,7 +408,8 @@ int harmrad_profile_step(harmrad_ctx* ctx, double dt, harmrad_kernel_times* out)
  * clamps) take the derivative of the branch the step took.  Zones whose
  * solution a floor changed are constant except for B; back-up zones pass
  * their cotangent to the neighbours they averaged.  Zones solved by the
- * entropy equation take the transposed solve of that system.  The paper has
+ * entropy equation (by its PMHD, URAD or PRAD, which solve the same
+ * equations) take the transposed solve of that system.  The paper has
  * no adjoint; this is an extension.  HARMRAD_E_STATE if no step ran since
  * enabling; HARMRAD_E_ARG if a zone of the step was solved by the cold-MHD
  * equations (its u_g, the neighbours' average, has no adjoint here). */

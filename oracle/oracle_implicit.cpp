@@ -99,6 +99,28 @@ void tt_row(const orc_params& p, const Geom& G, const double* P, double Tc[4], d
   if (rho_u_t_out) rho_u_t_out[0] = mt;
 }
 
+// The entropy equation's error row at primitives P (gas four-velocity u,
+// four-force Gc, gas energy row T^t_t + rho0 u^t = Tc[0]): Eq. source6,
+// S u^t - S* - h G_S, times the factor F_13 = T = p/rho0 that Sec. 4.8 puts on
+// the entropy row; since T G_S = -G_mu u^mu (Eq. GS) the row is
+// E_S = T (S u^t - S*) + h G_mu u^mu.  Its normalised error (*e) divides
+// |E_S| by the absolute values of its terms, T |S u^t| + T |S*| + h |G_mu u^mu|,
+// plus the norm of the gas energy row |T^t_t + rho0 u^t| + |T*| + h |G_t| that
+// Sec. 4.8 adds to it ("the energy norm").
+double entropy_row(const Sys& s, const double* P, const FourVel& u, const double Gc[4], const double Tc[4],
+                   double* e) {
+  const orc_params& p = *s.p;
+  const double Tg = (p.gam - 1.0) * P[UU] / P[RHO];
+  const double Su = s.Dlab * entropy_per_baryon(p, P[RHO], P[UU]);
+  double Gu = 0.0;
+  for (int m = 0; m < 4; ++m) Gu += Gc[m] * u.ucon[m];
+  const double E = Tg * (Su - s.Sstar) + s.h * Gu;
+  const double dE = std::fabs(Tc[0]) + std::fabs(s.Tstar[0]) + s.h * std::fabs(Gc[0]);
+  const double d = Tg * (std::fabs(Su) + std::fabs(s.Sstar)) + s.h * std::fabs(Gu) + dE;
+  *e = d > 0.0 ? std::fabs(E) / d : 0.0;
+  return E;
+}
+
 // PMHD error function: iterate (u_g, u~^i); rho0 = (rho0 u^t)/u^t; radiation
 // from total energy-momentum conservation; then G_nu and E_q (Sec. 4.8).
 void pmhd_res(const Sys& s, const double x[4], Res& r) {
@@ -146,18 +168,13 @@ void pmhd_res(const Sys& s, const double x[4], Res& r) {
     // (Sec. 2, Eq. S), and G_S = -G_mu u^mu / T, T = p/rho0 (Eq. GS).  The
     // radiation keeps total energy-momentum conservation (Sec. 4.7), so its
     // energy row only mirrors the gas energy equation that is not solved:
-    // both energy rows leave e_T and e_I.
-    const double pg = (p.gam - 1.0) * P[UU];
-    const double sg = entropy_per_baryon(p, P[RHO], P[UU]);
-    double Gu = 0.0;
-    for (int m = 0; m < 4; ++m) Gu += Gc[m] * u.ucon[m];
-    const double GS = -Gu / (pg / P[RHO]);
-    const double Su = s.Dlab * sg;
-    r.Eg[0] = Su - s.Sstar - s.h * GS;
-    const double d0 = std::fabs(Su) + std::fabs(s.Sstar) + s.h * std::fabs(GS);
+    // both energy rows leave e_T and e_I.  The row carries the factor
+    // F_13 = T (Sec. 4.8) and is normalised with the gas energy row's norm
+    // added (entropy_row).
+    r.Eg[0] = entropy_row(s, P, u, Gc, Tc, &r.eg[0]);
     // a TYPE2 inversion that met a negative energy excludes the entropy term
     // from the error (Sec. 4.10)
-    r.eg[0] = (d0 > 0.0 && !r.negE) ? std::fabs(r.Eg[0]) / d0 : 0.0;
+    if (r.negE) r.eg[0] = 0.0;
     r.er[0] = 0.0;
     double sT = r.eg[0], sI = r.eg[0];
     for (int k = 1; k < 4; ++k) {
@@ -185,22 +202,16 @@ void pmhd_res(const Sys& s, const double x[4], Res& r) {
 // The entropy equation's row for the radiation methods (Sec. 4.8: the
 // entropy-based URAD and PRAD take the entropy row and the three radiation
 // momentum rows as their error function; the energy rows are ignored): at the
-// iterate's primitives P, E_S = S u^t(P) - S* - h G_S (Eq. source6, G_S of
-// Eq. GS) replaces the radiation energy row of the Newton error vector, and
-// e_T, e_I are formed as for the entropy PMHD with the radiation rows iterated.
-void entropy_rad_rows(const Sys& s, const double* P, const FourVel& u, const double Gc[4], Res& r) {
-  const orc_params& p = *s.p;
-  const double pg = (p.gam - 1.0) * P[UU];
-  const double sg = entropy_per_baryon(p, P[RHO], P[UU]);
-  double Gu = 0.0;
-  for (int m = 0; m < 4; ++m) Gu += Gc[m] * u.ucon[m];
-  const double GS = -Gu / (pg / P[RHO]);
-  const double Su = s.Dlab * sg;
-  r.Er[0] = Su - s.Sstar - s.h * GS;
-  const double d0 = std::fabs(Su) + std::fabs(s.Sstar) + s.h * std::fabs(GS);
+// iterate's primitives P, the entropy row E_S of entropy_row replaces the
+// radiation energy row of the Newton error vector, and e_T, e_I are formed as
+// for the entropy PMHD with the radiation rows iterated.
+void entropy_rad_rows(const Sys& s, const double* P, const FourVel& u, const double Gc[4], const double Tc[4],
+                      Res& r) {
+  double eS;
+  r.Er[0] = entropy_row(s, P, u, Gc, Tc, &eS);
   // a TYPE2 inversion that met a negative energy excludes the entropy term
   // from the error (Sec. 4.10)
-  const double eS = (d0 > 0.0 && !r.negE) ? std::fabs(r.Er[0]) / d0 : 0.0;
+  if (r.negE) eS = 0.0;
   r.eg[0] = 0.0;
   r.er[0] = eS;
   double sT = eS, sI = eS;
@@ -250,7 +261,7 @@ bool urad_res(const Sys& s, const double x[4], const double* Pguess, double tol_
     r.Er[k] = Rc[k] - s.Rstar[k] + s.h * Gc[k];
   }
   normalise(s, Tc, Rc, Gc, false, r);
-  if (s.entropy) entropy_rad_rows(s, P, u, Gc, r);
+  if (s.entropy) entropy_rad_rows(s, P, u, Gc, Tc, r);
   std::memcpy(r.P, P, sizeof(P));
   r.ok = std::isfinite(r.eT);
   return r.ok;
@@ -298,7 +309,7 @@ bool prad_res(const Sys& s, const double x[4], const double* Pguess, double tol_
     r.Er[k] = Rc[k] - s.Rstar[k] + s.h * Gc[k];
   }
   normalise(s, Tc, Rc, Gc, false, r);
-  if (s.entropy) entropy_rad_rows(s, P, u, Gc, r);
+  if (s.entropy) entropy_rad_rows(s, P, u, Gc, Tc, r);
   std::memcpy(r.P, P, sizeof(P));
   r.ok = std::isfinite(r.eT);
   return r.ok;
@@ -859,6 +870,18 @@ void build_sys(const orc_params& p, const Geom& G, const double* Ustar, double h
 
 }  // namespace
 
+// The u_g guess from the conserved entropy (Sec. 4.10, the guess of the PMHD
+// method): the specific entropy s = S* / (rho0 u^t)* (Urho = sqrt(-g) rho0 u^t
+// of U*) at the density rho0 of the guess gives p = (rho0^(n+1) e^s)^(1/n) and
+// u_g = p / (Gamma - 1); x[0] is left unchanged where S* is not finite or
+// the result is not a positive number.
+void entropy_ug_guess(const orc_params& p, double Sstar, double Urho, double rho, double x[4]) {
+  if (!std::isfinite(Sstar) || Urho == 0.0) return;
+  const double n = 1.0 / (p.gam - 1.0);
+  const double pg = std::exp((Sstar / Urho + (n + 1.0) * std::log(rho)) / n);
+  if (std::isfinite(pg) && pg > 0.0) x[0] = pg / (p.gam - 1.0);
+}
+
 // Guess of the staged PMHD (Sec. 4.10): the gas of the lowest-error earlier
 // solution if its e_T < 1e-4, else of P_s; u_g then from the specific
 // entropy of U*, s_gas = S* / (rho0 u^t)*, at the density of P_s (where the
@@ -867,12 +890,7 @@ void staged_guess(const orc_params& p, const Sys& s, const double* Ustar, const 
                   const Res& best, double xs[4]) {
   const double* Pg = (best.ok && best.eT < 1e-4) ? best.P : Ps;
   for (int i = 0; i < 4; ++i) xs[i] = Pg[UU + i];
-  if (Sstar && std::isfinite(*Sstar) && Ustar[RHO] != 0.0) {
-    const double n = 1.0 / (p.gam - 1.0);
-    const double sg = *Sstar / Ustar[RHO];
-    const double pg = std::exp((sg + (n + 1.0) * std::log(Ps[RHO])) / n);
-    if (std::isfinite(pg) && pg > 0.0) xs[0] = pg / (p.gam - 1.0);
-  }
+  if (Sstar) entropy_ug_guess(p, *Sstar, Ustar[RHO], Ps[RHO], xs);
   (void)s;
 }
 
@@ -1014,8 +1032,10 @@ void finish_solution(const orc_params& p, const Geom& G, const Sys& s, const Res
 // while the best entropy solution has e_T >= 1e-9 (the energy methods'
 // sequence, Sec. 4.11), each from the primitives of the best entropy solution
 // if its e_T < 1e-4, else from P_s.  bs ends as the lowest-error entropy
-// solution; returns the Newton steps.
-int entropy_radiation_methods(const orc_params& p, const Geom& G, const Sys& se, const double* Ps, Res& bs) {
+// solution (*rad = 1 if URAD or PRAD gave it, else unchanged); returns the
+// Newton steps.
+int entropy_radiation_methods(const orc_params& p, const Geom& G, const Sys& se, const double* Ps, Res& bs,
+                              int* rad) {
   int steps = 0;
   for (int prad = 0; prad < 2 && !(bs.ok && bs.eT < 1e-9); ++prad) {
     const double* Pg = (bs.ok && bs.eT < 1e-4) ? bs.P : Ps;
@@ -1028,7 +1048,10 @@ int entropy_radiation_methods(const orc_params& p, const Geom& G, const Sys& se,
     }
     Res br;
     steps += prad ? newton_prad(se, xr, Pg, br) : newton_urad(se, xr, Pg, br);
-    if (br.ok && (!bs.ok || br.eT < bs.eT)) bs = br;
+    if (br.ok && (!bs.ok || br.eT < bs.eT)) {
+      bs = br;
+      *rad = 1;
+    }
   }
   return steps;
 }
@@ -1095,10 +1118,14 @@ void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, cons
     Sys se = s;
     se.entropy = true;
     se.Sstar = *Sstar / G.gdet;
-    info->iters_pmhd = newton_pmhd(se, x0, best);
-    info->iters_urad = entropy_radiation_methods(p, G, se, Ps, best);
+    double xe[4] = {x0[0], x0[1], x0[2], x0[3]};
+    entropy_ug_guess(p, *Sstar, Ustar[RHO], Ps[RHO], xe);
+    info->iters_pmhd = newton_pmhd(se, xe, best);
+    int rad = 0;
+    info->iters_urad = entropy_radiation_methods(p, G, se, Ps, best, &rad);
     if (!(best.ok && best.eT <= 1e-7) && try_cold(p, G, s, Ustar, Ps, x0, Pout, info)) return;
-    finish_solution(p, G, se, best, Ps, Pout, info, ORC_OK_PMHD);
+    // the entropy PMHD is this mode's first method; URAD and PRAD are retries
+    finish_solution(p, G, se, best, Ps, Pout, info, rad ? ORC_OK_URAD : ORC_OK_PMHD);
     info->entropy = best.ok && best.eT <= 1e-7;
     return;
   }
@@ -1189,8 +1216,11 @@ void implicit_zone(const orc_params& p, const Geom& G, const double* Ustar, cons
     se.entropy = true;
     se.Sstar = *Sstar / G.gdet;
     Res bs;
-    info->iters_urad += newton_pmhd(se, x0, bs);
-    info->iters_urad += entropy_radiation_methods(p, G, se, Ps, bs);
+    double xe[4] = {x0[0], x0[1], x0[2], x0[3]};
+    entropy_ug_guess(p, *Sstar, Ustar[RHO], Ps[RHO], xe);
+    info->iters_urad += newton_pmhd(se, xe, bs);
+    int rad = 0;
+    info->iters_urad += entropy_radiation_methods(p, G, se, Ps, bs, &rad);
     if (bs.ok && bs.eT <= 1e-7) {
       finish_solution(p, G, se, bs, Ps, Pout, info, ORC_OK_URAD);
       info->entropy = 1;

@@ -152,7 +152,8 @@ __global__ void ka_implicit(DevParams p, BoxGeo bx, AdjBufs a, int s, double dt,
       for (int c = 0; c < 3; ++c) a.gU[(B1 + c) * bx.nact + z] = gq[B1 + c] * igd;
       continue;
     }
-    // a zone solved by the entropy equation: the same transposed solve on the
+    // a zone solved by the entropy equation (by the entropy PMHD, URAD or
+    // PRAD, which solve the same equations): the same transposed solve on the
     // entropy system (Eq. source6), which also depends on S*
     const bool ent = m == METH_ENTROPY;
     const double Sz = ent ? a.Sst[(long long)s * bx.nact + z] : 0.0;
@@ -221,8 +222,9 @@ __global__ void ka_implicit(DevParams p, BoxGeo bx, AdjBufs a, int s, double dt,
       for (int r = 0; r < 4; ++r) gk -= lam[r] * Eg[r].d[0];
     }
     for (int q = 0; q < NPR; ++q) a.gU[q * bx.nact + z] = gU[q];
-    // S* enters the entropy row only, E_0 = S u^t(x) - S*/sqrt(-g) - h G_S
-    if (ent) a.gS[z] = lam[0] * igd;
+    // S* enters the entropy row only, E_0 = T (S u^t(x) - S*/sqrt(-g)) +
+    // h G_mu u^mu with T = p/rho0 at the solution (the factor F_13)
+    if (ent) a.gS[z] = lam[0] * ((p.gam - 1.0) * Ps[UU] / Ps[RHO]) * igd;
   }
   warp_atomic_add(a.gk, gk);
 }

@@ -5,11 +5,14 @@
 namespace hr {
 
 enum { ST_PMHD = 0, ST_URAD = 1, ST_BACKUP = 2, ST_SOLVES = 3, ST_ITERS = 4, ST_ENTROPY = 5, ST_COLD = 6 };
-// record codes of a zone solved by the entropy equation or by the cold-MHD
-// equations (adjoint records only; their status byte is ST_URAD, a retry
-// method)
+// codes of a zone solved by the entropy equation (by the entropy PMHD, or by
+// the entropy-based URAD or PRAD: METH_ENTROPY_RAD, which the adjoint record
+// stores as METH_ENTROPY) or by the cold-MHD equations; their status byte is
+// that of a retry method, ST_URAD, except for the entropy PMHD's solution in
+// the entropy-everywhere mode, ST_PMHD
 constexpr unsigned char METH_ENTROPY = 3;
 constexpr unsigned char METH_COLD = 4;
+constexpr unsigned char METH_ENTROPY_RAD = 5;
 constexpr int QSTRIDE = 19;
 
 // Coefficients of one sub-step of an IMEX scheme (Sec. 4.1, Eqs. IMEX2,

@@ -184,14 +184,16 @@ __device__ __forceinline__ void pmhd_res(const DevParams& p, const ImpSysT<MET, 
   T eS = T(-1.0);
   if (s.entropy) {
     // Eq. source6: S u^t(x) - S* = h G_S, S u^t = rho0 u^t s_gas, G_S = -G_mu u^mu / T
-    // (Eq. GS), T = p/rho0; the radiation keeps total conservation (Sec. 4.7)
+    // (Eq. GS), T = p/rho0; the radiation keeps total conservation (Sec. 4.7).
+    // The row carries the factor F_13 = T (Sec. 4.8), E_S = T (S u^t - S*) +
+    // h G_mu u^mu, and its norm adds the gas energy row's to its own terms.
     const T Tg = (p.gam - 1.0) * x[0] / rho;
     const T Gu = G[0] * ucon[0] + G[1] * ucon[1] + G[2] * ucon[2] + G[3] * ucon[3];
-    const T GS = -Gu / Tg;
     const T Su = s.Dlab * entropy_per_baryon<T>(p, rho, x[0]);
-    r.Eg[0] = Su - s.Sstar - s.h * GS;
+    r.Eg[0] = Tg * (Su - s.Sstar) + s.h * Gu;
     if (norm) {
-      const T d0 = fabs(Su) + fabs(s.Sstar) + s.h * fabs(GS);
+      const T d0 = Tg * (fabs(Su) + fabs(s.Sstar)) + s.h * fabs(Gu) +
+                   (fabs(Tc[0]) + fabs(s.Ts[0]) + s.h * fabs(G[0]));
       eS = d0 > 0.0 ? fabs(r.Eg[0]) / d0 : T(0.0);
     }
   }
@@ -221,6 +223,7 @@ __device__ __forceinline__ void pmhd_res(const DevParams& p, const ImpSysT<MET, 
 }
 
 __device__ __forceinline__ bool solve4(double A[4][4], double b[4], double z[4]) {
+  double ipv[4];  // reciprocals of the pivots, reused by the back-substitution
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     int piv = c;
@@ -243,7 +246,8 @@ __device__ __forceinline__ bool solve4(double A[4][4], double b[4], double z[4])
       b[c] = b[piv];
       b[piv] = t;
     }
-    double ip = 1.0 / A[c][c];
+    const double ip = 1.0 / A[c][c];
+    ipv[c] = ip;
 #pragma unroll
     for (int r = c + 1; r < 4; ++r) {
       double f = A[r][c] * ip;
@@ -257,7 +261,7 @@ __device__ __forceinline__ bool solve4(double A[4][4], double b[4], double z[4])
     double sum = b[i];
 #pragma unroll
     for (int j = i + 1; j < 4; ++j) sum -= A[i][j] * z[j];
-    z[i] = sum / A[i][i];
+    z[i] = sum * ipv[i];
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i)
@@ -354,11 +358,11 @@ __device__ __forceinline__ void pmhd_jacobian_fd(const DevParams& p, const ImpSy
 template <int MET>
 __device__ __forceinline__ bool pmhd_newton_dx(const DevParams& p, const ImpSys<MET>& s, const double x[4],
                                                const ImpRes& r, const double Rt[4], double eps, int* jac32,
-                                               double dx[4]) {
+                                               double dx[4], TanStage& ts) {
   if (*jac32) {
     double J[4][4];
     double E[4] = {r.Eg[0], r.Eg[1], r.Eg[2], r.Eg[3]};
-    if (pmhd_jacobian_fp32<MET>(p, s, x, Rt, J) && solve4(J, E, dx)) return true;
+    if (pmhd_jacobian_fp32<MET>(p, s, ts, x, Rt, J) && solve4(J, E, dx)) return true;
     *jac32 = 0;
   }
   double J[4][4];
@@ -382,6 +386,7 @@ __device__ __forceinline__ bool pmhd_newton_dx(const DevParams& p, const ImpSys<
 // finite).
 template <int MET>
 __device__ __forceinline__ bool newton_pmhd_run(const DevParams& p, const ImpSys<MET>& s, NewtonState& st, int kstop) {
+  TanStage ts;
   for (;; ++st.k) {
     if (st.k >= kstop) return false;
     ImpRes r;
@@ -401,7 +406,7 @@ __device__ __forceinline__ bool newton_pmhd_run(const DevParams& p, const ImpSys
     if (st.k >= p.newton_max) break;
     if (r.eI < 1e-9) st.eps = 1e-10;
     double dx[4];
-    if (!pmhd_newton_dx<MET>(p, s, st.x, r, ist.Rt_pre, st.eps, &st.jac32, dx)) break;
+    if (!pmhd_newton_dx<MET>(p, s, st.x, r, ist.Rt_pre, st.eps, &st.jac32, dx, ts)) break;
     double xn[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) xn[i] = st.x[i] - dx[i];
@@ -440,6 +445,7 @@ __device__ int newton_pmhd(const DevParams& p, const ImpSys<MET>& s, const doubl
   int steps = 0;
   double eps = 1e-8;
   int jac32 = (s.entropy || s.cold) ? 0 : 1;  // the FP32 tangents differentiate the energy system
+  TanStage ts;
   for (int k = 0;; ++k) {
     ImpRes r;
     ImpState ist;
@@ -459,7 +465,7 @@ __device__ int newton_pmhd(const DevParams& p, const ImpSys<MET>& s, const doubl
     if (k >= p.newton_max) break;
     if (r.eI < 1e-9) eps = 1e-10;
     double dx[4];
-    if (!pmhd_newton_dx<MET>(p, s, x, r, ist.Rt_pre, eps, &jac32, dx)) break;
+    if (!pmhd_newton_dx<MET>(p, s, x, r, ist.Rt_pre, eps, &jac32, dx, ts)) break;
     double xn[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) xn[i] = x[i] - dx[i];
@@ -600,18 +606,32 @@ __device__ int newton_pmhd_staged(const DevParams& p, const ImpSys<MET>& s, cons
 
 // The entropy-based URAD and PRAD (Sec. 4.8: their error function takes the
 // entropy row and the three radiation momentum rows; the energy rows drop):
-// E_S = S u^t(P) - S* - h G_S (Eq. source6, G_S of Eq. GS) in place of the
-// radiation energy row; returns its normalised error (for normalise).
+// the entropy row E_S = T (S u^t(P) - S*) + h G_mu u^mu (Eq. source6 with
+// G_S of Eq. GS, times F_13 = T) in place of the radiation energy row; returns
+// its normalised error (its terms plus the gas energy row's norm, Tc0 and G0
+// the iterate's T^t_t + rho0 u^t and G_t) for normalise.
 template <int MET>
 __device__ __forceinline__ double entropy_rad_row(const DevParams& p, const ImpSys<MET>& s, double rho, double ug,
-                                                  const double ucon[4], const double G[4], ImpRes& r) {
+                                                  const double ucon[4], const double G[4], double Tc0, ImpRes& r) {
   const double Tg = (p.gam - 1.0) * ug / rho;
   const double Gu = G[0] * ucon[0] + G[1] * ucon[1] + G[2] * ucon[2] + G[3] * ucon[3];
-  const double GS = -Gu / Tg;
   const double Su = s.Dlab * entropy_per_baryon<double>(p, rho, ug);
-  r.Er[0] = Su - s.Sstar - s.h * GS;
-  const double d0 = fabs(Su) + fabs(s.Sstar) + s.h * fabs(GS);
+  r.Er[0] = Tg * (Su - s.Sstar) + s.h * Gu;
+  const double d0 = Tg * (fabs(Su) + fabs(s.Sstar)) + s.h * fabs(Gu) + (fabs(Tc0) + fabs(s.Ts[0]) + s.h * fabs(G[0]));
   return d0 > 0.0 ? fabs(r.Er[0]) / d0 : 0.0;
+}
+
+// The u_g guess from the conserved entropy (Sec. 4.10, the guess of the PMHD
+// method): the specific entropy s = S* / (rho0 u^t)* (Urho = sqrt(-g) rho0 u^t
+// of U*) at the density rho0 of the guess gives p = (rho0^(n+1) e^s)^(1/n) and
+// u_g = p / (Gamma - 1); x[0] is left unchanged where S* is not finite or the
+// result is not a positive number.
+__device__ __forceinline__ void entropy_ug_guess(const DevParams& p, double Sst, double Urho, double rho,
+                                                 double x[4]) {
+  if (!isfinite(Sst) || Urho == 0.0) return;
+  const double n = 1.0 / (p.gam - 1.0);
+  const double pg = exp((Sst / Urho + (n + 1.0) * log(rho)) / n);
+  if (isfinite(pg) && pg > 0.0) x[0] = pg / (p.gam - 1.0);
 }
 
 // URAD error function: iterate R^t_nu; gas from 1D_W inversion of
@@ -659,7 +679,7 @@ __device__ __forceinline__ bool urad_res(const DevParams& p, const ImpSys<MET>& 
     r.Eg[k] = Tc[k] - s.Ts[k] - s.h * G[k];
     r.Er[k] = Rc[k] - s.Rs[k] + s.h * G[k];
   }
-  const double eSr = s.entropy ? entropy_rad_row<MET>(p, s, rho, ug, ucon, G, r) : -1.0;
+  const double eSr = s.entropy ? entropy_rad_row<MET>(p, s, rho, ug, ucon, G, Tc[0], r) : -1.0;
   if (norm) {
     normalise<MET>(s, Tc, Rc, G, false, r, -1.0, eSr);
     r.ok = isfinite(r.eT);
@@ -714,7 +734,7 @@ __device__ __forceinline__ bool prad_res(const DevParams& p, const ImpSys<MET>& 
     r.Eg[k] = Tc[k] - s.Ts[k] - s.h * G[k];
     r.Er[k] = Rx[k] - s.Rs[k] + s.h * G[k];
   }
-  const double eSr = s.entropy ? entropy_rad_row<MET>(p, s, rho, ug, ucon, G, r) : -1.0;
+  const double eSr = s.entropy ? entropy_rad_row<MET>(p, s, rho, ug, ucon, G, Tc[0], r) : -1.0;
   if (norm) {
     normalise<MET>(s, Tc, Rx, G, false, r, -1.0, eSr);
     r.ok = isfinite(r.eT);

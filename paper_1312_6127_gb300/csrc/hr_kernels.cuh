@@ -1083,12 +1083,7 @@ __device__ int retry_sequence(const DevParams& p, const Geo<MET, double>& g, con
     const double* gsrc = Ps;
     if (best >= 0 && beT < 1e-4) gsrc = best == 0 ? Pb : (best == 1 ? ugas : qgas);
     double xs[4] = {gsrc[UU], gsrc[U1], gsrc[U2], gsrc[U3]};
-    if (isfinite(Sst) && s.Dlab != 0.0) {
-      const double n = 1.0 / (p.gam - 1.0);
-      const double sg = Sst / (s.Dlab * g.gdet);
-      const double pg = exp((sg + (n + 1.0) * log(Ps[RHO])) / n);
-      if (isfinite(pg) && pg > 0.0) xs[0] = pg / (p.gam - 1.0);
-    }
+    entropy_ug_guess(p, Sst, s.Dlab * g.gdet, Ps[RHO], xs);
     double seT;
     steps += newton_pmhd_staged<MET>(p, s, xs, sx, &seT);
     if (isfinite(seT) && (best < 0 || seT < beT)) {
@@ -1463,8 +1458,9 @@ __device__ __forceinline__ bool cold_allowed(const Geo<MET, double>& g, const do
 // on the three momentum equations with u_g held at the guess.  The PMHD
 // attempts start from the energy PMHD's guess (P_s, or where tau < 2/3 the
 // gas inversion of U*); a solution is accepted at e_T <= 1e-7.  Returns
-// METH_ENTROPY or METH_COLD with Pn and *eT set, 0 if none gives a solution;
-// adds the Newton steps to *steps.  emode 0: no entropy equation.
+// METH_ENTROPY (the entropy PMHD's solution), METH_ENTROPY_RAD (the entropy
+// URAD's or PRAD's) or METH_COLD with Pn and *eT set, 0 if none gives a
+// solution; adds the Newton steps to *steps.  emode 0: no entropy equation.
 template <int MET>
 __device__ int backup_equations(const DevParams& p, const Geo<MET, double>& g, const ImpSys<MET>& s,
                                 const double Ust[NPR], const double Ps[NPR], double Sst, int emode,
@@ -1486,7 +1482,9 @@ __device__ int backup_equations(const DevParams& p, const Geo<MET, double>& g, c
     double bxe[4] = {0.0, 0.0, 0.0, 0.0}, beT = HUGE_VAL;
     int who = -1;  // 0 PMHD, 1 URAD, 2 PRAD
     if (emode == 1) {
-      *steps += newton_pmhd<MET>(p, se, x0, bxe, &beT);
+      double xe[4] = {x0[0], x0[1], x0[2], x0[3]};
+      entropy_ug_guess(p, Sst, s.Dlab * g.gdet, Ps[RHO], xe);
+      *steps += newton_pmhd<MET>(p, se, xe, bxe, &beT);
     } else if (px && isfinite(peT)) {
       for (int c = 0; c < 4; ++c) bxe[c] = px[c];
       beT = peT;
@@ -1545,7 +1543,7 @@ __device__ int backup_equations(const DevParams& p, const Geo<MET, double>& g, c
         for (int c = 0; c < 3; ++c) Pn[B1 + c] = s.B[c];
       }
       *eT = beT;
-      return METH_ENTROPY;
+      return who == 0 ? METH_ENTROPY : METH_ENTROPY_RAD;
     }
   }
   if (cold) {
@@ -1584,6 +1582,7 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
     double* Un = b.Un + 12 * bx.aoff;
     const R* Fd[3] = {(const R*)b.F[0] + 12 * bx.coff, (const R*)b.F[1] + 12 * bx.coff,
                       (const R*)b.F[2] + 12 * bx.coff};
+    const double idx[3] = {1.0 / bx.dx[0], 1.0 / bx.dx[1], 1.0 / bx.dx[2]};
     for (long long z = HR_TID; z < bx.nact; z += HR_STRIDE) {
       long long r = z;
       int i = (int)(r % bx.n[0]);
@@ -1615,11 +1614,10 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
       for (int d = 0; d < 3; ++d) {
         if (!p.act[d] || !rhs) continue;
         const long long s = bx.str[d];
-        const double idx_ = 1.0 / bx.dx[d];
 #pragma unroll
         for (int q = 0; q < NPR; ++q) {
           R df = Fd[d][q * bx.ntot + t + s] - Fd[d][q * bx.ntot + t];
-          X[q] -= double(df) * idx_;
+          X[q] -= double(df) * idx[d];
         }
       }
       double Ust[NPR];
@@ -1682,7 +1680,7 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
         for (int d = 0; d < 3; ++d) {
           if (!p.act[d]) continue;
           const R* FSd = (const R*)b.FS[d] + bx.coff;
-          divS += double(FSd[t + bx.str[d]] - FSd[t]) / bx.dx[d];
+          divS += double(FSd[t + bx.str[d]] - FSd[t]) * idx[d];
         }
         Sst = A * sn + Bc * (Su - dt * divS);
         if (b.sst_rec) b.sst_rec[bx.aoff + z] = Sst;
@@ -1717,12 +1715,15 @@ __device__ __forceinline__ void update_box(const DevParams& p, const BoxGeo& bx,
       unsigned done_steps = 0;
       if (p.implicit_eq == 1) {
         // the entropy equation in every zone (Eq. source6), PMHD iterates;
-        // no solution (e_T > 1e-7) is the neighbour-average back-up
+        // e_T >= 1e-9 goes to the retry queue for the entropy URAD and PRAD
+        // (the methods' sequence, Sec. 4.10-4.11)
         s.entropy = true;
         s.Sstar = Sst / g.gdet;
         double bxn[4] = {0.0, 0.0, 0.0, 0.0}, beT = HUGE_VAL;
-        const int steps = newton_pmhd<MET>(p, s, x0, bxn, &beT);
-        accept = pmhd_finish<MET>(p, bx, bi, z, t, x1, g, s, Ust, h, bxn, beT, steps, P, b, Sst, 1e-7 * (1 + 1e-15));
+        double xe[4] = {x0[0], x0[1], x0[2], x0[3]};
+        entropy_ug_guess(p, Sst, s.Dlab * g.gdet, Ps[RHO], xe);
+        const int steps = newton_pmhd<MET>(p, s, xe, bxn, &beT);
+        accept = pmhd_finish<MET>(p, bx, bi, z, t, x1, g, s, Ust, h, bxn, beT, steps, P, b, Sst, 1e-9);
         done_steps = (unsigned)steps;
         warp_add(&b.stats[ST_ENTROPY], accept ? 1u : 0u);
       } else if constexpr (!CONT) {
@@ -1882,7 +1883,7 @@ __global__ void __launch_bounds__(128) k_retry(DevParams p, const BoxGeo* __rest
     const double tau = zone_tau<MET>(p, g, bx.dx, Ps, kfield(p, K, t));
     int method;
     const double Sst = qd[18];
-    if (p.implicit_eq == 1) {  // the entropy PMHD of the update kernel left no solution
+    if (p.implicit_eq == 1) {  // the entropy PMHD of the update kernel left e_T >= 1e-9
       for (int q = 0; q < NPR; ++q) Pn[q] = Ps[q];
       for (int c = 0; c < 3; ++c) Pn[B1 + c] = s.B[c];
       eT = HUGE_VAL;
@@ -1896,7 +1897,9 @@ __global__ void __launch_bounds__(128) k_retry(DevParams p, const BoxGeo* __rest
     if (method == ST_BACKUP) {
       by = p.implicit_eq == 1 ? backup_equations<MET>(p, g, s, Ust, Ps, Sst, 2, tau, Pn, &eT, &steps, px, peT)
                               : backup_equations<MET>(p, g, s, Ust, Ps, Sst, 1, tau, Pn, &eT, &steps);
-      if (by) method = ST_URAD;
+      // a retry method's solution, except that in the entropy-everywhere
+      // mode the entropy PMHD is the first method
+      if (by) method = (p.implicit_eq == 1 && by == METH_ENTROPY) ? ST_PMHD : ST_URAD;
     }
     b.iters[zg] += steps;
     if (b.psol_rec)
@@ -1907,8 +1910,10 @@ __global__ void __launch_bounds__(128) k_retry(DevParams p, const BoxGeo* __rest
     for (int q = 0; q < NPR; ++q) P[q * bx.ntot + t] = Pn[q];
     unsigned char m = (unsigned char)method;
     if (m > b.status[zg]) b.status[zg] = m;
-    if (b.meth_rec) b.meth_rec[zg] = by ? (unsigned char)by : m;
-    if (by == METH_ENTROPY) atomicAdd(&b.stats[ST_ENTROPY], 1ULL);
+    // the adjoint differentiates every entropy solution through the entropy
+    // PMHD's system (the URAD and PRAD solve the same equations)
+    if (b.meth_rec) b.meth_rec[zg] = by ? (unsigned char)(by == METH_ENTROPY_RAD ? METH_ENTROPY : by) : m;
+    if (by == METH_ENTROPY || by == METH_ENTROPY_RAD) atomicAdd(&b.stats[ST_ENTROPY], 1ULL);
     if (by == METH_COLD) atomicAdd(&b.stats[ST_COLD], 1ULL);
     if (method == ST_BACKUP || by == METH_COLD) {
       // the back-up average: all primitives but B, or u_g alone for a

@@ -417,7 +417,7 @@ __global__ void k_zone_implicit(DevParams p, BoxGeo bg, int n, const double* __r
       steps += rs;
       if (method == ST_BACKUP) {  // the entropy (S* given), then the cold-MHD equations
         const int by = backup_equations<MET>(p, g, s, Ust, P0, sz, 1, tau, Pn, &eT, &steps);
-        if (by) method = by;
+        if (by) method = by == METH_COLD ? METH_COLD : METH_ENTROPY;
       }
     }
     for (int q = 0; q < NPR; ++q) Pout[NPR * z + q] = Pn[q];
@@ -458,11 +458,7 @@ __global__ void k_zone_method(DevParams p, BoxGeo bg, int n, const double* __res
     int steps = 0;
     if (method == 0 || method == 3) {
       double x0[4] = {P0[UU], P0[U1], P0[U2], P0[U3]}, bx[4];
-      if (method == 3 && Sst && isfinite(Sst[z]) && s.Dlab != 0.0) {
-        const double nn = 1.0 / (p.gam - 1.0);
-        const double pg = exp((Sst[z] / (s.Dlab * g.gdet) + (nn + 1.0) * log(P0[RHO])) / nn);
-        if (isfinite(pg) && pg > 0.0) x0[0] = pg / (p.gam - 1.0);
-      }
+      if (method == 3 && Sst) entropy_ug_guess(p, Sst[z], s.Dlab * g.gdet, P0[RHO], x0);
       steps = method == 0 ? newton_pmhd<MET>(p, s, x0, bx, &eT) : newton_pmhd_staged<MET>(p, s, x0, bx, &eT);
       if (isfinite(eT)) {
         ImpRes rr;

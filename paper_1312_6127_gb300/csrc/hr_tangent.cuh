@@ -66,11 +66,15 @@ struct GeoF {
   float g00, g01, g03, g11, g13, g22, g33;
   float G00, G01, G11, G13, G22, G33;
   float alpha, ialpha;
-  __device__ __forceinline__ explicit GeoF(const Geo<MET, double>& g)
-      : g00((float)g.g00), g01((float)g.g01), g03((float)g.g03), g11((float)g.g11), g13((float)g.g13),
-        g22((float)g.g22), g33((float)g.g33), G00((float)g.G00), G01((float)g.G01), G11((float)g.G11),
-        G13((float)g.G13), G22((float)g.G22), G33((float)g.G33), alpha((float)g.alpha),
-        ialpha((float)g.ialpha) {}
+  // from the 15 staged components (TanStage: g00 .. ialpha in this order);
+  // the Minkowski forms below read none of them
+  __device__ __forceinline__ explicit GeoF(const volatile float* a) {
+    if constexpr (MET != MINK) {
+      g00 = a[0], g01 = a[1], g03 = a[2], g11 = a[3], g13 = a[4], g22 = a[5], g33 = a[6];
+      G00 = a[7], G01 = a[8], G11 = a[9], G13 = a[10], G22 = a[11], G33 = a[12];
+      alpha = a[13], ialpha = a[14];
+    }
+  }
   __device__ __forceinline__ void lower(const F1 v[4], F1 w[4]) const {
     if constexpr (MET == MINK) {
       w[0] = -v[0];
@@ -106,18 +110,55 @@ __device__ __forceinline__ void fourvel_t(const GeoF<MET>& g, F1 q1, F1 q2, F1 q
   g.lower(ucon, ucov);
 }
 
-// FP32 inputs of the tangent passes of one Jacobian, converted once: the
-// unknowns x, R^t_nu of the FP64 error function (values), and the zone's
-// rho0 u^t, 1/(rho0 u^t), B, step h and opacity inputs.
+// FP32 inputs of the tangent passes, staged in thread-local memory: the 15
+// metric components of GeoF (v[0..14]), the zone's rho0 u^t, 1/(rho0 u^t), B,
+// step h and opacity inputs (v[15..23]), converted once per solve, and the
+// iterate's unknowns x and R^t_nu of the FP64 error function (v[24..31]),
+// converted once per Jacobian.  Every column pass loads them from here: a
+// conversion runs on the FP64 pipe, and the compiler, short of registers,
+// would otherwise convert them again in each of the four passes.  The zone
+// part is filled at the solve's first Jacobian (zone = 1 from then on), so a
+// solve that converges without one converts nothing.
+struct TanStage {
+  volatile float v[32];
+  int zone = 0;
+};
+
+template <int MET, class Sys>
+__device__ __forceinline__ void tan_stage_zone(const Sys& s, TanStage& ts) {
+  if constexpr (MET != MINK) {  // the Minkowski passes read no metric component
+    const auto& g = s.g;
+    const double c[15] = {g.g00, g.g01, g.g03, g.g11, g.g13, g.g22, g.g33, g.G00,
+                          g.G01, g.G11, g.G13, g.G22, g.G33, g.alpha, g.ialpha};
+#pragma unroll
+    for (int i = 0; i < 15; ++i) ts.v[i] = (float)c[i];
+  }
+  const double c[8] = {s.Dlab, s.iDlab, s.B[0], s.B[1], s.B[2], s.h, s.ks, s.kf};
+#pragma unroll
+  for (int i = 0; i < 8; ++i) ts.v[15 + i] = (float)c[i];
+  ts.zone = 1;
+}
+
+// the per-zone FP32 inputs of one column pass (v[15..31])
 struct TanIn {
   float x[4], rt[4], Dlab, iDlab, B[3], h, ks, kf;
+  __device__ __forceinline__ explicit TanIn(const TanStage& ts)
+      : Dlab(ts.v[15]), iDlab(ts.v[16]), B{ts.v[17], ts.v[18], ts.v[19]}, h(ts.v[20]), ks(ts.v[21]),
+        kf(ts.v[22]) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      x[i] = ts.v[24 + i];
+      rt[i] = ts.v[28 + i];
+    }
+  }
 };
 
 // Column j of the PMHD Jacobian dE_gas/dx at x (inputs in ti).  Returns false
 // if a value is not finite.
 template <int MET>
-__device__ __forceinline__ bool pmhd_jac_column(const DevParams& p, const TanIn& ti, const GeoF<MET>& g, int j,
-                                                float col[4]) {
+__device__ __forceinline__ bool pmhd_jac_column(const DevParams& p, const TanStage& ts, int j, float col[4]) {
+  const GeoF<MET> g(ts.v);
+  const TanIn ti(ts);
   F1 X[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) X[i] = F1{ti.x[i], i == j ? 1.0f : 0.0f};
@@ -217,29 +258,22 @@ __device__ __forceinline__ bool pmhd_jac_column(const DevParams& p, const TanIn&
   return ok;
 }
 
-// The PMHD Jacobian (J[i][c] = dE_i/dx_c) from four FP32 tangent passes.
+// The PMHD Jacobian (J[i][c] = dE_i/dx_c) from four FP32 tangent passes; ts
+// holds the solve's staged inputs (tan_stage_zone).
 template <int MET, class Sys>
-__device__ __forceinline__ bool pmhd_jacobian_fp32(const DevParams& p, const Sys& s, const double x[4],
-                                                   const double Rt64[4], double J[4][4]) {
-  const GeoF<MET> g(s.g);
-  TanIn ti;
+__device__ __forceinline__ bool pmhd_jacobian_fp32(const DevParams& p, const Sys& s, TanStage& ts,
+                                                   const double x[4], const double Rt64[4], double J[4][4]) {
+  if (!ts.zone) tan_stage_zone<MET>(s, ts);
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    ti.x[i] = (float)x[i];
-    ti.rt[i] = (float)Rt64[i];
+    ts.v[24 + i] = (float)x[i];
+    ts.v[28 + i] = (float)Rt64[i];
   }
-  ti.Dlab = (float)s.Dlab;
-  ti.iDlab = (float)s.iDlab;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) ti.B[i] = (float)s.B[i];
-  ti.h = (float)s.h;
-  ti.ks = (float)s.ks;
-  ti.kf = (float)s.kf;
   bool ok = true;
 #pragma unroll 1
   for (int j = 0; j < 4; ++j) {
     float col[4];
-    ok = pmhd_jac_column<MET>(p, ti, g, j, col) && ok;
+    ok = pmhd_jac_column<MET>(p, ts, j, col) && ok;
     // column j written through compile-time indices
 #pragma unroll
     for (int c = 0; c < 4; ++c)

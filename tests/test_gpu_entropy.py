@@ -47,12 +47,24 @@ def test_entropy_mode_matches_oracle_and_conserves_entropy(steps, tol):
 
 
 def test_entropy_mode_torus_matches_oracle():
+    """The entropy-everywhere torus, one step: the outcome of every zone as
+    in the oracle, and every zone within 1e-10 or, where the solve leaves u_g
+    less determined than that, within four times the oracle's own spread.  The
+    entropy row carries the factor T and is normalised with the gas energy
+    row's norm added (Sec. 4.8), so the Newton tolerance fixes u_g of the cold
+    atmosphere on that row's scale: the oracle's result moves by about 5e-10 in
+    u_g under a 1e-15 relative perturbation of its input (measured here)."""
     cfg, P = W.torus((32, 16, 8), seed=12345)
     cfg["implicit_eq"] = H.EQ_ENTROPY
     g, o = run_pair(cfg, P, 1)
-    e = zone_errors(cfg, g.get_prims(), o.get_prims())
-    print("entropy mode, torus, 1 step: per-zone error %.2e" % e.max())
-    assert e.max() < 1e-10
+    R = o.get_prims()
+    e = zone_errors(cfg, g.get_prims(), R)
+    o2 = O.Oracle(cfg)
+    o2.set_prims(P * (1.0 + 1e-15 * W.rng(17).standard_normal(P.shape)))
+    o2.step(o2.cfl_dt())
+    spread = zone_errors(cfg, o2.get_prims(), R).max()
+    print("entropy mode, torus, 1 step: per-zone error %.2e (the oracle's own spread %.2e)" % (e.max(), spread))
+    assert e.max() < max(1e-10, 4.0 * spread)
 
 
 def test_entropy_backup_matches_oracle():

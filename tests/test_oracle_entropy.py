@@ -154,13 +154,21 @@ def test_entropy_radiation_methods_reach_the_entropy_root(metric):
     """The entropy-based URAD and PRAD (Sec. 4.8: the entropy row and the three
     radiation momentum rows as the error, the gas from total energy-momentum
     conservation through the 1D_W inversion) solve the same equations as the
-    entropy PMHD (total conservation, the momentum equations and Eq. source6):
-    where both converge they reach its root, to 1e-9 in the median and 5e-5 at
-    worst (their tolerance is e_T < 1e-9, which bounds the residual, not each
-    primitive), on seeded states with the explicit entropy of the true state."""
+    entropy PMHD (total conservation, the momentum equations and Eq. source6),
+    on seeded states with the explicit entropy of the true state.  Where both
+    converge (e_T < 1e-9): their solution, put into the entropy PMHD's error
+    function as its only iterate, has e_T < 2e-9 there (the two error functions
+    take the radiation from different equations: conservation in PMHD, the
+    iterate in URAD and PRAD); rho0 agrees with
+    the entropy PMHD's root to 1e-7, and u_g to 1e-7 of u_g + |T^t_t + rho0 u^t|
+    (Sec. 4.8 normalises the entropy row, which carries the factor T, with the
+    gas energy row's norm added, so e_T bounds u_g on that scale: a plain
+    relative u_g difference can reach 1e-4 where u_g is 1e-5 of the energy
+    row)."""
     cfg, x, P = W.random_states(120, seed=301 + metric, metric=metric, gamma_max=5.0, gamma_rad_max=3.0)
     cfg.update(kappa_abs0=3.0, kappa_es0=1.0)
     p = O.make_params(cfg)
+    p0 = O.make_params(dict(cfg, newton_max=0))  # the error function at the guess alone
     g = W.rng(7)
     h = 10 ** g.uniform(-3, 0, len(x))
     nad = 1.0 / (cfg["gam"] - 1.0)
@@ -175,9 +183,15 @@ def test_entropy_radiation_methods_reach_the_entropy_root(metric):
         conv += [res[m][1] < 1e-9 for m in (6, 7, 8)]
         for m in (7, 8):
             if res[6][1] < 1e-10 and res[m][1] < 1e-9:
-                idx = [RHO, UU, W.ER]
-                diffs[m].append(np.max(np.abs(res[m][0][idx] - res[6][0][idx]) / np.abs(res[6][0][idx])))
-    print("entropy PMHD/URAD/PRAD converged", conv, {m: (np.median(d), np.max(d)) for m, d in diffs.items()})
+                a, b = res[m][0], res[6][0]
+                e6 = O.method_zone(p0, x[n], U, a, h[n], 6, Sstar=S)[1]
+                scale = b[UU] + abs(U[UU] / U[RHO]) * b[RHO]
+                diffs[m].append((e6, abs(a[RHO] - b[RHO]) / b[RHO], abs(a[UU] - b[UU]) / scale))
+    print("entropy PMHD/URAD/PRAD converged", conv,
+          {m: np.array(d).max(axis=0) for m, d in diffs.items()})
     for m in (7, 8):
-        assert len(diffs[m]) > 0.5 * len(x)
-        assert np.median(diffs[m]) < 1e-9 and np.max(diffs[m]) < 5e-5
+        d = np.array(diffs[m])
+        assert len(d) > 0.5 * len(x)
+        assert d[:, 0].max() < 2e-9
+        assert d[:, 1].max() < 1e-7 and d[:, 2].max() < 1e-7
+        assert np.median(d[:, 2]) < 1e-10
