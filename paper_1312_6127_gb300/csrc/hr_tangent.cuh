@@ -66,15 +66,11 @@ struct GeoF {
   float g00, g01, g03, g11, g13, g22, g33;
   float G00, G01, G11, G13, G22, G33;
   float alpha, ialpha;
-  // from the 15 staged components (TanStage: g00 .. ialpha in this order);
-  // the Minkowski forms below read none of them
-  __device__ __forceinline__ explicit GeoF(const volatile float* a) {
-    if constexpr (MET != MINK) {
-      g00 = a[0], g01 = a[1], g03 = a[2], g11 = a[3], g13 = a[4], g22 = a[5], g33 = a[6];
-      G00 = a[7], G01 = a[8], G11 = a[9], G13 = a[10], G22 = a[11], G33 = a[12];
-      alpha = a[13], ialpha = a[14];
-    }
-  }
+  __device__ __forceinline__ GeoF() {}  // Minkowski: the forms below read no component
+  // from the 15 staged components (TanStage: g00 .. ialpha in this order)
+  __device__ __forceinline__ explicit GeoF(const volatile float* a)
+      : g00(a[0]), g01(a[1]), g03(a[2]), g11(a[3]), g13(a[4]), g22(a[5]), g33(a[6]), G00(a[7]), G01(a[8]),
+        G11(a[9]), G13(a[10]), G22(a[11]), G33(a[12]), alpha(a[13]), ialpha(a[14]) {}
   __device__ __forceinline__ void lower(const F1 v[4], F1 w[4]) const {
     if constexpr (MET == MINK) {
       w[0] = -v[0];
@@ -110,7 +106,7 @@ __device__ __forceinline__ void fourvel_t(const GeoF<MET>& g, F1 q1, F1 q2, F1 q
   g.lower(ucon, ucov);
 }
 
-// FP32 inputs of the tangent passes, staged in thread-local memory: the 15
+// FP32 inputs of the Kerr-Schild tangent passes, staged in thread-local memory: the 15
 // metric components of GeoF (v[0..14]), the zone's rho0 u^t, 1/(rho0 u^t), B,
 // step h and opacity inputs (v[15..23]), converted once per solve, and the
 // iterate's unknowns x and R^t_nu of the FP64 error function (v[24..31]),
@@ -126,22 +122,31 @@ struct TanStage {
 
 template <int MET, class Sys>
 __device__ __forceinline__ void tan_stage_zone(const Sys& s, TanStage& ts) {
-  if constexpr (MET != MINK) {  // the Minkowski passes read no metric component
-    const auto& g = s.g;
-    const double c[15] = {g.g00, g.g01, g.g03, g.g11, g.g13, g.g22, g.g33, g.G00,
-                          g.G01, g.G11, g.G13, g.G22, g.G33, g.alpha, g.ialpha};
+  const auto& g = s.g;
+  const double m[15] = {g.g00, g.g01, g.g03, g.g11, g.g13, g.g22, g.g33, g.G00,
+                        g.G01, g.G11, g.G13, g.G22, g.G33, g.alpha, g.ialpha};
 #pragma unroll
-    for (int i = 0; i < 15; ++i) ts.v[i] = (float)c[i];
-  }
+  for (int i = 0; i < 15; ++i) ts.v[i] = (float)m[i];
   const double c[8] = {s.Dlab, s.iDlab, s.B[0], s.B[1], s.B[2], s.h, s.ks, s.kf};
 #pragma unroll
   for (int i = 0; i < 8; ++i) ts.v[15 + i] = (float)c[i];
   ts.zone = 1;
 }
 
-// the per-zone FP32 inputs of one column pass (v[15..31])
+// the FP32 inputs of one column pass: from the staged copy (v[15..31]), or,
+// on the Minkowski path, which has no metric to stage, converted in registers
 struct TanIn {
   float x[4], rt[4], Dlab, iDlab, B[3], h, ks, kf;
+  template <class Sys>
+  __device__ __forceinline__ TanIn(const Sys& s, const double xd[4], const double Rt64[4])
+      : Dlab((float)s.Dlab), iDlab((float)s.iDlab), B{(float)s.B[0], (float)s.B[1], (float)s.B[2]},
+        h((float)s.h), ks((float)s.ks), kf((float)s.kf) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      x[i] = (float)xd[i];
+      rt[i] = (float)Rt64[i];
+    }
+  }
   __device__ __forceinline__ explicit TanIn(const TanStage& ts)
       : Dlab(ts.v[15]), iDlab(ts.v[16]), B{ts.v[17], ts.v[18], ts.v[19]}, h(ts.v[20]), ks(ts.v[21]),
         kf(ts.v[22]) {
@@ -156,9 +161,8 @@ struct TanIn {
 // Column j of the PMHD Jacobian dE_gas/dx at x (inputs in ti).  Returns false
 // if a value is not finite.
 template <int MET>
-__device__ __forceinline__ bool pmhd_jac_column(const DevParams& p, const TanStage& ts, int j, float col[4]) {
-  const GeoF<MET> g(ts.v);
-  const TanIn ti(ts);
+__device__ __forceinline__ bool pmhd_jac_column(const DevParams& p, const TanIn& ti, const GeoF<MET>& g, int j,
+                                                float col[4]) {
   F1 X[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) X[i] = F1{ti.x[i], i == j ? 1.0f : 0.0f};
@@ -259,27 +263,42 @@ __device__ __forceinline__ bool pmhd_jac_column(const DevParams& p, const TanSta
 }
 
 // The PMHD Jacobian (J[i][c] = dE_i/dx_c) from four FP32 tangent passes; ts
-// holds the solve's staged inputs (tan_stage_zone).
+// holds the solve's staged inputs (tan_stage_zone; Kerr-Schild only).
+__device__ __forceinline__ void jac_store_column(double J[4][4], int j, const float col[4]) {
+  // column j written through compile-time indices
+#pragma unroll
+  for (int c = 0; c < 4; ++c)
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (c == j) J[i][c] = (double)col[i];
+}
+
 template <int MET, class Sys>
 __device__ __forceinline__ bool pmhd_jacobian_fp32(const DevParams& p, const Sys& s, TanStage& ts,
                                                    const double x[4], const double Rt64[4], double J[4][4]) {
-  if (!ts.zone) tan_stage_zone<MET>(s, ts);
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    ts.v[24 + i] = (float)x[i];
-    ts.v[28 + i] = (float)Rt64[i];
-  }
   bool ok = true;
+  if constexpr (MET == MINK) {
+    const TanIn ti(s, x, Rt64);
+    const GeoF<MET> g;
 #pragma unroll 1
-  for (int j = 0; j < 4; ++j) {
-    float col[4];
-    ok = pmhd_jac_column<MET>(p, ts, j, col) && ok;
-    // column j written through compile-time indices
+    for (int j = 0; j < 4; ++j) {
+      float col[4];
+      ok = pmhd_jac_column<MET>(p, ti, g, j, col) && ok;
+      jac_store_column(J, j, col);
+    }
+  } else {
+    if (!ts.zone) tan_stage_zone<MET>(s, ts);
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        if (c == j) J[i][c] = (double)col[i];
+    for (int i = 0; i < 4; ++i) {
+      ts.v[24 + i] = (float)x[i];
+      ts.v[28 + i] = (float)Rt64[i];
+    }
+#pragma unroll 1
+    for (int j = 0; j < 4; ++j) {
+      float col[4];
+      ok = pmhd_jac_column<MET>(p, TanIn(ts), GeoF<MET>(ts.v), j, col) && ok;
+      jac_store_column(J, j, col);
+    }
   }
   return ok;
 }
