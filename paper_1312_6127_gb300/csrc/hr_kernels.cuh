@@ -656,9 +656,10 @@ __device__ __forceinline__ void face_flux(const DevParams& p, const Geo<MET, R>&
                                           unsigned* code = nullptr, R* fs = nullptr, R* gas = nullptr) {
   R sL[4], sR[4];
   unsigned cL = 0, cR = 0;
-  R lL[2], lR[2];  // Lorentz factors of the states, for face_accum
-  face_speeds<MET, R>(p, g, d + 1, dxd, kL, ks, PL, sL, code ? &cL : nullptr, lL);
-  face_speeds<MET, R>(p, g, d + 1, dxd, kR, ks, PR, sR, code ? &cR : nullptr, lR);
+  R lL[3], lR[3];  // Lorentz factors and 1/u^t of the states, for face_accum
+  const R dl = sqrt(g.gdd(d + 1)) * dxd;  // proper cell length along d, for the optical depth
+  face_speeds<MET, R>(p, g, d + 1, dl, kL, ks, PL, sL, code ? &cL : nullptr, lL);
+  face_speeds<MET, R>(p, g, d + 1, dl, kR, ks, PR, sR, code ? &cR : nullptr, lR);
   R cmaxg = fmax(R(0), fmax(sL[1], sR[1]));
   R cming = -fmin(R(0), fmin(sL[0], sR[0]));
   R cmaxr = fmax(R(0), fmax(sL[3], sR[3]));

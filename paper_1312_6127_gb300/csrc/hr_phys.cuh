@@ -278,8 +278,9 @@ __device__ __forceinline__ R entropy_per_baryon(const DevParams& p, R rho, R ug)
     // n = 3/2: p^n / rho^(n+1) = x sqrt(x) / rho with x = p / rho, one
     // logarithm (FP64 only: the product would leave FP32's range first)
     if (p.gam == 5.0 / 3.0) {
-      const R x = R(2.0 / 3.0) * ug / rho;
-      return log(x * sqrt(x) / rho);
+      const R ir = R(1) / rho;
+      const R x = R(2.0 / 3.0) * ug * ir;
+      return log(x * sqrt(x) * ir);
     }
   }
   const R n = R(1.0 / (p.gam - 1.0));
@@ -409,12 +410,13 @@ __device__ __forceinline__ void face_state(const DevParams& p, const Geo<MET, R>
 }
 
 // Gas and radiation signal speeds (vmin, vmax) of one reconstructed state;
-// dxd is the cell size along d and kf the per-zone opacity of the state's cell.
-// lor (optional) returns the gas and radiation Lorentz factors for
+// dl = sqrt(g_dd) dx^d is the proper length of the cell along d (the same for
+// both states of a face) and kf the per-zone opacity of the state's cell.
+// lor (optional) returns the gas and radiation Lorentz factors and 1/u^t for
 // face_accum.  b^2 = (B^i B_i + (B^i u_i)^2) / (u^t)^2 (the identity behind
 // b^t = B^i u_i, b^i = (B^i + b^t u^i)/u^t), without forming b^mu.
 template <int MET, typename R>
-__device__ __forceinline__ void face_speeds(const DevParams& p, const Geo<MET, R>& g, int d, R dxd,
+__device__ __forceinline__ void face_speeds(const DevParams& p, const Geo<MET, R>& g, int d, R dl,
                                             R kf, R ks, const R P[NPR], R sp[4], unsigned* code = nullptr,
                                             R* lor = nullptr) {
   R ucon[4], ucov[4], gm;
@@ -425,8 +427,15 @@ __device__ __forceinline__ void face_speeds(const DevParams& p, const Geo<MET, R
   const R rho = P[RHO], ug = P[UU];
   const R pg = R(p.gam - 1.0) * ug;
   const R w = rho + ug + pg;
-  R cs2 = R(p.gam) * pg / w;
-  R va2 = bsq / (w + bsq);
+  R cs2, va2;
+  if constexpr (std::is_same<R, double>::value) {  // one division (w^2 stays in FP64's range)
+    const R iw = R(1) / (w * (w + bsq));
+    cs2 = R(p.gam) * pg * (w + bsq) * iw;
+    va2 = bsq * w * iw;
+  } else {
+    cs2 = R(p.gam) * pg / w;
+    va2 = bsq / (w + bsq);
+  }
   R cms2 = cs2 + va2 - cs2 * va2;
   if (code) *code = (cms2 > R(1) ? 1u : 0u) | (cms2 < R(0) ? 2u : 0u);
   cms2 = cms2 > R(1) ? R(1) : (cms2 < R(0) ? R(0) : cms2);
@@ -436,10 +445,11 @@ __device__ __forceinline__ void face_speeds(const DevParams& p, const Geo<MET, R
   if (lor) {
     lor[0] = gm;
     lor[1] = gr;
+    lor[2] = iut;
   }
   R kabs, ksca;
   opacity<R>(p, rho, ug, kf, &kabs, &ksca, ks);
-  R tau = (kabs + ksca) * sqrt(g.gdd(d)) * dxd;
+  R tau = (kabs + ksca) * dl;
   R cr2 = R(1.0 / 3.0);
   if (tau > R(0)) {
     R lim = R(4.0 / 3.0) / tau;
@@ -453,7 +463,9 @@ __device__ __forceinline__ void face_speeds(const DevParams& p, const Geo<MET, R
 // out[q] += aF_q F_q + aU_q U_q for one reconstructed state, with (aF, aU)
 // taking the gas values for q < 8 and the radiation values for q >= 8.  HLL
 // and LAXF are linear in (F_L, U_L, F_R, U_R), so each state adds its own
-// share and the two states' U and F never need to be held together.
+// share and the two states' U and F never need to be held together.  lor
+// (optional): the state's gas and radiation Lorentz factors and 1/u^t from
+// face_speeds.
 template <int MET, typename R>
 __device__ __forceinline__ void face_accum(const DevParams& p, const Geo<MET, R>& g, int d,
                                            const R P[NPR], R aFg, R aUg, R aFr, R aUr, R out[NPR],
@@ -465,7 +477,7 @@ __device__ __forceinline__ void face_accum(const DevParams& p, const Geo<MET, R>
   } else {
     fourvel<MET, R>(g, P[U1], P[U2], P[U3], ucon, ucov, &gm);
   }
-  const R iut = g.alpha / gm;
+  const R iut = lor ? lor[2] : g.alpha / gm;
   bvec_iut<MET, R>(g, ucon, ucov, iut, P[B1], P[B2], P[B3], bcon, bcov, &bsq);
   const R rho = P[RHO], ug = P[UU];
   const R pg = R(p.gam - 1.0) * ug;
